@@ -1,0 +1,274 @@
+"""FP64 CPU oracle for the ES adaptive moving-mesh scheme (2D RHD).
+
+TEST INFRASTRUCTURE.  This package is the independent checker of the CUDA
+library: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import it.  It shares no code with the CUDA path; the C
+source ``esmm_oracle.c`` restates the paper (Duan & Tang, arXiv 2107.12027)
+one node, pair and interface at a time.
+
+Array conventions match the C header: structure of arrays, ``[comp][j][i]``
+with ``i`` fastest, FP64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "esmm_oracle.c")
+_HDR = os.path.join(_HERE, "esmm_oracle.h")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PERIODIC, OUTFLOW = 0, 1
+MONITOR_RHO, MONITOR_LNRHO = 0, 1
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("bc", ctypes.c_int * 2),
+        ("period", ctypes.c_double * 2),
+        ("gamma", ctypes.c_double),
+        ("p", ctypes.c_int), ("w", ctypes.c_int),
+        ("weno_eps", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("monitor", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("n_filter", ctypes.c_int),
+        ("mu", ctypes.c_int),
+        ("move_mesh", ctypes.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build/liboracle.so``."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    newer = (os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
+             and os.path.getmtime(_LIB) >= os.path.getmtime(_HDR))
+    if force or not newer:
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        # -ffp-contract=off: every product and sum is rounded as written.
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            d = ctypes.POINTER(ctypes.c_double)
+            i = ctypes.POINTER(ctypes.c_int)
+            c = ctypes.POINTER(Cfg)
+            sig = {
+                "oref_alpha": (None, [ctypes.c_int, d]),
+                "oref_logmean": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+                "oref_prim2cons": (None, [ctypes.c_double, d, d]),
+                "oref_cons2prim": (ctypes.c_int, [ctypes.c_double, d, d, i]),
+                "oref_flux": (None, [ctypes.c_double, d, ctypes.c_int, d]),
+                "oref_entropy": (ctypes.c_double, [ctypes.c_double, d]),
+                "oref_entropy_vars": (None, [ctypes.c_double, d, d]),
+                "oref_potentials": (None, [d, d, d]),
+                "oref_ec_flux": (None, [ctypes.c_double, d, d, d, d, d]),
+                "oref_eigen": (None, [ctypes.c_double, d, d, d]),
+                "oref_weno": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, d]),
+                "oref_metrics": (None, [c, d, d, d]),
+                "oref_rhs": (ctypes.c_int, [c, d, d, d, d, d, d]),
+                "oref_cfl_dt": (ctypes.c_int, [c, d, d, d, d]),
+                "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d]),
+                "oref_rk_step": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d]),
+                "oref_init_state": (ctypes.c_int, [c, d, d, d, d]),
+                "oref_state_prim": (ctypes.c_int, [c, d, d, d]),
+                "oref_totals": (ctypes.c_int, [c, d, d, d, d, d]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _vec(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None:
+        assert a.size == n
+    return a
+
+
+def make_cfg(nx, ny, bc=(PERIODIC, PERIODIC), period=(1.0, 1.0), gamma=5.0 / 3.0,
+             p=2, w=5, weno_eps=1e-6, cfl=0.4, monitor=MONITOR_LNRHO, alpha=20.0,
+             n_filter=4, mu=10, move_mesh=1) -> Cfg:
+    c = Cfg()
+    c.nx, c.ny = nx, ny
+    c.bc[0], c.bc[1] = bc
+    c.period[0], c.period[1] = period
+    c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
+    c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
+    return c
+
+
+# ---- pointwise functions ---------------------------------------------------
+def alpha(p):
+    out = np.zeros(p)
+    lib().oref_alpha(p, _p(out))
+    return out
+
+
+def logmean(a, b):
+    return lib().oref_logmean(float(a), float(b))
+
+
+def prim2cons(gamma, w):
+    w = _vec(w, 4)
+    U = np.zeros(4)
+    lib().oref_prim2cons(gamma, _p(w), _p(U))
+    return U
+
+
+def cons2prim(gamma, U):
+    U = _vec(U, 4)
+    w = np.zeros(4)
+    it = ctypes.c_int(0)
+    st = lib().oref_cons2prim(gamma, _p(U), _p(w), ctypes.byref(it))
+    return w, st, it.value
+
+
+def flux(gamma, w, direction):
+    w = _vec(w, 4)
+    F = np.zeros(4)
+    lib().oref_flux(gamma, _p(w), direction, _p(F))
+    return F
+
+
+def entropy(gamma, w):
+    return lib().oref_entropy(gamma, _p(_vec(w, 4)))
+
+
+def entropy_vars(gamma, w):
+    V = np.zeros(4)
+    lib().oref_entropy_vars(gamma, _p(_vec(w, 4)), _p(V))
+    return V
+
+
+def potentials(w):
+    phi = np.zeros(1)
+    psi = np.zeros(2)
+    lib().oref_potentials(_p(_vec(w, 4)), _p(phi), _p(psi))
+    return phi[0], psi
+
+
+def ec_flux(gamma, wl, wr):
+    Ut, F1, F2 = np.zeros(4), np.zeros(4), np.zeros(4)
+    lib().oref_ec_flux(gamma, _p(_vec(wl, 4)), _p(_vec(wr, 4)), _p(Ut), _p(F1), _p(F2))
+    return Ut, F1, F2
+
+
+def eigen(gamma, w_rot):
+    lam, R = np.zeros(4), np.zeros(16)
+    lib().oref_eigen(gamma, _p(_vec(w_rot, 4)), _p(lam), _p(R))
+    return lam, R.reshape(4, 4)
+
+
+def weno(w, eps, s):
+    s = _vec(s, w)
+    return lib().oref_weno(w, eps, _p(s))
+
+
+# ---- grid functions --------------------------------------------------------
+def metrics(cfg, x):
+    N = cfg.nx * cfg.ny
+    x = _vec(x, 2 * N)
+    m = np.zeros(4 * N)
+    J0 = np.zeros(N)
+    lib().oref_metrics(ctypes.byref(cfg), _p(x), _p(m), _p(J0))
+    return m.reshape(4, cfg.ny, cfg.nx), J0.reshape(cfg.ny, cfg.nx)
+
+
+def init_state(cfg, prim, x):
+    N = cfg.nx * cfg.ny
+    prim, x = _vec(prim, 4 * N), _vec(x, 2 * N)
+    cons, J = np.zeros(4 * N), np.zeros(N)
+    lib().oref_init_state(ctypes.byref(cfg), _p(prim), _p(x), _p(cons), _p(J))
+    return cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx)
+
+
+def state_prim(cfg, cons, J):
+    N = cfg.nx * cfg.ny
+    prim = np.zeros(4 * N)
+    st = lib().oref_state_prim(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)), _p(prim))
+    return prim.reshape(4, cfg.ny, cfg.nx), st
+
+
+def rhs(cfg, cons, J, x, xdot=None):
+    N = cfg.nx * cfg.ny
+    if xdot is None:
+        xdot = np.zeros(2 * N)
+    dcons, dJ = np.zeros(4 * N), np.zeros(N)
+    st = lib().oref_rhs(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)),
+                        _p(_vec(x, 2 * N)), _p(_vec(xdot, 2 * N)), _p(dcons), _p(dJ))
+    if st != 0:
+        raise RuntimeError("oracle rhs: cons2prim failed")
+    return dcons.reshape(4, cfg.ny, cfg.nx), dJ.reshape(cfg.ny, cfg.nx)
+
+
+def cfl_dt(cfg, cons, J, x):
+    N = cfg.nx * cfg.ny
+    dt = np.zeros(1)
+    st = lib().oref_cfl_dt(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)),
+                           _p(_vec(x, 2 * N)), _p(dt))
+    if st != 0:
+        raise RuntimeError("oracle cfl: cons2prim failed")
+    return dt[0]
+
+
+def mesh(cfg, cons, J, x, dt):
+    N = cfg.nx * cfg.ny
+    xdot = np.zeros(2 * N)
+    tau = np.zeros(1)
+    st = lib().oref_mesh(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)),
+                         _p(_vec(x, 2 * N)), float(dt), _p(xdot), _p(tau))
+    if st != 0:
+        raise RuntimeError("oracle mesh: cons2prim failed")
+    return xdot.reshape(2, cfg.ny, cfg.nx), tau[0]
+
+
+def rk_step(cfg, cons, J, x, dt=0.0):
+    """One SSP-RK3 step; returns new (cons, J, x, dt_used)."""
+    N = cfg.nx * cfg.ny
+    cons = _vec(cons, 4 * N).copy()
+    J = _vec(J, N).copy()
+    x = _vec(x, 2 * N).copy()
+    dtu = np.zeros(1)
+    st = lib().oref_rk_step(ctypes.byref(cfg), _p(cons), _p(J), _p(x), float(dt), _p(dtu))
+    if st != 0:
+        raise RuntimeError("oracle rk_step: cons2prim failed")
+    return (cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx),
+            x.reshape(2, cfg.ny, cfg.nx), dtu[0])
+
+
+def totals(cfg, cons, J, dcons=None, dJ=None):
+    N = cfg.nx * cfg.ny
+    out = np.zeros(4)
+    dc = _vec(dcons, 4 * N) if dcons is not None else None
+    dj = _vec(dJ, N) if dJ is not None else None
+    lib().oref_totals(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)), _p(dc), _p(dj),
+                      _p(out))
+    return out

@@ -1,0 +1,109 @@
+/*
+ * esmm_oracle.h -- plain FP64 CPU oracle for the entropy-stable adaptive
+ * moving-mesh finite difference scheme of Duan & Tang, "High-order accurate
+ * entropy stable adaptive moving mesh finite difference schemes for special
+ * relativistic (magneto)hydrodynamics" (arXiv 2107.12027), 2D RHD case.
+ *
+ * TEST INFRASTRUCTURE.  This is the checker, not the product: only the test
+ * suite, the smoke check and the benchmark's CPU-baseline leg load it.  It
+ * shares no code with the CUDA library.
+ *
+ * Conventions (all arrays are caller-owned, FP64, structure of arrays):
+ *   nodes (i, j), i along xi (fastest), j along eta; N = nx * ny;
+ *   index(i, j) = j * nx + i;
+ *   prim[4][N]   = (rho, v_x, v_y, p);
+ *   cons[4][N]   = J * (D, m_x, m_y, E)   (the curvilinear unknown "J U");
+ *   J[N], x[2][N] (physical coordinates), xdot[2][N] (mesh velocity).
+ * The computational coordinates are node indices (Delta xi_k = 1).
+ */
+#ifndef ESMM_ORACLE_H
+#define ESMM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OREF_PERIODIC = 0, OREF_OUTFLOW = 1 };
+enum { OREF_MONITOR_RHO = 0, OREF_MONITOR_LNRHO = 1 };
+
+typedef struct {
+    int nx, ny;
+    int bc[2];            /* per direction: OREF_PERIODIC or OREF_OUTFLOW     */
+    double period[2];     /* physical period added to x (or y) across a
+                             periodic boundary                              */
+    double gamma;         /* ideal-gas adiabatic index, 1 < gamma <= 2        */
+    int p;                /* EC flux order 2p, p in {1, 2, 3}                 */
+    int w;                /* WENO order: 0 (EC only), 3 or 5                  */
+    double weno_eps;      /* WENO smoothness epsilon                          */
+    double cfl;           /* CFL number                                       */
+    int monitor;          /* OREF_MONITOR_RHO or OREF_MONITOR_LNRHO           */
+    double alpha;         /* monitor strength                                 */
+    int n_filter;         /* low-pass filter passes                           */
+    int mu;               /* Jacobi iterations per redistribution             */
+    int move_mesh;        /* 0: static mesh (xdot = 0)                        */
+} oref_cfg;
+
+/* Sec. 3.2, constraint eq. HOCoeff: alpha_{p,1..p}. */
+void oref_alpha(int p, double *alpha);
+/* Sec. 3.1 logarithmic mean [[a]]/[[ln a]]. */
+double oref_logmean(double a, double b);
+
+/* Sec. 1, eq. RMHDdiv2 with B = 0: primitive -> conservative, and back. */
+void oref_prim2cons(double gamma, const double *w, double *U);
+int oref_cons2prim(double gamma, const double *U, double *w, int *iters);
+void oref_flux(double gamma, const double *w, int dir, double *F);
+
+/* Sec. 2: entropy eta, entropy variables V, potentials phi and psi_k. */
+double oref_entropy(double gamma, const double *w);
+void oref_entropy_vars(double gamma, const double *w, double *V);
+void oref_potentials(const double *w, double *phi, double *psi);
+
+/* Sec. 3.1: the two-point parts U~ and F~_1, F~_2 of the EC flux. */
+void oref_ec_flux(double gamma, const double *wl, const double *wr,
+                  double *Ut, double *F1t, double *F2t);
+
+/* Sec. 4: eigenvalues lam[4] and scaled eigenvectors R[4][4] (row = component,
+ * column = wave) of dF_1/dU at a primitive state whose velocity is already
+ * rotated to the interface normal (w = rho, v_n, v_t, p). */
+void oref_eigen(double gamma, const double *w_rot, double *lam, double *R);
+
+/* Jiang-Shu WENO value at the right edge of the middle node of s[0..w-1]
+ * (w = 3 or 5), the stencil ordered from far upwind to far downwind. */
+double oref_weno(int w, double eps, const double *s);
+
+/* Sec. 3.3, eq. SCLCoeff / App. B: node metrics m[4][N] =
+ * (J xi_x, J xi_y, J eta_x, J eta_y), and J0[N] from the same differences. */
+void oref_metrics(const oref_cfg *c, const double *x, double *m, double *J0);
+
+/* Semi-discrete scheme, eqs. RMHDSemiU_O2p_ES / RMHDSemiJ_O2p_ES (B = 0). */
+int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
+             const double *x, const double *xdot, double *dcons, double *dJ);
+
+/* CFL time step, eq. cfl, with the static-mesh spectral radius. */
+int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
+                const double *x, double *dt);
+
+/* Sec. 5 mesh redistribution: xdot from the state at t^n and dt^n. */
+int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
+              const double *x, double dt, double *xdot, double *dtau);
+
+/* One SSP-RK3 step of (cons, J, x) in place; dt <= 0 selects the CFL step. */
+int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
+                 double dt, double *dt_used);
+
+/* Initial curvilinear state: J from the mesh and cons = J * U(prim). */
+int oref_init_state(const oref_cfg *c, const double *prim, const double *x,
+                    double *cons, double *J);
+/* Primitive variables of a state. */
+int oref_state_prim(const oref_cfg *c, const double *cons, const double *J,
+                    double *prim);
+
+/* out = (sum J eta, sum J D, sum J, sum (V . dcons - phi dJ)) -- the last
+ * only when dcons and dJ are given (else 0). */
+int oref_totals(const oref_cfg *c, const double *cons, const double *J,
+                const double *dcons, const double *dJ, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

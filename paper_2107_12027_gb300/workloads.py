@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs shaped like the paper's 2D RHD tests.
+
+This module only draws initial data and meshes (numpy PCG64, fixed seeds); it
+contains none of the scheme's arithmetic, so both the CUDA path and the oracle
+can be fed from it.  Arrays are structure-of-arrays, ``[comp][j][i]``, FP64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED = 20210726  # base seed; workloads add a config index and a problem id
+
+
+def rng(offset: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED + offset))
+
+
+# ---- meshes -----------------------------------------------------------------
+def uniform_mesh(nx, ny, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(True, True)):
+    """Nodes of a uniform mesh.  A periodic direction has nx distinct nodes
+    spaced L/nx starting at lo; an outflow direction has nodes on both ends."""
+    ax = []
+    for n, a, b, per in ((nx, lo[0], hi[0], periodic[0]), (ny, lo[1], hi[1], periodic[1])):
+        ax.append(a + (b - a) * np.arange(n) / (n if per else (n - 1)))
+    X, Y = np.meshgrid(ax[0], ax[1])
+    return np.ascontiguousarray(np.stack([X, Y]))
+
+
+def wavy_mesh(nx, ny, lo=(0.0, 0.0), hi=(1.0, 1.0), amp=0.05, t=0.0, periodic=(True, True)):
+    """A smooth curvilinear mesh: a uniform mesh displaced like the prescribed
+    vortex mesh, x = x0 + amp cos(pi t/4) sin(2 pi k y0/L), with k chosen so the
+    displacement is periodic (and zero on outflow boundaries)."""
+    x0 = uniform_mesh(nx, ny, lo, hi, periodic)
+    Lx, Ly = hi[0] - lo[0], hi[1] - lo[1]
+    s = amp * np.cos(np.pi * t / 4.0)
+    X = x0[0] + s * Lx * np.sin(2 * np.pi * (x0[1] - lo[1]) / Ly) * np.sin(np.pi * (x0[0] - lo[0]) / Lx) ** (0 if periodic[0] else 2)
+    Y = x0[1] + s * Ly * np.sin(2 * np.pi * (x0[0] - lo[0]) / Lx) * np.sin(np.pi * (x0[1] - lo[1]) / Ly) ** (0 if periodic[1] else 2)
+    return np.ascontiguousarray(np.stack([X, Y]))
+
+
+def wavy_mesh_velocity(nx, ny, lo=(0.0, 0.0), hi=(1.0, 1.0), amp=0.05, t=0.0, periodic=(True, True)):
+    """d/dt of :func:`wavy_mesh` (the prescribed mesh velocity)."""
+    x0 = uniform_mesh(nx, ny, lo, hi, periodic)
+    Lx, Ly = hi[0] - lo[0], hi[1] - lo[1]
+    ds = -amp * np.pi / 4.0 * np.sin(np.pi * t / 4.0)
+    X = ds * Lx * np.sin(2 * np.pi * (x0[1] - lo[1]) / Ly) * np.sin(np.pi * (x0[0] - lo[0]) / Lx) ** (0 if periodic[0] else 2)
+    Y = ds * Ly * np.sin(2 * np.pi * (x0[0] - lo[0]) / Lx) * np.sin(np.pi * (x0[1] - lo[1]) / Ly) ** (0 if periodic[1] else 2)
+    return np.ascontiguousarray(np.stack([X, Y]))
+
+
+def random_mesh(nx, ny, r, amp=0.15, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(True, True)):
+    """A uniform mesh with every node jittered by up to amp of a spacing
+    (non-smooth, untangled): used where an identity must hold for any mesh."""
+    x0 = uniform_mesh(nx, ny, lo, hi, periodic)
+    hx = (hi[0] - lo[0]) / (nx if periodic[0] else nx - 1)
+    hy = (hi[1] - lo[1]) / (ny if periodic[1] else ny - 1)
+    d = r.uniform(-amp, amp, size=x0.shape)
+    d[0] *= hx
+    d[1] *= hy
+    if not periodic[0]:
+        d[:, :, 0] = 0.0
+        d[:, :, -1] = 0.0
+    if not periodic[1]:
+        d[:, 0, :] = 0.0
+        d[:, -1, :] = 0.0
+    return np.ascontiguousarray(x0 + d)
+
+
+# ---- states -----------------------------------------------------------------
+def random_states(r, n, rho=(0.1, 10.0), p=(0.01, 10.0), vmax=0.9):
+    """n admissible primitive states (rho, vx, vy, p), log-uniform rho and p."""
+    rho_ = np.exp(r.uniform(np.log(rho[0]), np.log(rho[1]), n))
+    p_ = np.exp(r.uniform(np.log(p[0]), np.log(p[1]), n))
+    sp = vmax * np.sqrt(r.uniform(0.0, 1.0, n))
+    th = r.uniform(0.0, 2 * np.pi, n)
+    return np.stack([rho_, sp * np.cos(th), sp * np.sin(th), p_], axis=-1)
+
+
+def sine_wave(x, t=0.0):
+    """Smooth density advection: rho = 1 + 0.2 sin(2 pi (x + y - 0.4 t)),
+    v = (0.2, 0.2), p = 1 (an exact RHD solution)."""
+    X, Y = x[0], x[1]
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * (X + Y - 0.4 * t))
+    return np.ascontiguousarray(np.stack([rho, 0.2 + 0 * X, 0.2 + 0 * X, 1.0 + 0 * X]))
+
+
+def smooth_random_state(x, r, amp=0.2, modes=3):
+    """A smooth periodic state on [0,1]^2 with a few random Fourier modes in
+    each primitive variable (used for the entropy-identity checks)."""
+    X, Y = x[0], x[1]
+    out = []
+    for base, a in ((1.0, amp), (0.1, 0.3), (-0.1, 0.3), (1.0, amp)):
+        f = base + 0 * X
+        for _ in range(modes):
+            kx, ky = r.integers(-2, 3, 2)
+            ph = r.uniform(0, 2 * np.pi)
+            f = f + a / modes * np.sin(2 * np.pi * (kx * X + ky * Y) + ph)
+        out.append(f)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def quadrant_states(r):
+    """Four seeded states of a four-quadrant Riemann problem: rho in [0.1, 1],
+    p in [0.01, 1], |v| in [0, 0.9] with a uniform direction."""
+    rho = r.uniform(0.1, 1.0, 4)
+    p = r.uniform(0.01, 1.0, 4)
+    sp = r.uniform(0.0, 0.9, 4)
+    th = r.uniform(0.0, 2 * np.pi, 4)
+    return np.stack([rho, sp * np.cos(th), sp * np.sin(th), p], axis=-1)
+
+
+def quadrant_riemann(x, states, split=(0.0, 0.0)):
+    """Piecewise-constant data: quadrant q = (x > sx) + 2 (y > sy)."""
+    q = (x[0] > split[0]).astype(int) + 2 * (x[1] > split[1]).astype(int)
+    prim = np.empty((4,) + x.shape[1:])
+    for c in range(4):
+        prim[c] = states[q, c]
+    return np.ascontiguousarray(prim)
+
+
+def riemann_config(n=400, offset=1):
+    """2D RHD four-quadrant Riemann problem on [-1,1]^2 with outflow
+    boundaries, n x n nodes, seeded states (the 400^2 benchmark workload)."""
+    x = uniform_mesh(n, n, (-1.0, -1.0), (1.0, 1.0), (False, False))
+    states = quadrant_states(rng(offset))
+    return x, quadrant_riemann(x, states)
+
+
+def sine_config(n=64):
+    """2D RHD smooth sine wave on periodic [0,1]^2, n x n nodes."""
+    x = uniform_mesh(n, n, (0.0, 0.0), (1.0, 1.0), (True, True))
+    return x, sine_wave(x)
