@@ -1,0 +1,176 @@
+/*
+ * esmm.h -- C ABI of libesmm, the GB300 (sm_103a) implementation of the
+ * high-order entropy-stable adaptive moving-mesh finite difference scheme of
+ * Duan & Tang, "High-order accurate entropy stable adaptive moving mesh finite
+ * difference schemes for special relativistic (magneto)hydrodynamics"
+ * (arXiv 2107.12027), for 2D special relativistic hydrodynamics (RHD).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: ESMM_OK (0) or one ESMM_ERR_*.
+ *     On error nothing the caller owns has been written, except where stated;
+ *     esmm_last_error() returns a message.
+ *   - Arrays are structure of arrays, FP64, node-ordered with i (the xi
+ *     index, along x) fastest: element (c, j, i) of an array with C
+ *     components is at c*N + j*nx + i, N = nx*ny.  No ghost nodes.
+ *       prim  [4][N]  rho, v_x, v_y, p
+ *       cons  [4][N]  the curvilinear unknown J*U, U = (D, m_x, m_y, E)
+ *       J     [N]     the evolved Jacobian (volume) of each node
+ *       x     [2][N]  physical node coordinates (x, y)
+ *       xdot  [2][N]  mesh velocity
+ *   - The computational coordinates are node indices (Delta xi_k = 1), so
+ *     metrics, J and fluxes are per unit index.
+ *   - mem = ESMM_MEM_HOST: pointers are host memory; the call copies in,
+ *     computes on the grid's stream and copies out before returning.
+ *     mem = ESMM_MEM_DEVICE: pointers are device memory on the grid's device;
+ *     the call only enqueues work on the grid's stream and returns (the
+ *     caller synchronises).  Caller pointers are borrowed for the call only.
+ *   - A grid owns all device memory it allocates; esmm_grid_destroy frees it.
+ *   - Calls on one grid must not overlap; different grids are independent.
+ */
+#ifndef ESMM_H
+#define ESMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESMM_OK 0
+#define ESMM_ERR_ARG 1      /* invalid argument                               */
+#define ESMM_ERR_CUDA 2     /* a CUDA call failed (message in esmm_last_error) */
+#define ESMM_ERR_C2P 3      /* conservative-to-primitive recovery failed at
+                               some node (non-admissible state)               */
+#define ESMM_ERR_TIMEOUT 4  /* an iteration limit was reached                 */
+#define ESMM_ERR_STATE 5    /* the grid has no state yet                      */
+
+#define ESMM_RHD 0          /* physics: special relativistic hydrodynamics    */
+
+#define ESMM_PERIODIC 0     /* boundary: periodic (mesh shifted by the period) */
+#define ESMM_OUTFLOW 1      /* boundary: zero-gradient data, fixed boundary
+                               nodes, linearly extrapolated mesh ghosts        */
+
+#define ESMM_MEM_HOST 0
+#define ESMM_MEM_DEVICE 1
+
+#define ESMM_FP64 0         /* every step in FP64                              */
+#define ESMM_MIXED 1        /* fluxes, WENO and metrics in FP32; FP64 for the
+                               primitive recovery, near-equal log means, the
+                               state, and all totals                            */
+
+#define ESMM_MONITOR_RHO 0  /* monitor variable sigma = rho                    */
+#define ESMM_MONITOR_LNRHO 1/* monitor variable sigma = ln rho                 */
+
+#define ESMM_GET_PRIM 0     /* [4][N] primitive variables                      */
+#define ESMM_GET_CONS 1     /* [4][N] J*U                                       */
+#define ESMM_GET_J 2        /* [N]                                              */
+#define ESMM_GET_X 3        /* [2][N]                                           */
+#define ESMM_GET_XDOT 4     /* [2][N] mesh velocity of the last step            */
+
+typedef struct esmm_grid esmm_grid;
+
+/* Scheme parameters (Sec. 5 and 6 of the paper; defaults in brackets). */
+typedef struct {
+    double cfl;        /* CFL number of eq. cfl                       [0.4]  */
+    double weno_eps;   /* WENO smoothness epsilon                     [1e-6] */
+    int monitor;       /* ESMM_MONITOR_RHO or ESMM_MONITOR_LNRHO   [LNRHO]   */
+    double alpha;      /* monitor strength alpha of eq. monitor       [20]   */
+    int n_filter;      /* passes of the monitor's low-pass filter     [4]    */
+    int mu;            /* Jacobi iterations of the mesh equations     [10]   */
+    int move_mesh;     /* 0: static mesh (uniform-mesh scheme)        [1]    */
+    int precision;     /* ESMM_FP64 or ESMM_MIXED                     [FP64] */
+} esmm_params;
+
+/* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim must be 2, phys
+ * ESMM_RHD, bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4).  A periodic
+ * direction has n[k] distinct nodes with spacing (hi-lo)/n[k]; an outflow
+ * direction has nodes on both ends.  stream is a cudaStream_t (NULL: the
+ * legacy default stream) on the current device; the grid stays on that device.
+ * Defaults: Gamma = 5/3, p = 2, w = 5, the parameter defaults above. */
+int esmm_grid_create(esmm_grid **g, int dim, const int n[3], const double lo[3],
+                     const double hi[3], int phys, const int bc[3], void *stream);
+int esmm_grid_destroy(esmm_grid *g);
+int esmm_set_stream(esmm_grid *g, void *stream);
+
+/* Ideal-gas EOS p = (Gamma - 1) rho e (eq. EOS); 1 < Gamma <= 2. */
+int esmm_set_eos(esmm_grid *g, double gamma);
+/* 2p-th order EC flux (eq. ECFlux_O2p), p in {1, 2, 3}; WENO order w of
+ * the ES dissipation (eq. ESFlux_HO), w in {0 (EC scheme), 3, 5}. */
+int esmm_set_order(esmm_grid *g, int p, int w);
+int esmm_set_params(esmm_grid *g, const esmm_params *prm);
+int esmm_get_params(const esmm_grid *g, esmm_params *prm);
+
+/* Set the state from primitive variables and a mesh (x NULL: the uniform
+ * mesh of the grid's box).  J is initialised from the mesh by the same
+ * central differences as the metrics, cons = J * U(prim), t = 0.
+ * ESMM_ERR_ARG for a non-admissible state (rho <= 0, p <= 0 or |v| >= 1). */
+int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem);
+/* Set the curvilinear state directly (e.g. to resume from esmm_state_get). */
+int esmm_state_set_cons(esmm_grid *g, const double *cons, const double *J,
+                        const double *x, double t, int mem);
+/* Copy one field of the state (ESMM_GET_*) to out. */
+int esmm_state_get(esmm_grid *g, int what, double *out, int mem);
+int esmm_get_time(esmm_grid *g, double *t);
+
+/* One evaluation of the semi-discrete ES scheme, eqs. RMHDSemiU_O2p_ES and
+ * RMHDSemiJ_O2p_ES of Sec. 4 with B = 0: d(cons)/dt and dJ/dt for the given
+ * (cons, J, x, xdot) (xdot NULL: static mesh).  Independent of the grid's
+ * state; uses its EOS, order, boundary conditions and precision.
+ * ESMM_ERR_C2P if the primitive recovery failed at some node (outputs are then
+ * undefined at those nodes). */
+int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
+             const double *xdot, double *dcons, double *dJ, int mem);
+
+/* CFL time step of eq. cfl for the grid's state (static-mesh spectral
+ * radius).  Synchronises. */
+int esmm_cfl_dt(esmm_grid *g, double *dt);
+
+/* Adaptive mesh redistribution of Sec. 5 for the grid's state and time step
+ * dt (dt <= 0: the CFL step): monitor, low-pass filter, mu Jacobi sweeps,
+ * movement limiter.  Stores the mesh velocity in the grid (used by the next
+ * esmm_rk_step only through esmm_rk_step's own call of it) and, when given,
+ * writes it to xdot [2][N] and the limiter value to *dtau (host). */
+int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, int mem);
+
+/* One time step of the fully discrete scheme: CFL step (dt <= 0) or the given
+ * dt, mesh redistribution (unless move_mesh = 0), and three SSP-RK3 stages
+ * applied to (cons, J) and to the mesh with the step's mesh velocity.
+ * Asynchronous on the grid's stream; when dt_used is not NULL the call
+ * synchronises and writes the step used.  A recovery failure is reported by
+ * esmm_last_error / the next synchronising call. */
+int esmm_rk_step(esmm_grid *g, double dt, double *dt_used);
+/* nsteps asynchronous esmm_rk_step calls (dt as there). */
+int esmm_advance(esmm_grid *g, int nsteps, double dt);
+
+/* FP64 totals of the grid's state: out[0] = sum J eta (total entropy),
+ * out[1] = sum J D (mass), out[2] = sum J (volume).  Synchronises. */
+int esmm_totals(esmm_grid *g, double out[3]);
+
+/* Synchronise and return the accumulated error state: the number of nodes
+ * whose primitive recovery failed since the last call (then reset), and the
+ * last error message (copied into msg, at most len bytes, NUL-terminated). */
+int esmm_last_error(esmm_grid *g, int *n_c2p_fail, char *msg, int len);
+
+/* Profiling, an addition for measurement (the paper has no counterpart).
+ * Every kernel launch is counted under one kind; the kinds set in mask also
+ * get a CUDA event pair recorded on the grid's stream around each launch, so
+ * their device time can be read back.  esmm_profile() clears the counters
+ * and times and sets the mask (0: counting only).  esmm_profile_read()
+ * synchronises and returns, per kind, the summed device milliseconds of the
+ * timed launches, the number of launches, and how many of them were timed. */
+#define ESMM_KIND_NODE 0    /* per-node pass: recovery, logs, metrics          */
+#define ESMM_KIND_PAIRS 1   /* two-point EC pair fluxes                         */
+#define ESMM_KIND_IFACE 2   /* ES interface fluxes: EC sum + WENO dissipation   */
+#define ESMM_KIND_UPDATE 3  /* flux differences fused with the SSP-RK3 stage    */
+#define ESMM_KIND_MESH 4    /* mesh redistribution                              */
+#define ESMM_KIND_OTHER 5   /* CFL reduction, time step, totals                 */
+#define ESMM_NKINDS 6
+int esmm_profile(esmm_grid *g, int mask);
+int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
+                      long long timed[ESMM_NKINDS]);
+
+/* Library version string. */
+const char *esmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -38,6 +38,7 @@
 
 #define NV 4   /* 2D RHD: (D, m_x, m_y, E) */
 #define G 3    /* ghost layers of the node data: WENO5 and p <= 3 pairs */
+#define OREF_SIGN_TOL 1.0e-10
 
 /* ------------------------------------------------------------------------ */
 /* Coefficients alpha_{p,n} (Sec. 3.2, constraint eq. HOCoeff):
@@ -612,6 +613,7 @@ static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, do
     /* scaled entropy variables V~ = R^T T V on the stencil nodes */
     int lo = (c->w == 5) ? -2 : -1, hi = (c->w == 5) ? 3 : 2;
     double Vt[6][4];
+    double scale[4] = {0.0, 0.0, 0.0, 0.0};   /* magnitudes forming V~ at nodes 0, 1 */
     for (int q = lo; q <= hi; ++q) {
         double wq[4], V[4];
         pad_prim(P, i + q * di, j + q * dj, wq);
@@ -619,7 +621,10 @@ static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, do
         double TV[4] = {V[0], nx_ * V[1] + ny_ * V[2], tx_ * V[1] + ty_ * V[2], V[3]};
         for (int m = 0; m < 4; ++m) {
             double acc = 0.0;
-            for (int a = 0; a < 4; ++a) acc += R[a * 4 + m] * TV[a];
+            for (int a = 0; a < 4; ++a) {
+                acc += R[a * 4 + m] * TV[a];
+                if (q == 0 || q == 1) scale[m] += fabs(R[a * 4 + m] * TV[a]);
+            }
             Vt[q - lo][m] = acc;
         }
     }
@@ -635,7 +640,11 @@ static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, do
         double vplus = oref_weno(nw, c->weno_eps, sr);
         double jw = vplus - vminus;                        /* <<V~>>^WENO */
         double jump = Vt[1 - lo][m] - Vt[0 - lo][m];       /* [[V~]]      */
-        double Y = (sgn(jw) == sgn(jump)) ? 1.0 : 0.0;
+        /* Reading: a jump within OREF_SIGN_TOL of the magnitudes that form it
+         * is rounding noise and has sign 0 (then Y = 0, which keeps the
+         * entropy inequality of Thm. 4.1). */
+        int sj = fabs(jump) <= OREF_SIGN_TOL * scale[m] ? 0 : sgn(jump);
+        double Y = (sgn(jw) == sj) ? 1.0 : 0.0;
         z[m] = Y * jw;
     }
     double d[4];

@@ -1,0 +1,309 @@
+// esmm_device.cuh -- device arithmetic of the ES adaptive moving-mesh scheme
+// (Duan & Tang, arXiv 2107.12027), 2D RHD, templated on the working precision
+// R (double for the FP64 form, float for the mixed form).  The primitive
+// recovery and the near-equal branch of the logarithmic mean are always FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace esmm {
+
+constexpr int GH = 3;        // ghost layers of the padded node arrays
+constexpr int PMAX = 3;      // largest supported p
+// Node quantities stored per padded node (FP64, structure of arrays).
+enum {
+    Q_RHO = 0, Q_P, Q_BETA, Q_UX, Q_UY, Q_W, Q_LNR, Q_LNB,
+    Q_M00, Q_M01, Q_M10, Q_M11, Q_MT0, Q_MT1, NQ
+};
+
+struct Geom {
+    int nx, ny;       // interior nodes
+    int px, py;       // padded extents nx + 2 GH, ny + 2 GH
+    long long P;      // px * py
+    long long N;      // nx * ny
+    int bc0, bc1;     // 0 periodic, 1 outflow
+    double per0, per1;
+};
+
+struct Phys {
+    double gamma;
+    double eps;       // WENO epsilon
+    double ln_thr;    // log-mean series switch on ((b-a)/(b+a))^2
+    double sign_tol;  // relative size below which [[V~]] counts as zero
+    double alpha[PMAX];
+    int p, w;
+};
+
+__host__ __device__ __forceinline__ long long pidx(const Geom &g, int i, int j)
+{
+    return (long long)(j + GH) * g.px + (i + GH);
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+__device__ __forceinline__ int floordivi(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// Boundary data: periodic wrap or zero-gradient copy.
+__device__ __forceinline__ long long data_src(const Geom &g, int i, int j)
+{
+    int ii = g.bc0 == 0 ? wrapi(i, g.nx) : clampi(i, 0, g.nx - 1);
+    int jj = g.bc1 == 0 ? wrapi(j, g.ny) : clampi(j, 0, g.ny - 1);
+    return (long long)jj * g.nx + ii;
+}
+
+// Boundary mesh: periodic wrap plus the period (shift = 1 for coordinates,
+// 0 for velocities), or linear extrapolation of the two boundary nodes.
+__device__ __forceinline__ double mesh_along_i(const Geom &g, const double *a, int i, int j, int comp, int shift)
+{
+    const double *row = a + (long long)comp * g.N + (long long)j * g.nx;
+    if (g.bc0 == 0) {
+        double s = (shift && comp == 0) ? floordivi(i, g.nx) * g.per0 : 0.0;
+        return row[wrapi(i, g.nx)] + s;
+    }
+    if (i < 0) { double a0 = row[0], a1 = row[1]; return a0 + i * (a1 - a0); }
+    if (i >= g.nx) { double a0 = row[g.nx - 1], a1 = row[g.nx - 2]; return a0 + (i - (g.nx - 1)) * (a0 - a1); }
+    return row[i];
+}
+
+__device__ __forceinline__ double mesh_at(const Geom &g, const double *a, int i, int j, int comp, int shift)
+{
+    if (g.bc1 == 0) {
+        double s = (shift && comp == 1) ? floordivi(j, g.ny) * g.per1 : 0.0;
+        return mesh_along_i(g, a, i, wrapi(j, g.ny), comp, shift) + s;
+    }
+    if (j < 0) {
+        double a0 = mesh_along_i(g, a, i, 0, comp, shift), a1 = mesh_along_i(g, a, i, 1, comp, shift);
+        return a0 + j * (a1 - a0);
+    }
+    if (j >= g.ny) {
+        double a0 = mesh_along_i(g, a, i, g.ny - 1, comp, shift), a1 = mesh_along_i(g, a, i, g.ny - 2, comp, shift);
+        return a0 + (j - (g.ny - 1)) * (a0 - a1);
+    }
+    return mesh_along_i(g, a, i, j, comp, shift);
+}
+
+// ---------------------------------------------------------------------------
+// Conservative -> primitive recovery (FP64 in every form).  Newton on p for
+//   f(p) = (G-1)/G ((E+p)(1-v^2) - D sqrt(1-v^2)) - p,  v = |m|/(E+p),
+// safeguarded by bisection on [0, (G-1)E], stopping when a step moves p by at
+// most 1e-15 p; p0 is a warm start (ignored when outside the bracket).
+// Returns 0, 1 for a non-admissible state, 2 when the iteration cap is hit.
+__device__ __forceinline__ int cons2prim(double gam, double D, double mx, double my, double E,
+                                         double p0, double &rho, double &vx, double &vy, double &p)
+{
+    double S2 = mx * mx + my * my;
+    double S = sqrt(S2);
+    double gg = (gam - 1.0) / gam;
+    rho = 0.0; vx = 0.0; vy = 0.0; p = 0.0;
+    if (!(D > 0.0) || !(E * E > D * D + S2) || !(E > 0.0)) return 1;
+    double lo = 0.0, hi = (gam - 1.0) * E;
+    double pc = (p0 > lo && p0 < hi) ? p0 : 0.5 * (lo + hi);
+    int ok = 0;
+    for (int it = 0; it < 200; ++it) {
+        double Ep = E + pc;
+        double r = 1.0 / Ep;
+        double iW2 = (Ep - S) * (Ep + S) * r * r;   // 1 - v^2
+        double rs = rsqrt(iW2);
+        double iW = iW2 * rs;                        // sqrt(1 - v^2)
+        double v2 = S2 * r * r;
+        double f = gg * (Ep * iW2 - D * iW) - pc;
+        double df = gg * (1.0 + v2 - D * v2 * r * rs) - 1.0;
+        if (f > 0.0) lo = pc; else hi = pc;
+        double pn = pc - f / df;
+        if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
+        if (fabs(pn - pc) <= 1.0e-15 * pn) { pc = pn; ok = 1; break; }
+        pc = pn;
+    }
+    double Ep = E + pc;
+    double r = 1.0 / Ep;
+    double iW2 = (Ep - S) * (Ep + S) * r * r;
+    rho = D * sqrt(iW2);
+    vx = mx * r;
+    vy = my * r;
+    p = pc;
+    return ok ? 0 : 2;
+}
+
+// ---------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ R rsq(R x);
+template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <typename R> __device__ __forceinline__ R sq_rt(R x);
+template <> __device__ __forceinline__ double sq_rt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sq_rt<float>(float x) { return sqrtf(x); }
+template <typename R> __device__ __forceinline__ R fab(R x);
+template <> __device__ __forceinline__ double fab<double>(double x) { return fabs(x); }
+template <> __device__ __forceinline__ float fab<float>(float x) { return fabsf(x); }
+
+// Logarithmic mean [[a]]/[[ln a]] and its reciprocal from FP64 node values
+// and their FP64 logarithms.  Near-equal arguments, ((b-a)/(b+a))^2 < thr, use
+// the Ismail-Roe series in FP64: mean = (a+b)/(2 F), F = 1 + u/3 + u^2/5 + u^3/7.
+template <typename R>
+__device__ __forceinline__ void logmean(double a, double b, double la, double lb, double thr,
+                                        R &mean, R &inv_mean)
+{
+    double d = b - a, s = b + a;
+    if (d * d < thr * s * s) {
+        double u = d * d / (s * s);
+        double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
+        mean = (R)(s / (2.0 * F));
+        inv_mean = (R)(2.0 * F / s);
+    } else {
+        R dn = (R)d, dl = (R)(lb - la);
+        mean = dn / dl;
+        inv_mean = dl / dn;
+    }
+}
+
+// Node values of one two-point flux argument (the parameter variables).
+template <typename R>
+struct NodeV {
+    double rho, beta, lnr, lnb;  // FP64: log-mean arguments
+    R r, b, ux, uy, W;
+};
+
+// Curvilinear two-point EC flux of Sec. 3.1 for one node pair in direction k:
+//   F~_k = 1/2 (mt_l + mt_r) U~ + sum_j 1/2 (M_kj,l + M_kj,r) F~_j,
+// mt, mx, my the averaged metrics.  U~ is the paper's U~^RMHD at B = 0 and
+// F~_j the matching RHD spatial flux:
+//   U~_D = r_ln W,  U~_E = (alpha0 U~_D W + pm |u|^2)/Lam,
+//   U~_m = (U~_E + pm) u/W,  F~_D,j = r_ln u_j,
+//   F~_E,j = W (alpha0 r_ln + pm) u_j / Lam,  F~_m,j = F~_E,j u/W + pm e_j,
+// with the arithmetic means r, b, u, W, pm = r/b, Lam = W^2 - |u|^2 and
+// alpha0 = 1 + 1/((Gamma-1) b_ln).  Contracting with the metrics gives
+//   out_D = r_ln (mt W + un), out_E = mt U~_E + Es,
+//   out_m = u/W (mt (U~_E + pm) + Es) + pm (mx, my),
+// un = mx u_x + my u_y, Es = W (alpha0 r_ln + pm) un / Lam.
+template <typename R>
+__device__ __forceinline__ void ec_pair(const NodeV<R> &l, const NodeV<R> &r, R mt, R mx, R my,
+                                        R gm1inv, double thr, R out[4])
+{
+    R rln, irln, bln, ibln;
+    logmean<R>(l.rho, r.rho, l.lnr, r.lnr, thr, rln, irln);
+    logmean<R>(l.beta, r.beta, l.lnb, r.lnb, thr, bln, ibln);
+    R half = (R)0.5;
+    R rm = half * (l.r + r.r);
+    R bm = half * (l.b + r.b);
+    R Wm = half * (l.W + r.W);
+    R uxm = half * (l.ux + r.ux);
+    R uym = half * (l.uy + r.uy);
+    R usq = uxm * uxm + uym * uym;
+    R Lam = Wm * Wm - usq;
+    R alpha0 = (R)1 + gm1inv * ibln;
+    R pm = rm / bm;
+    R rinv = (R)1 / (Lam * Wm);
+    R iLam = rinv * Wm;
+    R iW = rinv * Lam;
+    R UD = rln * Wm;
+    R UE = (alpha0 * UD * Wm + pm * usq) * iLam;
+    R un = mx * uxm + my * uym;
+    R Es = Wm * (alpha0 * rln + pm) * un * iLam;
+    R cm = (mt * (UE + pm) + Es) * iW;
+    out[0] = rln * (mt * Wm + un);
+    out[1] = uxm * cm + pm * mx;
+    out[2] = uym * cm + pm * my;
+    out[3] = mt * UE + Es;
+}
+
+// Jiang-Shu WENO edge value on s[0..4] (far upwind .. far downwind), written
+// with a single division: sum_k (d_k/(eps+b_k)^2) q_k / sum_k d_k/(eps+b_k)^2
+// multiplied through by the three squared denominators.
+template <typename R>
+__device__ __forceinline__ R weno5(R s0, R s1, R s2, R s3, R s4, R eps)
+{
+    const R c13_12 = (R)(13.0 / 12.0), c1_4 = (R)0.25, c1_6 = (R)(1.0 / 6.0);
+    R q0 = ((R)2 * s0 - (R)7 * s1 + (R)11 * s2) * c1_6;
+    R q1 = (-s1 + (R)5 * s2 + (R)2 * s3) * c1_6;
+    R q2 = ((R)2 * s2 + (R)5 * s3 - s4) * c1_6;
+    R t0 = s0 - (R)2 * s1 + s2, r0 = s0 - (R)4 * s1 + (R)3 * s2;
+    R t1 = s1 - (R)2 * s2 + s3, r1 = s1 - s3;
+    R t2 = s2 - (R)2 * s3 + s4, r2 = (R)3 * s2 - (R)4 * s3 + s4;
+    R e0 = eps + c13_12 * t0 * t0 + c1_4 * r0 * r0;
+    R e1 = eps + c13_12 * t1 * t1 + c1_4 * r1 * r1;
+    R e2 = eps + c13_12 * t2 * t2 + c1_4 * r2 * r2;
+    e0 *= e0; e1 *= e1; e2 *= e2;
+    R a0 = (R)0.1 * e1 * e2, a1 = (R)0.6 * e0 * e2, a2 = (R)0.3 * e0 * e1;
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+template <typename R>
+__device__ __forceinline__ R weno3(R s0, R s1, R s2, R eps)
+{
+    R q0 = (-s0 + (R)3 * s1) * (R)0.5;
+    R q1 = (s1 + s2) * (R)0.5;
+    R e0 = eps + (s1 - s0) * (s1 - s0);
+    R e1 = eps + (s2 - s1) * (s2 - s1);
+    e0 *= e0; e1 *= e1;
+    R a0 = (R)(1.0 / 3.0) * e1, a1 = (R)(2.0 / 3.0) * e0;
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+__device__ __forceinline__ int sgn_d(double a) { return (a > 0.0) - (a < 0.0); }
+__device__ __forceinline__ int sgn_d(float a) { return (a > 0.0f) - (a < 0.0f); }
+
+// Scaled eigenvectors of dF_1/dU (Sec. 4) at the rotated state (rho, vn, vt, p)
+// with W = 1/sqrt(1 - vn^2 - vt^2): columns dU_m * s_m, s_m = (dU_m . dV_m)^-1/2,
+// for the waves (lambda_-, v_n [entropy, d rho = 1], v_n [shear, d v_t = 1],
+// lambda_+ [acoustic, dp = 1]).  dU (4 x 4, column per wave) and s are returned
+// separately; lam_m, lam_p are the acoustic speeds.
+template <typename R>
+__device__ __forceinline__ void eigen_rhd(R gam, R rho, R vn, R vt, R p, R W,
+                                          R dU[4][4], R s[4], R &lam_m, R &lam_p)
+{
+    R one = (R)1;
+    R gg = gam / (gam - one);
+    R W2 = W * W;
+    R iW2 = one / W2;                      // 1 - v^2
+    R v2 = one - iW2;
+    R irp = one / (rho * p);
+    R ip = rho * irp, ir = p * irp;
+    R rh = rho + gg * p;                   // rho h
+    R c2 = gam * p / rh;
+    R c = sq_rt<R>(c2);
+    R disc = sq_rt<R>(iW2 * (one - v2 * c2 - vn * vn * (one - c2)));
+    R den = one / (one - v2 * c2);
+    lam_m = (vn * (one - c2) - c * disc) * den;
+    lam_p = (vn * (one - c2) + c * disc) * den;
+    R Q = rh * W2;
+    R beta = rho * ip;
+    R un = W * vn, ut = W * vt;
+    R W4 = W2 * W2;
+    // entropy wave, d rho = 1:  dU = (W, W^2 v, W^2),  dU.dV = G W/((G-1) rho)
+    dU[0][1] = W; dU[1][1] = W2 * vn; dU[2][1] = W2 * vt; dU[3][1] = W2;
+    s[1] = rsq<R>(gg * W * ir);
+    // shear wave, d v_t = 1:  dU = (rho W^3 vt, 2 rho h W^4 vn vt,
+    //   rho h (2 W^4 vt^2 + W^2), 2 rho h W^4 vt),  dU.dV = rho h beta W^3 (1 + W^2 vt^2)
+    dU[0][2] = rho * W2 * W * vt;
+    dU[1][2] = (R)2 * rh * W4 * vn * vt;
+    dU[2][2] = rh * ((R)2 * W4 * vt * vt + W2);
+    dU[3][2] = (R)2 * rh * W4 * vt;
+    s[2] = rsq<R>(rh * beta * W2 * W * (one + W2 * vt * vt));
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        int m = side == 0 ? 0 : 3;
+        R l = side == 0 ? lam_m : lam_p;
+        R a = one / ((l - vn) * Q);          // 1 / ((lam - v_n) Q)
+        R dvn = (one - vn * l) * a;
+        R dvt = -l * vt * a;
+        R vdv = vn * dvn + vt * dvt;
+        R drho = rho * dvn * a * Q - rho * W2 * vdv;
+        // dU/dw dw with dp = 1
+        R h1 = drho + gg;                    // d(rho h)
+        R dW = W2 * W * vdv;
+        dU[0][m] = W * drho + rho * dW;
+        dU[1][m] = W2 * vn * h1 + rh * ((R)2 * W4 * vn * vdv + W2 * dvn);
+        dU[2][m] = W2 * vt * h1 + rh * ((R)2 * W4 * vt * vdv + W2 * dvt);
+        dU[3][m] = W2 * h1 - one + rh * (R)2 * W4 * vdv;
+        // dV/dw dw
+        R dbeta = drho * ip - beta * ip;
+        R dV0 = drho * ir + (drho * ir - ip) / (gam - one) + dbeta;
+        R dV1 = dbeta * un + beta * (W * dvn + vn * dW);
+        R dV2 = dbeta * ut + beta * (W * dvt + vt * dW);
+        R dV3 = -(dbeta * W + beta * dW);
+        s[m] = rsq<R>(dU[0][m] * dV0 + dU[1][m] * dV1 + dU[2][m] * dV2 + dU[3][m] * dV3);
+    }
+}
+
+}  // namespace esmm

@@ -1,0 +1,244 @@
+// esmm_flux.cuh -- the two flux kernels of one sweep direction:
+//   k_pairs: every two-point EC flux F~_k(U_A, U_{A+n}) (Sec. 3.1), n = 1..p,
+//            computed once per node pair and stored;
+//   k_iface: the w-th order ES interface flux (eq. ESFlux_HO): the 2p-th order
+//            combination of the stored pair fluxes (eq. ECFlux_O2p) minus the
+//            WENO dissipation on scaled entropy variables, plus the metric
+//            flux of the VCL (eq. MetricsFlux_O2p).
+// One thread per node pair / interface, flattened over the sweep so that warps
+// read consecutive nodes.
+#pragma once
+
+#include "esmm_device.cuh"
+#include "esmm_launch.h"
+
+namespace esmm {
+
+template <typename R>
+__device__ __forceinline__ NodeV<R> load_node(const Geom &g, const double *__restrict__ q, long long c)
+{
+    NodeV<R> v;
+    v.rho = q[Q_RHO * g.P + c];
+    v.beta = q[Q_BETA * g.P + c];
+    v.lnr = q[Q_LNR * g.P + c];
+    v.lnb = q[Q_LNB * g.P + c];
+    v.r = (R)v.rho;
+    v.b = (R)v.beta;
+    v.ux = (R)q[Q_UX * g.P + c];
+    v.uy = (R)q[Q_UY * g.P + c];
+    v.W = (R)q[Q_W * g.P + c];
+    return v;
+}
+
+// anchors A in [-P, n_dir - 1] along the sweep, every line of the other index
+template <typename R, int P>
+__global__ void __launch_bounds__(128) k_pairs(Geom g, Phys ph, const double *__restrict__ q,
+                                               R *__restrict__ pairs, int dir)
+{
+    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
+    const long long count = (long long)(nd + P) * no;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count) return;
+    int i, j;
+    if (dir == 0) { j = (int)(idx / (nd + P)); i = (int)(idx % (nd + P)) - P; }
+    else { i = (int)(idx % no); j = (int)(idx / no) - P; }
+    const long long c0 = pidx(g, i, j);
+    const long long sd = dir == 0 ? 1 : g.px;
+    const double *Mt = q + (Q_MT0 + dir) * g.P;
+    const double *Mx = q + (Q_M00 + 2 * dir) * g.P;
+    const double *My = q + (Q_M01 + 2 * dir) * g.P;
+    const R gm1inv = (R)(1.0 / (ph.gamma - 1.0));
+    NodeV<R> l = load_node<R>(g, q, c0);
+    const double mtl = Mt[c0], mxl = Mx[c0], myl = My[c0];
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        const long long cr = c0 + n * sd;
+        NodeV<R> r = load_node<R>(g, q, cr);
+        R mt = (R)(0.5 * (mtl + Mt[cr]));
+        R mx = (R)(0.5 * (mxl + Mx[cr]));
+        R my = (R)(0.5 * (myl + My[cr]));
+        R out[4];
+        ec_pair<R>(l, r, mt, mx, my, gm1inv, ph.ln_thr, out);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            pairs[((long long)((dir * PMAX + (n - 1)) * 4 + a)) * g.P + c0] = out[a];
+    }
+}
+
+// interfaces between left node L in [-1, n_dir - 1] and L + 1
+template <typename R, int P, int WW>
+__global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__restrict__ q,
+                                               const R *__restrict__ pairs, R *__restrict__ iflux, int dir)
+{
+    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
+    const long long count = (long long)(nd + 1) * no;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count) return;
+    int i, j;
+    if (dir == 0) { j = (int)(idx / (nd + 1)); i = (int)(idx % (nd + 1)) - 1; }
+    else { i = (int)(idx % no); j = (int)(idx / no) - 1; }
+    const long long c0 = pidx(g, i, j);
+    const long long sd = dir == 0 ? 1 : g.px;
+    const double *Mt = q + (Q_MT0 + dir) * g.P;
+
+    // eq. ECFlux_O2p: sum_n alpha_{p,n} sum_{s<n} F~(A - s, A - s + n)
+    R F[4] = {(R)0, (R)0, (R)0, (R)0};
+    double Ft = 0.0;
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        R Fs[4] = {(R)0, (R)0, (R)0, (R)0};
+        double Fts = 0.0;
+#pragma unroll
+        for (int s = 0; s < n; ++s) {
+            const long long ca = c0 - s * sd;
+            const R *pr = pairs + ((long long)(dir * PMAX + (n - 1)) * 4) * g.P + ca;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) Fs[a] += pr[a * g.P];
+            Fts += 0.5 * (Mt[ca] + Mt[ca + n * sd]);
+        }
+        const R an = (R)ph.alpha[n - 1];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) F[a] += an * Fs[a];
+        Ft += ph.alpha[n - 1] * Fts;
+    }
+
+    if (WW > 0) {
+        // eq. ESFlux_HO: subtract 1/2 lambda^ T^-1 R Y <<V~>>
+        const double *Mx = q + (Q_M00 + 2 * dir) * g.P;
+        const double *My = q + (Q_M01 + 2 * dir) * g.P;
+        const long long c1 = c0 + sd;
+        const R half = (R)0.5, one = (R)1;
+        const R gam = (R)ph.gamma;
+        R nvx = (R)(0.5 * (Mx[c0] + Mx[c1]));
+        R nvy = (R)(0.5 * (My[c0] + My[c1]));
+        R jt = (R)(0.5 * (Mt[c0] + Mt[c1]));
+        R Lk = sq_rt<R>(nvx * nvx + nvy * nvy);
+        R iLk = one / Lk;
+        R nx = nvx * iLk, ny = nvy * iLk;
+        // interface state: mean of (rho, u, p) of the two nodes
+        R rho = half * ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]);
+        R ux = half * ((R)q[Q_UX * g.P + c0] + (R)q[Q_UX * g.P + c1]);
+        R uy = half * ((R)q[Q_UY * g.P + c0] + (R)q[Q_UY * g.P + c1]);
+        R p = half * ((R)q[Q_P * g.P + c0] + (R)q[Q_P * g.P + c1]);
+        R W = sq_rt<R>(one + ux * ux + uy * uy);
+        R iW = one / W;
+        R vx = ux * iW, vy = uy * iW;
+        R vn = nx * vx + ny * vy, vt = -ny * vx + nx * vy;
+        R dU[4][4], s[4], lm, lp;
+        eigen_rhd<R>(gam, rho, vn, vt, p, W, dU, s, lm, lp);
+        R lhat = fmax(fab<R>(jt + Lk * lm), fab<R>(jt + Lk * lp));
+
+        constexpr int NS = WW + 1;              // stencil nodes
+        constexpr int OFF = (WW - 1) / 2;       // nodes left of c0
+        const R c1g = gam / (gam - one), ig = one / (gam - one);
+        R Vt[NS][4];
+        R aT[4] = {(R)0, (R)0, (R)0, (R)0};     // |T V| summed over the two interface nodes
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const long long c = c0 + (k - OFF) * sd;
+            R b = (R)q[Q_BETA * g.P + c];
+            R V0 = c1g + (R)q[Q_LNR * g.P + c] + ig * (R)q[Q_LNB * g.P + c] + b;
+            R Vx = b * (R)q[Q_UX * g.P + c];
+            R Vy = b * (R)q[Q_UY * g.P + c];
+            R VE = -b * (R)q[Q_W * g.P + c];
+            R T1 = nx * Vx + ny * Vy, T2 = -ny * Vx + nx * Vy;
+            if (k == OFF || k == OFF + 1) {
+                aT[0] += fab<R>(V0); aT[1] += fab<R>(T1); aT[2] += fab<R>(T2); aT[3] += fab<R>(VE);
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                Vt[k][m] = s[m] * (dU[0][m] * V0 + dU[1][m] * T1 + dU[2][m] * T2 + dU[3][m] * VE);
+        }
+        const R eps = (R)ph.eps;
+        const R sign_tol = (R)ph.sign_tol;
+        R z[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            R vminus, vplus;
+            if (WW == 5) {
+                vminus = weno5<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
+                vplus = weno5<R>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
+            } else {
+                vminus = weno3<R>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
+                vplus = weno3<R>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
+            }
+            R jw = vplus - vminus;
+            R jump = Vt[OFF + 1][m] - Vt[OFF][m];
+            // a jump within sign_tol of the magnitudes forming V~_m at the two
+            // interface nodes is rounding noise: its sign is 0 (so Y = 0)
+            R scale = s[m] * (fab<R>(dU[0][m]) * aT[0] + fab<R>(dU[1][m]) * aT[1] +
+                              fab<R>(dU[2][m]) * aT[2] + fab<R>(dU[3][m]) * aT[3]);
+            int sj = fab<R>(jump) <= sign_tol * scale ? 0 : sgn_d(jump);
+            z[m] = (sgn_d(jw) == sj) ? jw * s[m] : (R)0;
+        }
+        R d[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            d[a] = dU[a][0] * z[0] + dU[a][1] * z[1] + dU[a][2] * z[2] + dU[a][3] * z[3];
+        R hl = half * lhat;
+        F[0] -= hl * d[0];
+        F[1] -= hl * (nx * d[1] - ny * d[2]);
+        F[2] -= hl * (ny * d[1] + nx * d[2]);
+        F[3] -= hl * d[3];
+    }
+    R *out = iflux + (long long)(dir * 5) * g.P + c0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) out[a * g.P] = F[a];
+    out[4 * g.P] = (R)Ft;
+}
+
+template <typename R, int P>
+static void launch_pairs_p(const Geom &g, const Phys &ph, const double *q, R *pairs, int dir, cudaStream_t st)
+{
+    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
+    long long count = (long long)(nd + P) * no;
+    int bs = 128;
+    k_pairs<R, P><<<(unsigned)((count + bs - 1) / bs), bs, 0, st>>>(g, ph, q, pairs, dir);
+}
+
+template <typename R, int P, int WW>
+static void launch_iface_pw(const Geom &g, const Phys &ph, const double *q, const R *pairs, R *iflux,
+                            int dir, cudaStream_t st)
+{
+    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
+    long long count = (long long)(nd + 1) * no;
+    int bs = 128;
+    k_iface<R, P, WW><<<(unsigned)((count + bs - 1) / bs), bs, 0, st>>>(g, ph, q, pairs, iflux, dir);
+}
+
+template <typename R>
+void launch_pairs_t(const Geom &g, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st)
+{
+    R *pr = (R *)pairs;
+    switch (ph.p) {
+    case 1: launch_pairs_p<R, 1>(g, ph, q, pr, dir, st); break;
+    case 2: launch_pairs_p<R, 2>(g, ph, q, pr, dir, st); break;
+    default: launch_pairs_p<R, 3>(g, ph, q, pr, dir, st); break;
+    }
+}
+
+template <typename R, int P>
+static void launch_iface_p(const Geom &g, const Phys &ph, const double *q, const R *pr, R *fl, int dir,
+                           cudaStream_t st)
+{
+    switch (ph.w) {
+    case 0: launch_iface_pw<R, P, 0>(g, ph, q, pr, fl, dir, st); break;
+    case 3: launch_iface_pw<R, P, 3>(g, ph, q, pr, fl, dir, st); break;
+    default: launch_iface_pw<R, P, 5>(g, ph, q, pr, fl, dir, st); break;
+    }
+}
+
+template <typename R>
+void launch_iface_t(const Geom &g, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
+                    cudaStream_t st)
+{
+    const R *pr = (const R *)pairs;
+    R *fl = (R *)iflux;
+    switch (ph.p) {
+    case 1: launch_iface_p<R, 1>(g, ph, q, pr, fl, dir, st); break;
+    case 2: launch_iface_p<R, 2>(g, ph, q, pr, fl, dir, st); break;
+    default: launch_iface_p<R, 3>(g, ph, q, pr, fl, dir, st); break;
+    }
+}
+
+}  // namespace esmm

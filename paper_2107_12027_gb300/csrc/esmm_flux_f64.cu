@@ -1,0 +1,17 @@
+// esmm_flux_f64.cu -- flux kernels instantiated for the double working precision.
+#include "esmm_flux.cuh"
+
+namespace esmm {
+
+void launch_pairs_f64(const Geom &g, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st)
+{
+    launch_pairs_t<double>(g, ph, q, pairs, dir, st);
+}
+
+void launch_iface_f64(const Geom &g, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
+                       cudaStream_t st)
+{
+    launch_iface_t<double>(g, ph, q, pairs, iflux, dir, st);
+}
+
+}  // namespace esmm

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libesmm (the C ABI of ``include/esmm.h``).
+
+Argument marshalling only: every step of the scheme runs in the CUDA library.
+Arrays may be numpy arrays (host memory, ``ESMM_MEM_HOST``) or CUDA torch
+tensors (device memory, ``ESMM_MEM_DEVICE``); they must be C-contiguous FP64
+with the layouts of the header.  The library must have been built
+(``paper_2107_12027_gb300.build.build()``); importing this module without it,
+or calling into it without a GPU, raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_CUDA, ERR_C2P, ERR_TIMEOUT, ERR_STATE = 0, 1, 2, 3, 4, 5
+RHD = 0
+PERIODIC, OUTFLOW = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+FP64, MIXED = 0, 1
+MONITOR_RHO, MONITOR_LNRHO = 0, 1
+GET_PRIM, GET_CONS, GET_J, GET_X, GET_XDOT = 0, 1, 2, 3, 4
+_ERR = {1: "ESMM_ERR_ARG", 2: "ESMM_ERR_CUDA", 3: "ESMM_ERR_C2P", 4: "ESMM_ERR_TIMEOUT", 5: "ESMM_ERR_STATE"}
+
+#: every entry point declared in include/esmm.h
+SYMBOLS = (
+    "esmm_grid_create", "esmm_grid_destroy", "esmm_set_stream", "esmm_set_eos", "esmm_set_order",
+    "esmm_set_params", "esmm_get_params", "esmm_state_set", "esmm_state_set_cons", "esmm_state_get",
+    "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step",
+    "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
+)
+KIND_NODE, KIND_PAIRS, KIND_IFACE, KIND_UPDATE, KIND_MESH, KIND_OTHER = range(6)
+KINDS = ("node", "pairs", "iface", "update", "mesh", "other")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("monitor", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("n_filter", ctypes.c_int), ("mu", ctypes.c_int),
+                ("move_mesh", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+_lib = None
+
+
+class EsmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_ERR.get(code, code), msg))
+        self.code = code
+
+
+def lib():
+    """Load libesmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libesmm.so is not built (%s); run paper_2107_12027_gb300.build.build()" % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        dp = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "esmm_grid_create": [ctypes.POINTER(vp), i, ctypes.POINTER(i), dp, dp, i, ctypes.POINTER(i), vp],
+            "esmm_grid_destroy": [vp], "esmm_set_stream": [vp, vp], "esmm_set_eos": [vp, d],
+            "esmm_set_order": [vp, i, i], "esmm_set_params": [vp, ctypes.POINTER(Params)],
+            "esmm_get_params": [vp, ctypes.POINTER(Params)], "esmm_state_set": [vp, vp, vp, i],
+            "esmm_state_set_cons": [vp, vp, vp, vp, d, i], "esmm_state_get": [vp, i, vp, i],
+            "esmm_get_time": [vp, dp], "esmm_rhs": [vp, vp, vp, vp, vp, vp, vp, i],
+            "esmm_cfl_dt": [vp, dp], "esmm_mesh_redistribute": [vp, d, vp, dp, i],
+            "esmm_rk_step": [vp, d, dp], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
+            "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
+            "esmm_profile": [vp, i],
+            "esmm_profile_read": [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.esmm_version.restype = ctypes.c_char_p
+        L.esmm_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().esmm_version().decode()
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, n=None):
+    """(pointer, mem) of a numpy array or CUDA torch tensor (FP64, contiguous)."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+        assert a.dtype == torch.float64 and a.is_cuda and a.is_contiguous(), "need a contiguous CUDA float64 tensor"
+        assert n is None or a.numel() == n
+        return ctypes.c_void_p(a.data_ptr()), MEM_DEVICE
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], \
+        "need a C-contiguous float64 numpy array"
+    assert n is None or a.size == n
+    return ctypes.c_void_p(a.ctypes.data), MEM_HOST
+
+
+def _mem(*arrays):
+    mems = {m for _, m in arrays if m is not None}
+    assert len(mems) == 1, "arrays must all be host (numpy) or all device (torch)"
+    return mems.pop()
+
+
+class Grid:
+    """One 2D RHD problem: a handle of the C ABI plus argument marshalling."""
+
+    def __init__(self, n, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC), gamma=5.0 / 3.0, p=2, w=5,
+                 stream=None, **params):
+        self.nx, self.ny = int(n[0]), int(n[1])
+        self.N = self.nx * self.ny
+        h = ctypes.c_void_p()
+        nn = (ctypes.c_int * 3)(self.nx, self.ny, 1)
+        lo3 = (ctypes.c_double * 3)(lo[0], lo[1], 0.0)
+        hi3 = (ctypes.c_double * 3)(hi[0], hi[1], 1.0)
+        bc3 = (ctypes.c_int * 3)(bc[0], bc[1], 0)
+        st = ctypes.c_void_p(stream) if stream is not None else None
+        self._check(lib().esmm_grid_create(ctypes.byref(h), 2, nn, lo3, hi3, RHD, bc3, st))
+        self.h = h
+        self.set_eos(gamma)
+        self.set_order(p, w)
+        if params:
+            self.set_params(**params)
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            msg = ""
+            h = getattr(self, "h", None)
+            if h is not None:
+                buf = ctypes.create_string_buffer(256)
+                lib().esmm_last_error(h, None, buf, 256)
+                msg = buf.value.decode()
+            raise EsmmError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lib().esmm_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration -------------------------------------------------------
+    def set_stream(self, stream):
+        self._check(lib().esmm_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def set_eos(self, gamma):
+        self._check(lib().esmm_set_eos(self.h, float(gamma)))
+
+    def set_order(self, p, w):
+        self._check(lib().esmm_set_order(self.h, int(p), int(w)))
+
+    def get_params(self):
+        prm = Params()
+        self._check(lib().esmm_get_params(self.h, ctypes.byref(prm)))
+        return {k: getattr(prm, k) for k, _ in Params._fields_}
+
+    def set_params(self, **kw):
+        cur = self.get_params()
+        cur.update(kw)
+        prm = Params(**cur)
+        self._check(lib().esmm_set_params(self.h, ctypes.byref(prm)))
+
+    # -- state ----------------------------------------------------------------
+    def state_set(self, prim, x=None):
+        pp, mp = _ptr(prim, 4 * self.N)
+        px, mx = _ptr(x, 2 * self.N)
+        self._check(lib().esmm_state_set(self.h, pp, px, _mem((pp, mp), (px, mx))))
+
+    def state_set_cons(self, cons, J, x, t=0.0):
+        a = [_ptr(cons, 4 * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N)]
+        self._check(lib().esmm_state_set_cons(self.h, a[0][0], a[1][0], a[2][0], float(t), _mem(*a)))
+
+    def state_get(self, what, out=None):
+        size = {GET_PRIM: 4, GET_CONS: 4, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
+        shape = (size, self.ny, self.nx) if size > 1 else (self.ny, self.nx)
+        if out is None:
+            out = np.empty(shape)
+        po, mo = _ptr(out, size * self.N)
+        self._check(lib().esmm_state_get(self.h, what, po, mo))
+        return out
+
+    def time(self):
+        t = ctypes.c_double()
+        self._check(lib().esmm_get_time(self.h, ctypes.byref(t)))
+        return t.value
+
+    # -- the scheme -----------------------------------------------------------
+    def rhs(self, cons, J, x, xdot=None, dcons=None, dJ=None):
+        """d(cons)/dt, dJ/dt of the semi-discrete ES scheme (host or device)."""
+        host = not _is_torch(cons)
+        if dcons is None:
+            if host:
+                dcons, dJ = np.empty((4, self.ny, self.nx)), np.empty((self.ny, self.nx))
+            else:
+                import torch
+                dcons = torch.empty((4, self.ny, self.nx), dtype=torch.float64, device=cons.device)
+                dJ = torch.empty((self.ny, self.nx), dtype=torch.float64, device=cons.device)
+        a = [_ptr(cons, 4 * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N)]
+        xd = _ptr(xdot, 2 * self.N)
+        o = [_ptr(dcons, 4 * self.N), _ptr(dJ, self.N)]
+        mem = _mem(*a, *o, *([xd] if xdot is not None else []))
+        self._check(lib().esmm_rhs(self.h, a[0][0], a[1][0], a[2][0], xd[0], o[0][0], o[1][0], mem))
+        return dcons, dJ
+
+    def cfl_dt(self):
+        dt = ctypes.c_double()
+        self._check(lib().esmm_cfl_dt(self.h, ctypes.byref(dt)))
+        return dt.value
+
+    def mesh_redistribute(self, dt=0.0):
+        xdot = np.empty((2, self.ny, self.nx))
+        tau = ctypes.c_double()
+        self._check(lib().esmm_mesh_redistribute(self.h, float(dt), ctypes.c_void_p(xdot.ctypes.data),
+                                                  ctypes.byref(tau), MEM_HOST))
+        return xdot, tau.value
+
+    def rk_step(self, dt=0.0, sync=True):
+        """One SSP-RK3 step; returns the step used when sync (else None)."""
+        if sync:
+            d = ctypes.c_double()
+            self._check(lib().esmm_rk_step(self.h, float(dt), ctypes.byref(d)))
+            return d.value
+        self._check(lib().esmm_rk_step(self.h, float(dt), None))
+        return None
+
+    def advance(self, nsteps, dt=0.0):
+        self._check(lib().esmm_advance(self.h, int(nsteps), float(dt)))
+
+    def totals(self):
+        out = (ctypes.c_double * 3)()
+        self._check(lib().esmm_totals(self.h, out))
+        return np.array(out[:])
+
+    def profile(self, mask=0):
+        """Reset the launch counters; time the kernel kinds in mask (bit k = kind k)."""
+        self._check(lib().esmm_profile(self.h, int(mask)))
+
+    def profile_read(self):
+        """{kind: (device ms of timed launches, launches, timed launches)}."""
+        ms = (ctypes.c_double * 6)()
+        n = (ctypes.c_longlong * 6)()
+        t = (ctypes.c_longlong * 6)()
+        self._check(lib().esmm_profile_read(self.h, ms, n, t))
+        return {KINDS[k]: (ms[k], n[k], t[k]) for k in range(6)}
+
+    def last_error(self):
+        n = ctypes.c_int()
+        buf = ctypes.create_string_buffer(256)
+        self._check(lib().esmm_last_error(self.h, ctypes.byref(n), buf, 256))
+        return n.value, buf.value.decode()

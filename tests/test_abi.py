@@ -1,0 +1,34 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/esmm.h (no compute calls: this runs without a GPU)."""
+import os
+import re
+
+from paper_2107_12027_gb300 import build, esmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "esmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(esmm_[a-z_]+)\s*\(", src))
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    declared = _declared()
+    assert "esmm_rhs" in declared and "esmm_rk_step" in declared
+    assert declared == set(esmm.SYMBOLS)
+    L = esmm.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert "sm_103a" in esmm.version()
+
+
+def test_binding_rejects_wrong_array_types():
+    import numpy as np
+    import pytest
+    with pytest.raises(AssertionError):
+        esmm._ptr(np.zeros(4, dtype=np.float32))
+    with pytest.raises(AssertionError):
+        esmm._ptr(np.zeros((4, 4))[:, ::2])

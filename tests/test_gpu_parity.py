@@ -1,0 +1,211 @@
+"""GPU (sm_103a) path against the FP64 oracle, element by element.
+
+Every call goes through the C ABI (libesmm via the ctypes binding).  The FP64
+form must match the oracle to 1e-12 relative (max-norm per component,
+relative to that component's max-norm) per right-hand side and per RK stage.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_12027_gb300 import esmm
+from paper_2107_12027_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    if a.ndim == 3:
+        return max(_rel(a[c], b[c]) for c in range(a.shape[0]))
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _grid(nx, ny, bc, lo, hi, p, w, **kw):
+    return esmm.Grid((nx, ny), lo, hi, bc=bc, p=p, w=w, **kw)
+
+
+def _cfg(nx, ny, bc, lo, hi, p, w, **kw):
+    per = (hi[0] - lo[0], hi[1] - lo[1])
+    return oracle.make_cfg(nx, ny, bc=bc, period=per, p=p, w=w, **kw)
+
+
+def _case_smooth(nx, ny, seed):
+    x = wl.wavy_mesh(nx, ny, amp=0.04)
+    xdot = wl.wavy_mesh_velocity(nx, ny, amp=0.04, t=1.3)
+    prim = wl.smooth_random_state(x, wl.rng(seed))
+    return x, xdot, prim
+
+
+def _case_riemann(nx, ny, seed):
+    x = wl.random_mesh(nx, ny, wl.rng(seed), amp=0.2, lo=(-1, -1), hi=(1, 1), periodic=(False, False))
+    xdot = wl.rng(seed + 1).uniform(-0.3, 0.3, x.shape)
+    xdot[:, :, 0] = xdot[:, :, -1] = 0.0
+    xdot[:, 0, :] = xdot[:, -1, :] = 0.0
+    prim = wl.quadrant_riemann(x, wl.quadrant_states(wl.rng(seed + 2)), split=(0.1, -0.2))
+    return x, xdot, prim
+
+
+@pytest.mark.parametrize("p,w", [(1, 0), (2, 0), (3, 0), (1, 3), (2, 3), (2, 5), (3, 5)])
+def test_rhs_parity_smooth_periodic_moving_mesh(p, w):
+    nx, ny = 53, 37          # several 128-thread blocks, ragged tails
+    x, xdot, prim = _case_smooth(nx, ny, 40 + p + w)
+    cfg = _cfg(nx, ny, (0, 0), (0, 0), (1, 1), p, w)
+    cons, J = oracle.init_state(cfg, prim, x)
+    ref = oracle.rhs(cfg, cons, J, x, xdot)
+    with _grid(nx, ny, (0, 0), (0, 0), (1, 1), p, w) as g:
+        got = g.rhs(cons, J, x, xdot)
+    assert _rel(got[0], ref[0]) < TOL
+    assert _rel(got[1], ref[1]) < TOL
+
+
+@pytest.mark.parametrize("p,w", [(2, 0), (2, 5), (3, 5), (2, 3)])
+def test_rhs_parity_discontinuous_outflow(p, w):
+    nx, ny = 61, 45
+    x, xdot, prim = _case_riemann(nx, ny, 50 + p + w)
+    cfg = _cfg(nx, ny, (1, 1), (-1, -1), (1, 1), p, w)
+    cons, J = oracle.init_state(cfg, prim, x)
+    ref = oracle.rhs(cfg, cons, J, x, xdot)
+    with _grid(nx, ny, (1, 1), (-1, -1), (1, 1), p, w) as g:
+        got = g.rhs(cons, J, x, xdot)
+    assert _rel(got[0], ref[0]) < TOL
+    assert _rel(got[1], ref[1]) < TOL
+
+
+def test_rhs_parity_mixed_boundaries_and_tiny_grid():
+    for (nx, ny, bc) in ((4, 4, (0, 0)), (5, 7, (0, 1)), (9, 4, (1, 0))):
+        x, xdot, prim = _case_smooth(nx, ny, 60)
+        if bc[1] == 1:
+            xdot[:, 0, :] = xdot[:, -1, :] = 0.0
+        if bc[0] == 1:
+            xdot[:, :, 0] = xdot[:, :, -1] = 0.0
+        cfg = _cfg(nx, ny, bc, (0, 0), (1, 1), 2, 5)
+        cons, J = oracle.init_state(cfg, prim, x)
+        ref = oracle.rhs(cfg, cons, J, x, xdot)
+        with _grid(nx, ny, bc, (0, 0), (1, 1), 2, 5) as g:
+            got = g.rhs(cons, J, x, xdot)
+        assert _rel(got[0], ref[0]) < TOL, (nx, ny, bc)
+        assert _rel(got[1], ref[1]) < TOL, (nx, ny, bc)
+
+
+def test_state_set_and_cfl_parity():
+    nx, ny = 64, 48
+    x, prim = wl.riemann_config(nx)[0][:, :ny, :], None
+    x = wl.random_mesh(nx, ny, wl.rng(70), amp=0.2, lo=(-1, -1), hi=(1, 1), periodic=(False, False))
+    prim = wl.quadrant_riemann(x, wl.quadrant_states(wl.rng(71)))
+    cfg = _cfg(nx, ny, (1, 1), (-1, -1), (1, 1), 2, 5)
+    cons, J = oracle.init_state(cfg, prim, x)
+    with _grid(nx, ny, (1, 1), (-1, -1), (1, 1), 2, 5) as g:
+        g.state_set(prim, x)
+        assert _rel(g.state_get(esmm.GET_J), J) < 1e-14
+        assert _rel(g.state_get(esmm.GET_CONS), cons) < 1e-14
+        assert _rel(g.state_get(esmm.GET_PRIM), prim) < 1e-12
+        assert abs(g.cfl_dt() / oracle.cfl_dt(cfg, cons, J, x) - 1) < 1e-13
+
+
+@pytest.mark.parametrize("case", ["riemann", "sine"])
+def test_mesh_redistribution_parity(case):
+    if case == "riemann":
+        n = 56
+        x, prim = wl.riemann_config(n)
+        bc, lo, hi = (1, 1), (-1, -1), (1, 1)
+        kw = dict(alpha=1200.0, monitor=oracle.MONITOR_LNRHO)
+    else:
+        n = 40
+        x, prim = wl.sine_config(n)
+        bc, lo, hi = (0, 0), (0, 0), (1, 1)
+        kw = dict(alpha=20.0, monitor=oracle.MONITOR_RHO)
+    cfg = _cfg(n, n, bc, lo, hi, 2, 5, **kw)
+    cons, J = oracle.init_state(cfg, prim, x)
+    dt = oracle.cfl_dt(cfg, cons, J, x)
+    xd_ref, tau_ref = oracle.mesh(cfg, cons, J, x, dt)
+    with _grid(n, n, bc, lo, hi, 2, 5, **kw) as g:
+        g.state_set(prim, x)
+        xd, tau = g.mesh_redistribute(0.0)
+    assert abs(tau - tau_ref) <= 1e-13 * max(tau_ref, 1e-300)
+    assert _rel(xd, xd_ref) < 1e-11
+
+
+@pytest.mark.parametrize("case", ["sine", "riemann"])
+def test_rk_step_parity(case):
+    if case == "sine":
+        n = 48
+        x, prim = wl.sine_config(n)
+        bc, lo, hi, kw = (0, 0), (0, 0), (1, 1), dict(alpha=20.0, monitor=oracle.MONITOR_RHO)
+    else:
+        n = 48
+        x, prim = wl.riemann_config(n)
+        bc, lo, hi, kw = (1, 1), (-1, -1), (1, 1), dict(alpha=1200.0, monitor=oracle.MONITOR_LNRHO)
+    cfg = _cfg(n, n, bc, lo, hi, 2, 5, **kw)
+    cons, J = oracle.init_state(cfg, prim, x)
+    with _grid(n, n, bc, lo, hi, 2, 5, **kw) as g:
+        g.state_set(prim, x)
+        for step in range(3):
+            cons, J, x, dt_ref = oracle.rk_step(cfg, cons, J, x)
+            dt = g.rk_step()
+            assert abs(dt / dt_ref - 1) < 1e-12
+            assert _rel(g.state_get(esmm.GET_CONS), cons) < TOL, step
+            assert _rel(g.state_get(esmm.GET_J), J) < TOL, step
+            assert _rel(g.state_get(esmm.GET_X), x) < TOL, step
+        tot = g.totals()
+    ref = oracle.totals(cfg, cons, J)
+    np.testing.assert_allclose(tot, ref[:3], rtol=1e-12)
+
+
+def test_free_stream_on_gpu():
+    n = 40
+    x = wl.random_mesh(n, n, wl.rng(80), amp=0.3)
+    w0 = np.array([0.7, 0.4, -0.5, 1.3])
+    prim = np.ascontiguousarray(np.broadcast_to(w0[:, None, None], (4, n, n)))
+    with _grid(n, n, (0, 0), (0, 0), (1, 1), 3, 5) as g:
+        g.state_set(prim, x)
+        for _ in range(5):
+            g.rk_step()
+        got = g.state_get(esmm.GET_PRIM)
+        assert np.abs(g.state_get(esmm.GET_X) - x).max() > 1e-3
+    np.testing.assert_allclose(got, prim, rtol=0, atol=2e-13)
+
+
+def test_error_paths():
+    n = 16
+    x = wl.uniform_mesh(n, n)
+    prim = np.ascontiguousarray(np.broadcast_to(np.array([1.0, 0.2, 0.1, 1.0])[:, None, None], (4, n, n)))
+    with _grid(n, n, (0, 0), (0, 0), (1, 1), 2, 5) as g:
+        bad = prim.copy()
+        bad[1, 3, 3] = 1.2      # |v| > 1
+        with pytest.raises(esmm.EsmmError) as e:
+            g.state_set(bad, x)
+        assert e.value.code == esmm.ERR_ARG
+        with pytest.raises(esmm.EsmmError) as e:
+            g.rk_step()
+        assert e.value.code == esmm.ERR_STATE
+        g.state_set(prim, x)
+        cfg = oracle.make_cfg(n, n)
+        cons, J = oracle.init_state(cfg, prim, x)
+        cons = cons.copy()
+        cons[3, 5, 5] = 0.1 * cons[0, 5, 5]   # E < D: no admissible pressure
+        with pytest.raises(esmm.EsmmError) as e:
+            g.rhs(cons, J, x)
+        assert e.value.code == esmm.ERR_C2P
+        with pytest.raises(esmm.EsmmError):
+            g.set_order(4, 5)
+        with pytest.raises(esmm.EsmmError):
+            g.set_eos(2.5)
+
+
+@pytest.mark.parametrize("p,w", [(2, 5)])
+def test_rhs_parity_full_size_riemann_400(p, w):
+    # the benchmark's workload size, in the launch configuration it times
+    n = 400
+    x, prim = wl.riemann_config(n)
+    cfg = _cfg(n, n, (1, 1), (-1, -1), (1, 1), p, w, alpha=1200.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    xdot = wl.rng(90).uniform(-0.2, 0.2, x.shape)
+    xdot[:, :, 0] = xdot[:, :, -1] = 0.0
+    xdot[:, 0, :] = xdot[:, -1, :] = 0.0
+    ref = oracle.rhs(cfg, cons, J, x, xdot)
+    with _grid(n, n, (1, 1), (-1, -1), (1, 1), p, w, alpha=1200.0) as g:
+        got = g.rhs(cons, J, x, xdot)
+    assert _rel(got[0], ref[0]) < TOL
+    assert _rel(got[1], ref[1]) < TOL
