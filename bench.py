@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the ES adaptive moving-mesh 2D RHD scheme on GB300.
+
+Workload (default): the 2D RHD four-quadrant Riemann problem on [-1,1]^2 with
+400 x 400 nodes, outflow boundaries, Gamma = 5/3, seeded states (rho in
+[0.1,1], |v| <= 0.9, p in [0.01,1]), adaptive moving mesh (sigma = ln rho,
+alpha = 1200, 4 filter passes, 10 Jacobi sweeps), 4th-order EC flux (p = 2)
+with WENO5 dissipation, SSP-RK3 at CFL 0.4.  A step is one full rk_step: CFL
+reduction, mesh redistribution and three RK stages.
+
+Metric: cell-updates/s per RK stage = nodes * 3 * steps / device time.  Every
+timed step starts with the L2 cache flushed (a 256 MB write outside the timed
+events).  Under torchrun each rank runs its own independent problem (weak
+scaling, no data-path collective).
+
+``--impl reference`` times the FP64 CPU oracle (the paper's method restated
+plainly in C) on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage"
+UNIT = "cell-updates/s"
+N_SIDE = 400
+WORKLOAD = ("2D RHD four-quadrant Riemann problem, 400x400 nodes on [-1,1]^2, outflow, Gamma=5/3, seeded states "
+            "(rho in [0.1,1], |v|<=0.9, p in [0.01,1]), adaptive moving mesh (sigma=ln rho, alpha=1200, 4 filter "
+            "passes, 10 Jacobi sweeps), 4th-order EC flux (p=2) + WENO5 dissipation, SSP-RK3, CFL 0.4")
+# FP64 operations executed per interface by the FP64 interface kernel (p=2,
+# WENO5), from the ncu SASS counters dadd + dmul + 2 dfma of one capture
+# (profiles/iface_f64_riemann400.md); FLOP = add, mul, or half an FMA.
+FLOPS_PER_IFACE_F64 = None
+# Derived FP64 peak of GB300: 152 SMs x 4 FP64 flop/clk/SM (1.25 TFLOP/s at
+# the 2070 MHz maximum SM clock).
+FP64_FLOP_PER_CLK_SM = 4
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and mixed-form legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(n, rank=0):
+    from paper_2107_12027_gb300 import workloads as wl
+    return wl.riemann_config(n, offset=1 + rank)
+
+
+def grid_params(form):
+    from paper_2107_12027_gb300 import esmm
+    return dict(cfl=0.4, alpha=1200.0, monitor=esmm.MONITOR_LNRHO, n_filter=4, mu=10, move_mesh=1,
+                precision=esmm.MIXED if form == "mixed" else esmm.FP64)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample_rate(n, budget_s, nsteps=1, rows=None):
+    """Time the FP64 oracle's rk_step on a 400-wide strip of the workload
+    (rows chosen so the run takes about budget_s); returns (cell-updates/s,
+    description)."""
+    import oracle
+    x, prim = workload(n)
+    if rows is None:
+        r0 = 16
+        cfg = oracle.make_cfg(n, r0, bc=(1, 1), period=(2.0, 2.0), p=2, w=5, alpha=1200.0,
+                              monitor=oracle.MONITOR_LNRHO)
+        j0 = n // 2 - r0 // 2
+        xs, ps = np.ascontiguousarray(x[:, j0:j0 + r0]), np.ascontiguousarray(prim[:, j0:j0 + r0])
+        cons, J = oracle.init_state(cfg, ps, xs)
+        t = time.perf_counter()
+        oracle.rk_step(cfg, cons, J, xs)
+        per_row = (time.perf_counter() - t) / r0
+        rows = int(max(8, min(n, budget_s / max(nsteps * per_row, 1e-9))))
+    j0 = max(0, n // 2 - rows // 2)
+    cfg = oracle.make_cfg(n, rows, bc=(1, 1), period=(2.0, 2.0), p=2, w=5, alpha=1200.0,
+                          monitor=oracle.MONITOR_LNRHO)
+    xs, ps = np.ascontiguousarray(x[:, j0:j0 + rows]), np.ascontiguousarray(prim[:, j0:j0 + rows])
+    cons, J = oracle.init_state(cfg, ps, xs)
+    t = time.perf_counter()
+    for _ in range(nsteps):
+        cons, J, xs, _ = oracle.rk_step(cfg, cons, J, xs)
+    el = time.perf_counter() - t
+    rate = n * rows * 3 * nsteps / el
+    desc = ("%d rk_step(s) of the FP64 C oracle (single thread) on the central %dx%d strip of the %dx%d workload"
+            % (nsteps, n, rows, n, n))
+    return rate, desc, rows
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    budget = 150.0 / max(1, K + W)      # whole run in about 2.5 minutes
+    _, _, rows = oracle_sample_rate(args.n, budget, 1)
+    rates = []
+    for s in range(W + K):
+        rate, desc, _ = oracle_sample_rate(args.n, budget, 1, rows=rows)
+        if s >= W:
+            rates.append(rate)
+    value = float(len(rates) / sum(1.0 / r for r in rates))
+    ms = args.n * args.n * 3 / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": args.n * args.n, "form": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU legs
+def timed_steps(g, torch, K, W, flush, stream, clock=None):
+    for _ in range(W):
+        g.rk_step(sync=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    from paper_2107_12027_gb300 import esmm
+    g.profile(1 << esmm.KIND_IFACE)
+    if clock:
+        clock.start()
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            g.rk_step(sync=False)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clock.stop() if clock else None
+    prof = g.profile_read()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    return total_ms, prof, clk
+
+
+def e2e_leg(torch, n, form, K, W, stream):
+    """Same metric through the public API with host buffers: every step copies
+    the state in from pinned host memory and reads it back."""
+    from paper_2107_12027_gb300 import esmm
+    x, prim = workload(n)
+    with esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
+                   stream=stream.cuda_stream, **grid_params(form)) as g:
+        g.state_set(prim, x)
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        cons, J, xs = pin((4, n, n)), pin((n, n)), pin((2, n, n))
+        g.state_get(esmm.GET_CONS, cons)
+        g.state_get(esmm.GET_J, J)
+        g.state_get(esmm.GET_X, xs)
+        t = 0.0
+
+        def one():
+            g.state_set_cons(cons, J, xs, t)
+            g.rk_step(sync=False)
+            g.state_get(esmm.GET_CONS, cons)
+            g.state_get(esmm.GET_J, J)
+            g.state_get(esmm.GET_X, xs)
+        for _ in range(W):
+            one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            one()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    nb = (4 + 1 + 2) * n * n * 8
+    return {"value": n * n * 3 * K / el, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+
+def mixed_vs_fp64(torch, n, stream, nsteps=20):
+    """Mixed form against the FP64 form (itself at 1e-12 of the oracle) after
+    nsteps steps with the same fixed dt: L1 density error and entropy drift."""
+    from paper_2107_12027_gb300 import esmm
+    x, prim = workload(n)
+    out = {}
+    for form in ("fp64", "mixed"):
+        with esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
+                       stream=stream.cuda_stream, **grid_params(form)) as g:
+            g.state_set(prim, x)
+            if form == "fp64":
+                dt = 0.9 * g.cfl_dt()
+            S0 = g.totals()[0]
+            g.advance(nsteps, dt)
+            out[form] = (g.state_get(esmm.GET_PRIM)[0], g.totals()[0], S0)
+    rf, rm = out["fp64"][0], out["mixed"][0]
+    return {"steps": nsteps, "dt": dt,
+            "l1_rho_rel": float(np.abs(rm - rf).mean() / np.abs(rf).mean()),
+            "entropy_rel_diff": float(abs(out["mixed"][1] - out["fp64"][1]) / abs(out["fp64"][1])),
+            "entropy_change_fp64": float((out["fp64"][1] - out["fp64"][2]) / abs(out["fp64"][2])),
+            "entropy_change_mixed": float((out["mixed"][1] - out["mixed"][2]) / abs(out["mixed"][2]))}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2107_12027_gb300 import esmm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    esmm.lib()
+    stream = torch.cuda.Stream()
+    n, K, W = args.n, args.steps, args.warmup
+    x, prim = workload(n, rank)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    g = esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
+                  stream=stream.cuda_stream, **grid_params(args.form))
+    g.state_set(prim, x)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock = ClockSampler(local) if rank == 0 else None
+    total_ms, prof, clk = timed_steps(g, torch, K, W, flush, stream, clock)
+    nfail, msg = g.last_error()
+    if nfail:
+        raise RuntimeError("primitive recovery failed at %d nodes: %s" % (nfail, msg))
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    total_ms = float(t.item())
+    value = world * n * n * 3 * K / (total_ms * 1e-3)
+    launches = int(sum(v[1] for v in prof.values()))
+    g.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel: the FP64 interface kernel is bound by
+    # the FP64 pipe (no dense contraction, ~20 FP64 flop per byte)
+    iface_ms, iface_n, iface_timed = prof["iface"]
+    ifaces_per_launch = ((n + 1) * n + (n + 1) * n) / 2.0
+    avg_launch_s = iface_ms * 1e-3 / max(iface_timed, 1)
+    roof = None
+    if args.form == "fp64":
+        peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        if FLOPS_PER_IFACE_F64:
+            ach = FLOPS_PER_IFACE_F64 * ifaces_per_launch / avg_launch_s / 1e12
+        else:
+            ach = None
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": (ach / peak) if ach else None, "traffic": None,
+                "kernel": "k_iface<double,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
+                "share_of_step": iface_ms / total_ms,
+                "peak_note": "derived FP64 peak: 152 SMs x 4 flop/clk x 2070 MHz"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.form == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": n * n, "form": args.form,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "independent problem per rank" if world > 1 else "single GPU"},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if not args.no_extras:
+        line["e2e"] = e2e_leg(torch, n, args.form, max(3, K // 4), 2, stream)
+        rate, desc, _ = oracle_sample_rate(n, 15.0, 1)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        if args.form == "fp64":
+            with esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
+                           stream=stream.cuda_stream, **grid_params("mixed")) as gm:
+                gm.state_set(prim, x)
+                tm, _, _ = timed_steps(gm, torch, K, W, flush, stream, None)
+            forms = {"mixed": {"value": n * n * 3 * K / (tm * 1e-3), "ms_per_step": tm / K}}
+            forms["mixed"].update(mixed_vs_fp64(torch, n, stream))
+            line["forms"] = forms
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

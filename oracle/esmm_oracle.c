@@ -592,13 +592,17 @@ static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, do
      * vector, so that the first row is n) and the tangent t = (-n_y, n_x). */
     double nx_ = nvx / Lk, ny_ = nvy / Lk;
     double tx_ = -ny_, ty_ = nx_;
-    /* Reading: the interface state is the mean of (rho, u = W v, p). */
+    /* Reading: D is evaluated at the interface state built from the averages
+     * of the two-point EC flux: rho = {{rho}}^ln, u = {{u}} (u = W v) and
+     * p = {{rho}}/{{beta}} (beta = rho/p).  (With the arithmetic mean of
+     * (rho, u, p) the dissipation R R^T [[V]] turns anti-diffusive when beta
+     * jumps by two orders of magnitude across an interface.) */
     double WL = 1.0 / sqrt(1.0 - (wL[1] * wL[1] + wL[2] * wL[2]));
     double WR = 1.0 / sqrt(1.0 - (wR[1] * wR[1] + wR[2] * wR[2]));
-    double rho_m = 0.5 * (wL[0] + wR[0]);
+    double rho_m = oref_logmean(wL[0], wR[0]);
     double ux_m = 0.5 * (WL * wL[1] + WR * wR[1]);
     double uy_m = 0.5 * (WL * wL[2] + WR * wR[2]);
-    double p_m = 0.5 * (wL[3] + wR[3]);
+    double p_m = (0.5 * (wL[0] + wR[0])) / (0.5 * (wL[0] / wL[3] + wR[0] / wR[3]));
     double W_m = sqrt(1.0 + ux_m * ux_m + uy_m * uy_m);
     double vx_m = ux_m / W_m, vy_m = uy_m / W_m;
     double wrot[4] = {rho_m, nx_ * vx_m + ny_ * vy_m, tx_ * vx_m + ty_ * vy_m, p_m};

@@ -115,11 +115,15 @@ __global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__
         R Lk = sq_rt<R>(nvx * nvx + nvy * nvy);
         R iLk = one / Lk;
         R nx = nvx * iLk, ny = nvy * iLk;
-        // interface state: mean of (rho, u, p) of the two nodes
-        R rho = half * ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]);
+        // interface state from the two-point flux averages:
+        // rho = {{rho}}^ln, u = {{u}}, p = {{rho}}/{{beta}}
+        R rho, irho;
+        logmean<R>(q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1], q[Q_LNR * g.P + c0], q[Q_LNR * g.P + c1],
+                   ph.ln_thr, rho, irho);
         R ux = half * ((R)q[Q_UX * g.P + c0] + (R)q[Q_UX * g.P + c1]);
         R uy = half * ((R)q[Q_UY * g.P + c0] + (R)q[Q_UY * g.P + c1]);
-        R p = half * ((R)q[Q_P * g.P + c0] + (R)q[Q_P * g.P + c1]);
+        R p = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) /
+              ((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
         R W = sq_rt<R>(one + ux * ux + uy * uy);
         R iW = one / W;
         R vx = ux * iW, vy = uy * iW;
