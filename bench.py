@@ -50,8 +50,8 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--n", type=int, default=N_SIDE)
@@ -319,7 +319,7 @@ def run_gpu(args):
                        "parallelism": "independent problem per rank" if world > 1 else "single GPU"},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
     if not args.no_extras:
-        line["e2e"] = e2e_leg(torch, n, args.form, max(3, K // 4), 2, stream)
+        line["e2e"] = e2e_leg(torch, n, args.form, max(3, min(K, 50)), 2, stream)
         rate, desc, _ = oracle_sample_rate(n, 15.0, 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
         if args.form == "fp64":
