@@ -167,6 +167,35 @@ int esmm_profile(esmm_grid *g, int mask);
 int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
                       long long timed[ESMM_NKINDS]);
 
+/* Allocation-free right-hand side.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * running under an allocator or memory budget it does not own (a plug-in, a
+ * solver embedded in another framework, a library driven from inside a
+ * captured or pooled context) cannot call cudaMalloc or create a grid.
+ *
+ * Same arithmetic as esmm_rhs in the FP64 form (WENO epsilon 1e-6): d(cons)/dt
+ * and dJ/dt of the ES scheme for an nx x ny grid with boundaries bc[2] on the
+ * box [lo, hi].  All array pointers are DEVICE pointers on the current device
+ * with the layouts above (xdot may be NULL); the caller owns inputs and
+ * outputs.  The call only enqueues work on stream (a cudaStream_t, NULL for
+ * the legacy default stream) and returns; it allocates nothing (no cudaMalloc,
+ * no cudaFree, no allocating library routine).
+ *
+ * Scratch: one file-scope device array sized for (nx+6)*(ny+6) <=
+ * ESMM_STATIC_MAX_PADDED_NODES (e.g. grids up to 256 x 256), 48 doubles per
+ * padded node (~26 MB), held by every GPU that loads the library until the
+ * process exits.  Larger grids return ESMM_ERR_ARG, as do invalid arguments.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the one array and overwrites it, so calls that
+ * overlap on the GPU (other streams, other threads) race; serialise them.
+ * Primitive-recovery failures are not reported (those nodes' outputs are
+ * undefined). */
+#define ESMM_STATIC_MAX_PADDED_NODES 68644
+int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const double hi[2], double gamma,
+                    int p, int w, const double *cons, const double *J, const double *x, const double *xdot,
+                    double *dcons, double *dJ, void *stream);
+
 /* Library version string. */
 const char *esmm_version(void);
 

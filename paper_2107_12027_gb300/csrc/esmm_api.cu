@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <new>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -744,6 +745,44 @@ int copy_out(esmm_grid *g, double *dst, const double *src, size_t n, int mem)
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Allocation-free right-hand side (esmm_rhs_static).
+//
+// Its scratch lives in one file-scope device array: per padded node the NQ
+// node arrays, the pair fluxes [2][PMAX][4] and the interface fluxes [2][5]
+// (48 doubles), then two status ints.  Every GPU that loads the library holds
+// this array until the process exits.  Host code only ever passes the
+// device address obtained from cudaGetSymbolAddress: in host code the
+// array's name is a host-side stand-in, not a device address.
+constexpr long long STATIC_PER_NODE = NQ + 2 * PMAX * 4 + 2 * 5;
+constexpr long long STATIC_DOUBLES = STATIC_PER_NODE * ESMM_STATIC_MAX_PADDED_NODES + 32;
+static __device__ __align__(256) double esmm_static_scratch[STATIC_DOUBLES];
+
+namespace {
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex static_mu;
+double *static_ptr[STATIC_MAX_DEVICES];     // device address per device, set once
+
+// Device address of the scratch on the current device (set-up on the first
+// call per device, with that device current).
+cudaError_t static_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(static_mu);
+    if (!static_ptr[dev]) {
+        double *p = nullptr;
+        e = cudaGetSymbolAddress((void **)&p, esmm_static_scratch);
+        if (e != cudaSuccess) return e;
+        static_ptr[dev] = p;
+    }
+    *out = static_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 // ===========================================================================
 extern "C" {
 
@@ -1111,6 +1150,59 @@ int esmm_totals(esmm_grid *g, double out[3])
     CK(cudaStreamSynchronize(g->st));
     for (int k = 0; k < 3; ++k) out[k] = g->pin[k];
     return check_c2p(g);
+}
+
+int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const double hi[2], double gamma, int p,
+                    int w, const double *cons, const double *J, const double *x, const double *xdot, double *dcons,
+                    double *dJ, void *stream)
+{
+    if (!bc || !lo || !hi || !cons || !J || !x || !dcons || !dJ) return ESMM_ERR_ARG;
+    if (nx < 4 || ny < 4 || (long long)(nx + 2 * GH) * (ny + 2 * GH) > ESMM_STATIC_MAX_PADDED_NODES)
+        return ESMM_ERR_ARG;
+    for (int k = 0; k < 2; ++k)
+        if ((bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW) || !(hi[k] > lo[k])) return ESMM_ERR_ARG;
+    if (!(gamma > 1.0 && gamma <= 2.0) || p < 1 || p > PMAX || !(w == 0 || w == 3 || w == 5)) return ESMM_ERR_ARG;
+    double *scratch = nullptr;
+    if (static_scratch(&scratch) != cudaSuccess) return ESMM_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    Geom G;
+    G.nx = nx;
+    G.ny = ny;
+    G.px = nx + 2 * GH;
+    G.py = ny + 2 * GH;
+    G.P = (long long)G.px * G.py;
+    G.N = (long long)nx * ny;
+    G.bc0 = bc[0];
+    G.bc1 = bc[1];
+    G.per0 = hi[0] - lo[0];
+    G.per1 = hi[1] - lo[1];
+    MetricCoef mc;
+    mc.p = p;
+    mc.a[0] = p == 1 ? 1.0 : (p == 2 ? 4.0 / 3.0 : 3.0 / 2.0);
+    mc.a[1] = p == 1 ? 0.0 : (p == 2 ? -1.0 / 6.0 : -3.0 / 10.0);
+    mc.a[2] = p == 3 ? 1.0 / 30.0 : 0.0;
+    Phys ph;
+    ph.gamma = gamma;
+    ph.eps = 1e-6;
+    ph.ln_thr = 1.0e-4;
+    ph.sign_tol = 1.0e-10;
+    for (int n = 0; n < PMAX; ++n) ph.alpha[n] = mc.a[n];
+    ph.p = p;
+    ph.w = w;
+    // carve the scratch: node arrays, pair fluxes, interface fluxes, status
+    double *q = scratch;
+    double *pairs = q + (long long)NQ * G.P;
+    double *iflux = pairs + (long long)2 * PMAX * 4 * G.P;
+    int *status = (int *)(scratch + STATIC_PER_NODE * ESMM_STATIC_MAX_PADDED_NODES);
+    if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return ESMM_ERR_CUDA;
+    k_node<<<nblk(G.P), BS, 0, st>>>(G, gamma, mc, cons, J, x, xdot, nullptr, nullptr, q, status);
+    for (int dir = 0; dir < 2; ++dir) {
+        launch_pairs_f64(G, ph, q, pairs, dir, st);
+        launch_iface_f64(G, ph, q, pairs, iflux, dir, st);
+    }
+    k_update<double><<<nblk(G.N), BS, 0, st>>>(G, iflux, dcons, dJ, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                               nullptr, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? ESMM_OK : ESMM_ERR_CUDA;
 }
 
 int esmm_profile(esmm_grid *g, int mask)

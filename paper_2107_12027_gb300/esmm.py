@@ -31,7 +31,9 @@ SYMBOLS = (
     "esmm_set_params", "esmm_get_params", "esmm_state_set", "esmm_state_set_cons", "esmm_state_get",
     "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
+    "esmm_rhs_static",
 )
+STATIC_MAX_PADDED_NODES = 68644
 KIND_NODE, KIND_PAIRS, KIND_IFACE, KIND_UPDATE, KIND_MESH, KIND_OTHER = range(6)
 KINDS = ("node", "pairs", "iface", "update", "mesh", "other")
 
@@ -71,6 +73,7 @@ def lib():
             "esmm_rk_step": [vp, d, dp], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
             "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
             "esmm_profile": [vp, i],
+            "esmm_rhs_static": [i, i, ctypes.POINTER(i), dp, dp, d, i, i, vp, vp, vp, vp, vp, vp, vp],
             "esmm_profile_read": [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
         }
         for name, args in sig.items():
@@ -85,6 +88,22 @@ def lib():
 
 def version() -> str:
     return lib().esmm_version().decode()
+
+
+def rhs_static(nx, ny, bc, lo, hi, gamma, p, w, cons, J, x, xdot, dcons, dJ, stream=None):
+    """esmm_rhs_static: the allocation-free right-hand side (device tensors only).
+
+    Enqueues on ``stream`` (a raw cudaStream_t handle, None for the legacy
+    default stream) and returns the status code."""
+    ptrs = [_ptr(a) for a in (cons, J, x, dcons, dJ)]
+    assert all(m == MEM_DEVICE for _, m in ptrs), "esmm_rhs_static takes device tensors"
+    xd = _ptr(xdot)[0] if xdot is not None else None
+    b = (ctypes.c_int * 2)(bc[0], bc[1])
+    l2 = (ctypes.c_double * 2)(lo[0], lo[1])
+    h2 = (ctypes.c_double * 2)(hi[0], hi[1])
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    return lib().esmm_rhs_static(int(nx), int(ny), b, l2, h2, float(gamma), int(p), int(w), ptrs[0][0],
+                                 ptrs[1][0], ptrs[2][0], xd, ptrs[3][0], ptrs[4][0], st)
 
 
 def _is_torch(a):
