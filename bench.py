@@ -39,10 +39,13 @@ WORKLOAD = ("2D RHD four-quadrant Riemann problem, 400x400 nodes on [-1,1]^2, ou
 # FP64 operations executed per interface by the FP64 interface kernel (p=2,
 # WENO5), from the ncu SASS counters dadd + dmul + 2 dfma of one capture
 # (profiles/iface_f64_riemann400.md); FLOP = add, mul, or half an FMA.
-FLOPS_PER_IFACE_F64 = None
+FLOPS_PER_IFACE_F64 = 1548
 # Derived FP64 peak of GB300: 152 SMs x 4 FP64 flop/clk/SM (1.25 TFLOP/s at
 # the 2070 MHz maximum SM clock).
 FP64_FLOP_PER_CLK_SM = 4
+# DRAM bytes (read + write) of one interface-kernel launch in that capture;
+# None whenever the kernel has changed since the counters were taken.
+TRAFFIC_IFACE_F64 = 23.49e6
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
@@ -306,7 +309,7 @@ def run_gpu(args):
         else:
             ach = None
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": (ach / peak) if ach else None, "traffic": None,
+                "frac": (ach / peak) if ach else None, "traffic": TRAFFIC_IFACE_F64,
                 "kernel": "k_iface<double,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
                 "share_of_step": iface_ms / total_ms,
                 "peak_note": "derived FP64 peak: 152 SMs x 4 flop/clk x 2070 MHz"}
