@@ -110,8 +110,10 @@ void oref_flux(double gamma, const double *w, int dir, double *F)
  *   f(p) = (Gamma-1)/Gamma * ((E + p)/W^2 - D/W) - p,  v = m/(E + p),
  * safeguarded by bisection on the bracket [0, (Gamma-1) E] (f(0) > 0 and
  * f((Gamma-1)E) < 0 for every admissible state, f strictly decreasing).
- * Stops when a step changes p by at most 1e-15 p.  Returns 0 on success,
- * -1 for a non-admissible state, -2 without convergence.                  */
+ * Stops when a step changes p by at most 1e-15 (E + p): f is evaluated from
+ * E + p, so p is resolved only to that level (p << E in cold gas).
+ * Returns 0 on success, -1 for a non-admissible state, -2 without
+ * convergence.                                                             */
 int oref_cons2prim(double gamma, const double *U, double *w, int *iters)
 {
     double D = U[0], mx = U[1], my = U[2], E = U[3];
@@ -131,7 +133,7 @@ int oref_cons2prim(double gamma, const double *U, double *w, int *iters)
         if (f > 0.0) lo = p; else hi = p;
         double pn = p - f / df;
         if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
-        if (fabs(pn - p) <= 1.0e-15 * pn) {
+        if (fabs(pn - p) <= 1.0e-15 * (E + pn)) {
             p = pn;
             ok = 1;
             break;

@@ -168,16 +168,57 @@ __device__ __forceinline__ double delta_mesh(const Geom &g, const MetricCoef &mc
     return d;
 }
 
-__global__ void k_node(Geom g, double gam, MetricCoef mc, const double *__restrict__ cons,
-                       const double *__restrict__ J, const double *__restrict__ x,
-                       const double *__restrict__ xdot, const double *__restrict__ pg_in,
-                       double *__restrict__ pg_out, double *__restrict__ q, int *__restrict__ status)
+// alpha_{p,n} of eq. HOCoeff as compile-time constants
+template <int P> __device__ __forceinline__ constexpr double alpha_c(int n)
+{
+    return P == 1 ? 1.0
+                  : (P == 2 ? (n == 1 ? 4.0 / 3.0 : -1.0 / 6.0)
+                            : (n == 1 ? 1.5 : (n == 2 ? -0.3 : 1.0 / 30.0)));
+}
+
+// The four differences delta_xi[x], delta_xi[y], delta_eta[x], delta_eta[y]
+// at node (I, J) of the padded grid.  Nodes whose stencil stays inside the
+// mesh read it directly; the others go through the boundary mapping.
+template <int P>
+__device__ __forceinline__ void mesh_deltas(const Geom &g, const double *__restrict__ x, int I, int J,
+                                            double &dxi_x, double &dxi_y, double &deta_x, double &deta_y)
+{
+    dxi_x = dxi_y = deta_x = deta_y = 0.0;
+    if (I - P >= 0 && I + P < g.nx && J - P >= 0 && J + P < g.ny) {
+        const double *X = x, *Y = x + g.N;
+        const long long c = (long long)J * g.nx + I;
+#pragma unroll
+        for (int n = 1; n <= P; ++n) {
+            const double a = 0.5 * alpha_c<P>(n);
+            const long long s = (long long)n * g.nx;
+            dxi_x += a * (X[c + n] - X[c - n]);
+            dxi_y += a * (Y[c + n] - Y[c - n]);
+            deta_x += a * (X[c + s] - X[c - s]);
+            deta_y += a * (Y[c + s] - Y[c - s]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        const double a = 0.5 * alpha_c<P>(n);
+        dxi_x += a * (mesh_at(g, x, I + n, J, 0, 1) - mesh_at(g, x, I - n, J, 0, 1));
+        dxi_y += a * (mesh_at(g, x, I + n, J, 1, 1) - mesh_at(g, x, I - n, J, 1, 1));
+        deta_x += a * (mesh_at(g, x, I, J + n, 0, 1) - mesh_at(g, x, I, J - n, 0, 1));
+        deta_y += a * (mesh_at(g, x, I, J + n, 1, 1) - mesh_at(g, x, I, J - n, 1, 1));
+    }
+}
+
+template <int P>
+__global__ void k_node(Geom g, double gam, const double *__restrict__ cons, const double *__restrict__ J,
+                       const double *__restrict__ x, const double *__restrict__ xdot,
+                       const double *__restrict__ pg_in, double *__restrict__ pg_out, double *__restrict__ q,
+                       int *__restrict__ status)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.P) return;
     int I = (int)(t % g.px) - GH, Jn = (int)(t / g.px) - GH;
     long long src = data_src(g, I, Jn);
-    double iJ = 1.0 / J[src];
+    double iJ = __drcp_rn(J[src]);
     double D = cons[src] * iJ, mx = cons[g.N + src] * iJ, my = cons[2 * g.N + src] * iJ,
            E = cons[3 * g.N + src] * iJ;
     double rho, vx, vy, p;
@@ -187,8 +228,8 @@ __global__ void k_node(Geom g, double gam, MetricCoef mc, const double *__restri
         if (st) atomicAdd(status, 1);
         if (pg_out) pg_out[src] = p;
     }
-    double W = 1.0 / sqrt(1.0 - (vx * vx + vy * vy));
-    double beta = rho / p;
+    double W = rsqrt(1.0 - (vx * vx + vy * vy));
+    double beta = rho * __drcp_rn(p);
     q[Q_RHO * g.P + t] = rho;
     q[Q_P * g.P + t] = p;
     q[Q_BETA * g.P + t] = beta;
@@ -198,8 +239,8 @@ __global__ void k_node(Geom g, double gam, MetricCoef mc, const double *__restri
     q[Q_LNR * g.P + t] = log(rho);
     q[Q_LNB * g.P + t] = log(beta);
     // App. B with index-space computational coordinates
-    double dxi_x = delta_mesh(g, mc, x, I, Jn, 0, 0), dxi_y = delta_mesh(g, mc, x, I, Jn, 1, 0);
-    double deta_x = delta_mesh(g, mc, x, I, Jn, 0, 1), deta_y = delta_mesh(g, mc, x, I, Jn, 1, 1);
+    double dxi_x, dxi_y, deta_x, deta_y;
+    mesh_deltas<P>(g, x, I, Jn, dxi_x, dxi_y, deta_x, deta_y);
     double M00 = deta_y, M01 = -deta_x, M10 = -dxi_y, M11 = dxi_x;
     q[Q_M00 * g.P + t] = M00;
     q[Q_M01 * g.P + t] = M01;
@@ -209,6 +250,14 @@ __global__ void k_node(Geom g, double gam, MetricCoef mc, const double *__restri
     if (xdot) { xd = mesh_at(g, xdot, I, Jn, 0, 0); yd = mesh_at(g, xdot, I, Jn, 1, 0); }
     q[Q_MT0 * g.P + t] = -(xd * M00 + yd * M01);
     q[Q_MT1 * g.P + t] = -(xd * M10 + yd * M11);
+}
+
+void launch_node(int p, const Geom &G, double gam, const double *cons, const double *J, const double *x, const double *xdot, const double *pg_in, double *pg_out, double *q, int *status, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((G.P + 255) / 256);
+    if (p == 1) k_node<1><<<nb, 256, 0, st>>>(G, gam, cons, J, x, xdot, pg_in, pg_out, q, status);
+    else if (p == 2) k_node<2><<<nb, 256, 0, st>>>(G, gam, cons, J, x, xdot, pg_in, pg_out, q, status);
+    else k_node<3><<<nb, 256, 0, st>>>(G, gam, cons, J, x, xdot, pg_in, pg_out, q, status);
 }
 
 // temporal metrics only (the spatial ones and the state are unchanged)
@@ -531,8 +580,7 @@ int rhs_core(esmm_grid *g, const double *cons, const double *J, const double *x,
         double *pout = warm ? g->pg[1 - g->pgi] : nullptr;
         {
             Prof pr_(g, ESMM_KIND_NODE);
-            k_node<<<nblk(G.P), BS, 0, g->st>>>(G, g->gamma, metric_coef(g), cons, J, x, xdot, pin, pout, g->q,
-                                                g->status);
+            launch_node(g->p, G, g->gamma, cons, J, x, xdot, pin, pout, g->q, g->status, g->st);
         }
         if (warm) g->pgi = 1 - g->pgi;
     }
@@ -654,8 +702,7 @@ int rk_step_async(esmm_grid *g, double dt)
     // state's node data with a static mesh: CFL step and monitor (Sec. 5)
     {
         Prof pr_(g, ESMM_KIND_NODE);
-        k_node<<<nblk(G.P), BS, 0, g->st>>>(G, g->gamma, metric_coef(g), g->cons, g->J, g->x, nullptr,
-                                            g->pg[g->pgi], g->pg[1 - g->pgi], g->q, g->status);
+        launch_node(g->p, G, g->gamma, g->cons, g->J, g->x, nullptr, g->pg[g->pgi], g->pg[1 - g->pgi], g->q, g->status, g->st);
     }
     g->pgi = 1 - g->pgi;
     {
@@ -1062,8 +1109,7 @@ int esmm_cfl_dt(esmm_grid *g, double *dt)
     const Geom &G = g->g;
     {
         Prof pr_(g, ESMM_KIND_NODE);
-        k_node<<<nblk(G.P), BS, 0, g->st>>>(G, g->gamma, metric_coef(g), g->cons, g->J, g->x, nullptr, nullptr, nullptr,
-                                            g->q, g->status);
+        launch_node(g->p, G, g->gamma, g->cons, g->J, g->x, nullptr, nullptr, nullptr, g->q, g->status, g->st);
     }
     {
         Prof pr_(g, ESMM_KIND_OTHER);
@@ -1084,8 +1130,7 @@ int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, 
     const Geom &G = g->g;
     {
         Prof pr_(g, ESMM_KIND_NODE);
-        k_node<<<nblk(G.P), BS, 0, g->st>>>(G, g->gamma, metric_coef(g), g->cons, g->J, g->x, nullptr, nullptr, nullptr,
-                                            g->q, g->status);
+        launch_node(g->p, G, g->gamma, g->cons, g->J, g->x, nullptr, nullptr, nullptr, g->q, g->status, g->st);
     }
     {
         Prof pr_(g, ESMM_KIND_OTHER);
@@ -1133,8 +1178,7 @@ int esmm_totals(esmm_grid *g, double out[3])
     const Geom &G = g->g;
     {
         Prof pr_(g, ESMM_KIND_NODE);
-        k_node<<<nblk(G.P), BS, 0, g->st>>>(G, g->gamma, metric_coef(g), g->cons, g->J, g->x, nullptr, nullptr, nullptr,
-                                            g->q, g->status);
+        launch_node(g->p, G, g->gamma, g->cons, g->J, g->x, nullptr, nullptr, nullptr, g->q, g->status, g->st);
     }
     int nb = (int)nblk(G.N);
     {
@@ -1195,7 +1239,7 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     double *iflux = pairs + (long long)2 * PMAX * 4 * G.P;
     int *status = (int *)(scratch + STATIC_PER_NODE * ESMM_STATIC_MAX_PADDED_NODES);
     if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return ESMM_ERR_CUDA;
-    k_node<<<nblk(G.P), BS, 0, st>>>(G, gamma, mc, cons, J, x, xdot, nullptr, nullptr, q, status);
+    launch_node(p, G, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, st);
     for (int dir = 0; dir < 2; ++dir) {
         launch_pairs_f64(G, ph, q, pairs, dir, st);
         launch_iface_f64(G, ph, q, pairs, iflux, dir, st);

@@ -88,8 +88,9 @@ __device__ __forceinline__ double mesh_at(const Geom &g, const double *a, int i,
 // Conservative -> primitive recovery (FP64 in every form).  Newton on p for
 //   f(p) = (G-1)/G ((E+p)(1-v^2) - D sqrt(1-v^2)) - p,  v = |m|/(E+p),
 // safeguarded by bisection on [0, (G-1)E], stopping when a step moves p by at
-// most 1e-15 p; p0 is a warm start (ignored when outside the bracket).
-// Returns 0, 1 for a non-admissible state, 2 when the iteration cap is hit.
+// most 1e-15 (E + p), the resolution of E + p from which f is evaluated;
+// p0 is a warm start (ignored when outside the bracket).  Returns 0, 1 for a
+// non-admissible state, 2 when the iteration cap is hit.
 __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double my, double E,
                                          double p0, double &rho, double &vx, double &vy, double &p)
 {
@@ -103,7 +104,7 @@ __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double
     int ok = 0;
     for (int it = 0; it < 200; ++it) {
         double Ep = E + pc;
-        double r = 1.0 / Ep;
+        double r = __drcp_rn(Ep);
         double iW2 = (Ep - S) * (Ep + S) * r * r;   // 1 - v^2
         double rs = rsqrt(iW2);
         double iW = iW2 * rs;                        // sqrt(1 - v^2)
@@ -111,15 +112,16 @@ __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double
         double f = gg * (Ep * iW2 - D * iW) - pc;
         double df = gg * (1.0 + v2 - D * v2 * r * rs) - 1.0;
         if (f > 0.0) lo = pc; else hi = pc;
-        double pn = pc - f / df;
+        double pn = pc - f * __drcp_rn(df);
         if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
-        if (fabs(pn - pc) <= 1.0e-15 * pn) { pc = pn; ok = 1; break; }
+        if (fabs(pn - pc) <= 1.0e-15 * (E + pn)) { pc = pn; ok = 1; break; }
         pc = pn;
     }
     double Ep = E + pc;
-    double r = 1.0 / Ep;
+    double r = __drcp_rn(Ep);
     double iW2 = (Ep - S) * (Ep + S) * r * r;
-    rho = D * sqrt(iW2);
+    double rs = rsqrt(iW2);
+    rho = D * (iW2 * rs);
     vx = mx * r;
     vy = my * r;
     p = pc;
@@ -133,6 +135,13 @@ template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf
 template <typename R> __device__ __forceinline__ R sq_rt(R x);
 template <> __device__ __forceinline__ double sq_rt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float sq_rt<float>(float x) { return sqrtf(x); }
+// reciprocal (IEEE round-to-nearest) and a square root of a positive value
+// through the reciprocal square root: on GB300 both are cheaper than the
+// FP64 quotient and square root
+template <typename R> __device__ __forceinline__ R rcp(R x);
+template <> __device__ __forceinline__ double rcp<double>(double x) { return __drcp_rn(x); }
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <typename R> __device__ __forceinline__ R sqrt_pos(R x) { return x * rsq<R>(x); }
 template <typename R> __device__ __forceinline__ R fab(R x);
 template <> __device__ __forceinline__ double fab<double>(double x) { return fabs(x); }
 template <> __device__ __forceinline__ float fab<float>(float x) { return fabsf(x); }
@@ -152,8 +161,8 @@ __device__ __forceinline__ void logmean(double a, double b, double la, double lb
         inv_mean = (R)(2.0 * F / s);
     } else {
         R dn = (R)d, dl = (R)(lb - la);
-        mean = dn / dl;
-        inv_mean = dl / dn;
+        mean = dn * rcp<R>(dl);
+        inv_mean = dl * rcp<R>(dn);
     }
 }
 
@@ -192,8 +201,8 @@ __device__ __forceinline__ void ec_pair(const NodeV<R> &l, const NodeV<R> &r, R 
     R usq = uxm * uxm + uym * uym;
     R Lam = Wm * Wm - usq;
     R alpha0 = (R)1 + gm1inv * ibln;
-    R pm = rm / bm;
-    R rinv = (R)1 / (Lam * Wm);
+    R pm = rm * rcp<R>(bm);
+    R rinv = rcp<R>(Lam * Wm);
     R iLam = rinv * Wm;
     R iW = rinv * Lam;
     R UD = rln * Wm;
@@ -225,7 +234,7 @@ __device__ __forceinline__ R weno5(R s0, R s1, R s2, R s3, R s4, R eps)
     R e2 = eps + c13_12 * t2 * t2 + c1_4 * r2 * r2;
     e0 *= e0; e1 *= e1; e2 *= e2;
     R a0 = (R)0.1 * e1 * e2, a1 = (R)0.6 * e0 * e2, a2 = (R)0.3 * e0 * e1;
-    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    return (a0 * q0 + a1 * q1 + a2 * q2) * rcp<R>(a0 + a1 + a2);
 }
 
 template <typename R>
@@ -237,7 +246,7 @@ __device__ __forceinline__ R weno3(R s0, R s1, R s2, R eps)
     R e1 = eps + (s2 - s1) * (s2 - s1);
     e0 *= e0; e1 *= e1;
     R a0 = (R)(1.0 / 3.0) * e1, a1 = (R)(2.0 / 3.0) * e0;
-    return (a0 * q0 + a1 * q1) / (a0 + a1);
+    return (a0 * q0 + a1 * q1) * rcp<R>(a0 + a1);
 }
 
 __device__ __forceinline__ int sgn_d(double a) { return (a > 0.0) - (a < 0.0); }
@@ -253,17 +262,18 @@ __device__ __forceinline__ void eigen_rhd(R gam, R rho, R vn, R vt, R p, R W,
                                           R dU[4][4], R s[4], R &lam_m, R &lam_p)
 {
     R one = (R)1;
-    R gg = gam / (gam - one);
+    R gm1i = rcp<R>(gam - one);
+    R gg = gam * gm1i;
     R W2 = W * W;
-    R iW2 = one / W2;                      // 1 - v^2
+    R iW2 = rcp<R>(W2);                    // 1 - v^2
     R v2 = one - iW2;
-    R irp = one / (rho * p);
+    R irp = rcp<R>(rho * p);
     R ip = rho * irp, ir = p * irp;
     R rh = rho + gg * p;                   // rho h
-    R c2 = gam * p / rh;
-    R c = sq_rt<R>(c2);
-    R disc = sq_rt<R>(iW2 * (one - v2 * c2 - vn * vn * (one - c2)));
-    R den = one / (one - v2 * c2);
+    R c2 = gam * p * rcp<R>(rh);
+    R c = sqrt_pos<R>(c2);
+    R disc = sqrt_pos<R>(iW2 * (one - v2 * c2 - vn * vn * (one - c2)));
+    R den = rcp<R>(one - v2 * c2);
     lam_m = (vn * (one - c2) - c * disc) * den;
     lam_p = (vn * (one - c2) + c * disc) * den;
     R Q = rh * W2;
@@ -284,7 +294,7 @@ __device__ __forceinline__ void eigen_rhd(R gam, R rho, R vn, R vt, R p, R W,
     for (int side = 0; side < 2; ++side) {
         int m = side == 0 ? 0 : 3;
         R l = side == 0 ? lam_m : lam_p;
-        R a = one / ((l - vn) * Q);          // 1 / ((lam - v_n) Q)
+        R a = rcp<R>((l - vn) * Q);          // 1 / ((lam - v_n) Q)
         R dvn = (one - vn * l) * a;
         R dvt = -l * vt * a;
         R vdv = vn * dvn + vt * dvt;
@@ -298,7 +308,7 @@ __device__ __forceinline__ void eigen_rhd(R gam, R rho, R vn, R vt, R p, R W,
         dU[3][m] = W2 * h1 - one + rh * (R)2 * W4 * vdv;
         // dV/dw dw
         R dbeta = drho * ip - beta * ip;
-        R dV0 = drho * ir + (drho * ir - ip) / (gam - one) + dbeta;
+        R dV0 = drho * ir + (drho * ir - ip) * gm1i + dbeta;
         R dV1 = dbeta * un + beta * (W * dvn + vn * dW);
         R dV2 = dbeta * ut + beta * (W * dvt + vt * dW);
         R dV3 = -(dbeta * W + beta * dW);

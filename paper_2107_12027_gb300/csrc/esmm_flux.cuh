@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__
         R nvx = (R)(0.5 * (Mx[c0] + Mx[c1]));
         R nvy = (R)(0.5 * (My[c0] + My[c1]));
         R jt = (R)(0.5 * (Mt[c0] + Mt[c1]));
-        R Lk = sq_rt<R>(nvx * nvx + nvy * nvy);
-        R iLk = one / Lk;
+        R iLk = rsq<R>(nvx * nvx + nvy * nvy);
+        R Lk = (nvx * nvx + nvy * nvy) * iLk;
         R nx = nvx * iLk, ny = nvy * iLk;
         // interface state from the two-point flux averages:
         // rho = {{rho}}^ln, u = {{u}}, p = {{rho}}/{{beta}}
@@ -122,10 +122,10 @@ __global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__
                    ph.ln_thr, rho, irho);
         R ux = half * ((R)q[Q_UX * g.P + c0] + (R)q[Q_UX * g.P + c1]);
         R uy = half * ((R)q[Q_UY * g.P + c0] + (R)q[Q_UY * g.P + c1]);
-        R p = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) /
-              ((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
-        R W = sq_rt<R>(one + ux * ux + uy * uy);
-        R iW = one / W;
+        R p = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) *
+              rcp<R>((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
+        R iW = rsq<R>(one + ux * ux + uy * uy);
+        R W = (one + ux * ux + uy * uy) * iW;
         R vx = ux * iW, vy = uy * iW;
         R vn = nx * vx + ny * vy, vt = -ny * vx + nx * vy;
         R dU[4][4], s[4], lm, lp;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__
 
         constexpr int NS = WW + 1;              // stencil nodes
         constexpr int OFF = (WW - 1) / 2;       // nodes left of c0
-        const R c1g = gam / (gam - one), ig = one / (gam - one);
+        const R ig = rcp<R>(gam - one), c1g = gam * ig;
         R Vt[NS][4];
         R aT[4] = {(R)0, (R)0, (R)0, (R)0};     // |T V| summed over the two interface nodes
 #pragma unroll
