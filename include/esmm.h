@@ -140,6 +140,37 @@ int esmm_rk_step(esmm_grid *g, double dt, double *dt_used);
 /* nsteps asynchronous esmm_rk_step calls (dt as there). */
 int esmm_advance(esmm_grid *g, int nsteps, double dt);
 
+/* Batches: nprob independent problems of (possibly) different sizes in one
+ * handle (north star form 2).  n, lo, hi and bc are [nprob][2]; each problem
+ * obeys the rules of esmm_grid_create.  All problems share the EOS, order and
+ * parameters; every kernel of a step covers the whole batch in one launch
+ * (a block -> (problem, tile) map, blocks never span two problems), and
+ * esmm_advance replays one CUDA graph per step.  Each problem has its own CFL
+ * time step, time, monitor maximum and mesh limiter.  stream NULL: the batch
+ * creates its own non-blocking stream.  Batch handles accept esmm_set_*,
+ * esmm_rk_step (dt_used: problem 0's step), esmm_advance, esmm_tune,
+ * esmm_profile*, esmm_last_error, esmm_grid_destroy and the esmm_batch_*
+ * calls; the single-problem state, rhs, CFL, mesh and totals calls return
+ * ESMM_ERR_ARG for them. */
+int esmm_batch_create(esmm_grid **g, int nprob, const int *n, const double *lo, const double *hi, const int *bc,
+                      int phys, void *stream);
+int esmm_batch_size(const esmm_grid *g, int *nprob);
+/* state of problem b (arrays of that problem's size, as esmm_state_set) */
+int esmm_batch_state_set(esmm_grid *g, int b, const double *prim, const double *x, int mem);
+int esmm_batch_state_get(esmm_grid *g, int b, int what, double *out, int mem);
+/* t[nprob]: the time of every problem (synchronises) */
+int esmm_batch_times(esmm_grid *g, double *t);
+/* out[nprob][3]: the FP64 totals of esmm_totals for every problem */
+int esmm_batch_totals(esmm_grid *g, double *out);
+
+/* Launch autotuner: for each kernel kind (node pass, pair fluxes, interface
+ * fluxes, per-node kernels) time the candidate block sizes -- and, for
+ * batches, the tile orders natural / largest problem first -- on the current
+ * state, and keep the fastest.  Requires a state.  When block_sizes is given
+ * it receives the 7 chosen launch domains' block sizes (negative: largest
+ * first). */
+int esmm_tune(esmm_grid *g, int *block_sizes);
+
 /* FP64 totals of the grid's state: out[0] = sum J eta (total entropy),
  * out[1] = sum J D (mass), out[2] = sum J (volume).  Synchronises. */
 int esmm_totals(esmm_grid *g, double out[3]);

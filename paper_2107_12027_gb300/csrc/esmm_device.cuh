@@ -27,6 +27,36 @@ struct Geom {
     double per0, per1;
 };
 
+// One problem of a batch: its geometry and the offsets of its slices in the
+// concatenated arrays (on: node arrays, in units of nodes; op: padded-node
+// arrays, in units of padded nodes).
+struct ProbDesc {
+    Geom g;
+    long long on, op;
+};
+
+// Problem addressing of a launch: a single problem passed by value (tiles ==
+// nullptr), or a device table of problems with a map from block to
+// (problem, block within the problem), so that no block spans two problems.
+struct ProbArg {
+    const ProbDesc *pd;
+    const int2 *tiles;
+    ProbDesc one;
+};
+
+__device__ __forceinline__ int locate(const ProbArg &pa, ProbDesc &D, long long &local_block)
+{
+    if (pa.tiles) {
+        int2 t = pa.tiles[blockIdx.x];
+        D = pa.pd[t.x];
+        local_block = t.y;
+        return t.x;
+    }
+    D = pa.one;
+    local_block = blockIdx.x;
+    return 0;
+}
+
 struct Phys {
     double gamma;
     double eps;       // WENO epsilon

@@ -32,12 +32,18 @@ __device__ __forceinline__ NodeV<R> load_node(const Geom &g, const double *__res
 
 // anchors A in [-P, n_dir - 1] along the sweep, every line of the other index
 template <typename R, int P>
-__global__ void __launch_bounds__(128) k_pairs(Geom g, Phys ph, const double *__restrict__ q,
+__global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double *__restrict__ q,
                                                R *__restrict__ pairs, int dir)
 {
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    q += (long long)NQ * D.op;
+    pairs += (long long)2 * PMAX * 4 * D.op;
     const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
     const long long count = (long long)(nd + P) * no;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = lb * blockDim.x + threadIdx.x;
     if (idx >= count) return;
     int i, j;
     if (dir == 0) { j = (int)(idx / (nd + P)); i = (int)(idx % (nd + P)) - P; }
@@ -67,12 +73,19 @@ __global__ void __launch_bounds__(128) k_pairs(Geom g, Phys ph, const double *__
 
 // interfaces between left node L in [-1, n_dir - 1] and L + 1
 template <typename R, int P, int WW>
-__global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__restrict__ q,
+__global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double *__restrict__ q,
                                                const R *__restrict__ pairs, R *__restrict__ iflux, int dir)
 {
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    q += (long long)NQ * D.op;
+    pairs += (long long)2 * PMAX * 4 * D.op;
+    iflux += (long long)2 * 5 * D.op;
     const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
     const long long count = (long long)(nd + 1) * no;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = lb * blockDim.x + threadIdx.x;
     if (idx >= count) return;
     int i, j;
     if (dir == 0) { j = (int)(idx / (nd + 1)); i = (int)(idx % (nd + 1)) - 1; }
@@ -192,56 +205,50 @@ __global__ void __launch_bounds__(128) k_iface(Geom g, Phys ph, const double *__
 }
 
 template <typename R, int P>
-static void launch_pairs_p(const Geom &g, const Phys &ph, const double *q, R *pairs, int dir, cudaStream_t st)
+static void launch_pairs_p(const LaunchDom &L, const Phys &ph, const double *q, R *pairs, int dir, cudaStream_t st)
 {
-    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
-    long long count = (long long)(nd + P) * no;
-    int bs = 128;
-    k_pairs<R, P><<<(unsigned)((count + bs - 1) / bs), bs, 0, st>>>(g, ph, q, pairs, dir);
+    k_pairs<R, P><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, pairs, dir);
 }
 
 template <typename R, int P, int WW>
-static void launch_iface_pw(const Geom &g, const Phys &ph, const double *q, const R *pairs, R *iflux,
+static void launch_iface_pw(const LaunchDom &L, const Phys &ph, const double *q, const R *pairs, R *iflux,
                             int dir, cudaStream_t st)
 {
-    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
-    long long count = (long long)(nd + 1) * no;
-    int bs = 128;
-    k_iface<R, P, WW><<<(unsigned)((count + bs - 1) / bs), bs, 0, st>>>(g, ph, q, pairs, iflux, dir);
+    k_iface<R, P, WW><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, pairs, iflux, dir);
 }
 
 template <typename R>
-void launch_pairs_t(const Geom &g, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st)
+void launch_pairs_t(const LaunchDom &L, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st)
 {
     R *pr = (R *)pairs;
     switch (ph.p) {
-    case 1: launch_pairs_p<R, 1>(g, ph, q, pr, dir, st); break;
-    case 2: launch_pairs_p<R, 2>(g, ph, q, pr, dir, st); break;
-    default: launch_pairs_p<R, 3>(g, ph, q, pr, dir, st); break;
+    case 1: launch_pairs_p<R, 1>(L, ph, q, pr, dir, st); break;
+    case 2: launch_pairs_p<R, 2>(L, ph, q, pr, dir, st); break;
+    default: launch_pairs_p<R, 3>(L, ph, q, pr, dir, st); break;
     }
 }
 
 template <typename R, int P>
-static void launch_iface_p(const Geom &g, const Phys &ph, const double *q, const R *pr, R *fl, int dir,
+static void launch_iface_p(const LaunchDom &L, const Phys &ph, const double *q, const R *pr, R *fl, int dir,
                            cudaStream_t st)
 {
     switch (ph.w) {
-    case 0: launch_iface_pw<R, P, 0>(g, ph, q, pr, fl, dir, st); break;
-    case 3: launch_iface_pw<R, P, 3>(g, ph, q, pr, fl, dir, st); break;
-    default: launch_iface_pw<R, P, 5>(g, ph, q, pr, fl, dir, st); break;
+    case 0: launch_iface_pw<R, P, 0>(L, ph, q, pr, fl, dir, st); break;
+    case 3: launch_iface_pw<R, P, 3>(L, ph, q, pr, fl, dir, st); break;
+    default: launch_iface_pw<R, P, 5>(L, ph, q, pr, fl, dir, st); break;
     }
 }
 
 template <typename R>
-void launch_iface_t(const Geom &g, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
+void launch_iface_t(const LaunchDom &L, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
                     cudaStream_t st)
 {
     const R *pr = (const R *)pairs;
     R *fl = (R *)iflux;
     switch (ph.p) {
-    case 1: launch_iface_p<R, 1>(g, ph, q, pr, fl, dir, st); break;
-    case 2: launch_iface_p<R, 2>(g, ph, q, pr, fl, dir, st); break;
-    default: launch_iface_p<R, 3>(g, ph, q, pr, fl, dir, st); break;
+    case 1: launch_iface_p<R, 1>(L, ph, q, pr, fl, dir, st); break;
+    case 2: launch_iface_p<R, 2>(L, ph, q, pr, fl, dir, st); break;
+    default: launch_iface_p<R, 3>(L, ph, q, pr, fl, dir, st); break;
     }
 }
 

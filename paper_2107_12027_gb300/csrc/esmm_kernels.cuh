@@ -1,0 +1,536 @@
+// esmm_kernels.cuh -- the per-node, update, CFL, mesh-redistribution, state
+// and totals kernels (the flux kernels are in esmm_flux.cuh).  Every kernel
+// takes a ProbArg: one problem by value, or a batch of problems addressed
+// through a block -> (problem, tile) map; pointers are the bases of the
+// concatenated arrays and each kernel offsets them to its problem's slice.
+//
+// Scheme: Duan & Tang, arXiv 2107.12027 (2D RHD: B = 0).
+#pragma once
+
+#include "esmm_device.cuh"
+
+namespace esmm {
+
+// ---------------------------------------------------------------------------
+// block reductions (warp shuffles, then one value per warp in shared memory)
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// OP: 0 max, 1 min, 2 sum; the result is valid in thread 0.  Every thread of
+// the block must call it.
+template <int OP>
+__device__ double block_reduce(double v)
+{
+    __shared__ double sh[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = OP == 0 ? warp_max(v) : (OP == 1 ? warp_min(v) : warp_sum(v));
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    if (wid == 0) {
+        double init = OP == 0 ? 0.0 : (OP == 1 ? 1.0e300 : 0.0);
+        v = lane < nw ? sh[lane] : init;
+        v = OP == 0 ? warp_max(v) : (OP == 1 ? warp_min(v) : warp_sum(v));
+    }
+    __syncthreads();
+    return v;
+}
+
+// Non-negative doubles order like their bit patterns, so the max/min of such
+// values over many blocks is an integer atomic on the bits.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *a, double v)
+{
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_nonneg(unsigned long long *a, double v)
+{
+    atomicMin(a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// per-problem reduction slots: [0] max |grad sigma|, [1] Delta tau (min),
+// [2], [3] max spectral radius per direction
+constexpr int NRED = 4;
+
+// ---------------------------------------------------------------------------
+// alpha_{p,n} of eq. HOCoeff as compile-time constants
+template <int P> __device__ __forceinline__ constexpr double alpha_c(int n)
+{
+    return P == 1 ? 1.0
+                  : (P == 2 ? (n == 1 ? 4.0 / 3.0 : -1.0 / 6.0)
+                            : (n == 1 ? 1.5 : (n == 2 ? -0.3 : 1.0 / 30.0)));
+}
+
+// The four differences delta_xi[x], delta_xi[y], delta_eta[x], delta_eta[y]
+// (eq. SCLCoeff / App. B) at node (I, J) of the padded grid.  Nodes whose
+// stencil stays inside the mesh read it directly; the others go through the
+// boundary mapping.
+template <int P>
+__device__ __forceinline__ void mesh_deltas(const Geom &g, const double *__restrict__ x, int I, int J,
+                                            double &dxi_x, double &dxi_y, double &deta_x, double &deta_y)
+{
+    dxi_x = dxi_y = deta_x = deta_y = 0.0;
+    if (I - P >= 0 && I + P < g.nx && J - P >= 0 && J + P < g.ny) {
+        const double *X = x, *Y = x + g.N;
+        const long long c = (long long)J * g.nx + I;
+#pragma unroll
+        for (int n = 1; n <= P; ++n) {
+            const double a = 0.5 * alpha_c<P>(n);
+            const long long s = (long long)n * g.nx;
+            dxi_x += a * (X[c + n] - X[c - n]);
+            dxi_y += a * (Y[c + n] - Y[c - n]);
+            deta_x += a * (X[c + s] - X[c - s]);
+            deta_y += a * (Y[c + s] - Y[c - s]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        const double a = 0.5 * alpha_c<P>(n);
+        dxi_x += a * (mesh_at(g, x, I + n, J, 0, 1) - mesh_at(g, x, I - n, J, 0, 1));
+        dxi_y += a * (mesh_at(g, x, I + n, J, 1, 1) - mesh_at(g, x, I - n, J, 1, 1));
+        deta_x += a * (mesh_at(g, x, I, J + n, 0, 1) - mesh_at(g, x, I, J - n, 0, 1));
+        deta_y += a * (mesh_at(g, x, I, J + n, 1, 1) - mesh_at(g, x, I, J - n, 1, 1));
+    }
+}
+
+// Per padded node: primitive recovery (FP64 Newton, warm-started from pg_in
+// when given), W, u = W v, beta = rho/p, ln rho, ln beta, the CMM metrics and
+// the temporal metrics J xi_k,t = -xdot . (J xi_k,x) (eq. VCLCoeff).  Ghost
+// nodes take the data of their boundary source node and metrics of the
+// boundary-mapped mesh, so the flux kernels need no boundary logic.
+template <int P>
+__global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
+                       const double *__restrict__ x, const double *__restrict__ xdot,
+                       const double *__restrict__ pg_in, double *__restrict__ pg_out, double *__restrict__ q,
+                       int *__restrict__ status)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long t = lb * blockDim.x + threadIdx.x;
+    if (t >= g.P) return;
+    cons += 4 * D.on;
+    J += D.on;
+    x += 2 * D.on;
+    if (xdot) xdot += 2 * D.on;
+    if (pg_in) pg_in += D.on;
+    if (pg_out) pg_out += D.on;
+    q += (long long)NQ * D.op;
+    int I = (int)(t % g.px) - GH, Jn = (int)(t / g.px) - GH;
+    long long src = data_src(g, I, Jn);
+    double iJ = __drcp_rn(J[src]);
+    double Dd = cons[src] * iJ, mx = cons[g.N + src] * iJ, my = cons[2 * g.N + src] * iJ,
+           E = cons[3 * g.N + src] * iJ;
+    double rho, vx, vy, p;
+    int st = cons2prim(gam, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p);
+    bool interior = I >= 0 && I < g.nx && Jn >= 0 && Jn < g.ny;
+    if (interior) {
+        if (st) atomicAdd(status, 1);
+        if (pg_out) pg_out[src] = p;
+    }
+    double W = rsqrt(1.0 - (vx * vx + vy * vy));
+    double beta = rho * __drcp_rn(p);
+    q[Q_RHO * g.P + t] = rho;
+    q[Q_P * g.P + t] = p;
+    q[Q_BETA * g.P + t] = beta;
+    q[Q_UX * g.P + t] = W * vx;
+    q[Q_UY * g.P + t] = W * vy;
+    q[Q_W * g.P + t] = W;
+    q[Q_LNR * g.P + t] = log(rho);
+    q[Q_LNB * g.P + t] = log(beta);
+    double dxi_x, dxi_y, deta_x, deta_y;
+    mesh_deltas<P>(g, x, I, Jn, dxi_x, dxi_y, deta_x, deta_y);
+    double M00 = deta_y, M01 = -deta_x, M10 = -dxi_y, M11 = dxi_x;
+    q[Q_M00 * g.P + t] = M00;
+    q[Q_M01 * g.P + t] = M01;
+    q[Q_M10 * g.P + t] = M10;
+    q[Q_M11 * g.P + t] = M11;
+    double xd = 0.0, yd = 0.0;
+    if (xdot) { xd = mesh_at(g, xdot, I, Jn, 0, 0); yd = mesh_at(g, xdot, I, Jn, 1, 0); }
+    q[Q_MT0 * g.P + t] = -(xd * M00 + yd * M01);
+    q[Q_MT1 * g.P + t] = -(xd * M10 + yd * M11);
+}
+
+// temporal metrics only (the spatial ones and the state are unchanged)
+__global__ void k_tmetric(ProbArg pa, const double *__restrict__ xdot, double *__restrict__ q)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long t = lb * blockDim.x + threadIdx.x;
+    if (t >= g.P) return;
+    xdot += 2 * D.on;
+    q += (long long)NQ * D.op;
+    int I = (int)(t % g.px) - GH, Jn = (int)(t / g.px) - GH;
+    double xd = mesh_at(g, xdot, I, Jn, 0, 0), yd = mesh_at(g, xdot, I, Jn, 1, 0);
+    q[Q_MT0 * g.P + t] = -(xd * q[Q_M00 * g.P + t] + yd * q[Q_M01 * g.P + t]);
+    q[Q_MT1 * g.P + t] = -(xd * q[Q_M10 * g.P + t] + yd * q[Q_M11 * g.P + t]);
+}
+
+// d/dt = -sum_k (F_k(i + 1/2) - F_k(i - 1/2)) (eqs. RMHDSemiU_O2p_ES,
+// RMHDSemiJ_O2p_ES); written out (dcons != NULL) or combined into the SSP-RK3
+// stage  y_o = A y_n + B (y_s + dt L)  of (cons, J) and of the mesh x with
+// velocity xdot, dt the problem's step.
+template <typename R>
+__global__ void k_update(ProbArg pa, const R *__restrict__ fl, double *__restrict__ dcons, double *__restrict__ dJ,
+                         const double *__restrict__ cn, const double *__restrict__ Jn_,
+                         const double *__restrict__ xn, const double *__restrict__ cs,
+                         const double *__restrict__ Js, const double *__restrict__ xs,
+                         const double *__restrict__ xdot, double A, double B,
+                         const double *__restrict__ dt_dev, double *__restrict__ co, double *__restrict__ Jo,
+                         double *__restrict__ xo)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    fl += (long long)2 * 5 * D.op;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    long long c = pidx(g, i, j);
+    const R *f0 = fl, *f1 = fl + 5 * g.P;
+    double L[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        double d0 = (double)f0[a * g.P + c] - (double)f0[a * g.P + c - 1];
+        double d1 = (double)f1[a * g.P + c] - (double)f1[a * g.P + c - g.px];
+        L[a] = -(d0 + d1);
+    }
+    if (dcons) {
+        dcons += 4 * D.on;
+        dJ += D.on;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) dcons[a * g.N + id] = L[a];
+        dJ[id] = L[4];
+        return;
+    }
+    cn += 4 * D.on; cs += 4 * D.on; co += 4 * D.on;
+    Jn_ += D.on; Js += D.on; Jo += D.on;
+    xn += 2 * D.on; xs += 2 * D.on; xo += 2 * D.on; xdot += 2 * D.on;
+    double dt = dt_dev[b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) co[a * g.N + id] = A * cn[a * g.N + id] + B * (cs[a * g.N + id] + dt * L[a]);
+    Jo[id] = A * Jn_[id] + B * (Js[id] + dt * L[4]);
+    xo[id] = A * xn[id] + B * (xs[id] + dt * xdot[id]);
+    xo[g.N + id] = A * xn[g.N + id] + B * (xs[g.N + id] + dt * xdot[g.N + id]);
+}
+
+// spectral radius rho_k = L_k max |lambda_+-| / J at every node (eq. cfl,
+// static mesh), reduced to a per-problem maximum per direction
+__global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
+                      unsigned long long *red)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    q += (long long)NQ * D.op;
+    J += D.on;
+    double r[2] = {0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        long long c = pidx(g, i, j);
+        double rho = q[Q_RHO * g.P + c], p = q[Q_P * g.P + c], W = q[Q_W * g.P + c];
+        double iW = __drcp_rn(W);
+        double vx = q[Q_UX * g.P + c] * iW, vy = q[Q_UY * g.P + c] * iW;
+        double v2 = vx * vx + vy * vy;
+        double rh = rho + gam * p / (gam - 1.0);
+        double c2 = gam * p * __drcp_rn(rh), cs = sqrt(c2);
+        double iJ = __drcp_rn(J[id]);
+        for (int k = 0; k < 2; ++k) {
+            double mx = q[(Q_M00 + 2 * k) * g.P + c], my = q[(Q_M01 + 2 * k) * g.P + c];
+            double Lk = sqrt(mx * mx + my * my);
+            double vn = (mx * vx + my * vy) * __drcp_rn(Lk);
+            double disc = sqrt((1.0 - v2) * (1.0 - v2 * c2 - vn * vn * (1.0 - c2)));
+            double iden = __drcp_rn(1.0 - v2 * c2);
+            double lm = (vn * (1.0 - c2) - cs * disc) * iden, lp = (vn * (1.0 - c2) + cs * disc) * iden;
+            r[k] = Lk * fmax(fabs(lm), fabs(lp)) * iJ;
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        double m = block_reduce<0>(r[k]);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b + 2 + k, m);
+    }
+}
+
+__global__ void k_red_init(int nprob, unsigned long long *red)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nprob) return;
+    red[NRED * b + 0] = 0ull;
+    red[NRED * b + 1] = (unsigned long long)__double_as_longlong(1.0);
+    red[NRED * b + 2] = 0ull;
+    red[NRED * b + 3] = 0ull;
+}
+
+// dt of each problem: the given step, or CFL / sum_k max_i rho_k (eq. cfl)
+__global__ void k_dt(int nprob, double cfl, double dt_fixed, const unsigned long long *red, double *dt_dev)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nprob) return;
+    dt_dev[b] = dt_fixed > 0.0
+                    ? dt_fixed
+                    : cfl / (bits_to_double(red[NRED * b + 2]) + bits_to_double(red[NRED * b + 3]));
+}
+
+__global__ void k_time(int nprob, const double *dt_dev, double *t_dev)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nprob) t_dev[b] += dt_dev[b];
+}
+
+// ---- Sec. 5 mesh redistribution ---------------------------------------------
+__global__ void k_mesh_grad(ProbArg pa, int lnrho, const double *__restrict__ q, double *__restrict__ grad,
+                            unsigned long long *red)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    q += (long long)NQ * D.op;
+    grad += D.on;
+    double gv = 0.0;
+    if (id < g.N) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        long long c = pidx(g, i, j);
+        const double *s = q + (lnrho ? Q_LNR : Q_RHO) * g.P;
+        double gx = 0.5 * (s[c + 1] - s[c - 1]);
+        double gy = 0.5 * (s[c + g.px] - s[c - g.px]);
+        gv = sqrt(gx * gx + gy * gy);
+        grad[id] = gv;
+    }
+    double m = block_reduce<0>(gv);
+    if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b, m);
+}
+
+__global__ void k_mesh_omega(ProbArg pa, double alpha, const double *__restrict__ grad,
+                             const unsigned long long *red, double *__restrict__ om)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    double gmax = bits_to_double(red[(long long)NRED * b]);
+    om[D.on + id] = gmax > 0.0 ? sqrt(1.0 + alpha * grad[D.on + id] / gmax) : 1.0;
+}
+
+// omega <- sum_{a,b in {-1,0,1}} 2^-(|a|+|b|+2) omega_{i+a, j+b}
+__global__ void k_mesh_filter(ProbArg pa, const double *__restrict__ om, double *__restrict__ om2)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    om += D.on;
+    om2 += D.on;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    double acc = 0.0;
+    for (int bb = -1; bb <= 1; ++bb)
+        for (int a = -1; a <= 1; ++a) {
+            double wgt = (a == 0 && bb == 0) ? 0.25 : ((a == 0 || bb == 0) ? 0.125 : 0.0625);
+            acc += wgt * om[data_src(g, i + a, j + bb)];
+        }
+    om2[id] = acc;
+}
+
+// one Jacobi sweep of the Winslow mesh equations with omega frozen
+__global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ om, const double *__restrict__ X,
+                              double *__restrict__ Xn)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    om += D.on;
+    X += 2 * D.on;
+    Xn += 2 * D.on;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    bool fixed = (g.bc0 == 1 && (i == 0 || i == g.nx - 1)) || (g.bc1 == 1 && (j == 0 || j == g.ny - 1));
+    if (fixed) {
+        Xn[id] = X[id];
+        Xn[g.N + id] = X[g.N + id];
+        return;
+    }
+    double wi = om[id];
+    double we = om[data_src(g, i + 1, j)], ww = om[data_src(g, i - 1, j)];
+    double wn = om[data_src(g, i, j + 1)], ws = om[data_src(g, i, j - 1)];
+    double iden = __drcp_rn((2.0 * wi + we + ww) + (2.0 * wi + wn + ws));
+    for (int comp = 0; comp < 2; ++comp) {
+        double num = (wi + we) * mesh_at(g, X, i + 1, j, comp, 1) + (wi + ww) * mesh_at(g, X, i - 1, j, comp, 1) +
+                     (wi + wn) * mesh_at(g, X, i, j + 1, comp, 1) + (wi + ws) * mesh_at(g, X, i, j - 1, comp, 1);
+        Xn[comp * g.N + id] = num * iden;
+    }
+}
+
+// movement limiter: Delta tau = min over nodes and directions of half the
+// neighbour spacing over the displacement toward it, clipped to [0, 1]
+__global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const double *__restrict__ X,
+                           unsigned long long *red)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    x += 2 * D.on;
+    X += 2 * D.on;
+    double tau = 1.0;
+    if (id < g.N) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        for (int k = 0; k < 2; ++k) {
+            double d = X[k * g.N + id] - x[k * g.N + id];
+            int di = k == 0, dj = k == 1;
+            double bnd = 1.0;
+            if (d < 0.0) bnd = -(x[k * g.N + id] - mesh_at(g, x, i - di, j - dj, k, 1)) / (2.0 * d);
+            else if (d > 0.0) bnd = (mesh_at(g, x, i + di, j + dj, k, 1) - x[k * g.N + id]) / (2.0 * d);
+            tau = fmin(tau, bnd);
+        }
+        tau = fmax(tau, 0.0);
+    }
+    double m = block_reduce<1>(tau);
+    if (threadIdx.x == 0) atomic_min_nonneg(red + (long long)NRED * b + 1, m);
+}
+
+// xdot = Delta tau (x^[mu] - x^n) / dt (over 2 N values per problem)
+__global__ void k_mesh_xdot(ProbArg pa, const double *__restrict__ x, const double *__restrict__ X,
+                            const unsigned long long *red, const double *__restrict__ dt_dev,
+                            double *__restrict__ xdot)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= 2 * g.N) return;
+    double tau = bits_to_double(red[(long long)NRED * b + 1]);
+    long long o = 2 * D.on + id;
+    xdot[o] = tau * (X[o] - x[o]) / dt_dev[b];
+}
+
+// ---- state set-up and read-out ------------------------------------------------
+// initial J (reading: the determinant of the metric differences) and
+// cons = J U(prim); counts non-admissible states or tangled cells in status[1]
+template <int P>
+__global__ void k_init_state(ProbArg pa, double gam, const double *__restrict__ prim,
+                             const double *__restrict__ x, double *__restrict__ cons, double *__restrict__ J,
+                             int *status)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    prim += 4 * D.on;
+    x += 2 * D.on;
+    cons += 4 * D.on;
+    J += D.on;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    double dxi_x, dxi_y, deta_x, deta_y;
+    mesh_deltas<P>(g, x, i, j, dxi_x, dxi_y, deta_x, deta_y);
+    double J0 = dxi_x * deta_y - deta_x * dxi_y;
+    double rho = prim[id], vx = prim[g.N + id], vy = prim[2 * g.N + id], p = prim[3 * g.N + id];
+    double v2 = vx * vx + vy * vy;
+    if (!(rho > 0.0) || !(p > 0.0) || !(v2 < 1.0) || !(J0 > 0.0)) atomicAdd(status + 1, 1);
+    double W = 1.0 / sqrt(1.0 - v2);
+    double h = 1.0 + gam * p / ((gam - 1.0) * rho);
+    double rhW2 = rho * h * W * W;
+    J[id] = J0;
+    cons[id] = J0 * (rho * W);
+    cons[g.N + id] = J0 * (rhW2 * vx);
+    cons[2 * g.N + id] = J0 * (rhW2 * vy);
+    cons[3 * g.N + id] = J0 * (rhW2 - p);
+}
+
+__global__ void k_prim_out(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
+                           double *__restrict__ prim, int *status)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    cons += 4 * D.on;
+    J += D.on;
+    prim += 4 * D.on;
+    double iJ = 1.0 / J[id];
+    double rho, vx, vy, p;
+    int st = cons2prim(gam, cons[id] * iJ, cons[g.N + id] * iJ, cons[2 * g.N + id] * iJ, cons[3 * g.N + id] * iJ,
+                       -1.0, rho, vx, vy, p);
+    if (st) atomicAdd(status, 1);
+    prim[id] = rho;
+    prim[g.N + id] = vx;
+    prim[2 * g.N + id] = vy;
+    prim[3 * g.N + id] = p;
+}
+
+// totals: per-block partial sums of (J eta, J D, J) ...
+__global__ void k_totals(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ cons,
+                         const double *__restrict__ J, double *__restrict__ partials)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    q += (long long)NQ * D.op;
+    cons += 4 * D.on;
+    J += D.on;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        long long c = pidx(g, i, j);
+        double rho = q[Q_RHO * g.P + c], W = q[Q_W * g.P + c];
+        double lnr = q[Q_LNR * g.P + c], lnb = q[Q_LNB * g.P + c];
+        double s = (lnr - lnb) - gam * lnr;        // ln(p / rho^Gamma)
+        v[0] = J[id] * (-rho * W * s / (gam - 1.0));
+        v[1] = cons[id];
+        v[2] = J[id];
+    }
+    for (int k = 0; k < 3; ++k) {
+        double s = block_reduce<2>(v[k]);
+        if (threadIdx.x == 0) partials[(long long)blockIdx.x * 3 + k] = s;
+    }
+}
+
+// ... then a fixed-order sum per problem (deterministic): one thread per
+// (problem, quantity) walks the blocks of its problem
+__global__ void k_totals_final(int nprob, int nb, const int2 *__restrict__ tiles, const double *__restrict__ partials,
+                               double *__restrict__ out)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nprob) return;
+    int b = t / 3, k = t % 3;
+    double s = 0.0;
+    for (int blk = 0; blk < nb; ++blk)
+        if (!tiles || tiles[blk].x == b) s += partials[(long long)blk * 3 + k];
+    out[t] = s;
+}
+
+}  // namespace esmm

@@ -31,7 +31,8 @@ SYMBOLS = (
     "esmm_set_params", "esmm_get_params", "esmm_state_set", "esmm_state_set_cons", "esmm_state_get",
     "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
-    "esmm_rhs_static",
+    "esmm_rhs_static", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
+    "esmm_batch_times", "esmm_batch_totals", "esmm_tune",
 )
 STATIC_MAX_PADDED_NODES = 68644
 KIND_NODE, KIND_PAIRS, KIND_IFACE, KIND_UPDATE, KIND_MESH, KIND_OTHER = range(6)
@@ -74,6 +75,12 @@ def lib():
             "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
             "esmm_profile": [vp, i],
             "esmm_rhs_static": [i, i, ctypes.POINTER(i), dp, dp, d, i, i, vp, vp, vp, vp, vp, vp, vp],
+            "esmm_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(i), dp, dp, ctypes.POINTER(i), i, vp],
+            "esmm_batch_size": [vp, ctypes.POINTER(i)],
+            "esmm_batch_state_set": [vp, i, vp, vp, i],
+            "esmm_batch_state_get": [vp, i, i, vp, i],
+            "esmm_batch_times": [vp, dp], "esmm_batch_totals": [vp, dp],
+            "esmm_tune": [vp, ctypes.POINTER(i)],
             "esmm_profile_read": [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
         }
         for name, args in sig.items():
@@ -284,8 +291,67 @@ class Grid:
         self._check(lib().esmm_profile_read(self.h, ms, n, t))
         return {KINDS[k]: (ms[k], n[k], t[k]) for k in range(6)}
 
+    def tune(self):
+        """Run the launch autotuner on the current state; returns the 7 chosen
+        block sizes (negative: largest problem first)."""
+        bs = (ctypes.c_int * 7)()
+        self._check(lib().esmm_tune(self.h, bs))
+        return list(bs)
+
     def last_error(self):
         n = ctypes.c_int()
         buf = ctypes.create_string_buffer(256)
         self._check(lib().esmm_last_error(self.h, ctypes.byref(n), buf, 256))
         return n.value, buf.value.decode()
+
+
+class Batch(Grid):
+    """Many independent 2D RHD problems of different sizes in one handle.
+
+    sizes: [(nx, ny), ...]; lo, hi, bc: one pair per problem or one shared."""
+
+    def __init__(self, sizes, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC), gamma=5.0 / 3.0, p=2, w=5,
+                 stream=None, **params):
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        B = len(self.sizes)
+        per = lambda v: [tuple(v)] * B if np.ndim(v) == 1 else [tuple(t) for t in v]
+        los, his, bcs = per(lo), per(hi), per(bc)
+        n = (ctypes.c_int * (2 * B))(*[k for s in self.sizes for k in s])
+        lo2 = (ctypes.c_double * (2 * B))(*[k for s in los for k in s])
+        hi2 = (ctypes.c_double * (2 * B))(*[k for s in his for k in s])
+        bc2 = (ctypes.c_int * (2 * B))(*[int(k) for s in bcs for k in s])
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream is not None else None
+        self._check(lib().esmm_batch_create(ctypes.byref(h), B, n, lo2, hi2, bc2, RHD, st))
+        self.h = h
+        self.nprob = B
+        self.nx, self.ny, self.N = None, None, sum(a * b for a, b in self.sizes)
+        self.set_eos(gamma)
+        self.set_order(p, w)
+        if params:
+            self.set_params(**params)
+
+    def state_set(self, b, prim, x=None):
+        nx, ny = self.sizes[b]
+        pp, mp = _ptr(prim, 4 * nx * ny)
+        px, mx = _ptr(x, 2 * nx * ny)
+        self._check(lib().esmm_batch_state_set(self.h, int(b), pp, px, _mem((pp, mp), (px, mx))))
+
+    def state_get(self, b, what, out=None):
+        nx, ny = self.sizes[b]
+        size = {GET_PRIM: 4, GET_CONS: 4, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
+        if out is None:
+            out = np.empty((size, ny, nx) if size > 1 else (ny, nx))
+        po, mo = _ptr(out, size * nx * ny)
+        self._check(lib().esmm_batch_state_get(self.h, int(b), what, po, mo))
+        return out
+
+    def times(self):
+        t = (ctypes.c_double * self.nprob)()
+        self._check(lib().esmm_batch_times(self.h, t))
+        return np.array(t[:])
+
+    def totals(self):
+        out = (ctypes.c_double * (3 * self.nprob))()
+        self._check(lib().esmm_batch_totals(self.h, out))
+        return np.array(out[:]).reshape(self.nprob, 3)

@@ -99,12 +99,12 @@ def smooth_random_state(x, r, amp=0.2, modes=3):
     return np.ascontiguousarray(np.stack(out))
 
 
-def quadrant_states(r):
+def quadrant_states(r, vmax=0.9):
     """Four seeded states of a four-quadrant Riemann problem: rho in [0.1, 1],
-    p in [0.01, 1], |v| in [0, 0.9] with a uniform direction."""
+    p in [0.01, 1], |v| in [0, vmax] with a uniform direction."""
     rho = r.uniform(0.1, 1.0, 4)
     p = r.uniform(0.01, 1.0, 4)
-    sp = r.uniform(0.0, 0.9, 4)
+    sp = r.uniform(0.0, vmax, 4)
     th = r.uniform(0.0, 2 * np.pi, 4)
     return np.stack([rho, sp * np.cos(th), sp * np.sin(th), p], axis=-1)
 
@@ -130,3 +130,15 @@ def sine_config(n=64):
     """2D RHD smooth sine wave on periodic [0,1]^2, n x n nodes."""
     x = uniform_mesh(n, n, (0.0, 0.0), (1.0, 1.0), (True, True))
     return x, sine_wave(x)
+
+
+def batch_sizes(nprob=256, side=(64, 512), offset=4):
+    """Side lengths of the batched workload: uniform integers in [64, 512]."""
+    return rng(offset).integers(side[0], side[1] + 1, size=nprob)
+
+
+def batch_problem(k, n, vmax=0.5, offset=1000):
+    """Problem k of the batched workload: a seeded four-quadrant Riemann
+    problem on [-1,1]^2 with n x n nodes (outflow); speeds up to vmax."""
+    x = uniform_mesh(n, n, (-1.0, -1.0), (1.0, 1.0), (False, False))
+    return x, quadrant_riemann(x, quadrant_states(rng(offset + k), vmax=vmax))
