@@ -258,6 +258,39 @@ def mixed_vs_fp64(torch, n, stream, nsteps=20):
             "entropy_change_mixed": float((out["mixed"][1] - out["mixed"][2]) / abs(out["mixed"][2]))}
 
 
+def batch_leg(torch, stream, steps=50, warm=2):
+    """Batched workload: 256 independent seeded four-quadrant Riemann
+    problems with sides uniform in [64, 512] (|v| <= 0.5), FP32 bulk with FP64
+    recovery, every kernel one launch over the whole batch, steps replayed
+    from a CUDA graph, launch shapes autotuned; 50 RK3 steps.  The working
+    set (~18 GB) is far larger than L2."""
+    from paper_2107_12027_gb300 import esmm
+    from paper_2107_12027_gb300 import workloads as wl
+    sides = wl.batch_sizes()
+    with esmm.Batch([(int(s), int(s)) for s in sides], lo=(-1, -1), hi=(1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW),
+                    p=2, w=5, stream=stream.cuda_stream, **grid_params("mixed")) as b:
+        for k, s in enumerate(sides):
+            x, prim = wl.batch_problem(k, int(s))
+            b.state_set(k, prim, x)
+        shapes = b.tune()
+        b.advance(warm)
+        torch.cuda.synchronize()
+        b.profile(0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        nfail, _ = b.last_error()
+        launches = int(sum(v[1] for v in b.profile_read().values()))
+        nodes = int(sum(int(s) ** 2 for s in sides))
+    return {"value": nodes * 3 * steps / (ms * 1e-3), "unit": UNIT, "problems": len(sides), "nodes": nodes,
+            "side_range": [int(sides.min()), int(sides.max())], "steps": steps, "ms_per_step": ms / steps,
+            "precision": "f32 bulk + f64 recovery", "graph": True, "tile_shapes": shapes,
+            "gpu_launches": launches, "failed_recoveries": int(nfail)}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -332,6 +365,7 @@ def run_gpu(args):
                 tm, _, _ = timed_steps(gm, torch, K, W, flush, stream, None)
             forms = {"mixed": {"value": n * n * 3 * K / (tm * 1e-3), "ms_per_step": tm / K}}
             forms["mixed"].update(mixed_vs_fp64(torch, n, stream))
+            forms["batched"] = batch_leg(torch, stream)
             line["forms"] = forms
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -209,3 +209,31 @@ def test_rhs_parity_full_size_riemann_400(p, w):
         got = g.rhs(cons, J, x, xdot)
     assert _rel(got[0], ref[0]) < TOL
     assert _rel(got[1], ref[1]) < TOL
+
+
+def test_sine_wave_64_to_t01_against_oracle_and_exact():
+    # 2D RHD smooth sine wave on periodic [0,1]^2, 64x64, Gamma = 5/3,
+    # rho = 1 + 0.2 sin(2 pi (x + y)), v = (0.2, 0.2), p = 1, p = 2 + WENO5,
+    # adaptive mesh (sigma = rho), SSP-RK3 at CFL 0.4 to t = 0.1.  Per-step
+    # parity is 1e-12; over the whole run rounding differences may grow, so the
+    # final state is held to 1e-10.
+    n = 64
+    x, prim = wl.sine_config(n)
+    kw = dict(alpha=20.0, monitor=oracle.MONITOR_RHO)
+    cfg = _cfg(n, n, (0, 0), (0, 0), (1, 1), 2, 5, **kw)
+    cons, J = oracle.init_state(cfg, prim, x)
+    t = 0.0
+    with _grid(n, n, (0, 0), (0, 0), (1, 1), 2, 5, **kw) as g:
+        g.state_set(prim, x)
+        while t < 0.1 - 1e-14:
+            dt = min(oracle.cfl_dt(cfg, cons, J, x), 0.1 - t)
+            cons, J, x, _ = oracle.rk_step(cfg, cons, J, x, dt)
+            g.rk_step(dt)
+            t += dt
+        assert _rel(g.state_get(esmm.GET_CONS), cons) < 1e-10
+        assert _rel(g.state_get(esmm.GET_X), x) < 1e-10
+        rho = g.state_get(esmm.GET_PRIM)[0]
+        assert abs(g.time() - 0.1) < 1e-14
+        xs = g.state_get(esmm.GET_X)
+    exact = wl.sine_wave(xs, 0.1)[0]
+    assert np.abs(rho - exact).mean() < 5e-5    # L1 error of the scheme itself (the oracle agrees)
