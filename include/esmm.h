@@ -163,6 +163,30 @@ int esmm_batch_times(esmm_grid *g, double *t);
 /* out[nprob][3]: the FP64 totals of esmm_totals for every problem */
 int esmm_batch_totals(esmm_grid *g, double *out);
 
+/* Adjoint (spec form 3): gradients of a final-time functional with
+ * respect to the initial data, single problems only, FP64 arithmetic.
+ * esmm_adjoint_record advances nsteps steps (dt as esmm_rk_step) from the
+ * current state, keeping per-step checkpoints (state, mesh velocity, step) on
+ * the device (9 N doubles per step).  The adjoint differentiates the recorded
+ * map: each step with its recorded mesh velocity and dt held fixed (the
+ * monitor's maximum and the limiter's minimum are not differentiable), the
+ * sign switch Y and the lambda^ maximum frozen at their forward selection;
+ * esmm_adjoint_replay re-runs that map from the current state (for finite-
+ * difference checks).  esmm_adjoint_vjp takes lam_final [4][N] = dF/d(cons)
+ * at the last recorded step and returns lam_cons0 = dF/d(cons) at the first
+ * (may be NULL) and lam_prim0 = dF/d(prim) of the first state (may be NULL),
+ * recomputing the RK stages of each step backwards from its checkpoint.
+ * esmm_rhs_vjp returns lam = (d rhs/d cons)^T mu at (cons, J, x, xdot) (J, x
+ * and xdot held fixed), through the implicit-function adjoint of the Newton
+ * recovery, the log means, the scaled eigenvectors and the WENO weights. */
+int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt);
+int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt);
+int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int mem);
+int esmm_adjoint_replay(esmm_grid *g, int nsteps);
+int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem);
+int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
+                 const double *mu, double *lam, int mem);
+
 /* Launch autotuner: for each kernel kind (node pass, pair fluxes, interface
  * fluxes, per-node kernels) time the candidate block sizes -- and, for
  * batches, the tile orders natural / largest problem first -- on the current

@@ -87,6 +87,7 @@ def lib():
                 "oref_cfl_dt": (ctypes.c_int, [c, d, d, d, d]),
                 "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d]),
                 "oref_rk_step": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d]),
+                "oref_rk_step_given": (ctypes.c_int, [c, d, d, d, d, ctypes.c_double]),
                 "oref_init_state": (ctypes.c_int, [c, d, d, d, d]),
                 "oref_state_prim": (ctypes.c_int, [c, d, d, d]),
                 "oref_totals": (ctypes.c_int, [c, d, d, d, d, d]),
@@ -262,6 +263,18 @@ def rk_step(cfg, cons, J, x, dt=0.0):
         raise RuntimeError("oracle rk_step: cons2prim failed")
     return (cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx),
             x.reshape(2, cfg.ny, cfg.nx), dtu[0])
+
+
+def rk_step_given(cfg, cons, J, x, xdot, dt):
+    """One SSP-RK3 step with a given mesh velocity and step."""
+    N = cfg.nx * cfg.ny
+    cons = _vec(cons, 4 * N).copy()
+    J = _vec(J, N).copy()
+    x = _vec(x, 2 * N).copy()
+    st = lib().oref_rk_step_given(ctypes.byref(cfg), _p(cons), _p(J), _p(x), _p(_vec(xdot, 2 * N)), float(dt))
+    if st != 0:
+        raise RuntimeError("oracle rk_step_given: cons2prim failed")
+    return cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx), x.reshape(2, cfg.ny, cfg.nx)
 
 
 def totals(cfg, cons, J, dcons=None, dJ=None):

@@ -908,6 +908,37 @@ int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
     return status;
 }
 
+/* One SSP-RK3 step with a given mesh velocity xdot [2][N] and step dt (the
+ * map whose derivative the adjoint computes: the step's mesh motion and dt
+ * held at given values). */
+int oref_rk_step_given(const oref_cfg *c, double *cons, double *J, double *x,
+                       const double *xdot, double dt)
+{
+    int N = c->nx * c->ny, status = 0;
+    double *c1 = (double *)malloc(sizeof(double) * 4 * N);
+    double *c2 = (double *)malloc(sizeof(double) * 4 * N);
+    double *J1 = (double *)malloc(sizeof(double) * N);
+    double *J2 = (double *)malloc(sizeof(double) * N);
+    double *x1 = (double *)malloc(sizeof(double) * 2 * N);
+    double *x2 = (double *)malloc(sizeof(double) * 2 * N);
+    double *L = (double *)malloc(sizeof(double) * 4 * N);
+    double *LJ = (double *)malloc(sizeof(double) * N);
+    status |= oref_rhs(c, cons, J, x, xdot, L, LJ);
+    for (int a = 0; a < 4 * N; ++a) c1[a] = cons[a] + dt * L[a];
+    for (int a = 0; a < N; ++a) J1[a] = J[a] + dt * LJ[a];
+    for (int a = 0; a < 2 * N; ++a) x1[a] = x[a] + dt * xdot[a];
+    status |= oref_rhs(c, c1, J1, x1, xdot, L, LJ);
+    for (int a = 0; a < 4 * N; ++a) c2[a] = 0.75 * cons[a] + 0.25 * (c1[a] + dt * L[a]);
+    for (int a = 0; a < N; ++a) J2[a] = 0.75 * J[a] + 0.25 * (J1[a] + dt * LJ[a]);
+    for (int a = 0; a < 2 * N; ++a) x2[a] = 0.75 * x[a] + 0.25 * (x1[a] + dt * xdot[a]);
+    status |= oref_rhs(c, c2, J2, x2, xdot, L, LJ);
+    for (int a = 0; a < 4 * N; ++a) cons[a] = cons[a] / 3.0 + 2.0 / 3.0 * (c2[a] + dt * L[a]);
+    for (int a = 0; a < N; ++a) J[a] = J[a] / 3.0 + 2.0 / 3.0 * (J2[a] + dt * LJ[a]);
+    for (int a = 0; a < 2 * N; ++a) x[a] = x[a] / 3.0 + 2.0 / 3.0 * (x2[a] + dt * xdot[a]);
+    free(c1); free(c2); free(J1); free(J2); free(x1); free(x2); free(L); free(LJ);
+    return status;
+}
+
 /* Totals: sum_i J_i eta_i (Sec. 6 total entropy, without the 1/N^2),
  * sum_i (J D)_i, sum_i J_i and the semi-discrete entropy production
  * sum_i (V_i . d(JU)_i/dt - phi_i dJ_i/dt), which vanishes for the EC scheme

@@ -91,6 +91,11 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
 int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
                  double dt, double *dt_used);
 
+/* One SSP-RK3 step with a given mesh velocity and step (the map the adjoint
+ * differentiates). */
+int oref_rk_step_given(const oref_cfg *c, double *cons, double *J, double *x,
+                       const double *xdot, double dt);
+
 /* Initial curvilinear state: J from the mesh and cons = J * U(prim). */
 int oref_init_state(const oref_cfg *c, const double *prim, const double *x,
                     double *cons, double *J);

@@ -85,6 +85,12 @@ struct esmm_grid {
     long long launches[ESMM_NKINDS];
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *ev;
     std::vector<cudaEvent_t> *pool;
+    // adjoint: per-step checkpoints [cons 4N | J N | x 2N | xdot 2N] and steps
+    std::vector<double *> *ck;
+    std::vector<double> *ck_dt;
+    int ck_n;
+    double *adjG, *adjGp;            // local Jacobian-vector contributions
+    double *lam_a, *lam_b, *lam_c, *lam_v;
 };
 
 namespace {
@@ -358,6 +364,8 @@ int mesh_core(esmm_grid *g)
     return ESMM_OK;
 }
 
+int stages(esmm_grid *g);
+
 // One step of every problem (asynchronous on the grid's stream).
 int rk_step_async(esmm_grid *g, double dt)
 {
@@ -374,6 +382,13 @@ int rk_step_async(esmm_grid *g, double dt)
         LaunchDom L = dom(g, D_PAD);
         k_tmetric<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->xdot, g->q);
     }
+    return stages(g);
+}
+
+// The three SSP-RK3 stages, the node data of the state (with the step's mesh
+// velocity) already in g->q and the step in dt_dev.
+int stages(esmm_grid *g)
+{
     fluxes(g);
     update(g, nullptr, nullptr, g->cons, g->J, g->x, g->cons, g->J, g->x, g->xdot, 0.0, 1.0, g->c1, g->J1, g->x1);
     // stage 2: y2 = 3/4 y^n + 1/4 (y1 + dt L(y1))
@@ -440,6 +455,15 @@ void free_all(esmm_grid *g)
         delete g->pool;
         g->pool = nullptr;
     }
+    if (g->ck) {
+        for (double *b : *g->ck) cudaFree(b);
+        delete g->ck;
+        g->ck = nullptr;
+    }
+    if (g->ck_dt) { delete g->ck_dt; g->ck_dt = nullptr; }
+    double **abufs[] = {&g->adjG, &g->adjGp, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v};
+    for (double **b : abufs)
+        if (*b) { cudaFree(*b); *b = nullptr; }
     if (g->own_st) { cudaStreamDestroy(g->own_st); g->own_st = nullptr; }
     g->pairs = g->iflux = nullptr;
     g->red = nullptr;
@@ -484,7 +508,12 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     }
     g->ev = new (std::nothrow) std::vector<std::pair<cudaEvent_t, cudaEvent_t>>[ESMM_NKINDS];
     g->pool = new (std::nothrow) std::vector<cudaEvent_t>;
-    if (!g->ev || !g->pool || cudaGetDevice(&g->dev) != cudaSuccess) { release(g); return ESMM_ERR_CUDA; }
+    g->ck = new (std::nothrow) std::vector<double *>;
+    g->ck_dt = new (std::nothrow) std::vector<double>;
+    if (!g->ev || !g->pool || !g->ck || !g->ck_dt || cudaGetDevice(&g->dev) != cudaSuccess) {
+        release(g);
+        return ESMM_ERR_CUDA;
+    }
     g->nprob = nprob;
     g->st = (cudaStream_t)stream;
     if (!stream && own_stream) {
@@ -833,6 +862,66 @@ int tune(esmm_grid *g)
     return ESMM_OK;
 }
 
+// ---- adjoint (spec form 3) ---------------------------------------------
+int adj_alloc(esmm_grid *g)
+{
+    size_t P = (size_t)g->Ptot, N = (size_t)g->Ntot, d = sizeof(double);
+    if (!g->adjG) CK(cudaMalloc((void **)&g->adjG, ADJ_G_PER_NODE * P * d));
+    if (!g->adjGp) CK(cudaMalloc((void **)&g->adjGp, ADJ_GP_PER_NODE * P * d));
+    double **bufs[] = {&g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v};
+    for (double **b : bufs)
+        if (!*b) CK(cudaMalloc((void **)b, 4 * N * d));
+    return ESMM_OK;
+}
+
+// lam = (d rhs/d cons)^T mu at (cons, J, x, xdot), all device arrays
+int rhs_vjp_core(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
+                 const double *mu, double *lam)
+{
+    size_t P = (size_t)g->Ptot, N = (size_t)g->Ntot, d = sizeof(double);
+    node(g, cons, J, x, xdot, nullptr, nullptr);
+    CK(cudaMemsetAsync(g->adjG, 0, ADJ_G_PER_NODE * P * d, g->st));
+    CK(cudaMemsetAsync(g->adjGp, 0, ADJ_GP_PER_NODE * P * d, g->st));
+    CK(cudaMemsetAsync(lam, 0, 4 * N * d, g->st));
+    Phys ph = phys(g);
+    for (int dir = 0; dir < 2; ++dir) {
+        {
+            Prof pr_(g, ESMM_KIND_PAIRS);
+            launch_pairs_vjp(dom(g, dir ? D_PAIR1 : D_PAIR0), ph, g->q, mu, g->adjGp, dir, g->st);
+        }
+        if (g->w > 0) {
+            Prof pr_(g, ESMM_KIND_IFACE);
+            launch_iface_vjp(dom(g, dir ? D_IFACE1 : D_IFACE0), ph, g->q, mu, g->adjG, dir, g->st);
+        }
+    }
+    {
+        Prof pr_(g, ESMM_KIND_NODE);
+        launch_node_vjp(dom(g, D_PAD), g->gamma, g->p, g->w, g->q, g->adjG, g->adjGp, J, lam, g->st);
+    }
+    CK(cudaGetLastError());
+    return ESMM_OK;
+}
+
+int set_dt(esmm_grid *g, double dt)
+{
+    g->pin[0] = dt;
+    CK(cudaMemcpyAsync(g->dt_dev, g->pin, sizeof(double), cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+// One step with a given mesh velocity (device, [2][N]) and dt: the map the
+// adjoint differentiates.
+int step_given(esmm_grid *g, const double *xd, double dt)
+{
+    int rc;
+    if ((rc = ensure_doms(g)) || (rc = set_dt(g, dt))) return rc;
+    CK(cudaMemcpyAsync(g->xdot, xd, 2 * (size_t)g->Ntot * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    g->xdot_zero = 0;
+    node(g, g->cons, g->J, g->x, g->xdot, g->pg[0], g->pg[1]);
+    return stages(g);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1148,6 +1237,149 @@ int esmm_tune(esmm_grid *g, int *block_sizes)
     if (block_sizes)
         for (int k = 0; k < ND; ++k) block_sizes[k] = g->bs[k] * (g->order_lpt[k] ? -1 : 1);
     return ESMM_OK;
+}
+
+int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
+                 const double *mu, double *lam, int mem)
+{
+    if (!g || !cons || !J || !x || !mu || !lam || g->nprob != 1) return ESMM_ERR_ARG;
+    int rc;
+    if ((rc = ensure_doms(g)) || (rc = adj_alloc(g))) return rc;
+    size_t N = (size_t)g->Ntot;
+    if (mem == ESMM_MEM_HOST) {
+        if ((rc = copy_in(g, g->in_cons, cons, 4 * N, mem)) || (rc = copy_in(g, g->in_J, J, N, mem)) ||
+            (rc = copy_in(g, g->in_x, x, 2 * N, mem)) || (rc = copy_in(g, g->lam_a, mu, 4 * N, mem)))
+            return rc;
+        if (xdot && (rc = copy_in(g, g->in_xdot, xdot, 2 * N, mem))) return rc;
+        cons = g->in_cons;
+        J = g->in_J;
+        x = g->in_x;
+        xdot = xdot ? g->in_xdot : nullptr;
+        mu = g->lam_a;
+    }
+    double *out = mem == ESMM_MEM_HOST ? g->lam_v : lam;
+    if ((rc = rhs_vjp_core(g, cons, J, x, xdot, mu, out))) return rc;
+    if (mem == ESMM_MEM_HOST) {
+        if ((rc = copy_out(g, lam, g->lam_v, 4 * N, mem))) return rc;
+        CK(cudaStreamSynchronize(g->st));
+        return check_c2p(g);
+    }
+    return ESMM_OK;
+}
+
+int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
+{
+    if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
+    if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
+    size_t N = (size_t)g->Ntot, d = sizeof(double);
+    g->ck_dt->clear();
+    g->ck_n = 0;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((int)g->ck->size() <= n) {
+            double *b = nullptr;
+            CK(cudaMalloc((void **)&b, 9 * N * d));
+            g->ck->push_back(b);
+        }
+        double *b = (*g->ck)[n];
+        CK(cudaMemcpyAsync(b, g->cons, 4 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(b + 4 * N, g->J, N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(b + 5 * N, g->x, 2 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        int rc = rk_step_async(g, dt);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(b + 7 * N, g->xdot, 2 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(g->pin, g->dt_dev, d, cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        g->ck_dt->push_back(g->pin[0]);
+        g->ck_n = n + 1;
+    }
+    return check_c2p(g);
+}
+
+int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt)
+{
+    if (!g || !nsteps) return ESMM_ERR_ARG;
+    *nsteps = g->ck_n;
+    if (dt)
+        for (int n = 0; n < g->ck_n; ++n) dt[n] = (*g->ck_dt)[n];
+    return ESMM_OK;
+}
+
+int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int mem)
+{
+    if (!g || !out || step < 0 || step >= g->ck_n) return ESMM_ERR_ARG;
+    size_t N = (size_t)g->Ntot;
+    const double *b = (*g->ck)[step];
+    int rc;
+    switch (what) {
+    case ESMM_GET_CONS: rc = copy_out(g, out, b, 4 * N, mem); break;
+    case ESMM_GET_J: rc = copy_out(g, out, b + 4 * N, N, mem); break;
+    case ESMM_GET_X: rc = copy_out(g, out, b + 5 * N, 2 * N, mem); break;
+    case ESMM_GET_XDOT: rc = copy_out(g, out, b + 7 * N, 2 * N, mem); break;
+    default: return fail(g, ESMM_ERR_ARG, "unknown field");
+    }
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+int esmm_adjoint_replay(esmm_grid *g, int nsteps)
+{
+    if (!g || nsteps < 0 || nsteps > g->ck_n || g->nprob != 1) return ESMM_ERR_ARG;
+    if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
+    size_t N = (size_t)g->Ntot;
+    for (int n = 0; n < nsteps; ++n) {
+        int rc = step_given(g, (*g->ck)[n] + 7 * N, (*g->ck_dt)[n]);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(g->st));
+    return check_c2p(g);
+}
+
+int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem)
+{
+    if (!g || !lam_final || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->ck_n < 1) return fail(g, ESMM_ERR_STATE, "no recorded steps");
+    int rc;
+    if ((rc = ensure_doms(g)) || (rc = adj_alloc(g))) return rc;
+    size_t N = (size_t)g->Ntot;
+    const long long n4 = 4 * (long long)N;
+    double *la = g->lam_a, *lb = g->lam_b, *lc = g->lam_c, *v = g->lam_v;
+    if ((rc = copy_in(g, la, lam_final, 4 * N, mem))) return rc;
+    for (int n = g->ck_n - 1; n >= 0; --n) {
+        double *b = (*g->ck)[n];
+        double *c0 = b, *J0 = b + 4 * N, *x0 = b + 5 * N, *xd = b + 7 * N;
+        double dt = (*g->ck_dt)[n];
+        if ((rc = set_dt(g, dt))) return rc;
+        // recompute the stage states (c1, J1, x1), (c2, J2, x2)
+        node(g, c0, J0, x0, xd, nullptr, nullptr);
+        fluxes(g);
+        update(g, nullptr, nullptr, c0, J0, x0, c0, J0, x0, xd, 0.0, 1.0, g->c1, g->J1, g->x1);
+        node(g, g->c1, g->J1, g->x1, xd, nullptr, nullptr);
+        fluxes(g);
+        update(g, nullptr, nullptr, c0, J0, x0, g->c1, g->J1, g->x1, xd, 0.75, 0.25, g->c2, g->J2, g->x2);
+        // stage 3: c3 = 1/3 c0 + 2/3 (c2 + dt L(c2))
+        if ((rc = rhs_vjp_core(g, g->c2, g->J2, g->x2, xd, la, v))) return rc;
+        launch_lincomb(n4, 2.0 / 3.0, la, 2.0 / 3.0 * dt, v, lb, g->st);    // lambda_c2
+        launch_lincomb(n4, 1.0 / 3.0, la, 0.0, nullptr, lc, g->st);         // lambda_c0
+        // stage 2: c2 = 3/4 c0 + 1/4 (c1 + dt L(c1))
+        if ((rc = rhs_vjp_core(g, g->c1, g->J1, g->x1, xd, lb, v))) return rc;
+        launch_lincomb(n4, 0.25, lb, 0.25 * dt, v, la, g->st);              // lambda_c1
+        launch_lincomb(n4, 1.0, lc, 0.75, lb, lc, g->st);
+        // stage 1: c1 = c0 + dt L(c0)
+        if ((rc = rhs_vjp_core(g, c0, J0, x0, xd, la, v))) return rc;
+        launch_lincomb(n4, 1.0, lc, 1.0, la, lc, g->st);
+        launch_lincomb(n4, 1.0, lc, dt, v, la, g->st);                      // lambda of c^n
+    }
+    CK(cudaGetLastError());
+    if (lam_cons0 && (rc = copy_out(g, lam_cons0, la, 4 * N, mem))) return rc;
+    if (lam_prim0) {
+        double *b0 = (*g->ck)[0];
+        LaunchDom L = dom(g, D_NODE);
+        launch_prim_grad(L, g->gamma, b0, b0 + 4 * N, la, v, g->st);
+        if ((rc = copy_out(g, lam_prim0, v, 4 * N, mem))) return rc;
+    }
+    CK(cudaStreamSynchronize(g->st));
+    return check_c2p(g);
 }
 
 int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const double hi[2], double gamma, int p,

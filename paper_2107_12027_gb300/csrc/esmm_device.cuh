@@ -159,34 +159,92 @@ __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double
 }
 
 // ---------------------------------------------------------------------------
+// Dual number a + b eps (eps^2 = 0): the flux arithmetic below is templated on
+// its working type, and evaluating it on duals seeded at one input gives the
+// derivative of every output with respect to that input.  The adjoint kernels
+// use this for the local (per pair / per interface) Jacobian-vector products.
+struct dual {
+    double v, d;
+    __host__ __device__ dual() {}
+    __host__ __device__ constexpr dual(double a) : v(a), d(0.0) {}
+    __host__ __device__ constexpr dual(double a, double b) : v(a), d(b) {}
+};
+__device__ __forceinline__ dual operator+(dual a, dual b) { return dual(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ dual operator-(dual a, dual b) { return dual(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ dual operator-(dual a) { return dual(-a.v, -a.d); }
+__device__ __forceinline__ dual operator*(dual a, dual b) { return dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ dual operator/(dual a, dual b)
+{
+    double r = 1.0 / b.v;
+    double q = a.v * r;
+    return dual(q, (a.d - q * b.d) * r);
+}
+__device__ __forceinline__ dual operator+(dual a, double b) { return dual(a.v + b, a.d); }
+__device__ __forceinline__ dual operator+(double a, dual b) { return dual(a + b.v, b.d); }
+__device__ __forceinline__ dual operator-(dual a, double b) { return dual(a.v - b, a.d); }
+__device__ __forceinline__ dual operator-(double a, dual b) { return dual(a - b.v, -b.d); }
+__device__ __forceinline__ dual operator*(dual a, double b) { return dual(a.v * b, a.d * b); }
+__device__ __forceinline__ dual operator*(double a, dual b) { return dual(a * b.v, a * b.d); }
+__device__ __forceinline__ dual operator/(dual a, double b) { return dual(a.v / b, a.d / b); }
+__device__ __forceinline__ dual operator/(double a, dual b) { return dual(a) / b; }
+__device__ __forceinline__ dual &operator+=(dual &a, dual b) { a = a + b; return a; }
+__device__ __forceinline__ dual &operator-=(dual &a, dual b) { a = a - b; return a; }
+__device__ __forceinline__ dual &operator*=(dual &a, dual b) { a = a * b; return a; }
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ float val(float x) { return x; }
+__device__ __forceinline__ double val(dual x) { return x.v; }
+
+// type of the log-mean arguments: FP64 for the FP64 and FP32-bulk forms
+template <typename R> struct LogT { using type = double; };
+template <> struct LogT<dual> { using type = dual; };
+
 template <typename R> __device__ __forceinline__ R rsq(R x);
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ dual rsq<dual>(dual x)
+{
+    double r = rsqrt(x.v);
+    return dual(r, -0.5 * r * r * r * x.d);
+}
 template <typename R> __device__ __forceinline__ R sq_rt(R x);
 template <> __device__ __forceinline__ double sq_rt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float sq_rt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ dual sq_rt<dual>(dual x)
+{
+    double r = sqrt(x.v);
+    return dual(r, 0.5 * x.d / r);
+}
 // reciprocal (IEEE round-to-nearest) and a square root of a positive value
 // through the reciprocal square root: on GB300 both are cheaper than the
 // FP64 quotient and square root
 template <typename R> __device__ __forceinline__ R rcp(R x);
 template <> __device__ __forceinline__ double rcp<double>(double x) { return __drcp_rn(x); }
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ dual rcp<dual>(dual x)
+{
+    double r = __drcp_rn(x.v);
+    return dual(r, -r * r * x.d);
+}
 template <typename R> __device__ __forceinline__ R sqrt_pos(R x) { return x * rsq<R>(x); }
 template <typename R> __device__ __forceinline__ R fab(R x);
 template <> __device__ __forceinline__ double fab<double>(double x) { return fabs(x); }
 template <> __device__ __forceinline__ float fab<float>(float x) { return fabsf(x); }
+template <> __device__ __forceinline__ dual fab<dual>(dual x) { return x.v < 0.0 ? -x : x; }
+// larger of two values (the derivative follows the selected argument)
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ dual vmax(dual a, dual b) { return a.v >= b.v ? a : b; }
 
 // Logarithmic mean [[a]]/[[ln a]] and its reciprocal from FP64 node values
 // and their FP64 logarithms.  Near-equal arguments, ((b-a)/(b+a))^2 < thr, use
 // the Ismail-Roe series in FP64: mean = (a+b)/(2 F), F = 1 + u/3 + u^2/5 + u^3/7.
-template <typename R>
-__device__ __forceinline__ void logmean(double a, double b, double la, double lb, double thr,
-                                        R &mean, R &inv_mean)
+template <typename R, typename T>
+__device__ __forceinline__ void logmean(T a, T b, T la, T lb, double thr, R &mean, R &inv_mean)
 {
-    double d = b - a, s = b + a;
-    if (d * d < thr * s * s) {
-        double u = d * d / (s * s);
-        double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
+    T d = b - a, s = b + a;
+    if (val(d * d) < val(thr * s * s)) {
+        T u = d * d / (s * s);
+        T F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
         mean = (R)(s / (2.0 * F));
         inv_mean = (R)(2.0 * F / s);
     } else {
@@ -199,7 +257,7 @@ __device__ __forceinline__ void logmean(double a, double b, double la, double lb
 // Node values of one two-point flux argument (the parameter variables).
 template <typename R>
 struct NodeV {
-    double rho, beta, lnr, lnb;  // FP64: log-mean arguments
+    typename LogT<R>::type rho, beta, lnr, lnb;  // log-mean arguments (FP64 unless dual)
     R r, b, ux, uy, W;
 };
 
@@ -220,8 +278,8 @@ __device__ __forceinline__ void ec_pair(const NodeV<R> &l, const NodeV<R> &r, R 
                                         R gm1inv, double thr, R out[4])
 {
     R rln, irln, bln, ibln;
-    logmean<R>(l.rho, r.rho, l.lnr, r.lnr, thr, rln, irln);
-    logmean<R>(l.beta, r.beta, l.lnb, r.lnb, thr, bln, ibln);
+    logmean<R, typename LogT<R>::type>(l.rho, r.rho, l.lnr, r.lnr, thr, rln, irln);
+    logmean<R, typename LogT<R>::type>(l.beta, r.beta, l.lnb, r.lnb, thr, bln, ibln);
     R half = (R)0.5;
     R rm = half * (l.r + r.r);
     R bm = half * (l.b + r.b);
@@ -281,6 +339,10 @@ __device__ __forceinline__ R weno3(R s0, R s1, R s2, R eps)
 
 __device__ __forceinline__ int sgn_d(double a) { return (a > 0.0) - (a < 0.0); }
 __device__ __forceinline__ int sgn_d(float a) { return (a > 0.0f) - (a < 0.0f); }
+__device__ __forceinline__ int sgn_d(dual a) { return (a.v > 0.0) - (a.v < 0.0); }
+__device__ __forceinline__ bool le(double a, double b) { return a <= b; }
+__device__ __forceinline__ bool le(float a, float b) { return a <= b; }
+__device__ __forceinline__ bool le(dual a, dual b) { return a.v <= b.v; }
 
 // Scaled eigenvectors of dF_1/dU (Sec. 4) at the rotated state (rho, vn, vt, p)
 // with W = 1/sqrt(1 - vn^2 - vt^2): columns dU_m * s_m, s_m = (dU_m . dV_m)^-1/2,

@@ -30,6 +30,108 @@ __device__ __forceinline__ NodeV<R> load_node(const Geom &g, const double *__res
     return v;
 }
 
+// The ES dissipation 1/2 lambda^ T^-1 R Y <<V~>> of eq. ESFlux_HO at one
+// interface (to be subtracted from the EC flux).  nvx, nvy, jt: the interface
+// metrics (mean of the two nodes); rho0/1, lnr0/1: density and its log at the
+// two interface nodes (the log-mean arguments); st[k] = (beta, u_x, u_y, W,
+// ln rho, ln beta) of the w + 1 stencil nodes, the interface nodes at
+// k = (w-1)/2 and (w+1)/2.  The eigen-system is taken at rho = {{rho}}^ln,
+// u = {{u}}, p = {{rho}}/{{beta}}; Y has sign 0 for jumps at rounding level.
+// stencil values read straight from the node arrays (forward kernels)
+template <typename R>
+struct QStencil {
+    const double *q;
+    long long P, c0, sd;
+    int off;
+    __device__ __forceinline__ R operator()(int k, int j) const
+    {
+        const int f = j == 0 ? Q_BETA : (j == 1 ? Q_UX : (j == 2 ? Q_UY : (j == 3 ? Q_W : (j == 4 ? Q_LNR : Q_LNB))));
+        return (R)q[f * P + c0 + (k - off) * sd];
+    }
+};
+
+// stencil values held in an array (the adjoint's seeded duals)
+template <typename R, int NS>
+struct ArrStencil {
+    const R (*a)[6];
+    __device__ __forceinline__ R operator()(int k, int j) const { return a[k][j]; }
+};
+
+template <typename R, typename T, int WW, typename ST>
+__device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho1, T lnr0, T lnr1,
+                                               const ST &st, const Phys &ph, R diss[4])
+{
+    constexpr int NS = WW + 1, OFF = (WW - 1) / 2;
+    const R half = (R)0.5, one = (R)1;
+    const R gam = (R)ph.gamma;
+    R n2 = nvx * nvx + nvy * nvy;
+    R iLk = rsq<R>(n2);
+    R Lk = n2 * iLk;
+    R nx = nvx * iLk, ny = nvy * iLk;
+    R rho, irho;
+    logmean<R, T>(rho0, rho1, lnr0, lnr1, ph.ln_thr, rho, irho);
+    R ux = half * (st(OFF, 1) + st(OFF + 1, 1));
+    R uy = half * (st(OFF, 2) + st(OFF + 1, 2));
+    R p = ((R)rho0 + (R)rho1) * rcp<R>(st(OFF, 0) + st(OFF + 1, 0));
+    R w2 = one + ux * ux + uy * uy;
+    R iW = rsq<R>(w2);
+    R W = w2 * iW;
+    R vx = ux * iW, vy = uy * iW;
+    R vn = nx * vx + ny * vy, vt = -ny * vx + nx * vy;
+    R dU[4][4], s[4], lm, lp;
+    eigen_rhd<R>(gam, rho, vn, vt, p, W, dU, s, lm, lp);
+    R lhat = vmax(fab<R>(jt + Lk * lm), fab<R>(jt + Lk * lp));
+    const R ig = rcp<R>(gam - one), c1g = gam * ig;
+    R Vt[NS][4];
+    R aT[4] = {(R)0, (R)0, (R)0, (R)0};     // |T V| summed over the two interface nodes
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        R b = st(k, 0);
+        R V0 = c1g + st(k, 4) + ig * st(k, 5) + b;
+        R Vx = b * st(k, 1);
+        R Vy = b * st(k, 2);
+        R VE = -b * st(k, 3);
+        R T1 = nx * Vx + ny * Vy, T2 = -ny * Vx + nx * Vy;
+        if (k == OFF || k == OFF + 1) {
+            aT[0] += fab<R>(V0); aT[1] += fab<R>(T1); aT[2] += fab<R>(T2); aT[3] += fab<R>(VE);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            Vt[k][m] = s[m] * (dU[0][m] * V0 + dU[1][m] * T1 + dU[2][m] * T2 + dU[3][m] * VE);
+    }
+    const R eps = (R)ph.eps;
+    const R sign_tol = (R)ph.sign_tol;
+    R z[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        R vminus, vplus;
+        if (WW == 5) {
+            vminus = weno5<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
+            vplus = weno5<R>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
+        } else {
+            vminus = weno3<R>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
+            vplus = weno3<R>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
+        }
+        R jw = vplus - vminus;
+        R jump = Vt[OFF + 1][m] - Vt[OFF][m];
+        // a jump within sign_tol of the magnitudes forming V~_m at the two
+        // interface nodes is rounding noise: its sign is 0 (so Y = 0)
+        R scale = s[m] * (fab<R>(dU[0][m]) * aT[0] + fab<R>(dU[1][m]) * aT[1] +
+                          fab<R>(dU[2][m]) * aT[2] + fab<R>(dU[3][m]) * aT[3]);
+        int sj = le(fab<R>(jump), sign_tol * scale) ? 0 : sgn_d(jump);
+        z[m] = (sgn_d(jw) == sj) ? jw * s[m] : (R)0;
+    }
+    R d[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        d[a] = dU[a][0] * z[0] + dU[a][1] * z[1] + dU[a][2] * z[2] + dU[a][3] * z[3];
+    R hl = half * lhat;
+    diss[0] = hl * d[0];
+    diss[1] = hl * (nx * d[1] - ny * d[2]);
+    diss[2] = hl * (ny * d[1] + nx * d[2]);
+    diss[3] = hl * d[3];
+}
+
 // anchors A in [-P, n_dir - 1] along the sweep, every line of the other index
 template <typename R, int P>
 __global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double *__restrict__ q,
@@ -120,83 +222,13 @@ __global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double
         const double *Mx = q + (Q_M00 + 2 * dir) * g.P;
         const double *My = q + (Q_M01 + 2 * dir) * g.P;
         const long long c1 = c0 + sd;
-        const R half = (R)0.5, one = (R)1;
-        const R gam = (R)ph.gamma;
-        R nvx = (R)(0.5 * (Mx[c0] + Mx[c1]));
-        R nvy = (R)(0.5 * (My[c0] + My[c1]));
-        R jt = (R)(0.5 * (Mt[c0] + Mt[c1]));
-        R iLk = rsq<R>(nvx * nvx + nvy * nvy);
-        R Lk = (nvx * nvx + nvy * nvy) * iLk;
-        R nx = nvx * iLk, ny = nvy * iLk;
-        // interface state from the two-point flux averages:
-        // rho = {{rho}}^ln, u = {{u}}, p = {{rho}}/{{beta}}
-        R rho, irho;
-        logmean<R>(q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1], q[Q_LNR * g.P + c0], q[Q_LNR * g.P + c1],
-                   ph.ln_thr, rho, irho);
-        R ux = half * ((R)q[Q_UX * g.P + c0] + (R)q[Q_UX * g.P + c1]);
-        R uy = half * ((R)q[Q_UY * g.P + c0] + (R)q[Q_UY * g.P + c1]);
-        R p = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) *
-              rcp<R>((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
-        R iW = rsq<R>(one + ux * ux + uy * uy);
-        R W = (one + ux * ux + uy * uy) * iW;
-        R vx = ux * iW, vy = uy * iW;
-        R vn = nx * vx + ny * vy, vt = -ny * vx + nx * vy;
-        R dU[4][4], s[4], lm, lp;
-        eigen_rhd<R>(gam, rho, vn, vt, p, W, dU, s, lm, lp);
-        R lhat = fmax(fab<R>(jt + Lk * lm), fab<R>(jt + Lk * lp));
-
-        constexpr int NS = WW + 1;              // stencil nodes
-        constexpr int OFF = (WW - 1) / 2;       // nodes left of c0
-        const R ig = rcp<R>(gam - one), c1g = gam * ig;
-        R Vt[NS][4];
-        R aT[4] = {(R)0, (R)0, (R)0, (R)0};     // |T V| summed over the two interface nodes
+        QStencil<R> st{q, g.P, c0, sd, (WW - 1) / 2};
+        R diss[4];
+        es_dissipation<R, double, WW>((R)(0.5 * (Mx[c0] + Mx[c1])), (R)(0.5 * (My[c0] + My[c1])),
+                                      (R)(0.5 * (Mt[c0] + Mt[c1])), q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1],
+                                      q[Q_LNR * g.P + c0], q[Q_LNR * g.P + c1], st, ph, diss);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            const long long c = c0 + (k - OFF) * sd;
-            R b = (R)q[Q_BETA * g.P + c];
-            R V0 = c1g + (R)q[Q_LNR * g.P + c] + ig * (R)q[Q_LNB * g.P + c] + b;
-            R Vx = b * (R)q[Q_UX * g.P + c];
-            R Vy = b * (R)q[Q_UY * g.P + c];
-            R VE = -b * (R)q[Q_W * g.P + c];
-            R T1 = nx * Vx + ny * Vy, T2 = -ny * Vx + nx * Vy;
-            if (k == OFF || k == OFF + 1) {
-                aT[0] += fab<R>(V0); aT[1] += fab<R>(T1); aT[2] += fab<R>(T2); aT[3] += fab<R>(VE);
-            }
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                Vt[k][m] = s[m] * (dU[0][m] * V0 + dU[1][m] * T1 + dU[2][m] * T2 + dU[3][m] * VE);
-        }
-        const R eps = (R)ph.eps;
-        const R sign_tol = (R)ph.sign_tol;
-        R z[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            R vminus, vplus;
-            if (WW == 5) {
-                vminus = weno5<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
-                vplus = weno5<R>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
-            } else {
-                vminus = weno3<R>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
-                vplus = weno3<R>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
-            }
-            R jw = vplus - vminus;
-            R jump = Vt[OFF + 1][m] - Vt[OFF][m];
-            // a jump within sign_tol of the magnitudes forming V~_m at the two
-            // interface nodes is rounding noise: its sign is 0 (so Y = 0)
-            R scale = s[m] * (fab<R>(dU[0][m]) * aT[0] + fab<R>(dU[1][m]) * aT[1] +
-                              fab<R>(dU[2][m]) * aT[2] + fab<R>(dU[3][m]) * aT[3]);
-            int sj = fab<R>(jump) <= sign_tol * scale ? 0 : sgn_d(jump);
-            z[m] = (sgn_d(jw) == sj) ? jw * s[m] : (R)0;
-        }
-        R d[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-            d[a] = dU[a][0] * z[0] + dU[a][1] * z[1] + dU[a][2] * z[2] + dU[a][3] * z[3];
-        R hl = half * lhat;
-        F[0] -= hl * d[0];
-        F[1] -= hl * (nx * d[1] - ny * d[2]);
-        F[2] -= hl * (ny * d[1] + nx * d[2]);
-        F[3] -= hl * d[3];
+        for (int a = 0; a < 4; ++a) F[a] -= diss[a];
     }
     R *out = iflux + (long long)(dir * 5) * g.P + c0;
 #pragma unroll

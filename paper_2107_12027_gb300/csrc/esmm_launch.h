@@ -27,4 +27,21 @@ void launch_iface_f64(const LaunchDom &L, const Phys &ph, const double *q, const
 void launch_iface_f32(const LaunchDom &L, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
                       cudaStream_t st);
 
+// Adjoint (esmm_adjoint.cu): local Jacobian-vector products of the pair and
+// interface fluxes against the node adjoint mu ([4][N]) of d(cons)/dt, written
+// per (pair | interface, node, quantity); the node kernel gathers them and
+// adds (d rhs/d cons)^T mu into lam ([4][N], accumulated).
+void launch_pairs_vjp(const LaunchDom &L, const Phys &ph, const double *q, const double *mu, double *Gp, int dir,
+                      cudaStream_t st);
+void launch_iface_vjp(const LaunchDom &L, const Phys &ph, const double *q, const double *mu, double *G, int dir,
+                      cudaStream_t st);
+void launch_node_vjp(const LaunchDom &L, double gam, int p, int w, const double *q, const double *G,
+                     const double *Gp, const double *J, double *lam, cudaStream_t st);
+void launch_lincomb(long long n, double a, const double *x, double b, const double *y, double *out, cudaStream_t st);
+void launch_prim_grad(const LaunchDom &L, double gam, const double *cons, const double *J, const double *lam,
+                      double *out, cudaStream_t st);
+// sizes of the adjoint's contribution buffers, in doubles per padded node
+constexpr long long ADJ_G_PER_NODE = 2 * 6 * 7;
+constexpr long long ADJ_GP_PER_NODE = 2 * PMAX * 2 * 7;
+
 }  // namespace esmm

@@ -32,7 +32,8 @@ SYMBOLS = (
     "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
     "esmm_rhs_static", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
-    "esmm_batch_times", "esmm_batch_totals", "esmm_tune",
+    "esmm_batch_times", "esmm_batch_totals", "esmm_tune", "esmm_adjoint_record", "esmm_adjoint_steps",
+    "esmm_adjoint_checkpoint", "esmm_adjoint_replay", "esmm_adjoint_vjp", "esmm_rhs_vjp",
 )
 STATIC_MAX_PADDED_NODES = 68644
 KIND_NODE, KIND_PAIRS, KIND_IFACE, KIND_UPDATE, KIND_MESH, KIND_OTHER = range(6)
@@ -81,6 +82,9 @@ def lib():
             "esmm_batch_state_get": [vp, i, i, vp, i],
             "esmm_batch_times": [vp, dp], "esmm_batch_totals": [vp, dp],
             "esmm_tune": [vp, ctypes.POINTER(i)],
+            "esmm_adjoint_record": [vp, i, d], "esmm_adjoint_steps": [vp, ctypes.POINTER(i), dp],
+            "esmm_adjoint_checkpoint": [vp, i, i, vp, i], "esmm_adjoint_replay": [vp, i],
+            "esmm_adjoint_vjp": [vp, vp, vp, vp, i], "esmm_rhs_vjp": [vp, vp, vp, vp, vp, vp, vp, i],
             "esmm_profile_read": [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
         }
         for name, args in sig.items():
@@ -290,6 +294,55 @@ class Grid:
         t = (ctypes.c_longlong * 6)()
         self._check(lib().esmm_profile_read(self.h, ms, n, t))
         return {KINDS[k]: (ms[k], n[k], t[k]) for k in range(6)}
+
+    # -- adjoint ------------------------------------------------------------
+    def adjoint_record(self, nsteps, dt=0.0):
+        """Advance nsteps steps keeping per-step checkpoints for the adjoint."""
+        self._check(lib().esmm_adjoint_record(self.h, int(nsteps), float(dt)))
+
+    def adjoint_steps(self):
+        n = ctypes.c_int()
+        self._check(lib().esmm_adjoint_steps(self.h, ctypes.byref(n), None))
+        dts = (ctypes.c_double * max(n.value, 1))()
+        self._check(lib().esmm_adjoint_steps(self.h, ctypes.byref(n), dts))
+        return np.array(dts[:n.value])
+
+    def adjoint_checkpoint(self, step, what, out=None):
+        size = {GET_CONS: 4, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
+        if out is None:
+            out = np.empty((size, self.ny, self.nx) if size > 1 else (self.ny, self.nx))
+        po, mo = _ptr(out, size * self.N)
+        self._check(lib().esmm_adjoint_checkpoint(self.h, int(step), what, po, mo))
+        return out
+
+    def adjoint_replay(self, nsteps):
+        """Re-run the recorded map (recorded mesh velocities and steps) from
+        the current state."""
+        self._check(lib().esmm_adjoint_replay(self.h, int(nsteps)))
+
+    def adjoint_vjp(self, lam_final, lam_cons0=None, lam_prim0=None):
+        """dF/d(cons^0) and dF/d(prim^0) from lam_final = dF/d(cons^final)."""
+        host = not _is_torch(lam_final)
+        if host:
+            lam_cons0 = np.empty((4, self.ny, self.nx)) if lam_cons0 is None else lam_cons0
+            lam_prim0 = np.empty((4, self.ny, self.nx)) if lam_prim0 is None else lam_prim0
+        a = _ptr(lam_final, 4 * self.N)
+        c = _ptr(lam_cons0, 4 * self.N)
+        p_ = _ptr(lam_prim0, 4 * self.N)
+        mem = _mem(a, *([c] if lam_cons0 is not None else []), *([p_] if lam_prim0 is not None else []))
+        self._check(lib().esmm_adjoint_vjp(self.h, a[0], c[0], p_[0], mem))
+        return lam_cons0, lam_prim0
+
+    def rhs_vjp(self, cons, J, x, xdot, mu, lam=None):
+        """(d rhs / d cons)^T mu at (cons, J, x, xdot) with J, x, xdot fixed."""
+        if lam is None:
+            lam = np.empty((4, self.ny, self.nx))
+        a = [_ptr(cons, 4 * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N), _ptr(mu, 4 * self.N),
+             _ptr(lam, 4 * self.N)]
+        xd = _ptr(xdot, 2 * self.N)
+        mem = _mem(*a, *([xd] if xdot is not None else []))
+        self._check(lib().esmm_rhs_vjp(self.h, a[0][0], a[1][0], a[2][0], xd[0], a[3][0], a[4][0], mem))
+        return lam
 
     def tune(self):
         """Run the launch autotuner on the current state; returns the 7 chosen

@@ -232,3 +232,18 @@ def test_strong_shock_tube_stays_admissible(state):
     # reaches the boundaries by this time)
     assert t < 0.3
     assert abs(cons[0].sum() / oracle.init_state(cfg, prim, wl.uniform_mesh(n, ny, (0, 0), (1, 1), (False, True)))[0][0].sum() - 1) < 1e-12
+
+
+def test_rk_step_given_matches_rk_step_with_its_own_mesh_velocity():
+    # the step with given (xdot, dt) reproduces the full step when given the
+    # full step's own mesh velocity and dt
+    n = 20
+    x, prim = wl.sine_config(n)
+    cfg = oracle.make_cfg(n, n, monitor=oracle.MONITOR_RHO, alpha=20.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    dt = oracle.cfl_dt(cfg, cons, J, x)
+    xdot, _ = oracle.mesh(cfg, cons, J, x, dt)
+    a = oracle.rk_step(cfg, cons, J, x, dt)
+    b = oracle.rk_step_given(cfg, cons, J, x, xdot, dt)
+    for u, v in zip(a[:3], b):
+        np.testing.assert_array_equal(u, v)
