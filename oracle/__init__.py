@@ -1,9 +1,10 @@
-"""FP64 CPU oracle for the ES adaptive moving-mesh scheme (2D RHD).
+"""FP64 CPU oracle for the ES adaptive moving-mesh scheme (2D RHD and RMHD).
 
 TEST INFRASTRUCTURE.  This package is the independent checker of the CUDA
 library: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
 of ``bench.py`` may import it.  It shares no code with the CUDA path; the C
-source ``esmm_oracle.c`` restates the paper (Duan & Tang, arXiv 2107.12027)
+sources ``esmm_oracle.c`` (grid, mesh, RHD) and ``esmm_oracle_mhd.c``
+(pointwise RMHD) restate the paper (Duan & Tang, arXiv 2107.12027)
 one node, pair and interface at a time.
 
 Array conventions match the C header: structure of arrays, ``[comp][j][i]``
@@ -19,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "esmm_oracle.c")
+_SRCS = [os.path.join(_HERE, "esmm_oracle.c"), os.path.join(_HERE, "esmm_oracle_mhd.c")]
 _HDR = os.path.join(_HERE, "esmm_oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
@@ -27,6 +28,7 @@ _lib = None
 
 PERIODIC, OUTFLOW = 0, 1
 MONITOR_RHO, MONITOR_LNRHO = 0, 1
+RHD, RMHD = 0, 1
 
 
 class Cfg(ctypes.Structure):
@@ -43,19 +45,20 @@ class Cfg(ctypes.Structure):
         ("n_filter", ctypes.c_int),
         ("mu", ctypes.c_int),
         ("move_mesh", ctypes.c_int),
+        ("phys", ctypes.c_int),
     ]
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so``."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    newer = (os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
-             and os.path.getmtime(_LIB) >= os.path.getmtime(_HDR))
+    newer = (os.path.exists(_LIB)
+             and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS + [_HDR]))
     if force or not newer:
         tmp = _LIB + ".%d.tmp" % os.getpid()
         # -ffp-contract=off: every product and sum is rounded as written.
         cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -91,6 +94,15 @@ def lib():
                 "oref_init_state": (ctypes.c_int, [c, d, d, d, d]),
                 "oref_state_prim": (ctypes.c_int, [c, d, d, d]),
                 "oref_totals": (ctypes.c_int, [c, d, d, d, d, d]),
+                "oref_mhd_prim2cons": (None, [ctypes.c_double, d, d]),
+                "oref_mhd_flux": (None, [ctypes.c_double, d, ctypes.c_int, d]),
+                "oref_mhd_cons2prim": (ctypes.c_int, [ctypes.c_double, d, d, i]),
+                "oref_mhd_entropy": (ctypes.c_double, [ctypes.c_double, d]),
+                "oref_mhd_entropy_vars": (None, [ctypes.c_double, d, d]),
+                "oref_mhd_potentials": (None, [d, d, d, d]),
+                "oref_mhd_phiprime": (None, [d, d]),
+                "oref_mhd_ec_flux": (None, [ctypes.c_double, d, d, d, d]),
+                "oref_mhd_eigen": (None, [ctypes.c_double, d, d, d]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -116,14 +128,20 @@ def _vec(a, n=None):
 
 def make_cfg(nx, ny, bc=(PERIODIC, PERIODIC), period=(1.0, 1.0), gamma=5.0 / 3.0,
              p=2, w=5, weno_eps=1e-6, cfl=0.4, monitor=MONITOR_LNRHO, alpha=20.0,
-             n_filter=4, mu=10, move_mesh=1) -> Cfg:
+             n_filter=4, mu=10, move_mesh=1, phys=RHD) -> Cfg:
     c = Cfg()
     c.nx, c.ny = nx, ny
     c.bc[0], c.bc[1] = bc
     c.period[0], c.period[1] = period
     c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
     c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
+    c.phys = phys
     return c
+
+
+def nvar(cfg):
+    """Number of unknowns per node: 4 (RHD) or 8 (RMHD)."""
+    return 8 if cfg.phys == RMHD else 4
 
 
 # ---- pointwise functions ---------------------------------------------------
@@ -196,6 +214,7 @@ def weno(w, eps, s):
 # ---- grid functions --------------------------------------------------------
 def metrics(cfg, x):
     N = cfg.nx * cfg.ny
+    nv = nvar(cfg)
     x = _vec(x, 2 * N)
     m = np.zeros(4 * N)
     J0 = np.zeros(N)
@@ -205,35 +224,39 @@ def metrics(cfg, x):
 
 def init_state(cfg, prim, x):
     N = cfg.nx * cfg.ny
-    prim, x = _vec(prim, 4 * N), _vec(x, 2 * N)
-    cons, J = np.zeros(4 * N), np.zeros(N)
+    nv = nvar(cfg)
+    prim, x = _vec(prim, nv * N), _vec(x, 2 * N)
+    cons, J = np.zeros(nv * N), np.zeros(N)
     lib().oref_init_state(ctypes.byref(cfg), _p(prim), _p(x), _p(cons), _p(J))
-    return cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx)
+    return cons.reshape(nv, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx)
 
 
 def state_prim(cfg, cons, J):
     N = cfg.nx * cfg.ny
-    prim = np.zeros(4 * N)
-    st = lib().oref_state_prim(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)), _p(prim))
-    return prim.reshape(4, cfg.ny, cfg.nx), st
+    nv = nvar(cfg)
+    prim = np.zeros(nv * N)
+    st = lib().oref_state_prim(ctypes.byref(cfg), _p(_vec(cons, nv * N)), _p(_vec(J, N)), _p(prim))
+    return prim.reshape(nv, cfg.ny, cfg.nx), st
 
 
 def rhs(cfg, cons, J, x, xdot=None):
     N = cfg.nx * cfg.ny
+    nv = nvar(cfg)
     if xdot is None:
         xdot = np.zeros(2 * N)
-    dcons, dJ = np.zeros(4 * N), np.zeros(N)
-    st = lib().oref_rhs(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)),
+    dcons, dJ = np.zeros(nv * N), np.zeros(N)
+    st = lib().oref_rhs(ctypes.byref(cfg), _p(_vec(cons, nv * N)), _p(_vec(J, N)),
                         _p(_vec(x, 2 * N)), _p(_vec(xdot, 2 * N)), _p(dcons), _p(dJ))
     if st != 0:
         raise RuntimeError("oracle rhs: cons2prim failed")
-    return dcons.reshape(4, cfg.ny, cfg.nx), dJ.reshape(cfg.ny, cfg.nx)
+    return dcons.reshape(nv, cfg.ny, cfg.nx), dJ.reshape(cfg.ny, cfg.nx)
 
 
 def cfl_dt(cfg, cons, J, x):
     N = cfg.nx * cfg.ny
+    nv = nvar(cfg)
     dt = np.zeros(1)
-    st = lib().oref_cfl_dt(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)),
+    st = lib().oref_cfl_dt(ctypes.byref(cfg), _p(_vec(cons, nv * N)), _p(_vec(J, N)),
                            _p(_vec(x, 2 * N)), _p(dt))
     if st != 0:
         raise RuntimeError("oracle cfl: cons2prim failed")
@@ -242,9 +265,10 @@ def cfl_dt(cfg, cons, J, x):
 
 def mesh(cfg, cons, J, x, dt):
     N = cfg.nx * cfg.ny
+    nv = nvar(cfg)
     xdot = np.zeros(2 * N)
     tau = np.zeros(1)
-    st = lib().oref_mesh(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)),
+    st = lib().oref_mesh(ctypes.byref(cfg), _p(_vec(cons, nv * N)), _p(_vec(J, N)),
                          _p(_vec(x, 2 * N)), float(dt), _p(xdot), _p(tau))
     if st != 0:
         raise RuntimeError("oracle mesh: cons2prim failed")
@@ -254,34 +278,93 @@ def mesh(cfg, cons, J, x, dt):
 def rk_step(cfg, cons, J, x, dt=0.0):
     """One SSP-RK3 step; returns new (cons, J, x, dt_used)."""
     N = cfg.nx * cfg.ny
-    cons = _vec(cons, 4 * N).copy()
+    nv = nvar(cfg)
+    cons = _vec(cons, nv * N).copy()
     J = _vec(J, N).copy()
     x = _vec(x, 2 * N).copy()
     dtu = np.zeros(1)
     st = lib().oref_rk_step(ctypes.byref(cfg), _p(cons), _p(J), _p(x), float(dt), _p(dtu))
     if st != 0:
         raise RuntimeError("oracle rk_step: cons2prim failed")
-    return (cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx),
+    return (cons.reshape(nv, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx),
             x.reshape(2, cfg.ny, cfg.nx), dtu[0])
 
 
 def rk_step_given(cfg, cons, J, x, xdot, dt):
     """One SSP-RK3 step with a given mesh velocity and step."""
     N = cfg.nx * cfg.ny
-    cons = _vec(cons, 4 * N).copy()
+    nv = nvar(cfg)
+    cons = _vec(cons, nv * N).copy()
     J = _vec(J, N).copy()
     x = _vec(x, 2 * N).copy()
     st = lib().oref_rk_step_given(ctypes.byref(cfg), _p(cons), _p(J), _p(x), _p(_vec(xdot, 2 * N)), float(dt))
     if st != 0:
         raise RuntimeError("oracle rk_step_given: cons2prim failed")
-    return cons.reshape(4, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx), x.reshape(2, cfg.ny, cfg.nx)
+    return cons.reshape(nv, cfg.ny, cfg.nx), J.reshape(cfg.ny, cfg.nx), x.reshape(2, cfg.ny, cfg.nx)
 
 
 def totals(cfg, cons, J, dcons=None, dJ=None):
     N = cfg.nx * cfg.ny
+    nv = nvar(cfg)
     out = np.zeros(4)
-    dc = _vec(dcons, 4 * N) if dcons is not None else None
+    dc = _vec(dcons, nv * N) if dcons is not None else None
     dj = _vec(dJ, N) if dJ is not None else None
-    lib().oref_totals(ctypes.byref(cfg), _p(_vec(cons, 4 * N)), _p(_vec(J, N)), _p(dc), _p(dj),
+    lib().oref_totals(ctypes.byref(cfg), _p(_vec(cons, nv * N)), _p(_vec(J, N)), _p(dc), _p(dj),
                       _p(out))
     return out
+
+
+# ---- RMHD pointwise functions (8-component states) ---------------------------
+def mhd_prim2cons(gamma, w):
+    U = np.zeros(8)
+    lib().oref_mhd_prim2cons(gamma, _p(_vec(w, 8)), _p(U))
+    return U
+
+
+def mhd_cons2prim(gamma, U):
+    w = np.zeros(8)
+    it = ctypes.c_int(0)
+    st = lib().oref_mhd_cons2prim(gamma, _p(_vec(U, 8)), _p(w), ctypes.byref(it))
+    return w, st, it.value
+
+
+def mhd_flux(gamma, w, direction):
+    F = np.zeros(8)
+    lib().oref_mhd_flux(gamma, _p(_vec(w, 8)), direction, _p(F))
+    return F
+
+
+def mhd_entropy(gamma, w):
+    return lib().oref_mhd_entropy(gamma, _p(_vec(w, 8)))
+
+
+def mhd_entropy_vars(gamma, w):
+    V = np.zeros(8)
+    lib().oref_mhd_entropy_vars(gamma, _p(_vec(w, 8)), _p(V))
+    return V
+
+
+def mhd_potentials(w):
+    """(phi, psi[3], Phi)."""
+    phi, psi, Phi = np.zeros(1), np.zeros(3), np.zeros(1)
+    lib().oref_mhd_potentials(_p(_vec(w, 8)), _p(phi), _p(psi), _p(Phi))
+    return phi[0], psi, Phi[0]
+
+
+def mhd_phiprime(w):
+    P = np.zeros(8)
+    lib().oref_mhd_phiprime(_p(_vec(w, 8)), _p(P))
+    return P
+
+
+def mhd_ec_flux(gamma, wl, wr):
+    """(U~[8], F~[3][8])."""
+    Ut, Ft = np.zeros(8), np.zeros(24)
+    lib().oref_mhd_ec_flux(gamma, _p(_vec(wl, 8)), _p(_vec(wr, 8)), _p(Ut), _p(Ft))
+    return Ut, Ft.reshape(3, 8)
+
+
+def mhd_eigen(gamma, w_rot):
+    lam, R = np.zeros(8), np.zeros(64)
+    lib().oref_mhd_eigen(gamma, _p(_vec(w_rot, 8)), _p(lam), _p(R))
+    return lam, R.reshape(8, 8)

@@ -36,7 +36,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NV 4   /* 2D RHD: (D, m_x, m_y, E) */
+#define NV 4   /* 2D RHD: (D, m_x, m_y, E); RMHD states (8) in esmm_oracle_mhd.c */
 #define G 3    /* ghost layers of the node data: WENO5 and p <= 3 pairs */
 #define OREF_SIGN_TOL 1.0e-10
 
@@ -464,11 +464,45 @@ void oref_metrics(const oref_cfg *c, const double *x, double *m, double *J0)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Physics switch: the RHD and RMHD pointwise parts behind one interface.
+ * RHD states have 4 components (pressure at index 3), RMHD states 8
+ * (pressure at index 4, B at 5..7).                                        */
+#define NVMAX 8
+static int nvar(const oref_cfg *c) { return c->phys == OREF_RMHD ? 8 : 4; }
+
+static int c2p(const oref_cfg *c, const double *U, double *w)
+{
+    return c->phys == OREF_RMHD ? oref_mhd_cons2prim(c->gamma, U, w, NULL)
+                                : oref_cons2prim(c->gamma, U, w, NULL);
+}
+
+static void p2c(const oref_cfg *c, const double *w, double *U)
+{
+    if (c->phys == OREF_RMHD) oref_mhd_prim2cons(c->gamma, w, U);
+    else oref_prim2cons(c->gamma, w, U);
+}
+
+static void entropy_vars(const oref_cfg *c, const double *w, double *V)
+{
+    if (c->phys == OREF_RMHD) oref_mhd_entropy_vars(c->gamma, w, V);
+    else oref_entropy_vars(c->gamma, w, V);
+}
+
+/* Primitive state of node (conservative cons[nv][N] / J). */
+static int node_prim(const oref_cfg *c, const double *cons, const double *J, int id, double *w)
+{
+    int N = c->nx * c->ny, nv = nvar(c);
+    double U[NVMAX];
+    for (int a = 0; a < nv; ++a) U[a] = cons[(size_t)a * N + id] / J[id];
+    return c2p(c, U, w);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Padded node data used by one right-hand-side evaluation. */
 typedef struct {
     const oref_cfg *c;
     int px, py;              /* padded extents nx + 2G, ny + 2G */
-    double *prim;            /* [4][P] */
+    double *prim;            /* [nv][P] */
     double *M;               /* [4][P]: M00 M01 M10 M11 */
     double *Mt;              /* [2][P]: J xi_t, J eta_t */
 } oref_pad;
@@ -477,8 +511,8 @@ static int pad_index(const oref_pad *P, int i, int j) { return (j + G) * P->px +
 
 static void pad_prim(const oref_pad *P, int i, int j, double *w)
 {
-    int id = pad_index(P, i, j), S = P->px * P->py;
-    for (int a = 0; a < 4; ++a) w[a] = P->prim[a * S + id];
+    int id = pad_index(P, i, j), S = P->px * P->py, nv = nvar(P->c);
+    for (int a = 0; a < nv; ++a) w[a] = P->prim[a * S + id];
 }
 
 static void pad_M(const oref_pad *P, int i, int j, double M[2][2], double Mt[2])
@@ -495,27 +529,26 @@ static void pad_M(const oref_pad *P, int i, int j, double M[2][2], double Mt[2])
 static int build_pad(const oref_cfg *c, const double *cons, const double *J,
                      const double *x, const double *xdot, oref_pad *P)
 {
-    int nx = c->nx, ny = c->ny, N = nx * ny;
+    int nx = c->nx, ny = c->ny, N = nx * ny, nv = nvar(c);
     P->c = c;
     P->px = nx + 2 * G;
     P->py = ny + 2 * G;
     int S = P->px * P->py;
-    P->prim = (double *)malloc(sizeof(double) * 4 * S);
+    P->prim = (double *)malloc(sizeof(double) * nv * S);
     P->M = (double *)malloc(sizeof(double) * 4 * S);
     P->Mt = (double *)malloc(sizeof(double) * 2 * S);
-    double *w = (double *)malloc(sizeof(double) * 4 * N);
+    double *w = (double *)malloc(sizeof(double) * nv * N);
     int status = 0;
     /* cons2prim at every node: U = (J U)/J */
     for (int id = 0; id < N; ++id) {
-        double U[4], wi[4];
-        for (int a = 0; a < 4; ++a) U[a] = cons[a * N + id] / J[id];
-        if (oref_cons2prim(c->gamma, U, wi, NULL) != 0) status = -1;
-        for (int a = 0; a < 4; ++a) w[a * N + id] = wi[a];
+        double wi[NVMAX];
+        if (node_prim(c, cons, J, id, wi) != 0) status = -1;
+        for (int a = 0; a < nv; ++a) w[a * N + id] = wi[a];
     }
     for (int j = -G; j < ny + G; ++j)
         for (int i = -G; i < nx + G; ++i) {
             int id = pad_index(P, i, j), src = data_index(c, i, j);
-            for (int a = 0; a < 4; ++a) P->prim[a * S + id] = w[a * N + src];
+            for (int a = 0; a < nv; ++a) P->prim[a * S + id] = w[a * N + src];
             double M[2][2];
             node_metrics(c, x, i, j, M);
             P->M[0 * S + id] = M[0][0];
@@ -541,46 +574,109 @@ static void free_pad(oref_pad *P)
 
 static int sgn(double a) { return (a > 0.0) - (a < 0.0); }
 
+/* Rotation T (Sec. 4): T = diag(1, T_0, 1) for RHD and diag(1, T_0, 1, T_0)
+ * for RMHD, T_0 with rows n, t (and e_3 for the 3-vectors of RMHD).  In 2D
+ * the metric vector has no x_3 part, so varphi = 0 and t = (-n_y, n_x).   */
+static void rotate(const oref_cfg *c, double nx_, double ny_, const double *a, double *r)
+{
+    if (c->phys == OREF_RMHD) {
+        r[0] = a[0];
+        r[1] = nx_ * a[1] + ny_ * a[2];
+        r[2] = -ny_ * a[1] + nx_ * a[2];
+        r[3] = a[3];
+        r[4] = a[4];
+        r[5] = nx_ * a[5] + ny_ * a[6];
+        r[6] = -ny_ * a[5] + nx_ * a[6];
+        r[7] = a[7];
+    } else {
+        r[0] = a[0];
+        r[1] = nx_ * a[1] + ny_ * a[2];
+        r[2] = -ny_ * a[1] + nx_ * a[2];
+        r[3] = a[3];
+    }
+}
+
+static void unrotate(const oref_cfg *c, double nx_, double ny_, const double *r, double *a)
+{
+    if (c->phys == OREF_RMHD) {
+        a[0] = r[0];
+        a[1] = nx_ * r[1] - ny_ * r[2];
+        a[2] = ny_ * r[1] + nx_ * r[2];
+        a[3] = r[3];
+        a[4] = r[4];
+        a[5] = nx_ * r[5] - ny_ * r[6];
+        a[6] = ny_ * r[5] + nx_ * r[6];
+        a[7] = r[7];
+    } else {
+        a[0] = r[0];
+        a[1] = nx_ * r[1] - ny_ * r[2];
+        a[2] = ny_ * r[1] + nx_ * r[2];
+        a[3] = r[3];
+    }
+}
+
+/* Eigen-system in the rotated frame (Sec. 4). */
+static void eigen(const oref_cfg *c, const double *wrot, double *lam, double *R)
+{
+    if (c->phys == OREF_RMHD) oref_mhd_eigen(c->gamma, wrot, lam, R);
+    else oref_eigen(c->gamma, wrot, lam, R);
+}
+
 /* The w-th order ES flux at the interface between node (i, j) and its
  * neighbour in direction k (eq. ESFlux_HO), written to F; the 2p-th order
- * temporal-metric flux (eq. MetricsFlux_O2p) to Ft.                         */
-static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, double *Ft)
+ * temporal-metric flux (eq. MetricsFlux_O2p) to Ft and, for RMHD, the 2p-th
+ * order magnetic flux B~ (eqs. BFlux_O2p, BFlux_O2) to Bt.                  */
+static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, double *Ft,
+                           double *Bt)
 {
     const oref_cfg *c = P->c;
+    int nv = nvar(c), mhd = (c->phys == OREF_RMHD);
     int di = (k == 0), dj = (k == 1);
     double alpha[3];
     oref_alpha(c->p, alpha);
-    for (int a = 0; a < 4; ++a) F[a] = 0.0;
+    for (int a = 0; a < nv; ++a) F[a] = 0.0;
     *Ft = 0.0;
+    *Bt = 0.0;
 
     /* eq. ECFlux_O2p: sum_n alpha_{p,n} sum_{s=0}^{n-1} F~_k(U_{i-s}, U_{i-s+n}) */
     for (int n = 1; n <= c->p; ++n) {
-        double Fs[4] = {0.0, 0.0, 0.0, 0.0}, Fts = 0.0;
+        double Fs[NVMAX], Fts = 0.0, Bts = 0.0;
+        for (int a = 0; a < nv; ++a) Fs[a] = 0.0;
         for (int s = 0; s < n; ++s) {
             int il = i - s * di, jl = j - s * dj;
             int ir = i + (n - s) * di, jr = j + (n - s) * dj;
-            double wl[4], wr[4], Ml[2][2], Mr[2][2], Mtl[2], Mtr[2];
+            double wl[NVMAX], wr[NVMAX], Ml[2][2], Mr[2][2], Mtl[2], Mtr[2];
             pad_prim(P, il, jl, wl);
             pad_prim(P, ir, jr, wr);
             pad_M(P, il, jl, Ml, Mtl);
             pad_M(P, ir, jr, Mr, Mtr);
-            double Ut[4], F1t[4], F2t[4];
-            oref_ec_flux(c->gamma, wl, wr, Ut, F1t, F2t);
             /* eq. ECFluxCurv / UFcircle: averaged metrics times U~, F~_j */
             double mt = 0.5 * (Mtl[k] + Mtr[k]);
             double mx = 0.5 * (Ml[k][0] + Mr[k][0]);
             double my = 0.5 * (Ml[k][1] + Mr[k][1]);
-            for (int a = 0; a < 4; ++a) Fs[a] += mt * Ut[a] + mx * F1t[a] + my * F2t[a];
+            if (mhd) {
+                double Ut[8], Ftj[24];
+                oref_mhd_ec_flux(c->gamma, wl, wr, Ut, Ftj);
+                for (int a = 0; a < 8; ++a) Fs[a] += mt * Ut[a] + mx * Ftj[a] + my * Ftj[8 + a];
+                /* eq. BFlux_O2: sum_j 1/4 (M_l + M_r)(B_j,l + B_j,r) */
+                Bts += 0.25 * (Ml[k][0] + Mr[k][0]) * (wl[5] + wr[5])
+                     + 0.25 * (Ml[k][1] + Mr[k][1]) * (wl[6] + wr[6]);
+            } else {
+                double Ut[4], F1t[4], F2t[4];
+                oref_ec_flux(c->gamma, wl, wr, Ut, F1t, F2t);
+                for (int a = 0; a < 4; ++a) Fs[a] += mt * Ut[a] + mx * F1t[a] + my * F2t[a];
+            }
             /* eq. MetricsFlux_O2 */
             Fts += 0.5 * (Mtl[k] + Mtr[k]);
         }
-        for (int a = 0; a < 4; ++a) F[a] += alpha[n - 1] * Fs[a];
+        for (int a = 0; a < nv; ++a) F[a] += alpha[n - 1] * Fs[a];
         *Ft += alpha[n - 1] * Fts;
+        *Bt += alpha[n - 1] * Bts;
     }
     if (c->w == 0) return;
 
     /* eq. ESFlux_HO: F^ = F~ - 1/2 D Y <<V~>>, D = lambda^ T^{-1} R(TU). */
-    double wL[4], wR[4], ML[2][2], MR[2][2], MtL[2], MtR[2];
+    double wL[NVMAX], wR[NVMAX], ML[2][2], MR[2][2], MtL[2], MtR[2];
     pad_prim(P, i, j, wL);
     pad_prim(P, i + di, j + dj, wR);
     pad_M(P, i, j, ML, MtL);
@@ -593,49 +689,63 @@ static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, do
     /* T_0 rows: the unit normal n (theta is read as the angle of the metric
      * vector, so that the first row is n) and the tangent t = (-n_y, n_x). */
     double nx_ = nvx / Lk, ny_ = nvy / Lk;
-    double tx_ = -ny_, ty_ = nx_;
     /* Reading: D is evaluated at the interface state built from the averages
      * of the two-point EC flux: rho = {{rho}}^ln, u = {{u}} (u = W v) and
-     * p = {{rho}}/{{beta}} (beta = rho/p).  (With the arithmetic mean of
-     * (rho, u, p) the dissipation R R^T [[V]] turns anti-diffusive when beta
-     * jumps by two orders of magnitude across an interface.) */
-    double WL = 1.0 / sqrt(1.0 - (wL[1] * wL[1] + wL[2] * wL[2]));
-    double WR = 1.0 / sqrt(1.0 - (wR[1] * wR[1] + wR[2] * wR[2]));
-    double rho_m = oref_logmean(wL[0], wR[0]);
-    double ux_m = 0.5 * (WL * wL[1] + WR * wR[1]);
-    double uy_m = 0.5 * (WL * wL[2] + WR * wR[2]);
-    double p_m = (0.5 * (wL[0] + wR[0])) / (0.5 * (wL[0] / wL[3] + wR[0] / wR[3]));
-    double W_m = sqrt(1.0 + ux_m * ux_m + uy_m * uy_m);
-    double vx_m = ux_m / W_m, vy_m = uy_m / W_m;
-    double wrot[4] = {rho_m, nx_ * vx_m + ny_ * vy_m, tx_ * vx_m + ty_ * vy_m, p_m};
-    double lam[4], R[16];
-    oref_eigen(c->gamma, wrot, lam, R);
+     * p = {{rho}}/{{beta}} (beta = rho/p); for RMHD also B = {{B}}.  (With the
+     * arithmetic mean of (rho, u, p) the dissipation R R^T [[V]] turns
+     * anti-diffusive when beta jumps by two orders of magnitude across an
+     * interface.) */
+    double wm[NVMAX], wrot[NVMAX];
+    {
+        int nvel = mhd ? 3 : 2, ip = mhd ? 4 : 3;
+        double v2L = 0.0, v2R = 0.0;
+        for (int q = 0; q < nvel; ++q) {
+            v2L += wL[1 + q] * wL[1 + q];
+            v2R += wR[1 + q] * wR[1 + q];
+        }
+        double WL = 1.0 / sqrt(1.0 - v2L), WR = 1.0 / sqrt(1.0 - v2R);
+        double um[3], W2_m = 1.0;
+        for (int q = 0; q < nvel; ++q) {
+            um[q] = 0.5 * (WL * wL[1 + q] + WR * wR[1 + q]);
+            W2_m += um[q] * um[q];
+        }
+        double W_m = sqrt(W2_m);
+        wm[0] = oref_logmean(wL[0], wR[0]);
+        for (int q = 0; q < nvel; ++q) wm[1 + q] = um[q] / W_m;
+        wm[ip] = (0.5 * (wL[0] + wR[0])) / (0.5 * (wL[0] / wL[ip] + wR[0] / wR[ip]));
+        if (mhd)
+            for (int q = 5; q < 8; ++q) wm[q] = 0.5 * (wL[q] + wR[q]);
+    }
+    rotate(c, nx_, ny_, wm, wrot);
+    double lam[NVMAX], R[NVMAX * NVMAX];
+    eigen(c, wrot, lam, R);
     /* lambda^ = max_m |J xi_t + L_k lambda_m(TU)| */
     double lhat = 0.0;
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < nv; ++m) {
         double a = fabs(jt + Lk * lam[m]);
         if (a > lhat) lhat = a;
     }
     /* scaled entropy variables V~ = R^T T V on the stencil nodes */
     int lo = (c->w == 5) ? -2 : -1, hi = (c->w == 5) ? 3 : 2;
-    double Vt[6][4];
-    double scale[4] = {0.0, 0.0, 0.0, 0.0};   /* magnitudes forming V~ at nodes 0, 1 */
+    double Vt[6][NVMAX];
+    double scale[NVMAX];   /* magnitudes forming V~ at nodes 0, 1 */
+    for (int m = 0; m < nv; ++m) scale[m] = 0.0;
     for (int q = lo; q <= hi; ++q) {
-        double wq[4], V[4];
+        double wq[NVMAX], V[NVMAX], TV[NVMAX];
         pad_prim(P, i + q * di, j + q * dj, wq);
-        oref_entropy_vars(c->gamma, wq, V);
-        double TV[4] = {V[0], nx_ * V[1] + ny_ * V[2], tx_ * V[1] + ty_ * V[2], V[3]};
-        for (int m = 0; m < 4; ++m) {
+        entropy_vars(c, wq, V);
+        rotate(c, nx_, ny_, V, TV);
+        for (int m = 0; m < nv; ++m) {
             double acc = 0.0;
-            for (int a = 0; a < 4; ++a) {
-                acc += R[a * 4 + m] * TV[a];
-                if (q == 0 || q == 1) scale[m] += fabs(R[a * 4 + m] * TV[a]);
+            for (int a = 0; a < nv; ++a) {
+                acc += R[a * nv + m] * TV[a];
+                if (q == 0 || q == 1) scale[m] += fabs(R[a * nv + m] * TV[a]);
             }
             Vt[q - lo][m] = acc;
         }
     }
-    double z[4];
-    for (int m = 0; m < 4; ++m) {
+    double z[NVMAX];
+    for (int m = 0; m < nv; ++m) {
         double sl[5], sr[5];
         int nw = c->w;
         for (int q = 0; q < nw; ++q) {
@@ -653,41 +763,48 @@ static void interface_flux(const oref_pad *P, int k, int i, int j, double *F, do
         double Y = (sgn(jw) == sj) ? 1.0 : 0.0;
         z[m] = Y * jw;
     }
-    double d[4];
-    for (int a = 0; a < 4; ++a) {
+    double d[NVMAX], dr[NVMAX];
+    for (int a = 0; a < nv; ++a) {
         double acc = 0.0;
-        for (int m = 0; m < 4; ++m) acc += R[a * 4 + m] * z[m];
+        for (int m = 0; m < nv; ++m) acc += R[a * nv + m] * z[m];
         d[a] = acc;
     }
-    /* T^{-1} = T^T: rotate the momentum part back */
-    double dmx = nx_ * d[1] + tx_ * d[2];
-    double dmy = ny_ * d[1] + ty_ * d[2];
-    F[0] -= 0.5 * lhat * d[0];
-    F[1] -= 0.5 * lhat * dmx;
-    F[2] -= 0.5 * lhat * dmy;
-    F[3] -= 0.5 * lhat * d[3];
+    /* T^{-1} = T^T: rotate the vector parts back */
+    unrotate(c, nx_, ny_, d, dr);
+    for (int a = 0; a < nv; ++a) F[a] -= 0.5 * lhat * dr[a];
 }
 
 int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
              const double *x, const double *xdot, double *dcons, double *dJ)
 {
-    int nx = c->nx, ny = c->ny, N = nx * ny;
+    int nx = c->nx, ny = c->ny, N = nx * ny, nv = nvar(c);
     oref_pad P;
     int status = build_pad(c, cons, J, x, xdot, &P);
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < nv; ++a)
         for (int id = 0; id < N; ++id) dcons[a * N + id] = 0.0;
     for (int id = 0; id < N; ++id) dJ[id] = 0.0;
-    /* eqs. RMHDSemiU_O2p_ES and RMHDSemiJ_O2p_ES (Delta xi_k = 1, B = 0) */
-    for (int k = 0; k < 2; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                int id = j * nx + i;
-                double Fp[4], Fm[4], Ftp, Ftm;
-                interface_flux(&P, k, i, j, Fp, &Ftp);
-                interface_flux(&P, k, i - (k == 0), j - (k == 1), Fm, &Ftm);
-                for (int a = 0; a < 4; ++a) dcons[a * N + id] -= Fp[a] - Fm[a];
+    /* eqs. RMHDSemiU_O2p_ES and RMHDSemiJ_O2p_ES (Delta xi_k = 1):
+     * flux differences, and for RMHD the Godunov-Powell source
+     * -Phi'(V_i)^T sum_k (B~_{i+1/2} - B~_{i-1/2}). */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int id = j * nx + i;
+            double divB = 0.0;
+            for (int k = 0; k < 2; ++k) {
+                double Fp[NVMAX], Fm[NVMAX], Ftp, Ftm, Btp, Btm;
+                interface_flux(&P, k, i, j, Fp, &Ftp, &Btp);
+                interface_flux(&P, k, i - (k == 0), j - (k == 1), Fm, &Ftm, &Btm);
+                for (int a = 0; a < nv; ++a) dcons[a * N + id] -= Fp[a] - Fm[a];
                 dJ[id] -= Ftp - Ftm;
+                divB += Btp - Btm;
             }
+            if (c->phys == OREF_RMHD) {
+                double w[8], Pp[8];
+                pad_prim(&P, i, j, w);
+                oref_mhd_phiprime(w, Pp);
+                for (int a = 0; a < 8; ++a) dcons[a * N + id] -= Pp[a] * divB;
+            }
+        }
     free_pad(&P);
     return status;
 }
@@ -695,12 +812,11 @@ int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
 /* ------------------------------------------------------------------------ */
 int oref_state_prim(const oref_cfg *c, const double *cons, const double *J, double *prim)
 {
-    int N = c->nx * c->ny, status = 0;
+    int N = c->nx * c->ny, nv = nvar(c), status = 0;
     for (int id = 0; id < N; ++id) {
-        double U[4], w[4];
-        for (int a = 0; a < 4; ++a) U[a] = cons[a * N + id] / J[id];
-        if (oref_cons2prim(c->gamma, U, w, NULL) != 0) status = -1;
-        for (int a = 0; a < 4; ++a) prim[a * N + id] = w[a];
+        double w[NVMAX];
+        if (node_prim(c, cons, J, id, w) != 0) status = -1;
+        for (int a = 0; a < nv; ++a) prim[a * N + id] = w[a];
     }
     return status;
 }
@@ -708,15 +824,15 @@ int oref_state_prim(const oref_cfg *c, const double *cons, const double *J, doub
 int oref_init_state(const oref_cfg *c, const double *prim, const double *x,
                     double *cons, double *J)
 {
-    int N = c->nx * c->ny;
+    int N = c->nx * c->ny, nv = nvar(c);
     double *m = (double *)malloc(sizeof(double) * 4 * N);
     oref_metrics(c, x, m, J);
     free(m);
     for (int id = 0; id < N; ++id) {
-        double w[4], U[4];
-        for (int a = 0; a < 4; ++a) w[a] = prim[a * N + id];
-        oref_prim2cons(c->gamma, w, U);
-        for (int a = 0; a < 4; ++a) cons[a * N + id] = J[id] * U[a];
+        double w[NVMAX], U[NVMAX];
+        for (int a = 0; a < nv; ++a) w[a] = prim[a * N + id];
+        p2c(c, w, U);
+        for (int a = 0; a < nv; ++a) cons[a * N + id] = J[id] * U[a];
     }
     return 0;
 }
@@ -728,23 +844,22 @@ int oref_init_state(const oref_cfg *c, const double *prim, const double *x,
 int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
                 const double *x, double *dt)
 {
-    int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
+    int nx = c->nx, ny = c->ny, nv = nvar(c), status = 0;
     double rmax[2] = {0.0, 0.0};
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int id = j * nx + i;
-            double U[4], w[4], M[2][2];
-            for (int a = 0; a < 4; ++a) U[a] = cons[a * N + id] / J[id];
-            if (oref_cons2prim(c->gamma, U, w, NULL) != 0) status = -1;
+            double w[NVMAX], M[2][2];
+            if (node_prim(c, cons, J, id, w) != 0) status = -1;
             node_metrics(c, x, i, j, M);
             for (int k = 0; k < 2; ++k) {
                 double Lk = sqrt(M[k][0] * M[k][0] + M[k][1] * M[k][1]);
                 double nx_ = M[k][0] / Lk, ny_ = M[k][1] / Lk;
-                double wr[4] = {w[0], nx_ * w[1] + ny_ * w[2], -ny_ * w[1] + nx_ * w[2], w[3]};
-                double lam[4], R[16];
-                oref_eigen(c->gamma, wr, lam, R);
+                double wr[NVMAX], lam[NVMAX], R[NVMAX * NVMAX];
+                rotate(c, nx_, ny_, w, wr);
+                eigen(c, wr, lam, R);
                 double a = 0.0;
-                for (int m = 0; m < 4; ++m)
+                for (int m = 0; m < nv; ++m)
                     if (fabs(lam[m]) > a) a = fabs(lam[m]);
                 double r = Lk * a / J[id];
                 if (r > rmax[k]) rmax[k] = r;
@@ -782,9 +897,8 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
     double *X = (double *)malloc(sizeof(double) * 2 * N);
     double *Xn = (double *)malloc(sizeof(double) * 2 * N);
     for (int id = 0; id < N; ++id) {
-        double U[4], w[4];
-        for (int a = 0; a < 4; ++a) U[a] = cons[a * N + id] / J[id];
-        if (oref_cons2prim(c->gamma, U, w, NULL) != 0) status = -1;
+        double w[NVMAX];
+        if (node_prim(c, cons, J, id, w) != 0) status = -1;
         sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
     }
     double gmax = 0.0;
@@ -873,32 +987,32 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
 int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
                  double dt, double *dt_used)
 {
-    int N = c->nx * c->ny, status = 0;
+    int N = c->nx * c->ny, nv = nvar(c), status = 0;
     if (!(dt > 0.0)) status |= oref_cfl_dt(c, cons, J, x, &dt);
     double *xdot = (double *)calloc(2 * (size_t)N, sizeof(double));
-    double *c1 = (double *)malloc(sizeof(double) * 4 * N);
-    double *c2 = (double *)malloc(sizeof(double) * 4 * N);
+    double *c1 = (double *)malloc(sizeof(double) * nv * N);
+    double *c2 = (double *)malloc(sizeof(double) * nv * N);
     double *J1 = (double *)malloc(sizeof(double) * N);
     double *J2 = (double *)malloc(sizeof(double) * N);
     double *x1 = (double *)malloc(sizeof(double) * 2 * N);
     double *x2 = (double *)malloc(sizeof(double) * 2 * N);
-    double *L = (double *)malloc(sizeof(double) * 4 * N);
+    double *L = (double *)malloc(sizeof(double) * nv * N);
     double *LJ = (double *)malloc(sizeof(double) * N);
     double dtau = 0.0;
     status |= oref_mesh(c, cons, J, x, dt, xdot, &dtau);
 
     status |= oref_rhs(c, cons, J, x, xdot, L, LJ);
-    for (int a = 0; a < 4 * N; ++a) c1[a] = cons[a] + dt * L[a];
+    for (int a = 0; a < nv * N; ++a) c1[a] = cons[a] + dt * L[a];
     for (int a = 0; a < N; ++a) J1[a] = J[a] + dt * LJ[a];
     for (int a = 0; a < 2 * N; ++a) x1[a] = x[a] + dt * xdot[a];
 
     status |= oref_rhs(c, c1, J1, x1, xdot, L, LJ);
-    for (int a = 0; a < 4 * N; ++a) c2[a] = 0.75 * cons[a] + 0.25 * (c1[a] + dt * L[a]);
+    for (int a = 0; a < nv * N; ++a) c2[a] = 0.75 * cons[a] + 0.25 * (c1[a] + dt * L[a]);
     for (int a = 0; a < N; ++a) J2[a] = 0.75 * J[a] + 0.25 * (J1[a] + dt * LJ[a]);
     for (int a = 0; a < 2 * N; ++a) x2[a] = 0.75 * x[a] + 0.25 * (x1[a] + dt * xdot[a]);
 
     status |= oref_rhs(c, c2, J2, x2, xdot, L, LJ);
-    for (int a = 0; a < 4 * N; ++a) cons[a] = cons[a] / 3.0 + 2.0 / 3.0 * (c2[a] + dt * L[a]);
+    for (int a = 0; a < nv * N; ++a) cons[a] = cons[a] / 3.0 + 2.0 / 3.0 * (c2[a] + dt * L[a]);
     for (int a = 0; a < N; ++a) J[a] = J[a] / 3.0 + 2.0 / 3.0 * (J2[a] + dt * LJ[a]);
     for (int a = 0; a < 2 * N; ++a) x[a] = x[a] / 3.0 + 2.0 / 3.0 * (x2[a] + dt * xdot[a]);
 
@@ -914,25 +1028,25 @@ int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
 int oref_rk_step_given(const oref_cfg *c, double *cons, double *J, double *x,
                        const double *xdot, double dt)
 {
-    int N = c->nx * c->ny, status = 0;
-    double *c1 = (double *)malloc(sizeof(double) * 4 * N);
-    double *c2 = (double *)malloc(sizeof(double) * 4 * N);
+    int N = c->nx * c->ny, nv = nvar(c), status = 0;
+    double *c1 = (double *)malloc(sizeof(double) * nv * N);
+    double *c2 = (double *)malloc(sizeof(double) * nv * N);
     double *J1 = (double *)malloc(sizeof(double) * N);
     double *J2 = (double *)malloc(sizeof(double) * N);
     double *x1 = (double *)malloc(sizeof(double) * 2 * N);
     double *x2 = (double *)malloc(sizeof(double) * 2 * N);
-    double *L = (double *)malloc(sizeof(double) * 4 * N);
+    double *L = (double *)malloc(sizeof(double) * nv * N);
     double *LJ = (double *)malloc(sizeof(double) * N);
     status |= oref_rhs(c, cons, J, x, xdot, L, LJ);
-    for (int a = 0; a < 4 * N; ++a) c1[a] = cons[a] + dt * L[a];
+    for (int a = 0; a < nv * N; ++a) c1[a] = cons[a] + dt * L[a];
     for (int a = 0; a < N; ++a) J1[a] = J[a] + dt * LJ[a];
     for (int a = 0; a < 2 * N; ++a) x1[a] = x[a] + dt * xdot[a];
     status |= oref_rhs(c, c1, J1, x1, xdot, L, LJ);
-    for (int a = 0; a < 4 * N; ++a) c2[a] = 0.75 * cons[a] + 0.25 * (c1[a] + dt * L[a]);
+    for (int a = 0; a < nv * N; ++a) c2[a] = 0.75 * cons[a] + 0.25 * (c1[a] + dt * L[a]);
     for (int a = 0; a < N; ++a) J2[a] = 0.75 * J[a] + 0.25 * (J1[a] + dt * LJ[a]);
     for (int a = 0; a < 2 * N; ++a) x2[a] = 0.75 * x[a] + 0.25 * (x1[a] + dt * xdot[a]);
     status |= oref_rhs(c, c2, J2, x2, xdot, L, LJ);
-    for (int a = 0; a < 4 * N; ++a) cons[a] = cons[a] / 3.0 + 2.0 / 3.0 * (c2[a] + dt * L[a]);
+    for (int a = 0; a < nv * N; ++a) cons[a] = cons[a] / 3.0 + 2.0 / 3.0 * (c2[a] + dt * L[a]);
     for (int a = 0; a < N; ++a) J[a] = J[a] / 3.0 + 2.0 / 3.0 * (J2[a] + dt * LJ[a]);
     for (int a = 0; a < 2 * N; ++a) x[a] = x[a] / 3.0 + 2.0 / 3.0 * (x2[a] + dt * xdot[a]);
     free(c1); free(c2); free(J1); free(J2); free(x1); free(x2); free(L); free(LJ);
@@ -946,21 +1060,29 @@ int oref_rk_step_given(const oref_cfg *c, double *cons, double *J, double *x,
 int oref_totals(const oref_cfg *c, const double *cons, const double *J,
                 const double *dcons, const double *dJ, double *out)
 {
-    int N = c->nx * c->ny, status = 0;
+    int N = c->nx * c->ny, nv = nvar(c), status = 0;
     double S = 0.0, mass = 0.0, vol = 0.0, prod = 0.0;
     for (int id = 0; id < N; ++id) {
-        double U[4], w[4];
-        for (int a = 0; a < 4; ++a) U[a] = cons[a * N + id] / J[id];
-        if (oref_cons2prim(c->gamma, U, w, NULL) != 0) status = -1;
-        S += J[id] * oref_entropy(c->gamma, w);
+        double w[NVMAX];
+        if (node_prim(c, cons, J, id, w) != 0) status = -1;
+        double eta, phi;
+        if (c->phys == OREF_RMHD) {
+            double psi[3], Phi;
+            eta = oref_mhd_entropy(c->gamma, w);
+            oref_mhd_potentials(w, &phi, psi, &Phi);
+        } else {
+            double psi[2];
+            eta = oref_entropy(c->gamma, w);
+            oref_potentials(w, &phi, psi);
+        }
+        S += J[id] * eta;
         mass += cons[id];
         vol += J[id];
         if (dcons && dJ) {
-            double V[4], phi, psi[2];
-            oref_entropy_vars(c->gamma, w, V);
-            oref_potentials(w, &phi, psi);
+            double V[NVMAX];
+            entropy_vars(c, w, V);
             double vd = 0.0;
-            for (int a = 0; a < 4; ++a) vd += V[a] * dcons[a * N + id];
+            for (int a = 0; a < nv; ++a) vd += V[a] * dcons[a * N + id];
             prod += vd - phi * dJ[id];
         }
     }

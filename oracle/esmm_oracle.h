@@ -11,8 +11,10 @@
  * Conventions (all arrays are caller-owned, FP64, structure of arrays):
  *   nodes (i, j), i along xi (fastest), j along eta; N = nx * ny;
  *   index(i, j) = j * nx + i;
- *   prim[4][N]   = (rho, v_x, v_y, p);
- *   cons[4][N]   = J * (D, m_x, m_y, E)   (the curvilinear unknown "J U");
+ *   RHD:  prim[4][N] = (rho, v_x, v_y, p),  cons[4][N] = J * (D, m_x, m_y, E);
+ *   RMHD: prim[8][N] = (rho, v_1, v_2, v_3, p, B_1, B_2, B_3),
+ *         cons[8][N] = J * (D, m_1, m_2, m_3, E, B_1, B_2, B_3)
+ *   (cons is the curvilinear unknown "J U");
  *   J[N], x[2][N] (physical coordinates), xdot[2][N] (mesh velocity).
  * The computational coordinates are node indices (Delta xi_k = 1).
  */
@@ -25,6 +27,7 @@ extern "C" {
 
 enum { OREF_PERIODIC = 0, OREF_OUTFLOW = 1 };
 enum { OREF_MONITOR_RHO = 0, OREF_MONITOR_LNRHO = 1 };
+enum { OREF_RHD = 0, OREF_RMHD = 1 };
 
 typedef struct {
     int nx, ny;
@@ -41,6 +44,7 @@ typedef struct {
     int n_filter;         /* low-pass filter passes                           */
     int mu;               /* Jacobi iterations per redistribution             */
     int move_mesh;        /* 0: static mesh (xdot = 0)                        */
+    int phys;             /* OREF_RHD (4 unknowns) or OREF_RMHD (8 unknowns)  */
 } oref_cfg;
 
 /* Sec. 3.2, constraint eq. HOCoeff: alpha_{p,1..p}. */
@@ -75,7 +79,8 @@ double oref_weno(int w, double eps, const double *s);
  * (J xi_x, J xi_y, J eta_x, J eta_y), and J0[N] from the same differences. */
 void oref_metrics(const oref_cfg *c, const double *x, double *m, double *J0);
 
-/* Semi-discrete scheme, eqs. RMHDSemiU_O2p_ES / RMHDSemiJ_O2p_ES (B = 0). */
+/* Semi-discrete scheme, eqs. RMHDSemiU_O2p_ES / RMHDSemiJ_O2p_ES (RHD: the
+ * same with B = 0, no Powell source). */
 int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
              const double *x, const double *xdot, double *dcons, double *dJ);
 
@@ -95,6 +100,23 @@ int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
  * differentiates). */
 int oref_rk_step_given(const oref_cfg *c, double *cons, double *J, double *x,
                        const double *xdot, double dt);
+
+/* RMHD pointwise parts (esmm_oracle_mhd.c), 8-component states. */
+void oref_mhd_prim2cons(double gamma, const double *w, double *U);
+void oref_mhd_flux(double gamma, const double *w, int dir, double *F);
+int oref_mhd_cons2prim(double gamma, const double *U, double *w, int *iters);
+double oref_mhd_entropy(double gamma, const double *w);
+void oref_mhd_entropy_vars(double gamma, const double *w, double *V);
+/* phi, psi[3] (eq. EntropyPotential) and Phi (eq. Phi) */
+void oref_mhd_potentials(const double *w, double *phi, double *psi, double *Phi);
+/* Phi'(V)[8] of eq. Phi */
+void oref_mhd_phiprime(const double *w, double *P);
+/* U~[8] and F~_j[3][8] (Sec. 3.1) */
+void oref_mhd_ec_flux(double gamma, const double *wl, const double *wr,
+                      double *Ut, double *Ft);
+/* speeds lam[8] and scaled eigenvectors R[8][8] (row = component, column =
+ * wave) of the symmetrized x_1 system at a rotated primitive state */
+void oref_mhd_eigen(double gamma, const double *w_rot, double *lam, double *R);
 
 /* Initial curvilinear state: J from the mesh and cons = J * U(prim). */
 int oref_init_state(const oref_cfg *c, const double *prim, const double *x,

@@ -142,3 +142,75 @@ def batch_problem(k, n, vmax=0.5, offset=1000):
     problem on [-1,1]^2 with n x n nodes (outflow); speeds up to vmax."""
     x = uniform_mesh(n, n, (-1.0, -1.0), (1.0, 1.0), (False, False))
     return x, quadrant_riemann(x, quadrant_states(rng(offset + k), vmax=vmax))
+
+
+# ---- RMHD states: prim[8] = (rho, v_1, v_2, v_3, p, B_1, B_2, B_3) -------------
+def random_states_mhd(r, n, rho=(0.1, 10.0), p=(0.01, 10.0), vmax=0.9, bmax=1.5):
+    """n admissible RMHD primitive states: log-uniform rho and p, |v| <= vmax
+    with a uniform direction in 3D, each B component uniform in [-bmax, bmax]."""
+    rho_ = np.exp(r.uniform(np.log(rho[0]), np.log(rho[1]), n))
+    p_ = np.exp(r.uniform(np.log(p[0]), np.log(p[1]), n))
+    d = r.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    v = d * (vmax * np.cbrt(r.uniform(0.0, 1.0, n)))[:, None]
+    B = r.uniform(-bmax, bmax, (n, 3))
+    return np.concatenate([rho_[:, None], v, p_[:, None], B], axis=1)
+
+
+def smooth_random_state_mhd(x, r, amp=0.2, modes=3):
+    """A smooth periodic RMHD state on [0,1]^2: a few random Fourier modes in
+    each of the eight primitive variables (entropy-identity checks)."""
+    X, Y = x[0], x[1]
+    out = []
+    for base, a in ((1.0, amp), (0.1, 0.3), (-0.1, 0.3), (0.05, 0.2), (1.0, amp),
+                    (0.5, 0.3), (-0.3, 0.3), (0.2, 0.3)):
+        f = base + 0 * X
+        for _ in range(modes):
+            kx, ky = r.integers(-2, 3, 2)
+            ph = r.uniform(0, 2 * np.pi)
+            f = f + a / modes * np.sin(2 * np.pi * (kx * X + ky * Y) + ph)
+        out.append(f)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def quadrant_states_mhd(r, vmax=0.5, bmax=1.0):
+    """Four seeded RMHD quadrant states: rho in [0.1, 1], p in [0.01, 1],
+    in-plane |v| in [0, vmax] with a uniform direction, v_3 = 0, B_1, B_2 in
+    [-bmax, bmax], B_3 in [-bmax/2, bmax/2]."""
+    rho = r.uniform(0.1, 1.0, 4)
+    p = r.uniform(0.01, 1.0, 4)
+    sp = r.uniform(0.0, vmax, 4)
+    th = r.uniform(0.0, 2 * np.pi, 4)
+    B = np.stack([r.uniform(-bmax, bmax, 4), r.uniform(-bmax, bmax, 4),
+                  r.uniform(-0.5 * bmax, 0.5 * bmax, 4)], axis=-1)
+    return np.concatenate([np.stack([rho, sp * np.cos(th), sp * np.sin(th), 0 * rho, p], axis=-1), B],
+                          axis=1)
+
+
+def quadrant_riemann_mhd(x, states, split=(0.0, 0.0)):
+    """Piecewise-constant RMHD data: quadrant q = (x > sx) + 2 (y > sy)."""
+    q = (x[0] > split[0]).astype(int) + 2 * (x[1] > split[1]).astype(int)
+    prim = np.empty((8,) + x.shape[1:])
+    for c in range(8):
+        prim[c] = states[q, c]
+    return np.ascontiguousarray(prim)
+
+
+def rotor(x, rho_in=10.0, omega=9.95, r0=0.1, rho_out=1.0, p=1.0, Bx=1.0):
+    """The rotor: a disk r < r0 of density rho_in spinning rigidly at angular
+    speed omega (|v| <= omega r0 = 0.995), background rho_out at rest,
+    uniform pressure p and field B = (Bx, 0, 0)."""
+    X, Y = x[0], x[1]
+    inside = (X * X + Y * Y) < r0 * r0
+    z = 0 * X
+    rho = np.where(inside, rho_in, rho_out)
+    vx = np.where(inside, -omega * Y, 0.0)
+    vy = np.where(inside, omega * X, 0.0)
+    return np.ascontiguousarray(np.stack([rho, vx, vy, z, p + z, Bx + z, z, z]))
+
+
+def rotor_config(n=512):
+    """2D RMHD rotor on [-0.5,0.5]^2 with outflow boundaries, n x n nodes,
+    Gamma = 4/3 (the 512^2 RMHD workload)."""
+    x = uniform_mesh(n, n, (-0.5, -0.5), (0.5, 0.5), (False, False))
+    return x, rotor(x)
