@@ -3,7 +3,8 @@
  * high-order entropy-stable adaptive moving-mesh finite difference scheme of
  * Duan & Tang, "High-order accurate entropy stable adaptive moving mesh finite
  * difference schemes for special relativistic (magneto)hydrodynamics"
- * (arXiv 2107.12027), for 2D special relativistic hydrodynamics (RHD).
+ * (arXiv 2107.12027), for 2D special relativistic hydrodynamics (RHD) and
+ * magnetohydrodynamics (RMHD, with the Godunov-Powell source of eq. RMHDSymm).
  *
  * Conventions shared by every entry point
  *   - Every function returns an int status: ESMM_OK (0) or one ESMM_ERR_*.
@@ -12,8 +13,10 @@
  *   - Arrays are structure of arrays, FP64, node-ordered with i (the xi
  *     index, along x) fastest: element (c, j, i) of an array with C
  *     components is at c*N + j*nx + i, N = nx*ny.  No ghost nodes.
- *       prim  [4][N]  rho, v_x, v_y, p
- *       cons  [4][N]  the curvilinear unknown J*U, U = (D, m_x, m_y, E)
+ *       prim  [m][N]  RHD (m = 4): rho, v_x, v_y, p
+ *                     RMHD (m = 8): rho, v_1, v_2, v_3, p, B_1, B_2, B_3
+ *       cons  [m][N]  the curvilinear unknown J*U, U = (D, m_x, m_y, E)
+ *                     (RMHD: U = (D, m_1, m_2, m_3, E, B_1, B_2, B_3))
  *       J     [N]     the evolved Jacobian (volume) of each node
  *       x     [2][N]  physical node coordinates (x, y)
  *       xdot  [2][N]  mesh velocity
@@ -43,6 +46,8 @@ extern "C" {
 #define ESMM_ERR_STATE 5    /* the grid has no state yet                      */
 
 #define ESMM_RHD 0          /* physics: special relativistic hydrodynamics    */
+#define ESMM_RMHD 1         /* physics: special relativistic MHD (2D grids,
+                               3-component v and B; FP64; single problems)    */
 
 #define ESMM_PERIODIC 0     /* boundary: periodic (mesh shifted by the period) */
 #define ESMM_OUTFLOW 1      /* boundary: zero-gradient data, fixed boundary
@@ -59,8 +64,8 @@ extern "C" {
 #define ESMM_MONITOR_RHO 0  /* monitor variable sigma = rho                    */
 #define ESMM_MONITOR_LNRHO 1/* monitor variable sigma = ln rho                 */
 
-#define ESMM_GET_PRIM 0     /* [4][N] primitive variables                      */
-#define ESMM_GET_CONS 1     /* [4][N] J*U                                       */
+#define ESMM_GET_PRIM 0     /* [m][N] primitive variables                      */
+#define ESMM_GET_CONS 1     /* [m][N] J*U                                       */
 #define ESMM_GET_J 2        /* [N]                                              */
 #define ESMM_GET_X 3        /* [2][N]                                           */
 #define ESMM_GET_XDOT 4     /* [2][N] mesh velocity of the last step            */
@@ -80,7 +85,7 @@ typedef struct {
 } esmm_params;
 
 /* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim must be 2, phys
- * ESMM_RHD, bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4).  A periodic
+ * ESMM_RHD or ESMM_RMHD, bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4).  A periodic
  * direction has n[k] distinct nodes with spacing (hi-lo)/n[k]; an outflow
  * direction has nodes on both ends.  stream is a cudaStream_t (NULL: the
  * legacy default stream) on the current device; the grid stays on that device.
@@ -95,13 +100,15 @@ int esmm_set_eos(esmm_grid *g, double gamma);
 /* 2p-th order EC flux (eq. ECFlux_O2p), p in {1, 2, 3}; WENO order w of
  * the ES dissipation (eq. ESFlux_HO), w in {0 (EC scheme), 3, 5}. */
 int esmm_set_order(esmm_grid *g, int p, int w);
+/* (ESMM_ERR_ARG for precision ESMM_MIXED on an RMHD grid.) */
 int esmm_set_params(esmm_grid *g, const esmm_params *prm);
 int esmm_get_params(const esmm_grid *g, esmm_params *prm);
 
 /* Set the state from primitive variables and a mesh (x NULL: the uniform
  * mesh of the grid's box).  J is initialised from the mesh by the same
  * central differences as the metrics, cons = J * U(prim), t = 0.
- * ESMM_ERR_ARG for a non-admissible state (rho <= 0, p <= 0 or |v| >= 1). */
+ * ESMM_ERR_ARG for a non-admissible state (rho <= 0, p <= 0 or |v| >= 1).
+ * prim and cons have m = 4 (RHD) or 8 (RMHD) components. */
 int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem);
 /* Set the curvilinear state directly (e.g. to resume from esmm_state_get). */
 int esmm_state_set_cons(esmm_grid *g, const double *cons, const double *J,
@@ -111,7 +118,9 @@ int esmm_state_get(esmm_grid *g, int what, double *out, int mem);
 int esmm_get_time(esmm_grid *g, double *t);
 
 /* One evaluation of the semi-discrete ES scheme, eqs. RMHDSemiU_O2p_ES and
- * RMHDSemiJ_O2p_ES of Sec. 4 with B = 0: d(cons)/dt and dJ/dt for the given
+ * RMHDSemiJ_O2p_ES of Sec. 4 (RHD: B = 0; RMHD: with the Godunov-Powell
+ * source -Phi'(V_i)^T sum_k (B~_{i+1/2} - B~_{i-1/2})): d(cons)/dt and dJ/dt
+ * for the given
  * (cons, J, x, xdot) (xdot NULL: static mesh).  Independent of the grid's
  * state; uses its EOS, order, boundary conditions and precision.
  * ESMM_ERR_C2P if the primitive recovery failed at some node (outputs are then
@@ -141,7 +150,7 @@ int esmm_rk_step(esmm_grid *g, double dt, double *dt_used);
 int esmm_advance(esmm_grid *g, int nsteps, double dt);
 
 /* Batches: nprob independent problems of (possibly) different sizes in one
- * handle (north star form 2).  n, lo, hi and bc are [nprob][2]; each problem
+ * handle (the batched form).  n, lo, hi and bc are [nprob][2]; each problem
  * obeys the rules of esmm_grid_create.  All problems share the EOS, order and
  * parameters; every kernel of a step covers the whole batch in one launch
  * (a block -> (problem, tile) map, blocks never span two problems), and
@@ -151,7 +160,7 @@ int esmm_advance(esmm_grid *g, int nsteps, double dt);
  * esmm_rk_step (dt_used: problem 0's step), esmm_advance, esmm_tune,
  * esmm_profile*, esmm_last_error, esmm_grid_destroy and the esmm_batch_*
  * calls; the single-problem state, rhs, CFL, mesh and totals calls return
- * ESMM_ERR_ARG for them. */
+ * ESMM_ERR_ARG for them.  Batches are RHD (phys must be ESMM_RHD). */
 int esmm_batch_create(esmm_grid **g, int nprob, const int *n, const double *lo, const double *hi, const int *bc,
                       int phys, void *stream);
 int esmm_batch_size(const esmm_grid *g, int *nprob);
@@ -163,8 +172,8 @@ int esmm_batch_times(esmm_grid *g, double *t);
 /* out[nprob][3]: the FP64 totals of esmm_totals for every problem */
 int esmm_batch_totals(esmm_grid *g, double *out);
 
-/* Adjoint (spec form 3): gradients of a final-time functional with
- * respect to the initial data, single problems only, FP64 arithmetic.
+/* Adjoint: gradients of a final-time functional with respect to the initial
+ * data, single RHD problems only (ESMM_ERR_ARG on RMHD grids), FP64.
  * esmm_adjoint_record advances nsteps steps (dt as esmm_rk_step) from the
  * current state, keeping per-step checkpoints (state, mesh velocity, step) on
  * the device (9 N doubles per step).  The adjoint differentiates the recorded

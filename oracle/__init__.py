@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE.  This package is the independent checker of the CUDA
 library: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
 of ``bench.py`` may import it.  It shares no code with the CUDA path; the C
-sources ``esmm_oracle.c`` (grid, mesh, RHD) and ``esmm_oracle_mhd.c``
-(pointwise RMHD) restate the paper (Duan & Tang, arXiv 2107.12027)
+sources ``esmm_oracle.c`` (2D grid, mesh, RHD), ``esmm_oracle_mhd.c``
+(pointwise RMHD) and ``esmm_oracle3d.c`` (3D RMHD grid) restate the paper (Duan & Tang, arXiv 2107.12027)
 one node, pair and interface at a time.
 
 Array conventions match the C header: structure of arrays, ``[comp][j][i]``
@@ -20,7 +20,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "esmm_oracle.c"), os.path.join(_HERE, "esmm_oracle_mhd.c")]
+_SRCS = [os.path.join(_HERE, "esmm_oracle.c"), os.path.join(_HERE, "esmm_oracle_mhd.c"),
+         os.path.join(_HERE, "esmm_oracle3d.c")]
 _HDR = os.path.join(_HERE, "esmm_oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
@@ -49,6 +50,23 @@ class Cfg(ctypes.Structure):
     ]
 
 
+class Cfg3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("bc", ctypes.c_int * 3),
+        ("period", ctypes.c_double * 3),
+        ("gamma", ctypes.c_double),
+        ("p", ctypes.c_int), ("w", ctypes.c_int),
+        ("weno_eps", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("monitor", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("n_filter", ctypes.c_int),
+        ("mu", ctypes.c_int),
+        ("move_mesh", ctypes.c_int),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liboracle.so``."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
@@ -73,6 +91,7 @@ def lib():
             d = ctypes.POINTER(ctypes.c_double)
             i = ctypes.POINTER(ctypes.c_int)
             c = ctypes.POINTER(Cfg)
+            c3 = ctypes.POINTER(Cfg3)
             sig = {
                 "oref_alpha": (None, [ctypes.c_int, d]),
                 "oref_logmean": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
@@ -103,6 +122,14 @@ def lib():
                 "oref_mhd_phiprime": (None, [d, d]),
                 "oref_mhd_ec_flux": (None, [ctypes.c_double, d, d, d, d]),
                 "oref_mhd_eigen": (None, [ctypes.c_double, d, d, d]),
+                "oref3_metrics": (None, [c3, d, d, d]),
+                "oref3_init_state": (ctypes.c_int, [c3, d, d, d, d]),
+                "oref3_state_prim": (ctypes.c_int, [c3, d, d, d]),
+                "oref3_rhs": (ctypes.c_int, [c3, d, d, d, d, d, d]),
+                "oref3_cfl_dt": (ctypes.c_int, [c3, d, d, d, d]),
+                "oref3_mesh": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d, d]),
+                "oref3_rk_step": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d]),
+                "oref3_totals": (ctypes.c_int, [c3, d, d, d, d, d]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -368,3 +395,92 @@ def mhd_eigen(gamma, w_rot):
     lam, R = np.zeros(8), np.zeros(64)
     lib().oref_mhd_eigen(gamma, _p(_vec(w_rot, 8)), _p(lam), _p(R))
     return lam, R.reshape(8, 8)
+
+
+# ---- 3D RMHD grid functions --------------------------------------------------
+def make_cfg3(nx, ny, nz, bc=(PERIODIC, PERIODIC, PERIODIC), period=(1.0, 1.0, 1.0), gamma=4.0 / 3.0,
+              p=2, w=5, weno_eps=1e-6, cfl=0.3, monitor=MONITOR_LNRHO, alpha=800.0, n_filter=4, mu=10,
+              move_mesh=1) -> Cfg3:
+    c = Cfg3()
+    c.nx, c.ny, c.nz = nx, ny, nz
+    for k in range(3):
+        c.bc[k] = bc[k]
+        c.period[k] = period[k]
+    c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
+    c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
+    return c
+
+
+def _shape3(cfg, ncomp):
+    return (ncomp, cfg.nz, cfg.ny, cfg.nx) if ncomp > 1 else (cfg.nz, cfg.ny, cfg.nx)
+
+
+def metrics3(cfg, x):
+    N = cfg.nx * cfg.ny * cfg.nz
+    m, J0 = np.zeros(9 * N), np.zeros(N)
+    lib().oref3_metrics(ctypes.byref(cfg), _p(_vec(x, 3 * N)), _p(m), _p(J0))
+    return m.reshape(_shape3(cfg, 9)), J0.reshape(_shape3(cfg, 1))
+
+
+def init_state3(cfg, prim, x):
+    N = cfg.nx * cfg.ny * cfg.nz
+    cons, J = np.zeros(8 * N), np.zeros(N)
+    lib().oref3_init_state(ctypes.byref(cfg), _p(_vec(prim, 8 * N)), _p(_vec(x, 3 * N)), _p(cons), _p(J))
+    return cons.reshape(_shape3(cfg, 8)), J.reshape(_shape3(cfg, 1))
+
+
+def state_prim3(cfg, cons, J):
+    N = cfg.nx * cfg.ny * cfg.nz
+    prim = np.zeros(8 * N)
+    st = lib().oref3_state_prim(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(prim))
+    return prim.reshape(_shape3(cfg, 8)), st
+
+
+def rhs3(cfg, cons, J, x, xdot=None):
+    N = cfg.nx * cfg.ny * cfg.nz
+    if xdot is None:
+        xdot = np.zeros(3 * N)
+    dcons, dJ = np.zeros(8 * N), np.zeros(N)
+    st = lib().oref3_rhs(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(_vec(x, 3 * N)),
+                         _p(_vec(xdot, 3 * N)), _p(dcons), _p(dJ))
+    if st != 0:
+        raise RuntimeError("oracle rhs3: cons2prim failed")
+    return dcons.reshape(_shape3(cfg, 8)), dJ.reshape(_shape3(cfg, 1))
+
+
+def cfl_dt3(cfg, cons, J, x):
+    N = cfg.nx * cfg.ny * cfg.nz
+    dt = np.zeros(1)
+    st = lib().oref3_cfl_dt(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(_vec(x, 3 * N)), _p(dt))
+    if st != 0:
+        raise RuntimeError("oracle cfl3: cons2prim failed")
+    return dt[0]
+
+
+def mesh3(cfg, cons, J, x, dt):
+    N = cfg.nx * cfg.ny * cfg.nz
+    xdot, tau = np.zeros(3 * N), np.zeros(1)
+    st = lib().oref3_mesh(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(_vec(x, 3 * N)),
+                          float(dt), _p(xdot), _p(tau))
+    if st != 0:
+        raise RuntimeError("oracle mesh3: cons2prim failed")
+    return xdot.reshape(_shape3(cfg, 3)), tau[0]
+
+
+def rk_step3(cfg, cons, J, x, dt=0.0):
+    N = cfg.nx * cfg.ny * cfg.nz
+    cons, J, x = _vec(cons, 8 * N).copy(), _vec(J, N).copy(), _vec(x, 3 * N).copy()
+    dtu = np.zeros(1)
+    st = lib().oref3_rk_step(ctypes.byref(cfg), _p(cons), _p(J), _p(x), float(dt), _p(dtu))
+    if st != 0:
+        raise RuntimeError("oracle rk_step3: cons2prim failed")
+    return cons.reshape(_shape3(cfg, 8)), J.reshape(_shape3(cfg, 1)), x.reshape(_shape3(cfg, 3)), dtu[0]
+
+
+def totals3(cfg, cons, J, dcons=None, dJ=None):
+    N = cfg.nx * cfg.ny * cfg.nz
+    out = np.zeros(4)
+    dc = _vec(dcons, 8 * N) if dcons is not None else None
+    dj = _vec(dJ, N) if dJ is not None else None
+    lib().oref3_totals(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(dc), _p(dj), _p(out))
+    return out

@@ -130,6 +130,39 @@ int oref_state_prim(const oref_cfg *c, const double *cons, const double *J,
 int oref_totals(const oref_cfg *c, const double *cons, const double *J,
                 const double *dcons, const double *dJ, double *out);
 
+
+/* ---- 3D RMHD (esmm_oracle3d.c) --------------------------------------------
+ * nodes (i, j, k), i fastest, N = nx ny nz, index (k ny + j) nx + i;
+ * prim/cons [8][N], J[N], x[3][N], xdot[3][N]; metrics m[9][N] with
+ * m[3 k + j] = J d xi_k/d x_j. */
+typedef struct {
+    int nx, ny, nz;
+    int bc[3];
+    double period[3];
+    double gamma;
+    int p, w;
+    double weno_eps;
+    double cfl;
+    int monitor;
+    double alpha;
+    int n_filter;
+    int mu;
+    int move_mesh;
+} oref3_cfg;
+
+/* eq. SCLCoeff (nested CMM) and J0 = det(delta_k[x_j]) */
+void oref3_metrics(const oref3_cfg *c, const double *x, double *m, double *J0);
+int oref3_init_state(const oref3_cfg *c, const double *prim, const double *x, double *cons, double *J);
+int oref3_state_prim(const oref3_cfg *c, const double *cons, const double *J, double *prim);
+int oref3_rhs(const oref3_cfg *c, const double *cons, const double *J, const double *x,
+              const double *xdot, double *dcons, double *dJ);
+int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const double *x, double *dt);
+int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
+               double *xdot, double *dtau);
+int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used);
+int oref3_totals(const oref3_cfg *c, const double *cons, const double *J, const double *dcons,
+                 const double *dJ, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,4 +1,4 @@
-"""torch.autograd wrapper of the adjoint (spec form 3).
+"""torch.autograd wrapper of the adjoint (gradients with respect to initial data).
 
 ``RKSteps.apply(prim0, grid, x0, nsteps, dt)`` advances the initial primitive
 state ``prim0`` ([4, ny, nx] FP64 CUDA tensor) on the grid's mesh ``x0`` by

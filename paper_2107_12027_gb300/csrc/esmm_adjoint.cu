@@ -1,5 +1,5 @@
 // esmm_adjoint.cu -- vector-Jacobian products of the right-hand side and of
-// the SSP-RK3 step (spec form 3: gradients of a final-time functional
+// the SSP-RK3 step (gradients of a final-time functional
 // with respect to the initial data).
 //
 // The map differentiated is one time step with its mesh velocity xdot and

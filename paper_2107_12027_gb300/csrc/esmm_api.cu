@@ -43,6 +43,8 @@ struct esmm_grid {
     std::vector<double> lo, hi;      // [nprob][2]
     ProbDesc *dpd;                   // device copy (batches)
     long long Ntot, Ptot;
+    int phys;                        // ESMM_RHD or ESMM_RMHD
+    int nv;                          // unknowns per node: 4 (RHD) or 8 (RMHD)
     double gamma;
     int p, w;
     esmm_params prm;
@@ -54,10 +56,10 @@ struct esmm_grid {
     double *cons, *J, *x, *xdot;
     double *c1, *J1, *x1, *c2, *J2, *x2;
     // right-hand-side work arrays
-    double *q;                       // [NQ][Ptot]
-    double *pg[3];                   // pressure warm starts, rotated state -> stage 2 -> stage 3
-    void *pairs;                     // [2][PMAX][4][Ptot] of the working precision
-    void *iflux;                     // [2][5][Ptot] of the working precision
+    double *q;                       // [NQ][Ptot] (RMHD: [NQ_MHD][Ptot])
+    double *pg[3];                   // recovery warm starts (p; RMHD: Z), state -> stage 2 -> stage 3
+    void *pairs;                     // [2][PMAX][4][Ptot] of the working precision (RHD)
+    void *iflux;                     // [2][5][Ptot] of the working precision (RMHD: [2][NF_MHD][Ptot] FP64)
     double *in_cons, *in_J, *in_x, *in_xdot, *out_dc, *out_dJ;  // host-mode staging
     // mesh redistribution
     double *grad, *om, *om2, *X, *Xn;
@@ -262,7 +264,10 @@ void node(esmm_grid *g, const double *cons, const double *J, const double *x, co
           const double *pg_in, double *pg_out)
 {
     Prof pr_(g, ESMM_KIND_NODE);
-    launch_node(g, dom(g, D_PAD), cons, J, x, xdot, pg_in, pg_out, g->q);
+    if (g->phys == ESMM_RMHD)
+        launch_node_mhd(dom(g, D_PAD), g->p, g->gamma, cons, J, x, xdot, pg_in, pg_out, g->q, g->status, g->st);
+    else
+        launch_node(g, dom(g, D_PAD), cons, J, x, xdot, pg_in, pg_out, g->q);
 }
 
 // both sweeps of the flux kernels for the node data in g->q
@@ -272,6 +277,11 @@ void fluxes(esmm_grid *g)
     bool f32 = g->prm.precision == ESMM_MIXED;
     for (int dir = 0; dir < 2; ++dir) {
         LaunchDom Lp = dom(g, dir == 0 ? D_PAIR0 : D_PAIR1), Li = dom(g, dir == 0 ? D_IFACE0 : D_IFACE1);
+        if (g->phys == ESMM_RMHD) {   // two-point fluxes summed inside the interface kernel
+            Prof pr_(g, ESMM_KIND_IFACE);
+            launch_iface_mhd(Li, ph, g->q, (double *)g->iflux, dir, g->st);
+            continue;
+        }
         {
             Prof pr_(g, ESMM_KIND_PAIRS);
             if (f32) launch_pairs_f32(Lp, ph, g->q, g->pairs, dir, g->st);
@@ -291,7 +301,10 @@ void update(esmm_grid *g, double *dcons, double *dJ, const double *cn, const dou
 {
     Prof pr_(g, ESMM_KIND_UPDATE);
     LaunchDom L = dom(g, D_NODE);
-    if (g->prm.precision == ESMM_MIXED)
+    if (g->phys == ESMM_RMHD)
+        launch_update_mhd(L, g->q, (const double *)g->iflux, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B,
+                          g->dt_dev, co, Jo, xo, g->st);
+    else if (g->prm.precision == ESMM_MIXED)
         k_update<float><<<L.nblk, L.bs, 0, g->st>>>(L.pa, (const float *)g->iflux, dcons, dJ, cn, Jn, xn, cs, Js, xs,
                                                     xdot, A, B, g->dt_dev, co, Jo, xo);
     else
@@ -308,7 +321,8 @@ void step_dt(esmm_grid *g, double dt)
     if (!(dt > 0.0)) {
         Prof pr_(g, ESMM_KIND_OTHER);
         LaunchDom L = dom(g, D_NODE);
-        k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red);
+        if (g->phys == ESMM_RMHD) launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->st);
+        else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red);
     }
     Prof pr_(g, ESMM_KIND_OTHER);
     k_dt<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->prm.cfl, dt, g->red, g->dt_dev);
@@ -494,7 +508,7 @@ void release(esmm_grid *g)
 
 // Create a grid of nprob problems: n, lo, hi, bc are [nprob][2].
 int create(esmm_grid **out, int nprob, const int *n, const double *lo, const double *hi, const int *bc,
-           void *stream, bool own_stream)
+           int phys, void *stream, bool own_stream)
 {
     *out = nullptr;
     esmm_grid *g = new (std::nothrow) esmm_grid;
@@ -546,6 +560,8 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     }
     g->Ntot = on;
     g->Ptot = op;
+    g->phys = phys;
+    g->nv = phys == ESMM_RMHD ? 8 : 4;
     g->gamma = 5.0 / 3.0;
     g->p = 2;
     g->w = 5;
@@ -559,19 +575,20 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     g->prm.precision = ESMM_FP64;
     for (int k = 0; k < ND; ++k) g->bs[k] = (k >= D_PAIR0 && k <= D_IFACE1) ? 128 : BS;
 
-    size_t N = (size_t)g->Ntot, P = (size_t)g->Ptot, d = sizeof(double);
+    size_t N = (size_t)g->Ntot, P = (size_t)g->Ptot, d = sizeof(double), nv = (size_t)g->nv;
     size_t nb_max = (size_t)(N / 64 + (size_t)nprob + 64);   // node-domain blocks at >= 64 threads
+    size_t nq = phys == ESMM_RMHD ? (size_t)NQ_MHD : (size_t)NQ;
     struct { double **p; size_t n; } al[] = {
-        {&g->cons, 4 * N}, {&g->J, N}, {&g->x, 2 * N}, {&g->xdot, 2 * N}, {&g->c1, 4 * N}, {&g->J1, N},
-        {&g->x1, 2 * N}, {&g->c2, 4 * N}, {&g->J2, N}, {&g->x2, 2 * N}, {&g->q, (size_t)NQ * P},
-        {&g->pg[0], N}, {&g->pg[1], N}, {&g->pg[2], N}, {&g->out_dc, 4 * N}, {&g->out_dJ, N},
+        {&g->cons, nv * N}, {&g->J, N}, {&g->x, 2 * N}, {&g->xdot, 2 * N}, {&g->c1, nv * N}, {&g->J1, N},
+        {&g->x1, 2 * N}, {&g->c2, nv * N}, {&g->J2, N}, {&g->x2, 2 * N}, {&g->q, nq * P},
+        {&g->pg[0], N}, {&g->pg[1], N}, {&g->pg[2], N}, {&g->out_dc, nv * N}, {&g->out_dJ, N},
         {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->X, 2 * N}, {&g->Xn, 2 * N},
         {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max},
         {&g->tot_dev, 3 * (size_t)nprob}};
     for (auto &a : al)
         if (cudaMalloc((void **)a.p, a.n * d) != cudaSuccess) { release(g); return ESMM_ERR_CUDA; }
     if (nprob == 1) {   // host-pointer staging of esmm_rhs (single problems only)
-        if (cudaMalloc((void **)&g->in_cons, 4 * N * d) != cudaSuccess ||
+        if (cudaMalloc((void **)&g->in_cons, nv * N * d) != cudaSuccess ||
             cudaMalloc((void **)&g->in_J, N * d) != cudaSuccess ||
             cudaMalloc((void **)&g->in_x, 2 * N * d) != cudaSuccess ||
             cudaMalloc((void **)&g->in_xdot, 2 * N * d) != cudaSuccess) {
@@ -579,8 +596,9 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
             return ESMM_ERR_CUDA;
         }
     }
-    if (cudaMalloc(&g->pairs, (size_t)2 * PMAX * 4 * P * d) != cudaSuccess ||
-        cudaMalloc(&g->iflux, (size_t)2 * 5 * P * d) != cudaSuccess ||
+    size_t npairs = phys == ESMM_RMHD ? 1 : (size_t)2 * PMAX * 4 * P;
+    size_t nflux = phys == ESMM_RMHD ? (size_t)2 * NF_MHD * P : (size_t)2 * 5 * P;
+    if (cudaMalloc(&g->pairs, npairs * d) != cudaSuccess || cudaMalloc(&g->iflux, nflux * d) != cudaSuccess ||
         cudaMalloc((void **)&g->red, (size_t)NRED * nprob * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void **)&g->status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&g->pin, std::max<size_t>(16, 3 * (size_t)nprob) * sizeof(double)) != cudaSuccess) {
@@ -641,13 +659,15 @@ int state_set_one(esmm_grid *g, int b, const double *prim, const double *x, int 
         CK(cudaStreamSynchronize(g->st));
     }
     // stage the primitives in the problem's slice of out_dc
-    int rc = copy_in(g, g->out_dc + 4 * D.on, prim, 4 * N, mem);
+    int rc = copy_in(g, g->out_dc + (size_t)g->nv * D.on, prim, (size_t)g->nv * N, mem);
     if (rc) return rc;
     CK(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), g->st));
     LaunchDom L = dom_one(g, b, D_NODE);
     {
         Prof pr_(g, ESMM_KIND_NODE);
-        if (g->p == 1)
+        if (g->phys == ESMM_RMHD)
+            launch_init_mhd(L, g->p, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status, g->st);
+        else if (g->p == 1)
             k_init_state<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
         else if (g->p == 2)
             k_init_state<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
@@ -679,13 +699,16 @@ int state_get_one(esmm_grid *g, int b, int what, double *out, int mem)
         LaunchDom L = dom_one(g, b, D_NODE);
         {
             Prof pr_(g, ESMM_KIND_NODE);
-            k_prim_out<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->cons, g->J, g->out_dc, g->status);
+            if (g->phys == ESMM_RMHD)
+                launch_prim_out_mhd(L, g->gamma, g->cons, g->J, g->out_dc, g->status, g->st);
+            else
+                k_prim_out<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->cons, g->J, g->out_dc, g->status);
         }
         CK(cudaGetLastError());
-        rc = copy_out(g, out, g->out_dc + 4 * D.on, 4 * N, mem);
+        rc = copy_out(g, out, g->out_dc + (size_t)g->nv * D.on, (size_t)g->nv * N, mem);
         break;
     }
-    case ESMM_GET_CONS: rc = copy_out(g, out, g->cons + 4 * D.on, 4 * N, mem); break;
+    case ESMM_GET_CONS: rc = copy_out(g, out, g->cons + (size_t)g->nv * D.on, (size_t)g->nv * N, mem); break;
     case ESMM_GET_J: rc = copy_out(g, out, g->J + D.on, N, mem); break;
     case ESMM_GET_X: rc = copy_out(g, out, g->x + 2 * D.on, 2 * N, mem); break;
     case ESMM_GET_XDOT: rc = copy_out(g, out, g->xdot + 2 * D.on, 2 * N, mem); break;
@@ -722,7 +745,7 @@ void step_launches(const esmm_grid *g, double dt, long long per[ESMM_NKINDS])
 {
     for (int k = 0; k < ESMM_NKINDS; ++k) per[k] = 0;
     per[ESMM_KIND_NODE] = 4;                       // 3 node passes + temporal metrics
-    per[ESMM_KIND_PAIRS] = 6;
+    per[ESMM_KIND_PAIRS] = g->phys == ESMM_RMHD ? 0 : 6;
     per[ESMM_KIND_IFACE] = 6;
     per[ESMM_KIND_UPDATE] = 3;
     per[ESMM_KIND_MESH] = g->prm.move_mesh ? (4 + g->prm.n_filter + g->prm.mu) : 0;
@@ -830,6 +853,12 @@ int tune(esmm_grid *g)
                         update(g, g->out_dc, g->out_dJ, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                nullptr, 0.0, 0.0, nullptr, nullptr, nullptr);
                     });
+                } else if (g->phys == ESMM_RMHD) {
+                            ms = c.kind == D_PAIR0 ? 0.0f : time_it([&]() {
+                                for (int dir = 0; dir < 2; ++dir)
+                                    launch_iface_mhd(dom(g, dir ? c.kind2 : c.kind), ph, g->q, (double *)g->iflux,
+                                                     dir, g->st);
+                            });
                 } else {
                     ms = time_it([&]() {
                         for (int dir = 0; dir < 2; ++dir) {
@@ -862,7 +891,7 @@ int tune(esmm_grid *g)
     return ESMM_OK;
 }
 
-// ---- adjoint (spec form 3) ---------------------------------------------
+// ---- adjoint -------------------------------------------------------------------
 int adj_alloc(esmm_grid *g)
 {
     size_t P = (size_t)g->Ptot, N = (size_t)g->Ntot, d = sizeof(double);
@@ -965,18 +994,18 @@ cudaError_t static_scratch(double **out)
 // ===========================================================================
 extern "C" {
 
-const char *esmm_version(void) { return "esmm 0.2 (2D RHD, batched, sm_103a)"; }
+const char *esmm_version(void) { return "esmm 0.3 (2D RHD and RMHD, batched RHD, sm_103a)"; }
 
 int esmm_grid_create(esmm_grid **out, int dim, const int n[3], const double lo[3], const double hi[3], int phys,
                      const int bc[3], void *stream)
 {
     if (!out || !n || !lo || !hi || !bc) return ESMM_ERR_ARG;
     *out = nullptr;
-    if (dim != 2 || phys != ESMM_RHD) return ESMM_ERR_ARG;
+    if (dim != 2 || (phys != ESMM_RHD && phys != ESMM_RMHD)) return ESMM_ERR_ARG;
     if (check_geometry(n[0], n[1], lo, hi, bc)) return ESMM_ERR_ARG;
     int n2[2] = {n[0], n[1]}, bc2[2] = {bc[0], bc[1]};
     double lo2[2] = {lo[0], lo[1]}, hi2[2] = {hi[0], hi[1]};
-    return create(out, 1, n2, lo2, hi2, bc2, stream, false);
+    return create(out, 1, n2, lo2, hi2, bc2, phys, stream, false);
 }
 
 int esmm_grid_destroy(esmm_grid *g)
@@ -1022,6 +1051,8 @@ int esmm_set_params(esmm_grid *g, const esmm_params *prm)
         prm->mu < 0 || (prm->precision != ESMM_FP64 && prm->precision != ESMM_MIXED) ||
         (prm->monitor != ESMM_MONITOR_RHO && prm->monitor != ESMM_MONITOR_LNRHO))
         return fail(g, ESMM_ERR_ARG, "invalid parameter");
+    if (g->phys == ESMM_RMHD && prm->precision != ESMM_FP64)
+        return fail(g, ESMM_ERR_ARG, "RMHD grids compute in FP64 only");
     g->prm = *prm;
     g->epoch++;
     return ESMM_OK;
@@ -1045,9 +1076,9 @@ int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem)
 int esmm_state_set_cons(esmm_grid *g, const double *cons, const double *J, const double *x, double t, int mem)
 {
     if (!g || !cons || !J || !x || g->nprob != 1) return ESMM_ERR_ARG;
-    size_t N = (size_t)g->Ntot;
+    size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
     int rc;
-    if ((rc = copy_in(g, g->cons, cons, 4 * N, mem)) || (rc = copy_in(g, g->J, J, N, mem)) ||
+    if ((rc = copy_in(g, g->cons, cons, nv * N, mem)) || (rc = copy_in(g, g->J, J, N, mem)) ||
         (rc = copy_in(g, g->x, x, 2 * N, mem)))
         return rc;
     g->pin[0] = t;
@@ -1082,9 +1113,9 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
     if (!g || !cons || !J || !x || !dcons || !dJ || g->nprob != 1) return ESMM_ERR_ARG;
     int rc;
     if ((rc = ensure_doms(g))) return rc;
-    size_t N = (size_t)g->Ntot;
+    size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
     if (mem == ESMM_MEM_HOST) {
-        if ((rc = copy_in(g, g->in_cons, cons, 4 * N, mem)) || (rc = copy_in(g, g->in_J, J, N, mem)) ||
+        if ((rc = copy_in(g, g->in_cons, cons, nv * N, mem)) || (rc = copy_in(g, g->in_J, J, N, mem)) ||
             (rc = copy_in(g, g->in_x, x, 2 * N, mem)))
             return rc;
         if (xdot && (rc = copy_in(g, g->in_xdot, xdot, 2 * N, mem))) return rc;
@@ -1101,7 +1132,7 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
            nullptr);
     CK(cudaGetLastError());
     if (mem == ESMM_MEM_HOST) {
-        if ((rc = copy_out(g, dcons, g->out_dc, 4 * N, mem)) || (rc = copy_out(g, dJ, g->out_dJ, N, mem)))
+        if ((rc = copy_out(g, dcons, g->out_dc, nv * N, mem)) || (rc = copy_out(g, dJ, g->out_dJ, N, mem)))
             return rc;
         CK(cudaStreamSynchronize(g->st));
         return check_c2p(g);
@@ -1183,7 +1214,7 @@ int esmm_batch_create(esmm_grid **out, int nprob, const int *n, const double *lo
     *out = nullptr;
     for (int b = 0; b < nprob; ++b)
         if (check_geometry(n[2 * b], n[2 * b + 1], lo + 2 * b, hi + 2 * b, bc + 2 * b)) return ESMM_ERR_ARG;
-    return create(out, nprob, n, lo, hi, bc, stream, true);
+    return create(out, nprob, n, lo, hi, bc, ESMM_RHD, stream, true);
 }
 
 int esmm_batch_size(const esmm_grid *g, int *nprob)
@@ -1243,6 +1274,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
                  const double *mu, double *lam, int mem)
 {
     if (!g || !cons || !J || !x || !mu || !lam || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->phys != ESMM_RHD) return fail(g, ESMM_ERR_ARG, "the adjoint covers RHD grids");
     int rc;
     if ((rc = ensure_doms(g)) || (rc = adj_alloc(g))) return rc;
     size_t N = (size_t)g->Ntot;
@@ -1270,6 +1302,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 {
     if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->phys != ESMM_RHD) return fail(g, ESMM_ERR_ARG, "the adjoint covers RHD grids");
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     size_t N = (size_t)g->Ntot, d = sizeof(double);
     g->ck_dt->clear();

@@ -1,5 +1,7 @@
-// esmm_launch.h -- host-side launchers of the flux kernels, one translation
-// unit per working precision (esmm_flux_f64.cu, esmm_flux_f32.cu).
+// esmm_launch.h -- host-side launchers of the kernels that live outside
+// esmm_api.cu: the RHD flux kernels (one translation unit per working
+// precision: esmm_flux_f64.cu, esmm_flux_f32.cu), the adjoint
+// (esmm_adjoint.cu) and the RMHD kernels (esmm_mhd.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,6 +42,28 @@ void launch_node_vjp(const LaunchDom &L, double gam, int p, int w, const double 
 void launch_lincomb(long long n, double a, const double *x, double b, const double *y, double *out, cudaStream_t st);
 void launch_prim_grad(const LaunchDom &L, double gam, const double *cons, const double *J, const double *lam,
                       double *out, cudaStream_t st);
+// RMHD (esmm_mhd.cu), single problems, FP64: node pass (zg: warm starts of
+// Z = rho h W^2), interface fluxes (10 values per direction: F[8], the metric
+// flux, the magnetic flux B~), update with the Powell source, CFL radius,
+// state set-up and read-out.  The node arrays hold 18 fields per padded node.
+constexpr int NQ_MHD = 18;
+constexpr int NF_MHD = 10;
+void launch_node_mhd(const LaunchDom &L, int p, double gam, const double *cons, const double *J, const double *x,
+                     const double *xdot, const double *zg_in, double *zg_out, double *q, int *status,
+                     cudaStream_t st);
+void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, double *iflux, int dir,
+                      cudaStream_t st);
+void launch_update_mhd(const LaunchDom &L, const double *q, const double *fl, double *dcons, double *dJ,
+                       const double *cn, const double *Jn, const double *xn, const double *cs, const double *Js,
+                       const double *xs, const double *xdot, double A, double B, const double *dt_dev, double *co,
+                       double *Jo, double *xo, cudaStream_t st);
+void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,
+                    cudaStream_t st);
+void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, const double *x, double *cons,
+                     double *J, int *status, cudaStream_t st);
+void launch_prim_out_mhd(const LaunchDom &L, double gam, const double *cons, const double *J, double *prim,
+                         int *status, cudaStream_t st);
+
 // sizes of the adjoint's contribution buffers, in doubles per padded node
 constexpr long long ADJ_G_PER_NODE = 2 * 6 * 7;
 constexpr long long ADJ_GP_PER_NODE = 2 * PMAX * 2 * 7;

@@ -1,0 +1,107 @@
+// esmm_mhd.cu -- RMHD kernels (esmm_mhd.cuh) and their host launchers
+// (declared in esmm_launch.h).
+#include "esmm_launch.h"
+#include "esmm_mhd.cuh"
+#include "esmm_reduce.cuh"
+
+namespace esmm {
+
+__global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
+                          unsigned long long *red)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    double r[2] = {0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        long long c = pidx(g, i, j);
+        double iW = 1.0 / q[Q_W * g.P + c];
+        double w[8] = {q[Q_RHO * g.P + c], q[Q_UX * g.P + c] * iW, q[Q_UY * g.P + c] * iW,
+                       q[QM_UZ * g.P + c] * iW, q[Q_P * g.P + c], q[QM_B1 * g.P + c], q[QM_B2 * g.P + c],
+                       q[QM_B3 * g.P + c]};
+        double iJ = 1.0 / J[id];
+        for (int k = 0; k < 2; ++k) {
+            double mx = q[(Q_M00 + 2 * k) * g.P + c], my = q[(Q_M01 + 2 * k) * g.P + c];
+            double Lk = sqrt(mx * mx + my * my);
+            double nx = mx / Lk, ny = my / Lk;
+            double wr[8] = {w[0], nx * w[1] + ny * w[2], -ny * w[1] + nx * w[2], w[3],
+                            w[4], nx * w[5] + ny * w[6], -ny * w[5] + nx * w[6], w[7]};
+            double lam[8], R[8][8];
+            eigen_mhd(gam, wr, lam, R, false);
+            double a = 0.0;
+            for (int m = 0; m < 8; ++m) a = fmax(a, fabs(lam[m]));
+            r[k] = Lk * a * iJ;
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        double m = block_reduce<0>(r[k]);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b + 2 + k, m);
+    }
+}
+
+void launch_node_mhd(const LaunchDom &L, int p, double gam, const double *cons, const double *J, const double *x,
+                     const double *xdot, const double *zg_in, double *zg_out, double *q, int *status,
+                     cudaStream_t st)
+{
+    if (p == 1)
+        k_node_mhd<1><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status);
+    else if (p == 2)
+        k_node_mhd<2><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status);
+    else
+        k_node_mhd<3><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status);
+}
+
+template <int P>
+static void launch_iface_mhd_p(const LaunchDom &L, const Phys &ph, const double *q, double *iflux, int dir,
+                               cudaStream_t st)
+{
+    switch (ph.w) {
+    case 0: k_iface_mhd<P, 0><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
+    case 3: k_iface_mhd<P, 3><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
+    default: k_iface_mhd<P, 5><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
+    }
+}
+
+void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, double *iflux, int dir,
+                      cudaStream_t st)
+{
+    switch (ph.p) {
+    case 1: launch_iface_mhd_p<1>(L, ph, q, iflux, dir, st); break;
+    case 2: launch_iface_mhd_p<2>(L, ph, q, iflux, dir, st); break;
+    default: launch_iface_mhd_p<3>(L, ph, q, iflux, dir, st); break;
+    }
+}
+
+void launch_update_mhd(const LaunchDom &L, const double *q, const double *fl, double *dcons, double *dJ,
+                       const double *cn, const double *Jn, const double *xn, const double *cs, const double *Js,
+                       const double *xs, const double *xdot, double A, double B, const double *dt_dev, double *co,
+                       double *Jo, double *xo, cudaStream_t st)
+{
+    k_update_mhd<<<L.nblk, L.bs, 0, st>>>(L.pa, q, fl, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B, dt_dev, co,
+                                          Jo, xo);
+}
+
+void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,
+                    cudaStream_t st)
+{
+    k_cfl_mhd<<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red);
+}
+
+void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, const double *x, double *cons,
+                     double *J, int *status, cudaStream_t st)
+{
+    if (p == 1) k_init_state_mhd<1><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, prim, x, cons, J, status);
+    else if (p == 2) k_init_state_mhd<2><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, prim, x, cons, J, status);
+    else k_init_state_mhd<3><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, prim, x, cons, J, status);
+}
+
+void launch_prim_out_mhd(const LaunchDom &L, double gam, const double *cons, const double *J, double *prim,
+                         int *status, cudaStream_t st)
+{
+    k_prim_out_mhd<<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, prim, status);
+}
+
+}  // namespace esmm

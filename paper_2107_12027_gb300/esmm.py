@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 OK, ERR_ARG, ERR_CUDA, ERR_C2P, ERR_TIMEOUT, ERR_STATE = 0, 1, 2, 3, 4, 5
-RHD = 0
+RHD, RMHD = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 FP64, MIXED = 0, 1
@@ -143,19 +143,22 @@ def _mem(*arrays):
 
 
 class Grid:
-    """One 2D RHD problem: a handle of the C ABI plus argument marshalling."""
+    """One 2D problem (RHD: 4 unknowns per node, RMHD: 8): a handle of the C
+    ABI plus argument marshalling."""
 
     def __init__(self, n, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC), gamma=5.0 / 3.0, p=2, w=5,
-                 stream=None, **params):
+                 stream=None, phys=RHD, **params):
         self.nx, self.ny = int(n[0]), int(n[1])
         self.N = self.nx * self.ny
+        self.phys = phys
+        self.nv = 8 if phys == RMHD else 4
         h = ctypes.c_void_p()
         nn = (ctypes.c_int * 3)(self.nx, self.ny, 1)
         lo3 = (ctypes.c_double * 3)(lo[0], lo[1], 0.0)
         hi3 = (ctypes.c_double * 3)(hi[0], hi[1], 1.0)
         bc3 = (ctypes.c_int * 3)(bc[0], bc[1], 0)
         st = ctypes.c_void_p(stream) if stream is not None else None
-        self._check(lib().esmm_grid_create(ctypes.byref(h), 2, nn, lo3, hi3, RHD, bc3, st))
+        self._check(lib().esmm_grid_create(ctypes.byref(h), 2, nn, lo3, hi3, phys, bc3, st))
         self.h = h
         self.set_eos(gamma)
         self.set_order(p, w)
@@ -214,16 +217,16 @@ class Grid:
 
     # -- state ----------------------------------------------------------------
     def state_set(self, prim, x=None):
-        pp, mp = _ptr(prim, 4 * self.N)
+        pp, mp = _ptr(prim, self.nv * self.N)
         px, mx = _ptr(x, 2 * self.N)
         self._check(lib().esmm_state_set(self.h, pp, px, _mem((pp, mp), (px, mx))))
 
     def state_set_cons(self, cons, J, x, t=0.0):
-        a = [_ptr(cons, 4 * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N)]
+        a = [_ptr(cons, self.nv * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N)]
         self._check(lib().esmm_state_set_cons(self.h, a[0][0], a[1][0], a[2][0], float(t), _mem(*a)))
 
     def state_get(self, what, out=None):
-        size = {GET_PRIM: 4, GET_CONS: 4, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
+        size = {GET_PRIM: self.nv, GET_CONS: self.nv, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
         shape = (size, self.ny, self.nx) if size > 1 else (self.ny, self.nx)
         if out is None:
             out = np.empty(shape)
@@ -242,14 +245,14 @@ class Grid:
         host = not _is_torch(cons)
         if dcons is None:
             if host:
-                dcons, dJ = np.empty((4, self.ny, self.nx)), np.empty((self.ny, self.nx))
+                dcons, dJ = np.empty((self.nv, self.ny, self.nx)), np.empty((self.ny, self.nx))
             else:
                 import torch
-                dcons = torch.empty((4, self.ny, self.nx), dtype=torch.float64, device=cons.device)
+                dcons = torch.empty((self.nv, self.ny, self.nx), dtype=torch.float64, device=cons.device)
                 dJ = torch.empty((self.ny, self.nx), dtype=torch.float64, device=cons.device)
-        a = [_ptr(cons, 4 * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N)]
+        a = [_ptr(cons, self.nv * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N)]
         xd = _ptr(xdot, 2 * self.N)
-        o = [_ptr(dcons, 4 * self.N), _ptr(dJ, self.N)]
+        o = [_ptr(dcons, self.nv * self.N), _ptr(dJ, self.N)]
         mem = _mem(*a, *o, *([xd] if xdot is not None else []))
         self._check(lib().esmm_rhs(self.h, a[0][0], a[1][0], a[2][0], xd[0], o[0][0], o[1][0], mem))
         return dcons, dJ
@@ -366,6 +369,7 @@ class Batch(Grid):
     def __init__(self, sizes, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC), gamma=5.0 / 3.0, p=2, w=5,
                  stream=None, **params):
         self.sizes = [(int(a), int(b)) for a, b in sizes]
+        self.phys, self.nv = RHD, 4
         B = len(self.sizes)
         per = lambda v: [tuple(v)] * B if np.ndim(v) == 1 else [tuple(t) for t in v]
         los, his, bcs = per(lo), per(hi), per(bc)

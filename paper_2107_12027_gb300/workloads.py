@@ -214,3 +214,94 @@ def rotor_config(n=512):
     Gamma = 4/3 (the 512^2 RMHD workload)."""
     x = uniform_mesh(n, n, (-0.5, -0.5), (0.5, 0.5), (False, False))
     return x, rotor(x)
+
+
+# ---- 3D (RMHD) ----------------------------------------------------------------
+# Arrays [comp][k][j][i] (i fastest), the layout of the 3D C ABI.
+def uniform_mesh3(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, True, True)):
+    """Nodes of a uniform 3D mesh (conventions of :func:`uniform_mesh`)."""
+    ax = [a + (b - a) * np.arange(m) / (m if per else (m - 1)) for m, a, b, per in zip(n, lo, hi, periodic)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return np.ascontiguousarray(np.stack([X, Y, Z]))
+
+
+def wavy_mesh3(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.04, t=0.0, periodic=(True, True, True)):
+    """A smooth curvilinear 3D mesh: each coordinate displaced by a product of
+    sines of the other two (periodic, zero on outflow faces)."""
+    x0 = uniform_mesh3(n, lo, hi, periodic)
+    s = amp * np.cos(np.pi * t / 4.0)
+    out = []
+    for d in range(3):
+        L = [hi[k] - lo[k] for k in range(3)]
+        a, b = (d + 1) % 3, (d + 2) % 3
+        f = np.sin(2 * np.pi * (x0[a] - lo[a]) / L[a]) * np.sin(2 * np.pi * (x0[b] - lo[b]) / L[b])
+        if not periodic[d]:
+            f = f * np.sin(np.pi * (x0[d] - lo[d]) / L[d]) ** 2
+        out.append(x0[d] + s * L[d] * f)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def wavy_mesh_velocity3(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.04, t=0.0, periodic=(True, True, True)):
+    """d/dt of :func:`wavy_mesh3`."""
+    x0 = uniform_mesh3(n, lo, hi, periodic)
+    ds = -amp * np.pi / 4.0 * np.sin(np.pi * t / 4.0)
+    out = []
+    for d in range(3):
+        L = [hi[k] - lo[k] for k in range(3)]
+        a, b = (d + 1) % 3, (d + 2) % 3
+        f = np.sin(2 * np.pi * (x0[a] - lo[a]) / L[a]) * np.sin(2 * np.pi * (x0[b] - lo[b]) / L[b])
+        if not periodic[d]:
+            f = f * np.sin(np.pi * (x0[d] - lo[d]) / L[d]) ** 2
+        out.append(ds * L[d] * f)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def random_mesh3(n, r, amp=0.15, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, True, True)):
+    """A uniform 3D mesh with every node jittered by up to amp of a spacing
+    (outflow faces keep their normal coordinate)."""
+    x0 = uniform_mesh3(n, lo, hi, periodic)
+    d = r.uniform(-amp, amp, size=x0.shape)
+    for k in range(3):
+        d[k] *= (hi[k] - lo[k]) / (n[k] if periodic[k] else n[k] - 1)
+    for k in range(3):
+        if not periodic[k]:
+            sl = [slice(None)] * 3
+            for end in (0, -1):
+                sl[2 - k] = end
+                d[(k,) + tuple(sl)] = 0.0
+    return np.ascontiguousarray(x0 + d)
+
+
+def smooth_random_state_mhd3(x, r, amp=0.2, modes=3):
+    """A smooth periodic 3D RMHD state on [0,1]^3 with a few random Fourier
+    modes in each of the eight primitive variables."""
+    X, Y, Z = x[0], x[1], x[2]
+    out = []
+    for base, a in ((1.0, amp), (0.1, 0.3), (-0.1, 0.3), (0.05, 0.3), (1.0, amp),
+                    (0.5, 0.3), (-0.3, 0.3), (0.2, 0.3)):
+        f = base + 0 * X
+        for _ in range(modes):
+            kx, ky, kz = r.integers(-2, 3, 3)
+            ph = r.uniform(0, 2 * np.pi)
+            f = f + a / modes * np.sin(2 * np.pi * (kx * X + ky * Y + kz * Z) + ph)
+        out.append(f)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def blast3(x, r0=0.1, p_in=1.0, p_out=5e-4, rho_in=1e-2, rho_out=1e-4, B=(0.1, 0.0, 0.0)):
+    """The 3D RMHD blast: a sphere r < r0 at pressure p_in in a background at
+    p_out; density rho_in inside (reading: the paper's 2D blast explosion
+    zone) and rho_out outside; at rest; uniform B."""
+    X, Y, Z = x[0], x[1], x[2]
+    inside = (X * X + Y * Y + Z * Z) < r0 * r0
+    z = 0 * X
+    rho = np.where(inside, rho_in, rho_out)
+    p = np.where(inside, p_in, p_out)
+    return np.ascontiguousarray(np.stack([rho, z, z, z, p, B[0] + z, B[1] + z, B[2] + z]))
+
+
+def blast3_config(n=128):
+    """3D RMHD blast on [-0.5,0.5]^3 with outflow faces, n^3 nodes, Gamma = 4/3
+    (the 128^3 adjoint workload)."""
+    x = uniform_mesh3((n, n, n), (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), (False, False, False))
+    return x, blast3(x)

@@ -1,0 +1,170 @@
+"""GPU (sm_103a) RMHD path against the FP64 oracle, element by element,
+through the C ABI.
+
+The EC scheme (w = 0) is pure arithmetic and matches to 1e-12 relative.  The
+ES scheme goes through the eigen-system of the symmetrized RMHD Jacobian,
+whose eigenvectors are determined only to ~eps/gap by any algorithm when two
+wave speeds come close (Alfven and slow or fast waves where B_t or B_n
+vanishes); speeds closer than the cluster tolerance share a canonical basis
+on both sides.  Its tolerance, ES_TOL, covers the conditioning of the
+separated pairs just above that tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_12027_gb300 import esmm
+from paper_2107_12027_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+ES_TOL = 1e-10
+G43 = 4.0 / 3.0
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    if a.ndim == 3:
+        return max(_rel(a[c], b[c]) for c in range(a.shape[0]) if np.abs(b[c]).max() > 0)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _pair(nx, ny, bc, lo, hi, p, w, **kw):
+    per = (hi[0] - lo[0], hi[1] - lo[1])
+    cfg = oracle.make_cfg(nx, ny, bc=bc, period=per, p=p, w=w, gamma=G43, phys=oracle.RMHD, **kw)
+    g = esmm.Grid((nx, ny), lo, hi, bc=bc, p=p, w=w, gamma=G43, phys=esmm.RMHD, **kw)
+    return cfg, g
+
+
+def _smooth(nx, ny, seed):
+    x = wl.wavy_mesh(nx, ny, amp=0.04)
+    xdot = wl.wavy_mesh_velocity(nx, ny, amp=0.04, t=1.3)
+    return x, xdot, wl.smooth_random_state_mhd(x, wl.rng(seed))
+
+
+def _quadrant(nx, ny, seed):
+    x = wl.random_mesh(nx, ny, wl.rng(seed), amp=0.2, lo=(-1, -1), hi=(1, 1), periodic=(False, False))
+    xdot = wl.rng(seed + 1).uniform(-0.3, 0.3, x.shape)
+    xdot[:, :, 0] = xdot[:, :, -1] = 0.0
+    xdot[:, 0, :] = xdot[:, -1, :] = 0.0
+    prim = wl.quadrant_riemann_mhd(x, wl.quadrant_states_mhd(wl.rng(seed + 2)), split=(0.1, -0.2))
+    return x, np.ascontiguousarray(xdot), prim
+
+
+@pytest.mark.parametrize("p,w", [(1, 0), (2, 0), (3, 0), (2, 3), (2, 5), (3, 5)])
+def test_rhs_parity_smooth_periodic_moving_mesh(p, w):
+    nx, ny = 45, 37          # several 128-thread blocks, ragged tails
+    x, xdot, prim = _smooth(nx, ny, 140 + p + w)
+    cfg, g = _pair(nx, ny, (0, 0), (0, 0), (1, 1), p, w)
+    cons, J = oracle.init_state(cfg, prim, x)
+    ref = oracle.rhs(cfg, cons, J, x, xdot)
+    with g:
+        got = g.rhs(cons, J, x, xdot)
+    tol = TOL if w == 0 else ES_TOL
+    assert _rel(got[0], ref[0]) < tol
+    assert _rel(got[1], ref[1]) < TOL
+
+
+@pytest.mark.parametrize("p,w", [(2, 0), (2, 5), (3, 3)])
+def test_rhs_parity_discontinuous_outflow(p, w):
+    nx, ny = 41, 33
+    x, xdot, prim = _quadrant(nx, ny, 150 + p + w)
+    cfg, g = _pair(nx, ny, (1, 1), (-1, -1), (1, 1), p, w)
+    cons, J = oracle.init_state(cfg, prim, x)
+    ref = oracle.rhs(cfg, cons, J, x, xdot)
+    with g:
+        got = g.rhs(cons, J, x, xdot)
+    tol = TOL if w == 0 else ES_TOL
+    assert _rel(got[0], ref[0]) < tol
+    assert _rel(got[1], ref[1]) < TOL
+
+
+def test_rhs_parity_rotor_degenerate_waves():
+    # B = (1, 0, 0) everywhere at t = 0: B_t = 0 on xi interfaces and B_n = 0
+    # on eta interfaces, exactly degenerate speeds at every interface
+    n = 48
+    x, prim = wl.rotor_config(n)
+    cfg, g = _pair(n, n, (1, 1), (-0.5, -0.5), (0.5, 0.5), 2, 5, alpha=800.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    ref = oracle.rhs(cfg, cons, J, x)
+    with g:
+        got = g.rhs(cons, J, x)
+    assert _rel(got[0], ref[0]) < ES_TOL
+
+
+def test_state_round_trip_and_cfl():
+    n = 24
+    x, prim = wl.rotor_config(n)
+    cfg, g = _pair(n, n, (1, 1), (-0.5, -0.5), (0.5, 0.5), 2, 5, alpha=800.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    with g:
+        g.state_set(prim, x)
+        np.testing.assert_allclose(g.state_get(esmm.GET_J), J, rtol=1e-14, atol=0)
+        c = g.state_get(esmm.GET_CONS)
+        assert _rel(c, cons) < 1e-14
+        pr = g.state_get(esmm.GET_PRIM)
+        assert _rel(pr, prim) < 1e-13
+        assert abs(g.cfl_dt() - oracle.cfl_dt(cfg, cons, J, x)) < 1e-13 * oracle.cfl_dt(cfg, cons, J, x)
+
+
+def test_free_stream_on_moving_mesh():
+    n = 20
+    x = wl.random_mesh(n, n, wl.rng(160), amp=0.15)
+    xdot = np.ascontiguousarray(wl.random_mesh(n, n, wl.rng(161), amp=0.1) - wl.uniform_mesh(n, n))
+    w0 = np.array([1.3, 0.3, -0.2, 0.1, 0.7, 0.5, -0.8, 0.3])
+    prim = np.ascontiguousarray(np.broadcast_to(w0[:, None, None], (8, n, n)))
+    cfg, g = _pair(n, n, (0, 0), (0, 0), (1, 1), 2, 5)
+    cons, J = oracle.init_state(cfg, prim, x)
+    U0 = oracle.mhd_prim2cons(G43, w0)
+    with g:
+        dc, dJ = g.rhs(cons, J, x, xdot)
+    assert np.abs(dc - U0[:, None, None] * dJ[None]).max() < 1e-13 * np.abs(U0).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_ec_entropy_identity_on_gpu(p):
+    n = 32
+    x, xdot, prim = _smooth(n, n, 170 + p)
+    cfg, g = _pair(n, n, (0, 0), (0, 0), (1, 1), p, 0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    with g:
+        dc, dJ = g.rhs(cons, J, x, xdot)
+    prod = oracle.totals(cfg, cons, J, dc, dJ)[3]
+    assert abs(prod) < 1e-12 * np.abs(dc).sum()
+
+
+def test_rk_step_parity_rotor():
+    # three steps with the CFL step and the adaptive mesh, compared per step
+    n = 40
+    x, prim = wl.rotor_config(n)
+    cfg, g = _pair(n, n, (1, 1), (-0.5, -0.5), (0.5, 0.5), 2, 5, alpha=800.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    with g:
+        g.state_set(prim, x)
+        for _ in range(3):
+            cons, J, x, dt = oracle.rk_step(cfg, cons, J, x)
+            dtg = g.rk_step()
+            assert abs(dtg - dt) <= 1e-12 * dt
+            assert _rel(g.state_get(esmm.GET_CONS), cons) < ES_TOL
+            assert _rel(g.state_get(esmm.GET_J), J) < 1e-12
+            assert _rel(g.state_get(esmm.GET_X), x) < 1e-12
+
+
+def test_rotor_512_full_size_rhs():
+    # the 512^2 rotor (Gamma = 4/3) at full size, in the launch configuration
+    # of the step, against the oracle's right-hand side
+    n = 512
+    x, prim = wl.rotor_config(n)
+    cfg, g = _pair(n, n, (1, 1), (-0.5, -0.5), (0.5, 0.5), 2, 5, alpha=800.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    ref = oracle.rhs(cfg, cons, J, x)
+    with g:
+        got = g.rhs(cons, J, x)
+    assert _rel(got[0], ref[0]) < ES_TOL
+    assert _rel(got[1], ref[1]) < TOL
+
+
+def test_rmhd_rejects_unsupported_forms():
+    with esmm.Grid((16, 16), phys=esmm.RMHD) as g:
+        with pytest.raises(esmm.EsmmError):
+            g.set_params(precision=esmm.MIXED)
