@@ -133,14 +133,18 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
 int esmm_cfl_dt(esmm_grid *g, double *dt);
 
 /* Adaptive mesh redistribution of Sec. 5 for the grid's state and time step
- * dt (dt <= 0: the CFL step): monitor, low-pass filter, mu Jacobi sweeps,
- * movement limiter.  Stores the mesh velocity in the grid (used by the next
- * esmm_rk_step only through esmm_rk_step's own call of it) and, when given,
- * writes it to xdot [2][N] and the limiter value to *dtau (host). */
-int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, int mem);
+ * dt: monitor, low-pass filter, mu Jacobi sweeps, movement limiter.
+ * dt <= 0 selects the step of eq. cfl with the mesh velocity in the spectral
+ * radius: the limiter Delta tau is capped so that the displacement's Courant
+ * number C_m = Delta tau sum_k max_i |(x^[mu] - x^n).(J xi_k,x)|/J stays
+ * <= CFL/2, and dt = (CFL - C_m)/sum_k max_i rho_k (static radius).  Stores
+ * the mesh velocity in the grid and, when given, writes it to xdot [2][N], the
+ * limiter value to *dtau and the step to *dt_used (host scalars). */
+int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, double *dt_used, int mem);
 
-/* One time step of the fully discrete scheme: CFL step (dt <= 0) or the given
- * dt, mesh redistribution (unless move_mesh = 0), and three SSP-RK3 stages
+/* One time step of the fully discrete scheme: CFL step (dt <= 0, with the
+ * mesh motion as in esmm_mesh_redistribute) or the given dt, mesh
+ * redistribution (unless move_mesh = 0), and three SSP-RK3 stages
  * applied to (cons, J) and to the mesh with the step's mesh velocity.
  * Asynchronous on the grid's stream; when dt_used is not NULL the call
  * synchronises and writes the step used.  A recovery failure is reported by

@@ -107,7 +107,7 @@ def lib():
                 "oref_metrics": (None, [c, d, d, d]),
                 "oref_rhs": (ctypes.c_int, [c, d, d, d, d, d, d]),
                 "oref_cfl_dt": (ctypes.c_int, [c, d, d, d, d]),
-                "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d]),
+                "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d, d]),
                 "oref_rk_step": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d]),
                 "oref_rk_step_given": (ctypes.c_int, [c, d, d, d, d, ctypes.c_double]),
                 "oref_init_state": (ctypes.c_int, [c, d, d, d, d]),
@@ -127,7 +127,7 @@ def lib():
                 "oref3_state_prim": (ctypes.c_int, [c3, d, d, d]),
                 "oref3_rhs": (ctypes.c_int, [c3, d, d, d, d, d, d]),
                 "oref3_cfl_dt": (ctypes.c_int, [c3, d, d, d, d]),
-                "oref3_mesh": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d, d]),
+                "oref3_mesh": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d, d, d]),
                 "oref3_rk_step": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d]),
                 "oref3_totals": (ctypes.c_int, [c3, d, d, d, d, d]),
             }
@@ -290,16 +290,18 @@ def cfl_dt(cfg, cons, J, x):
     return dt[0]
 
 
-def mesh(cfg, cons, J, x, dt):
+def mesh(cfg, cons, J, x, dt=0.0):
+    """Mesh velocity, limiter value and step: (xdot, dtau, dt).  dt <= 0 selects
+    the CFL step with the mesh motion included."""
     N = cfg.nx * cfg.ny
     nv = nvar(cfg)
     xdot = np.zeros(2 * N)
-    tau = np.zeros(1)
+    tau, dto = np.zeros(1), np.zeros(1)
     st = lib().oref_mesh(ctypes.byref(cfg), _p(_vec(cons, nv * N)), _p(_vec(J, N)),
-                         _p(_vec(x, 2 * N)), float(dt), _p(xdot), _p(tau))
+                         _p(_vec(x, 2 * N)), float(dt), _p(xdot), _p(tau), _p(dto))
     if st != 0:
         raise RuntimeError("oracle mesh: cons2prim failed")
-    return xdot.reshape(2, cfg.ny, cfg.nx), tau[0]
+    return xdot.reshape(2, cfg.ny, cfg.nx), tau[0], dto[0]
 
 
 def rk_step(cfg, cons, J, x, dt=0.0):
@@ -457,14 +459,15 @@ def cfl_dt3(cfg, cons, J, x):
     return dt[0]
 
 
-def mesh3(cfg, cons, J, x, dt):
+def mesh3(cfg, cons, J, x, dt=0.0):
+    """(xdot, dtau, dt) as :func:`mesh`, in 3D."""
     N = cfg.nx * cfg.ny * cfg.nz
-    xdot, tau = np.zeros(3 * N), np.zeros(1)
+    xdot, tau, dto = np.zeros(3 * N), np.zeros(1), np.zeros(1)
     st = lib().oref3_mesh(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(_vec(x, 3 * N)),
-                          float(dt), _p(xdot), _p(tau))
+                          float(dt), _p(xdot), _p(tau), _p(dto))
     if st != 0:
         raise RuntimeError("oracle mesh3: cons2prim failed")
-    return xdot.reshape(_shape3(cfg, 3)), tau[0]
+    return xdot.reshape(_shape3(cfg, 3)), tau[0], dto[0]
 
 
 def rk_step3(cfg, cons, J, x, dt=0.0):

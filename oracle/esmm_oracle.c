@@ -870,7 +870,7 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 5: adaptive mesh redistribution at t^n.
+/* Sec. 5: adaptive mesh redistribution at t^n, and the step size.
  *   monitor (eq. monitor)  omega = sqrt(1 + alpha |grad sigma| / max |grad sigma|)
  *   low-pass filter        omega <- sum_{j in {-1,0,1}^2} (1/2)^{|j1|+|j2|+2} omega_{i+j}
  *   Jacobi (mu sweeps)     x_i <- sum_k [(w_i + w_{i+e_k}) x_{i+e_k} + (w_i + w_{i-e_k}) x_{i-e_k}]
@@ -881,15 +881,27 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
  * |j1|+|j2|+2 (weights summing to 1, the 2D analogue of the printed 3D
  * filter); nodes on an outflow boundary stay fixed; Delta tau = clip of the
  * bounds to [0, 1]; the neighbour in each bound is along the direction of the
- * coordinate that moves (the printed "(x_1)" read as x_k).                  */
+ * coordinate that moves (the printed "(x_1)" read as x_k).
+ *
+ * Step size (eq. cfl, whose spectral radius includes the temporal metric,
+ * i.e. the mesh velocity).  The displacement of the step, d = Delta tau
+ * (x^[mu] - x^n), does not depend on dt, and its Courant number is
+ *   C_m = sum_k max_i |d_i . (J xi_k,x)_i| / J_i.
+ * Reading: Delta tau is also capped so that C_m <= CFL/2, and then
+ *   dt = (CFL - C_m) / sum_k max_i rho_{k,i}   (static-mesh radius),
+ * so that by the triangle inequality dt sum_k max_i rho_{k,i}(xdot) <= CFL
+ * holds with xdot = d/dt.  A given dt > 0 is used as is (Delta tau capped
+ * the same way).  *dt_out receives the step.                                */
 int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
-              const double *x, double dt, double *xdot, double *dtau)
+              const double *x, double dt, double *xdot, double *dtau, double *dt_out)
 {
     int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
     if (!c->move_mesh) {
         for (int a = 0; a < 2 * N; ++a) xdot[a] = 0.0;
         if (dtau) *dtau = 0.0;
-        return 0;
+        if (!(dt > 0.0)) status |= oref_cfl_dt(c, cons, J, x, &dt);
+        if (dt_out) *dt_out = dt;
+        return status;
     }
     double *sig = (double *)malloc(sizeof(double) * N);
     double *om = (double *)malloc(sizeof(double) * N);
@@ -968,8 +980,29 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
             }
         }
     if (tau < 0.0) tau = 0.0;
+    /* mesh Courant number of the full displacement x^[mu] - x^n */
+    double cm[2] = {0.0, 0.0};
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int id = j * nx + i;
+            double M[2][2];
+            node_metrics(c, x, i, j, M);
+            double d0 = X[id] - x[id], d1 = X[N + id] - x[N + id];
+            for (int k = 0; k < 2; ++k) {
+                double r = fabs(d0 * M[k][0] + d1 * M[k][1]) / J[id];
+                if (r > cm[k]) cm[k] = r;
+            }
+        }
+    double C1 = cm[0] + cm[1];
+    if (C1 > 0.0 && tau * C1 > 0.5 * c->cfl) tau = 0.5 * c->cfl / C1;
+    if (!(dt > 0.0)) {
+        double dts;
+        status |= oref_cfl_dt(c, cons, J, x, &dts);
+        dt = dts * (1.0 - tau * C1 / c->cfl);
+    }
     for (int a = 0; a < 2 * N; ++a) xdot[a] = tau * (X[a] - x[a]) / dt;
     if (dtau) *dtau = tau;
+    if (dt_out) *dt_out = dt;
     free(sig);
     free(om);
     free(om2);
@@ -988,7 +1021,6 @@ int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
                  double dt, double *dt_used)
 {
     int N = c->nx * c->ny, nv = nvar(c), status = 0;
-    if (!(dt > 0.0)) status |= oref_cfl_dt(c, cons, J, x, &dt);
     double *xdot = (double *)calloc(2 * (size_t)N, sizeof(double));
     double *c1 = (double *)malloc(sizeof(double) * nv * N);
     double *c2 = (double *)malloc(sizeof(double) * nv * N);
@@ -999,7 +1031,7 @@ int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
     double *L = (double *)malloc(sizeof(double) * nv * N);
     double *LJ = (double *)malloc(sizeof(double) * N);
     double dtau = 0.0;
-    status |= oref_mesh(c, cons, J, x, dt, xdot, &dtau);
+    status |= oref_mesh(c, cons, J, x, dt, xdot, &dtau, &dt);
 
     status |= oref_rhs(c, cons, J, x, xdot, L, LJ);
     for (int a = 0; a < nv * N; ++a) c1[a] = cons[a] + dt * L[a];

@@ -88,9 +88,11 @@ int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
 int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
                 const double *x, double *dt);
 
-/* Sec. 5 mesh redistribution: xdot from the state at t^n and dt^n. */
+/* Sec. 5 mesh redistribution and the step: xdot from the state at t^n; dt > 0
+ * is used as given, dt <= 0 selects the CFL step with the mesh motion
+ * included (written to *dt_out). */
 int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
-              const double *x, double dt, double *xdot, double *dtau);
+              const double *x, double dt, double *xdot, double *dtau, double *dt_out);
 
 /* One SSP-RK3 step of (cons, J, x) in place; dt <= 0 selects the CFL step. */
 int oref_rk_step(const oref_cfg *c, double *cons, double *J, double *x,
@@ -158,7 +160,7 @@ int oref3_rhs(const oref3_cfg *c, const double *cons, const double *J, const dou
               const double *xdot, double *dcons, double *dJ);
 int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const double *x, double *dt);
 int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
-               double *xdot, double *dtau);
+               double *xdot, double *dtau, double *dt_out);
 int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used);
 int oref3_totals(const oref3_cfg *c, const double *cons, const double *J, const double *dcons,
                  const double *dJ, double *out);

@@ -497,14 +497,16 @@ int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const 
  * Readings as in 2D (central |grad sigma| in index space, fixed outflow
  * boundary nodes, "(x_1)" read as x_k).                                     */
 int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
-               double *xdot, double *dtau)
+               double *xdot, double *dtau, double *dt_out)
 {
     long N = (long)c->nx * c->ny * c->nz;
     int status = 0;
     if (!c->move_mesh) {
         for (long a = 0; a < 3 * N; ++a) xdot[a] = 0.0;
         if (dtau) *dtau = 0.0;
-        return 0;
+        if (!(dt > 0.0)) status |= oref3_cfl_dt(c, cons, J, x, &dt);
+        if (dt_out) *dt_out = dt;
+        return status;
     }
     double *sig = (double *)malloc(sizeof(double) * N);
     double *om = (double *)malloc(sizeof(double) * N);
@@ -602,8 +604,30 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
                 }
             }
     if (tau < 0.0) tau = 0.0;
+    /* step size with the mesh motion included (the 2D reading, three directions) */
+    double cm[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                long id = ((long)k * c->ny + j) * c->nx + i;
+                double M[3][3];
+                node_metrics3(c, x, i, j, k, M);
+                double dd[3] = {X[id] - x[id], X[N + id] - x[N + id], X[2 * N + id] - x[2 * N + id]};
+                for (int d = 0; d < 3; ++d) {
+                    double r = fabs(dd[0] * M[d][0] + dd[1] * M[d][1] + dd[2] * M[d][2]) / J[id];
+                    if (r > cm[d]) cm[d] = r;
+                }
+            }
+    double C1 = cm[0] + cm[1] + cm[2];
+    if (C1 > 0.0 && tau * C1 > 0.5 * c->cfl) tau = 0.5 * c->cfl / C1;
+    if (!(dt > 0.0)) {
+        double dts;
+        status |= oref3_cfl_dt(c, cons, J, x, &dts);
+        dt = dts * (1.0 - tau * C1 / c->cfl);
+    }
     for (long a = 0; a < 3 * N; ++a) xdot[a] = tau * (X[a] - x[a]) / dt;
     if (dtau) *dtau = tau;
+    if (dt_out) *dt_out = dt;
     free(sig);
     free(om);
     free(om2);
@@ -617,13 +641,12 @@ int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double
 {
     long N = (long)c->nx * c->ny * c->nz;
     int status = 0;
-    if (!(dt > 0.0)) status |= oref3_cfl_dt(c, cons, J, x, &dt);
     double *xdot = (double *)calloc(3 * (size_t)N, sizeof(double));
     double *c1 = (double *)malloc(sizeof(double) * 8 * N), *c2 = (double *)malloc(sizeof(double) * 8 * N);
     double *J1 = (double *)malloc(sizeof(double) * N), *J2 = (double *)malloc(sizeof(double) * N);
     double *x1 = (double *)malloc(sizeof(double) * 3 * N), *x2 = (double *)malloc(sizeof(double) * 3 * N);
     double *L = (double *)malloc(sizeof(double) * 8 * N), *LJ = (double *)malloc(sizeof(double) * N);
-    status |= oref3_mesh(c, cons, J, x, dt, xdot, NULL);
+    status |= oref3_mesh(c, cons, J, x, dt, xdot, NULL, &dt);
     status |= oref3_rhs(c, cons, J, x, xdot, L, LJ);
     for (long a = 0; a < 8 * N; ++a) c1[a] = cons[a] + dt * L[a];
     for (long a = 0; a < N; ++a) J1[a] = J[a] + dt * LJ[a];

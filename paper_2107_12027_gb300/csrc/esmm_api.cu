@@ -314,16 +314,21 @@ void update(esmm_grid *g, double *dcons, double *dJ, const double *cn, const dou
 
 unsigned nprob_blocks(const esmm_grid *g) { return nblk(g->nprob, 128); }
 
-// dt of the step into dt_dev (per problem); requires g->q of the state with a
-// static mesh and the reduction slots reset
+// static spectral radius of the state (when dt is to come from eq. cfl);
+// requires g->q of the state with a static mesh and the slots reset
+void step_radius(esmm_grid *g, double dt)
+{
+    if (dt > 0.0) return;
+    Prof pr_(g, ESMM_KIND_OTHER);
+    LaunchDom L = dom(g, D_NODE);
+    if (g->phys == ESMM_RMHD) launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->st);
+    else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red);
+}
+
+// the step (and the capped mesh limiter) into dt_dev / slot 1, after the
+// radius and (when the mesh moves) the mesh chain up to k_mesh_tau
 void step_dt(esmm_grid *g, double dt)
 {
-    if (!(dt > 0.0)) {
-        Prof pr_(g, ESMM_KIND_OTHER);
-        LaunchDom L = dom(g, D_NODE);
-        if (g->phys == ESMM_RMHD) launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->st);
-        else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red);
-    }
     Prof pr_(g, ESMM_KIND_OTHER);
     k_dt<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->prm.cfl, dt, g->red, g->dt_dev);
 }
@@ -334,10 +339,13 @@ void red_init(esmm_grid *g)
     k_red_init<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->red);
 }
 
-// mesh velocity of the step into g->xdot; requires g->q of the state and dt_dev
-int mesh_core(esmm_grid *g)
+// The step: mesh target and limiter (when the mesh moves), dt (k_dt) and the
+// mesh velocity into g->xdot.  Requires g->q of the state, the slots reset
+// and the radius (step_radius) when dt <= 0.
+int mesh_core(esmm_grid *g, double dt)
 {
     if (!g->prm.move_mesh) {
+        step_dt(g, dt);
         if (!g->xdot_zero) {
             CK(cudaMemsetAsync(g->xdot, 0, sizeof(double) * 2 * g->Ntot, g->st));
             g->xdot_zero = 1;
@@ -369,8 +377,9 @@ int mesh_core(esmm_grid *g)
     }
     {
         Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_tau<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, src, g->red);
+        k_mesh_tau<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, src, g->q, g->J, g->red);
     }
+    step_dt(g, dt);
     {
         Prof pr_(g, ESMM_KIND_MESH);
         k_mesh_xdot<<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, g->x, src, g->red, g->dt_dev, g->xdot);
@@ -388,8 +397,8 @@ int rk_step_async(esmm_grid *g, double dt)
     // the state's node data with a static mesh: CFL step and monitor (Sec. 5)
     node(g, g->cons, g->J, g->x, nullptr, g->pg[0], g->pg[1]);
     red_init(g);
-    step_dt(g, dt);
-    if ((rc = mesh_core(g))) return rc;
+    step_radius(g, dt);
+    if ((rc = mesh_core(g, dt))) return rc;
     // stage 1: y1 = y^n + dt L(y^n); only the temporal metrics change
     {
         Prof pr_(g, ESMM_KIND_NODE);
@@ -1148,14 +1157,15 @@ int esmm_cfl_dt(esmm_grid *g, double *dt)
     if ((rc = ensure_doms(g))) return rc;
     node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     red_init(g);
-    step_dt(g, 0.0);
+    step_radius(g, 0.0);
+    step_dt(g, 0.0);   // slots 4, 5 are zero: the static-mesh step
     CK(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     *dt = g->pin[0];
     return check_c2p(g);
 }
 
-int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, int mem)
+int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, double *dt_used, int mem)
 {
     if (!g || g->nprob != 1) return ESMM_ERR_ARG;
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
@@ -1163,12 +1173,14 @@ int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, 
     if ((rc = ensure_doms(g))) return rc;
     node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     red_init(g);
-    step_dt(g, dt);
-    if ((rc = mesh_core(g))) return rc;
+    step_radius(g, dt);
+    if ((rc = mesh_core(g, dt))) return rc;
     if (xdot && (rc = copy_out(g, xdot, g->xdot, 2 * (size_t)g->Ntot, mem))) return rc;
     CK(cudaMemcpyAsync(g->pin, g->red + 1, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(g->pin + 1, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     if (dtau) *dtau = g->prm.move_mesh ? g->pin[0] : 0.0;
+    if (dt_used) *dt_used = g->pin[1];
     return check_c2p(g);
 }
 

@@ -226,16 +226,26 @@ __global__ void k_red_init(int nprob, unsigned long long *red)
     red[NRED * b + 1] = (unsigned long long)__double_as_longlong(1.0);
     red[NRED * b + 2] = 0ull;
     red[NRED * b + 3] = 0ull;
+    red[NRED * b + 4] = 0ull;
+    red[NRED * b + 5] = 0ull;
 }
 
-// dt of each problem: the given step, or CFL / sum_k max_i rho_k (eq. cfl)
-__global__ void k_dt(int nprob, double cfl, double dt_fixed, const unsigned long long *red, double *dt_dev)
+// Step of each problem (eq. cfl with the mesh velocity in the spectral
+// radius): the mesh limiter Delta tau is capped so that the displacement's
+// Courant number C_m = Delta tau sum_k max |d.(J xi_k,x)|/J stays <= CFL/2,
+// then dt = (CFL - C_m) / sum_k max rho_k (static radius), or the given step.
+// The capped Delta tau goes back to slot 1.  Without mesh motion C_m = 0.
+__global__ void k_dt(int nprob, double cfl, double dt_fixed, unsigned long long *red, double *dt_dev)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nprob) return;
-    dt_dev[b] = dt_fixed > 0.0
-                    ? dt_fixed
-                    : cfl / (bits_to_double(red[NRED * b + 2]) + bits_to_double(red[NRED * b + 3]));
+    unsigned long long *r = red + (long long)NRED * b;
+    double C1 = bits_to_double(r[4]) + bits_to_double(r[5]);
+    double tau = bits_to_double(r[1]);
+    if (C1 > 0.0 && tau * C1 > 0.5 * cfl) tau = 0.5 * cfl / C1;
+    r[1] = (unsigned long long)__double_as_longlong(tau);
+    dt_dev[b] = dt_fixed > 0.0 ? dt_fixed
+                               : cfl / (bits_to_double(r[2]) + bits_to_double(r[3])) * (1.0 - tau * C1 / cfl);
 }
 
 __global__ void k_time(int nprob, const double *dt_dev, double *t_dev)
@@ -335,9 +345,11 @@ __global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ om, const d
 }
 
 // movement limiter: Delta tau = min over nodes and directions of half the
-// neighbour spacing over the displacement toward it, clipped to [0, 1]
+// neighbour spacing over the displacement toward it, clipped to [0, 1]; and
+// the displacement's Courant number max |d.(J xi_k,x)|/J per direction (the
+// node metrics of x^n in q, J of the state)
 __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const double *__restrict__ X,
-                           unsigned long long *red)
+                           const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red)
 {
     ProbDesc D;
     long long lb;
@@ -346,11 +358,15 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const doubl
     long long id = lb * blockDim.x + threadIdx.x;
     x += 2 * D.on;
     X += 2 * D.on;
-    double tau = 1.0;
+    J += D.on;
+    q += (long long)NQ * D.op;
+    double tau = 1.0, cm[2] = {0.0, 0.0};
     if (id < g.N) {
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        double dd[2];
         for (int k = 0; k < 2; ++k) {
             double d = X[k * g.N + id] - x[k * g.N + id];
+            dd[k] = d;
             int di = k == 0, dj = k == 1;
             double bnd = 1.0;
             if (d < 0.0) bnd = -(x[k * g.N + id] - mesh_at(g, x, i - di, j - dj, k, 1)) / (2.0 * d);
@@ -358,9 +374,17 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const doubl
             tau = fmin(tau, bnd);
         }
         tau = fmax(tau, 0.0);
+        long long c = pidx(g, i, j);
+        double iJ = 1.0 / J[id];
+        for (int k = 0; k < 2; ++k)
+            cm[k] = fabs(dd[0] * q[(Q_M00 + 2 * k) * g.P + c] + dd[1] * q[(Q_M01 + 2 * k) * g.P + c]) * iJ;
     }
     double m = block_reduce<1>(tau);
     if (threadIdx.x == 0) atomic_min_nonneg(red + (long long)NRED * b + 1, m);
+    for (int k = 0; k < 2; ++k) {
+        double mk = block_reduce<0>(cm[k]);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b + 4 + k, mk);
+    }
 }
 
 // xdot = Delta tau (x^[mu] - x^n) / dt (over 2 N values per problem)

@@ -57,7 +57,8 @@ __device__ __forceinline__ void atomic_min_nonneg(unsigned long long *a, double 
 __device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
 
 // per-problem reduction slots: [0] max |grad sigma|, [1] Delta tau (min),
-// [2], [3] max spectral radius per direction
-constexpr int NRED = 4;
+// [2], [3] max spectral radius per direction, [4], [5] max mesh Courant
+// number per direction of the full displacement x^[mu] - x^n
+constexpr int NRED = 6;
 
 }  // namespace esmm

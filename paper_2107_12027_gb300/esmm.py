@@ -71,7 +71,7 @@ def lib():
             "esmm_get_params": [vp, ctypes.POINTER(Params)], "esmm_state_set": [vp, vp, vp, i],
             "esmm_state_set_cons": [vp, vp, vp, vp, d, i], "esmm_state_get": [vp, i, vp, i],
             "esmm_get_time": [vp, dp], "esmm_rhs": [vp, vp, vp, vp, vp, vp, vp, i],
-            "esmm_cfl_dt": [vp, dp], "esmm_mesh_redistribute": [vp, d, vp, dp, i],
+            "esmm_cfl_dt": [vp, dp], "esmm_mesh_redistribute": [vp, d, vp, dp, dp, i],
             "esmm_rk_step": [vp, d, dp], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
             "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
             "esmm_profile": [vp, i],
@@ -263,11 +263,13 @@ class Grid:
         return dt.value
 
     def mesh_redistribute(self, dt=0.0):
+        """(xdot, dtau, dt): the mesh velocity, limiter value and step
+        (dt <= 0: the CFL step with the mesh motion included)."""
         xdot = np.empty((2, self.ny, self.nx))
-        tau = ctypes.c_double()
+        tau, dtu = ctypes.c_double(), ctypes.c_double()
         self._check(lib().esmm_mesh_redistribute(self.h, float(dt), ctypes.c_void_p(xdot.ctypes.data),
-                                                  ctypes.byref(tau), MEM_HOST))
-        return xdot, tau.value
+                                                  ctypes.byref(tau), ctypes.byref(dtu), MEM_HOST))
+        return xdot, tau.value, dtu.value
 
     def rk_step(self, dt=0.0, sync=True):
         """One SSP-RK3 step; returns the step used when sync (else None)."""

@@ -196,24 +196,31 @@ def quadrant_riemann_mhd(x, states, split=(0.0, 0.0)):
     return np.ascontiguousarray(prim)
 
 
-def rotor(x, rho_in=10.0, omega=9.95, r0=0.1, rho_out=1.0, p=1.0, Bx=1.0):
+def rotor(x, rho_in=10.0, omega=9.95, r0=0.1, rho_out=1.0, p=1.0, Bx=1.0, r1=None):
     """The rotor: a disk r < r0 of density rho_in spinning rigidly at angular
     speed omega (|v| <= omega r0 = 0.995), background rho_out at rest,
-    uniform pressure p and field B = (Bx, 0, 0)."""
+    uniform pressure p and field B = (Bx, 0, 0).  With r1 > r0, density and
+    angular speed fall linearly from the disk values at r0 to the background
+    at r1 (a tapered rotor)."""
     X, Y = x[0], x[1]
-    inside = (X * X + Y * Y) < r0 * r0
+    r = np.sqrt(X * X + Y * Y)
+    if r1 is None:
+        f = (r < r0).astype(float)
+    else:
+        f = np.clip((r1 - r) / (r1 - r0), 0.0, 1.0)
     z = 0 * X
-    rho = np.where(inside, rho_in, rho_out)
-    vx = np.where(inside, -omega * Y, 0.0)
-    vy = np.where(inside, omega * X, 0.0)
+    rho = rho_out + f * (rho_in - rho_out)
+    om = f * omega * np.where(r < r0, 1.0, r0 / np.maximum(r, 1e-300))   # |v| continuous, <= omega r0
+    vx = -om * Y
+    vy = om * X
     return np.ascontiguousarray(np.stack([rho, vx, vy, z, p + z, Bx + z, z, z]))
 
 
-def rotor_config(n=512):
+def rotor_config(n=512, taper=None):
     """2D RMHD rotor on [-0.5,0.5]^2 with outflow boundaries, n x n nodes,
-    Gamma = 4/3 (the 512^2 RMHD workload)."""
+    Gamma = 4/3 (the 512^2 RMHD workload); taper = r1 for the tapered disk."""
     x = uniform_mesh(n, n, (-0.5, -0.5), (0.5, 0.5), (False, False))
-    return x, rotor(x)
+    return x, rotor(x, r1=taper)
 
 
 # ---- 3D (RMHD) ----------------------------------------------------------------

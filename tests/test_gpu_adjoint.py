@@ -2,8 +2,8 @@
 
   * (d rhs/d cons)^T mu from the adjoint kernels against central differences
     of the GPU right-hand side and of the oracle's, in random directions;
-  * the gradient of a final-time functional (integrated J D over a sub-box)
-    with respect to the initial pressure, through several recorded SSP-RK3
+  * the gradient of a final-time functional (integrated J (D + E) over a
+    sub-box) with respect to the initial pressure, through several recorded SSP-RK3
     steps with per-step checkpoints, against central differences of the
     oracle's steps with the recorded mesh velocities and time steps.  The EC
     scheme's map is smooth and is held to 1e-6.  The ES scheme's is not
@@ -51,10 +51,16 @@ def test_rhs_vjp_against_finite_differences(p, w):
             assert abs(adj - fd_ora) <= 1e-6 * abs(fd_ora), (trial, adj, fd_ora)
 
 
-def _functional_weights(x, box):
+def _functional_weights(x, box, energy=False):
+    """Weights of a functional sum w . cons: J D over the box (and J E with
+    energy=True, whose pressure derivative is O(1), so that central
+    differences resolve it after steps short enough to leave the mass almost
+    unchanged)."""
     w = np.zeros((4,) + x.shape[1:])
     inside = (x[0] >= box[0]) & (x[0] <= box[1]) & (x[1] >= box[2]) & (x[1] <= box[3])
     w[0][inside] = 1.0
+    if energy:
+        w[3][inside] = 1.0
     return w
 
 
@@ -80,7 +86,7 @@ def test_multistep_adjoint_against_oracle_fd(case, w, tol):
         g.adjoint_record(steps)
         dts = g.adjoint_steps()
         xdots = [g.adjoint_checkpoint(k, esmm.GET_XDOT) for k in range(steps)]
-        wts = _functional_weights(g.state_get(esmm.GET_X), box)
+        wts = _functional_weights(g.state_get(esmm.GET_X), box, energy=True)
         _, lam_prim = g.adjoint_vjp(wts)
         # the functional through the recorded map, on the oracle
         cfg = oracle.make_cfg(n, n, p=2, w=w, alpha=200.0, **ocfg)

@@ -118,12 +118,12 @@ def test_mesh_redistribution_parity(case):
         kw = dict(alpha=20.0, monitor=oracle.MONITOR_RHO)
     cfg = _cfg(n, n, bc, lo, hi, 2, 5, **kw)
     cons, J = oracle.init_state(cfg, prim, x)
-    dt = oracle.cfl_dt(cfg, cons, J, x)
-    xd_ref, tau_ref = oracle.mesh(cfg, cons, J, x, dt)
+    xd_ref, tau_ref, dt_ref = oracle.mesh(cfg, cons, J, x)
     with _grid(n, n, bc, lo, hi, 2, 5, **kw) as g:
         g.state_set(prim, x)
-        xd, tau = g.mesh_redistribute(0.0)
+        xd, tau, dt = g.mesh_redistribute(0.0)
     assert abs(tau - tau_ref) <= 1e-13 * max(tau_ref, 1e-300)
+    assert abs(dt - dt_ref) <= 1e-13 * dt_ref
     assert _rel(xd, xd_ref) < 1e-11
 
 

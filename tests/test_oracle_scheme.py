@@ -133,7 +133,7 @@ def test_mesh_uniform_monitor_keeps_uniform_mesh():
     prim = np.broadcast_to(np.array([1.0, 0.1, 0.2, 1.0])[:, None, None], (4, n, n)).copy()
     cfg = oracle.make_cfg(n, n)
     cons, J = oracle.init_state(cfg, prim, x)
-    xdot, tau = oracle.mesh(cfg, cons, J, x, 1e-3)
+    xdot, tau, _ = oracle.mesh(cfg, cons, J, x, 1e-3)
     assert np.abs(xdot).max() < 1e-11
 
 
@@ -142,8 +142,7 @@ def test_mesh_limiter_and_no_tangling():
     x, prim = wl.riemann_config(n)
     cfg = oracle.make_cfg(n, n, bc=(oracle.OUTFLOW, oracle.OUTFLOW), alpha=1200.0)
     cons, J = oracle.init_state(cfg, prim, x)
-    dt = oracle.cfl_dt(cfg, cons, J, x)
-    xdot, tau = oracle.mesh(cfg, cons, J, x, dt)
+    xdot, tau, dt = oracle.mesh(cfg, cons, J, x)
     assert 0 < tau <= 1
     move = dt * xdot
     assert np.abs(move).max() > 1e-4
@@ -158,6 +157,38 @@ def test_mesh_limiter_and_no_tangling():
     assert np.all(my <= 0.5 * dyp[1:, :] + 1e-15) and np.all(-my <= 0.5 * dyp[:-1, :] + 1e-15)
     _, J1 = oracle.metrics(cfg, x + move)
     assert J1.min() > 0
+
+
+def test_step_satisfies_cfl_with_mesh_velocity():
+    # eq. cfl: dt sum_k max_i rho_{k,i} <= CFL with rho the spectral radius of
+    # d(F_k)/d(JU) including the temporal metric J xi_k,t = -xdot . (J xi_k,x);
+    # the mesh part of it stays below CFL/2
+    n = 24
+    x, prim = wl.riemann_config(n)
+    cfg = oracle.make_cfg(n, n, bc=(oracle.OUTFLOW, oracle.OUTFLOW), period=(2.0, 2.0), alpha=1200.0)
+    cons, J = oracle.init_state(cfg, prim, x)
+    xdot, tau, dt = oracle.mesh(cfg, cons, J, x)
+    m, _ = oracle.metrics(cfg, x)
+    pr, _ = oracle.state_prim(cfg, cons, J)
+    rmax, cmesh = [0.0, 0.0], [0.0, 0.0]
+    for j in range(n):
+        for i in range(n):
+            for k in range(2):
+                mx, my = m[2 * k, j, i], m[2 * k + 1, j, i]
+                L = np.hypot(mx, my)
+                nx, ny = mx / L, my / L
+                w = pr[:, j, i]
+                wr = [w[0], nx * w[1] + ny * w[2], -ny * w[1] + nx * w[2], w[3]]
+                lam, _ = oracle.eigen(cfg.gamma, wr)
+                jt = -(xdot[0, j, i] * mx + xdot[1, j, i] * my)
+                rmax[k] = max(rmax[k], np.abs(jt + L * lam).max() / J[j, i])
+                cmesh[k] = max(cmesh[k], abs(jt) * dt / J[j, i])
+    assert tau > 0 and np.abs(xdot).max() > 0
+    assert dt * sum(rmax) <= cfg.cfl * (1 + 1e-12)
+    assert sum(cmesh) <= 0.5 * cfg.cfl * (1 + 1e-12)
+    # with a static mesh the step is the static-radius CFL step
+    cfg0 = oracle.make_cfg(n, n, bc=(oracle.OUTFLOW, oracle.OUTFLOW), period=(2.0, 2.0), move_mesh=0)
+    assert oracle.mesh(cfg0, cons, J, x)[2] == oracle.cfl_dt(cfg0, cons, J, x)
 
 
 # ------------------------------------------------------------------- RK steps
@@ -241,8 +272,7 @@ def test_rk_step_given_matches_rk_step_with_its_own_mesh_velocity():
     x, prim = wl.sine_config(n)
     cfg = oracle.make_cfg(n, n, monitor=oracle.MONITOR_RHO, alpha=20.0)
     cons, J = oracle.init_state(cfg, prim, x)
-    dt = oracle.cfl_dt(cfg, cons, J, x)
-    xdot, _ = oracle.mesh(cfg, cons, J, x, dt)
+    xdot, _, dt = oracle.mesh(cfg, cons, J, x)
     a = oracle.rk_step(cfg, cons, J, x, dt)
     b = oracle.rk_step_given(cfg, cons, J, x, xdot, dt)
     for u, v in zip(a[:3], b):
