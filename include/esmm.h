@@ -13,12 +13,14 @@
  *   - Arrays are structure of arrays, FP64, node-ordered with i (the xi
  *     index, along x) fastest: element (c, j, i) of an array with C
  *     components is at c*N + j*nx + i, N = nx*ny.  No ghost nodes.
+ *     3D grids (dim = 3, RMHD): element (c, k, j, i) at c*N + (k*ny + j)*nx + i,
+ *     N = nx*ny*nz, and x, xdot have 3 components.
  *       prim  [m][N]  RHD (m = 4): rho, v_x, v_y, p
  *                     RMHD (m = 8): rho, v_1, v_2, v_3, p, B_1, B_2, B_3
  *       cons  [m][N]  the curvilinear unknown J*U, U = (D, m_x, m_y, E)
  *                     (RMHD: U = (D, m_1, m_2, m_3, E, B_1, B_2, B_3))
  *       J     [N]     the evolved Jacobian (volume) of each node
- *       x     [2][N]  physical node coordinates (x, y)
+ *       x     [d][N]  physical node coordinates (x, y[, z])
  *       xdot  [2][N]  mesh velocity
  *   - The computational coordinates are node indices (Delta xi_k = 1), so
  *     metrics, J and fluxes are per unit index.
@@ -84,8 +86,12 @@ typedef struct {
     int precision;     /* ESMM_FP64 or ESMM_MIXED                     [FP64] */
 } esmm_params;
 
-/* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim must be 2, phys
- * ESMM_RHD or ESMM_RMHD, bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4).  A periodic
+/* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim 2, phys ESMM_RHD or
+ * ESMM_RMHD), or of n[0] x n[1] x n[2] nodes (dim 3, phys ESMM_RMHD: the
+ * nested metrics of eq. SCLCoeff, FP64; defaults Gamma = 4/3, CFL 0.3,
+ * alpha = 800), bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4.  3D grids
+ * accept the single-problem calls; batches, the tuner, the adjoint and
+ * profiling return ESMM_ERR_ARG for them.  A periodic
  * direction has n[k] distinct nodes with spacing (hi-lo)/n[k]; an outflow
  * direction has nodes on both ends.  stream is a cudaStream_t (NULL: the
  * legacy default stream) on the current device; the grid stays on that device.

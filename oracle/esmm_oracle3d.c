@@ -251,7 +251,10 @@ static void frame3(const double n[3], double T[3][3])
 
 /* Reading: the tangential axes of T_0 are then turned about n so that the
  * first lies along the tangential magnetic field of the state w (along the
- * tangential velocity when |B_t| <= 1e-10 |B|; unchanged when both vanish).
+ * tangential velocity when |B_t| <= 1e-10 max(1, |B|); unchanged when also
+ * |v_t| <= 1e-10, c = 1).  The thresholds are absolute so that a field or a
+ * velocity that is zero up to rounding (a gas at rest, a symmetry plane) does
+ * not orient the frame.
  * The paper's theta, phi fix them by the coordinate axes, and the
  * characteristic split of degenerate waves (and, at a normal along x_3,
  * rounding noise in theta) would then depend on the coordinates; aligned
@@ -262,12 +265,11 @@ static void align3(double T[3][3], const double *w)
     double b2 = T[2][0] * w[5] + T[2][1] * w[6] + T[2][2] * w[7];
     double B2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
     double t2 = b1 * b1 + b2 * b2;
-    if (!(B2 > 0.0) || !(t2 > 1.0e-20 * B2)) {
+    if (!(t2 > 1.0e-20 * (1.0 + B2))) {
         b1 = T[1][0] * w[1] + T[1][1] * w[2] + T[1][2] * w[3];
         b2 = T[2][0] * w[1] + T[2][1] * w[2] + T[2][2] * w[3];
-        double v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
         t2 = b1 * b1 + b2 * b2;
-        if (!(v2 > 0.0) || !(t2 > 1.0e-20 * v2)) return;
+        if (!(t2 > 1.0e-20)) return;
     }
     double tn = sqrt(t2), c = b1 / tn, s = b2 / tn;
     for (int q = 0; q < 3; ++q) {

@@ -1,0 +1,1236 @@
+// esmm_3d.cu -- the 3D RMHD path (Duan & Tang, arXiv 2107.12027): nested
+// conservative metrics (eq. SCLCoeff), the ES interface flux with the
+// Godunov-Powell source on a moving curvilinear mesh, the CFL step with the
+// mesh velocity, the 3D mesh redistribution (Sec. 5) and SSP-RK3, behind the
+// esmm3_* functions that the C ABI dispatches to for dim = 3 grids.
+//
+// Layout: nodes (i, j, k), i fastest, N = nx ny nz; node data on the padded
+// grid (n + 2 GH per direction), NQ3 fields per padded node.  Single problems.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "esmm.h"
+#include "esmm_3d.h"
+#include "esmm_mhd.cuh"
+#include "esmm_reduce.cuh"
+
+namespace esmm {
+namespace d3 {
+
+struct Geom3 {
+    int n[3];
+    int pd[3];
+    long long P, N;
+    int bc[3];
+    double per[3];
+};
+
+// node data fields (FP64, padded grid)
+enum {
+    F_RHO = 0, F_P, F_BETA, F_U0, F_U1, F_U2, F_W, F_LNR, F_LNB, F_B0, F_B1, F_B2,
+    F_M = 12,      // 9 spatial metrics M[k][j] = J d xi_k / d x_j at F_M + 3k + j
+    F_MT = 21,     // 3 temporal metrics J d xi_k / dt
+    NQ3 = 24
+};
+constexpr int NF3 = 10;     // per direction and padded node: F[8], metric flux, B~
+constexpr int NR3 = 8;      // reduction slots: grad, tau, radius[3], mesh Courant[3]
+
+__host__ __device__ __forceinline__ long long pidx3(const Geom3 &g, int i, int j, int k)
+{
+    return ((long long)(k + GH) * g.pd[1] + (j + GH)) * g.pd[0] + (i + GH);
+}
+
+__device__ __forceinline__ long long data_src3(const Geom3 &g, int i, int j, int k)
+{
+    int ii = g.bc[0] == 0 ? wrapi(i, g.n[0]) : clampi(i, 0, g.n[0] - 1);
+    int jj = g.bc[1] == 0 ? wrapi(j, g.n[1]) : clampi(j, 0, g.n[1] - 1);
+    int kk = g.bc[2] == 0 ? wrapi(k, g.n[2]) : clampi(k, 0, g.n[2] - 1);
+    return ((long long)kk * g.n[1] + jj) * g.n[0] + ii;
+}
+
+// Boundary-mapped mesh value, one direction at a time (2, then 1, then 0):
+// periodic wrap plus the period for the coordinate along that direction
+// (shift = 1), or linear extrapolation of the two nodes next to the boundary.
+__device__ __forceinline__ double mesh_d0(const Geom3 &g, const double *a, int comp, int i, int j, int k, int shift)
+{
+    const double *row = a + (long long)comp * g.N + ((long long)k * g.n[1] + j) * g.n[0];
+    int n = g.n[0];
+    if (g.bc[0] == 0) {
+        double s = (shift && comp == 0) ? floordivi(i, n) * g.per[0] : 0.0;
+        return row[wrapi(i, n)] + s;
+    }
+    if (i < 0) { double v0 = row[0], v1 = row[1]; return v0 + (double)(-i) * (v0 - v1); }
+    if (i > n - 1) { double v0 = row[n - 1], v1 = row[n - 2]; return v0 + (double)(i - (n - 1)) * (v0 - v1); }
+    return row[i];
+}
+
+__device__ __forceinline__ double mesh_d1(const Geom3 &g, const double *a, int comp, int i, int j, int k, int shift)
+{
+    int n = g.n[1];
+    if (g.bc[1] == 0) {
+        double s = (shift && comp == 1) ? floordivi(j, n) * g.per[1] : 0.0;
+        return mesh_d0(g, a, comp, i, wrapi(j, n), k, shift) + s;
+    }
+    if (j >= 0 && j <= n - 1) return mesh_d0(g, a, comp, i, j, k, shift);
+    int b0 = j < 0 ? 0 : n - 1, b1 = j < 0 ? 1 : n - 2;
+    double v0 = mesh_d0(g, a, comp, i, b0, k, shift), v1 = mesh_d0(g, a, comp, i, b1, k, shift);
+    double off = j < 0 ? (double)(-j) : (double)(j - (n - 1));
+    return v0 + off * (v0 - v1);
+}
+
+__device__ __forceinline__ double mesh3_at(const Geom3 &g, const double *a, int comp, int i, int j, int k, int shift)
+{
+    int n = g.n[2];
+    if (g.bc[2] == 0) {
+        double s = (shift && comp == 2) ? floordivi(k, n) * g.per[2] : 0.0;
+        return mesh_d1(g, a, comp, i, j, wrapi(k, n), shift) + s;
+    }
+    if (k >= 0 && k <= n - 1) return mesh_d1(g, a, comp, i, j, k, shift);
+    int b0 = k < 0 ? 0 : n - 1, b1 = k < 0 ? 1 : n - 2;
+    double v0 = mesh_d1(g, a, comp, i, j, b0, shift), v1 = mesh_d1(g, a, comp, i, j, b1, shift);
+    double off = k < 0 ? (double)(-k) : (double)(k - (n - 1));
+    return v0 + off * (v0 - v1);
+}
+
+template <int P> __device__ __forceinline__ constexpr double alpha3(int n)
+{
+    return P == 1 ? 1.0 : (P == 2 ? (n == 1 ? 4.0 / 3.0 : -1.0 / 6.0) : (n == 1 ? 1.5 : (n == 2 ? -0.3 : 1.0 / 30.0)));
+}
+
+__device__ __forceinline__ void step3(int i, int j, int k, int d, int s, int &a, int &b, int &c)
+{
+    a = i + (d == 0) * s;
+    b = j + (d == 1) * s;
+    c = k + (d == 2) * s;
+}
+
+// delta_d[x_comp] at (i, j, k)
+template <int P>
+__device__ __forceinline__ double delta_x3(const Geom3 &g, const double *x, int comp, int i, int j, int k, int d)
+{
+    double s = 0.0;
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        int a0, a1, a2, b0, b1, b2;
+        step3(i, j, k, d, n, a0, a1, a2);
+        step3(i, j, k, d, -n, b0, b1, b2);
+        s += 0.5 * alpha3<P>(n) * (mesh3_at(g, x, comp, a0, a1, a2, 1) - mesh3_at(g, x, comp, b0, b1, b2, 1));
+    }
+    return s;
+}
+
+// eq. SCLCoeff: M[k][j] = delta_{k2}[delta_{k1}[x_{j1}] x_{j2}] - delta_{k1}[delta_{k2}[x_{j1}] x_{j2}]
+template <int P>
+__device__ __forceinline__ double nested3(const Geom3 &g, const double *x, int d_out, int d_in, int ja, int jb, int i,
+                                          int j, int k)
+{
+    double s = 0.0;
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        int a0, a1, a2, b0, b1, b2;
+        step3(i, j, k, d_out, n, a0, a1, a2);
+        step3(i, j, k, d_out, -n, b0, b1, b2);
+        double fa = delta_x3<P>(g, x, ja, a0, a1, a2, d_in) * mesh3_at(g, x, jb, a0, a1, a2, 1);
+        double fb = delta_x3<P>(g, x, ja, b0, b1, b2, d_in) * mesh3_at(g, x, jb, b0, b1, b2, 1);
+        s += 0.5 * alpha3<P>(n) * (fa - fb);
+    }
+    return s;
+}
+
+template <int P>
+__device__ void metrics3(const Geom3 &g, const double *x, int i, int j, int k, double M[3][3])
+{
+#pragma unroll 1
+    for (int kk = 0; kk < 3; ++kk) {
+        int k1 = (kk + 1) % 3, k2 = (kk + 2) % 3;
+#pragma unroll 1
+        for (int jj = 0; jj < 3; ++jj) {
+            int j1 = (jj + 1) % 3, j2 = (jj + 2) % 3;
+            M[kk][jj] = nested3<P>(g, x, k2, k1, j1, j2, i, j, k) - nested3<P>(g, x, k1, k2, j1, j2, i, j, k);
+        }
+    }
+}
+
+// Sec. 4 rotation for the unit normal n (rows n, t1, t2; theta = 0 when the
+// x_1-x_2 part of n is below 1e-12), then turned about n so that t1 lies
+// along the tangential B of the state w (along the tangential v when
+// |B_t| <= 1e-10 max(1, |B|); unchanged when also |v_t| <= 1e-10, c = 1;
+// absolute thresholds, so that rounding noise in a field or velocity that
+// vanishes does not orient the frame).
+__device__ __forceinline__ void frame3(const double n[3], double T[3][3])
+{
+    double r = sqrt(n[0] * n[0] + n[1] * n[1]);
+    bool pole = r <= 1.0e-12;
+    double ct = pole ? 1.0 : n[0] / r, st = pole ? 0.0 : n[1] / r;
+    double cp = r, sp = n[2];
+    T[0][0] = cp * ct; T[0][1] = cp * st; T[0][2] = sp;
+    T[1][0] = -st;     T[1][1] = ct;      T[1][2] = 0.0;
+    T[2][0] = -sp * ct; T[2][1] = -sp * st; T[2][2] = cp;
+}
+
+__device__ __forceinline__ void align3(double T[3][3], const double w[8])
+{
+    double b1 = T[1][0] * w[5] + T[1][1] * w[6] + T[1][2] * w[7];
+    double b2 = T[2][0] * w[5] + T[2][1] * w[6] + T[2][2] * w[7];
+    double B2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+    double t2 = b1 * b1 + b2 * b2;
+    if (!(t2 > 1.0e-20 * (1.0 + B2))) {
+        b1 = T[1][0] * w[1] + T[1][1] * w[2] + T[1][2] * w[3];
+        b2 = T[2][0] * w[1] + T[2][1] * w[2] + T[2][2] * w[3];
+        t2 = b1 * b1 + b2 * b2;
+        if (!(t2 > 1.0e-20)) return;
+    }
+    double tn = sqrt(t2), c = b1 / tn, s = b2 / tn;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double a1 = T[1][q], a2 = T[2][q];
+        T[1][q] = c * a1 + s * a2;
+        T[2][q] = -s * a1 + c * a2;
+    }
+}
+
+__device__ __forceinline__ void rot3(const double T[3][3], const double *a, double *r)
+{
+    r[0] = a[0];
+    r[4] = a[4];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        r[1 + q] = T[q][0] * a[1] + T[q][1] * a[2] + T[q][2] * a[3];
+        r[5 + q] = T[q][0] * a[5] + T[q][1] * a[6] + T[q][2] * a[7];
+    }
+}
+
+__device__ __forceinline__ void unrot3(const double T[3][3], const double *r, double *a)
+{
+    a[0] = r[0];
+    a[4] = r[4];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        a[1 + q] = T[0][q] * r[1] + T[1][q] * r[2] + T[2][q] * r[3];
+        a[5 + q] = T[0][q] * r[5] + T[1][q] * r[6] + T[2][q] * r[7];
+    }
+}
+
+__device__ __forceinline__ NodeM load3(const double *__restrict__ q, long long P, long long c)
+{
+    NodeM v;
+    v.rho = q[F_RHO * P + c];
+    v.beta = q[F_BETA * P + c];
+    v.lnr = q[F_LNR * P + c];
+    v.lnb = q[F_LNB * P + c];
+    v.W = q[F_W * P + c];
+    v.u[0] = q[F_U0 * P + c];
+    v.u[1] = q[F_U1 * P + c];
+    v.u[2] = q[F_U2 * P + c];
+    v.B[0] = q[F_B0 * P + c];
+    v.B[1] = q[F_B1 * P + c];
+    v.B[2] = q[F_B2 * P + c];
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void k3_node(Geom3 g, double gam, const double *__restrict__ cons, const double *__restrict__ J,
+                        const double *__restrict__ x, const double *__restrict__ xdot,
+                        const double *__restrict__ zg_in, double *__restrict__ zg_out, double *__restrict__ q,
+                        int *__restrict__ status)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.P) return;
+    int I = (int)(t % g.pd[0]) - GH;
+    int Jn = (int)((t / g.pd[0]) % g.pd[1]) - GH;
+    int K = (int)(t / ((long long)g.pd[0] * g.pd[1])) - GH;
+    long long src = data_src3(g, I, Jn, K);
+    double iJ = 1.0 / J[src];
+    double U[8], w[8], Z;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) U[a] = cons[a * g.N + src] * iJ;
+    int st = cons2prim_mhd(gam, U, zg_in ? zg_in[src] : -1.0, w, Z);
+    bool interior = I >= 0 && I < g.n[0] && Jn >= 0 && Jn < g.n[1] && K >= 0 && K < g.n[2];
+    if (interior) {
+        if (st) atomicAdd(status, 1);
+        if (zg_out) zg_out[src] = Z;
+    }
+    double W = 1.0 / sqrt(1.0 - (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+    double beta = w[0] / w[4];
+    q[F_RHO * g.P + t] = w[0];
+    q[F_P * g.P + t] = w[4];
+    q[F_BETA * g.P + t] = beta;
+    q[F_U0 * g.P + t] = W * w[1];
+    q[F_U1 * g.P + t] = W * w[2];
+    q[F_U2 * g.P + t] = W * w[3];
+    q[F_W * g.P + t] = W;
+    q[F_LNR * g.P + t] = log(w[0]);
+    q[F_LNB * g.P + t] = log(beta);
+    q[F_B0 * g.P + t] = w[5];
+    q[F_B1 * g.P + t] = w[6];
+    q[F_B2 * g.P + t] = w[7];
+    double M[3][3];
+    metrics3<P>(g, x, I, Jn, K, M);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) q[(F_M + 3 * a + b) * g.P + t] = M[a][b];
+    double xd[3] = {0.0, 0.0, 0.0};
+    if (xdot)
+        for (int b = 0; b < 3; ++b) xd[b] = mesh3_at(g, xdot, b, I, Jn, K, 0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[(F_MT + a) * g.P + t] = -(xd[0] * M[a][0] + xd[1] * M[a][1] + xd[2] * M[a][2]);
+}
+
+__global__ void k3_tmetric(Geom3 g, const double *__restrict__ xdot, double *__restrict__ q)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.P) return;
+    int I = (int)(t % g.pd[0]) - GH;
+    int Jn = (int)((t / g.pd[0]) % g.pd[1]) - GH;
+    int K = (int)(t / ((long long)g.pd[0] * g.pd[1])) - GH;
+    double xd[3];
+    for (int b = 0; b < 3; ++b) xd[b] = mesh3_at(g, xdot, b, I, Jn, K, 0);
+    for (int a = 0; a < 3; ++a)
+        q[(F_MT + a) * g.P + t] = -(xd[0] * q[(F_M + 3 * a) * g.P + t] + xd[1] * q[(F_M + 3 * a + 1) * g.P + t] +
+                                    xd[2] * q[(F_M + 3 * a + 2) * g.P + t]);
+}
+
+__device__ __forceinline__ void node_V3(const double *__restrict__ q, long long P, long long c, double c1g, double ig,
+                                        double V[8])
+{
+    double beta = q[F_BETA * P + c], W = q[F_W * P + c];
+    double u0 = q[F_U0 * P + c], u1 = q[F_U1 * P + c], u2 = q[F_U2 * P + c];
+    double B0 = q[F_B0 * P + c], B1 = q[F_B1 * P + c], B2 = q[F_B2 * P + c];
+    double b0 = u0 * B0 + u1 * B1 + u2 * B2;
+    double bW = beta / W;
+    V[0] = c1g + q[F_LNR * P + c] + ig * q[F_LNB * P + c] + beta;
+    V[1] = beta * u0;
+    V[2] = beta * u1;
+    V[3] = beta * u2;
+    V[4] = -beta * W;
+    V[5] = bW * (B0 + b0 * u0);
+    V[6] = bW * (B1 + b0 * u1);
+    V[7] = bW * (B2 + b0 * u2);
+}
+
+// ES interface flux (eq. ESFlux_HO) between node L (index -1 .. n_d - 1 along
+// the sweep) and L + 1, every line of the other two indices.
+template <int P, int WW>
+__global__ void __launch_bounds__(128) k3_iface(Geom3 g, Phys ph, const double *__restrict__ q,
+                                                double *__restrict__ iflux, int dir)
+{
+    const int nd = g.n[dir];
+    const int oa = dir == 0 ? 1 : 0, ob = dir == 2 ? 1 : 2;
+    const long long count = (long long)(nd + 1) * g.n[oa] * g.n[ob];
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count) return;
+    int c3[3];
+    c3[dir] = (int)(idx % (nd + 1)) - 1;
+    c3[oa] = (int)((idx / (nd + 1)) % g.n[oa]);
+    c3[ob] = (int)(idx / ((long long)(nd + 1) * g.n[oa]));
+    const long long c0 = pidx3(g, c3[0], c3[1], c3[2]);
+    const long long sd = dir == 0 ? 1 : (dir == 1 ? (long long)g.pd[0] : (long long)g.pd[0] * g.pd[1]);
+    const double *Mt = q + (F_MT + dir) * g.P;
+    const double *Md = q + (F_M + 3 * dir) * g.P;   // M[dir][0..2] at Md + q' P
+    const double gm1inv = 1.0 / (ph.gamma - 1.0);
+    double F[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ft = 0.0, Bt = 0.0;
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        double Fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Fts = 0.0, Bts = 0.0;
+#pragma unroll
+        for (int s = 0; s < n; ++s) {
+            const long long cl = c0 - s * sd, cr = cl + n * sd;
+            NodeM l = load3(q, g.P, cl), r = load3(q, g.P, cr);
+            double mm[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) mm[a] = 0.5 * (Md[a * g.P + cl] + Md[a * g.P + cr]);
+            double out[8];
+            ec_pair_mhd<3>(l, r, gm1inv, ph.ln_thr, 0.5 * (Mt[cl] + Mt[cr]), mm, out);
+#pragma unroll
+            for (int a = 0; a < 8; ++a) Fs[a] += out[a];
+            Fts += 0.5 * (Mt[cl] + Mt[cr]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Bts += 0.5 * mm[a] * (l.B[a] + r.B[a]);
+        }
+        const double an = ph.alpha[n - 1];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) F[a] += an * Fs[a];
+        Ft += an * Fts;
+        Bt += an * Bts;
+    }
+    if (WW > 0) {
+        constexpr int NS = WW + 1, OFF = (WW - 1) / 2;
+        const long long c1 = c0 + sd;
+        double nv[3], nn[3], T[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nv[a] = 0.5 * (Md[a * g.P + c0] + Md[a * g.P + c1]);
+        const double jt = 0.5 * (Mt[c0] + Mt[c1]);
+        const double Lk = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nn[a] = nv[a] / Lk;
+        frame3(nn, T);
+        double wm[8], wrot[8];
+        {
+            double rho, irho;
+            logmean<double, double>(q[F_RHO * g.P + c0], q[F_RHO * g.P + c1], q[F_LNR * g.P + c0],
+                                    q[F_LNR * g.P + c1], ph.ln_thr, rho, irho);
+            double um[3], W2 = 1.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                um[a] = 0.5 * (q[(F_U0 + a) * g.P + c0] + q[(F_U0 + a) * g.P + c1]);
+                W2 += um[a] * um[a];
+            }
+            double W = sqrt(W2);
+            wm[0] = rho;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) wm[1 + a] = um[a] / W;
+            wm[4] = (q[F_RHO * g.P + c0] + q[F_RHO * g.P + c1]) / (q[F_BETA * g.P + c0] + q[F_BETA * g.P + c1]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) wm[5 + a] = 0.5 * (q[(F_B0 + a) * g.P + c0] + q[(F_B0 + a) * g.P + c1]);
+        }
+        align3(T, wm);
+        rot3(T, wm, wrot);
+        double lam[8], R[8][8];
+        eigen_mhd(ph.gamma, wrot, lam, R, true);
+        double lhat = 0.0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) lhat = fmax(lhat, fabs(jt + Lk * lam[m]));
+        const double ig = gm1inv, c1g = ph.gamma * gm1inv;
+        double Vt[NS][8], scale[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) scale[m] = 0.0;
+        for (int kk = 0; kk < NS; ++kk) {
+            double V[8], TV[8];
+            node_V3(q, g.P, c0 + (kk - OFF) * sd, c1g, ig, V);
+            rot3(T, V, TV);
+            for (int m = 0; m < 8; ++m) {
+                double acc = 0.0;
+                for (int a = 0; a < 8; ++a) {
+                    double t = R[a][m] * TV[a];
+                    acc += t;
+                    if (kk == OFF || kk == OFF + 1) scale[m] += fabs(t);
+                }
+                Vt[kk][m] = acc;
+            }
+        }
+        double z[8];
+        for (int m = 0; m < 8; ++m) {
+            double vminus, vplus;
+            if (WW == 5) {
+                vminus = weno5<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], ph.eps);
+                vplus = weno5<double>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
+            } else {
+                vminus = weno3<double>(Vt[0][m], Vt[1][m], Vt[2][m], ph.eps);
+                vplus = weno3<double>(Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
+            }
+            double jw = vplus - vminus;
+            double jump = Vt[OFF + 1][m] - Vt[OFF][m];
+            int sj = fabs(jump) <= ph.sign_tol * scale[m] ? 0 : sgn_d(jump);
+            z[m] = (sgn_d(jw) == sj) ? jw : 0.0;
+        }
+        double d[8], dr[8];
+        for (int a = 0; a < 8; ++a) {
+            double acc = 0.0;
+            for (int m = 0; m < 8; ++m) acc += R[a][m] * z[m];
+            d[a] = acc;
+        }
+        unrot3(T, d, dr);
+        const double hl = 0.5 * lhat;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) F[a] -= hl * dr[a];
+    }
+    double *out = iflux + (long long)(dir * NF3) * g.P + c0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) out[a * g.P] = F[a];
+    out[8 * g.P] = Ft;
+    out[9 * g.P] = Bt;
+}
+
+// flux differences over the three directions, the Powell source, written out
+// or fused with the SSP-RK3 stage y_o = A y_n + B (y_s + dt L)
+__global__ void k3_update(Geom3 g, const double *__restrict__ q, const double *__restrict__ fl,
+                          double *__restrict__ dcons, double *__restrict__ dJ, const double *__restrict__ cn,
+                          const double *__restrict__ Jn_, const double *__restrict__ xn,
+                          const double *__restrict__ cs, const double *__restrict__ Js,
+                          const double *__restrict__ xs, const double *__restrict__ xdot, double A, double B,
+                          const double *__restrict__ dt_dev, double *__restrict__ co, double *__restrict__ Jo,
+                          double *__restrict__ xo)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+    long long c = pidx3(g, i, j, k);
+    const long long sd[3] = {1, (long long)g.pd[0], (long long)g.pd[0] * g.pd[1]};
+    double L[10];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double *f = fl + (long long)(d * NF3 + a) * g.P;
+            s += f[c] - f[c - sd[d]];
+        }
+        L[a] = -s;
+    }
+    double iW = 1.0 / q[F_W * g.P + c];
+    double w[8];
+    w[1] = q[F_U0 * g.P + c] * iW;
+    w[2] = q[F_U1 * g.P + c] * iW;
+    w[3] = q[F_U2 * g.P + c] * iW;
+    w[5] = q[F_B0 * g.P + c];
+    w[6] = q[F_B1 * g.P + c];
+    w[7] = q[F_B2 * g.P + c];
+    double Pp[8];
+    mhd_phiprime(w, Pp);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) L[a] += Pp[a] * L[9];
+    if (dcons) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) dcons[a * g.N + id] = L[a];
+        dJ[id] = L[8];
+        return;
+    }
+    double dt = dt_dev[0];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) co[a * g.N + id] = A * cn[a * g.N + id] + B * (cs[a * g.N + id] + dt * L[a]);
+    Jo[id] = A * Jn_[id] + B * (Js[id] + dt * L[8]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        xo[a * g.N + id] = A * xn[a * g.N + id] + B * (xs[a * g.N + id] + dt * xdot[a * g.N + id]);
+}
+
+// static spectral radius per direction (eq. cfl)
+__global__ void k3_cfl(Geom3 g, double gam, const double *__restrict__ q, const double *__restrict__ J,
+                       unsigned long long *red)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double r[3] = {0.0, 0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+        long long c = pidx3(g, i, j, k);
+        double iW = 1.0 / q[F_W * g.P + c];
+        double w[8] = {q[F_RHO * g.P + c], q[F_U0 * g.P + c] * iW, q[F_U1 * g.P + c] * iW, q[F_U2 * g.P + c] * iW,
+                       q[F_P * g.P + c], q[F_B0 * g.P + c], q[F_B1 * g.P + c], q[F_B2 * g.P + c]};
+        double iJ = 1.0 / J[id];
+        for (int d = 0; d < 3; ++d) {
+            double m[3];
+            for (int a = 0; a < 3; ++a) m[a] = q[(F_M + 3 * d + a) * g.P + c];
+            double Lk = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            double nn[3] = {m[0] / Lk, m[1] / Lk, m[2] / Lk}, T[3][3], wr[8], lam[8], R[8][8];
+            frame3(nn, T);
+            rot3(T, w, wr);
+            eigen_mhd(gam, wr, lam, R, false);
+            double a = 0.0;
+            for (int mm = 0; mm < 8; ++mm) a = fmax(a, fabs(lam[mm]));
+            r[d] = Lk * a * iJ;
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        double m = block_reduce<0>(r[d]);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + 2 + d, m);
+    }
+}
+
+__global__ void k3_red_init(unsigned long long *red)
+{
+    int t = threadIdx.x;
+    if (t < NR3) red[t] = t == 1 ? (unsigned long long)__double_as_longlong(1.0) : 0ull;
+}
+
+// the step with the mesh velocity (the 2D rule over three directions)
+__global__ void k3_dt(double cfl, double dt_fixed, unsigned long long *red, double *dt_dev)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    double C1 = bits_to_double(red[5]) + bits_to_double(red[6]) + bits_to_double(red[7]);
+    double tau = bits_to_double(red[1]);
+    if (C1 > 0.0 && tau * C1 > 0.5 * cfl) tau = 0.5 * cfl / C1;
+    red[1] = (unsigned long long)__double_as_longlong(tau);
+    double S = bits_to_double(red[2]) + bits_to_double(red[3]) + bits_to_double(red[4]);
+    dt_dev[0] = dt_fixed > 0.0 ? dt_fixed : cfl / S * (1.0 - tau * C1 / cfl);
+}
+
+__global__ void k3_time(const double *dt_dev, double *t_dev)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) t_dev[0] += dt_dev[0];
+}
+
+// ---- Sec. 5 in 3D ------------------------------------------------------------
+__global__ void k3_mesh_grad(Geom3 g, int lnrho, const double *__restrict__ q, double *__restrict__ grad,
+                             unsigned long long *red)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double gv = 0.0;
+    if (id < g.N) {
+        int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+        long long c = pidx3(g, i, j, k);
+        const double *s = q + (lnrho ? F_LNR : F_RHO) * g.P;
+        long long sy = g.pd[0], sz = (long long)g.pd[0] * g.pd[1];
+        double gx = 0.5 * (s[c + 1] - s[c - 1]);
+        double gy = 0.5 * (s[c + sy] - s[c - sy]);
+        double gz = 0.5 * (s[c + sz] - s[c - sz]);
+        gv = sqrt(gx * gx + gy * gy + gz * gz);
+        grad[id] = gv;
+    }
+    double m = block_reduce<0>(gv);
+    if (threadIdx.x == 0) atomic_max_nonneg(red, m);
+}
+
+__global__ void k3_mesh_omega(Geom3 g, double alpha, const double *__restrict__ grad, const unsigned long long *red,
+                              double *__restrict__ om)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    double gmax = bits_to_double(red[0]);
+    om[id] = gmax > 0.0 ? sqrt(1.0 + alpha * grad[id] / gmax) : 1.0;
+}
+
+// omega <- sum_{a,b,c in {-1,0,1}} 2^-(|a|+|b|+|c|+3) omega_{i+a, j+b, k+c}
+__global__ void k3_mesh_filter(Geom3 g, const double *__restrict__ om, double *__restrict__ om2)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+    double acc = 0.0;
+    for (int cc = -1; cc <= 1; ++cc)
+        for (int bb = -1; bb <= 1; ++bb)
+            for (int a = -1; a <= 1; ++a) {
+                int e = (a != 0) + (bb != 0) + (cc != 0) + 3;
+                acc += ldexp(1.0, -e) * om[data_src3(g, i + a, j + bb, k + cc)];
+            }
+    om2[id] = acc;
+}
+
+__global__ void k3_mesh_jacobi(Geom3 g, const double *__restrict__ om, const double *__restrict__ X,
+                               double *__restrict__ Xn)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+    bool fixed = (g.bc[0] == 1 && (i == 0 || i == g.n[0] - 1)) || (g.bc[1] == 1 && (j == 0 || j == g.n[1] - 1)) ||
+                 (g.bc[2] == 1 && (k == 0 || k == g.n[2] - 1));
+    if (fixed) {
+        for (int comp = 0; comp < 3; ++comp) Xn[comp * g.N + id] = X[comp * g.N + id];
+        return;
+    }
+    double wi = om[id];
+    double wp[3] = {om[data_src3(g, i + 1, j, k)], om[data_src3(g, i, j + 1, k)], om[data_src3(g, i, j, k + 1)]};
+    double wm[3] = {om[data_src3(g, i - 1, j, k)], om[data_src3(g, i, j - 1, k)], om[data_src3(g, i, j, k - 1)]};
+    double den = 0.0;
+    for (int d = 0; d < 3; ++d) den += 2.0 * wi + wp[d] + wm[d];
+    for (int comp = 0; comp < 3; ++comp) {
+        double num = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            int a0, a1, a2, b0, b1, b2;
+            step3(i, j, k, d, 1, a0, a1, a2);
+            step3(i, j, k, d, -1, b0, b1, b2);
+            num += (wi + wp[d]) * mesh3_at(g, X, comp, a0, a1, a2, 1) + (wi + wm[d]) * mesh3_at(g, X, comp, b0, b1, b2, 1);
+        }
+        Xn[comp * g.N + id] = num / den;
+    }
+}
+
+// limiter (half the neighbour spacing toward the displacement, three
+// directions) and the displacement's Courant number per direction
+__global__ void k3_mesh_tau(Geom3 g, const double *__restrict__ x, const double *__restrict__ X,
+                            const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double tau = 1.0, cm[3] = {0.0, 0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+        double dd[3];
+        for (int d = 0; d < 3; ++d) {
+            double dv = X[d * g.N + id] - x[d * g.N + id];
+            dd[d] = dv;
+            double bnd = 1.0;
+            int a0, a1, a2;
+            if (dv < 0.0) {
+                step3(i, j, k, d, -1, a0, a1, a2);
+                bnd = -(x[d * g.N + id] - mesh3_at(g, x, d, a0, a1, a2, 1)) / (2.0 * dv);
+            } else if (dv > 0.0) {
+                step3(i, j, k, d, 1, a0, a1, a2);
+                bnd = (mesh3_at(g, x, d, a0, a1, a2, 1) - x[d * g.N + id]) / (2.0 * dv);
+            }
+            tau = fmin(tau, bnd);
+        }
+        tau = fmax(tau, 0.0);
+        long long c = pidx3(g, i, j, k);
+        double iJ = 1.0 / J[id];
+        for (int d = 0; d < 3; ++d)
+            cm[d] = fabs(dd[0] * q[(F_M + 3 * d) * g.P + c] + dd[1] * q[(F_M + 3 * d + 1) * g.P + c] +
+                         dd[2] * q[(F_M + 3 * d + 2) * g.P + c]) * iJ;
+    }
+    double m = block_reduce<1>(tau);
+    if (threadIdx.x == 0) atomic_min_nonneg(red + 1, m);
+    for (int d = 0; d < 3; ++d) {
+        double mk = block_reduce<0>(cm[d]);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + 5 + d, mk);
+    }
+}
+
+__global__ void k3_mesh_xdot(Geom3 g, const double *__restrict__ x, const double *__restrict__ X,
+                             const unsigned long long *red, const double *__restrict__ dt_dev, double *__restrict__ xdot)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 3 * g.N) return;
+    xdot[id] = bits_to_double(red[1]) * (X[id] - x[id]) / dt_dev[0];
+}
+
+// initial J = det(delta_k[x_j]) and cons = J U(prim)
+template <int P>
+__global__ void k3_init(Geom3 g, double gam, const double *__restrict__ prim, const double *__restrict__ x,
+                        double *__restrict__ cons, double *__restrict__ J, int *status)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+    double D[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) D[a][b] = delta_x3<P>(g, x, b, i, j, k, a);
+    double J0 = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) - D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+    double w[8], U[8], F[8], V[8];
+    for (int a = 0; a < 8; ++a) w[a] = prim[a * g.N + id];
+    double v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
+    if (!(w[0] > 0.0) || !(w[4] > 0.0) || !(v2 < 1.0) || !(J0 > 0.0)) {
+        atomicAdd(status + 1, 1);
+        w[0] = 1.0; w[4] = 1.0; w[1] = w[2] = w[3] = 0.0;
+    }
+    mhd_UFV<double>(gam, w, U, F, V);
+    J[id] = J0;
+    for (int a = 0; a < 8; ++a) cons[a * g.N + id] = J0 * U[a];
+}
+
+__global__ void k3_prim_out(Geom3 g, double gam, const double *__restrict__ cons, const double *__restrict__ J,
+                            double *__restrict__ prim, int *status)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    double iJ = 1.0 / J[id];
+    double U[8], w[8], Z;
+    for (int a = 0; a < 8; ++a) U[a] = cons[a * g.N + id] * iJ;
+    if (cons2prim_mhd(gam, U, -1.0, w, Z)) atomicAdd(status, 1);
+    for (int a = 0; a < 8; ++a) prim[a * g.N + id] = w[a];
+}
+
+// totals: per-block partial sums of (J eta, J D, J), then a fixed-order sum
+__global__ void k3_totals(Geom3 g, double gam, const double *__restrict__ q, const double *__restrict__ cons,
+                          const double *__restrict__ J, double *__restrict__ partials)
+{
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
+        long long c = pidx3(g, i, j, k);
+        double rho = q[F_RHO * g.P + c], W = q[F_W * g.P + c];
+        double lnr = q[F_LNR * g.P + c], lnb = q[F_LNB * g.P + c];
+        double s = (lnr - lnb) - gam * lnr;
+        v[0] = J[id] * (-rho * W * s / (gam - 1.0));
+        v[1] = cons[id];
+        v[2] = J[id];
+    }
+    for (int a = 0; a < 3; ++a) {
+        double s = block_reduce<2>(v[a]);
+        if (threadIdx.x == 0) partials[(long long)blockIdx.x * 3 + a] = s;
+    }
+}
+
+__global__ void k3_totals_final(int nb, const double *__restrict__ partials, double *__restrict__ out)
+{
+    int t = threadIdx.x;
+    if (t >= 3) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partials[(long long)b * 3 + t];
+    out[t] = s;
+}
+
+}  // namespace d3
+}  // namespace esmm
+
+// ===========================================================================
+using namespace esmm;
+using namespace esmm::d3;
+
+struct esmm3 {
+    Geom3 g;
+    double lo[3], hi[3];
+    double gamma;
+    int p, w;
+    esmm_params prm;
+    cudaStream_t st;
+    int has_state, xdot_zero;
+    double *cons, *J, *x, *xdot, *c1, *J1, *x1, *c2, *J2, *x2;
+    double *q, *zg[3], *iflux, *out_dc, *out_dJ, *in_cons, *in_J, *in_x, *in_xdot;
+    double *grad, *om, *om2, *X, *Xn, *dt_dev, *t_dev, *partials, *tot;
+    unsigned long long *red;
+    int *status;
+    double *pin;
+    char msg[256];
+    long long launches;
+};
+
+namespace {
+
+constexpr int BS3 = 128;
+inline unsigned nb3(long long n, int bs = BS3) { return (unsigned)((n + bs - 1) / bs); }
+
+int fail3(esmm3 *g, int code, const char *what, cudaError_t e = cudaSuccess)
+{
+    if (e != cudaSuccess) snprintf(g->msg, sizeof g->msg, "%s: %s", what, cudaGetErrorString(e));
+    else snprintf(g->msg, sizeof g->msg, "%s", what);
+    return code;
+}
+
+#define CK3(call)                                                          \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return fail3(g, ESMM_ERR_CUDA, #call, e_);  \
+    } while (0)
+
+Phys phys3(const esmm3 *g)
+{
+    Phys ph;
+    ph.gamma = g->gamma;
+    ph.eps = g->prm.weno_eps;
+    ph.ln_thr = 1.0e-4;
+    ph.sign_tol = 1.0e-10;
+    double a[3][3] = {{1.0, 0.0, 0.0}, {4.0 / 3.0, -1.0 / 6.0, 0.0}, {1.5, -0.3, 1.0 / 30.0}};
+    for (int n = 0; n < PMAX; ++n) ph.alpha[n] = a[g->p - 1][n];
+    ph.p = g->p;
+    ph.w = g->w;
+    return ph;
+}
+
+void node3(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot, const double *zi,
+           double *zo)
+{
+    unsigned nb = nb3(g->g.P);
+    g->launches++;
+    if (g->p == 1) k3_node<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
+    else if (g->p == 2) k3_node<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
+    else k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
+}
+
+template <int P>
+void iface3_p(esmm3 *g, const Phys &ph, unsigned nb, int dir)
+{
+    switch (g->w) {
+    case 0: k3_iface<P, 0><<<nb, 128, 0, g->st>>>(g->g, ph, g->q, g->iflux, dir); break;
+    case 3: k3_iface<P, 3><<<nb, 128, 0, g->st>>>(g->g, ph, g->q, g->iflux, dir); break;
+    default: k3_iface<P, 5><<<nb, 128, 0, g->st>>>(g->g, ph, g->q, g->iflux, dir); break;
+    }
+}
+
+void fluxes3(esmm3 *g)
+{
+    Phys ph = phys3(g);
+    for (int dir = 0; dir < 3; ++dir) {
+        int oa = dir == 0 ? 1 : 0, ob = dir == 2 ? 1 : 2;
+        long long count = (long long)(g->g.n[dir] + 1) * g->g.n[oa] * g->g.n[ob];
+        unsigned nb = nb3(count, 128);
+        g->launches++;
+        if (g->p == 1) iface3_p<1>(g, ph, nb, dir);
+        else if (g->p == 2) iface3_p<2>(g, ph, nb, dir);
+        else iface3_p<3>(g, ph, nb, dir);
+    }
+}
+
+void update3(esmm3 *g, double *dc, double *dJ, const double *cn, const double *Jn, const double *xn, const double *cs,
+             const double *Js, const double *xs, double A, double B, double *co, double *Jo, double *xo)
+{
+    g->launches++;
+    k3_update<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->q, g->iflux, dc, dJ, cn, Jn, xn, cs, Js, xs, g->xdot, A, B,
+                                              g->dt_dev, co, Jo, xo);
+}
+
+int mesh_and_dt3(esmm3 *g, double dt)
+{
+    unsigned nb = nb3(g->g.N);
+    g->launches++;
+    k3_red_init<<<1, 32, 0, g->st>>>(g->red);
+    if (!(dt > 0.0)) {
+        g->launches++;
+        k3_cfl<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
+    }
+    if (!g->prm.move_mesh) {
+        g->launches++;
+        k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->dt_dev);
+        if (!g->xdot_zero) {
+            CK3(cudaMemsetAsync(g->xdot, 0, 3 * g->g.N * sizeof(double), g->st));
+            g->xdot_zero = 1;
+        }
+        return ESMM_OK;
+    }
+    g->xdot_zero = 0;
+    k3_mesh_grad<<<nb, BS3, 0, g->st>>>(g->g, g->prm.monitor == ESMM_MONITOR_LNRHO, g->q, g->grad, g->red);
+    k3_mesh_omega<<<nb, BS3, 0, g->st>>>(g->g, g->prm.alpha, g->grad, g->red, g->om);
+    double *om = g->om, *om2 = g->om2;
+    for (int f = 0; f < g->prm.n_filter; ++f) {
+        k3_mesh_filter<<<nb, BS3, 0, g->st>>>(g->g, om, om2);
+        std::swap(om, om2);
+    }
+    const double *src = g->x;
+    for (int nu = 0; nu < g->prm.mu; ++nu) {
+        double *dst = (nu % 2 == 0) ? g->X : g->Xn;
+        k3_mesh_jacobi<<<nb, BS3, 0, g->st>>>(g->g, om, src, dst);
+        src = dst;
+    }
+    k3_mesh_tau<<<nb, BS3, 0, g->st>>>(g->g, g->x, src, g->q, g->J, g->red);
+    k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->dt_dev);
+    k3_mesh_xdot<<<nb3(3 * g->g.N), BS3, 0, g->st>>>(g->g, g->x, src, g->red, g->dt_dev, g->xdot);
+    g->launches += 6 + g->prm.n_filter + g->prm.mu;
+    return ESMM_OK;
+}
+
+int stages3(esmm3 *g)
+{
+    fluxes3(g);
+    update3(g, nullptr, nullptr, g->cons, g->J, g->x, g->cons, g->J, g->x, 0.0, 1.0, g->c1, g->J1, g->x1);
+    node3(g, g->c1, g->J1, g->x1, g->xdot, g->zg[1], g->zg[2]);
+    fluxes3(g);
+    update3(g, nullptr, nullptr, g->cons, g->J, g->x, g->c1, g->J1, g->x1, 0.75, 0.25, g->c2, g->J2, g->x2);
+    node3(g, g->c2, g->J2, g->x2, g->xdot, g->zg[2], g->zg[0]);
+    fluxes3(g);
+    update3(g, nullptr, nullptr, g->cons, g->J, g->x, g->c2, g->J2, g->x2, 1.0 / 3.0, 2.0 / 3.0, g->cons, g->J, g->x);
+    g->launches++;
+    k3_time<<<1, 32, 0, g->st>>>(g->dt_dev, g->t_dev);
+    CK3(cudaGetLastError());
+    return ESMM_OK;
+}
+
+int check3(esmm3 *g)
+{
+    int h[2];
+    CK3(cudaMemcpyAsync(h, g->status, sizeof h, cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    if (h[0] > 0) {
+        CK3(cudaMemsetAsync(g->status, 0, sizeof(int), g->st));
+        snprintf(g->msg, sizeof g->msg, "primitive recovery failed at %d node(s)", h[0]);
+        return ESMM_ERR_C2P;
+    }
+    return ESMM_OK;
+}
+
+int copy3(esmm3 *g, double *dst, const double *src, size_t n, int mem, bool in)
+{
+    cudaMemcpyKind k = mem == ESMM_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                              : (in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    CK3(cudaMemcpyAsync(dst, src, n * sizeof(double), k, g->st));
+    return ESMM_OK;
+}
+
+void free3(esmm3 *g)
+{
+    double **b[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2, &g->q,
+                    &g->zg[0], &g->zg[1], &g->zg[2], &g->iflux, &g->out_dc, &g->out_dJ, &g->in_cons, &g->in_J,
+                    &g->in_x, &g->in_xdot, &g->grad, &g->om, &g->om2, &g->X, &g->Xn, &g->dt_dev, &g->t_dev,
+                    &g->partials, &g->tot};
+    for (double **p : b)
+        if (*p) { cudaFree(*p); *p = nullptr; }
+    if (g->red) cudaFree(g->red);
+    if (g->status) cudaFree(g->status);
+    if (g->pin) cudaFreeHost(g->pin);
+}
+
+}  // namespace
+
+// ---- the esmm3_* entry points (esmm_3d.h) ------------------------------------------
+int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double hi[3], const int bc[3], void *stream)
+{
+    *out = nullptr;
+    for (int k = 0; k < 3; ++k)
+        if (n[k] < 4 || n[k] > 4096 || (bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW) || !(hi[k] > lo[k]))
+            return ESMM_ERR_ARG;
+    esmm3 *g = new (std::nothrow) esmm3;
+    if (!g) return ESMM_ERR_ARG;
+    memset((void *)g, 0, sizeof *g);
+    for (int k = 0; k < 3; ++k) {
+        g->g.n[k] = n[k];
+        g->g.pd[k] = n[k] + 2 * GH;
+        g->g.bc[k] = bc[k];
+        g->g.per[k] = hi[k] - lo[k];
+        g->lo[k] = lo[k];
+        g->hi[k] = hi[k];
+    }
+    g->g.N = (long long)n[0] * n[1] * n[2];
+    g->g.P = (long long)g->g.pd[0] * g->g.pd[1] * g->g.pd[2];
+    g->st = (cudaStream_t)stream;
+    g->gamma = 4.0 / 3.0;
+    g->p = 2;
+    g->w = 5;
+    g->prm.cfl = 0.3;
+    g->prm.weno_eps = 1e-6;
+    g->prm.monitor = ESMM_MONITOR_LNRHO;
+    g->prm.alpha = 800.0;
+    g->prm.n_filter = 4;
+    g->prm.mu = 10;
+    g->prm.move_mesh = 1;
+    g->prm.precision = ESMM_FP64;
+    size_t N = (size_t)g->g.N, P = (size_t)g->g.P, d = sizeof(double);
+    size_t nb = N / BS3 + 2;
+    struct { double **p; size_t n; } al[] = {
+        {&g->cons, 8 * N}, {&g->J, N}, {&g->x, 3 * N}, {&g->xdot, 3 * N}, {&g->c1, 8 * N}, {&g->J1, N},
+        {&g->x1, 3 * N}, {&g->c2, 8 * N}, {&g->J2, N}, {&g->x2, 3 * N}, {&g->q, (size_t)NQ3 * P},
+        {&g->zg[0], N}, {&g->zg[1], N}, {&g->zg[2], N}, {&g->iflux, (size_t)3 * NF3 * P}, {&g->out_dc, 8 * N},
+        {&g->out_dJ, N}, {&g->in_cons, 8 * N}, {&g->in_J, N}, {&g->in_x, 3 * N}, {&g->in_xdot, 3 * N},
+        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->X, 3 * N}, {&g->Xn, 3 * N}, {&g->dt_dev, 1},
+        {&g->t_dev, 1}, {&g->partials, 3 * nb}, {&g->tot, 3}};
+    bool ok = true;
+    for (auto &a : al) ok = ok && cudaMalloc((void **)a.p, a.n * d) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&g->red, NR3 * sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMalloc((void **)&g->status, 2 * sizeof(int)) == cudaSuccess &&
+         cudaMallocHost((void **)&g->pin, 16 * sizeof(double)) == cudaSuccess;
+    for (int k = 0; ok && k < 3; ++k) ok = cudaMemsetAsync(g->zg[k], 0xff, N * d, g->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->status, 0, 2 * sizeof(int), g->st) == cudaSuccess &&
+         cudaMemsetAsync(g->t_dev, 0, d, g->st) == cudaSuccess && cudaStreamSynchronize(g->st) == cudaSuccess;
+    if (!ok) {
+        free3(g);
+        delete g;
+        return ESMM_ERR_CUDA;
+    }
+    *out = g;
+    return ESMM_OK;
+}
+
+void esmm3_destroy(esmm3 *g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->st);
+    free3(g);
+    delete g;
+}
+
+int esmm3_set_stream(esmm3 *g, void *stream)
+{
+    CK3(cudaStreamSynchronize(g->st));
+    g->st = (cudaStream_t)stream;
+    return ESMM_OK;
+}
+
+int esmm3_set_eos(esmm3 *g, double gamma) { g->gamma = gamma; return ESMM_OK; }
+int esmm3_set_order(esmm3 *g, int p, int w) { g->p = p; g->w = w; return ESMM_OK; }
+int esmm3_set_params(esmm3 *g, const esmm_params *prm)
+{
+    if (prm->precision != ESMM_FP64) return fail3(g, ESMM_ERR_ARG, "3D grids compute in FP64 only");
+    g->prm = *prm;
+    return ESMM_OK;
+}
+int esmm3_get_params(const esmm3 *g, esmm_params *prm) { *prm = g->prm; return ESMM_OK; }
+
+int esmm3_state_set(esmm3 *g, const double *prim, const double *x, int mem)
+{
+    size_t N = (size_t)g->g.N;
+    int rc;
+    if (x) {
+        if ((rc = copy3(g, g->x, x, 3 * N, mem, true))) return rc;
+    } else {
+        std::vector<double> hx(3 * N);
+        int den[3];
+        for (int k = 0; k < 3; ++k) den[k] = g->g.bc[k] == ESMM_PERIODIC ? g->g.n[k] : g->g.n[k] - 1;
+        for (int k = 0; k < g->g.n[2]; ++k)
+            for (int j = 0; j < g->g.n[1]; ++j)
+                for (int i = 0; i < g->g.n[0]; ++i) {
+                    size_t id = ((size_t)k * g->g.n[1] + j) * g->g.n[0] + i;
+                    int ijk[3] = {i, j, k};
+                    for (int c = 0; c < 3; ++c)
+                        hx[c * N + id] = g->lo[c] + (g->hi[c] - g->lo[c]) * ijk[c] / den[c];
+                }
+        CK3(cudaMemcpyAsync(g->x, hx.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, g->st));
+        CK3(cudaStreamSynchronize(g->st));
+    }
+    if ((rc = copy3(g, g->out_dc, prim, 8 * N, mem, true))) return rc;
+    CK3(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), g->st));
+    g->launches++;
+    unsigned nb = nb3(g->g.N);
+    if (g->p == 1) k3_init<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
+    else if (g->p == 2) k3_init<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
+    else k3_init<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
+    CK3(cudaGetLastError());
+    CK3(cudaMemsetAsync(g->xdot, 0, 3 * N * sizeof(double), g->st));
+    for (int k = 0; k < 3; ++k) CK3(cudaMemsetAsync(g->zg[k], 0xff, N * sizeof(double), g->st));
+    CK3(cudaMemsetAsync(g->t_dev, 0, sizeof(double), g->st));
+    int h[2];
+    CK3(cudaMemcpyAsync(h, g->status, sizeof h, cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    g->xdot_zero = 1;
+    if (h[1] > 0) {
+        CK3(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), g->st));
+        g->has_state = 0;
+        return fail3(g, ESMM_ERR_ARG, "non-admissible initial state or tangled mesh");
+    }
+    g->has_state = 1;
+    return ESMM_OK;
+}
+
+int esmm3_state_set_cons(esmm3 *g, const double *cons, const double *J, const double *x, double t, int mem)
+{
+    size_t N = (size_t)g->g.N;
+    int rc;
+    if ((rc = copy3(g, g->cons, cons, 8 * N, mem, true)) || (rc = copy3(g, g->J, J, N, mem, true)) ||
+        (rc = copy3(g, g->x, x, 3 * N, mem, true)))
+        return rc;
+    g->pin[0] = t;
+    CK3(cudaMemcpyAsync(g->t_dev, g->pin, sizeof(double), cudaMemcpyHostToDevice, g->st));
+    CK3(cudaMemsetAsync(g->xdot, 0, 3 * N * sizeof(double), g->st));
+    for (int k = 0; k < 3; ++k) CK3(cudaMemsetAsync(g->zg[k], 0xff, N * sizeof(double), g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    g->xdot_zero = 1;
+    g->has_state = 1;
+    return ESMM_OK;
+}
+
+int esmm3_state_get(esmm3 *g, int what, double *out, int mem)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    size_t N = (size_t)g->g.N;
+    int rc = ESMM_OK;
+    switch (what) {
+    case ESMM_GET_PRIM:
+        g->launches++;
+        k3_prim_out<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->gamma, g->cons, g->J, g->out_dc, g->status);
+        CK3(cudaGetLastError());
+        rc = copy3(g, out, g->out_dc, 8 * N, mem, false);
+        break;
+    case ESMM_GET_CONS: rc = copy3(g, out, g->cons, 8 * N, mem, false); break;
+    case ESMM_GET_J: rc = copy3(g, out, g->J, N, mem, false); break;
+    case ESMM_GET_X: rc = copy3(g, out, g->x, 3 * N, mem, false); break;
+    case ESMM_GET_XDOT: rc = copy3(g, out, g->xdot, 3 * N, mem, false); break;
+    default: return fail3(g, ESMM_ERR_ARG, "unknown field");
+    }
+    if (rc) return rc;
+    CK3(cudaStreamSynchronize(g->st));
+    return what == ESMM_GET_PRIM ? check3(g) : ESMM_OK;
+}
+
+int esmm3_get_time(esmm3 *g, double *t)
+{
+    CK3(cudaMemcpyAsync(g->pin, g->t_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    *t = g->pin[0];
+    return ESMM_OK;
+}
+
+int esmm3_rhs(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot, double *dcons,
+              double *dJ, int mem)
+{
+    size_t N = (size_t)g->g.N;
+    int rc;
+    if (mem == ESMM_MEM_HOST) {
+        if ((rc = copy3(g, g->in_cons, cons, 8 * N, mem, true)) || (rc = copy3(g, g->in_J, J, N, mem, true)) ||
+            (rc = copy3(g, g->in_x, x, 3 * N, mem, true)))
+            return rc;
+        if (xdot && (rc = copy3(g, g->in_xdot, xdot, 3 * N, mem, true))) return rc;
+        cons = g->in_cons;
+        J = g->in_J;
+        x = g->in_x;
+        xdot = xdot ? g->in_xdot : nullptr;
+    }
+    node3(g, cons, J, x, xdot, nullptr, nullptr);
+    fluxes3(g);
+    double *dc = mem == ESMM_MEM_HOST ? g->out_dc : dcons;
+    double *dj = mem == ESMM_MEM_HOST ? g->out_dJ : dJ;
+    update3(g, dc, dj, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr);
+    CK3(cudaGetLastError());
+    if (mem == ESMM_MEM_HOST) {
+        if ((rc = copy3(g, dcons, g->out_dc, 8 * N, mem, false)) || (rc = copy3(g, dJ, g->out_dJ, N, mem, false)))
+            return rc;
+        CK3(cudaStreamSynchronize(g->st));
+        return check3(g);
+    }
+    return ESMM_OK;
+}
+
+int esmm3_cfl_dt(esmm3 *g, double *dt)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
+    g->launches += 3;
+    k3_red_init<<<1, 32, 0, g->st>>>(g->red);
+    k3_cfl<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
+    k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, 0.0, g->red, g->dt_dev);
+    CK3(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    *dt = g->pin[0];
+    return check3(g);
+}
+
+int esmm3_mesh_redistribute(esmm3 *g, double dt, double *xdot, double *dtau, double *dt_used, int mem)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
+    int rc = mesh_and_dt3(g, dt);
+    if (rc) return rc;
+    if (xdot && (rc = copy3(g, xdot, g->xdot, 3 * (size_t)g->g.N, mem, false))) return rc;
+    CK3(cudaMemcpyAsync(g->pin, g->red + 1, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaMemcpyAsync(g->pin + 1, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    if (dtau) *dtau = g->prm.move_mesh ? g->pin[0] : 0.0;
+    if (dt_used) *dt_used = g->pin[1];
+    return check3(g);
+}
+
+static int rk_step_async3(esmm3 *g, double dt)
+{
+    node3(g, g->cons, g->J, g->x, nullptr, g->zg[0], g->zg[1]);
+    int rc = mesh_and_dt3(g, dt);
+    if (rc) return rc;
+    g->launches++;
+    k3_tmetric<<<nb3(g->g.P), BS3, 0, g->st>>>(g->g, g->xdot, g->q);
+    return stages3(g);
+}
+
+int esmm3_rk_step(esmm3 *g, double dt, double *dt_used)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    int rc = rk_step_async3(g, dt);
+    if (rc) return rc;
+    if (dt_used) {
+        CK3(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+        CK3(cudaStreamSynchronize(g->st));
+        *dt_used = g->pin[0];
+        return check3(g);
+    }
+    return ESMM_OK;
+}
+
+int esmm3_advance(esmm3 *g, int nsteps, double dt)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = rk_step_async3(g, dt);
+        if (rc) return rc;
+    }
+    return ESMM_OK;
+}
+
+int esmm3_totals(esmm3 *g, double out[3])
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
+    unsigned nb = nb3(g->g.N);
+    g->launches += 2;
+    k3_totals<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->cons, g->J, g->partials);
+    k3_totals_final<<<1, 32, 0, g->st>>>((int)nb, g->partials, g->tot);
+    CK3(cudaMemcpyAsync(g->pin, g->tot, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    for (int k = 0; k < 3; ++k) out[k] = g->pin[k];
+    return check3(g);
+}
+
+int esmm3_last_error(esmm3 *g, int *n_c2p_fail, char *msg, int len)
+{
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, g->status, sizeof h, cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e == cudaSuccess) cudaMemsetAsync(g->status, 0, sizeof(int), g->st);
+    if (n_c2p_fail) *n_c2p_fail = h[0];
+    if (msg && len > 0) {
+        strncpy(msg, g->msg, (size_t)len - 1);
+        msg[len - 1] = 0;
+    }
+    return e == cudaSuccess ? ESMM_OK : ESMM_ERR_CUDA;
+}
+
+long long esmm3_launches(const esmm3 *g) { return g->launches; }

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "esmm.h"
+#include "esmm_3d.h"
 #include "esmm_device.cuh"
 #include "esmm_kernels.cuh"
 #include "esmm_launch.h"
@@ -37,6 +38,8 @@ enum { D_PAD = 0, D_PAIR0, D_PAIR1, D_IFACE0, D_IFACE1, D_NODE, D_NODE2, ND };
 }  // namespace
 
 struct esmm_grid {
+    int dim;                         // 2, or 3 (then every call goes to g3)
+    esmm3 *g3;
     int dev;
     int nprob;
     std::vector<ProbDesc> hpd;       // per-problem geometry and offsets
@@ -511,8 +514,33 @@ int copy_out(esmm_grid *g, double *dst, const double *src, size_t n, int mem)
 
 void release(esmm_grid *g)
 {
+    if (g->g3) esmm3_destroy(g->g3);
+    g->g3 = nullptr;
     free_all(g);
     delete g;   // destroys the member vectors
+}
+
+// a dim = 3 grid: a shell that forwards to the 3D handle
+int create3(esmm_grid **out, const int n[3], const double lo[3], const double hi[3], const int bc[3], void *stream)
+{
+    *out = nullptr;
+    esmm_grid *g = new (std::nothrow) esmm_grid;
+    if (!g) return ESMM_ERR_ARG;
+    memset((void *)g, 0, sizeof *g);
+    new (&g->hpd) std::vector<ProbDesc>();
+    new (&g->lo) std::vector<double>();
+    new (&g->hi) std::vector<double>();
+    g->dim = 3;
+    g->nprob = 1;
+    g->phys = ESMM_RMHD;
+    g->nv = 8;
+    int rc = esmm3_create(&g->g3, n, lo, hi, bc, stream);
+    if (rc) {
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return ESMM_OK;
 }
 
 // Create a grid of nprob problems: n, lo, hi, bc are [nprob][2].
@@ -529,6 +557,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         new (&g->lo) std::vector<double>();
         new (&g->hi) std::vector<double>();
     }
+    g->dim = 2;
     g->ev = new (std::nothrow) std::vector<std::pair<cudaEvent_t, cudaEvent_t>>[ESMM_NKINDS];
     g->pool = new (std::nothrow) std::vector<cudaEvent_t>;
     g->ck = new (std::nothrow) std::vector<double *>;
@@ -1010,6 +1039,7 @@ int esmm_grid_create(esmm_grid **out, int dim, const int n[3], const double lo[3
 {
     if (!out || !n || !lo || !hi || !bc) return ESMM_ERR_ARG;
     *out = nullptr;
+    if (dim == 3) return phys == ESMM_RMHD ? create3(out, n, lo, hi, bc, stream) : ESMM_ERR_ARG;
     if (dim != 2 || (phys != ESMM_RHD && phys != ESMM_RMHD)) return ESMM_ERR_ARG;
     if (check_geometry(n[0], n[1], lo, hi, bc)) return ESMM_ERR_ARG;
     int n2[2] = {n[0], n[1]}, bc2[2] = {bc[0], bc[1]};
@@ -1028,6 +1058,7 @@ int esmm_grid_destroy(esmm_grid *g)
 int esmm_set_stream(esmm_grid *g, void *stream)
 {
     if (!g) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_set_stream(g->g3, stream);
     CK(cudaStreamSynchronize(g->st));
     g->st = stream ? (cudaStream_t)stream : (g->own_st ? g->own_st : nullptr);
     drop_graph(g);
@@ -1037,6 +1068,7 @@ int esmm_set_stream(esmm_grid *g, void *stream)
 int esmm_set_eos(esmm_grid *g, double gamma)
 {
     if (!g || !(gamma > 1.0 && gamma <= 2.0)) return fail(g, ESMM_ERR_ARG, "Gamma must be in (1, 2]");
+    if (g->dim == 3) return esmm3_set_eos(g->g3, gamma);
     g->gamma = gamma;
     g->epoch++;
     return ESMM_OK;
@@ -1046,6 +1078,7 @@ int esmm_set_order(esmm_grid *g, int p, int w)
 {
     if (!g || p < 1 || p > PMAX || !(w == 0 || w == 3 || w == 5))
         return fail(g, ESMM_ERR_ARG, "p must be 1..3 and w one of 0, 3, 5");
+    if (g->dim == 3) return esmm3_set_order(g->g3, p, w);
     if (p != g->p) g->doms_valid = 0;
     g->p = p;
     g->w = w;
@@ -1060,6 +1093,7 @@ int esmm_set_params(esmm_grid *g, const esmm_params *prm)
         prm->mu < 0 || (prm->precision != ESMM_FP64 && prm->precision != ESMM_MIXED) ||
         (prm->monitor != ESMM_MONITOR_RHO && prm->monitor != ESMM_MONITOR_LNRHO))
         return fail(g, ESMM_ERR_ARG, "invalid parameter");
+    if (g->dim == 3) return esmm3_set_params(g->g3, prm);
     if (g->phys == ESMM_RMHD && prm->precision != ESMM_FP64)
         return fail(g, ESMM_ERR_ARG, "RMHD grids compute in FP64 only");
     g->prm = *prm;
@@ -1070,6 +1104,7 @@ int esmm_set_params(esmm_grid *g, const esmm_params *prm)
 int esmm_get_params(const esmm_grid *g, esmm_params *prm)
 {
     if (!g || !prm) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_get_params(g->g3, prm);
     *prm = g->prm;
     return ESMM_OK;
 }
@@ -1077,6 +1112,7 @@ int esmm_get_params(const esmm_grid *g, esmm_params *prm)
 int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem)
 {
     if (!g || !prim || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_state_set(g->g3, prim, x, mem);
     int rc = state_set_one(g, 0, prim, x, mem);
     g->has_state = rc == ESMM_OK;
     return rc;
@@ -1085,6 +1121,7 @@ int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem)
 int esmm_state_set_cons(esmm_grid *g, const double *cons, const double *J, const double *x, double t, int mem)
 {
     if (!g || !cons || !J || !x || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_state_set_cons(g->g3, cons, J, x, t, mem);
     size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
     int rc;
     if ((rc = copy_in(g, g->cons, cons, nv * N, mem)) || (rc = copy_in(g, g->J, J, N, mem)) ||
@@ -1103,6 +1140,7 @@ int esmm_state_set_cons(esmm_grid *g, const double *cons, const double *J, const
 int esmm_state_get(esmm_grid *g, int what, double *out, int mem)
 {
     if (!g || !out || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_state_get(g->g3, what, out, mem);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     return state_get_one(g, 0, what, out, mem);
 }
@@ -1110,6 +1148,7 @@ int esmm_state_get(esmm_grid *g, int what, double *out, int mem)
 int esmm_get_time(esmm_grid *g, double *t)
 {
     if (!g || !t) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_get_time(g->g3, t);
     CK(cudaMemcpyAsync(g->pin, g->t_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     *t = g->pin[0];
@@ -1120,6 +1159,7 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
              double *dcons, double *dJ, int mem)
 {
     if (!g || !cons || !J || !x || !dcons || !dJ || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_rhs(g->g3, cons, J, x, xdot, dcons, dJ, mem);
     int rc;
     if ((rc = ensure_doms(g))) return rc;
     size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
@@ -1152,6 +1192,7 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
 int esmm_cfl_dt(esmm_grid *g, double *dt)
 {
     if (!g || !dt || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_cfl_dt(g->g3, dt);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     int rc;
     if ((rc = ensure_doms(g))) return rc;
@@ -1168,6 +1209,7 @@ int esmm_cfl_dt(esmm_grid *g, double *dt)
 int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, double *dt_used, int mem)
 {
     if (!g || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_mesh_redistribute(g->g3, dt, xdot, dtau, dt_used, mem);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     int rc;
     if ((rc = ensure_doms(g))) return rc;
@@ -1187,6 +1229,7 @@ int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, 
 int esmm_rk_step(esmm_grid *g, double dt, double *dt_used)
 {
     if (!g) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_rk_step(g->g3, dt, dt_used);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     int rc = rk_step_async(g, dt);
     if (rc) return rc;
@@ -1202,6 +1245,7 @@ int esmm_rk_step(esmm_grid *g, double dt, double *dt_used)
 int esmm_advance(esmm_grid *g, int nsteps, double dt)
 {
     if (!g || nsteps < 0) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_advance(g->g3, nsteps, dt);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     return advance(g, nsteps, dt);
 }
@@ -1209,6 +1253,7 @@ int esmm_advance(esmm_grid *g, int nsteps, double dt)
 int esmm_totals(esmm_grid *g, double out[3])
 {
     if (!g || !out || g->nprob != 1) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_totals(g->g3, out);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     int rc = totals_async(g);
     if (rc) return rc;
@@ -1231,6 +1276,7 @@ int esmm_batch_create(esmm_grid **out, int nprob, const int *n, const double *lo
 
 int esmm_batch_size(const esmm_grid *g, int *nprob)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !nprob) return ESMM_ERR_ARG;
     *nprob = g->nprob;
     return ESMM_OK;
@@ -1238,6 +1284,7 @@ int esmm_batch_size(const esmm_grid *g, int *nprob)
 
 int esmm_batch_state_set(esmm_grid *g, int b, const double *prim, const double *x, int mem)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !prim || b < 0 || b >= g->nprob) return ESMM_ERR_ARG;
     int rc = state_set_one(g, b, prim, x, mem);
     if (rc == ESMM_OK) g->has_state = 1;
@@ -1246,6 +1293,7 @@ int esmm_batch_state_set(esmm_grid *g, int b, const double *prim, const double *
 
 int esmm_batch_state_get(esmm_grid *g, int b, int what, double *out, int mem)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !out || b < 0 || b >= g->nprob) return ESMM_ERR_ARG;
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     return state_get_one(g, b, what, out, mem);
@@ -1253,6 +1301,7 @@ int esmm_batch_state_get(esmm_grid *g, int b, int what, double *out, int mem)
 
 int esmm_batch_times(esmm_grid *g, double *t)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !t) return ESMM_ERR_ARG;
     CK(cudaMemcpyAsync(g->pin, g->t_dev, g->nprob * sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
@@ -1262,6 +1311,7 @@ int esmm_batch_times(esmm_grid *g, double *t)
 
 int esmm_batch_totals(esmm_grid *g, double *out)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !out) return ESMM_ERR_ARG;
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     int rc = totals_async(g);
@@ -1274,6 +1324,7 @@ int esmm_batch_totals(esmm_grid *g, double *out)
 
 int esmm_tune(esmm_grid *g, int *block_sizes)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g) return ESMM_ERR_ARG;
     int rc = tune(g);
     if (rc) return rc;
@@ -1285,6 +1336,7 @@ int esmm_tune(esmm_grid *g, int *block_sizes)
 int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
                  const double *mu, double *lam, int mem)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !cons || !J || !x || !mu || !lam || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->phys != ESMM_RHD) return fail(g, ESMM_ERR_ARG, "the adjoint covers RHD grids");
     int rc;
@@ -1313,6 +1365,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->phys != ESMM_RHD) return fail(g, ESMM_ERR_ARG, "the adjoint covers RHD grids");
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
@@ -1342,6 +1395,7 @@ int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 
 int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !nsteps) return ESMM_ERR_ARG;
     *nsteps = g->ck_n;
     if (dt)
@@ -1351,6 +1405,7 @@ int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt)
 
 int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int mem)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !out || step < 0 || step >= g->ck_n) return ESMM_ERR_ARG;
     size_t N = (size_t)g->Ntot;
     const double *b = (*g->ck)[step];
@@ -1369,6 +1424,7 @@ int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int m
 
 int esmm_adjoint_replay(esmm_grid *g, int nsteps)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || nsteps < 0 || nsteps > g->ck_n || g->nprob != 1) return ESMM_ERR_ARG;
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     size_t N = (size_t)g->Ntot;
@@ -1382,6 +1438,7 @@ int esmm_adjoint_replay(esmm_grid *g, int nsteps)
 
 int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !lam_final || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->ck_n < 1) return fail(g, ESMM_ERR_STATE, "no recorded steps");
     int rc;
@@ -1496,6 +1553,7 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
 
 int esmm_profile(esmm_grid *g, int mask)
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || mask < 0 || mask >= (1 << ESMM_NKINDS)) return ESMM_ERR_ARG;
     CK(cudaStreamSynchronize(g->st));
     for (int k = 0; k < ESMM_NKINDS; ++k) {
@@ -1510,6 +1568,7 @@ int esmm_profile(esmm_grid *g, int mask)
 int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
                       long long timed[ESMM_NKINDS])
 {
+    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g) return ESMM_ERR_ARG;
     CK(cudaStreamSynchronize(g->st));
     for (int k = 0; k < ESMM_NKINDS; ++k) {
@@ -1529,6 +1588,7 @@ int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[E
 int esmm_last_error(esmm_grid *g, int *n_c2p_fail, char *msg, int len)
 {
     if (!g) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_last_error(g->g3, n_c2p_fail, msg, len);
     int h[2] = {0, 0};
     CK(cudaMemcpyAsync(h, g->status, sizeof h, cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));

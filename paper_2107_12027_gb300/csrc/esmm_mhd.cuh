@@ -7,8 +7,8 @@
 // (rho, v_1, v_2, v_3, p, B_1, B_2, B_3).  Node data extend the RHD layout of
 // esmm_device.cuh (indices 0..13 keep their meaning) by u_3 and B_1..B_3, so
 // the mesh, temporal-metric and totals kernels serve both systems.
-// Single problems, 2D (the metric vector has no x_3 part).  Holds kernel
-// definitions: include it from esmm_mhd.cu only.
+// Device arithmetic and the templated kernels; the 2D instantiations live in
+// esmm_mhd.cu and the 3D kernels (esmm_3d.cu) reuse the arithmetic.
 #pragma once
 
 #include "esmm_device.cuh"
@@ -175,7 +175,7 @@ __device__ __forceinline__ void mhd_phiprime(const double w[8], double P[8])
 // their span (pivoted Gram-Schmidt of the projected C-space unit vectors).
 constexpr double MHD_CLUSTER_TOL = 1.0e-5;
 
-__device__ __noinline__ void eigen_mhd(double gam, const double w[8], double lam[8], double R[8][8],
+static __device__ __noinline__ void eigen_mhd(double gam, const double w[8], double lam[8], double R[8][8],
                                        bool want_vectors)
 {
     double Pp[8];
@@ -376,13 +376,14 @@ __device__ __forceinline__ NodeM load_node_m(const double *__restrict__ q, long 
 }
 
 // Curvilinear two-point EC flux (Sec. 3.1) of one node pair:
-//   out = mt U~ + mx F~_1 + my F~_2 with the averaged metrics mt, mx, my.
+//   out = mt U~ + sum_{j<NJ} m_j F~_j with the averaged metrics mt, m.
 // U~: the paper's U~^RMHD with R_1 summed over three components and its
 // magnetic term 1/2 {{W (b^k)^2}}; F~_j: coefficient matching with exact
 // product-rule expansions, including the -{{B_j}}[[Phi]] term.  Here
 // b = (B + (u.B) u)/W, b^0 = u.B, c = W b^0, v = u/W.
+template <int NJ>
 __device__ __forceinline__ void ec_pair_mhd(const NodeM &L, const NodeM &Rn, double gm1inv, double thr, double mt,
-                                            double mx, double my, double out[8])
+                                            const double m[3], double out[8])
 {
     double rln, irln, bln, ibln;
     logmean<double, double>(L.rho, Rn.rho, L.lnr, Rn.lnr, thr, rln, irln);
@@ -439,10 +440,10 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeM &L, const NodeM &Rn, dou
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) out[a] = mt * Ut[a];
-    // F~_j, j = 1, 2
+    // F~_j, j = 1..NJ
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const double mj = j == 0 ? mx : my;
+    for (int j = 0; j < NJ; ++j) {
+        const double mj = m[j];
         double ujbsq = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) ujbsq += 0.5 * (L.u[j] * bL[k] * bL[k] + Rn.u[j] * bR[k] * bR[k]);
@@ -602,8 +603,8 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
             const long long cl = c0 - s * sd, cr = cl + n * sd;
             NodeM l = load_node_m(q, g.P, cl), r = load_node_m(q, g.P, cr);
             double out[8];
-            ec_pair_mhd(l, r, gm1inv, ph.ln_thr, 0.5 * (Mt[cl] + Mt[cr]), 0.5 * (Mx[cl] + Mx[cr]),
-                        0.5 * (My[cl] + My[cr]), out);
+            const double mm[3] = {0.5 * (Mx[cl] + Mx[cr]), 0.5 * (My[cl] + My[cr]), 0.0};
+            ec_pair_mhd<2>(l, r, gm1inv, ph.ln_thr, 0.5 * (Mt[cl] + Mt[cr]), mm, out);
 #pragma unroll
             for (int a = 0; a < 8; ++a) Fs[a] += out[a];
             Fts += 0.5 * (Mt[cl] + Mt[cr]);
@@ -718,64 +719,6 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
     out[9 * g.P] = Bt;
 }
 
-// d/dt = -sum_k (F_k(i+1/2) - F_k(i-1/2)) - Phi'(V_i) sum_k (B~_k(i+1/2) -
-// B~_k(i-1/2)) (eq. RMHDSemiU_O2p_ES), dJ/dt from the metric flux; written
-// out (dcons != NULL) or combined into the SSP-RK3 stage as in k_update.
-__global__ void k_update_mhd(ProbArg pa, const double *__restrict__ q, const double *__restrict__ fl,
-                             double *__restrict__ dcons, double *__restrict__ dJ, const double *__restrict__ cn,
-                             const double *__restrict__ Jn_, const double *__restrict__ xn,
-                             const double *__restrict__ cs, const double *__restrict__ Js,
-                             const double *__restrict__ xs, const double *__restrict__ xdot, double A, double B,
-                             const double *__restrict__ dt_dev, double *__restrict__ co, double *__restrict__ Jo,
-                             double *__restrict__ xo)
-{
-    ProbDesc D;
-    long long lb;
-    int b = locate(pa, D, lb);
-    const Geom &g = D.g;
-    long long id = lb * blockDim.x + threadIdx.x;
-    if (id >= g.N) return;
-    int i = (int)(id % g.nx), j = (int)(id / g.nx);
-    long long c = pidx(g, i, j);
-    const double *f0 = fl, *f1 = fl + NFM * g.P;
-    double L[10];
-#pragma unroll
-    for (int a = 0; a < 10; ++a) {
-        double d0 = f0[a * g.P + c] - f0[a * g.P + c - 1];
-        double d1 = f1[a * g.P + c] - f1[a * g.P + c - g.px];
-        L[a] = -(d0 + d1);
-    }
-    // Powell source: L[9] = -div B~ here
-    double iW = 1.0 / q[Q_W * g.P + c];
-    double w[8];
-    w[1] = q[Q_UX * g.P + c] * iW;
-    w[2] = q[Q_UY * g.P + c] * iW;
-    w[3] = q[QM_UZ * g.P + c] * iW;
-    w[5] = q[QM_B1 * g.P + c];
-    w[6] = q[QM_B2 * g.P + c];
-    w[7] = q[QM_B3 * g.P + c];
-    double Pp[8];
-    mhd_phiprime(w, Pp);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) L[a] += Pp[a] * L[9];
-    if (dcons) {
-#pragma unroll
-        for (int a = 0; a < 8; ++a) dcons[a * g.N + id] = L[a];
-        dJ[id] = L[8];
-        return;
-    }
-    double dt = dt_dev[b];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) co[a * g.N + id] = A * cn[a * g.N + id] + B * (cs[a * g.N + id] + dt * L[a]);
-    Jo[id] = A * Jn_[id] + B * (Js[id] + dt * L[8]);
-    xo[id] = A * xn[id] + B * (xs[id] + dt * xdot[id]);
-    xo[g.N + id] = A * xn[g.N + id] + B * (xs[g.N + id] + dt * xdot[g.N + id]);
-}
-
-// spectral radius rho_k = L_k max_m |lambda_m| / J (eq. cfl, static mesh)
-__global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
-                          unsigned long long *red);
-
 // initial J and cons = J U(prim)
 template <int P>
 __global__ void k_init_state_mhd(ProbArg pa, double gam, const double *__restrict__ prim,
@@ -812,24 +755,6 @@ __global__ void k_init_state_mhd(ProbArg pa, double gam, const double *__restric
     J[id] = J0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) cons[a * g.N + id] = J0 * U[a];
-}
-
-__global__ void k_prim_out_mhd(ProbArg pa, double gam, const double *__restrict__ cons,
-                               const double *__restrict__ J, double *__restrict__ prim, int *status)
-{
-    ProbDesc D;
-    long long lb;
-    locate(pa, D, lb);
-    const Geom &g = D.g;
-    long long id = lb * blockDim.x + threadIdx.x;
-    if (id >= g.N) return;
-    double iJ = 1.0 / J[id];
-    double U[8], w[8], Z;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) U[a] = cons[a * g.N + id] * iJ;
-    if (cons2prim_mhd(gam, U, -1.0, w, Z)) atomicAdd(status, 1);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) prim[a * g.N + id] = w[a];
 }
 
 }  // namespace esmm

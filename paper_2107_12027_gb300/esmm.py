@@ -363,6 +363,73 @@ class Grid:
         return n.value, buf.value.decode()
 
 
+class Grid3(Grid):
+    """One 3D RMHD problem (n = (nx, ny, nz)); arrays are [c][z][y][x] with 8
+    state components and 3 mesh components."""
+
+    def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC, PERIODIC, PERIODIC),
+                 gamma=4.0 / 3.0, p=2, w=5, stream=None, **params):
+        self.nx, self.ny, self.nz = int(n[0]), int(n[1]), int(n[2])
+        self.N = self.nx * self.ny * self.nz
+        self.phys, self.nv = RMHD, 8
+        h = ctypes.c_void_p()
+        nn = (ctypes.c_int * 3)(self.nx, self.ny, self.nz)
+        lo3 = (ctypes.c_double * 3)(*lo)
+        hi3 = (ctypes.c_double * 3)(*hi)
+        bc3 = (ctypes.c_int * 3)(*bc)
+        st = ctypes.c_void_p(stream) if stream is not None else None
+        self._check(lib().esmm_grid_create(ctypes.byref(h), 3, nn, lo3, hi3, RMHD, bc3, st))
+        self.h = h
+        self.set_eos(gamma)
+        self.set_order(p, w)
+        if params:
+            self.set_params(**params)
+
+    def _shape(self, c):
+        return (c, self.nz, self.ny, self.nx) if c > 1 else (self.nz, self.ny, self.nx)
+
+    def state_set(self, prim, x=None):
+        pp, mp = _ptr(prim, 8 * self.N)
+        px, mx = _ptr(x, 3 * self.N)
+        self._check(lib().esmm_state_set(self.h, pp, px, _mem((pp, mp), (px, mx))))
+
+    def state_set_cons(self, cons, J, x, t=0.0):
+        a = [_ptr(cons, 8 * self.N), _ptr(J, self.N), _ptr(x, 3 * self.N)]
+        self._check(lib().esmm_state_set_cons(self.h, a[0][0], a[1][0], a[2][0], float(t), _mem(*a)))
+
+    def state_get(self, what, out=None):
+        size = {GET_PRIM: 8, GET_CONS: 8, GET_J: 1, GET_X: 3, GET_XDOT: 3}[what]
+        if out is None:
+            out = np.empty(self._shape(size))
+        po, mo = _ptr(out, size * self.N)
+        self._check(lib().esmm_state_get(self.h, what, po, mo))
+        return out
+
+    def rhs(self, cons, J, x, xdot=None, dcons=None, dJ=None):
+        host = not _is_torch(cons)
+        if dcons is None:
+            if host:
+                dcons, dJ = np.empty(self._shape(8)), np.empty(self._shape(1))
+            else:
+                import torch
+                dcons = torch.empty(self._shape(8), dtype=torch.float64, device=cons.device)
+                dJ = torch.empty(self._shape(1), dtype=torch.float64, device=cons.device)
+        a = [_ptr(cons, 8 * self.N), _ptr(J, self.N), _ptr(x, 3 * self.N)]
+        xd = _ptr(xdot, 3 * self.N)
+        o = [_ptr(dcons, 8 * self.N), _ptr(dJ, self.N)]
+        mem = _mem(*a, *o, *([xd] if xdot is not None else []))
+        self._check(lib().esmm_rhs(self.h, a[0][0], a[1][0], a[2][0], xd[0], o[0][0], o[1][0], mem))
+        return dcons, dJ
+
+    def mesh_redistribute(self, dt=0.0):
+        """(xdot, dtau, dt) as :meth:`Grid.mesh_redistribute`, in 3D."""
+        xdot = np.empty(self._shape(3))
+        tau, dtu = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().esmm_mesh_redistribute(self.h, float(dt), ctypes.c_void_p(xdot.ctypes.data),
+                                                  ctypes.byref(tau), ctypes.byref(dtu), MEM_HOST))
+        return xdot, tau.value, dtu.value
+
+
 class Batch(Grid):
     """Many independent 2D RHD problems of different sizes in one handle.
 
