@@ -15,6 +15,14 @@ scaling, no data-path collective).
 
 ``--impl reference`` times the FP64 CPU oracle (the paper's method restated
 plainly in C) on the host cores over a bounded sample of the same workload.
+
+``--workload rotor`` (2D RMHD rotor, 512^2, Gamma = 4/3, alpha = 800) and
+``--workload blast3d`` (3D RMHD blast, 128^3, CFL 0.3) time the RMHD paths in
+FP64 on the same metric.  Each timed step advances the workload's initial
+state by one full step (the state is restored on the device between steps,
+outside the timed events): the untapered rotor loses admissibility after a
+few steps (the scheme has no positivity limiter), and restoring keeps every
+timed step a valid one.
 """
 from __future__ import annotations
 
@@ -46,6 +54,12 @@ FP64_FLOP_PER_CLK_SM = 4
 # DRAM bytes (read + write) of one interface-kernel launch in that capture;
 # None whenever the kernel has changed since the counters were taken.
 TRAFFIC_IFACE_F64 = 23.48e6
+# The same for the RMHD interface kernels (k_iface_mhd<2,5>, k3_iface<2,5>),
+# from their captures (profiles/iface_mhd_*.md); None until measured.
+FLOPS_PER_IFACE_MHD2 = None
+TRAFFIC_IFACE_MHD2 = None
+FLOPS_PER_IFACE_MHD3 = None
+TRAFFIC_IFACE_MHD3 = None
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
@@ -57,7 +71,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--n", type=int, default=None, help="nodes per side (default per workload)")
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "rotor", "blast3d"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and mixed-form legs")
     return ap.parse_args()
 
@@ -372,8 +387,105 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- RMHD workloads
+def run_rmhd(args):
+    """Time the 2D RMHD rotor or the 3D RMHD blast (FP64) on one GPU."""
+    import torch
+    from paper_2107_12027_gb300 import esmm
+    from paper_2107_12027_gb300 import workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    esmm.lib()
+    stream = torch.cuda.Stream()
+    three = args.workload == "blast3d"
+    n = args.n or (128 if three else 512)
+    K, W = args.steps, args.warmup
+    if three:
+        x, prim = wl.blast3_config(n)
+        g = esmm.Grid3((n, n, n), (-0.5,) * 3, (0.5,) * 3, bc=(1, 1, 1), p=2, w=5, stream=stream.cuda_stream)
+        nodes = n ** 3
+        ifaces = (n + 1) * n * n
+        desc = ("3D RMHD blast, %d^3 nodes on [-0.5,0.5]^3, outflow, Gamma=4/3, sphere r<0.1 with p=1, rho=1e-2, "
+                "background p=5e-4, rho=1e-4, B=(0.1,0,0), at rest, adaptive moving mesh (sigma=ln rho, alpha=800), "
+                "4th-order EC flux (p=2) + WENO5, SSP-RK3, CFL 0.3" % n)
+        flops, traffic, kname = FLOPS_PER_IFACE_MHD3, TRAFFIC_IFACE_MHD3, "k3_iface<2,5>"
+    else:
+        x, prim = wl.rotor_config(n)
+        g = esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
+                      stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO)
+        nodes = n * n
+        ifaces = (n + 1) * n
+        desc = ("2D RMHD rotor, %dx%d nodes on [-0.5,0.5]^2, outflow, Gamma=4/3, disk r<0.1 with rho=10 at angular "
+                "speed 9.95, background rho=1, p=1, B=(1,0,0), adaptive moving mesh (sigma=ln rho, alpha=800), "
+                "4th-order EC flux (p=2) + WENO5 + Powell source, SSP-RK3, CFL 0.4" % (n, n))
+        flops, traffic, kname = FLOPS_PER_IFACE_MHD2, TRAFFIC_IFACE_MHD2, "k_iface_mhd<2,5>"
+    g.state_set(prim, x)
+    dev = torch.device("cuda", local)
+    c0 = torch.empty(((8,) + tuple(prim.shape[1:])), dtype=torch.float64, device=dev)
+    J0 = torch.empty(tuple(prim.shape[1:]), dtype=torch.float64, device=dev)
+    x0 = torch.empty(((3 if three else 2,) + tuple(prim.shape[1:])), dtype=torch.float64, device=dev)
+    g.state_get(esmm.GET_CONS, c0)
+    g.state_get(esmm.GET_J, J0)
+    g.state_get(esmm.GET_X, x0)
+    torch.cuda.synchronize()
+    for _ in range(W):
+        g.state_set_cons(c0, J0, x0)
+        g.rk_step()
+    if not three:
+        g.profile(1 << esmm.KIND_IFACE)
+    flush = None if three else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    clock = ClockSampler(local)
+    clock.start()
+    total_ms = 0.0
+    for _ in range(K):
+        g.state_set_cons(c0, J0, x0)
+        if flush is not None:
+            flush.zero_()
+            torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.rk_step(sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    clk = clock.stop()
+    nfail, msg = g.last_error()
+    if nfail:
+        raise RuntimeError("primitive recovery failed at %d nodes: %s" % (nfail, msg))
+    roof, launches = None, None
+    if not three:
+        prof = g.profile_read()
+        launches = int(sum(v[1] for v in prof.values()))
+        iface_ms, _, iface_timed = prof["iface"]
+        avg = iface_ms * 1e-3 / max(iface_timed, 1)
+        peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        ach = flops * ifaces / avg / 1e12 if flops else None
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": kname,
+                "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms,
+                "peak_note": "derived FP64 peak: 152 SMs x 4 flop/clk x 2070 MHz"}
+    g.close()
+    line = {"metric": METRIC, "value": nodes * 3 * K / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "nodes": nodes, "form": "fp64",
+                       "steps": "each from the initial state (restored on the device, outside the timed events)",
+                       "l2": ("working set (~0.5 GB of node data) larger than L2" if three
+                              else "flushed (256 MB write) before every timed step"),
+                       "parallelism": "single GPU"},
+            "roofline": roof, "clocks": clk}
+    if launches is not None:
+        line["gpu_launches"] = launches
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != "riemann":
+        run_rmhd(args)
+        return
+    if args.n is None:
+        args.n = N_SIDE
     if args.impl == "reference":
         run_reference(args)
     else:
