@@ -51,6 +51,9 @@ FLOPS_PER_IFACE_F64 = 1430
 # Derived FP64 peak of GB300: 152 SMs x 4 FP64 flop/clk/SM (1.25 TFLOP/s at
 # the 2070 MHz maximum SM clock).
 FP64_FLOP_PER_CLK_SM = 4
+# FP32: 128 FMA lanes per SM, 256 flop/clk/SM (80.5 TFLOP/s at 2070 MHz); the
+# peak of the mixed form's interface kernel.
+FP32_FLOP_PER_CLK_SM = 256
 # DRAM bytes (read + write) of one interface-kernel launch in that capture;
 # None whenever the kernel has changed since the counters were taken.
 TRAFFIC_IFACE_F64 = 23.48e6
@@ -388,8 +391,39 @@ def run_gpu(args):
 
 
 # ---------------------------------------------------------------- RMHD workloads
+def rotor_mixed_vs_fp64(torch, n, stream, nsteps=1):
+    """Mixed form against the FP64 form on the rotor after nsteps steps with
+    the FP64 form's time steps: L1 density error and total-entropy difference.
+    The untapered 512^2 rotor loses admissibility in its second step in
+    either form (the disk edge is a jump of 10 in density moving at 0.995),
+    so the comparison takes one step."""
+    from paper_2107_12027_gb300 import esmm
+    from paper_2107_12027_gb300 import workloads as wl
+    x, prim = wl.rotor_config(n)
+    out = {}
+    for form in ("fp64", "mixed"):
+        with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
+                       stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,
+                       precision=esmm.MIXED if form == "mixed" else esmm.FP64) as g:
+            g.state_set(prim, x)
+            S0 = g.totals()[0]
+            if form == "fp64":
+                dts = [g.rk_step() for _ in range(nsteps)]
+            else:
+                for dt in dts:
+                    g.advance(1, dt)
+            out[form] = (g.state_get(esmm.GET_PRIM)[0], g.totals()[0], S0)
+    rf, rm = out["fp64"][0], out["mixed"][0]
+    return {"steps": nsteps, "dt": dts,
+            "l1_rho_rel": float(np.abs(rm - rf).mean() / np.abs(rf).mean()),
+            "entropy_rel_diff": float(abs(out["mixed"][1] - out["fp64"][1]) / abs(out["fp64"][1])),
+            "entropy_change_fp64": float((out["fp64"][1] - out["fp64"][2]) / abs(out["fp64"][2])),
+            "entropy_change_mixed": float((out["mixed"][1] - out["mixed"][2]) / abs(out["mixed"][2]))}
+
+
 def run_rmhd(args):
-    """Time the 2D RMHD rotor or the 3D RMHD blast (FP64) on one GPU."""
+    """Time the 2D RMHD rotor (FP64 or mixed form) or the 3D RMHD blast (FP64)
+    on one GPU."""
     import torch
     from paper_2107_12027_gb300 import esmm
     from paper_2107_12027_gb300 import workloads as wl
@@ -398,6 +432,8 @@ def run_rmhd(args):
     esmm.lib()
     stream = torch.cuda.Stream()
     three = args.workload == "blast3d"
+    if three and args.form != "fp64":
+        raise SystemExit("the 3D blast runs in the FP64 form only")
     n = args.n or (128 if three else 512)
     K, W = args.steps, args.warmup
     if three:
@@ -412,13 +448,16 @@ def run_rmhd(args):
     else:
         x, prim = wl.rotor_config(n)
         g = esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
-                      stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO)
+                      stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,
+                      precision=esmm.MIXED if args.form == "mixed" else esmm.FP64)
         nodes = n * n
         ifaces = (n + 1) * n
         desc = ("2D RMHD rotor, %dx%d nodes on [-0.5,0.5]^2, outflow, Gamma=4/3, disk r<0.1 with rho=10 at angular "
                 "speed 9.95, background rho=1, p=1, B=(1,0,0), adaptive moving mesh (sigma=ln rho, alpha=800), "
                 "4th-order EC flux (p=2) + WENO5 + Powell source, SSP-RK3, CFL 0.4" % (n, n))
-        flops, traffic, kname = FLOPS_PER_IFACE_MHD2, TRAFFIC_IFACE_MHD2, "k_iface_mhd<2,5>"
+        flops, traffic, kname = FLOPS_PER_IFACE_MHD2, TRAFFIC_IFACE_MHD2, "k_iface_mhd<double,2,5>"
+        if args.form == "mixed":
+            flops, traffic, kname = None, None, "k_iface_mhd<float,2,5>"
     g.state_set(prim, x)
     dev = torch.device("cuda", local)
     c0 = torch.empty(((8,) + tuple(prim.shape[1:])), dtype=torch.float64, device=dev)
@@ -458,17 +497,20 @@ def run_rmhd(args):
         launches = int(sum(v[1] for v in prof.values()))
         iface_ms, _, iface_timed = prof["iface"]
         avg = iface_ms * 1e-3 / max(iface_timed, 1)
-        peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        mixed = args.form == "mixed"
+        per_clk = FP32_FLOP_PER_CLK_SM if mixed else FP64_FLOP_PER_CLK_SM
+        peak = N_SM * per_clk * SM_MAX_MHZ * 1e6 / 1e12
         ach = flops * ifaces / avg / 1e12 if flops else None
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": kname,
                 "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms,
-                "peak_note": "derived FP64 peak: 152 SMs x 4 flop/clk x 2070 MHz"}
+                "peak_note": "derived %s peak: 152 SMs x %d flop/clk x 2070 MHz" % ("FP32" if mixed else "FP64",
+                                                                                  per_clk)}
     g.close()
     line = {"metric": METRIC, "value": nodes * 3 * K / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "nodes": nodes, "form": "fp64",
+            "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": desc, "nodes": nodes, "form": args.form,
                        "steps": "each from the initial state (restored on the device, outside the timed events)",
                        "l2": ("working set (~0.5 GB of node data) larger than L2" if three
                               else "flushed (256 MB write) before every timed step"),
@@ -476,6 +518,27 @@ def run_rmhd(args):
             "roofline": roof, "clocks": clk}
     if launches is not None:
         line["gpu_launches"] = launches
+    if not three and args.form == "fp64" and not args.no_extras:
+        with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
+                       stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,
+                       precision=esmm.MIXED) as gm:
+            gm.state_set(prim, x)
+            tm = 0.0
+            for k in range(W + K):
+                gm.state_set_cons(c0, J0, x0)
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gm.rk_step(sync=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k >= W:
+                    tm += e0.elapsed_time(e1)
+            if gm.last_error()[0]:
+                raise RuntimeError("mixed form: primitive recovery failed")
+        line["forms"] = {"mixed": {"value": nodes * 3 * K / (tm * 1e-3), "ms_per_step": tm / K}}
+        line["forms"]["mixed"].update(rotor_mixed_vs_fp64(torch, n, stream))
     print(json.dumps(line), flush=True)
 
 

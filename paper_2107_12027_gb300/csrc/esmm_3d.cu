@@ -223,6 +223,8 @@ __device__ __forceinline__ NodeM load3(const double *__restrict__ q, long long P
     v.beta = q[F_BETA * P + c];
     v.lnr = q[F_LNR * P + c];
     v.lnb = q[F_LNB * P + c];
+    v.r = v.rho;
+    v.b = v.beta;
     v.W = q[F_W * P + c];
     v.u[0] = q[F_U0 * P + c];
     v.u[1] = q[F_U1 * P + c];

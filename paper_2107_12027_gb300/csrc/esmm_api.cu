@@ -62,7 +62,7 @@ struct esmm_grid {
     double *q;                       // [NQ][Ptot] (RMHD: [NQ_MHD][Ptot])
     double *pg[3];                   // recovery warm starts (p; RMHD: Z), state -> stage 2 -> stage 3
     void *pairs;                     // [2][PMAX][4][Ptot] of the working precision (RHD)
-    void *iflux;                     // [2][5][Ptot] of the working precision (RMHD: [2][NF_MHD][Ptot] FP64)
+    void *iflux;                     // [2][5][Ptot] (RMHD: [2][NF_MHD][Ptot]) of the working precision
     double *in_cons, *in_J, *in_x, *in_xdot, *out_dc, *out_dJ;  // host-mode staging
     // mesh redistribution
     double *grad, *om, *om2, *X, *Xn;
@@ -282,7 +282,8 @@ void fluxes(esmm_grid *g)
         LaunchDom Lp = dom(g, dir == 0 ? D_PAIR0 : D_PAIR1), Li = dom(g, dir == 0 ? D_IFACE0 : D_IFACE1);
         if (g->phys == ESMM_RMHD) {   // two-point fluxes summed inside the interface kernel
             Prof pr_(g, ESMM_KIND_IFACE);
-            launch_iface_mhd(Li, ph, g->q, (double *)g->iflux, dir, g->st);
+            if (f32) launch_iface_mhd_f32(Li, ph, g->q, g->iflux, dir, g->st);
+            else launch_iface_mhd(Li, ph, g->q, g->iflux, dir, g->st);
             continue;
         }
         {
@@ -304,9 +305,12 @@ void update(esmm_grid *g, double *dcons, double *dJ, const double *cn, const dou
 {
     Prof pr_(g, ESMM_KIND_UPDATE);
     LaunchDom L = dom(g, D_NODE);
-    if (g->phys == ESMM_RMHD)
-        launch_update_mhd(L, g->q, (const double *)g->iflux, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B,
-                          g->dt_dev, co, Jo, xo, g->st);
+    if (g->phys == ESMM_RMHD && g->prm.precision == ESMM_MIXED)
+        launch_update_mhd_f32(L, g->q, g->iflux, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B, g->dt_dev, co, Jo,
+                              xo, g->st);
+    else if (g->phys == ESMM_RMHD)
+        launch_update_mhd(L, g->q, g->iflux, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B, g->dt_dev, co, Jo, xo,
+                          g->st);
     else if (g->prm.precision == ESMM_MIXED)
         k_update<float><<<L.nblk, L.bs, 0, g->st>>>(L.pa, (const float *)g->iflux, dcons, dJ, cn, Jn, xn, cs, Js, xs,
                                                     xdot, A, B, g->dt_dev, co, Jo, xo);
@@ -894,8 +898,12 @@ int tune(esmm_grid *g)
                 } else if (g->phys == ESMM_RMHD) {
                             ms = c.kind == D_PAIR0 ? 0.0f : time_it([&]() {
                                 for (int dir = 0; dir < 2; ++dir)
-                                    launch_iface_mhd(dom(g, dir ? c.kind2 : c.kind), ph, g->q, (double *)g->iflux,
-                                                     dir, g->st);
+                                    if (f32)
+                                        launch_iface_mhd_f32(dom(g, dir ? c.kind2 : c.kind), ph, g->q, g->iflux,
+                                                             dir, g->st);
+                                    else
+                                        launch_iface_mhd(dom(g, dir ? c.kind2 : c.kind), ph, g->q, g->iflux, dir,
+                                                         g->st);
                             });
                 } else {
                     ms = time_it([&]() {
@@ -1094,8 +1102,6 @@ int esmm_set_params(esmm_grid *g, const esmm_params *prm)
         (prm->monitor != ESMM_MONITOR_RHO && prm->monitor != ESMM_MONITOR_LNRHO))
         return fail(g, ESMM_ERR_ARG, "invalid parameter");
     if (g->dim == 3) return esmm3_set_params(g->g3, prm);
-    if (g->phys == ESMM_RMHD && prm->precision != ESMM_FP64)
-        return fail(g, ESMM_ERR_ARG, "RMHD grids compute in FP64 only");
     g->prm = *prm;
     g->epoch++;
     return ESMM_OK;

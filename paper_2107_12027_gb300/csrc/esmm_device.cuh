@@ -194,6 +194,40 @@ __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ float val(float x) { return x; }
 __device__ __forceinline__ double val(dual x) { return x.v; }
 
+// The FP32 dual number (directional derivatives inside the FP32 bulk form).
+// FP64 constants are rounded to FP32 before they meet an fdual, so no FP64
+// arithmetic runs on its values.
+struct fdual {
+    float v, d;
+    __host__ __device__ fdual() {}
+    __host__ __device__ constexpr fdual(float a) : v(a), d(0.0f) {}
+    __host__ __device__ constexpr fdual(float a, float b) : v(a), d(b) {}
+};
+__device__ __forceinline__ fdual operator+(fdual a, fdual b) { return fdual(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ fdual operator-(fdual a, fdual b) { return fdual(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ fdual operator-(fdual a) { return fdual(-a.v, -a.d); }
+__device__ __forceinline__ fdual operator*(fdual a, fdual b) { return fdual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ fdual operator/(fdual a, fdual b)
+{
+    float r = __frcp_rn(b.v);
+    float q = a.v * r;
+    return fdual(q, (a.d - q * b.d) * r);
+}
+__device__ __forceinline__ fdual operator+(fdual a, double b) { return fdual(a.v + (float)b, a.d); }
+__device__ __forceinline__ fdual operator+(double a, fdual b) { return fdual((float)a + b.v, b.d); }
+__device__ __forceinline__ fdual operator-(fdual a, double b) { return fdual(a.v - (float)b, a.d); }
+__device__ __forceinline__ fdual operator-(double a, fdual b) { return fdual((float)a - b.v, -b.d); }
+__device__ __forceinline__ fdual operator*(fdual a, double b) { return fdual(a.v * (float)b, a.d * (float)b); }
+__device__ __forceinline__ fdual operator*(double a, fdual b) { return fdual((float)a * b.v, (float)a * b.d); }
+__device__ __forceinline__ fdual operator/(fdual a, double b) { return a / fdual((float)b); }
+__device__ __forceinline__ fdual operator/(double a, fdual b) { return fdual((float)a) / b; }
+__device__ __forceinline__ fdual &operator+=(fdual &a, fdual b) { a = a + b; return a; }
+__device__ __forceinline__ fdual &operator-=(fdual &a, fdual b) { a = a - b; return a; }
+
+// the dual number over a working precision
+template <typename R> struct DualOf { using type = dual; };
+template <> struct DualOf<float> { using type = fdual; };
+
 // type of the log-mean arguments: FP64 for the FP64 and FP32-bulk forms
 template <typename R> struct LogT { using type = double; };
 template <> struct LogT<dual> { using type = dual; };
@@ -213,6 +247,11 @@ template <> __device__ __forceinline__ dual sq_rt<dual>(dual x)
 {
     double r = sqrt(x.v);
     return dual(r, 0.5 * x.d / r);
+}
+template <> __device__ __forceinline__ fdual sq_rt<fdual>(fdual x)
+{
+    float r = sqrtf(x.v);
+    return fdual(r, 0.5f * x.d * __frcp_rn(r));
 }
 // reciprocal (IEEE round-to-nearest) and a square root of a positive value
 // through the reciprocal square root: on GB300 both are cheaper than the

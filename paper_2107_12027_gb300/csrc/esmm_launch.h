@@ -42,21 +42,28 @@ void launch_node_vjp(const LaunchDom &L, double gam, int p, int w, const double 
 void launch_lincomb(long long n, double a, const double *x, double b, const double *y, double *out, cudaStream_t st);
 void launch_prim_grad(const LaunchDom &L, double gam, const double *cons, const double *J, const double *lam,
                       double *out, cudaStream_t st);
-// RMHD (esmm_mhd.cu), single problems, FP64: node pass (zg: warm starts of
+// RMHD (esmm_mhd.cu), single problems: node pass (zg: warm starts of
 // Z = rho h W^2), interface fluxes (10 values per direction: F[8], the metric
 // flux, the magnetic flux B~), update with the Powell source, CFL radius,
-// state set-up and read-out.  The node arrays hold 18 fields per padded node.
+// state set-up and read-out, all FP64; the _f32 pair (esmm_mhd_f32.cu) keeps
+// the interface fluxes in FP32 for the mixed form.  The node arrays hold 18
+// fields per padded node.
 constexpr int NQ_MHD = 18;
 constexpr int NF_MHD = 10;
 void launch_node_mhd(const LaunchDom &L, int p, double gam, const double *cons, const double *J, const double *x,
                      const double *xdot, const double *zg_in, double *zg_out, double *q, int *status,
                      cudaStream_t st);
-void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, double *iflux, int dir,
-                      cudaStream_t st);
-void launch_update_mhd(const LaunchDom &L, const double *q, const double *fl, double *dcons, double *dJ,
+void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, void *iflux, int dir, cudaStream_t st);
+void launch_update_mhd(const LaunchDom &L, const double *q, const void *fl, double *dcons, double *dJ,
                        const double *cn, const double *Jn, const double *xn, const double *cs, const double *Js,
                        const double *xs, const double *xdot, double A, double B, const double *dt_dev, double *co,
                        double *Jo, double *xo, cudaStream_t st);
+void launch_iface_mhd_f32(const LaunchDom &L, const Phys &ph, const double *q, void *iflux, int dir,
+                          cudaStream_t st);
+void launch_update_mhd_f32(const LaunchDom &L, const double *q, const void *fl, double *dcons, double *dJ,
+                           const double *cn, const double *Jn, const double *xn, const double *cs, const double *Js,
+                           const double *xs, const double *xdot, double A, double B, const double *dt_dev,
+                           double *co, double *Jo, double *xo, cudaStream_t st);
 void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,
                     cudaStream_t st);
 void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, const double *x, double *cons,

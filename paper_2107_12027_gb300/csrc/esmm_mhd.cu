@@ -6,60 +6,6 @@
 
 namespace esmm {
 
-// d/dt = -sum_k (F_k(i+1/2) - F_k(i-1/2)) - Phi'(V_i) sum_k (B~_k(i+1/2) -
-// B~_k(i-1/2)) (eq. RMHDSemiU_O2p_ES), dJ/dt from the metric flux; written
-// out (dcons != NULL) or combined into the SSP-RK3 stage as in k_update.
-__global__ void k_update_mhd(ProbArg pa, const double *__restrict__ q, const double *__restrict__ fl,
-                             double *__restrict__ dcons, double *__restrict__ dJ, const double *__restrict__ cn,
-                             const double *__restrict__ Jn_, const double *__restrict__ xn,
-                             const double *__restrict__ cs, const double *__restrict__ Js,
-                             const double *__restrict__ xs, const double *__restrict__ xdot, double A, double B,
-                             const double *__restrict__ dt_dev, double *__restrict__ co, double *__restrict__ Jo,
-                             double *__restrict__ xo)
-{
-    ProbDesc D;
-    long long lb;
-    int b = locate(pa, D, lb);
-    const Geom &g = D.g;
-    long long id = lb * blockDim.x + threadIdx.x;
-    if (id >= g.N) return;
-    int i = (int)(id % g.nx), j = (int)(id / g.nx);
-    long long c = pidx(g, i, j);
-    const double *f0 = fl, *f1 = fl + NFM * g.P;
-    double L[10];
-#pragma unroll
-    for (int a = 0; a < 10; ++a) {
-        double d0 = f0[a * g.P + c] - f0[a * g.P + c - 1];
-        double d1 = f1[a * g.P + c] - f1[a * g.P + c - g.px];
-        L[a] = -(d0 + d1);
-    }
-    // Powell source: L[9] = -div B~ here
-    double iW = 1.0 / q[Q_W * g.P + c];
-    double w[8];
-    w[1] = q[Q_UX * g.P + c] * iW;
-    w[2] = q[Q_UY * g.P + c] * iW;
-    w[3] = q[QM_UZ * g.P + c] * iW;
-    w[5] = q[QM_B1 * g.P + c];
-    w[6] = q[QM_B2 * g.P + c];
-    w[7] = q[QM_B3 * g.P + c];
-    double Pp[8];
-    mhd_phiprime(w, Pp);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) L[a] += Pp[a] * L[9];
-    if (dcons) {
-#pragma unroll
-        for (int a = 0; a < 8; ++a) dcons[a * g.N + id] = L[a];
-        dJ[id] = L[8];
-        return;
-    }
-    double dt = dt_dev[b];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) co[a * g.N + id] = A * cn[a * g.N + id] + B * (cs[a * g.N + id] + dt * L[a]);
-    Jo[id] = A * Jn_[id] + B * (Js[id] + dt * L[8]);
-    xo[id] = A * xn[id] + B * (xs[id] + dt * xdot[id]);
-    xo[g.N + id] = A * xn[g.N + id] + B * (xs[g.N + id] + dt * xdot[g.N + id]);
-}
-
 __global__ void k_prim_out_mhd(ProbArg pa, double gam, const double *__restrict__ cons,
                                const double *__restrict__ J, double *__restrict__ prim, int *status)
 {
@@ -127,34 +73,17 @@ void launch_node_mhd(const LaunchDom &L, int p, double gam, const double *cons, 
         k_node_mhd<3><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status);
 }
 
-template <int P>
-static void launch_iface_mhd_p(const LaunchDom &L, const Phys &ph, const double *q, double *iflux, int dir,
-                               cudaStream_t st)
+void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, void *iflux, int dir, cudaStream_t st)
 {
-    switch (ph.w) {
-    case 0: k_iface_mhd<P, 0><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
-    case 3: k_iface_mhd<P, 3><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
-    default: k_iface_mhd<P, 5><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
-    }
+    launch_iface_mhd_t<double>(L, ph, q, iflux, dir, st);
 }
 
-void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, double *iflux, int dir,
-                      cudaStream_t st)
-{
-    switch (ph.p) {
-    case 1: launch_iface_mhd_p<1>(L, ph, q, iflux, dir, st); break;
-    case 2: launch_iface_mhd_p<2>(L, ph, q, iflux, dir, st); break;
-    default: launch_iface_mhd_p<3>(L, ph, q, iflux, dir, st); break;
-    }
-}
-
-void launch_update_mhd(const LaunchDom &L, const double *q, const double *fl, double *dcons, double *dJ,
+void launch_update_mhd(const LaunchDom &L, const double *q, const void *fl, double *dcons, double *dJ,
                        const double *cn, const double *Jn, const double *xn, const double *cs, const double *Js,
                        const double *xs, const double *xdot, double A, double B, const double *dt_dev, double *co,
                        double *Jo, double *xo, cudaStream_t st)
 {
-    k_update_mhd<<<L.nblk, L.bs, 0, st>>>(L.pa, q, fl, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B, dt_dev, co,
-                                          Jo, xo);
+    launch_update_mhd_t<double>(L, q, fl, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B, dt_dev, co, Jo, xo, st);
 }
 
 void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "esmm_device.cuh"
+#include "esmm_launch.h"
 
 namespace esmm {
 
@@ -88,6 +89,7 @@ __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], doub
 template <typename T> __device__ __forceinline__ T lg(T x);
 template <> __device__ __forceinline__ double lg<double>(double x) { return log(x); }
 template <> __device__ __forceinline__ dual lg<dual>(dual x) { return dual(log(x.v), x.d / x.v); }
+template <> __device__ __forceinline__ fdual lg<fdual>(fdual x) { return fdual(logf(x.v), x.d * __frcp_rn(x.v)); }
 
 template <typename T>
 __device__ __forceinline__ void mhd_UFV(double gam, const T w[8], T U[8], T F[8], T V[8])
@@ -127,14 +129,16 @@ __device__ __forceinline__ void mhd_UFV(double gam, const T w[8], T U[8], T F[8]
 }
 
 // Images (dU, dV, dF~) of the primitive perturbation dir at w, with the
-// Godunov-Powell column: dF~ = dF_1 + Phi'(V) dB_1.
-__device__ __forceinline__ void mhd_images(double gam, const double w[8], const double dir[8], const double Pp[8],
-                                           double dU[8], double dV[8], double dF[8])
+// Godunov-Powell column: dF~ = dF_1 + Phi'(V) dB_1, in the working precision R.
+template <typename R>
+__device__ __forceinline__ void mhd_images(double gam, const R w[8], const R dir[8], const R Pp[8], R dU[8], R dV[8],
+                                           R dF[8])
 {
-    dual wd[8], U[8], F[8], V[8];
+    using D = typename DualOf<R>::type;
+    D wd[8], U[8], F[8], V[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) wd[a] = dual(w[a], dir[a]);
-    mhd_UFV<dual>(gam, wd, U, F, V);
+    for (int a = 0; a < 8; ++a) wd[a] = D(w[a], dir[a]);
+    mhd_UFV<D>(gam, wd, U, F, V);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
         dU[a] = U[a].d;
@@ -143,20 +147,22 @@ __device__ __forceinline__ void mhd_images(double gam, const double w[8], const 
     }
 }
 
-__device__ __forceinline__ double dot8(const double *a, const double *b)
+template <typename R>
+__device__ __forceinline__ R dot8(const R *a, const R *b)
 {
-    double s = 0.0;
+    R s = (R)0;
 #pragma unroll
     for (int r = 0; r < 8; ++r) s += a[r] * b[r];
     return s;
 }
 
 // Phi'(V) = (0, B/W^2 + v (v.B), v.B, v) (eq. Phi)
-__device__ __forceinline__ void mhd_phiprime(const double w[8], double P[8])
+template <typename R>
+__device__ __forceinline__ void mhd_phiprime(const R w[8], R P[8])
 {
-    double iW2 = 1.0 - (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
-    double vB = w[1] * w[5] + w[2] * w[6] + w[3] * w[7];
-    P[0] = 0.0;
+    R iW2 = (R)1 - (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+    R vB = w[1] * w[5] + w[2] * w[6] + w[3] * w[7];
+    P[0] = (R)0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) P[1 + k] = w[5 + k] * iW2 + w[1 + k] * vB;
     P[4] = vB;
@@ -175,48 +181,60 @@ __device__ __forceinline__ void mhd_phiprime(const double w[8], double P[8])
 // their span (pivoted Gram-Schmidt of the projected C-space unit vectors).
 constexpr double MHD_CLUSTER_TOL = 1.0e-5;
 
-static __device__ __noinline__ void eigen_mhd(double gam, const double w[8], double lam[8], double R[8][8],
-                                       bool want_vectors)
+template <typename R>
+static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8], R Rv[8][8], bool want_vectors)
 {
-    double Pp[8];
+    R Pp[8];
     mhd_phiprime(w, Pp);
-    const double v1 = w[1];
-    double a_rho[8] = {1, 0, 0, 0, 0, 0, 0, 0};
-    double a_div[8] = {0, 0, 0, 0, 0, 1.0 - v1 * v1, -v1 * w[2], -v1 * w[3]};
-    double Ur[8], Vr[8], Fr[8], Ud[8], Vd[8], Fd[8];
+    const R v1 = w[1];
+    R a_rho[8] = {(R)1, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+    R a_div[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)1 - v1 * v1, -v1 * w[2], -v1 * w[3]};
+    R Ur[8], Vr[8], Fr[8], Ud[8], Vd[8], Fd[8];
     mhd_images(gam, w, a_rho, Pp, Ur, Vr, Fr);
     mhd_images(gam, w, a_div, Pp, Ud, Vd, Fd);
-    const double n_rho = dot8(Ur, Vr), n_div = dot8(Ud, Vd);
+    const R n_rho = dot8(Ur, Vr), n_div = dot8(Ud, Vd);
     const int comp[6] = {1, 2, 3, 4, 6, 7};
-    double Uy[6][8], Vy[6][8], Fy[6][8];
+    R Uy[6][8], Vy[6][8], Fy[6][8];
     for (int a = 0; a < 6; ++a) {
-        double e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        e[comp[a]] = 1.0;
-        double Ue[8], Ve[8], Fe[8];
+        R e[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+        e[comp[a]] = (R)1;
+        R Ue[8], Ve[8], Fe[8];
         mhd_images(gam, w, e, Pp, Ue, Ve, Fe);
-        double cr = dot8(Ue, Vr) / n_rho, cd = dot8(Ue, Vd) / n_div;
+        R cr = dot8(Ue, Vr) / n_rho, cd = dot8(Ue, Vd) / n_div;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             Uy[a][r] = Ue[r] - cr * Ur[r] - cd * Ud[r];
             Vy[a][r] = Ve[r] - cr * Vr[r] - cd * Vd[r];
             Fy[a][r] = Fe[r] - cr * Fr[r] - cd * Fd[r];
         }
+        if (sizeof(R) == 4) {
+            // FP32: scale y_a to unit <y_a, y_a> (the Gram diagonal spans
+            // many decades at large W); C = L^-1 K L^-T is unchanged by it
+            R sa = rsq<R>(dot8(Uy[a], Vy[a]));
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                Uy[a][r] *= sa;
+                Vy[a][r] *= sa;
+                Fy[a][r] *= sa;
+            }
+        }
     }
-    double Gm[6][6], C[6][6];
+    R Gm[6][6], C[6][6];
     for (int a = 0; a < 6; ++a)
         for (int b = 0; b <= a; ++b) {
-            double g = 0.5 * (dot8(Uy[a], Vy[b]) + dot8(Uy[b], Vy[a]));
-            double k = 0.5 * (dot8(Vy[a], Fy[b]) + dot8(Vy[b], Fy[a]));
+            R g = (R)0.5 * (dot8(Uy[a], Vy[b]) + dot8(Uy[b], Vy[a]));
+            R k = (R)0.5 * (dot8(Vy[a], Fy[b]) + dot8(Vy[b], Fy[a]));
             Gm[a][b] = Gm[b][a] = g;
             C[a][b] = C[b][a] = k;
         }
     // Cholesky G = L L^T (lower triangle of Gm)
     for (int j = 0; j < 6; ++j) {
-        double d = Gm[j][j];
+        R d = Gm[j][j];
         for (int k = 0; k < j; ++k) d -= Gm[j][k] * Gm[j][k];
-        Gm[j][j] = sqrt(d);
+        if (sizeof(R) == 4 && !(d > (R)1.0e-12)) d = (R)1.0e-12;   // FP32: keep the factor finite
+        Gm[j][j] = sq_rt<R>(d);
         for (int i = j + 1; i < 6; ++i) {
-            double s = Gm[i][j];
+            R s = Gm[i][j];
             for (int k = 0; k < j; ++k) s -= Gm[i][k] * Gm[j][k];
             Gm[i][j] = s / Gm[j][j];
         }
@@ -224,28 +242,31 @@ static __device__ __noinline__ void eigen_mhd(double gam, const double w[8], dou
     // C <- L^-1 K L^-T (column solves, then row solves)
     for (int c = 0; c < 6; ++c)
         for (int i = 0; i < 6; ++i) {
-            double s = C[i][c];
+            R s = C[i][c];
             for (int k = 0; k < i; ++k) s -= Gm[i][k] * C[k][c];
             C[i][c] = s / Gm[i][i];
         }
     for (int r = 0; r < 6; ++r)
         for (int i = 0; i < 6; ++i) {
-            double s = C[r][i];
+            R s = C[r][i];
             for (int k = 0; k < i; ++k) s -= Gm[i][k] * C[r][k];
             C[r][i] = s / Gm[i][i];
         }
     for (int a = 0; a < 6; ++a)
-        for (int b = 0; b < a; ++b) C[a][b] = C[b][a] = 0.5 * (C[a][b] + C[b][a]);
-    double Q[6][6];
+        for (int b = 0; b < a; ++b) C[a][b] = C[b][a] = (R)0.5 * (C[a][b] + C[b][a]);
+    R Q[6][6];
     for (int a = 0; a < 6; ++a)
-        for (int b = 0; b < 6; ++b) Q[a][b] = a == b ? 1.0 : 0.0;
+        for (int b = 0; b < 6; ++b) Q[a][b] = a == b ? (R)1 : (R)0;
+    // converged when the off-diagonal part is at rounding level: (1e-15)^2
+    // of the diagonal in FP64, (1e-6)^2 in FP32 (the next sweep squares it)
+    const R conv = sizeof(R) == 4 ? (R)1.0e-12 : (R)1.0e-30;
     for (int sweep = 0; sweep < 50; ++sweep) {
-        double off = 0.0, dg = 0.0;
+        R off = (R)0, dg = (R)0;
         for (int a = 0; a < 6; ++a) {
             dg += C[a][a] * C[a][a];
             for (int b = a + 1; b < 6; ++b) off += C[a][b] * C[a][b];
         }
-        if (off <= 1.0e-30 * dg) break;
+        if (off <= conv * dg) break;
         // The rotation loops stay rolled: fully unrolled, this sweep came out
         // of nvcc 13.0 -O3 (sm_103a) as a non-similarity transform (wrong
         // eigenvalues; the host build and the -G build of the same source are
@@ -254,26 +275,26 @@ static __device__ __noinline__ void eigen_mhd(double gam, const double w[8], dou
         for (int p = 0; p < 5; ++p)
 #pragma unroll 1
             for (int q = p + 1; q < 6; ++q) {
-                if (C[p][q] == 0.0) continue;
-                double theta = (C[q][q] - C[p][p]) / (2.0 * C[p][q]);
-                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                if (C[p][q] == (R)0) continue;
+                R theta = (C[q][q] - C[p][p]) / ((R)2 * C[p][q]);
+                R t = (theta >= (R)0 ? (R)1 : (R)-1) / (fab<R>(theta) + sq_rt<R>(theta * theta + (R)1));
+                R cs = (R)1 / sq_rt<R>(t * t + (R)1), sn = t * cs;
 #pragma unroll 1
                 for (int k = 0; k < 6; ++k) {
-                    double ckp = C[k][p], ckq = C[k][q];
+                    R ckp = C[k][p], ckq = C[k][q];
                     C[k][p] = cs * ckp - sn * ckq;
                     C[k][q] = sn * ckp + cs * ckq;
                 }
 #pragma unroll 1
                 for (int k = 0; k < 6; ++k) {
-                    double cpk = C[p][k], cqk = C[q][k];
+                    R cpk = C[p][k], cqk = C[q][k];
                     C[p][k] = cs * cpk - sn * cqk;
                     C[q][k] = sn * cpk + cs * cqk;
                 }
                 if (want_vectors)
 #pragma unroll 1
                     for (int k = 0; k < 6; ++k) {
-                        double qkp = Q[k][p], qkq = Q[k][q];
+                        R qkp = Q[k][p], qkq = Q[k][q];
                         Q[k][p] = cs * qkp - sn * qkq;
                         Q[k][q] = sn * qkp + cs * qkq;
                     }
@@ -287,42 +308,42 @@ static __device__ __noinline__ void eigen_mhd(double gam, const double w[8], dou
     lam[1] = v1;
     for (int m = 0; m < 6; ++m) lam[2 + m] = C[ord[m]][ord[m]];
     if (!want_vectors) return;
-    double E6[6][6];
+    R E6[6][6];
     for (int m = 0; m < 6; ++m)
         for (int r = 0; r < 6; ++r) E6[r][m] = Q[r][ord[m]];
     int start = 0;
     while (start < 6) {
         int end = start + 1;
-        while (end < 6 && lam[2 + end] - lam[1 + end] < MHD_CLUSTER_TOL) ++end;
+        while (end < 6 && lam[2 + end] - lam[1 + end] < (R)MHD_CLUSTER_TOL) ++end;
         const int k = end - start;
         if (k > 1) {
-            double z[6][6], basis[6][6];
+            R z[6][6], basis[6][6];
             bool used[6] = {false, false, false, false, false, false};
             for (int i = 0; i < 6; ++i)
                 for (int c = 0; c < k; ++c) z[i][c] = E6[i][start + c];
             for (int t = 0; t < k; ++t) {
                 int best = -1;
-                double bn = -1.0;
+                R bn = (R)-1;
                 for (int i = 0; i < 6; ++i) {
                     if (used[i]) continue;
-                    double n2 = 0.0;
+                    R n2 = (R)0;
                     for (int c = 0; c < k; ++c) n2 += z[i][c] * z[i][c];
                     if (best < 0 || n2 > bn) { bn = n2; best = i; }
                 }
                 used[best] = true;
-                double inr = 1.0 / sqrt(bn);
+                R inr = (R)1 / sq_rt<R>(bn);
                 for (int c = 0; c < k; ++c) basis[t][c] = z[best][c] * inr;
                 for (int i = 0; i < 6; ++i) {
                     if (used[i]) continue;
-                    double pr = 0.0;
+                    R pr = (R)0;
                     for (int c = 0; c < k; ++c) pr += z[i][c] * basis[t][c];
                     for (int c = 0; c < k; ++c) z[i][c] -= pr * basis[t][c];
                 }
             }
-            double nE[6][6];
+            R nE[6][6];
             for (int t = 0; t < k; ++t)
                 for (int r = 0; r < 6; ++r) {
-                    double acc = 0.0;
+                    R acc = (R)0;
                     for (int c = 0; c < k; ++c) acc += E6[r][start + c] * basis[t][c];
                     nE[r][t] = acc;
                 }
@@ -331,47 +352,54 @@ static __device__ __noinline__ void eigen_mhd(double gam, const double w[8], dou
         }
         start = end;
     }
-    const double srho = rsqrt(n_rho), sdiv = rsqrt(n_div);
+    const R srho = rsq<R>(n_rho), sdiv = rsq<R>(n_div);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        R[r][0] = Ur[r] * srho;
-        R[r][1] = Ud[r] * sdiv;
+        Rv[r][0] = Ur[r] * srho;
+        Rv[r][1] = Ud[r] * sdiv;
     }
     for (int m = 0; m < 6; ++m) {
-        double s[6];
+        R s[6];
         for (int i = 5; i >= 0; --i) {
-            double acc = E6[i][m];
+            R acc = E6[i][m];
             for (int k = i + 1; k < 6; ++k) acc -= Gm[k][i] * s[k];
             s[i] = acc / Gm[i][i];
         }
         for (int r = 0; r < 8; ++r) {
-            double acc = 0.0;
+            R acc = (R)0;
             for (int a = 0; a < 6; ++a) acc += s[a] * Uy[a][r];
-            R[r][2 + m] = acc;
+            Rv[r][2 + m] = acc;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Node values of one two-point flux argument.
-struct NodeM {
-    double rho, beta, lnr, lnb, W, u[3], B[3];
+// Node values of one two-point flux argument: the log-mean arguments in FP64,
+// the rest (with copies r, b of rho, beta) in the working precision R.
+template <typename R>
+struct NodeMT {
+    double rho, beta, lnr, lnb;
+    R r, b, W, u[3], B[3];
 };
+using NodeM = NodeMT<double>;
 
-__device__ __forceinline__ NodeM load_node_m(const double *__restrict__ q, long long P, long long c)
+template <typename R = double>
+__device__ __forceinline__ NodeMT<R> load_node_m(const double *__restrict__ q, long long P, long long c)
 {
-    NodeM v;
+    NodeMT<R> v;
     v.rho = q[Q_RHO * P + c];
     v.beta = q[Q_BETA * P + c];
     v.lnr = q[Q_LNR * P + c];
     v.lnb = q[Q_LNB * P + c];
-    v.W = q[Q_W * P + c];
-    v.u[0] = q[Q_UX * P + c];
-    v.u[1] = q[Q_UY * P + c];
-    v.u[2] = q[QM_UZ * P + c];
-    v.B[0] = q[QM_B1 * P + c];
-    v.B[1] = q[QM_B2 * P + c];
-    v.B[2] = q[QM_B3 * P + c];
+    v.r = (R)v.rho;
+    v.b = (R)v.beta;
+    v.W = (R)q[Q_W * P + c];
+    v.u[0] = (R)q[Q_UX * P + c];
+    v.u[1] = (R)q[Q_UY * P + c];
+    v.u[2] = (R)q[QM_UZ * P + c];
+    v.B[0] = (R)q[QM_B1 * P + c];
+    v.B[1] = (R)q[QM_B2 * P + c];
+    v.B[2] = (R)q[QM_B3 * P + c];
     return v;
 }
 
@@ -381,18 +409,19 @@ __device__ __forceinline__ NodeM load_node_m(const double *__restrict__ q, long 
 // magnetic term 1/2 {{W (b^k)^2}}; F~_j: coefficient matching with exact
 // product-rule expansions, including the -{{B_j}}[[Phi]] term.  Here
 // b = (B + (u.B) u)/W, b^0 = u.B, c = W b^0, v = u/W.
-template <int NJ>
-__device__ __forceinline__ void ec_pair_mhd(const NodeM &L, const NodeM &Rn, double gm1inv, double thr, double mt,
-                                            const double m[3], double out[8])
+template <int NJ, typename R>
+__device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> &Rn, R gm1inv, double thr, R mt,
+                                            const R m[3], R out[8])
 {
-    double rln, irln, bln, ibln;
-    logmean<double, double>(L.rho, Rn.rho, L.lnr, Rn.lnr, thr, rln, irln);
-    logmean<double, double>(L.beta, Rn.beta, L.lnb, Rn.lnb, thr, bln, ibln);
-    double bL[3], bR[3], vL[3], vR[3];
+    R rln, irln, bln, ibln;
+    logmean<R, double>(L.rho, Rn.rho, L.lnr, Rn.lnr, thr, rln, irln);
+    logmean<R, double>(L.beta, Rn.beta, L.lnb, Rn.lnb, thr, bln, ibln);
+    const R half = (R)0.5;
+    R bL[3], bR[3], vL[3], vR[3];
     // b^0 = W (v.B) = u.B
-    double b0L = L.u[0] * L.B[0] + L.u[1] * L.B[1] + L.u[2] * L.B[2];
-    double b0R = Rn.u[0] * Rn.B[0] + Rn.u[1] * Rn.B[1] + Rn.u[2] * Rn.B[2];
-    double iWL = 1.0 / L.W, iWR = 1.0 / Rn.W;
+    R b0L = L.u[0] * L.B[0] + L.u[1] * L.B[1] + L.u[2] * L.B[2];
+    R b0R = Rn.u[0] * Rn.B[0] + Rn.u[1] * Rn.B[1] + Rn.u[2] * Rn.B[2];
+    R iWL = (R)1 / L.W, iWR = (R)1 / Rn.W;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         bL[k] = (L.B[k] + b0L * L.u[k]) * iWL;
@@ -400,37 +429,37 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeM &L, const NodeM &Rn, dou
         vL[k] = L.u[k] * iWL;
         vR[k] = Rn.u[k] * iWR;
     }
-    const double rho_m = 0.5 * (L.rho + Rn.rho), beta_m = 0.5 * (L.beta + Rn.beta), W_m = 0.5 * (L.W + Rn.W);
-    double u_m[3], b_m[3], bsq_m[3], Wbsq_m[3];
+    const R rho_m = half * (L.r + Rn.r), beta_m = half * (L.b + Rn.b), W_m = half * (L.W + Rn.W);
+    R u_m[3], b_m[3], bsq_m[3], Wbsq_m[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        u_m[k] = 0.5 * (L.u[k] + Rn.u[k]);
-        b_m[k] = 0.5 * (bL[k] + bR[k]);
-        bsq_m[k] = 0.5 * (bL[k] * bL[k] + bR[k] * bR[k]);
-        Wbsq_m[k] = 0.5 * (L.W * bL[k] * bL[k] + Rn.W * bR[k] * bR[k]);
+        u_m[k] = half * (L.u[k] + Rn.u[k]);
+        b_m[k] = half * (bL[k] + bR[k]);
+        bsq_m[k] = half * (bL[k] * bL[k] + bR[k] * bR[k]);
+        Wbsq_m[k] = half * (L.W * bL[k] * bL[k] + Rn.W * bR[k] * bR[k]);
     }
-    const double c_m = 0.5 * (L.W * b0L + Rn.W * b0R);
-    const double Wb0sq_m = 0.5 * (L.W * b0L * b0L + Rn.W * b0R * b0R);
-    const double b0_m = 0.5 * (b0L + b0R);
-    const double usq = u_m[0] * u_m[0] + u_m[1] * u_m[1] + u_m[2] * u_m[2];
-    const double Lam = W_m * W_m - usq;
-    const double alpha0 = 1.0 + gm1inv * ibln;
-    const double iW_m = 1.0 / W_m, ibeta_m = 1.0 / beta_m;
-    const double bsq_sum = bsq_m[0] + bsq_m[1] + bsq_m[2];
+    const R c_m = half * (L.W * b0L + Rn.W * b0R);
+    const R Wb0sq_m = half * (L.W * b0L * b0L + Rn.W * b0R * b0R);
+    const R b0_m = half * (b0L + b0R);
+    const R usq = u_m[0] * u_m[0] + u_m[1] * u_m[1] + u_m[2] * u_m[2];
+    const R Lam = W_m * W_m - usq;
+    const R alpha0 = (R)1 + gm1inv * ibln;
+    const R iW_m = (R)1 / W_m, ibeta_m = (R)1 / beta_m;
+    const R bsq_sum = bsq_m[0] + bsq_m[1] + bsq_m[2];
     // U~
-    double Ut[8];
+    R Ut[8];
     {
-        const double alpha1 = rho_m + 0.5 * beta_m * bsq_sum + 0.5 * beta_m * Wb0sq_m * iW_m;
-        const double U1 = rln * W_m;
-        double UB[3], Rk[3];
+        const R alpha1 = rho_m + half * beta_m * bsq_sum + half * beta_m * Wb0sq_m * iW_m;
+        const R U1 = rln * W_m;
+        R UB[3], Rk[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) UB[k] = (W_m * W_m * b_m[k] - c_m * u_m[k]) * iW_m;
-        double R1 = -alpha0 * U1 - 0.5 * Wb0sq_m;
+        R R1 = -alpha0 * U1 - half * Wb0sq_m;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) R1 += 0.5 * Wbsq_m[k] - b_m[k] * UB[k];
+        for (int k = 0; k < 3; ++k) R1 += half * Wbsq_m[k] - b_m[k] * UB[k];
 #pragma unroll
         for (int k = 0; k < 3; ++k) Rk[k] = (alpha1 * u_m[k] - beta_m * c_m * b_m[k]) * iW_m;
-        const double U5 = (u_m[0] * Rk[0] + u_m[1] * Rk[1] + u_m[2] * Rk[2] - beta_m * R1) * W_m / (beta_m * Lam);
+        const R U5 = (u_m[0] * Rk[0] + u_m[1] * Rk[1] + u_m[2] * Rk[2] - beta_m * R1) * W_m / (beta_m * Lam);
         Ut[0] = U1;
 #pragma unroll
         for (int k = 0; k < 3; ++k) Ut[1 + k] = u_m[k] * U5 * iW_m + Rk[k] * ibeta_m;
@@ -443,24 +472,24 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeM &L, const NodeM &Rn, dou
     // F~_j, j = 1..NJ
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-        const double mj = m[j];
-        double ujbsq = 0.0;
+        const R mj = m[j];
+        R ujbsq = (R)0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) ujbsq += 0.5 * (L.u[j] * bL[k] * bL[k] + Rn.u[j] * bR[k] * bR[k]);
-        const double ujb0sq = 0.5 * (L.u[j] * b0L * b0L + Rn.u[j] * b0R * b0R);
-        const double vj_m = 0.5 * (vL[j] + vR[j]);
-        const double Bj_m = 0.5 * (L.B[j] + Rn.B[j]);
-        double r_beta = 0.0, r_u[3] = {0.0, 0.0, 0.0}, r_b[3];
-        double cW = 0.0, cc = 0.0;
+        for (int k = 0; k < 3; ++k) ujbsq += half * (L.u[j] * bL[k] * bL[k] + Rn.u[j] * bR[k] * bR[k]);
+        const R ujb0sq = half * (L.u[j] * b0L * b0L + Rn.u[j] * b0R * b0R);
+        const R vj_m = half * (vL[j] + vR[j]);
+        const R Bj_m = half * (L.B[j] + Rn.B[j]);
+        R r_beta = (R)0, r_u[3] = {(R)0, (R)0, (R)0}, r_b[3];
+        R cW = (R)0, cc = (R)0;
         r_u[j] += rho_m;
-        r_beta += 0.5 * ujbsq;
-        r_u[j] += 0.5 * beta_m * bsq_sum;
+        r_beta += half * ujbsq;
+        r_u[j] += half * beta_m * bsq_sum;
 #pragma unroll
         for (int k = 0; k < 3; ++k) r_b[k] = beta_m * u_m[j] * b_m[k];
-        r_beta -= 0.5 * ujb0sq;
+        r_beta -= half * ujb0sq;
         cc -= beta_m * vj_m * c_m * iW_m;
         cW += beta_m * vj_m * Wb0sq_m * iW_m;        // both [[W]] terms of -(1/2)[[beta u_j (b^0)^2]]
-        r_u[j] -= 0.5 * beta_m * Wb0sq_m * iW_m;
+        r_u[j] -= half * beta_m * Wb0sq_m * iW_m;
         r_beta -= Bj_m * b0_m;
         cc -= Bj_m * beta_m * iW_m;
         cW += Bj_m * beta_m * b0_m * iW_m;
@@ -469,11 +498,11 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeM &L, const NodeM &Rn, dou
             r_u[k] += cW * u_m[k] * iW_m + cc * b_m[k];
             r_b[k] += cc * u_m[k];
         }
-        double F[8];
+        R F[8];
         F[0] = rln * u_m[j];
 #pragma unroll
         for (int k = 0; k < 3; ++k) F[5 + k] = r_b[k] * ibeta_m;
-        double acc = alpha0 * F[0] - r_beta;
+        R acc = alpha0 * F[0] - r_beta;
 #pragma unroll
         for (int k = 0; k < 3; ++k) acc += u_m[k] * r_u[k] * ibeta_m + b_m[k] * F[5 + k];
         F[4] = W_m * acc / Lam;
@@ -547,15 +576,16 @@ __global__ void k_node_mhd(ProbArg pa, double gam, const double *__restrict__ co
 
 // entropy variables of a node from its stored values: V = (Gamma/(Gamma-1) +
 // ln rho + ln beta/(Gamma-1) + beta, beta u, -beta W, beta b)
-__device__ __forceinline__ void node_V_mhd(const double *__restrict__ q, long long P, long long c, double c1g,
-                                           double ig, double V[8])
+template <typename R>
+__device__ __forceinline__ void node_V_mhd(const double *__restrict__ q, long long P, long long c, R c1g, R ig,
+                                           R V[8])
 {
-    double beta = q[Q_BETA * P + c], W = q[Q_W * P + c];
-    double u0 = q[Q_UX * P + c], u1 = q[Q_UY * P + c], u2 = q[QM_UZ * P + c];
-    double B0 = q[QM_B1 * P + c], B1 = q[QM_B2 * P + c], B2 = q[QM_B3 * P + c];
-    double b0 = u0 * B0 + u1 * B1 + u2 * B2;
-    double bW = beta / W;
-    V[0] = c1g + q[Q_LNR * P + c] + ig * q[Q_LNB * P + c] + beta;
+    R beta = (R)q[Q_BETA * P + c], W = (R)q[Q_W * P + c];
+    R u0 = (R)q[Q_UX * P + c], u1 = (R)q[Q_UY * P + c], u2 = (R)q[QM_UZ * P + c];
+    R B0 = (R)q[QM_B1 * P + c], B1 = (R)q[QM_B2 * P + c], B2 = (R)q[QM_B3 * P + c];
+    R b0 = u0 * B0 + u1 * B1 + u2 * B2;
+    R bW = beta / W;
+    V[0] = c1g + (R)q[Q_LNR * P + c] + ig * (R)q[Q_LNB * P + c] + beta;
     V[1] = beta * u0;
     V[2] = beta * u1;
     V[3] = beta * u2;
@@ -571,9 +601,9 @@ __device__ __forceinline__ void node_V_mhd(const double *__restrict__ q, long lo
 // (eqs. BFlux_O2p / BFlux_O2) and the WENO dissipation on scaled entropy
 // variables at the interface state rho = {{rho}}^ln, u = {{u}},
 // p = {{rho}}/{{beta}}, B = {{B}}.
-template <int P, int WW>
+template <typename R, int P, int WW>
 __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const double *__restrict__ q,
-                                                   double *__restrict__ iflux, int dir)
+                                                   R *__restrict__ iflux, int dir)
 {
     ProbDesc D;
     long long lb;
@@ -592,55 +622,59 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
     const double *Mx = q + (Q_M00 + 2 * dir) * g.P;
     const double *My = q + (Q_M01 + 2 * dir) * g.P;
     const double *B1 = q + QM_B1 * g.P, *B2 = q + QM_B2 * g.P;
-    const double gm1inv = 1.0 / (ph.gamma - 1.0);
+    const R gm1inv = (R)(1.0 / (ph.gamma - 1.0));
 
-    double F[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ft = 0.0, Bt = 0.0;
+    R F[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+    double Ft = 0.0, Bt = 0.0;
 #pragma unroll
     for (int n = 1; n <= P; ++n) {
-        double Fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Fts = 0.0, Bts = 0.0;
+        R Fs[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+        double Fts = 0.0, Bts = 0.0;
 #pragma unroll
         for (int s = 0; s < n; ++s) {
             const long long cl = c0 - s * sd, cr = cl + n * sd;
-            NodeM l = load_node_m(q, g.P, cl), r = load_node_m(q, g.P, cr);
-            double out[8];
-            const double mm[3] = {0.5 * (Mx[cl] + Mx[cr]), 0.5 * (My[cl] + My[cr]), 0.0};
-            ec_pair_mhd<2>(l, r, gm1inv, ph.ln_thr, 0.5 * (Mt[cl] + Mt[cr]), mm, out);
+            NodeMT<R> l = load_node_m<R>(q, g.P, cl), r = load_node_m<R>(q, g.P, cr);
+            R out[8];
+            const R mm[3] = {(R)(0.5 * (Mx[cl] + Mx[cr])), (R)(0.5 * (My[cl] + My[cr])), (R)0};
+            ec_pair_mhd<2, R>(l, r, gm1inv, ph.ln_thr, (R)(0.5 * (Mt[cl] + Mt[cr])), mm, out);
 #pragma unroll
             for (int a = 0; a < 8; ++a) Fs[a] += out[a];
             Fts += 0.5 * (Mt[cl] + Mt[cr]);
             Bts += 0.25 * (Mx[cl] + Mx[cr]) * (B1[cl] + B1[cr]) + 0.25 * (My[cl] + My[cr]) * (B2[cl] + B2[cr]);
         }
-        const double an = ph.alpha[n - 1];
+        const R an = (R)ph.alpha[n - 1];
 #pragma unroll
         for (int a = 0; a < 8; ++a) F[a] += an * Fs[a];
-        Ft += an * Fts;
-        Bt += an * Bts;
+        Ft += ph.alpha[n - 1] * Fts;
+        Bt += ph.alpha[n - 1] * Bts;
     }
 
     if (WW > 0) {
         constexpr int NS = WW + 1, OFF = (WW - 1) / 2;
+        const R half = (R)0.5;
         const long long c1 = c0 + sd;
-        const double nvx = 0.5 * (Mx[c0] + Mx[c1]), nvy = 0.5 * (My[c0] + My[c1]);
-        const double jt = 0.5 * (Mt[c0] + Mt[c1]);
-        const double Lk = sqrt(nvx * nvx + nvy * nvy);
-        const double nx = nvx / Lk, ny = nvy / Lk;
+        const R nvx = (R)(0.5 * (Mx[c0] + Mx[c1])), nvy = (R)(0.5 * (My[c0] + My[c1]));
+        const R jt = (R)(0.5 * (Mt[c0] + Mt[c1]));
+        const R Lk = sq_rt<R>(nvx * nvx + nvy * nvy);
+        const R nx = nvx / Lk, ny = nvy / Lk;
         // interface state
-        double wm[8], wrot[8];
+        R wm[8], wrot[8];
         {
-            double rho, irho;
-            logmean<double, double>(q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1], q[Q_LNR * g.P + c0],
-                                    q[Q_LNR * g.P + c1], ph.ln_thr, rho, irho);
-            double um[3] = {0.5 * (q[Q_UX * g.P + c0] + q[Q_UX * g.P + c1]),
-                            0.5 * (q[Q_UY * g.P + c0] + q[Q_UY * g.P + c1]),
-                            0.5 * (q[QM_UZ * g.P + c0] + q[QM_UZ * g.P + c1])};
-            double W2 = 1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
-            double W = sqrt(W2);
+            R rho, irho;
+            logmean<R, double>(q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1], q[Q_LNR * g.P + c0],
+                               q[Q_LNR * g.P + c1], ph.ln_thr, rho, irho);
+            R um[3] = {half * ((R)q[Q_UX * g.P + c0] + (R)q[Q_UX * g.P + c1]),
+                       half * ((R)q[Q_UY * g.P + c0] + (R)q[Q_UY * g.P + c1]),
+                       half * ((R)q[QM_UZ * g.P + c0] + (R)q[QM_UZ * g.P + c1])};
+            R W2 = (R)1 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+            R W = sq_rt<R>(W2);
             wm[0] = rho;
             for (int k = 0; k < 3; ++k) wm[1 + k] = um[k] / W;
-            wm[4] = (q[Q_RHO * g.P + c0] + q[Q_RHO * g.P + c1]) / (q[Q_BETA * g.P + c0] + q[Q_BETA * g.P + c1]);
-            wm[5] = 0.5 * (B1[c0] + B1[c1]);
-            wm[6] = 0.5 * (B2[c0] + B2[c1]);
-            wm[7] = 0.5 * (q[QM_B3 * g.P + c0] + q[QM_B3 * g.P + c1]);
+            wm[4] = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) /
+                    ((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
+            wm[5] = half * ((R)B1[c0] + (R)B1[c1]);
+            wm[6] = half * ((R)B2[c0] + (R)B2[c1]);
+            wm[7] = half * ((R)q[QM_B3 * g.P + c0] + (R)q[QM_B3 * g.P + c1]);
             wrot[0] = wm[0];
             wrot[1] = nx * wm[1] + ny * wm[2];
             wrot[2] = -ny * wm[1] + nx * wm[2];
@@ -650,18 +684,18 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
             wrot[6] = -ny * wm[5] + nx * wm[6];
             wrot[7] = wm[7];
         }
-        double lam[8], R[8][8];
-        eigen_mhd(ph.gamma, wrot, lam, R, true);
-        double lhat = 0.0;
+        R lam[8], Rm[8][8];
+        eigen_mhd<R>(ph.gamma, wrot, lam, Rm, true);
+        R lhat = (R)0;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) lhat = fmax(lhat, fabs(jt + Lk * lam[m]));
-        const double ig = gm1inv, c1g = ph.gamma * gm1inv;
-        double Vt[NS][8], scale[8];
+        for (int m = 0; m < 8; ++m) lhat = vmax(lhat, fab<R>(jt + Lk * lam[m]));
+        const R ig = gm1inv, c1g = (R)ph.gamma * gm1inv;
+        R Vt[NS][8], scale[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) scale[m] = 0.0;
+        for (int m = 0; m < 8; ++m) scale[m] = (R)0;
         for (int k = 0; k < NS; ++k) {
-            double V[8], TV[8];
-            node_V_mhd(q, g.P, c0 + (k - OFF) * sd, c1g, ig, V);
+            R V[8], TV[8];
+            node_V_mhd<R>(q, g.P, c0 + (k - OFF) * sd, c1g, ig, V);
             TV[0] = V[0];
             TV[1] = nx * V[1] + ny * V[2];
             TV[2] = -ny * V[1] + nx * V[2];
@@ -671,38 +705,38 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
             TV[6] = -ny * V[5] + nx * V[6];
             TV[7] = V[7];
             for (int m = 0; m < 8; ++m) {
-                double acc = 0.0;
+                R acc = (R)0;
                 for (int a = 0; a < 8; ++a) {
-                    double t = R[a][m] * TV[a];
+                    R t = Rm[a][m] * TV[a];
                     acc += t;
-                    if (k == OFF || k == OFF + 1) scale[m] += fabs(t);
+                    if (k == OFF || k == OFF + 1) scale[m] += fab<R>(t);
                 }
                 Vt[k][m] = acc;
             }
         }
-        double z[8];
-        const double eps = ph.eps;
+        R z[8];
+        const R eps = (R)ph.eps, sign_tol = (R)ph.sign_tol;
         for (int m = 0; m < 8; ++m) {
-            double vminus, vplus;
+            R vminus, vplus;
             if (WW == 5) {
-                vminus = weno5<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
-                vplus = weno5<double>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
+                vminus = weno5<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
+                vplus = weno5<R>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
             } else {
-                vminus = weno3<double>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
-                vplus = weno3<double>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
+                vminus = weno3<R>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
+                vplus = weno3<R>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
             }
-            double jw = vplus - vminus;
-            double jump = Vt[OFF + 1][m] - Vt[OFF][m];
-            int sj = fabs(jump) <= ph.sign_tol * scale[m] ? 0 : sgn_d(jump);
-            z[m] = (sgn_d(jw) == sj) ? jw : 0.0;
+            R jw = vplus - vminus;
+            R jump = Vt[OFF + 1][m] - Vt[OFF][m];
+            int sj = le(fab<R>(jump), sign_tol * scale[m]) ? 0 : sgn_d(jump);
+            z[m] = (sgn_d(jw) == sj) ? jw : (R)0;
         }
-        double d[8];
+        R d[8];
         for (int a = 0; a < 8; ++a) {
-            double acc = 0.0;
-            for (int m = 0; m < 8; ++m) acc += R[a][m] * z[m];
+            R acc = (R)0;
+            for (int m = 0; m < 8; ++m) acc += Rm[a][m] * z[m];
             d[a] = acc;
         }
-        const double hl = 0.5 * lhat;
+        const R hl = half * lhat;
         F[0] -= hl * d[0];
         F[1] -= hl * (nx * d[1] - ny * d[2]);
         F[2] -= hl * (ny * d[1] + nx * d[2]);
@@ -712,11 +746,11 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
         F[6] -= hl * (ny * d[5] + nx * d[6]);
         F[7] -= hl * d[7];
     }
-    double *out = iflux + (long long)(dir * NFM) * g.P + c0;
+    R *out = iflux + (long long)(dir * NFM) * g.P + c0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) out[a * g.P] = F[a];
-    out[8 * g.P] = Ft;
-    out[9 * g.P] = Bt;
+    out[8 * g.P] = (R)Ft;
+    out[9 * g.P] = (R)Bt;
 }
 
 // initial J and cons = J U(prim)
@@ -755,6 +789,95 @@ __global__ void k_init_state_mhd(ProbArg pa, double gam, const double *__restric
     J[id] = J0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) cons[a * g.N + id] = J0 * U[a];
+}
+
+// d/dt = -sum_k (F_k(i+1/2) - F_k(i-1/2)) - Phi'(V_i) sum_k (B~_k(i+1/2) -
+// B~_k(i-1/2)) (eq. RMHDSemiU_O2p_ES), dJ/dt from the metric flux; written
+// out (dcons != NULL) or combined into the SSP-RK3 stage as in k_update.
+template <typename R>
+__global__ void k_update_mhd(ProbArg pa, const double *__restrict__ q, const R *__restrict__ fl,
+                             double *__restrict__ dcons, double *__restrict__ dJ, const double *__restrict__ cn,
+                             const double *__restrict__ Jn_, const double *__restrict__ xn,
+                             const double *__restrict__ cs, const double *__restrict__ Js,
+                             const double *__restrict__ xs, const double *__restrict__ xdot, double A, double B,
+                             const double *__restrict__ dt_dev, double *__restrict__ co, double *__restrict__ Jo,
+                             double *__restrict__ xo)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    long long c = pidx(g, i, j);
+    const R *f0 = fl, *f1 = fl + NFM * g.P;
+    double L[10];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+        double d0 = (double)f0[a * g.P + c] - (double)f0[a * g.P + c - 1];
+        double d1 = (double)f1[a * g.P + c] - (double)f1[a * g.P + c - g.px];
+        L[a] = -(d0 + d1);
+    }
+    // Powell source: L[9] = -div B~ here
+    double iW = 1.0 / q[Q_W * g.P + c];
+    double w[8];
+    w[1] = q[Q_UX * g.P + c] * iW;
+    w[2] = q[Q_UY * g.P + c] * iW;
+    w[3] = q[QM_UZ * g.P + c] * iW;
+    w[5] = q[QM_B1 * g.P + c];
+    w[6] = q[QM_B2 * g.P + c];
+    w[7] = q[QM_B3 * g.P + c];
+    double Pp[8];
+    mhd_phiprime(w, Pp);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) L[a] += Pp[a] * L[9];
+    if (dcons) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) dcons[a * g.N + id] = L[a];
+        dJ[id] = L[8];
+        return;
+    }
+    double dt = dt_dev[b];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) co[a * g.N + id] = A * cn[a * g.N + id] + B * (cs[a * g.N + id] + dt * L[a]);
+    Jo[id] = A * Jn_[id] + B * (Js[id] + dt * L[8]);
+    xo[id] = A * xn[id] + B * (xs[id] + dt * xdot[id]);
+    xo[g.N + id] = A * xn[g.N + id] + B * (xs[g.N + id] + dt * xdot[g.N + id]);
+}
+
+
+template <typename R, int P>
+static void launch_iface_mhd_p(const LaunchDom &L, const Phys &ph, const double *q, R *iflux, int dir, cudaStream_t st)
+{
+    switch (ph.w) {
+    case 0: k_iface_mhd<R, P, 0><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
+    case 3: k_iface_mhd<R, P, 3><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
+    default: k_iface_mhd<R, P, 5><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, iflux, dir); break;
+    }
+}
+
+// interface fluxes of one sweep direction in the working precision R
+template <typename R>
+static void launch_iface_mhd_t(const LaunchDom &L, const Phys &ph, const double *q, void *iflux, int dir,
+                               cudaStream_t st)
+{
+    R *fl = (R *)iflux;
+    switch (ph.p) {
+    case 1: launch_iface_mhd_p<R, 1>(L, ph, q, fl, dir, st); break;
+    case 2: launch_iface_mhd_p<R, 2>(L, ph, q, fl, dir, st); break;
+    default: launch_iface_mhd_p<R, 3>(L, ph, q, fl, dir, st); break;
+    }
+}
+
+template <typename R>
+static void launch_update_mhd_t(const LaunchDom &L, const double *q, const void *fl, double *dcons, double *dJ,
+                                const double *cn, const double *Jn, const double *xn, const double *cs,
+                                const double *Js, const double *xs, const double *xdot, double A, double B,
+                                const double *dt_dev, double *co, double *Jo, double *xo, cudaStream_t st)
+{
+    k_update_mhd<R><<<L.nblk, L.bs, 0, st>>>(L.pa, q, (const R *)fl, dcons, dJ, cn, Jn, xn, cs, Js, xs, xdot, A, B,
+                                             dt_dev, co, Jo, xo);
 }
 
 }  // namespace esmm

@@ -165,6 +165,9 @@ def test_rotor_512_full_size_rhs():
 
 
 def test_rmhd_rejects_unsupported_forms():
-    with esmm.Grid((16, 16), phys=esmm.RMHD) as g:
+    # the adjoint is built for RHD grids only
+    x = wl.uniform_mesh(16, 16, (-0.5, -0.5), (0.5, 0.5), (False, False))
+    with esmm.Grid((16, 16), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), phys=esmm.RMHD) as g:
+        g.state_set(wl.rotor(x), x)
         with pytest.raises(esmm.EsmmError):
-            g.set_params(precision=esmm.MIXED)
+            g.adjoint_record(1)
