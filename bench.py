@@ -57,12 +57,19 @@ FP32_FLOP_PER_CLK_SM = 256
 # DRAM bytes (read + write) of one interface-kernel launch in that capture;
 # None whenever the kernel has changed since the counters were taken.
 TRAFFIC_IFACE_F64 = 23.48e6
-# The same for the RMHD interface kernels (k_iface_mhd<2,5>, k3_iface<2,5>),
-# from their captures (profiles/iface_mhd_*.md); None until measured.
-FLOPS_PER_IFACE_MHD2 = None
-TRAFFIC_IFACE_MHD2 = None
-FLOPS_PER_IFACE_MHD3 = None
-TRAFFIC_IFACE_MHD3 = None
+# The same for the RMHD interface kernels at p = 2, WENO5 (profiles/
+# iface_mhd_ops_rotor512_blast64.md): the FP64 2D kernel on the 512^2 rotor
+# (16,354 FP64 flops per interface; 1.021 GB of DRAM traffic per launch, the
+# eigen-system's per-thread stack), its FP32 instance (12,325 FP32 flops per
+# interface besides 492 FP64 ones; 0.443 GB), and the 3D kernel (20,351 FP64
+# flops per interface; 1.112 GB at 64^3, scaled by the 7.94x interfaces of
+# a 128^3 launch -- the stack traffic grows with the threads).
+FLOPS_PER_IFACE_MHD2 = 16354
+TRAFFIC_IFACE_MHD2 = 1.021e9
+FLOPS_PER_IFACE_MHD2_F32 = 12325
+TRAFFIC_IFACE_MHD2_F32 = 0.443e9
+FLOPS_PER_IFACE_MHD3 = 20351
+TRAFFIC_IFACE_MHD3 = 8.83e9
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
@@ -457,7 +464,7 @@ def run_rmhd(args):
                 "4th-order EC flux (p=2) + WENO5 + Powell source, SSP-RK3, CFL 0.4" % (n, n))
         flops, traffic, kname = FLOPS_PER_IFACE_MHD2, TRAFFIC_IFACE_MHD2, "k_iface_mhd<double,2,5>"
         if args.form == "mixed":
-            flops, traffic, kname = None, None, "k_iface_mhd<float,2,5>"
+            flops, traffic, kname = FLOPS_PER_IFACE_MHD2_F32, TRAFFIC_IFACE_MHD2_F32, "k_iface_mhd<float,2,5>"
     g.state_set(prim, x)
     dev = torch.device("cuda", local)
     c0 = torch.empty(((8,) + tuple(prim.shape[1:])), dtype=torch.float64, device=dev)
@@ -470,8 +477,7 @@ def run_rmhd(args):
     for _ in range(W):
         g.state_set_cons(c0, J0, x0)
         g.rk_step()
-    if not three:
-        g.profile(1 << esmm.KIND_IFACE)
+    g.profile(1 << esmm.KIND_IFACE)
     flush = None if three else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     clock = ClockSampler(local)
     clock.start()
@@ -491,21 +497,19 @@ def run_rmhd(args):
     nfail, msg = g.last_error()
     if nfail:
         raise RuntimeError("primitive recovery failed at %d nodes: %s" % (nfail, msg))
-    roof, launches = None, None
-    if not three:
-        prof = g.profile_read()
-        launches = int(sum(v[1] for v in prof.values()))
-        iface_ms, _, iface_timed = prof["iface"]
-        avg = iface_ms * 1e-3 / max(iface_timed, 1)
-        mixed = args.form == "mixed"
-        per_clk = FP32_FLOP_PER_CLK_SM if mixed else FP64_FLOP_PER_CLK_SM
-        peak = N_SM * per_clk * SM_MAX_MHZ * 1e6 / 1e12
-        ach = flops * ifaces / avg / 1e12 if flops else None
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": kname,
-                "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms,
-                "peak_note": "derived %s peak: 152 SMs x %d flop/clk x 2070 MHz" % ("FP32" if mixed else "FP64",
-                                                                                  per_clk)}
+    prof = g.profile_read()
+    launches = int(sum(v[1] for v in prof.values()))
+    iface_ms, _, iface_timed = prof["iface"]
+    avg = iface_ms * 1e-3 / max(iface_timed, 1)
+    mixed = args.form == "mixed"
+    per_clk = FP32_FLOP_PER_CLK_SM if mixed else FP64_FLOP_PER_CLK_SM
+    peak = N_SM * per_clk * SM_MAX_MHZ * 1e6 / 1e12
+    ach = flops * ifaces / avg / 1e12 if flops else None
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": kname,
+            "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms,
+            "peak_note": "derived %s peak: 152 SMs x %d flop/clk x 2070 MHz" % ("FP32" if mixed else "FP64",
+                                                                              per_clk)}
     g.close()
     line = {"metric": METRIC, "value": nodes * 3 * K / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -516,8 +520,7 @@ def run_rmhd(args):
                               else "flushed (256 MB write) before every timed step"),
                        "parallelism": "single GPU"},
             "roofline": roof, "clocks": clk}
-    if launches is not None:
-        line["gpu_launches"] = launches
+    line["gpu_launches"] = launches
     if not three and args.form == "fp64" and not args.no_extras:
         with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
                        stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,

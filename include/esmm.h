@@ -90,8 +90,9 @@ typedef struct {
  * ESMM_RMHD), or of n[0] x n[1] x n[2] nodes (dim 3, phys ESMM_RMHD: the
  * nested metrics of eq. SCLCoeff, FP64; defaults Gamma = 4/3, CFL 0.3,
  * alpha = 800), bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4.  3D grids
- * accept the single-problem calls; batches, the tuner, the adjoint and
- * profiling return ESMM_ERR_ARG for them.  A periodic
+ * accept the single-problem calls and profiling; batches, the tuner, the
+ * adjoint and ESMM_MIXED return ESMM_ERR_ARG for them (RMHD 2D grids take
+ * ESMM_MIXED; batches are RHD).  A periodic
  * direction has n[k] distinct nodes with spacing (hi-lo)/n[k]; an outflow
  * direction has nodes on both ends.  stream is a cudaStream_t (NULL: the
  * legacy default stream) on the current device; the grid stays on that device.

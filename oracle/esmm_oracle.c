@@ -111,7 +111,9 @@ void oref_flux(double gamma, const double *w, int dir, double *F)
  * safeguarded by bisection on the bracket [0, (Gamma-1) E] (f(0) > 0 and
  * f((Gamma-1)E) < 0 for every admissible state, f strictly decreasing).
  * Stops when a step changes p by at most 1e-15 (E + p): f is evaluated from
- * E + p, so p is resolved only to that level (p << E in cold gas).
+ * E + p, so p is resolved only to that level (p << E in cold gas); an
+ * iterate at which f is exactly 0 is a root and is kept (the open bracket
+ * would reject its zero step and bisect away from it).
  * Returns 0 on success, -1 for a non-admissible state, -2 without
  * convergence.                                                             */
 int oref_cons2prim(double gamma, const double *U, double *w, int *iters)
@@ -130,9 +132,12 @@ int oref_cons2prim(double gamma, const double *U, double *w, int *iters)
         double v2 = S * S / (Ep * Ep);
         double f = gg * (Ep * iW2 - D * iW) - p;
         double df = gg * (1.0 + v2 - D * v2 / (iW * Ep)) - 1.0;
-        if (f > 0.0) lo = p; else hi = p;
-        double pn = p - f / df;
-        if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
+        double pn = p;                      /* f = 0: p is a root */
+        if (f != 0.0) {
+            if (f > 0.0) lo = p; else hi = p;
+            pn = p - f / df;
+            if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
+        }
         if (fabs(pn - p) <= 1.0e-15 * (E + pn)) {
             p = pn;
             ok = 1;

@@ -771,6 +771,10 @@ struct esmm3 {
     double *pin;
     char msg[256];
     long long launches;
+    // profiling: launches per kind, CUDA events around the kinds in prof_mask
+    long long nl[ESMM_NKINDS];
+    int prof_mask;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *ev;   // [ESMM_NKINDS]
 };
 
 namespace {
@@ -783,6 +787,37 @@ int fail3(esmm3 *g, int code, const char *what, cudaError_t e = cudaSuccess)
     if (e != cudaSuccess) snprintf(g->msg, sizeof g->msg, "%s: %s", what, cudaGetErrorString(e));
     else snprintf(g->msg, sizeof g->msg, "%s", what);
     return code;
+}
+
+// counts n launches of one kind; times them (one event pair) when the kind is
+// in the profile mask
+struct Prof3 {
+    esmm3 *g;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Prof3(esmm3 *g_, int kind_, int n = 1) : g(g_), kind(kind_)
+    {
+        g->launches += n;
+        g->nl[kind] += n;
+        if (g->ev && (g->prof_mask & (1 << kind)) && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, g->st);
+    }
+    ~Prof3()
+    {
+        cudaEvent_t b;
+        if (a && cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, g->st);
+            g->ev[kind].push_back({a, b});
+        }
+    }
+};
+
+void prof_clear3(esmm3 *g)
+{
+    if (!g->ev) return;
+    for (int k = 0; k < ESMM_NKINDS; ++k) {
+        for (auto &pr : g->ev[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+        g->ev[k].clear();
+    }
 }
 
 #define CK3(call)                                                          \
@@ -809,7 +844,7 @@ void node3(esmm3 *g, const double *cons, const double *J, const double *x, const
            double *zo)
 {
     unsigned nb = nb3(g->g.P);
-    g->launches++;
+    Prof3 pr_(g, ESMM_KIND_NODE);
     if (g->p == 1) k3_node<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
     else if (g->p == 2) k3_node<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
     else k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
@@ -832,7 +867,7 @@ void fluxes3(esmm3 *g)
         int oa = dir == 0 ? 1 : 0, ob = dir == 2 ? 1 : 2;
         long long count = (long long)(g->g.n[dir] + 1) * g->g.n[oa] * g->g.n[ob];
         unsigned nb = nb3(count, 128);
-        g->launches++;
+        Prof3 pr_(g, ESMM_KIND_IFACE);
         if (g->p == 1) iface3_p<1>(g, ph, nb, dir);
         else if (g->p == 2) iface3_p<2>(g, ph, nb, dir);
         else iface3_p<3>(g, ph, nb, dir);
@@ -842,7 +877,7 @@ void fluxes3(esmm3 *g)
 void update3(esmm3 *g, double *dc, double *dJ, const double *cn, const double *Jn, const double *xn, const double *cs,
              const double *Js, const double *xs, double A, double B, double *co, double *Jo, double *xo)
 {
-    g->launches++;
+    Prof3 pr_(g, ESMM_KIND_UPDATE);
     k3_update<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->q, g->iflux, dc, dJ, cn, Jn, xn, cs, Js, xs, g->xdot, A, B,
                                               g->dt_dev, co, Jo, xo);
 }
@@ -850,14 +885,13 @@ void update3(esmm3 *g, double *dc, double *dJ, const double *cn, const double *J
 int mesh_and_dt3(esmm3 *g, double dt)
 {
     unsigned nb = nb3(g->g.N);
-    g->launches++;
-    k3_red_init<<<1, 32, 0, g->st>>>(g->red);
-    if (!(dt > 0.0)) {
-        g->launches++;
-        k3_cfl<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
+    {
+        Prof3 pr_(g, ESMM_KIND_OTHER, dt > 0.0 ? 1 : 2);
+        k3_red_init<<<1, 32, 0, g->st>>>(g->red);
+        if (!(dt > 0.0)) k3_cfl<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
     }
     if (!g->prm.move_mesh) {
-        g->launches++;
+        Prof3 pr_(g, ESMM_KIND_OTHER);
         k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->dt_dev);
         if (!g->xdot_zero) {
             CK3(cudaMemsetAsync(g->xdot, 0, 3 * g->g.N * sizeof(double), g->st));
@@ -866,6 +900,7 @@ int mesh_and_dt3(esmm3 *g, double dt)
         return ESMM_OK;
     }
     g->xdot_zero = 0;
+    Prof3 pr_(g, ESMM_KIND_MESH, 6 + g->prm.n_filter + g->prm.mu);
     k3_mesh_grad<<<nb, BS3, 0, g->st>>>(g->g, g->prm.monitor == ESMM_MONITOR_LNRHO, g->q, g->grad, g->red);
     k3_mesh_omega<<<nb, BS3, 0, g->st>>>(g->g, g->prm.alpha, g->grad, g->red, g->om);
     double *om = g->om, *om2 = g->om2;
@@ -882,7 +917,6 @@ int mesh_and_dt3(esmm3 *g, double dt)
     k3_mesh_tau<<<nb, BS3, 0, g->st>>>(g->g, g->x, src, g->q, g->J, g->red);
     k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->dt_dev);
     k3_mesh_xdot<<<nb3(3 * g->g.N), BS3, 0, g->st>>>(g->g, g->x, src, g->red, g->dt_dev, g->xdot);
-    g->launches += 6 + g->prm.n_filter + g->prm.mu;
     return ESMM_OK;
 }
 
@@ -896,7 +930,7 @@ int stages3(esmm3 *g)
     node3(g, g->c2, g->J2, g->x2, g->xdot, g->zg[2], g->zg[0]);
     fluxes3(g);
     update3(g, nullptr, nullptr, g->cons, g->J, g->x, g->c2, g->J2, g->x2, 1.0 / 3.0, 2.0 / 3.0, g->cons, g->J, g->x);
-    g->launches++;
+    Prof3 pr_(g, ESMM_KIND_OTHER);
     k3_time<<<1, 32, 0, g->st>>>(g->dt_dev, g->t_dev);
     CK3(cudaGetLastError());
     return ESMM_OK;
@@ -1000,6 +1034,8 @@ void esmm3_destroy(esmm3 *g)
 {
     if (!g) return;
     cudaStreamSynchronize(g->st);
+    prof_clear3(g);
+    delete[] g->ev;
     free3(g);
     delete g;
 }
@@ -1044,7 +1080,7 @@ int esmm3_state_set(esmm3 *g, const double *prim, const double *x, int mem)
     }
     if ((rc = copy3(g, g->out_dc, prim, 8 * N, mem, true))) return rc;
     CK3(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), g->st));
-    g->launches++;
+    Prof3 pr_(g, ESMM_KIND_OTHER);
     unsigned nb = nb3(g->g.N);
     if (g->p == 1) k3_init<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
     else if (g->p == 2) k3_init<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->out_dc, g->x, g->cons, g->J, g->status);
@@ -1091,6 +1127,7 @@ int esmm3_state_get(esmm3 *g, int what, double *out, int mem)
     switch (what) {
     case ESMM_GET_PRIM:
         g->launches++;
+        g->nl[ESMM_KIND_OTHER]++;
         k3_prim_out<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->gamma, g->cons, g->J, g->out_dc, g->status);
         CK3(cudaGetLastError());
         rc = copy3(g, out, g->out_dc, 8 * N, mem, false);
@@ -1149,6 +1186,7 @@ int esmm3_cfl_dt(esmm3 *g, double *dt)
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
     node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     g->launches += 3;
+    g->nl[ESMM_KIND_OTHER] += 3;
     k3_red_init<<<1, 32, 0, g->st>>>(g->red);
     k3_cfl<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
     k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, 0.0, g->red, g->dt_dev);
@@ -1178,8 +1216,10 @@ static int rk_step_async3(esmm3 *g, double dt)
     node3(g, g->cons, g->J, g->x, nullptr, g->zg[0], g->zg[1]);
     int rc = mesh_and_dt3(g, dt);
     if (rc) return rc;
-    g->launches++;
-    k3_tmetric<<<nb3(g->g.P), BS3, 0, g->st>>>(g->g, g->xdot, g->q);
+    {
+        Prof3 pr_(g, ESMM_KIND_OTHER);
+        k3_tmetric<<<nb3(g->g.P), BS3, 0, g->st>>>(g->g, g->xdot, g->q);
+    }
     return stages3(g);
 }
 
@@ -1213,6 +1253,7 @@ int esmm3_totals(esmm3 *g, double out[3])
     node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     unsigned nb = nb3(g->g.N);
     g->launches += 2;
+    g->nl[ESMM_KIND_OTHER] += 2;
     k3_totals<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->cons, g->J, g->partials);
     k3_totals_final<<<1, 32, 0, g->st>>>((int)nb, g->partials, g->tot);
     CK3(cudaMemcpyAsync(g->pin, g->tot, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
@@ -1236,3 +1277,33 @@ int esmm3_last_error(esmm3 *g, int *n_c2p_fail, char *msg, int len)
 }
 
 long long esmm3_launches(const esmm3 *g) { return g->launches; }
+
+int esmm3_profile(esmm3 *g, int mask)
+{
+    CK3(cudaStreamSynchronize(g->st));
+    if (!g->ev) g->ev = new (std::nothrow) std::vector<std::pair<cudaEvent_t, cudaEvent_t>>[ESMM_NKINDS];
+    if (!g->ev) return fail3(g, ESMM_ERR_ARG, "out of host memory");
+    prof_clear3(g);
+    for (int k = 0; k < ESMM_NKINDS; ++k) g->nl[k] = 0;
+    g->prof_mask = mask;
+    return ESMM_OK;
+}
+
+int esmm3_profile_read(esmm3 *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
+                       long long timed[ESMM_NKINDS])
+{
+    CK3(cudaStreamSynchronize(g->st));
+    for (int k = 0; k < ESMM_NKINDS; ++k) {
+        double acc = 0.0;
+        if (g->ev)
+            for (auto &pr : g->ev[k]) {
+                float t = 0.0f;
+                CK3(cudaEventElapsedTime(&t, pr.first, pr.second));
+                acc += t;
+            }
+        if (ms) ms[k] = acc;
+        if (launches) launches[k] = g->nl[k];
+        if (timed) timed[k] = g->ev ? (long long)g->ev[k].size() : 0;
+    }
+    return ESMM_OK;
+}

@@ -27,3 +27,6 @@ int esmm3_advance(esmm3 *g, int nsteps, double dt);
 int esmm3_totals(esmm3 *g, double out[3]);
 int esmm3_last_error(esmm3 *g, int *n_c2p_fail, char *msg, int len);
 long long esmm3_launches(const esmm3 *g);
+int esmm3_profile(esmm3 *g, int mask);
+int esmm3_profile_read(esmm3 *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
+                       long long timed[ESMM_NKINDS]);

@@ -328,7 +328,8 @@ void step_radius(esmm_grid *g, double dt)
     if (dt > 0.0) return;
     Prof pr_(g, ESMM_KIND_OTHER);
     LaunchDom L = dom(g, D_NODE);
-    if (g->phys == ESMM_RMHD) launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->st);
+    if (g->phys == ESMM_RMHD)
+        launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->prm.precision == ESMM_MIXED, g->st);
     else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red);
 }
 
@@ -1559,8 +1560,8 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
 
 int esmm_profile(esmm_grid *g, int mask)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || mask < 0 || mask >= (1 << ESMM_NKINDS)) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_profile(g->g3, mask);
     CK(cudaStreamSynchronize(g->st));
     for (int k = 0; k < ESMM_NKINDS; ++k) {
         for (auto &pr : g->ev[k]) { g->pool->push_back(pr.first); g->pool->push_back(pr.second); }
@@ -1574,8 +1575,8 @@ int esmm_profile(esmm_grid *g, int mask)
 int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
                       long long timed[ESMM_NKINDS])
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_profile_read(g->g3, ms, launches, timed);
     CK(cudaStreamSynchronize(g->st));
     for (int k = 0; k < ESMM_NKINDS; ++k) {
         double acc = 0.0;

@@ -25,6 +25,11 @@ __global__ void k_prim_out_mhd(ProbArg pa, double gam, const double *__restrict_
 }
 
 
+// Spectral radius of the 8-wave system per node and direction (eq. cfl),
+// with the speeds from the eigen-system in the working precision R (FP32 in
+// the mixed form: the step carries ~1e-6 relative rounding, harmless for a
+// stability bound).
+template <typename R>
 __global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
                           unsigned long long *red)
 {
@@ -46,12 +51,12 @@ __global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, 
             double mx = q[(Q_M00 + 2 * k) * g.P + c], my = q[(Q_M01 + 2 * k) * g.P + c];
             double Lk = sqrt(mx * mx + my * my);
             double nx = mx / Lk, ny = my / Lk;
-            double wr[8] = {w[0], nx * w[1] + ny * w[2], -ny * w[1] + nx * w[2], w[3],
-                            w[4], nx * w[5] + ny * w[6], -ny * w[5] + nx * w[6], w[7]};
-            double lam[8], R[8][8];
-            eigen_mhd(gam, wr, lam, R, false);
+            R wr[8] = {(R)w[0], (R)(nx * w[1] + ny * w[2]), (R)(-ny * w[1] + nx * w[2]), (R)w[3],
+                       (R)w[4], (R)(nx * w[5] + ny * w[6]), (R)(-ny * w[5] + nx * w[6]), (R)w[7]};
+            R lam[8], Rm[8][8];
+            eigen_mhd<R>(gam, wr, lam, Rm, false);
             double a = 0.0;
-            for (int m = 0; m < 8; ++m) a = fmax(a, fabs(lam[m]));
+            for (int m = 0; m < 8; ++m) a = fmax(a, fabs((double)lam[m]));
             r[k] = Lk * a * iJ;
         }
     }
@@ -87,9 +92,10 @@ void launch_update_mhd(const LaunchDom &L, const double *q, const void *fl, doub
 }
 
 void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,
-                    cudaStream_t st)
+                    bool f32, cudaStream_t st)
 {
-    k_cfl_mhd<<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red);
+    if (f32) k_cfl_mhd<float><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red);
+    else k_cfl_mhd<double><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red);
 }
 
 void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, const double *x, double *cons,

@@ -191,3 +191,18 @@ def test_blast_128_full_size():
             assert dt > 0
         pr = g.state_get(esmm.GET_PRIM)
         assert pr[0].min() > 0 and pr[4].min() > 0
+
+
+def test_profile_counts_3d():
+    # one step: 3 node passes, 9 interface launches (3 stages x 3 directions)
+    # and 3 updates; the interface launches are timed when asked for
+    m = 12
+    x, prim = wl.blast3_config(m)
+    with esmm.Grid3((m, m, m), (-0.5,) * 3, (0.5,) * 3, bc=(1, 1, 1), p=2, w=5) as g:
+        g.state_set(prim, x)
+        g.profile(1 << esmm.KIND_IFACE)
+        g.rk_step()
+        prof = g.profile_read()
+    assert prof["node"][1] == 3 and prof["iface"][1] == 9 and prof["update"][1] == 3
+    assert prof["iface"][2] == 9 and prof["iface"][0] > 0.0
+    assert prof["node"][2] == 0
