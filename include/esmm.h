@@ -92,7 +92,7 @@ typedef struct {
  * alpha = 800), bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4.  3D grids
  * accept the single-problem calls and profiling; batches, the tuner, the
  * adjoint and ESMM_MIXED return ESMM_ERR_ARG for them (RMHD 2D grids take
- * ESMM_MIXED; batches are RHD).  A periodic
+ * ESMM_MIXED and, in FP64, the adjoint; batches are RHD).  A periodic
  * direction has n[k] distinct nodes with spacing (hi-lo)/n[k]; an outflow
  * direction has nodes on both ends.  stream is a cudaStream_t (NULL: the
  * legacy default stream) on the current device; the grid stays on that device.
@@ -184,21 +184,26 @@ int esmm_batch_times(esmm_grid *g, double *t);
 int esmm_batch_totals(esmm_grid *g, double *out);
 
 /* Adjoint: gradients of a final-time functional with respect to the initial
- * data, single RHD problems only (ESMM_ERR_ARG on RMHD grids), FP64.
+ * data, single 2D problems (RHD, or RMHD in the FP64 form; ESMM_ERR_ARG for
+ * batches, 3D grids and mixed-form RMHD grids), FP64.  m = 4 (RHD) or 8
+ * (RMHD) components below.
  * esmm_adjoint_record advances nsteps steps (dt as esmm_rk_step) from the
  * current state, keeping per-step checkpoints (state, mesh velocity, step) on
- * the device (9 N doubles per step).  The adjoint differentiates the recorded
- * map: each step with its recorded mesh velocity and dt held fixed (the
- * monitor's maximum and the limiter's minimum are not differentiable), the
- * sign switch Y and the lambda^ maximum frozen at their forward selection;
- * esmm_adjoint_replay re-runs that map from the current state (for finite-
- * difference checks).  esmm_adjoint_vjp takes lam_final [4][N] = dF/d(cons)
- * at the last recorded step and returns lam_cons0 = dF/d(cons) at the first
- * (may be NULL) and lam_prim0 = dF/d(prim) of the first state (may be NULL),
- * recomputing the RK stages of each step backwards from its checkpoint.
- * esmm_rhs_vjp returns lam = (d rhs/d cons)^T mu at (cons, J, x, xdot) (J, x
- * and xdot held fixed), through the implicit-function adjoint of the Newton
- * recovery, the log means, the scaled eigenvectors and the WENO weights. */
+ * the device ((m + 5) N doubles per step).  The adjoint differentiates the
+ * recorded map: each step with its recorded mesh velocity and dt held fixed
+ * (the monitor's maximum and the limiter's minimum are not differentiable),
+ * the sign switch Y and the lambda^ maximum frozen at their forward
+ * selection; esmm_adjoint_replay re-runs that map from the current state (for
+ * finite-difference checks).  esmm_adjoint_vjp takes lam_final [m][N] =
+ * dF/d(cons) at the last recorded step and returns lam_cons0 = dF/d(cons) at
+ * the first (may be NULL) and lam_prim0 = dF/d(prim) of the first state (may
+ * be NULL), recomputing the RK stages of each step backwards from its
+ * checkpoint.  esmm_rhs_vjp returns lam = (d rhs/d cons)^T mu at (cons, J, x,
+ * xdot) (J, x and xdot held fixed), through the implicit-function adjoint of
+ * the Newton recovery, the log means, the scaled eigenvectors (RMHD: the
+ * first-order perturbation of the 8-wave construction, a cluster of
+ * near-equal speeds through its span), the WENO weights and, for RMHD, the
+ * Godunov-Powell source. */
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt);
 int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt);
 int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int mem);
@@ -270,6 +275,19 @@ int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[E
 int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const double hi[2], double gamma,
                     int p, int w, const double *cons, const double *J, const double *x, const double *xdot,
                     double *dcons, double *dJ, void *stream);
+
+/* The scaled eigen-system of the symmetrized RMHD x_1 system (Sec. 4) that
+ * the ES dissipation uses, for n rotated primitive states w [n][8] (rho,
+ * v_1..3, p, B_1..3): lam [n][8] (the entropy and divergence waves first,
+ * then the other six ascending) and R [n][8][8] (row = component, column =
+ * wave; R R^T = dU/dV; for a cluster of speeds closer than 1e-5 the canonical
+ * basis of its span).  With dw non-NULL also the tangents dlam, dR along the
+ * directions dw [n][8]: the first-order perturbation of that construction (a
+ * cluster through its span) as the adjoint uses it.  Host arrays, computed on
+ * the current device; dlam and dR may be NULL when dw is.  ESMM_ERR_ARG for
+ * n < 1 or missing arrays, ESMM_ERR_CUDA on a CUDA failure. */
+int esmm_mhd_eigen(double gamma, int n, const double *w, const double *dw, double *lam, double *R, double *dlam,
+                   double *dR);
 
 /* Library version string. */
 const char *esmm_version(void);

@@ -366,10 +366,15 @@ void oref_mhd_ec_flux(double gamma, const double *wl, const double *wr,
  *     an eigenspace to rounding, and the WENO reconstruction and the sign
  *     switch Y do depend on that basis.  So the sorted speeds are grouped in
  *     clusters of consecutive gaps below OREF_MHD_CLUSTER_TOL, and each
- *     cluster gets a canonical basis: pivoted Gram-Schmidt of the coordinate
- *     vectors e_1..e_6 of the C-space projected onto the cluster's span
- *     (largest remaining norm first, lowest index on ties).  This depends
- *     only on the span, so it is reproducible.
+ *     cluster gets a canonical basis: Gram-Schmidt, in index order, of the
+ *     coordinate vectors e_1..e_6 of the C-space projected onto the
+ *     cluster's span, taking a projected vector when its remaining squared
+ *     norm is at least 1/8 (for a k-dimensional span the squared norms of
+ *     the six projections sum to k, so k of them are always taken).  This
+ *     depends only on the span, so it is reproducible, and it is continuous
+ *     in the span away from the 1/8 threshold: a choice by largest norm
+ *     would switch on the exact ties that symmetric states (B along n, gas
+ *     at rest) create, and the dissipation with it.
  *  6. Column order: a_rho, a_div, then the six in ascending speed.  (Order and
  *     sign of the columns do not change the dissipation.)
  * lam[8] gets the speeds, R[8*8] row-major (row = component, column = wave).*/
@@ -570,30 +575,25 @@ void oref_mhd_eigen(double gamma, const double *w, double *lam, double *R)
         if (k > 1) {
             /* z_i = coordinates of P e_i in the cluster basis = row i of E6 */
             double z[6][6], basis[6][6];
-            int used[6] = {0, 0, 0, 0, 0, 0};
             for (int i = 0; i < 6; ++i)
                 for (int c = 0; c < k; ++c) z[i][c] = E6[i][start + c];
-            for (int t = 0; t < k; ++t) {
-                int best = -1;
-                double bn = -1.0;
-                for (int i = 0; i < 6; ++i) {
-                    if (used[i]) continue;
-                    double n2 = 0.0;
-                    for (int c = 0; c < k; ++c) n2 += z[i][c] * z[i][c];
-                    if (best < 0 || n2 > bn) {   /* the first unused if all are NaN */
-                        bn = n2;
-                        best = i;
-                    }
-                }
-                used[best] = 1;
-                double nrm = sqrt(bn);
-                for (int c = 0; c < k; ++c) basis[t][c] = z[best][c] / nrm;
-                for (int i = 0; i < 6; ++i) {
-                    if (used[i]) continue;
+            int nt = 0;
+            for (int i = 0; i < 6 && nt < k; ++i) {
+                double n2 = 0.0;
+                for (int c = 0; c < k; ++c) n2 += z[i][c] * z[i][c];
+                if (!(n2 >= 0.125)) continue;
+                double nrm = sqrt(n2);
+                for (int c = 0; c < k; ++c) basis[nt][c] = z[i][c] / nrm;
+                for (int ii = i + 1; ii < 6; ++ii) {
                     double pr = 0.0;
-                    for (int c = 0; c < k; ++c) pr += z[i][c] * basis[t][c];
-                    for (int c = 0; c < k; ++c) z[i][c] -= pr * basis[t][c];
+                    for (int c = 0; c < k; ++c) pr += z[ii][c] * basis[nt][c];
+                    for (int c = 0; c < k; ++c) z[ii][c] -= pr * basis[nt][c];
                 }
+                ++nt;
+            }
+            if (nt < k) {   /* only for non-finite input: keep the Jacobi basis */
+                start = end;
+                continue;
             }
             double newE[6][6];
             for (int t = 0; t < k; ++t)

@@ -1,7 +1,8 @@
 """torch.autograd wrapper of the adjoint (gradients with respect to initial data).
 
 ``RKSteps.apply(prim0, grid, x0, nsteps, dt)`` advances the initial primitive
-state ``prim0`` ([4, ny, nx] FP64 CUDA tensor) on the grid's mesh ``x0`` by
+state ``prim0`` ([m, ny, nx] FP64 CUDA tensor; m = 4 on RHD grids, 8 on RMHD
+grids) on the grid's mesh ``x0`` by
 ``nsteps`` SSP-RK3 steps and returns the final conserved state J U; its
 backward pass runs the library's adjoint (recorded mesh velocities and steps,
 per-step checkpoints) and returns the gradient with respect to ``prim0``.

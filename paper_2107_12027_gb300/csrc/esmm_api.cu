@@ -946,7 +946,7 @@ int adj_alloc(esmm_grid *g)
     if (!g->adjGp) CK(cudaMalloc((void **)&g->adjGp, ADJ_GP_PER_NODE * P * d));
     double **bufs[] = {&g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v};
     for (double **b : bufs)
-        if (!*b) CK(cudaMalloc((void **)b, 4 * N * d));
+        if (!*b) CK(cudaMalloc((void **)b, (size_t)g->nv * N * d));
     return ESMM_OK;
 }
 
@@ -956,6 +956,30 @@ int rhs_vjp_core(esmm_grid *g, const double *cons, const double *J, const double
 {
     size_t P = (size_t)g->Ptot, N = (size_t)g->Ntot, d = sizeof(double);
     node(g, cons, J, x, xdot, nullptr, nullptr);
+    if (g->phys == ESMM_RMHD) {
+        // forward interface fluxes first: the Powell term needs div B~
+        fluxes(g);
+        CK(cudaMemsetAsync(g->adjG, 0, ADJ_LAMQ_PER_NODE * P * d, g->st));
+        CK(cudaMemsetAsync(lam, 0, 8 * N * d, g->st));
+        Phys ph = phys(g);
+        for (int dir = 0; dir < 2; ++dir) {
+            {
+                Prof pr_(g, ESMM_KIND_PAIRS);
+                launch_pairs_vjp_mhd(dom(g, dir ? D_PAIR1 : D_PAIR0), ph, g->q, mu, g->adjG, dir, g->st);
+            }
+            if (g->w > 0) {
+                Prof pr_(g, ESMM_KIND_IFACE);
+                launch_iface_vjp_mhd(dom(g, dir ? D_IFACE1 : D_IFACE0), ph, g->q, mu, g->adjG, dir, g->st);
+            }
+        }
+        {
+            Prof pr_(g, ESMM_KIND_NODE);
+            launch_node_vjp_mhd(dom(g, D_PAD), g->gamma, g->q, g->adjG, (const double *)g->iflux, mu, J, lam,
+                                g->st);
+        }
+        CK(cudaGetLastError());
+        return ESMM_OK;
+    }
     CK(cudaMemsetAsync(g->adjG, 0, ADJ_G_PER_NODE * P * d, g->st));
     CK(cudaMemsetAsync(g->adjGp, 0, ADJ_GP_PER_NODE * P * d, g->st));
     CK(cudaMemsetAsync(lam, 0, 4 * N * d, g->st));
@@ -1040,6 +1064,13 @@ cudaError_t static_scratch(double **out)
 
 // ===========================================================================
 extern "C" {
+
+int esmm_mhd_eigen(double gamma, int n, const double *w, const double *dw, double *lam, double *R, double *dlam,
+                   double *dR)
+{
+    if (n < 1 || !w || !lam || !R || (dw && (!dlam || !dR))) return ESMM_ERR_ARG;
+    return mhd_eigen_host(gamma, n, w, dw, lam, R, dlam, dR) ? ESMM_ERR_CUDA : ESMM_OK;
+}
 
 const char *esmm_version(void) { return "esmm 0.3 (2D RHD and RMHD, batched RHD, sm_103a)"; }
 
@@ -1345,13 +1376,14 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 {
     if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !cons || !J || !x || !mu || !lam || g->nprob != 1) return ESMM_ERR_ARG;
-    if (g->phys != ESMM_RHD) return fail(g, ESMM_ERR_ARG, "the adjoint covers RHD grids");
+    if (g->phys == ESMM_RMHD && g->prm.precision != ESMM_FP64)
+        return fail(g, ESMM_ERR_ARG, "the RMHD adjoint is FP64");
     int rc;
     if ((rc = ensure_doms(g)) || (rc = adj_alloc(g))) return rc;
-    size_t N = (size_t)g->Ntot;
+    size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
     if (mem == ESMM_MEM_HOST) {
-        if ((rc = copy_in(g, g->in_cons, cons, 4 * N, mem)) || (rc = copy_in(g, g->in_J, J, N, mem)) ||
-            (rc = copy_in(g, g->in_x, x, 2 * N, mem)) || (rc = copy_in(g, g->lam_a, mu, 4 * N, mem)))
+        if ((rc = copy_in(g, g->in_cons, cons, nv * N, mem)) || (rc = copy_in(g, g->in_J, J, N, mem)) ||
+            (rc = copy_in(g, g->in_x, x, 2 * N, mem)) || (rc = copy_in(g, g->lam_a, mu, nv * N, mem)))
             return rc;
         if (xdot && (rc = copy_in(g, g->in_xdot, xdot, 2 * N, mem))) return rc;
         cons = g->in_cons;
@@ -1363,7 +1395,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
     double *out = mem == ESMM_MEM_HOST ? g->lam_v : lam;
     if ((rc = rhs_vjp_core(g, cons, J, x, xdot, mu, out))) return rc;
     if (mem == ESMM_MEM_HOST) {
-        if ((rc = copy_out(g, lam, g->lam_v, 4 * N, mem))) return rc;
+        if ((rc = copy_out(g, lam, g->lam_v, nv * N, mem))) return rc;
         CK(cudaStreamSynchronize(g->st));
         return check_c2p(g);
     }
@@ -1374,24 +1406,25 @@ int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 {
     if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
-    if (g->phys != ESMM_RHD) return fail(g, ESMM_ERR_ARG, "the adjoint covers RHD grids");
+    if (g->phys == ESMM_RMHD && g->prm.precision != ESMM_FP64)
+        return fail(g, ESMM_ERR_ARG, "the RMHD adjoint is FP64");
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
-    size_t N = (size_t)g->Ntot, d = sizeof(double);
+    size_t N = (size_t)g->Ntot, d = sizeof(double), nv = (size_t)g->nv;
     g->ck_dt->clear();
     g->ck_n = 0;
     for (int n = 0; n < nsteps; ++n) {
         if ((int)g->ck->size() <= n) {
             double *b = nullptr;
-            CK(cudaMalloc((void **)&b, 9 * N * d));
+            CK(cudaMalloc((void **)&b, (nv + 5) * N * d));   // cons, J, x, xdot
             g->ck->push_back(b);
         }
         double *b = (*g->ck)[n];
-        CK(cudaMemcpyAsync(b, g->cons, 4 * N * d, cudaMemcpyDeviceToDevice, g->st));
-        CK(cudaMemcpyAsync(b + 4 * N, g->J, N * d, cudaMemcpyDeviceToDevice, g->st));
-        CK(cudaMemcpyAsync(b + 5 * N, g->x, 2 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(b, g->cons, nv * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(b + nv * N, g->J, N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(b + (nv + 1) * N, g->x, 2 * N * d, cudaMemcpyDeviceToDevice, g->st));
         int rc = rk_step_async(g, dt);
         if (rc) return rc;
-        CK(cudaMemcpyAsync(b + 7 * N, g->xdot, 2 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK(cudaMemcpyAsync(b + (nv + 3) * N, g->xdot, 2 * N * d, cudaMemcpyDeviceToDevice, g->st));
         CK(cudaMemcpyAsync(g->pin, g->dt_dev, d, cudaMemcpyDeviceToHost, g->st));
         CK(cudaStreamSynchronize(g->st));
         g->ck_dt->push_back(g->pin[0]);
@@ -1414,14 +1447,14 @@ int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int m
 {
     if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g || !out || step < 0 || step >= g->ck_n) return ESMM_ERR_ARG;
-    size_t N = (size_t)g->Ntot;
+    size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
     const double *b = (*g->ck)[step];
     int rc;
     switch (what) {
-    case ESMM_GET_CONS: rc = copy_out(g, out, b, 4 * N, mem); break;
-    case ESMM_GET_J: rc = copy_out(g, out, b + 4 * N, N, mem); break;
-    case ESMM_GET_X: rc = copy_out(g, out, b + 5 * N, 2 * N, mem); break;
-    case ESMM_GET_XDOT: rc = copy_out(g, out, b + 7 * N, 2 * N, mem); break;
+    case ESMM_GET_CONS: rc = copy_out(g, out, b, nv * N, mem); break;
+    case ESMM_GET_J: rc = copy_out(g, out, b + nv * N, N, mem); break;
+    case ESMM_GET_X: rc = copy_out(g, out, b + (nv + 1) * N, 2 * N, mem); break;
+    case ESMM_GET_XDOT: rc = copy_out(g, out, b + (nv + 3) * N, 2 * N, mem); break;
     default: return fail(g, ESMM_ERR_ARG, "unknown field");
     }
     if (rc) return rc;
@@ -1436,7 +1469,7 @@ int esmm_adjoint_replay(esmm_grid *g, int nsteps)
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     size_t N = (size_t)g->Ntot;
     for (int n = 0; n < nsteps; ++n) {
-        int rc = step_given(g, (*g->ck)[n] + 7 * N, (*g->ck_dt)[n]);
+        int rc = step_given(g, (*g->ck)[n] + (g->nv + 3) * N, (*g->ck_dt)[n]);
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(g->st));
@@ -1450,13 +1483,13 @@ int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, d
     if (g->ck_n < 1) return fail(g, ESMM_ERR_STATE, "no recorded steps");
     int rc;
     if ((rc = ensure_doms(g)) || (rc = adj_alloc(g))) return rc;
-    size_t N = (size_t)g->Ntot;
-    const long long n4 = 4 * (long long)N;
+    size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
+    const long long n4 = (long long)(nv * N);
     double *la = g->lam_a, *lb = g->lam_b, *lc = g->lam_c, *v = g->lam_v;
-    if ((rc = copy_in(g, la, lam_final, 4 * N, mem))) return rc;
+    if ((rc = copy_in(g, la, lam_final, nv * N, mem))) return rc;
     for (int n = g->ck_n - 1; n >= 0; --n) {
         double *b = (*g->ck)[n];
-        double *c0 = b, *J0 = b + 4 * N, *x0 = b + 5 * N, *xd = b + 7 * N;
+        double *c0 = b, *J0 = b + nv * N, *x0 = b + (nv + 1) * N, *xd = b + (nv + 3) * N;
         double dt = (*g->ck_dt)[n];
         if ((rc = set_dt(g, dt))) return rc;
         // recompute the stage states (c1, J1, x1), (c2, J2, x2)
@@ -1480,12 +1513,13 @@ int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, d
         launch_lincomb(n4, 1.0, lc, dt, v, la, g->st);                      // lambda of c^n
     }
     CK(cudaGetLastError());
-    if (lam_cons0 && (rc = copy_out(g, lam_cons0, la, 4 * N, mem))) return rc;
+    if (lam_cons0 && (rc = copy_out(g, lam_cons0, la, nv * N, mem))) return rc;
     if (lam_prim0) {
         double *b0 = (*g->ck)[0];
         LaunchDom L = dom(g, D_NODE);
-        launch_prim_grad(L, g->gamma, b0, b0 + 4 * N, la, v, g->st);
-        if ((rc = copy_out(g, lam_prim0, v, 4 * N, mem))) return rc;
+        if (g->phys == ESMM_RMHD) launch_prim_grad_mhd(L, g->gamma, b0, b0 + nv * N, la, v, g->status, g->st);
+        else launch_prim_grad(L, g->gamma, b0, b0 + 4 * N, la, v, g->st);
+        if ((rc = copy_out(g, lam_prim0, v, nv * N, mem))) return rc;
     }
     CK(cudaStreamSynchronize(g->st));
     return check_c2p(g);

@@ -228,9 +228,57 @@ __device__ __forceinline__ fdual operator/(double a, fdual b) { return fdual((fl
 __device__ __forceinline__ fdual &operator+=(fdual &a, fdual b) { a = a + b; return a; }
 __device__ __forceinline__ fdual &operator-=(fdual &a, fdual b) { a = a - b; return a; }
 
-// the dual number over a working precision
+// Hyper-dual number v + a e1 + b e2 + ab e1 e2 (e1^2 = e2^2 = 0): e1 carries a
+// Jacobian image direction, e2 the adjoint's seeded state direction, and ab
+// the mixed second derivative.  Used for the images of the RMHD
+// eigen-system inside the adjoint.
+struct hdual {
+    double v, a, b, ab;
+    __host__ __device__ hdual() {}
+    __host__ __device__ constexpr hdual(double x) : v(x), a(0.0), b(0.0), ab(0.0) {}
+    __host__ __device__ constexpr hdual(double x, double a_, double b_, double ab_) : v(x), a(a_), b(b_), ab(ab_) {}
+};
+__device__ __forceinline__ hdual operator+(hdual x, hdual y) { return hdual(x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab); }
+__device__ __forceinline__ hdual operator-(hdual x, hdual y) { return hdual(x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab); }
+__device__ __forceinline__ hdual operator-(hdual x) { return hdual(-x.v, -x.a, -x.b, -x.ab); }
+__device__ __forceinline__ hdual operator*(hdual x, hdual y)
+{
+    return hdual(x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b,
+                 x.ab * y.v + x.a * y.b + x.b * y.a + x.v * y.ab);
+}
+// f(x) for a scalar function with value f, first and second derivatives f1, f2 at x.v
+__device__ __forceinline__ hdual hchain(hdual x, double f, double f1, double f2)
+{
+    return hdual(f, f1 * x.a, f1 * x.b, f1 * x.ab + f2 * x.a * x.b);
+}
+__device__ __forceinline__ hdual hrcp(hdual x)
+{
+    double r = 1.0 / x.v;
+    return hchain(x, r, -r * r, 2.0 * r * r * r);
+}
+__device__ __forceinline__ hdual operator/(hdual x, hdual y) { return x * hrcp(y); }
+__device__ __forceinline__ hdual operator+(hdual x, double y) { return hdual(x.v + y, x.a, x.b, x.ab); }
+__device__ __forceinline__ hdual operator+(double x, hdual y) { return hdual(x + y.v, y.a, y.b, y.ab); }
+__device__ __forceinline__ hdual operator-(hdual x, double y) { return hdual(x.v - y, x.a, x.b, x.ab); }
+__device__ __forceinline__ hdual operator-(double x, hdual y) { return hdual(x - y.v, -y.a, -y.b, -y.ab); }
+__device__ __forceinline__ hdual operator*(hdual x, double y) { return hdual(x.v * y, x.a * y, x.b * y, x.ab * y); }
+__device__ __forceinline__ hdual operator*(double x, hdual y) { return hdual(x * y.v, x * y.a, x * y.b, x * y.ab); }
+__device__ __forceinline__ hdual operator/(hdual x, double y) { return x * (1.0 / y); }
+__device__ __forceinline__ hdual operator/(double x, hdual y) { return x * hrcp(y); }
+
+// the dual number over a working precision (hdual over dual)
 template <typename R> struct DualOf { using type = dual; };
 template <> struct DualOf<float> { using type = fdual; };
+template <> struct DualOf<dual> { using type = hdual; };
+// an image seed: value w moved along direction d (for hdual: w, d are duals
+// whose .d parts are the seeded state direction and d's derivative along it)
+__device__ __forceinline__ dual img_seed(double w, double d) { return dual(w, d); }
+__device__ __forceinline__ fdual img_seed(float w, float d) { return fdual(w, d); }
+__device__ __forceinline__ hdual img_seed(dual w, dual d) { return hdual(w.v, d.v, w.d, d.d); }
+// the image part of a seeded result, in the working precision
+__device__ __forceinline__ double img_part(dual x) { return x.d; }
+__device__ __forceinline__ float img_part(fdual x) { return x.d; }
+__device__ __forceinline__ dual img_part(hdual x) { return dual(x.a, x.ab); }
 
 // type of the log-mean arguments: FP64 for the FP64 and FP32-bulk forms
 template <typename R> struct LogT { using type = double; };
@@ -256,6 +304,12 @@ template <> __device__ __forceinline__ fdual sq_rt<fdual>(fdual x)
 {
     float r = sqrtf(x.v);
     return fdual(r, 0.5f * x.d * __frcp_rn(r));
+}
+template <> __device__ __forceinline__ hdual sq_rt<hdual>(hdual x)
+{
+    double r = sqrt(x.v);
+    double r1 = 0.5 / r;
+    return hchain(x, r, r1, -0.5 * r1 / x.v);
 }
 // reciprocal (IEEE round-to-nearest) and a square root of a positive value
 // through the reciprocal square root: on GB300 both are cheaper than the

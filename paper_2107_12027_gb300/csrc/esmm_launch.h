@@ -71,6 +71,21 @@ void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, 
 void launch_prim_out_mhd(const LaunchDom &L, double gam, const double *cons, const double *J, double *prim,
                          int *status, cudaStream_t st);
 
+// RMHD adjoint (esmm_mhd_adjoint.cu): node-quantity adjoints lamq[11][P]
+// accumulated by the pair and interface passes, then the node pass.
+void launch_pairs_vjp_mhd(const LaunchDom &L, const Phys &ph, const double *q, const double *mu, double *lamq,
+                          int dir, cudaStream_t st);
+void launch_iface_vjp_mhd(const LaunchDom &L, const Phys &ph, const double *q, const double *mu, double *lamq,
+                          int dir, cudaStream_t st);
+void launch_node_vjp_mhd(const LaunchDom &L, double gam, const double *q, const double *lamq, const double *iflux,
+                         const double *mu, const double *J, double *lam, cudaStream_t st);
+void launch_prim_grad_mhd(const LaunchDom &L, double gam, const double *cons, const double *J, const double *lam,
+                          double *out, int *status, cudaStream_t st);
+constexpr long long ADJ_LAMQ_PER_NODE = 11;
+// esmm_mhd_eigen (host arrays): 0, or 1 on a CUDA failure
+int mhd_eigen_host(double gam, int n, const double *w, const double *dw, double *lam, double *R, double *dlam,
+                   double *dR);
+
 // sizes of the adjoint's contribution buffers, in doubles per padded node
 constexpr long long ADJ_G_PER_NODE = 2 * 6 * 7;
 constexpr long long ADJ_GP_PER_NODE = 2 * PMAX * 2 * 7;

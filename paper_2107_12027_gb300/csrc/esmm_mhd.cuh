@@ -11,6 +11,8 @@
 // esmm_mhd.cu and the 3D kernels (esmm_3d.cu) reuse the arithmetic.
 #pragma once
 
+#include <type_traits>
+
 #include "esmm_device.cuh"
 #include "esmm_launch.h"
 
@@ -94,6 +96,11 @@ template <typename T> __device__ __forceinline__ T lg(T x);
 template <> __device__ __forceinline__ double lg<double>(double x) { return log(x); }
 template <> __device__ __forceinline__ dual lg<dual>(dual x) { return dual(log(x.v), x.d / x.v); }
 template <> __device__ __forceinline__ fdual lg<fdual>(fdual x) { return fdual(logf(x.v), x.d * __frcp_rn(x.v)); }
+template <> __device__ __forceinline__ hdual lg<hdual>(hdual x)
+{
+    double r = 1.0 / x.v;
+    return hchain(x, log(x.v), r, -r * r);
+}
 
 template <typename T>
 __device__ __forceinline__ void mhd_UFV(double gam, const T w[8], T U[8], T F[8], T V[8])
@@ -141,13 +148,13 @@ __device__ __forceinline__ void mhd_images(double gam, const R w[8], const R dir
     using D = typename DualOf<R>::type;
     D wd[8], U[8], F[8], V[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) wd[a] = D(w[a], dir[a]);
+    for (int a = 0; a < 8; ++a) wd[a] = img_seed(w[a], dir[a]);
     mhd_UFV<D>(gam, wd, U, F, V);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-        dU[a] = U[a].d;
-        dV[a] = V[a].d;
-        dF[a] = F[a].d + Pp[a] * dir[5];
+        dU[a] = img_part(U[a]);
+        dV[a] = img_part(V[a]);
+        dF[a] = img_part(F[a]) + Pp[a] * dir[5];
     }
 }
 
@@ -182,8 +189,63 @@ __device__ __forceinline__ void mhd_phiprime(const R w[8], R P[8])
 // span the <.,.> complement of y_a = e_a - projections (a = v_1, v_2, v_3,
 // p, B_2, B_3) and come from cyclic Jacobi on C = L^-1 K L^-T (G = L L^T);
 // clusters of speeds closer than CLUSTER_TOL get the canonical basis of
-// their span (pivoted Gram-Schmidt of the projected C-space unit vectors).
+// their span (Gram-Schmidt, in index order, of the projected C-space unit
+// vectors whose remaining squared norm is at least 1/8: continuous in the
+// span, unlike a largest-norm choice, which switches on the exact ties of
+// symmetric states).
 constexpr double MHD_CLUSTER_TOL = 1.0e-5;
+
+// Cyclic Jacobi on the symmetric 6 x 6 C (in place: its diagonal becomes the
+// eigenvalues), accumulating the rotations in Q when want_vectors.
+template <typename S>
+__device__ __forceinline__ void jacobi6(S C[6][6], S Q[6][6], bool want_vectors)
+{
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) Q[a][b] = a == b ? (S)1 : (S)0;
+    // converged when the off-diagonal part is at rounding level: (1e-15)^2
+    // of the diagonal in FP64, (1e-6)^2 in FP32 (the next sweep squares it)
+    const S conv = sizeof(S) == 4 ? (S)1.0e-12 : (S)1.0e-30;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        S off = (S)0, dg = (S)0;
+        for (int a = 0; a < 6; ++a) {
+            dg += C[a][a] * C[a][a];
+            for (int b = a + 1; b < 6; ++b) off += C[a][b] * C[a][b];
+        }
+        if (off <= conv * dg) break;
+        // The rotation loops stay rolled: fully unrolled, this sweep came out
+        // of nvcc 13.0 -O3 (sm_103a) as a non-similarity transform (wrong
+        // eigenvalues; the host build and the -G build of the same source are
+        // right), so unrolling is disabled here.
+#pragma unroll 1
+        for (int p = 0; p < 5; ++p)
+#pragma unroll 1
+            for (int q = p + 1; q < 6; ++q) {
+                if (C[p][q] == (S)0) continue;
+                S theta = (C[q][q] - C[p][p]) / ((S)2 * C[p][q]);
+                S t = (theta >= (S)0 ? (S)1 : (S)-1) / (fab<S>(theta) + sq_rt<S>(theta * theta + (S)1));
+                S cs = (S)1 / sq_rt<S>(t * t + (S)1), sn = t * cs;
+#pragma unroll 1
+                for (int k = 0; k < 6; ++k) {
+                    S ckp = C[k][p], ckq = C[k][q];
+                    C[k][p] = cs * ckp - sn * ckq;
+                    C[k][q] = sn * ckp + cs * ckq;
+                }
+#pragma unroll 1
+                for (int k = 0; k < 6; ++k) {
+                    S cpk = C[p][k], cqk = C[q][k];
+                    C[p][k] = cs * cpk - sn * cqk;
+                    C[q][k] = sn * cpk + cs * cqk;
+                }
+                if (want_vectors)
+#pragma unroll 1
+                    for (int k = 0; k < 6; ++k) {
+                        S qkp = Q[k][p], qkq = Q[k][q];
+                        Q[k][p] = cs * qkp - sn * qkq;
+                        Q[k][q] = sn * qkp + cs * qkq;
+                    }
+            }
+    }
+}
 
 template <typename R>
 static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8], R Rv[8][8], bool want_vectors)
@@ -211,7 +273,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
             Vy[a][r] = Ve[r] - cr * Vr[r] - cd * Vd[r];
             Fy[a][r] = Fe[r] - cr * Fr[r] - cd * Fd[r];
         }
-        if (sizeof(R) == 4) {
+        if constexpr (std::is_same<R, float>::value) {
             // FP32: scale y_a to unit <y_a, y_a> (the Gram diagonal spans
             // many decades at large W); C = L^-1 K L^-T is unchanged by it
             R sa = rsq<R>(dot8(Uy[a], Vy[a]));
@@ -235,7 +297,8 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
     for (int j = 0; j < 6; ++j) {
         R d = Gm[j][j];
         for (int k = 0; k < j; ++k) d -= Gm[j][k] * Gm[j][k];
-        if (sizeof(R) == 4 && !(d > (R)1.0e-12)) d = (R)1.0e-12;   // FP32: keep the factor finite
+        if constexpr (std::is_same<R, float>::value)
+            if (!(d > (R)1.0e-12)) d = (R)1.0e-12;   // FP32: keep the factor finite
         Gm[j][j] = sq_rt<R>(d);
         for (int i = j + 1; i < 6; ++i) {
             R s = Gm[i][j];
@@ -258,91 +321,92 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
         }
     for (int a = 0; a < 6; ++a)
         for (int b = 0; b < a; ++b) C[a][b] = C[b][a] = (R)0.5 * (C[a][b] + C[b][a]);
-    R Q[6][6];
-    for (int a = 0; a < 6; ++a)
-        for (int b = 0; b < 6; ++b) Q[a][b] = a == b ? (R)1 : (R)0;
-    // converged when the off-diagonal part is at rounding level: (1e-15)^2
-    // of the diagonal in FP64, (1e-6)^2 in FP32 (the next sweep squares it)
-    const R conv = sizeof(R) == 4 ? (R)1.0e-12 : (R)1.0e-30;
-    for (int sweep = 0; sweep < 50; ++sweep) {
-        R off = (R)0, dg = (R)0;
-        for (int a = 0; a < 6; ++a) {
-            dg += C[a][a] * C[a][a];
-            for (int b = a + 1; b < 6; ++b) off += C[a][b] * C[a][b];
-        }
-        if (off <= conv * dg) break;
-        // The rotation loops stay rolled: fully unrolled, this sweep came out
-        // of nvcc 13.0 -O3 (sm_103a) as a non-similarity transform (wrong
-        // eigenvalues; the host build and the -G build of the same source are
-        // right), so unrolling is disabled here.
-#pragma unroll 1
-        for (int p = 0; p < 5; ++p)
-#pragma unroll 1
-            for (int q = p + 1; q < 6; ++q) {
-                if (C[p][q] == (R)0) continue;
-                R theta = (C[q][q] - C[p][p]) / ((R)2 * C[p][q]);
-                R t = (theta >= (R)0 ? (R)1 : (R)-1) / (fab<R>(theta) + sq_rt<R>(theta * theta + (R)1));
-                R cs = (R)1 / sq_rt<R>(t * t + (R)1), sn = t * cs;
-#pragma unroll 1
-                for (int k = 0; k < 6; ++k) {
-                    R ckp = C[k][p], ckq = C[k][q];
-                    C[k][p] = cs * ckp - sn * ckq;
-                    C[k][q] = sn * ckp + cs * ckq;
-                }
-#pragma unroll 1
-                for (int k = 0; k < 6; ++k) {
-                    R cpk = C[p][k], cqk = C[q][k];
-                    C[p][k] = cs * cpk - sn * cqk;
-                    C[q][k] = sn * cpk + cs * cqk;
-                }
-                if (want_vectors)
-#pragma unroll 1
-                    for (int k = 0; k < 6; ++k) {
-                        R qkp = Q[k][p], qkq = Q[k][q];
-                        Q[k][p] = cs * qkp - sn * qkq;
-                        Q[k][q] = sn * qkp + cs * qkq;
-                    }
-            }
-    }
     int ord[6] = {0, 1, 2, 3, 4, 5};
-    for (int a = 0; a < 6; ++a)
-        for (int b = a + 1; b < 6; ++b)
-            if (C[ord[b]][ord[b]] < C[ord[a]][ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
-    lam[0] = v1;
-    lam[1] = v1;
-    for (int m = 0; m < 6; ++m) lam[2 + m] = C[ord[m]][ord[m]];
-    if (!want_vectors) return;
     R E6[6][6];
-    for (int m = 0; m < 6; ++m)
-        for (int r = 0; r < 6; ++r) E6[r][m] = Q[r][ord[m]];
+    if constexpr (std::is_same<R, dual>::value) {
+        // Adjoint tangent: Jacobi on the values; first-order perturbation
+        // theory for the tangent.  With M = Q^T C' Q (C' = C.d), an eigenvalue
+        // moves by M_ii and eigenvector i by sum_j M_ji / (lam_i - lam_j) e_j
+        // over the j outside i's cluster: inside a cluster only the span is
+        // defined, and the canonical basis below is a function of the span.
+        double Cv[6][6], Qv[6][6], M[6][6];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) Cv[i][j] = C[i][j].v;
+        jacobi6<double>(Cv, Qv, true);
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < 6; ++k)
+                    for (int l = 0; l < 6; ++l) acc += Qv[k][i] * C[k][l].d * Qv[l][j];
+                M[i][j] = acc;
+            }
+        for (int a = 0; a < 6; ++a)
+            for (int b = a + 1; b < 6; ++b)
+                if (Cv[ord[b]][ord[b]] < Cv[ord[a]][ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
+        int cl[6];   // cluster id of each sorted wave
+        cl[0] = 0;
+        for (int m = 1; m < 6; ++m)
+            cl[m] = cl[m - 1] + (Cv[ord[m]][ord[m]] - Cv[ord[m - 1]][ord[m - 1]] < MHD_CLUSTER_TOL ? 0 : 1);
+        for (int m = 0; m < 6; ++m) {
+            const int i = ord[m];
+            const double li = Cv[i][i];
+            lam[2 + m] = dual(li, M[i][i]);
+            if (!want_vectors) continue;
+            for (int r = 0; r < 6; ++r) {
+                double t = 0.0;
+                for (int n = 0; n < 6; ++n) {
+                    if (cl[n] == cl[m]) continue;
+                    const int j = ord[n];
+                    t += M[j][i] / (li - Cv[j][j]) * Qv[r][j];
+                }
+                E6[r][m] = dual(Qv[r][i], t);
+            }
+        }
+        lam[0] = v1;
+        lam[1] = v1;
+        if (!want_vectors) return;
+    } else {
+        R Q[6][6];
+        jacobi6<R>(C, Q, want_vectors);
+        for (int a = 0; a < 6; ++a)
+            for (int b = a + 1; b < 6; ++b)
+                if (C[ord[b]][ord[b]] < C[ord[a]][ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
+        lam[0] = v1;
+        lam[1] = v1;
+        for (int m = 0; m < 6; ++m) lam[2 + m] = C[ord[m]][ord[m]];
+        if (!want_vectors) return;
+        for (int m = 0; m < 6; ++m)
+            for (int r = 0; r < 6; ++r) E6[r][m] = Q[r][ord[m]];
+    }
     int start = 0;
     while (start < 6) {
         int end = start + 1;
-        while (end < 6 && lam[2 + end] - lam[1 + end] < (R)MHD_CLUSTER_TOL) ++end;
+        while (end < 6 && val(lam[2 + end]) - val(lam[1 + end]) < MHD_CLUSTER_TOL) ++end;
         const int k = end - start;
         if (k > 1) {
+            // Gram-Schmidt in index order of the C-space unit vectors projected
+            // on the cluster's span, taking those with remaining squared norm
+            // >= 1/8 (k of them always are: the six squared norms sum to k)
             R z[6][6], basis[6][6];
-            bool used[6] = {false, false, false, false, false, false};
             for (int i = 0; i < 6; ++i)
                 for (int c = 0; c < k; ++c) z[i][c] = E6[i][start + c];
-            for (int t = 0; t < k; ++t) {
-                int best = -1;
-                R bn = (R)-1;
-                for (int i = 0; i < 6; ++i) {
-                    if (used[i]) continue;
-                    R n2 = (R)0;
-                    for (int c = 0; c < k; ++c) n2 += z[i][c] * z[i][c];
-                    if (best < 0 || n2 > bn) { bn = n2; best = i; }
-                }
-                used[best] = true;
-                R inr = (R)1 / sq_rt<R>(bn);
-                for (int c = 0; c < k; ++c) basis[t][c] = z[best][c] * inr;
-                for (int i = 0; i < 6; ++i) {
-                    if (used[i]) continue;
+            int nt = 0;
+            for (int i = 0; i < 6 && nt < k; ++i) {
+                R n2 = (R)0;
+                for (int c = 0; c < k; ++c) n2 += z[i][c] * z[i][c];
+                if (!(val(n2) >= 0.125)) continue;
+                R inr = (R)1 / sq_rt<R>(n2);
+                for (int c = 0; c < k; ++c) basis[nt][c] = z[i][c] * inr;
+                for (int ii = i + 1; ii < 6; ++ii) {
                     R pr = (R)0;
-                    for (int c = 0; c < k; ++c) pr += z[i][c] * basis[t][c];
-                    for (int c = 0; c < k; ++c) z[i][c] -= pr * basis[t][c];
+                    for (int c = 0; c < k; ++c) pr += z[ii][c] * basis[nt][c];
+                    for (int c = 0; c < k; ++c) z[ii][c] -= pr * basis[nt][c];
                 }
+                ++nt;
+            }
+            if (nt < k) {   // only for non-finite input: keep the Jacobi basis
+                start = end;
+                continue;
             }
             R nE[6][6];
             for (int t = 0; t < k; ++t)
@@ -382,7 +446,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
 // the rest (with copies r, b of rho, beta) in the working precision R.
 template <typename R>
 struct NodeMT {
-    double rho, beta, lnr, lnb;
+    typename LogT<R>::type rho, beta, lnr, lnb;   // FP64 (dual in the adjoint)
     R r, b, W, u[3], B[3];
 };
 using NodeM = NodeMT<double>;
@@ -418,8 +482,8 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> 
                                             const R m[3], R out[8])
 {
     R rln, irln, bln, ibln;
-    logmean<R, double>(L.rho, Rn.rho, L.lnr, Rn.lnr, thr, rln, irln);
-    logmean<R, double>(L.beta, Rn.beta, L.lnb, Rn.lnb, thr, bln, ibln);
+    logmean<R, typename LogT<R>::type>(L.rho, Rn.rho, L.lnr, Rn.lnr, thr, rln, irln);
+    logmean<R, typename LogT<R>::type>(L.beta, Rn.beta, L.lnb, Rn.lnb, thr, bln, ibln);
     const R half = (R)0.5;
     R bL[3], bR[3], vL[3], vR[3];
     // b^0 = W (v.B) = u.B

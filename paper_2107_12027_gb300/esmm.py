@@ -31,7 +31,7 @@ SYMBOLS = (
     "esmm_set_params", "esmm_get_params", "esmm_state_set", "esmm_state_set_cons", "esmm_state_get",
     "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
-    "esmm_rhs_static", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
+    "esmm_rhs_static", "esmm_mhd_eigen", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
     "esmm_batch_times", "esmm_batch_totals", "esmm_tune", "esmm_adjoint_record", "esmm_adjoint_steps",
     "esmm_adjoint_checkpoint", "esmm_adjoint_replay", "esmm_adjoint_vjp", "esmm_rhs_vjp",
 )
@@ -76,6 +76,7 @@ def lib():
             "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
             "esmm_profile": [vp, i],
             "esmm_rhs_static": [i, i, ctypes.POINTER(i), dp, dp, d, i, i, vp, vp, vp, vp, vp, vp, vp],
+            "esmm_mhd_eigen": [d, i, vp, vp, vp, vp, vp, vp],
             "esmm_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(i), dp, dp, ctypes.POINTER(i), i, vp],
             "esmm_batch_size": [vp, ctypes.POINTER(i)],
             "esmm_batch_state_set": [vp, i, vp, vp, i],
@@ -99,6 +100,23 @@ def lib():
 
 def version() -> str:
     return lib().esmm_version().decode()
+
+
+def mhd_eigen(gamma, w, dw=None):
+    """Scaled RMHD eigen-system of rotated primitive states w [n][8] (and, with
+    dw, its tangent): (lam [n][8], R [n][8][8]) or (lam, R, dlam, dR)."""
+    w = np.ascontiguousarray(np.atleast_2d(w), dtype=np.float64)
+    n = w.shape[0]
+    lam, R = np.empty((n, 8)), np.empty((n, 8, 8))
+    args = [float(gamma), n, w.ctypes.data, None, lam.ctypes.data, R.ctypes.data, None, None]
+    if dw is not None:
+        dw = np.ascontiguousarray(np.atleast_2d(dw), dtype=np.float64)
+        dlam, dR = np.empty((n, 8)), np.empty((n, 8, 8))
+        args[3], args[6], args[7] = dw.ctypes.data, dlam.ctypes.data, dR.ctypes.data
+    rc = lib().esmm_mhd_eigen(*args)
+    if rc != OK:
+        raise EsmmError(rc, "esmm_mhd_eigen")
+    return (lam, R) if dw is None else (lam, R, dlam, dR)
 
 
 def rhs_static(nx, ny, bc, lo, hi, gamma, p, w, cons, J, x, xdot, dcons, dJ, stream=None):
@@ -313,7 +331,7 @@ class Grid:
         return np.array(dts[:n.value])
 
     def adjoint_checkpoint(self, step, what, out=None):
-        size = {GET_CONS: 4, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
+        size = {GET_CONS: self.nv, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
         if out is None:
             out = np.empty((size, self.ny, self.nx) if size > 1 else (self.ny, self.nx))
         po, mo = _ptr(out, size * self.N)
@@ -329,11 +347,11 @@ class Grid:
         """dF/d(cons^0) and dF/d(prim^0) from lam_final = dF/d(cons^final)."""
         host = not _is_torch(lam_final)
         if host:
-            lam_cons0 = np.empty((4, self.ny, self.nx)) if lam_cons0 is None else lam_cons0
-            lam_prim0 = np.empty((4, self.ny, self.nx)) if lam_prim0 is None else lam_prim0
-        a = _ptr(lam_final, 4 * self.N)
-        c = _ptr(lam_cons0, 4 * self.N)
-        p_ = _ptr(lam_prim0, 4 * self.N)
+            lam_cons0 = np.empty((self.nv, self.ny, self.nx)) if lam_cons0 is None else lam_cons0
+            lam_prim0 = np.empty((self.nv, self.ny, self.nx)) if lam_prim0 is None else lam_prim0
+        a = _ptr(lam_final, self.nv * self.N)
+        c = _ptr(lam_cons0, self.nv * self.N)
+        p_ = _ptr(lam_prim0, self.nv * self.N)
         mem = _mem(a, *([c] if lam_cons0 is not None else []), *([p_] if lam_prim0 is not None else []))
         self._check(lib().esmm_adjoint_vjp(self.h, a[0], c[0], p_[0], mem))
         return lam_cons0, lam_prim0
@@ -341,9 +359,9 @@ class Grid:
     def rhs_vjp(self, cons, J, x, xdot, mu, lam=None):
         """(d rhs / d cons)^T mu at (cons, J, x, xdot) with J, x, xdot fixed."""
         if lam is None:
-            lam = np.empty((4, self.ny, self.nx))
-        a = [_ptr(cons, 4 * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N), _ptr(mu, 4 * self.N),
-             _ptr(lam, 4 * self.N)]
+            lam = np.empty((self.nv, self.ny, self.nx))
+        a = [_ptr(cons, self.nv * self.N), _ptr(J, self.N), _ptr(x, 2 * self.N), _ptr(mu, self.nv * self.N),
+             _ptr(lam, self.nv * self.N)]
         xd = _ptr(xdot, 2 * self.N)
         mem = _mem(*a, *([xd] if xdot is not None else []))
         self._check(lib().esmm_rhs_vjp(self.h, a[0][0], a[1][0], a[2][0], xd[0], a[3][0], a[4][0], mem))

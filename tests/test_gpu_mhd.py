@@ -165,9 +165,14 @@ def test_rotor_512_full_size_rhs():
 
 
 def test_rmhd_rejects_unsupported_forms():
-    # the adjoint is built for RHD grids only
+    # the RMHD adjoint is FP64 and 2D; batches are RHD
     x = wl.uniform_mesh(16, 16, (-0.5, -0.5), (0.5, 0.5), (False, False))
-    with esmm.Grid((16, 16), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), phys=esmm.RMHD) as g:
+    with esmm.Grid((16, 16), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), phys=esmm.RMHD, precision=esmm.MIXED) as g:
         g.state_set(wl.rotor(x), x)
+        with pytest.raises(esmm.EsmmError):
+            g.adjoint_record(1)
+    x3, prim3 = wl.blast3_config(8)
+    with esmm.Grid3((8, 8, 8), (-0.5,) * 3, (0.5,) * 3, bc=(1, 1, 1)) as g:
+        g.state_set(prim3, x3)
         with pytest.raises(esmm.EsmmError):
             g.adjoint_record(1)
