@@ -90,8 +90,8 @@ typedef struct {
  * ESMM_RMHD), or of n[0] x n[1] x n[2] nodes (dim 3, phys ESMM_RMHD: the
  * nested metrics of eq. SCLCoeff, FP64; defaults Gamma = 4/3, CFL 0.3,
  * alpha = 800), bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4.  3D grids
- * accept the single-problem calls and profiling; batches, the tuner, the
- * adjoint and ESMM_MIXED return ESMM_ERR_ARG for them (RMHD 2D grids take
+ * accept the single-problem calls, the adjoint and profiling; batches, the
+ * tuner and ESMM_MIXED return ESMM_ERR_ARG for them (RMHD 2D grids take
  * ESMM_MIXED and, in FP64, the adjoint; batches are RHD).  A periodic
  * direction has n[k] distinct nodes with spacing (hi-lo)/n[k]; an outflow
  * direction has nodes on both ends.  stream is a cudaStream_t (NULL: the
@@ -184,12 +184,12 @@ int esmm_batch_times(esmm_grid *g, double *t);
 int esmm_batch_totals(esmm_grid *g, double *out);
 
 /* Adjoint: gradients of a final-time functional with respect to the initial
- * data, single 2D problems (RHD, or RMHD in the FP64 form; ESMM_ERR_ARG for
- * batches, 3D grids and mixed-form RMHD grids), FP64.  m = 4 (RHD) or 8
- * (RMHD) components below.
+ * data, single problems (2D RHD, 2D RMHD in the FP64 form, 3D RMHD;
+ * ESMM_ERR_ARG for batches and mixed-form RMHD grids), FP64.  m = 4 (RHD) or
+ * 8 (RMHD) components and d = 2 or 3 mesh components below.
  * esmm_adjoint_record advances nsteps steps (dt as esmm_rk_step) from the
  * current state, keeping per-step checkpoints (state, mesh velocity, step) on
- * the device ((m + 5) N doubles per step).  The adjoint differentiates the
+ * the device ((m + 1 + 2 d) N doubles per step).  The adjoint differentiates the
  * recorded map: each step with its recorded mesh velocity and dt held fixed
  * (the monitor's maximum and the limiter's minimum are not differentiable),
  * the sign switch Y and the lambda^ maximum frozen at their forward
@@ -203,7 +203,8 @@ int esmm_batch_totals(esmm_grid *g, double *out);
  * the Newton recovery, the log means, the scaled eigenvectors (RMHD: the
  * first-order perturbation of the 8-wave construction, a cluster of
  * near-equal speeds through its span), the WENO weights and, for RMHD, the
- * Godunov-Powell source. */
+ * Godunov-Powell source; in 3D also through the angle by which the Sec. 4
+ * rotation is turned to the tangential B (or v) of the interface state. */
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt);
 int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt);
 int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int mem);

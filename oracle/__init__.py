@@ -129,6 +129,7 @@ def lib():
                 "oref3_cfl_dt": (ctypes.c_int, [c3, d, d, d, d]),
                 "oref3_mesh": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d, d, d]),
                 "oref3_rk_step": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d]),
+                "oref3_rk_step_given": (ctypes.c_int, [c3, d, d, d, d, ctypes.c_double]),
                 "oref3_totals": (ctypes.c_int, [c3, d, d, d, d, d]),
             }
             for name, (res, args) in sig.items():
@@ -478,6 +479,16 @@ def rk_step3(cfg, cons, J, x, dt=0.0):
     if st != 0:
         raise RuntimeError("oracle rk_step3: cons2prim failed")
     return cons.reshape(_shape3(cfg, 8)), J.reshape(_shape3(cfg, 1)), x.reshape(_shape3(cfg, 3)), dtu[0]
+
+
+def rk_step3_given(cfg, cons, J, x, xdot, dt):
+    """One 3D SSP-RK3 step with a given mesh velocity [3][nz][ny][nx] and step."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    cons, J, x = _vec(cons, 8 * N).copy(), _vec(J, N).copy(), _vec(x, 3 * N).copy()
+    st = lib().oref3_rk_step_given(ctypes.byref(cfg), _p(cons), _p(J), _p(x), _p(_vec(xdot, 3 * N)), float(dt))
+    if st != 0:
+        raise RuntimeError("oracle rk_step3_given: cons2prim failed")
+    return cons.reshape(_shape3(cfg, 8)), J.reshape(_shape3(cfg, 1)), x.reshape(_shape3(cfg, 3))
 
 
 def totals3(cfg, cons, J, dcons=None, dJ=None):

@@ -162,6 +162,7 @@ int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const 
 int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
                double *xdot, double *dtau, double *dt_out);
 int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used);
+int oref3_rk_step_given(const oref3_cfg *c, double *cons, double *J, double *x, const double *xdot, double dt);
 int oref3_totals(const oref3_cfg *c, const double *cons, const double *J, const double *dcons,
                  const double *dJ, double *out);
 

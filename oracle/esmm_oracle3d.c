@@ -638,17 +638,17 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
     return status;
 }
 
-/* SSP-RK3 (as in 2D) on (cons, J) and the mesh with xdot held for the step */
-int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used)
+/* SSP-RK3 (as in 2D) on (cons, J) and the mesh with a given mesh velocity
+ * xdot [3][N] and step dt, both held for the step: the map the adjoint
+ * differentiates. */
+int oref3_rk_step_given(const oref3_cfg *c, double *cons, double *J, double *x, const double *xdot, double dt)
 {
     long N = (long)c->nx * c->ny * c->nz;
     int status = 0;
-    double *xdot = (double *)calloc(3 * (size_t)N, sizeof(double));
     double *c1 = (double *)malloc(sizeof(double) * 8 * N), *c2 = (double *)malloc(sizeof(double) * 8 * N);
     double *J1 = (double *)malloc(sizeof(double) * N), *J2 = (double *)malloc(sizeof(double) * N);
     double *x1 = (double *)malloc(sizeof(double) * 3 * N), *x2 = (double *)malloc(sizeof(double) * 3 * N);
     double *L = (double *)malloc(sizeof(double) * 8 * N), *LJ = (double *)malloc(sizeof(double) * N);
-    status |= oref3_mesh(c, cons, J, x, dt, xdot, NULL, &dt);
     status |= oref3_rhs(c, cons, J, x, xdot, L, LJ);
     for (long a = 0; a < 8 * N; ++a) c1[a] = cons[a] + dt * L[a];
     for (long a = 0; a < N; ++a) J1[a] = J[a] + dt * LJ[a];
@@ -661,8 +661,20 @@ int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double
     for (long a = 0; a < 8 * N; ++a) cons[a] = cons[a] / 3.0 + 2.0 / 3.0 * (c2[a] + dt * L[a]);
     for (long a = 0; a < N; ++a) J[a] = J[a] / 3.0 + 2.0 / 3.0 * (J2[a] + dt * LJ[a]);
     for (long a = 0; a < 3 * N; ++a) x[a] = x[a] / 3.0 + 2.0 / 3.0 * (x2[a] + dt * xdot[a]);
+    free(c1); free(c2); free(J1); free(J2); free(x1); free(x2); free(L); free(LJ);
+    return status;
+}
+
+/* SSP-RK3 (as in 2D) on (cons, J) and the mesh with xdot held for the step */
+int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used)
+{
+    long N = (long)c->nx * c->ny * c->nz;
+    int status = 0;
+    double *xdot = (double *)calloc(3 * (size_t)N, sizeof(double));
+    status |= oref3_mesh(c, cons, J, x, dt, xdot, NULL, &dt);
+    status |= oref3_rk_step_given(c, cons, J, x, xdot, dt);
     if (dt_used) *dt_used = dt;
-    free(xdot); free(c1); free(c2); free(J1); free(J2); free(x1); free(x2); free(L); free(LJ);
+    free(xdot);
     return status;
 }
 

@@ -16,224 +16,11 @@
 
 #include "esmm.h"
 #include "esmm_3d.h"
-#include "esmm_mhd.cuh"
+#include "esmm_3d.cuh"
 #include "esmm_reduce.cuh"
 
 namespace esmm {
 namespace d3 {
-
-struct Geom3 {
-    int n[3];
-    int pd[3];
-    long long P, N;
-    int bc[3];
-    double per[3];
-};
-
-// node data fields (FP64, padded grid)
-enum {
-    F_RHO = 0, F_P, F_BETA, F_U0, F_U1, F_U2, F_W, F_LNR, F_LNB, F_B0, F_B1, F_B2,
-    F_M = 12,      // 9 spatial metrics M[k][j] = J d xi_k / d x_j at F_M + 3k + j
-    F_MT = 21,     // 3 temporal metrics J d xi_k / dt
-    NQ3 = 24
-};
-constexpr int NF3 = 10;     // per direction and padded node: F[8], metric flux, B~
-constexpr int NR3 = 8;      // reduction slots: grad, tau, radius[3], mesh Courant[3]
-
-__host__ __device__ __forceinline__ long long pidx3(const Geom3 &g, int i, int j, int k)
-{
-    return ((long long)(k + GH) * g.pd[1] + (j + GH)) * g.pd[0] + (i + GH);
-}
-
-__device__ __forceinline__ long long data_src3(const Geom3 &g, int i, int j, int k)
-{
-    int ii = g.bc[0] == 0 ? wrapi(i, g.n[0]) : clampi(i, 0, g.n[0] - 1);
-    int jj = g.bc[1] == 0 ? wrapi(j, g.n[1]) : clampi(j, 0, g.n[1] - 1);
-    int kk = g.bc[2] == 0 ? wrapi(k, g.n[2]) : clampi(k, 0, g.n[2] - 1);
-    return ((long long)kk * g.n[1] + jj) * g.n[0] + ii;
-}
-
-// Boundary-mapped mesh value, one direction at a time (2, then 1, then 0):
-// periodic wrap plus the period for the coordinate along that direction
-// (shift = 1), or linear extrapolation of the two nodes next to the boundary.
-__device__ __forceinline__ double mesh_d0(const Geom3 &g, const double *a, int comp, int i, int j, int k, int shift)
-{
-    const double *row = a + (long long)comp * g.N + ((long long)k * g.n[1] + j) * g.n[0];
-    int n = g.n[0];
-    if (g.bc[0] == 0) {
-        double s = (shift && comp == 0) ? floordivi(i, n) * g.per[0] : 0.0;
-        return row[wrapi(i, n)] + s;
-    }
-    if (i < 0) { double v0 = row[0], v1 = row[1]; return v0 + (double)(-i) * (v0 - v1); }
-    if (i > n - 1) { double v0 = row[n - 1], v1 = row[n - 2]; return v0 + (double)(i - (n - 1)) * (v0 - v1); }
-    return row[i];
-}
-
-__device__ __forceinline__ double mesh_d1(const Geom3 &g, const double *a, int comp, int i, int j, int k, int shift)
-{
-    int n = g.n[1];
-    if (g.bc[1] == 0) {
-        double s = (shift && comp == 1) ? floordivi(j, n) * g.per[1] : 0.0;
-        return mesh_d0(g, a, comp, i, wrapi(j, n), k, shift) + s;
-    }
-    if (j >= 0 && j <= n - 1) return mesh_d0(g, a, comp, i, j, k, shift);
-    int b0 = j < 0 ? 0 : n - 1, b1 = j < 0 ? 1 : n - 2;
-    double v0 = mesh_d0(g, a, comp, i, b0, k, shift), v1 = mesh_d0(g, a, comp, i, b1, k, shift);
-    double off = j < 0 ? (double)(-j) : (double)(j - (n - 1));
-    return v0 + off * (v0 - v1);
-}
-
-__device__ __forceinline__ double mesh3_at(const Geom3 &g, const double *a, int comp, int i, int j, int k, int shift)
-{
-    int n = g.n[2];
-    if (g.bc[2] == 0) {
-        double s = (shift && comp == 2) ? floordivi(k, n) * g.per[2] : 0.0;
-        return mesh_d1(g, a, comp, i, j, wrapi(k, n), shift) + s;
-    }
-    if (k >= 0 && k <= n - 1) return mesh_d1(g, a, comp, i, j, k, shift);
-    int b0 = k < 0 ? 0 : n - 1, b1 = k < 0 ? 1 : n - 2;
-    double v0 = mesh_d1(g, a, comp, i, j, b0, shift), v1 = mesh_d1(g, a, comp, i, j, b1, shift);
-    double off = k < 0 ? (double)(-k) : (double)(k - (n - 1));
-    return v0 + off * (v0 - v1);
-}
-
-template <int P> __device__ __forceinline__ constexpr double alpha3(int n)
-{
-    return P == 1 ? 1.0 : (P == 2 ? (n == 1 ? 4.0 / 3.0 : -1.0 / 6.0) : (n == 1 ? 1.5 : (n == 2 ? -0.3 : 1.0 / 30.0)));
-}
-
-__device__ __forceinline__ void step3(int i, int j, int k, int d, int s, int &a, int &b, int &c)
-{
-    a = i + (d == 0) * s;
-    b = j + (d == 1) * s;
-    c = k + (d == 2) * s;
-}
-
-// delta_d[x_comp] at (i, j, k)
-template <int P>
-__device__ __forceinline__ double delta_x3(const Geom3 &g, const double *x, int comp, int i, int j, int k, int d)
-{
-    double s = 0.0;
-#pragma unroll
-    for (int n = 1; n <= P; ++n) {
-        int a0, a1, a2, b0, b1, b2;
-        step3(i, j, k, d, n, a0, a1, a2);
-        step3(i, j, k, d, -n, b0, b1, b2);
-        s += 0.5 * alpha3<P>(n) * (mesh3_at(g, x, comp, a0, a1, a2, 1) - mesh3_at(g, x, comp, b0, b1, b2, 1));
-    }
-    return s;
-}
-
-// eq. SCLCoeff: M[k][j] = delta_{k2}[delta_{k1}[x_{j1}] x_{j2}] - delta_{k1}[delta_{k2}[x_{j1}] x_{j2}]
-template <int P>
-__device__ __forceinline__ double nested3(const Geom3 &g, const double *x, int d_out, int d_in, int ja, int jb, int i,
-                                          int j, int k)
-{
-    double s = 0.0;
-#pragma unroll
-    for (int n = 1; n <= P; ++n) {
-        int a0, a1, a2, b0, b1, b2;
-        step3(i, j, k, d_out, n, a0, a1, a2);
-        step3(i, j, k, d_out, -n, b0, b1, b2);
-        double fa = delta_x3<P>(g, x, ja, a0, a1, a2, d_in) * mesh3_at(g, x, jb, a0, a1, a2, 1);
-        double fb = delta_x3<P>(g, x, ja, b0, b1, b2, d_in) * mesh3_at(g, x, jb, b0, b1, b2, 1);
-        s += 0.5 * alpha3<P>(n) * (fa - fb);
-    }
-    return s;
-}
-
-template <int P>
-__device__ void metrics3(const Geom3 &g, const double *x, int i, int j, int k, double M[3][3])
-{
-#pragma unroll 1
-    for (int kk = 0; kk < 3; ++kk) {
-        int k1 = (kk + 1) % 3, k2 = (kk + 2) % 3;
-#pragma unroll 1
-        for (int jj = 0; jj < 3; ++jj) {
-            int j1 = (jj + 1) % 3, j2 = (jj + 2) % 3;
-            M[kk][jj] = nested3<P>(g, x, k2, k1, j1, j2, i, j, k) - nested3<P>(g, x, k1, k2, j1, j2, i, j, k);
-        }
-    }
-}
-
-// Sec. 4 rotation for the unit normal n (rows n, t1, t2; theta = 0 when the
-// x_1-x_2 part of n is below 1e-12), then turned about n so that t1 lies
-// along the tangential B of the state w (along the tangential v when
-// |B_t| <= 1e-10 max(1, |B|); unchanged when also |v_t| <= 1e-10, c = 1;
-// absolute thresholds, so that rounding noise in a field or velocity that
-// vanishes does not orient the frame).
-__device__ __forceinline__ void frame3(const double n[3], double T[3][3])
-{
-    double r = sqrt(n[0] * n[0] + n[1] * n[1]);
-    bool pole = r <= 1.0e-12;
-    double ct = pole ? 1.0 : n[0] / r, st = pole ? 0.0 : n[1] / r;
-    double cp = r, sp = n[2];
-    T[0][0] = cp * ct; T[0][1] = cp * st; T[0][2] = sp;
-    T[1][0] = -st;     T[1][1] = ct;      T[1][2] = 0.0;
-    T[2][0] = -sp * ct; T[2][1] = -sp * st; T[2][2] = cp;
-}
-
-__device__ __forceinline__ void align3(double T[3][3], const double w[8])
-{
-    double b1 = T[1][0] * w[5] + T[1][1] * w[6] + T[1][2] * w[7];
-    double b2 = T[2][0] * w[5] + T[2][1] * w[6] + T[2][2] * w[7];
-    double B2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
-    double t2 = b1 * b1 + b2 * b2;
-    if (!(t2 > 1.0e-20 * (1.0 + B2))) {
-        b1 = T[1][0] * w[1] + T[1][1] * w[2] + T[1][2] * w[3];
-        b2 = T[2][0] * w[1] + T[2][1] * w[2] + T[2][2] * w[3];
-        t2 = b1 * b1 + b2 * b2;
-        if (!(t2 > 1.0e-20)) return;
-    }
-    double tn = sqrt(t2), c = b1 / tn, s = b2 / tn;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        double a1 = T[1][q], a2 = T[2][q];
-        T[1][q] = c * a1 + s * a2;
-        T[2][q] = -s * a1 + c * a2;
-    }
-}
-
-__device__ __forceinline__ void rot3(const double T[3][3], const double *a, double *r)
-{
-    r[0] = a[0];
-    r[4] = a[4];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        r[1 + q] = T[q][0] * a[1] + T[q][1] * a[2] + T[q][2] * a[3];
-        r[5 + q] = T[q][0] * a[5] + T[q][1] * a[6] + T[q][2] * a[7];
-    }
-}
-
-__device__ __forceinline__ void unrot3(const double T[3][3], const double *r, double *a)
-{
-    a[0] = r[0];
-    a[4] = r[4];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        a[1 + q] = T[0][q] * r[1] + T[1][q] * r[2] + T[2][q] * r[3];
-        a[5 + q] = T[0][q] * r[5] + T[1][q] * r[6] + T[2][q] * r[7];
-    }
-}
-
-__device__ __forceinline__ NodeM load3(const double *__restrict__ q, long long P, long long c)
-{
-    NodeM v;
-    v.rho = q[F_RHO * P + c];
-    v.beta = q[F_BETA * P + c];
-    v.lnr = q[F_LNR * P + c];
-    v.lnb = q[F_LNB * P + c];
-    v.r = v.rho;
-    v.b = v.beta;
-    v.W = q[F_W * P + c];
-    v.u[0] = q[F_U0 * P + c];
-    v.u[1] = q[F_U1 * P + c];
-    v.u[2] = q[F_U2 * P + c];
-    v.B[0] = q[F_B0 * P + c];
-    v.B[1] = q[F_B1 * P + c];
-    v.B[2] = q[F_B2 * P + c];
-    return v;
-}
 
 // ---------------------------------------------------------------------------
 template <int P>
@@ -297,157 +84,6 @@ __global__ void k3_tmetric(Geom3 g, const double *__restrict__ xdot, double *__r
     for (int a = 0; a < 3; ++a)
         q[(F_MT + a) * g.P + t] = -(xd[0] * q[(F_M + 3 * a) * g.P + t] + xd[1] * q[(F_M + 3 * a + 1) * g.P + t] +
                                     xd[2] * q[(F_M + 3 * a + 2) * g.P + t]);
-}
-
-__device__ __forceinline__ void node_V3(const double *__restrict__ q, long long P, long long c, double c1g, double ig,
-                                        double V[8])
-{
-    double beta = q[F_BETA * P + c], W = q[F_W * P + c];
-    double u0 = q[F_U0 * P + c], u1 = q[F_U1 * P + c], u2 = q[F_U2 * P + c];
-    double B0 = q[F_B0 * P + c], B1 = q[F_B1 * P + c], B2 = q[F_B2 * P + c];
-    double b0 = u0 * B0 + u1 * B1 + u2 * B2;
-    double bW = beta / W;
-    V[0] = c1g + q[F_LNR * P + c] + ig * q[F_LNB * P + c] + beta;
-    V[1] = beta * u0;
-    V[2] = beta * u1;
-    V[3] = beta * u2;
-    V[4] = -beta * W;
-    V[5] = bW * (B0 + b0 * u0);
-    V[6] = bW * (B1 + b0 * u1);
-    V[7] = bW * (B2 + b0 * u2);
-}
-
-// ES interface flux (eq. ESFlux_HO) between node L (index -1 .. n_d - 1 along
-// the sweep) and L + 1, every line of the other two indices.
-template <int P, int WW>
-__global__ void __launch_bounds__(128) k3_iface(Geom3 g, Phys ph, const double *__restrict__ q,
-                                                double *__restrict__ iflux, int dir)
-{
-    const int nd = g.n[dir];
-    const int oa = dir == 0 ? 1 : 0, ob = dir == 2 ? 1 : 2;
-    const long long count = (long long)(nd + 1) * g.n[oa] * g.n[ob];
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= count) return;
-    int c3[3];
-    c3[dir] = (int)(idx % (nd + 1)) - 1;
-    c3[oa] = (int)((idx / (nd + 1)) % g.n[oa]);
-    c3[ob] = (int)(idx / ((long long)(nd + 1) * g.n[oa]));
-    const long long c0 = pidx3(g, c3[0], c3[1], c3[2]);
-    const long long sd = dir == 0 ? 1 : (dir == 1 ? (long long)g.pd[0] : (long long)g.pd[0] * g.pd[1]);
-    const double *Mt = q + (F_MT + dir) * g.P;
-    const double *Md = q + (F_M + 3 * dir) * g.P;   // M[dir][0..2] at Md + q' P
-    const double gm1inv = 1.0 / (ph.gamma - 1.0);
-    double F[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Ft = 0.0, Bt = 0.0;
-#pragma unroll
-    for (int n = 1; n <= P; ++n) {
-        double Fs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Fts = 0.0, Bts = 0.0;
-#pragma unroll
-        for (int s = 0; s < n; ++s) {
-            const long long cl = c0 - s * sd, cr = cl + n * sd;
-            NodeM l = load3(q, g.P, cl), r = load3(q, g.P, cr);
-            double mm[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) mm[a] = 0.5 * (Md[a * g.P + cl] + Md[a * g.P + cr]);
-            double out[8];
-            ec_pair_mhd<3>(l, r, gm1inv, ph.ln_thr, 0.5 * (Mt[cl] + Mt[cr]), mm, out);
-#pragma unroll
-            for (int a = 0; a < 8; ++a) Fs[a] += out[a];
-            Fts += 0.5 * (Mt[cl] + Mt[cr]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) Bts += 0.5 * mm[a] * (l.B[a] + r.B[a]);
-        }
-        const double an = ph.alpha[n - 1];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) F[a] += an * Fs[a];
-        Ft += an * Fts;
-        Bt += an * Bts;
-    }
-    if (WW > 0) {
-        constexpr int NS = WW + 1, OFF = (WW - 1) / 2;
-        const long long c1 = c0 + sd;
-        double nv[3], nn[3], T[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) nv[a] = 0.5 * (Md[a * g.P + c0] + Md[a * g.P + c1]);
-        const double jt = 0.5 * (Mt[c0] + Mt[c1]);
-        const double Lk = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) nn[a] = nv[a] / Lk;
-        frame3(nn, T);
-        double wm[8], wrot[8];
-        {
-            double rho, irho;
-            logmean<double, double>(q[F_RHO * g.P + c0], q[F_RHO * g.P + c1], q[F_LNR * g.P + c0],
-                                    q[F_LNR * g.P + c1], ph.ln_thr, rho, irho);
-            double um[3], W2 = 1.0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                um[a] = 0.5 * (q[(F_U0 + a) * g.P + c0] + q[(F_U0 + a) * g.P + c1]);
-                W2 += um[a] * um[a];
-            }
-            double W = sqrt(W2);
-            wm[0] = rho;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) wm[1 + a] = um[a] / W;
-            wm[4] = (q[F_RHO * g.P + c0] + q[F_RHO * g.P + c1]) / (q[F_BETA * g.P + c0] + q[F_BETA * g.P + c1]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) wm[5 + a] = 0.5 * (q[(F_B0 + a) * g.P + c0] + q[(F_B0 + a) * g.P + c1]);
-        }
-        align3(T, wm);
-        rot3(T, wm, wrot);
-        double lam[8], R[8][8];
-        eigen_mhd(ph.gamma, wrot, lam, R, true);
-        double lhat = 0.0;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) lhat = fmax(lhat, fabs(jt + Lk * lam[m]));
-        const double ig = gm1inv, c1g = ph.gamma * gm1inv;
-        double Vt[NS][8], scale[8];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) scale[m] = 0.0;
-        for (int kk = 0; kk < NS; ++kk) {
-            double V[8], TV[8];
-            node_V3(q, g.P, c0 + (kk - OFF) * sd, c1g, ig, V);
-            rot3(T, V, TV);
-            for (int m = 0; m < 8; ++m) {
-                double acc = 0.0;
-                for (int a = 0; a < 8; ++a) {
-                    double t = R[a][m] * TV[a];
-                    acc += t;
-                    if (kk == OFF || kk == OFF + 1) scale[m] += fabs(t);
-                }
-                Vt[kk][m] = acc;
-            }
-        }
-        double z[8];
-        for (int m = 0; m < 8; ++m) {
-            double vminus, vplus;
-            if (WW == 5) {
-                vminus = weno5<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], ph.eps);
-                vplus = weno5<double>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
-            } else {
-                vminus = weno3<double>(Vt[0][m], Vt[1][m], Vt[2][m], ph.eps);
-                vplus = weno3<double>(Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
-            }
-            double jw = vplus - vminus;
-            double jump = Vt[OFF + 1][m] - Vt[OFF][m];
-            int sj = fabs(jump) <= ph.sign_tol * scale[m] ? 0 : sgn_d(jump);
-            z[m] = (sgn_d(jw) == sj) ? jw : 0.0;
-        }
-        double d[8], dr[8];
-        for (int a = 0; a < 8; ++a) {
-            double acc = 0.0;
-            for (int m = 0; m < 8; ++m) acc += R[a][m] * z[m];
-            d[a] = acc;
-        }
-        unrot3(T, d, dr);
-        const double hl = 0.5 * lhat;
-#pragma unroll
-        for (int a = 0; a < 8; ++a) F[a] -= hl * dr[a];
-    }
-    double *out = iflux + (long long)(dir * NF3) * g.P + c0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) out[a * g.P] = F[a];
-    out[8 * g.P] = Ft;
-    out[9 * g.P] = Bt;
 }
 
 // flux differences over the three directions, the Powell source, written out
@@ -775,6 +411,12 @@ struct esmm3 {
     long long nl[ESMM_NKINDS];
     int prof_mask;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *ev;   // [ESMM_NKINDS]
+    // adjoint: per-step checkpoints [cons 8N | J N | x 3N | xdot 3N], steps,
+    // adjoint state buffers and the node-quantity adjoints lamq[11][P]
+    std::vector<double *> *ck;
+    std::vector<double> *ck_dt;
+    int ck_n;
+    double *lam_a, *lam_b, *lam_c, *lam_v, *lamq;
 };
 
 namespace {
@@ -850,16 +492,6 @@ void node3(esmm3 *g, const double *cons, const double *J, const double *x, const
     else k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
 }
 
-template <int P>
-void iface3_p(esmm3 *g, const Phys &ph, unsigned nb, int dir)
-{
-    switch (g->w) {
-    case 0: k3_iface<P, 0><<<nb, 128, 0, g->st>>>(g->g, ph, g->q, g->iflux, dir); break;
-    case 3: k3_iface<P, 3><<<nb, 128, 0, g->st>>>(g->g, ph, g->q, g->iflux, dir); break;
-    default: k3_iface<P, 5><<<nb, 128, 0, g->st>>>(g->g, ph, g->q, g->iflux, dir); break;
-    }
-}
-
 void fluxes3(esmm3 *g)
 {
     Phys ph = phys3(g);
@@ -868,9 +500,7 @@ void fluxes3(esmm3 *g)
         long long count = (long long)(g->g.n[dir] + 1) * g->g.n[oa] * g->g.n[ob];
         unsigned nb = nb3(count, 128);
         Prof3 pr_(g, ESMM_KIND_IFACE);
-        if (g->p == 1) iface3_p<1>(g, ph, nb, dir);
-        else if (g->p == 2) iface3_p<2>(g, ph, nb, dir);
-        else iface3_p<3>(g, ph, nb, dir);
+        launch3_iface(g->g, ph, g->p, g->w, g->q, g->iflux, dir, nb, g->st);
     }
 }
 
@@ -962,12 +592,80 @@ void free3(esmm3 *g)
     double **b[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2, &g->q,
                     &g->zg[0], &g->zg[1], &g->zg[2], &g->iflux, &g->out_dc, &g->out_dJ, &g->in_cons, &g->in_J,
                     &g->in_x, &g->in_xdot, &g->grad, &g->om, &g->om2, &g->X, &g->Xn, &g->dt_dev, &g->t_dev,
-                    &g->partials, &g->tot};
+                    &g->partials, &g->tot, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v, &g->lamq};
     for (double **p : b)
         if (*p) { cudaFree(*p); *p = nullptr; }
+    if (g->ck) {
+        for (double *c : *g->ck) cudaFree(c);
+        delete g->ck;
+        g->ck = nullptr;
+    }
+    delete g->ck_dt;
+    g->ck_dt = nullptr;
     if (g->red) cudaFree(g->red);
     if (g->status) cudaFree(g->status);
     if (g->pin) cudaFreeHost(g->pin);
+}
+
+// ---- adjoint -------------------------------------------------------------------
+int adj_alloc3(esmm3 *g)
+{
+    size_t N = (size_t)g->g.N, P = (size_t)g->g.P, d = sizeof(double);
+    double **b[] = {&g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v};
+    for (double **p : b)
+        if (!*p) CK3(cudaMalloc((void **)p, 8 * N * d));
+    if (!g->lamq) CK3(cudaMalloc((void **)&g->lamq, 11 * P * d));
+    if (!g->ck) g->ck = new (std::nothrow) std::vector<double *>;
+    if (!g->ck_dt) g->ck_dt = new (std::nothrow) std::vector<double>;
+    if (!g->ck || !g->ck_dt) return fail3(g, ESMM_ERR_ARG, "out of host memory");
+    return ESMM_OK;
+}
+
+// lam = (d rhs/d cons)^T mu at (cons, J, x, xdot), device arrays
+int rhs_vjp_core3(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot,
+                  const double *mu, double *lam)
+{
+    size_t N = (size_t)g->g.N, P = (size_t)g->g.P, d = sizeof(double);
+    node3(g, cons, J, x, xdot, nullptr, nullptr);
+    fluxes3(g);   // the Powell term's div B~
+    CK3(cudaMemsetAsync(g->lamq, 0, 11 * P * d, g->st));
+    CK3(cudaMemsetAsync(lam, 0, 8 * N * d, g->st));
+    Phys ph = phys3(g);
+    for (int dir = 0; dir < 3; ++dir) {
+        {
+            Prof3 pr_(g, ESMM_KIND_PAIRS);
+            launch3_pairs_vjp(g->g, ph, g->q, mu, g->lamq, dir, g->st);
+        }
+        if (g->w > 0) {
+            Prof3 pr_(g, ESMM_KIND_IFACE);
+            launch3_iface_vjp(g->g, ph, g->q, mu, g->lamq, dir, g->st);
+        }
+    }
+    {
+        Prof3 pr_(g, ESMM_KIND_NODE);
+        launch3_node_vjp(g->g, g->gamma, g->q, g->lamq, g->iflux, mu, J, lam, g->st);
+    }
+    CK3(cudaGetLastError());
+    return ESMM_OK;
+}
+
+int set_dt3(esmm3 *g, double dt)
+{
+    g->pin[0] = dt;
+    CK3(cudaMemcpyAsync(g->dt_dev, g->pin, sizeof(double), cudaMemcpyHostToDevice, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+// one step with a given mesh velocity (device, [3][N]) and dt
+int step_given3(esmm3 *g, const double *xd, double dt)
+{
+    int rc;
+    if ((rc = set_dt3(g, dt))) return rc;
+    CK3(cudaMemcpyAsync(g->xdot, xd, 3 * (size_t)g->g.N * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    g->xdot_zero = 0;
+    node3(g, g->cons, g->J, g->x, g->xdot, g->zg[0], g->zg[1]);
+    return stages3(g);
 }
 
 }  // namespace
@@ -1306,4 +1004,148 @@ int esmm3_profile_read(esmm3 *g, double ms[ESMM_NKINDS], long long launches[ESMM
         if (timed) timed[k] = g->ev ? (long long)g->ev[k].size() : 0;
     }
     return ESMM_OK;
+}
+
+// ---- adjoint entry points --------------------------------------------------------
+int esmm3_rhs_vjp(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot,
+                  const double *mu, double *lam, int mem)
+{
+    int rc;
+    if ((rc = adj_alloc3(g))) return rc;
+    size_t N = (size_t)g->g.N;
+    if (mem == ESMM_MEM_HOST) {
+        if ((rc = copy3(g, g->in_cons, cons, 8 * N, mem, true)) || (rc = copy3(g, g->in_J, J, N, mem, true)) ||
+            (rc = copy3(g, g->in_x, x, 3 * N, mem, true)) || (rc = copy3(g, g->lam_a, mu, 8 * N, mem, true)))
+            return rc;
+        if (xdot && (rc = copy3(g, g->in_xdot, xdot, 3 * N, mem, true))) return rc;
+        cons = g->in_cons;
+        J = g->in_J;
+        x = g->in_x;
+        xdot = xdot ? g->in_xdot : nullptr;
+        mu = g->lam_a;
+    }
+    double *out = mem == ESMM_MEM_HOST ? g->lam_v : lam;
+    if ((rc = rhs_vjp_core3(g, cons, J, x, xdot, mu, out))) return rc;
+    if (mem == ESMM_MEM_HOST) {
+        if ((rc = copy3(g, lam, g->lam_v, 8 * N, mem, false))) return rc;
+        CK3(cudaStreamSynchronize(g->st));
+        return check3(g);
+    }
+    return ESMM_OK;
+}
+
+int esmm3_adjoint_record(esmm3 *g, int nsteps, double dt)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    int rc;
+    if ((rc = adj_alloc3(g))) return rc;
+    size_t N = (size_t)g->g.N, d = sizeof(double);
+    g->ck_dt->clear();
+    g->ck_n = 0;
+    for (int n = 0; n < nsteps; ++n) {
+        if ((int)g->ck->size() <= n) {
+            double *b = nullptr;
+            CK3(cudaMalloc((void **)&b, 15 * N * d));   // cons, J, x, xdot
+            g->ck->push_back(b);
+        }
+        double *b = (*g->ck)[n];
+        CK3(cudaMemcpyAsync(b, g->cons, 8 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK3(cudaMemcpyAsync(b + 8 * N, g->J, N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK3(cudaMemcpyAsync(b + 9 * N, g->x, 3 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        if ((rc = rk_step_async3(g, dt))) return rc;
+        CK3(cudaMemcpyAsync(b + 12 * N, g->xdot, 3 * N * d, cudaMemcpyDeviceToDevice, g->st));
+        CK3(cudaMemcpyAsync(g->pin, g->dt_dev, d, cudaMemcpyDeviceToHost, g->st));
+        CK3(cudaStreamSynchronize(g->st));
+        g->ck_dt->push_back(g->pin[0]);
+        g->ck_n = n + 1;
+    }
+    return check3(g);
+}
+
+int esmm3_adjoint_steps(esmm3 *g, int *nsteps, double *dt)
+{
+    *nsteps = g->ck_n;
+    if (dt)
+        for (int n = 0; n < g->ck_n; ++n) dt[n] = (*g->ck_dt)[n];
+    return ESMM_OK;
+}
+
+int esmm3_adjoint_checkpoint(esmm3 *g, int step, int what, double *out, int mem)
+{
+    if (step < 0 || step >= g->ck_n) return ESMM_ERR_ARG;
+    size_t N = (size_t)g->g.N;
+    const double *b = (*g->ck)[step];
+    int rc;
+    switch (what) {
+    case ESMM_GET_CONS: rc = copy3(g, out, b, 8 * N, mem, false); break;
+    case ESMM_GET_J: rc = copy3(g, out, b + 8 * N, N, mem, false); break;
+    case ESMM_GET_X: rc = copy3(g, out, b + 9 * N, 3 * N, mem, false); break;
+    case ESMM_GET_XDOT: rc = copy3(g, out, b + 12 * N, 3 * N, mem, false); break;
+    default: return fail3(g, ESMM_ERR_ARG, "unknown field");
+    }
+    if (rc) return rc;
+    CK3(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+int esmm3_adjoint_replay(esmm3 *g, int nsteps)
+{
+    if (nsteps < 0 || nsteps > g->ck_n) return ESMM_ERR_ARG;
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    size_t N = (size_t)g->g.N;
+    for (int n = 0; n < nsteps; ++n) {
+        int rc = step_given3(g, (*g->ck)[n] + 12 * N, (*g->ck_dt)[n]);
+        if (rc) return rc;
+    }
+    CK3(cudaStreamSynchronize(g->st));
+    return check3(g);
+}
+
+// the three SSP-RK3 stages in reverse, per recorded step (as in 2D)
+int esmm3_adjoint_vjp(esmm3 *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem)
+{
+    if (g->ck_n < 1) return fail3(g, ESMM_ERR_STATE, "no recorded steps");
+    int rc;
+    if ((rc = adj_alloc3(g))) return rc;
+    size_t N = (size_t)g->g.N;
+    const long long n8 = 8 * (long long)N;
+    double *la = g->lam_a, *lb = g->lam_b, *lc = g->lam_c, *v = g->lam_v;
+    if ((rc = copy3(g, la, lam_final, 8 * N, mem, true))) return rc;
+    for (int n = g->ck_n - 1; n >= 0; --n) {
+        double *b = (*g->ck)[n];
+        double *c0 = b, *J0 = b + 8 * N, *x0 = b + 9 * N, *xd = b + 12 * N;
+        const double dt = (*g->ck_dt)[n];
+        if ((rc = set_dt3(g, dt))) return rc;
+        CK3(cudaMemcpyAsync(g->xdot, xd, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+        g->xdot_zero = 0;
+        // recompute the stage states (c1, J1, x1), (c2, J2, x2)
+        node3(g, c0, J0, x0, xd, nullptr, nullptr);
+        fluxes3(g);
+        update3(g, nullptr, nullptr, c0, J0, x0, c0, J0, x0, 0.0, 1.0, g->c1, g->J1, g->x1);
+        node3(g, g->c1, g->J1, g->x1, xd, nullptr, nullptr);
+        fluxes3(g);
+        update3(g, nullptr, nullptr, c0, J0, x0, g->c1, g->J1, g->x1, 0.75, 0.25, g->c2, g->J2, g->x2);
+        // stage 3: c3 = 1/3 c0 + 2/3 (c2 + dt L(c2))
+        if ((rc = rhs_vjp_core3(g, g->c2, g->J2, g->x2, xd, la, v))) return rc;
+        launch3_lincomb(n8, 2.0 / 3.0, la, 2.0 / 3.0 * dt, v, lb, g->st);    // lambda_c2
+        launch3_lincomb(n8, 1.0 / 3.0, la, 0.0, nullptr, lc, g->st);         // lambda_c0
+        // stage 2: c2 = 3/4 c0 + 1/4 (c1 + dt L(c1))
+        if ((rc = rhs_vjp_core3(g, g->c1, g->J1, g->x1, xd, lb, v))) return rc;
+        launch3_lincomb(n8, 0.25, lb, 0.25 * dt, v, la, g->st);              // lambda_c1
+        launch3_lincomb(n8, 1.0, lc, 0.75, lb, lc, g->st);
+        // stage 1: c1 = c0 + dt L(c0)
+        if ((rc = rhs_vjp_core3(g, c0, J0, x0, xd, la, v))) return rc;
+        launch3_lincomb(n8, 1.0, lc, 1.0, la, lc, g->st);
+        launch3_lincomb(n8, 1.0, lc, dt, v, la, g->st);                      // lambda of c^n
+        g->launches += 6;
+    }
+    CK3(cudaGetLastError());
+    if (lam_cons0 && (rc = copy3(g, lam_cons0, la, 8 * N, mem, false))) return rc;
+    if (lam_prim0) {
+        double *b0 = (*g->ck)[0];
+        launch3_prim_grad(g->g, g->gamma, b0, b0 + 8 * N, la, v, g->status, g->st);
+        if ((rc = copy3(g, lam_prim0, v, 8 * N, mem, false))) return rc;
+    }
+    CK3(cudaStreamSynchronize(g->st));
+    return check3(g);
 }

@@ -27,6 +27,13 @@ int esmm3_advance(esmm3 *g, int nsteps, double dt);
 int esmm3_totals(esmm3 *g, double out[3]);
 int esmm3_last_error(esmm3 *g, int *n_c2p_fail, char *msg, int len);
 long long esmm3_launches(const esmm3 *g);
+int esmm3_rhs_vjp(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot,
+                  const double *mu, double *lam, int mem);
+int esmm3_adjoint_record(esmm3 *g, int nsteps, double dt);
+int esmm3_adjoint_steps(esmm3 *g, int *nsteps, double *dt);
+int esmm3_adjoint_checkpoint(esmm3 *g, int step, int what, double *out, int mem);
+int esmm3_adjoint_replay(esmm3 *g, int nsteps);
+int esmm3_adjoint_vjp(esmm3 *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem);
 int esmm3_profile(esmm3 *g, int mask);
 int esmm3_profile_read(esmm3 *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
                        long long timed[ESMM_NKINDS]);

@@ -1374,7 +1374,10 @@ int esmm_tune(esmm_grid *g, int *block_sizes)
 int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
                  const double *mu, double *lam, int mem)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
+    if (g && g->dim == 3) {
+        if (!cons || !J || !x || !mu || !lam) return ESMM_ERR_ARG;
+        return esmm3_rhs_vjp(g->g3, cons, J, x, xdot, mu, lam, mem);
+    }
     if (!g || !cons || !J || !x || !mu || !lam || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->phys == ESMM_RMHD && g->prm.precision != ESMM_FP64)
         return fail(g, ESMM_ERR_ARG, "the RMHD adjoint is FP64");
@@ -1404,7 +1407,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
+    if (g && g->dim == 3) return nsteps < 0 ? ESMM_ERR_ARG : esmm3_adjoint_record(g->g3, nsteps, dt);
     if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->phys == ESMM_RMHD && g->prm.precision != ESMM_FP64)
         return fail(g, ESMM_ERR_ARG, "the RMHD adjoint is FP64");
@@ -1435,7 +1438,7 @@ int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 
 int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
+    if (g && g->dim == 3) return nsteps ? esmm3_adjoint_steps(g->g3, nsteps, dt) : ESMM_ERR_ARG;
     if (!g || !nsteps) return ESMM_ERR_ARG;
     *nsteps = g->ck_n;
     if (dt)
@@ -1445,7 +1448,7 @@ int esmm_adjoint_steps(esmm_grid *g, int *nsteps, double *dt)
 
 int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int mem)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
+    if (g && g->dim == 3) return out ? esmm3_adjoint_checkpoint(g->g3, step, what, out, mem) : ESMM_ERR_ARG;
     if (!g || !out || step < 0 || step >= g->ck_n) return ESMM_ERR_ARG;
     size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
     const double *b = (*g->ck)[step];
@@ -1464,7 +1467,7 @@ int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int m
 
 int esmm_adjoint_replay(esmm_grid *g, int nsteps)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
+    if (g && g->dim == 3) return esmm3_adjoint_replay(g->g3, nsteps);
     if (!g || nsteps < 0 || nsteps > g->ck_n || g->nprob != 1) return ESMM_ERR_ARG;
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     size_t N = (size_t)g->Ntot;
@@ -1478,7 +1481,8 @@ int esmm_adjoint_replay(esmm_grid *g, int nsteps)
 
 int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem)
 {
-    if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
+    if (g && g->dim == 3) return lam_final ? esmm3_adjoint_vjp(g->g3, lam_final, lam_cons0, lam_prim0, mem)
+                                           : ESMM_ERR_ARG;
     if (!g || !lam_final || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->ck_n < 1) return fail(g, ESMM_ERR_STATE, "no recorded steps");
     int rc;

@@ -439,6 +439,37 @@ class Grid3(Grid):
         self._check(lib().esmm_rhs(self.h, a[0][0], a[1][0], a[2][0], xd[0], o[0][0], o[1][0], mem))
         return dcons, dJ
 
+    def adjoint_checkpoint(self, step, what, out=None):
+        size = {GET_CONS: 8, GET_J: 1, GET_X: 3, GET_XDOT: 3}[what]
+        if out is None:
+            out = np.empty(self._shape(size))
+        po, mo = _ptr(out, size * self.N)
+        self._check(lib().esmm_adjoint_checkpoint(self.h, int(step), what, po, mo))
+        return out
+
+    def adjoint_vjp(self, lam_final, lam_cons0=None, lam_prim0=None):
+        """dF/d(cons^0) and dF/d(prim^0) from lam_final = dF/d(cons^final)."""
+        if not _is_torch(lam_final):
+            lam_cons0 = np.empty(self._shape(8)) if lam_cons0 is None else lam_cons0
+            lam_prim0 = np.empty(self._shape(8)) if lam_prim0 is None else lam_prim0
+        a = _ptr(lam_final, 8 * self.N)
+        c = _ptr(lam_cons0, 8 * self.N)
+        p_ = _ptr(lam_prim0, 8 * self.N)
+        mem = _mem(a, *([c] if lam_cons0 is not None else []), *([p_] if lam_prim0 is not None else []))
+        self._check(lib().esmm_adjoint_vjp(self.h, a[0], c[0], p_[0], mem))
+        return lam_cons0, lam_prim0
+
+    def rhs_vjp(self, cons, J, x, xdot, mu, lam=None):
+        """(d rhs / d cons)^T mu at (cons, J, x, xdot) with J, x, xdot fixed."""
+        if lam is None:
+            lam = np.empty(self._shape(8))
+        a = [_ptr(cons, 8 * self.N), _ptr(J, self.N), _ptr(x, 3 * self.N), _ptr(mu, 8 * self.N),
+             _ptr(lam, 8 * self.N)]
+        xd = _ptr(xdot, 3 * self.N)
+        mem = _mem(*a, *([xd] if xdot is not None else []))
+        self._check(lib().esmm_rhs_vjp(self.h, a[0][0], a[1][0], a[2][0], xd[0], a[3][0], a[4][0], mem))
+        return lam
+
     def mesh_redistribute(self, dt=0.0):
         """(xdot, dtau, dt) as :meth:`Grid.mesh_redistribute`, in 3D."""
         xdot = np.empty(self._shape(3))

@@ -165,7 +165,7 @@ def test_rotor_512_full_size_rhs():
 
 
 def test_rmhd_rejects_unsupported_forms():
-    # the RMHD adjoint is FP64 and 2D; batches are RHD
+    # the RMHD adjoint is FP64; 3D grids compute in FP64 only
     x = wl.uniform_mesh(16, 16, (-0.5, -0.5), (0.5, 0.5), (False, False))
     with esmm.Grid((16, 16), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), phys=esmm.RMHD, precision=esmm.MIXED) as g:
         g.state_set(wl.rotor(x), x)
@@ -175,4 +175,4 @@ def test_rmhd_rejects_unsupported_forms():
     with esmm.Grid3((8, 8, 8), (-0.5,) * 3, (0.5,) * 3, bc=(1, 1, 1)) as g:
         g.state_set(prim3, x3)
         with pytest.raises(esmm.EsmmError):
-            g.adjoint_record(1)
+            g.set_params(precision=esmm.MIXED)
