@@ -112,8 +112,9 @@ void oref_flux(double gamma, const double *w, int dir, double *F)
  * f((Gamma-1)E) < 0 for every admissible state, f strictly decreasing).
  * Stops when a step changes p by at most 1e-15 (E + p): f is evaluated from
  * E + p, so p is resolved only to that level (p << E in cold gas); an
- * iterate at which f is exactly 0 is a root and is kept (the open bracket
- * would reject its zero step and bisect away from it).
+ * iterate at which |f| <= 2e-15 (E + p), f's own rounding level, is taken
+ * as the root (where df/dp is small, steps at that level exceed the first
+ * bound, and the open bracket would reject them and bisect).
  * Returns 0 on success, -1 for a non-admissible state, -2 without
  * convergence.                                                             */
 int oref_cons2prim(double gamma, const double *U, double *w, int *iters)
@@ -132,6 +133,10 @@ int oref_cons2prim(double gamma, const double *U, double *w, int *iters)
         double v2 = S * S / (Ep * Ep);
         double f = gg * (Ep * iW2 - D * iW) - p;
         double df = gg * (1.0 + v2 - D * v2 / (iW * Ep)) - 1.0;
+        if (fabs(f) <= 2.0e-15 * (E + p)) { /* residual at rounding level */
+            ok = 1;
+            break;
+        }
         double pn = p;                      /* f = 0: p is a root */
         if (f != 0.0) {
             if (f > 0.0) lo = p; else hi = p;

@@ -71,8 +71,9 @@ void oref_mhd_flux(double gamma, const double *w, int dir, double *F)
  *   f(Z) = Z - p(Z) + |B|^2 (1 + |v|^2)/2 - S^2/(2 Z^2) - E.
  * f > 0 at Z = Gamma E (there Z - p >= Z/Gamma = E), and a trial Z with
  * |v|^2(Z) >= 1 lies below the root, so [0, Gamma E] brackets it.  Stops when
- * a step changes Z by at most 1e-15 (E + Z), or at an iterate where f is
- * exactly 0 (the open bracket would reject that root's zero step).  Returns 0, -1 (non-admissible
+ * a step changes Z by at most 1e-15 (E + Z), or at an iterate where
+ * |f| <= 2e-15 (E + Z), f's rounding level (the open bracket would reject
+ * that root's tiny steps and bisect).  Returns 0, -1 (non-admissible
  * input or result) or -2 (no convergence).                                 */
 int oref_mhd_cons2prim(double gamma, const double *U, double *w, int *iters)
 {
@@ -103,6 +104,10 @@ int oref_mhd_cons2prim(double gamma, const double *U, double *w, int *iters)
             double dv2 = dN / (ZB * ZB) - 2.0 * N / (ZB * ZB * ZB);
             double dp = g * (iW2 - Z * dv2 + 0.5 * D * dv2 / iW);
             double df = 1.0 - dp + 0.5 * B2 * dv2 + S2 / (Z * Z * Z);
+            if (fabs(f) <= 2.0e-15 * (E + Z)) { /* residual at rounding level */
+                ok = 1;
+                break;
+            }
             Zn = Z;                         /* f = 0: Z is a root */
             if (f != 0.0) {
                 if (f < 0.0) lo = Z; else hi = Z;

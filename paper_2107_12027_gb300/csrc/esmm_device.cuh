@@ -119,7 +119,8 @@ __device__ __forceinline__ double mesh_at(const Geom &g, const double *a, int i,
 //   f(p) = (G-1)/G ((E+p)(1-v^2) - D sqrt(1-v^2)) - p,  v = |m|/(E+p),
 // safeguarded by bisection on [0, (G-1)E], stopping when a step moves p by at
 // most 1e-15 (E + p), the resolution of E + p from which f is evaluated, or
-// at an iterate where f is exactly 0 (the open bracket would reject it);
+// when |f| <= 2e-15 (E + p), f's own rounding level (where df/dp is small,
+// steps at that level exceed the first bound and the loop would bisect);
 // p0 is a warm start (ignored when outside the bracket).  Returns 0, 1 for a
 // non-admissible state, 2 when the iteration cap is hit.
 __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double my, double E,
@@ -142,6 +143,7 @@ __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double
         double v2 = S2 * r * r;
         double f = gg * (Ep * iW2 - D * iW) - pc;
         double df = gg * (1.0 + v2 - D * v2 * r * rs) - 1.0;
+        if (fabs(f) <= 2.0e-15 * (E + pc)) { ok = 1; break; }   // residual at rounding level
         double pn = pc;                              // f = 0: pc is a root
         if (f != 0.0) {
             if (f > 0.0) lo = pc; else hi = pc;

@@ -28,8 +28,8 @@ constexpr int NFM = 10;                          // interface values per directi
 //   p = (Gamma-1)/Gamma (Z/W^2 - D/W),
 //   f(Z) = Z - p + |B|^2 (1 + |v|^2)/2 - S^2/(2 Z^2) - E,
 // a trial Z with |v|^2 >= 1 lying below the root.  Stops when a step moves Z
-// by at most 1e-15 (E + Z), or where f is exactly 0 (a root, which the open
-// bracket would otherwise reject).  Z0: warm start (ignored outside the bracket).
+// by at most 1e-15 (E + Z), or where |f| <= 2e-15 (E + Z), f's rounding
+// level (a root, whose tiny steps the open bracket would otherwise reject).  Z0: warm start (ignored outside the bracket).
 // Returns 0, 1 (non-admissible) or 2 (iteration cap).
 __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], double Z0, double w[8], double &Zout)
 {
@@ -64,6 +64,7 @@ __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], doub
             double dv2 = dN * iZB * iZB - 2.0 * N * iZB * iZB * iZB;
             double dp = g * (iW2 - Z * dv2 + 0.5 * D * dv2 / iW);
             double df = 1.0 - dp + 0.5 * B2 * dv2 + S2 * iZ * iZ * iZ;
+            if (fabs(f) <= 2.0e-15 * (E + Z)) { ok = 1; break; }   // residual at rounding level
             Zn = Z;                          // f = 0: Z is a root
             if (f != 0.0) {
                 if (f < 0.0) lo = Z; else hi = Z;
