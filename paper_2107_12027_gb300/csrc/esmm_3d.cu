@@ -23,9 +23,64 @@ namespace esmm {
 namespace d3 {
 
 // ---------------------------------------------------------------------------
+// The metrics of eq. SCLCoeff in two passes.  k3_dx stores, on the grid
+// extended by HE = GH + PMAX nodes per side, the boundary-mapped mesh x[3]
+// and its first differences delta_d[x_c] (at 3 + 3 d + c); k3_node then forms
+// M[k][j] = delta_{k2}[delta_{k1}[x_{j1}] x_{j2}] - delta_{k1}[delta_{k2}[x_{j1}] x_{j2}]
+// from those values at +-n along k2 and k1 (eq. SCLCoeff's nested central
+// differences, evaluated once per difference instead of once per use).
+constexpr int HE = GH + PMAX;
+constexpr int NXE = 12;
+
+__host__ __device__ __forceinline__ long long eidx3(const Geom3 &g, int i, int j, int k)
+{
+    return ((long long)(k + HE) * (g.n[1] + 2 * HE) + (j + HE)) * (g.n[0] + 2 * HE) + (i + HE);
+}
+
+__host__ __device__ __forceinline__ long long ext_count3(const Geom3 &g)
+{
+    return (long long)(g.n[0] + 2 * HE) * (g.n[1] + 2 * HE) * (g.n[2] + 2 * HE);
+}
+
+template <int P>
+__global__ void k3_dx(Geom3 g, const double *__restrict__ x, double *__restrict__ xe)
+{
+    const long long E = ext_count3(g);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E) return;
+    const int e0 = g.n[0] + 2 * HE, e1 = g.n[1] + 2 * HE;
+    const int I = (int)(t % e0) - HE, Jn = (int)((t / e0) % e1) - HE, K = (int)(t / ((long long)e0 * e1)) - HE;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xe[c * E + t] = mesh3_at(g, x, c, I, Jn, K, 1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xe[(3 + 3 * d + c) * E + t] = delta_x3<P>(g, x, c, I, Jn, K, d);
+}
+
+// nested3 from the stored differences
+template <int P>
+__device__ __forceinline__ double nested_e3(const Geom3 &g, const double *__restrict__ xe, long long E, int d_out,
+                                            int d_in, int ja, int jb, int i, int j, int k)
+{
+    double s = 0.0;
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        int a0, a1, a2, b0, b1, b2;
+        step3(i, j, k, d_out, n, a0, a1, a2);
+        step3(i, j, k, d_out, -n, b0, b1, b2);
+        const long long ea = eidx3(g, a0, a1, a2), eb = eidx3(g, b0, b1, b2);
+        const double *Dd = xe + (3 + 3 * d_in + ja) * E, *X = xe + jb * E;
+        double fa = Dd[ea] * X[ea];
+        double fb = Dd[eb] * X[eb];
+        s += 0.5 * alpha3<P>(n) * (fa - fb);
+    }
+    return s;
+}
+
 template <int P>
 __global__ void k3_node(Geom3 g, double gam, const double *__restrict__ cons, const double *__restrict__ J,
-                        const double *__restrict__ x, const double *__restrict__ xdot,
+                        const double *__restrict__ xe, const double *__restrict__ xdot,
                         const double *__restrict__ zg_in, double *__restrict__ zg_out, double *__restrict__ q,
                         int *__restrict__ status)
 {
@@ -60,7 +115,19 @@ __global__ void k3_node(Geom3 g, double gam, const double *__restrict__ cons, co
     q[F_B1 * g.P + t] = w[6];
     q[F_B2 * g.P + t] = w[7];
     double M[3][3];
-    metrics3<P>(g, x, I, Jn, K, M);
+    {
+        const long long E = ext_count3(g);
+#pragma unroll 1
+        for (int kk = 0; kk < 3; ++kk) {
+            const int k1 = (kk + 1) % 3, k2 = (kk + 2) % 3;
+#pragma unroll 1
+            for (int jj = 0; jj < 3; ++jj) {
+                const int j1 = (jj + 1) % 3, j2 = (jj + 2) % 3;
+                M[kk][jj] = nested_e3<P>(g, xe, E, k2, k1, j1, j2, I, Jn, K) -
+                            nested_e3<P>(g, xe, E, k1, k2, j1, j2, I, Jn, K);
+            }
+        }
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -417,6 +484,7 @@ struct esmm3 {
     std::vector<double> *ck_dt;
     int ck_n;
     double *lam_a, *lam_b, *lam_c, *lam_v, *lamq;
+    double *xe;   // the mesh and its first differences on the extended grid (k3_dx)
 };
 
 namespace {
@@ -485,11 +553,19 @@ Phys phys3(const esmm3 *g)
 void node3(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot, const double *zi,
            double *zo)
 {
-    unsigned nb = nb3(g->g.P);
-    Prof3 pr_(g, ESMM_KIND_NODE);
-    if (g->p == 1) k3_node<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
-    else if (g->p == 2) k3_node<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
-    else k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, x, xdot, zi, zo, g->q, g->status);
+    unsigned nb = nb3(g->g.P), nbe = nb3(ext_count3(g->g));
+    Prof3 pr_(g, ESMM_KIND_NODE, 2);
+    double *xe = g->xe;
+    if (g->p == 1) {
+        k3_dx<1><<<nbe, BS3, 0, g->st>>>(g->g, x, xe);
+        k3_node<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status);
+    } else if (g->p == 2) {
+        k3_dx<2><<<nbe, BS3, 0, g->st>>>(g->g, x, xe);
+        k3_node<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status);
+    } else {
+        k3_dx<3><<<nbe, BS3, 0, g->st>>>(g->g, x, xe);
+        k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status);
+    }
 }
 
 void fluxes3(esmm3 *g)
@@ -592,7 +668,7 @@ void free3(esmm3 *g)
     double **b[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2, &g->q,
                     &g->zg[0], &g->zg[1], &g->zg[2], &g->iflux, &g->out_dc, &g->out_dJ, &g->in_cons, &g->in_J,
                     &g->in_x, &g->in_xdot, &g->grad, &g->om, &g->om2, &g->X, &g->Xn, &g->dt_dev, &g->t_dev,
-                    &g->partials, &g->tot, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v, &g->lamq};
+                    &g->partials, &g->tot, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v, &g->lamq, &g->xe};
     for (double **p : b)
         if (*p) { cudaFree(*p); *p = nullptr; }
     if (g->ck) {
@@ -710,7 +786,7 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
         {&g->zg[0], N}, {&g->zg[1], N}, {&g->zg[2], N}, {&g->iflux, (size_t)3 * NF3 * P}, {&g->out_dc, 8 * N},
         {&g->out_dJ, N}, {&g->in_cons, 8 * N}, {&g->in_J, N}, {&g->in_x, 3 * N}, {&g->in_xdot, 3 * N},
         {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->X, 3 * N}, {&g->Xn, 3 * N}, {&g->dt_dev, 1},
-        {&g->t_dev, 1}, {&g->partials, 3 * nb}, {&g->tot, 3}};
+        {&g->t_dev, 1}, {&g->partials, 3 * nb}, {&g->tot, 3}, {&g->xe, (size_t)NXE * ext_count3(g->g)}};
     bool ok = true;
     for (auto &a : al) ok = ok && cudaMalloc((void **)a.p, a.n * d) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&g->red, NR3 * sizeof(unsigned long long)) == cudaSuccess &&

@@ -112,38 +112,6 @@ __device__ __forceinline__ double delta_x3(const Geom3 &g, const double *x, int 
     return s;
 }
 
-// eq. SCLCoeff: M[k][j] = delta_{k2}[delta_{k1}[x_{j1}] x_{j2}] - delta_{k1}[delta_{k2}[x_{j1}] x_{j2}]
-template <int P>
-__device__ __forceinline__ double nested3(const Geom3 &g, const double *x, int d_out, int d_in, int ja, int jb, int i,
-                                          int j, int k)
-{
-    double s = 0.0;
-#pragma unroll
-    for (int n = 1; n <= P; ++n) {
-        int a0, a1, a2, b0, b1, b2;
-        step3(i, j, k, d_out, n, a0, a1, a2);
-        step3(i, j, k, d_out, -n, b0, b1, b2);
-        double fa = delta_x3<P>(g, x, ja, a0, a1, a2, d_in) * mesh3_at(g, x, jb, a0, a1, a2, 1);
-        double fb = delta_x3<P>(g, x, ja, b0, b1, b2, d_in) * mesh3_at(g, x, jb, b0, b1, b2, 1);
-        s += 0.5 * alpha3<P>(n) * (fa - fb);
-    }
-    return s;
-}
-
-template <int P>
-__device__ void metrics3(const Geom3 &g, const double *x, int i, int j, int k, double M[3][3])
-{
-#pragma unroll 1
-    for (int kk = 0; kk < 3; ++kk) {
-        int k1 = (kk + 1) % 3, k2 = (kk + 2) % 3;
-#pragma unroll 1
-        for (int jj = 0; jj < 3; ++jj) {
-            int j1 = (jj + 1) % 3, j2 = (jj + 2) % 3;
-            M[kk][jj] = nested3<P>(g, x, k2, k1, j1, j2, i, j, k) - nested3<P>(g, x, k1, k2, j1, j2, i, j, k);
-        }
-    }
-}
-
 // Sec. 4 rotation for the unit normal n (rows n, t1, t2; theta = 0 when the
 // x_1-x_2 part of n is below 1e-12), then turned about n so that t1 lies
 // along the tangential B of the state w (along the tangential v when

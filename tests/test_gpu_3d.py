@@ -194,7 +194,8 @@ def test_blast_128_full_size():
 
 
 def test_profile_counts_3d():
-    # one step: 3 node passes, 9 interface launches (3 stages x 3 directions)
+    # one step: 3 node passes (2 launches each: the mesh differences, then the
+    # node values and metrics), 9 interface launches (3 stages x 3 directions)
     # and 3 updates; the interface launches are timed when asked for
     m = 12
     x, prim = wl.blast3_config(m)
@@ -203,6 +204,6 @@ def test_profile_counts_3d():
         g.profile(1 << esmm.KIND_IFACE)
         g.rk_step()
         prof = g.profile_read()
-    assert prof["node"][1] == 3 and prof["iface"][1] == 9 and prof["update"][1] == 3
+    assert prof["node"][1] == 6 and prof["iface"][1] == 9 and prof["update"][1] == 3
     assert prof["iface"][2] == 9 and prof["iface"][0] > 0.0
     assert prof["node"][2] == 0
