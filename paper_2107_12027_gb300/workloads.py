@@ -312,3 +312,53 @@ def blast3_config(n=128):
     (the 128^3 adjoint workload)."""
     x = uniform_mesh3((n, n, n), (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), (False, False, False))
     return x, blast3(x)
+
+
+# ---- the 2D RMHD isentropic vortex (Sec. 6, 2D RMHD vortex example) --------
+def vortex_mesh(n, t=0.0, R=5.0, amp=0.2):
+    """The example's prescribed moving mesh on the periodic box [-R, R]^2 (n
+    distinct nodes per direction, spacing 2R/n): x_1 = x0_1 + amp cos(pi t/4)
+    sin(3 pi x0_2 / R), x_2 = x0_2 + amp cos(pi t/4) sin(3 pi x0_1 / R)."""
+    x0 = uniform_mesh(n, n, (-R, -R), (R, R))
+    s = amp * np.cos(np.pi * t / 4.0)
+    return np.ascontiguousarray(np.stack([x0[0] + s * np.sin(3 * np.pi * x0[1] / R),
+                                          x0[1] + s * np.sin(3 * np.pi * x0[0] / R)]))
+
+
+def vortex_mesh_velocity(n, t=0.0, R=5.0, amp=0.2):
+    """d/dt of vortex_mesh at fixed computational coordinates."""
+    x0 = uniform_mesh(n, n, (-R, -R), (R, R))
+    s = -amp * (np.pi / 4.0) * np.sin(np.pi * t / 4.0)
+    return np.ascontiguousarray(np.stack([s * np.sin(3 * np.pi * x0[1] / R), s * np.sin(3 * np.pi * x0[0] / R)]))
+
+
+def rmhd_vortex(x, t=0.0, R=5.0, gamma=5.0 / 3.0, sigma=0.2, B0=0.05):
+    """The example's analytic RMHD vortex (primitives [8][...] at the points
+    x [2][...] and time t): a rotated, boosted isentropic vortex moving with
+    velocity (-0.5, -0.5) on the periodic box [-R, R]^2, Gamma = 5/3.
+
+    The magnetic field of the vortex frame is B0 exp((1 - r^2)/2)(-x2, x1):
+    radial balance of the rotating equilibrium, d(p + B^2/2)/dr = (rho h W^2
+    v^2 - B^2)/r, gives the printed rotation rate f with the printed kappa =
+    2 Gamma sigma rho + (Gamma-1) B0^2 (2 - r^2) for that field (with
+    exp(1 - r^2), as the text reads, kappa's field term would be
+    2 (Gamma-1) B0^2 exp(1 - r^2)(1 - r^2) instead)."""
+    s2 = np.sqrt(2.0)
+    xh = [np.mod(x[k] + t / 2.0 - 1.0 + R, 2.0 * R) - R for k in range(2)]
+    xt = [xh[k] + (s2 - 1.0) * (xh[0] + xh[1]) / 2.0 for k in range(2)]
+    r2 = xt[0] ** 2 + xt[1] ** 2
+    e = np.exp(1.0 - r2)
+    rho = (1.0 - sigma * e) ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    kappa = 2.0 * gamma * sigma * rho + (gamma - 1.0) * B0 ** 2 * (2.0 - r2)
+    f = np.sqrt(kappa * e / (kappa * r2 * e + (gamma - 1.0) * rho + gamma * p))
+    vt1, vt2 = -xt[1] * f, xt[0] * f
+    den = 4.0 - 2.0 * (vt1 + vt2)
+    v1 = ((2.0 + s2) * vt1 + (2.0 - s2) * vt2 - 2.0) / den
+    v2 = ((2.0 + s2) * vt2 + (2.0 - s2) * vt1 - 2.0) / den
+    eb = np.exp(0.5 * (1.0 - r2))       # see the docstring
+    Bt1, Bt2 = -B0 * eb * xt[1], B0 * eb * xt[0]
+    B1 = 0.5 * ((s2 + 1.0) * Bt1 - (s2 - 1.0) * Bt2)
+    B2 = 0.5 * ((s2 + 1.0) * Bt2 - (s2 - 1.0) * Bt1)
+    z = np.zeros_like(rho)
+    return np.ascontiguousarray(np.stack([rho, v1, v2, z, p, B1, B2, z]))
