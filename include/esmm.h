@@ -84,6 +84,11 @@ typedef struct {
     int mu;            /* Jacobi iterations of the mesh equations     [10]   */
     int move_mesh;     /* 0: static mesh (uniform-mesh scheme)        [1]    */
     int precision;     /* ESMM_FP64 or ESMM_MIXED                     [FP64] */
+    double alpha_lap;  /* strength of a Laplacian term added to the
+                          monitor: omega = sqrt(1 + alpha |grad sigma|/max
+                          + alpha_lap |lap sigma|/max), the monitor of the
+                          vortex examples of Sec. 6 (there sigma = rho,
+                          alpha = 20, alpha_lap = 10); 0: eq. monitor   [0]   */
 } esmm_params;
 
 /* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim 2, phys ESMM_RHD or
@@ -157,6 +162,15 @@ int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, 
  * synchronises and writes the step used.  A recovery failure is reported by
  * esmm_last_error / the next synchronising call. */
 int esmm_rk_step(esmm_grid *g, double dt, double *dt_used);
+/* One time step with a prescribed mesh motion (the given-mesh runs of the
+ * vortex examples of Sec. 6): the caller's mesh velocity xdot [d][N] (host or
+ * device per mem, d = 2 or 3) is held over the step, the mesh of stage s is
+ * x^n + c_s dt xdot with the SSP-RK3 weights, and J follows eq. VCL, so the
+ * GCL holds for any xdot.  dt > 0 is the caller's (no CFL check); the params'
+ * move_mesh is ignored.  Synchronises; ESMM_ERR_ARG for dt <= 0, a NULL xdot
+ * or a batch, ESMM_ERR_STATE without a state, ESMM_ERR_C2P if a recovery
+ * failed. */
+int esmm_rk_step_given(esmm_grid *g, const double *xdot, double dt, int mem);
 /* nsteps asynchronous esmm_rk_step calls (dt as there). */
 int esmm_advance(esmm_grid *g, int nsteps, double dt);
 

@@ -47,6 +47,7 @@ class Cfg(ctypes.Structure):
         ("mu", ctypes.c_int),
         ("move_mesh", ctypes.c_int),
         ("phys", ctypes.c_int),
+        ("alpha_lap", ctypes.c_double),
     ]
 
 
@@ -64,6 +65,7 @@ class Cfg3(ctypes.Structure):
         ("n_filter", ctypes.c_int),
         ("mu", ctypes.c_int),
         ("move_mesh", ctypes.c_int),
+        ("alpha_lap", ctypes.c_double),
     ]
 
 
@@ -107,6 +109,7 @@ def lib():
                 "oref_metrics": (None, [c, d, d, d]),
                 "oref_rhs": (ctypes.c_int, [c, d, d, d, d, d, d]),
                 "oref_cfl_dt": (ctypes.c_int, [c, d, d, d, d]),
+                "oref_monitor": (ctypes.c_int, [c, d, d, d]),
                 "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d, d]),
                 "oref_rk_step": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d]),
                 "oref_rk_step_given": (ctypes.c_int, [c, d, d, d, d, ctypes.c_double]),
@@ -127,6 +130,7 @@ def lib():
                 "oref3_state_prim": (ctypes.c_int, [c3, d, d, d]),
                 "oref3_rhs": (ctypes.c_int, [c3, d, d, d, d, d, d]),
                 "oref3_cfl_dt": (ctypes.c_int, [c3, d, d, d, d]),
+                "oref3_monitor": (ctypes.c_int, [c3, d, d, d]),
                 "oref3_mesh": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d, d, d]),
                 "oref3_rk_step": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d]),
                 "oref3_rk_step_given": (ctypes.c_int, [c3, d, d, d, d, ctypes.c_double]),
@@ -156,14 +160,14 @@ def _vec(a, n=None):
 
 def make_cfg(nx, ny, bc=(PERIODIC, PERIODIC), period=(1.0, 1.0), gamma=5.0 / 3.0,
              p=2, w=5, weno_eps=1e-6, cfl=0.4, monitor=MONITOR_LNRHO, alpha=20.0,
-             n_filter=4, mu=10, move_mesh=1, phys=RHD) -> Cfg:
+             n_filter=4, mu=10, move_mesh=1, phys=RHD, alpha_lap=0.0) -> Cfg:
     c = Cfg()
     c.nx, c.ny = nx, ny
     c.bc[0], c.bc[1] = bc
     c.period[0], c.period[1] = period
     c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
     c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
-    c.phys = phys
+    c.phys, c.alpha_lap = phys, alpha_lap
     return c
 
 
@@ -291,6 +295,17 @@ def cfl_dt(cfg, cons, J, x):
     return dt[0]
 
 
+def monitor(cfg, cons, J):
+    """Sec. 5 monitor omega [ny][nx] before the low-pass filter (with the
+    Laplacian term of the vortex example when cfg.alpha_lap > 0)."""
+    N = cfg.nx * cfg.ny
+    om = np.zeros(N)
+    st = lib().oref_monitor(ctypes.byref(cfg), _p(_vec(cons, nvar(cfg) * N)), _p(_vec(J, N)), _p(om))
+    if st != 0:
+        raise RuntimeError("oracle monitor: cons2prim failed")
+    return om.reshape(cfg.ny, cfg.nx)
+
+
 def mesh(cfg, cons, J, x, dt=0.0):
     """Mesh velocity, limiter value and step: (xdot, dtau, dt).  dt <= 0 selects
     the CFL step with the mesh motion included."""
@@ -403,7 +418,7 @@ def mhd_eigen(gamma, w_rot):
 # ---- 3D RMHD grid functions --------------------------------------------------
 def make_cfg3(nx, ny, nz, bc=(PERIODIC, PERIODIC, PERIODIC), period=(1.0, 1.0, 1.0), gamma=4.0 / 3.0,
               p=2, w=5, weno_eps=1e-6, cfl=0.3, monitor=MONITOR_LNRHO, alpha=800.0, n_filter=4, mu=10,
-              move_mesh=1) -> Cfg3:
+              move_mesh=1, alpha_lap=0.0) -> Cfg3:
     c = Cfg3()
     c.nx, c.ny, c.nz = nx, ny, nz
     for k in range(3):
@@ -411,6 +426,7 @@ def make_cfg3(nx, ny, nz, bc=(PERIODIC, PERIODIC, PERIODIC), period=(1.0, 1.0, 1
         c.period[k] = period[k]
     c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
     c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
+    c.alpha_lap = alpha_lap
     return c
 
 
@@ -458,6 +474,16 @@ def cfl_dt3(cfg, cons, J, x):
     if st != 0:
         raise RuntimeError("oracle cfl3: cons2prim failed")
     return dt[0]
+
+
+def monitor3(cfg, cons, J):
+    """:func:`monitor` in 3D ([nz][ny][nx])."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    om = np.zeros(N)
+    st = lib().oref3_monitor(ctypes.byref(cfg), _p(_vec(cons, 8 * N)), _p(_vec(J, N)), _p(om))
+    if st != 0:
+        raise RuntimeError("oracle monitor3: cons2prim failed")
+    return om.reshape(cfg.nz, cfg.ny, cfg.nx)
 
 
 def mesh3(cfg, cons, J, x, dt=0.0):

@@ -902,6 +902,40 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
  * so that by the triangle inequality dt sum_k max_i rho_{k,i}(xdot) <= CFL
  * holds with xdot = d/dt.  A given dt > 0 is used as is (Delta tau capped
  * the same way).  *dt_out receives the step.                                */
+int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double *om)
+{
+    int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
+    double *sig = (double *)malloc(sizeof(double) * N);
+    double *lap = (double *)malloc(sizeof(double) * N);
+    for (int id = 0; id < N; ++id) {
+        double w[NVMAX];
+        if (node_prim(c, cons, J, id, w) != 0) status = -1;
+        sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
+    }
+    double gmax = 0.0, lmax = 0.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double e = sig[data_index(c, i + 1, j)], wv = sig[data_index(c, i - 1, j)];
+            double n = sig[data_index(c, i, j + 1)], s = sig[data_index(c, i, j - 1)];
+            double gx = 0.5 * (e - wv), gy = 0.5 * (n - s);
+            double g = sqrt(gx * gx + gy * gy);
+            double l = fabs(e + wv + n + s - 4.0 * sig[j * nx + i]);
+            om[j * nx + i] = g;
+            lap[j * nx + i] = l;
+            if (g > gmax) gmax = g;
+            if (l > lmax) lmax = l;
+        }
+    for (int id = 0; id < N; ++id) {
+        double a = 1.0;
+        if (gmax > 0.0) a += c->alpha * om[id] / gmax;
+        if (lmax > 0.0) a += c->alpha_lap * lap[id] / lmax;
+        om[id] = sqrt(a);
+    }
+    free(sig);
+    free(lap);
+    return status;
+}
+
 int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
               const double *x, double dt, double *xdot, double *dtau, double *dt_out)
 {
@@ -913,27 +947,11 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
         if (dt_out) *dt_out = dt;
         return status;
     }
-    double *sig = (double *)malloc(sizeof(double) * N);
     double *om = (double *)malloc(sizeof(double) * N);
     double *om2 = (double *)malloc(sizeof(double) * N);
     double *X = (double *)malloc(sizeof(double) * 2 * N);
     double *Xn = (double *)malloc(sizeof(double) * 2 * N);
-    for (int id = 0; id < N; ++id) {
-        double w[NVMAX];
-        if (node_prim(c, cons, J, id, w) != 0) status = -1;
-        sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
-    }
-    double gmax = 0.0;
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            double gx = 0.5 * (sig[data_index(c, i + 1, j)] - sig[data_index(c, i - 1, j)]);
-            double gy = 0.5 * (sig[data_index(c, i, j + 1)] - sig[data_index(c, i, j - 1)]);
-            double g = sqrt(gx * gx + gy * gy);
-            om[j * nx + i] = g;
-            if (g > gmax) gmax = g;
-        }
-    for (int id = 0; id < N; ++id)
-        om[id] = (gmax > 0.0) ? sqrt(1.0 + c->alpha * om[id] / gmax) : 1.0;
+    status |= oref_monitor(c, cons, J, om);
     for (int f = 0; f < c->n_filter; ++f) {
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -1013,7 +1031,6 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
     for (int a = 0; a < 2 * N; ++a) xdot[a] = tau * (X[a] - x[a]) / dt;
     if (dtau) *dtau = tau;
     if (dt_out) *dt_out = dt;
-    free(sig);
     free(om);
     free(om2);
     free(X);

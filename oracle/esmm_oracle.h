@@ -45,6 +45,8 @@ typedef struct {
     int mu;               /* Jacobi iterations per redistribution             */
     int move_mesh;        /* 0: static mesh (xdot = 0)                        */
     int phys;             /* OREF_RHD (4 unknowns) or OREF_RMHD (8 unknowns)  */
+    double alpha_lap;     /* strength of the monitor's Laplacian term (the
+                             vortex examples of Sec. 6; 0: eq. monitor)     */
 } oref_cfg;
 
 /* Sec. 3.2, constraint eq. HOCoeff: alpha_{p,1..p}. */
@@ -87,6 +89,12 @@ int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
 /* CFL time step, eq. cfl, with the static-mesh spectral radius. */
 int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
                 const double *x, double *dt);
+
+/* Sec. 5 monitor, before the low-pass filter: om[N] = sqrt(1 + alpha
+ * |grad_xi sigma| / max |grad_xi sigma| + alpha_lap |lap_xi sigma| /
+ * max |lap_xi sigma|) with central differences in the node indices; a term
+ * whose maximum is 0 is left out (alpha_lap = 0 gives eq. monitor). */
+int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double *om);
 
 /* Sec. 5 mesh redistribution and the step: xdot from the state at t^n; dt > 0
  * is used as given, dt <= 0 selects the CFL step with the mesh motion
@@ -150,6 +158,7 @@ typedef struct {
     int n_filter;
     int mu;
     int move_mesh;
+    double alpha_lap;
 } oref3_cfg;
 
 /* eq. SCLCoeff (nested CMM) and J0 = det(delta_k[x_j]) */
@@ -159,6 +168,7 @@ int oref3_state_prim(const oref3_cfg *c, const double *cons, const double *J, do
 int oref3_rhs(const oref3_cfg *c, const double *cons, const double *J, const double *x,
               const double *xdot, double *dcons, double *dJ);
 int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const double *x, double *dt);
+int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, double *om);
 int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
                double *xdot, double *dtau, double *dt_out);
 int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used);

@@ -498,6 +498,46 @@ int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const 
  * limiter over the three directions, xdot = Delta tau (x^[mu] - x^n)/dt.
  * Readings as in 2D (central |grad sigma| in index space, fixed outflow
  * boundary nodes, "(x_1)" read as x_k).                                     */
+/* Sec. 5 monitor (and the Laplacian term of the 3D vortex example), before
+ * the low-pass filter; the 3D form of oref_monitor. */
+int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, double *om)
+{
+    long N = (long)c->nx * c->ny * c->nz;
+    int status = 0;
+    double *sig = (double *)malloc(sizeof(double) * N);
+    double *lap = (double *)malloc(sizeof(double) * N);
+    for (long id = 0; id < N; ++id) {
+        double w[8];
+        if (node_prim3(c, cons, J, id, w) != 0) status = -1;
+        sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
+    }
+    double gmax = 0.0, lmax = 0.0;
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                long id = ((long)k * c->ny + j) * c->nx + i;
+                double xp = sig[data_index3(c, i + 1, j, k)], xm = sig[data_index3(c, i - 1, j, k)];
+                double yp = sig[data_index3(c, i, j + 1, k)], ym = sig[data_index3(c, i, j - 1, k)];
+                double zp = sig[data_index3(c, i, j, k + 1)], zm = sig[data_index3(c, i, j, k - 1)];
+                double gx = 0.5 * (xp - xm), gy = 0.5 * (yp - ym), gz = 0.5 * (zp - zm);
+                double g = sqrt(gx * gx + gy * gy + gz * gz);
+                double l = fabs(xp + xm + yp + ym + zp + zm - 6.0 * sig[id]);
+                om[id] = g;
+                lap[id] = l;
+                if (g > gmax) gmax = g;
+                if (l > lmax) lmax = l;
+            }
+    for (long id = 0; id < N; ++id) {
+        double a = 1.0;
+        if (gmax > 0.0) a += c->alpha * om[id] / gmax;
+        if (lmax > 0.0) a += c->alpha_lap * lap[id] / lmax;
+        om[id] = sqrt(a);
+    }
+    free(sig);
+    free(lap);
+    return status;
+}
+
 int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
                double *xdot, double *dtau, double *dt_out)
 {
@@ -510,29 +550,11 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
         if (dt_out) *dt_out = dt;
         return status;
     }
-    double *sig = (double *)malloc(sizeof(double) * N);
     double *om = (double *)malloc(sizeof(double) * N);
     double *om2 = (double *)malloc(sizeof(double) * N);
     double *X = (double *)malloc(sizeof(double) * 3 * N);
     double *Xn = (double *)malloc(sizeof(double) * 3 * N);
-    for (long id = 0; id < N; ++id) {
-        double w[8];
-        if (node_prim3(c, cons, J, id, w) != 0) status = -1;
-        sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
-    }
-    double gmax = 0.0;
-    for (int k = 0; k < c->nz; ++k)
-        for (int j = 0; j < c->ny; ++j)
-            for (int i = 0; i < c->nx; ++i) {
-                long id = ((long)k * c->ny + j) * c->nx + i;
-                double gx = 0.5 * (sig[data_index3(c, i + 1, j, k)] - sig[data_index3(c, i - 1, j, k)]);
-                double gy = 0.5 * (sig[data_index3(c, i, j + 1, k)] - sig[data_index3(c, i, j - 1, k)]);
-                double gz = 0.5 * (sig[data_index3(c, i, j, k + 1)] - sig[data_index3(c, i, j, k - 1)]);
-                double g = sqrt(gx * gx + gy * gy + gz * gz);
-                om[id] = g;
-                if (g > gmax) gmax = g;
-            }
-    for (long id = 0; id < N; ++id) om[id] = (gmax > 0.0) ? sqrt(1.0 + c->alpha * om[id] / gmax) : 1.0;
+    status |= oref3_monitor(c, cons, J, om);
     for (int f = 0; f < c->n_filter; ++f) {
         for (int k = 0; k < c->nz; ++k)
             for (int j = 0; j < c->ny; ++j)
@@ -630,7 +652,6 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
     for (long a = 0; a < 3 * N; ++a) xdot[a] = tau * (X[a] - x[a]) / dt;
     if (dtau) *dtau = tau;
     if (dt_out) *dt_out = dt;
-    free(sig);
     free(om);
     free(om2);
     free(X);

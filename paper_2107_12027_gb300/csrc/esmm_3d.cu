@@ -262,33 +262,48 @@ __global__ void k3_time(const double *dt_dev, double *t_dev)
 }
 
 // ---- Sec. 5 in 3D ------------------------------------------------------------
-__global__ void k3_mesh_grad(Geom3 g, int lnrho, const double *__restrict__ q, double *__restrict__ grad,
-                             unsigned long long *red)
+__global__ void k3_mesh_grad(Geom3 g, int lnrho, int with_lap, const double *__restrict__ q,
+                             double *__restrict__ grad, double *__restrict__ lap, unsigned long long *red)
 {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double gv = 0.0;
+    double gv = 0.0, lv = 0.0;
     if (id < g.N) {
         int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
         long long c = pidx3(g, i, j, k);
         const double *s = q + (lnrho ? F_LNR : F_RHO) * g.P;
         long long sy = g.pd[0], sz = (long long)g.pd[0] * g.pd[1];
-        double gx = 0.5 * (s[c + 1] - s[c - 1]);
-        double gy = 0.5 * (s[c + sy] - s[c - sy]);
-        double gz = 0.5 * (s[c + sz] - s[c - sz]);
+        double xp = s[c + 1], xm = s[c - 1], yp = s[c + sy], ym = s[c - sy], zp = s[c + sz], zm = s[c - sz];
+        double gx = 0.5 * (xp - xm);
+        double gy = 0.5 * (yp - ym);
+        double gz = 0.5 * (zp - zm);
         gv = sqrt(gx * gx + gy * gy + gz * gz);
         grad[id] = gv;
+        if (with_lap) {
+            lv = fabs(xp + xm + yp + ym + zp + zm - 6.0 * s[c]);
+            lap[id] = lv;
+        }
     }
     double m = block_reduce<0>(gv);
     if (threadIdx.x == 0) atomic_max_nonneg(red, m);
+    if (with_lap) {
+        double ml = block_reduce<0>(lv);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + 8, ml);
+    }
 }
 
-__global__ void k3_mesh_omega(Geom3 g, double alpha, const double *__restrict__ grad, const unsigned long long *red,
-                              double *__restrict__ om)
+__global__ void k3_mesh_omega(Geom3 g, double alpha, double alpha_lap, const double *__restrict__ grad,
+                              const double *__restrict__ lap, const unsigned long long *red, double *__restrict__ om)
 {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= g.N) return;
     double gmax = bits_to_double(red[0]);
-    om[id] = gmax > 0.0 ? sqrt(1.0 + alpha * grad[id] / gmax) : 1.0;
+    double a = 1.0;
+    if (gmax > 0.0) a += alpha * grad[id] / gmax;
+    if (alpha_lap > 0.0) {
+        double lmax = bits_to_double(red[8]);
+        if (lmax > 0.0) a += alpha_lap * lap[id] / lmax;
+    }
+    om[id] = sqrt(a);
 }
 
 // omega <- sum_{a,b,c in {-1,0,1}} 2^-(|a|+|b|+|c|+3) omega_{i+a, j+b, k+c}
@@ -607,8 +622,10 @@ int mesh_and_dt3(esmm3 *g, double dt)
     }
     g->xdot_zero = 0;
     Prof3 pr_(g, ESMM_KIND_MESH, 6 + g->prm.n_filter + g->prm.mu);
-    k3_mesh_grad<<<nb, BS3, 0, g->st>>>(g->g, g->prm.monitor == ESMM_MONITOR_LNRHO, g->q, g->grad, g->red);
-    k3_mesh_omega<<<nb, BS3, 0, g->st>>>(g->g, g->prm.alpha, g->grad, g->red, g->om);
+    // the Laplacian goes to om2, which the filter overwrites only after k3_mesh_omega
+    k3_mesh_grad<<<nb, BS3, 0, g->st>>>(g->g, g->prm.monitor == ESMM_MONITOR_LNRHO, g->prm.alpha_lap > 0.0, g->q,
+                                        g->grad, g->om2, g->red);
+    k3_mesh_omega<<<nb, BS3, 0, g->st>>>(g->g, g->prm.alpha, g->prm.alpha_lap, g->grad, g->om2, g->red, g->om);
     double *om = g->om, *om2 = g->om2;
     for (int f = 0; f < g->prm.n_filter; ++f) {
         k3_mesh_filter<<<nb, BS3, 0, g->st>>>(g->g, om, om2);
@@ -734,11 +751,11 @@ int set_dt3(esmm3 *g, double dt)
 }
 
 // one step with a given mesh velocity (device, [3][N]) and dt
-int step_given3(esmm3 *g, const double *xd, double dt)
+int step_given3(esmm3 *g, const double *xd, double dt, int mem)
 {
     int rc;
     if ((rc = set_dt3(g, dt))) return rc;
-    CK3(cudaMemcpyAsync(g->xdot, xd, 3 * (size_t)g->g.N * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    if ((rc = copy3(g, g->xdot, xd, 3 * (size_t)g->g.N, mem, true))) return rc;
     g->xdot_zero = 0;
     node3(g, g->cons, g->J, g->x, g->xdot, g->zg[0], g->zg[1]);
     return stages3(g);
@@ -774,6 +791,7 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
     g->prm.weno_eps = 1e-6;
     g->prm.monitor = ESMM_MONITOR_LNRHO;
     g->prm.alpha = 800.0;
+    g->prm.alpha_lap = 0.0;
     g->prm.n_filter = 4;
     g->prm.mu = 10;
     g->prm.move_mesh = 1;
@@ -1011,6 +1029,15 @@ int esmm3_rk_step(esmm3 *g, double dt, double *dt_used)
     return ESMM_OK;
 }
 
+int esmm3_rk_step_given(esmm3 *g, const double *xdot, double dt, int mem)
+{
+    if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    int rc = step_given3(g, xdot, dt, mem);
+    if (rc) return rc;
+    CK3(cudaStreamSynchronize(g->st));
+    return check3(g);
+}
+
 int esmm3_advance(esmm3 *g, int nsteps, double dt)
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
@@ -1170,7 +1197,7 @@ int esmm3_adjoint_replay(esmm3 *g, int nsteps)
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
     size_t N = (size_t)g->g.N;
     for (int n = 0; n < nsteps; ++n) {
-        int rc = step_given3(g, (*g->ck)[n] + 12 * N, (*g->ck_dt)[n]);
+        int rc = step_given3(g, (*g->ck)[n] + 12 * N, (*g->ck_dt)[n], ESMM_MEM_DEVICE);
         if (rc) return rc;
     }
     CK3(cudaStreamSynchronize(g->st));

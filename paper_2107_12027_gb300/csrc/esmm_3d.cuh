@@ -26,7 +26,7 @@ enum {
     NQ3 = 24
 };
 constexpr int NF3 = 10;     // per direction and padded node: F[8], metric flux, B~
-constexpr int NR3 = 8;      // reduction slots: grad, tau, radius[3], mesh Courant[3]
+constexpr int NR3 = 9;      // reduction slots: grad, tau, radius[3], mesh Courant[3], Laplacian
 
 __host__ __device__ __forceinline__ long long pidx3(const Geom3 &g, int i, int j, int k)
 {

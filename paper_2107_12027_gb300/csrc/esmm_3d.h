@@ -23,6 +23,7 @@ int esmm3_rhs(esmm3 *g, const double *cons, const double *J, const double *x, co
 int esmm3_cfl_dt(esmm3 *g, double *dt);
 int esmm3_mesh_redistribute(esmm3 *g, double dt, double *xdot, double *dtau, double *dt_used, int mem);
 int esmm3_rk_step(esmm3 *g, double dt, double *dt_used);
+int esmm3_rk_step_given(esmm3 *g, const double *xdot, double dt, int mem);
 int esmm3_advance(esmm3 *g, int nsteps, double dt);
 int esmm3_totals(esmm3 *g, double out[3]);
 int esmm3_last_error(esmm3 *g, int *n_c2p_fail, char *msg, int len);

@@ -364,11 +364,14 @@ int mesh_core(esmm_grid *g, double dt)
     LaunchDom L = dom(g, D_NODE), L2 = dom(g, D_NODE2);
     {
         Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_grad<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.monitor == ESMM_MONITOR_LNRHO, g->q, g->grad, g->red);
+        // the Laplacian goes to om2, which the filter overwrites only after k_mesh_omega
+        k_mesh_grad<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.monitor == ESMM_MONITOR_LNRHO, g->prm.alpha_lap > 0.0,
+                                                g->q, g->grad, g->om2, g->red);
     }
     {
         Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_omega<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.alpha, g->grad, g->red, g->om);
+        k_mesh_omega<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.alpha, g->prm.alpha_lap, g->grad, g->om2, g->red,
+                                                 g->om);
     }
     double *om = g->om, *om2 = g->om2;
     for (int f = 0; f < g->prm.n_filter; ++f) {
@@ -613,6 +616,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     g->prm.monitor = ESMM_MONITOR_LNRHO;
     g->prm.alpha = 20.0;
     g->prm.n_filter = 4;
+    g->prm.alpha_lap = 0.0;
     g->prm.mu = 10;
     g->prm.move_mesh = 1;
     g->prm.precision = ESMM_FP64;
@@ -1010,13 +1014,13 @@ int set_dt(esmm_grid *g, double dt)
     return ESMM_OK;
 }
 
-// One step with a given mesh velocity (device, [2][N]) and dt: the map the
-// adjoint differentiates.
-int step_given(esmm_grid *g, const double *xd, double dt)
+// One step with a given mesh velocity ([2][N], host or device) and dt: the
+// map the adjoint differentiates, and the prescribed mesh motion.
+int step_given(esmm_grid *g, const double *xd, double dt, int mem)
 {
     int rc;
     if ((rc = ensure_doms(g)) || (rc = set_dt(g, dt))) return rc;
-    CK(cudaMemcpyAsync(g->xdot, xd, 2 * (size_t)g->Ntot * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+    if ((rc = copy_in(g, g->xdot, xd, 2 * (size_t)g->Ntot, mem))) return rc;
     g->xdot_zero = 0;
     node(g, g->cons, g->J, g->x, g->xdot, g->pg[0], g->pg[1]);
     return stages(g);
@@ -1129,7 +1133,8 @@ int esmm_set_order(esmm_grid *g, int p, int w)
 int esmm_set_params(esmm_grid *g, const esmm_params *prm)
 {
     if (!g || !prm) return ESMM_ERR_ARG;
-    if (!(prm->cfl > 0.0) || !(prm->weno_eps > 0.0) || !(prm->alpha >= 0.0) || prm->n_filter < 0 ||
+    if (!(prm->cfl > 0.0) || !(prm->weno_eps > 0.0) || !(prm->alpha >= 0.0) || !(prm->alpha_lap >= 0.0) ||
+        prm->n_filter < 0 ||
         prm->mu < 0 || (prm->precision != ESMM_FP64 && prm->precision != ESMM_MIXED) ||
         (prm->monitor != ESMM_MONITOR_RHO && prm->monitor != ESMM_MONITOR_LNRHO))
         return fail(g, ESMM_ERR_ARG, "invalid parameter");
@@ -1278,6 +1283,18 @@ int esmm_rk_step(esmm_grid *g, double dt, double *dt_used)
         return check_c2p(g);
     }
     return ESMM_OK;
+}
+
+int esmm_rk_step_given(esmm_grid *g, const double *xdot, double dt, int mem)
+{
+    if (!g || !xdot || !(dt > 0.0) || (mem != ESMM_MEM_HOST && mem != ESMM_MEM_DEVICE)) return ESMM_ERR_ARG;
+    if (g->dim == 3) return esmm3_rk_step_given(g->g3, xdot, dt, mem);
+    if (g->nprob != 1) return fail(g, ESMM_ERR_ARG, "a batch steps with its adaptive meshes");
+    if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
+    int rc = step_given(g, xdot, dt, mem);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(g->st));
+    return check_c2p(g);
 }
 
 int esmm_advance(esmm_grid *g, int nsteps, double dt)
@@ -1472,7 +1489,7 @@ int esmm_adjoint_replay(esmm_grid *g, int nsteps)
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
     size_t N = (size_t)g->Ntot;
     for (int n = 0; n < nsteps; ++n) {
-        int rc = step_given(g, (*g->ck)[n] + (g->nv + 3) * N, (*g->ck_dt)[n]);
+        int rc = step_given(g, (*g->ck)[n] + (g->nv + 3) * N, (*g->ck_dt)[n], ESMM_MEM_DEVICE);
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(g->st));

@@ -228,6 +228,8 @@ __global__ void k_red_init(int nprob, unsigned long long *red)
     red[NRED * b + 3] = 0ull;
     red[NRED * b + 4] = 0ull;
     red[NRED * b + 5] = 0ull;
+    red[NRED * b + 6] = 0ull;
+    red[NRED * b + 7] = 0ull;
 }
 
 // Step of each problem (eq. cfl with the mesh velocity in the spectral
@@ -255,8 +257,9 @@ __global__ void k_time(int nprob, const double *dt_dev, double *t_dev)
 }
 
 // ---- Sec. 5 mesh redistribution ---------------------------------------------
-__global__ void k_mesh_grad(ProbArg pa, int lnrho, const double *__restrict__ q, double *__restrict__ grad,
-                            unsigned long long *red)
+// |grad_xi sigma| (max to slot 0) and, with_lap, |lap_xi sigma| (max to slot 6)
+__global__ void k_mesh_grad(ProbArg pa, int lnrho, int with_lap, const double *__restrict__ q,
+                            double *__restrict__ grad, double *__restrict__ lap, unsigned long long *red)
 {
     ProbDesc D;
     long long lb;
@@ -265,22 +268,32 @@ __global__ void k_mesh_grad(ProbArg pa, int lnrho, const double *__restrict__ q,
     long long id = lb * blockDim.x + threadIdx.x;
     q += (long long)NQ * D.op;
     grad += D.on;
-    double gv = 0.0;
+    lap += D.on;
+    double gv = 0.0, lv = 0.0;
     if (id < g.N) {
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
         long long c = pidx(g, i, j);
         const double *s = q + (lnrho ? Q_LNR : Q_RHO) * g.P;
-        double gx = 0.5 * (s[c + 1] - s[c - 1]);
-        double gy = 0.5 * (s[c + g.px] - s[c - g.px]);
+        double e = s[c + 1], w = s[c - 1], n = s[c + g.px], so = s[c - g.px];
+        double gx = 0.5 * (e - w);
+        double gy = 0.5 * (n - so);
         gv = sqrt(gx * gx + gy * gy);
         grad[id] = gv;
+        if (with_lap) {
+            lv = fabs(e + w + n + so - 4.0 * s[c]);
+            lap[id] = lv;
+        }
     }
     double m = block_reduce<0>(gv);
     if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b, m);
+    if (with_lap) {
+        double ml = block_reduce<0>(lv);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b + 6, ml);
+    }
 }
 
-__global__ void k_mesh_omega(ProbArg pa, double alpha, const double *__restrict__ grad,
-                             const unsigned long long *red, double *__restrict__ om)
+__global__ void k_mesh_omega(ProbArg pa, double alpha, double alpha_lap, const double *__restrict__ grad,
+                             const double *__restrict__ lap, const unsigned long long *red, double *__restrict__ om)
 {
     ProbDesc D;
     long long lb;
@@ -289,7 +302,13 @@ __global__ void k_mesh_omega(ProbArg pa, double alpha, const double *__restrict_
     long long id = lb * blockDim.x + threadIdx.x;
     if (id >= g.N) return;
     double gmax = bits_to_double(red[(long long)NRED * b]);
-    om[D.on + id] = gmax > 0.0 ? sqrt(1.0 + alpha * grad[D.on + id] / gmax) : 1.0;
+    double a = 1.0;
+    if (gmax > 0.0) a += alpha * grad[D.on + id] / gmax;
+    if (alpha_lap > 0.0) {
+        double lmax = bits_to_double(red[(long long)NRED * b + 6]);
+        if (lmax > 0.0) a += alpha_lap * lap[D.on + id] / lmax;
+    }
+    om[D.on + id] = sqrt(a);
 }
 
 // omega <- sum_{a,b in {-1,0,1}} 2^-(|a|+|b|+2) omega_{i+a, j+b}

@@ -58,7 +58,8 @@ __device__ __forceinline__ double bits_to_double(unsigned long long b) { return 
 
 // per-problem reduction slots: [0] max |grad sigma|, [1] Delta tau (min),
 // [2], [3] max spectral radius per direction, [4], [5] max mesh Courant
-// number per direction of the full displacement x^[mu] - x^n
-constexpr int NRED = 6;
+// number per direction of the full displacement x^[mu] - x^n, [6] max
+// |lap sigma| (monitor with a Laplacian term), [7] unused
+constexpr int NRED = 8;
 
 }  // namespace esmm

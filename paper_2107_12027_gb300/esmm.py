@@ -29,7 +29,7 @@ _ERR = {1: "ESMM_ERR_ARG", 2: "ESMM_ERR_CUDA", 3: "ESMM_ERR_C2P", 4: "ESMM_ERR_T
 SYMBOLS = (
     "esmm_grid_create", "esmm_grid_destroy", "esmm_set_stream", "esmm_set_eos", "esmm_set_order",
     "esmm_set_params", "esmm_get_params", "esmm_state_set", "esmm_state_set_cons", "esmm_state_get",
-    "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step",
+    "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step", "esmm_rk_step_given",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
     "esmm_rhs_static", "esmm_mhd_eigen", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
     "esmm_batch_times", "esmm_batch_totals", "esmm_tune", "esmm_adjoint_record", "esmm_adjoint_steps",
@@ -43,7 +43,8 @@ KINDS = ("node", "pairs", "iface", "update", "mesh", "other")
 class Params(ctypes.Structure):
     _fields_ = [("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("monitor", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("n_filter", ctypes.c_int), ("mu", ctypes.c_int),
-                ("move_mesh", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("move_mesh", ctypes.c_int), ("precision", ctypes.c_int),
+                ("alpha_lap", ctypes.c_double)]
 
 
 _lib = None
@@ -72,7 +73,7 @@ def lib():
             "esmm_state_set_cons": [vp, vp, vp, vp, d, i], "esmm_state_get": [vp, i, vp, i],
             "esmm_get_time": [vp, dp], "esmm_rhs": [vp, vp, vp, vp, vp, vp, vp, i],
             "esmm_cfl_dt": [vp, dp], "esmm_mesh_redistribute": [vp, d, vp, dp, dp, i],
-            "esmm_rk_step": [vp, d, dp], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
+            "esmm_rk_step": [vp, d, dp], "esmm_rk_step_given": [vp, vp, d, i], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
             "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
             "esmm_profile": [vp, i],
             "esmm_rhs_static": [i, i, ctypes.POINTER(i), dp, dp, d, i, i, vp, vp, vp, vp, vp, vp, vp],
@@ -297,6 +298,13 @@ class Grid:
             return d.value
         self._check(lib().esmm_rk_step(self.h, float(dt), None))
         return None
+
+    def rk_step_given(self, xdot, dt):
+        """One step with the prescribed mesh velocity xdot ([d][...], numpy or
+        CUDA tensor, d = 2 or 3) held over the step; dt > 0."""
+        nd = 3 if isinstance(self, Grid3) else 2
+        px, mx = _ptr(xdot, nd * self.N)
+        self._check(lib().esmm_rk_step_given(self.h, px, float(dt), mx))
 
     def advance(self, nsteps, dt=0.0):
         self._check(lib().esmm_advance(self.h, int(nsteps), float(dt)))

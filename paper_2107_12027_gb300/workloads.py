@@ -362,3 +362,70 @@ def rmhd_vortex(x, t=0.0, R=5.0, gamma=5.0 / 3.0, sigma=0.2, B0=0.05):
     B2 = 0.5 * ((s2 + 1.0) * Bt2 - (s2 - 1.0) * Bt1)
     z = np.zeros_like(rho)
     return np.ascontiguousarray(np.stack([rho, v1, v2, z, p, B1, B2, z]))
+
+
+# ---- the 3D RMHD isentropic vortex (Sec. 6, 3D RMHD vortex example) --------
+def vortex_mesh3(n, t=0.0, R=5.0, amp=0.2):
+    """The example's prescribed moving mesh on the periodic box [-R, R]^2 x
+    [-5R, 5R] with n x n x 5n distinct nodes (spacing 2R/n): each coordinate
+    displaced by amp cos(pi t/4) times the product of sines of the other two,
+    sin(3 pi x0_{1,2}/R) and sin(3 pi x0_3/(5R))."""
+    x0 = uniform_mesh3((n, n, 5 * n), (-R, -R, -5 * R), (R, R, 5 * R))
+    return np.ascontiguousarray(x0 + np.cos(np.pi * t / 4.0) * _vortex3_shape(x0, R, amp))
+
+
+def vortex_mesh3_velocity(n, t=0.0, R=5.0, amp=0.2):
+    """d/dt of vortex_mesh3 at fixed computational coordinates."""
+    x0 = uniform_mesh3((n, n, 5 * n), (-R, -R, -5 * R), (R, R, 5 * R))
+    return np.ascontiguousarray(-(np.pi / 4.0) * np.sin(np.pi * t / 4.0) * _vortex3_shape(x0, R, amp))
+
+
+def _vortex3_shape(x0, R, amp):
+    s1, s2 = np.sin(3 * np.pi * x0[0] / R), np.sin(3 * np.pi * x0[1] / R)
+    s3 = np.sin(3 * np.pi * x0[2] / (5 * R))
+    return amp * np.stack([s2 * s3, s3 * s1, s1 * s2])
+
+
+def _vortex_plane(xt, gamma, sigma, B0):
+    """The rotating equilibrium of the vortex frame at the points xt [2][...]:
+    (rho, p, vt [2], Bt [2]), with the field B0 exp((1 - r^2)/2)(-x2, x1) (the
+    field for which radial balance gives the examples' rotation rate f and
+    kappa; see rmhd_vortex)."""
+    r2 = xt[0] ** 2 + xt[1] ** 2
+    e = np.exp(1.0 - r2)
+    rho = (1.0 - sigma * e) ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    kappa = 2.0 * gamma * sigma * rho + (gamma - 1.0) * B0 ** 2 * (2.0 - r2)
+    f = np.sqrt(kappa * e / (kappa * r2 * e + (gamma - 1.0) * rho + gamma * p))
+    eb = np.exp(0.5 * (1.0 - r2))
+    return rho, p, (-xt[1] * f, xt[0] * f), (-B0 * eb * xt[1], B0 * eb * xt[0])
+
+
+def rmhd_vortex3(x, t=0.0, R=5.0, gamma=5.0 / 3.0, sigma=0.2, B0=0.05):
+    """The example's analytic 3D RMHD vortex (primitives [8][...] at the points
+    x [3][...] and time t) on the periodic box [-R, R]^2 x [-5R, 5R]: the 2D
+    vortex in the plane coordinates xh_k = x_k + (x_1 + x_2 + x_3)/3 + t
+    (k = 1, 2), boosted along (1, 1, 1).  Shifts of x by the box's periods move
+    xh on the lattice spanned by (8R/3, 2R/3) and (2R/3, 8R/3); the vortex
+    frame point xt is the lattice image of xh nearest to the origin."""
+    s = (x[0] + x[1] + x[2]) / 3.0 + t
+    xh = np.stack([x[0] + s, x[1] + s])
+    L = np.array([[8.0 * R / 3.0, 2.0 * R / 3.0], [2.0 * R / 3.0, 8.0 * R / 3.0]])   # columns: lattice
+    c = np.floor(np.tensordot(np.linalg.inv(L), xh, axes=1))
+    best, bd = None, None
+    for a in (-1, 0, 1, 2):
+        for b in (-1, 0, 1, 2):
+            k = np.stack([c[0] + a, c[1] + b])
+            cand = xh - np.tensordot(L, k, axes=1)
+            d = cand[0] ** 2 + cand[1] ** 2
+            if best is None:
+                best, bd = cand, d
+            else:
+                m = d < bd
+                best = np.where(m, cand, best)
+                bd = np.where(m, d, bd)
+    rho, p, vt, Bt = _vortex_plane(best, gamma, sigma, B0)
+    den = 6.0 - 3.0 * (vt[0] + vt[1])
+    v = [(4.0 * vt[0] + vt[1] - 3.0) / den, (4.0 * vt[1] + vt[0] - 3.0) / den, (vt[0] + vt[1] - 3.0) / den]
+    B = [(5.0 * Bt[0] - Bt[1]) / 3.0, (5.0 * Bt[1] - Bt[0]) / 3.0, -(Bt[0] + Bt[1]) / 3.0]
+    return np.ascontiguousarray(np.stack([rho, v[0], v[1], v[2], p, B[0], B[1], B[2]]))

@@ -160,3 +160,29 @@ def test_blast_steps_3d():
     # they move (at -xdot of their mirror node) and the face carries a small
     # temporal-metric flux even where the gas is at rest.
     assert abs(cons[0].sum() - m0) < 1e-2 * m0
+
+
+@pytest.mark.parametrize("alpha_lap", [0.0, 10.0])
+def test_monitor_closed_form_on_trigonometric_sigma_3d(alpha_lap):
+    # sigma = rho = 1 + sum_d a_d cos(t_d i_d) on a periodic grid: central
+    # first differences -a_d sin(t_d) sin(t_d i_d), the seven-point Laplacian
+    # sum_d 2 a_d (cos t_d - 1) cos(t_d i_d) (sum-to-product identities); with
+    # every n_d a multiple of 4 the gradient's maximum is reached at
+    # (n/4, n/4, n/4) and the Laplacian's at the origin (the monitor of the 3D
+    # vortex example, Sec. 6).
+    n, a = (8, 12, 4), (0.1, 0.05, 0.02)
+    t = [2 * np.pi / m for m in n]
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    idx = (i, j, k)
+    rho = 1.0 + sum(a[d] * np.cos(t[d] * idx[d]) for d in range(3))
+    z = 0.0 * rho
+    prim = np.ascontiguousarray(np.stack([rho, z + 0.1, z - 0.05, z + 0.02, z + 1.0, z + 0.2, z + 0.1, z - 0.1]))
+    x = wl.uniform_mesh3(n)
+    c = oracle.make_cfg3(*n, monitor=oracle.MONITOR_RHO, alpha=20.0, alpha_lap=alpha_lap)
+    cons, J = oracle.init_state3(c, prim, x)
+    g = np.sqrt(sum((a[d] * np.sin(t[d]) * np.sin(t[d] * idx[d])) ** 2 for d in range(3)))
+    lap = np.abs(sum(2 * a[d] * (np.cos(t[d]) - 1) * np.cos(t[d] * idx[d]) for d in range(3)))
+    gmax = np.sqrt(sum((a[d] * np.sin(t[d])) ** 2 for d in range(3)))
+    lmax = sum(2 * a[d] * (1 - np.cos(t[d])) for d in range(3))
+    want = np.sqrt(1.0 + 20.0 * g / gmax + alpha_lap * lap / lmax)
+    assert np.abs(oracle.monitor3(c, cons, J) - want).max() < 1e-12

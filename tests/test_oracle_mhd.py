@@ -16,6 +16,7 @@ import oracle
 from paper_2107_12027_gb300 import workloads as wl
 
 GAMMAS = (4.0 / 3.0, 5.0 / 3.0)
+G53 = 5.0 / 3.0
 EPS = np.finfo(float).eps
 
 
@@ -418,3 +419,46 @@ def test_vortex_truncation_order(p, order):
     # the periodic wrap of the vortex's e^{-r^2/2} tails stays below 1e-12.
     e1, e2 = _vortex_truncation_error(128, p), _vortex_truncation_error(256, p)
     assert np.log2(e1 / e2) > order, (e1, e2)
+
+
+def _pde_residual(fun, dim, pts, t=0.7, d=1e-3):
+    """max |dU/dt + sum_k dF_k/dx_k| / max |dU/dt| of the primitive field
+    fun(x [dim][1], t) at the points, by fourth-order central differences in
+    t and x of the oracle's pointwise U and F_k (eq. RMHDdiv2, div B = 0)."""
+    stencil = ((-1.0, 2), (8.0, 1), (-8.0, -1), (1.0, -2))
+    res, scale = 0.0, 0.0
+    for P in pts.T:
+        w = lambda xx, tt: fun(xx.reshape(dim, 1), tt)[:, 0]
+        dU = sum(c * oracle.mhd_prim2cons(G53, w(P, t + o * d)) for c, o in stencil) / (12 * d)
+        r = dU.copy()
+        for k in range(dim):
+            e = np.zeros(dim)
+            e[k] = d
+            r += sum(c * oracle.mhd_flux(G53, w(P + o * e, t), k) for c, o in stencil) / (12 * d)
+        res, scale = max(res, np.abs(r).max()), max(scale, np.abs(dU).max())
+    return res / scale
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_analytic_vortices_solve_rmhd(dim):
+    # The 2D and 3D RMHD vortices of Sec. 6 are exact solutions: the PDE's
+    # residual at random points is at the level of the difference formulas'
+    # error (~1e-11).  With the field's exponent as printed, exp(1 - r^2),
+    # the same check leaves a residual of ~4e-4.
+    pts = wl.rng(90 + dim).uniform(-2.5, 2.5, (dim, 120))
+    if dim == 2:
+        f = lambda x, t: wl.rmhd_vortex(x, t, R=8.0)
+    else:
+        f = lambda x, t: wl.rmhd_vortex3(x, t)
+    assert _pde_residual(f, dim, pts) < 1e-9
+
+
+def test_vortex3_is_periodic_on_its_box():
+    # shifting a point by a period of [-R, R]^2 x [-5R, 5R] moves the plane
+    # coordinates by a lattice vector: the field repeats
+    pts = wl.rng(95).uniform(-5.0, 5.0, (3, 500)) * np.array([[1.0], [1.0], [5.0]])
+    base = wl.rmhd_vortex3(pts, 0.3)
+    for d, per in enumerate((10.0, 10.0, 50.0)):
+        q = pts.copy()
+        q[d] += per
+        assert np.abs(wl.rmhd_vortex3(q, 0.3) - base).max() < 1e-13

@@ -277,3 +277,65 @@ def test_rk_step_given_matches_rk_step_with_its_own_mesh_velocity():
     b = oracle.rk_step_given(cfg, cons, J, x, xdot, dt)
     for u, v in zip(a[:3], b):
         np.testing.assert_array_equal(u, v)
+
+
+# ------------------------------------------------ monitor with a Laplacian term
+@pytest.mark.parametrize("mon", [oracle.MONITOR_RHO, oracle.MONITOR_LNRHO])
+@pytest.mark.parametrize("alpha_lap", [0.0, 10.0])
+def test_monitor_closed_form_on_trigonometric_sigma(mon, alpha_lap):
+    # sigma = a cos(tx i) + b cos(ty j) (+ const) on a periodic grid: the
+    # central first difference along i is -a sin(tx) sin(tx i) and the
+    # five-point Laplacian is 2a (cos tx - 1) cos(tx i) + 2b (cos ty - 1)
+    # cos(ty j) (sum-to-product identities).  With nx, ny multiples of 4 the
+    # gradient's maximum sqrt(a^2 sin^2 tx + b^2 sin^2 ty) is reached at
+    # (nx/4, ny/4) and the Laplacian's 2a(1 - cos tx) + 2b(1 - cos ty) at
+    # (0, 0), so omega has the closed form of the vortex examples' monitor
+    # (Sec. 6; alpha_lap = 0 is eq. monitor of Sec. 5).
+    nx, ny, a, b = 16, 12, 0.1, 0.05
+    tx, ty = 2 * np.pi / nx, 2 * np.pi / ny
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny))
+    f = a * np.cos(tx * i) + b * np.cos(ty * j)
+    rho = 1.0 + f if mon == oracle.MONITOR_RHO else np.exp(f)
+    prim = np.stack([rho, 0.1 + 0 * f, 0.05 + 0 * f, 1.0 + 0 * f])
+    x = wl.uniform_mesh(nx, ny)
+    cfg = oracle.make_cfg(nx, ny, monitor=mon, alpha=20.0, alpha_lap=alpha_lap)
+    cons, J = oracle.init_state(cfg, prim, x)
+    g = np.hypot(a * np.sin(tx) * np.sin(tx * i), b * np.sin(ty) * np.sin(ty * j))
+    lap = np.abs(2 * a * (np.cos(tx) - 1) * np.cos(tx * i) + 2 * b * (np.cos(ty) - 1) * np.cos(ty * j))
+    gmax = np.hypot(a * np.sin(tx), b * np.sin(ty))
+    lmax = 2 * a * (1 - np.cos(tx)) + 2 * b * (1 - np.cos(ty))
+    want = np.sqrt(1.0 + 20.0 * g / gmax + alpha_lap * lap / lmax)
+    assert np.abs(oracle.monitor(cfg, cons, J) - want).max() < 1e-12
+
+
+# ------------------------------------------- entropy on the RMHD vortex (Sec. 6)
+def _vortex_run(p, w, dt, T, n=24, R=5.0):
+    """Total entropy sum J eta after each SSP-RK3 step of the RMHD vortex on the
+    example's prescribed moving mesh (mesh velocity held over each step)."""
+    x = wl.vortex_mesh(n, 0.0, R=R)
+    cfg = oracle.make_cfg(n, n, period=(2 * R, 2 * R), p=p, w=w, gamma=G53, phys=oracle.RMHD)
+    cons, J = oracle.init_state(cfg, wl.rmhd_vortex(x, 0.0, R=R), x)
+    ent = [oracle.totals(cfg, cons, J)[0]]
+    for s in range(int(round(T / dt))):
+        cons, J, x = oracle.rk_step_given(cfg, cons, J, x, wl.vortex_mesh_velocity(n, s * dt, R=R), dt)
+        ent.append(oracle.totals(cfg, cons, J)[0])
+    return np.array(ent)
+
+
+def test_vortex_ec_entropy_change_is_the_rk3_error():
+    # The EC scheme conserves the total entropy semi-discretely on a moving
+    # mesh (Thm. 3.1 with the GCL), so the fully discrete change after a fixed
+    # time is SSP-RK3's error: it falls by 2^3 per halving of dt.
+    e = [_vortex_run(3, 0, dt, 0.4) for dt in (0.1, 0.05, 0.025)]
+    d = [ei[-1] - ei[0] for ei in e]
+    assert abs(d[0]) < 1e-3
+    assert d[0] / d[1] > 7.5 and d[1] / d[2] > 7.5, d
+
+
+def test_vortex_es_entropy_decays_every_step():
+    # The ES scheme dissipates entropy (Thm. 4.1): on the coarse vortex grid
+    # the dissipation dominates the RK3 error, and the total decreases in
+    # every step, by an amount that converges as dt -> 0.
+    e1, e2 = _vortex_run(3, 5, 0.05, 0.4), _vortex_run(3, 5, 0.025, 0.4)
+    assert (np.diff(e1) < 0).all() and (np.diff(e2) < 0).all()
+    assert abs((e1[-1] - e1[0]) / (e2[-1] - e2[0]) - 1) < 1e-2
