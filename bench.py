@@ -56,7 +56,11 @@ FP64_FLOP_PER_CLK_SM = 4
 FP32_FLOP_PER_CLK_SM = 256
 # DRAM bytes (read + write) of one interface-kernel launch in that capture;
 # None whenever the kernel has changed since the counters were taken.
-TRAFFIC_IFACE_F64 = 23.48e6
+TRAFFIC_IFACE_F64 = 23.51e6
+# The mixed form's interface kernel (profiles/flux_f32_riemann400.md): FP32
+# flops per interface (fadd + fmul + 2 ffma) and DRAM bytes per launch.
+FLOPS_PER_IFACE_F32 = 1259
+TRAFFIC_IFACE_F32 = 13.08e6
 # The same for the RMHD interface kernels at p = 2, WENO5 (profiles/
 # iface_mhd_ops_rotor512_blast64.md): the FP64 2D kernel on the 512^2 rotor
 # (16,156 FP64 flops per interface; 1.036 GB of DRAM traffic per launch, the
@@ -72,6 +76,56 @@ FLOPS_PER_IFACE_MHD3 = 20147
 TRAFFIC_IFACE_MHD3 = 9.66e9
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+# Algorithmic HBM bytes per node and RK stage of the whole step, fused to the
+# minimum: each stage reads the state and J of the stage and of t^n, x^n and
+# the mesh velocity and writes the new state and J (stage 1 reads t^n's only),
+# averaged over the three stages; plus the mesh redistribution once per step
+# (read rho and x^n, write the mesh velocity), a third of it per stage.
+#   2D RHD  (m = 4): (112 + 152 + 152)/3 + 40/3 = 152.0 B
+#   2D RMHD (m = 8): (176 + 248 + 248)/3 + 40/3 = 237.3 B
+#   3D RMHD (m = 8): (192 + 264 + 264)/3 + 56/3 = 258.7 B
+HBM_BYTES_PER_NODE_STAGE = {"rhd2": 152.0, "rmhd2": 237.3, "rmhd3": 258.7}
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    else the fallback measurement of 6.8 TB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def hbm_roofline(rate, kind):
+    """Whole-step fraction of the HBM roofline: algorithmic bytes per
+    node-stage x node-stages per second over the measured copy bandwidth."""
+    peak, src = hbm_peak_gbs()
+    ach = rate * HBM_BYTES_PER_NODE_STAGE[kind] / 1e9
+    return {"bytes_per_node_stage": HBM_BYTES_PER_NODE_STAGE[kind], "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "peak_source": src}
+
+
+def kind_rates(g, torch, nodes, steps, restore=None):
+    """Device time per step of each kernel kind (the library's per-launch
+    event profiling, outside the timed region) and the RHS-only and
+    mesh-only rates derived from it."""
+    from paper_2107_12027_gb300 import esmm
+    g.profile((1 << len(esmm.KINDS)) - 1)
+    for _ in range(steps):
+        if restore:
+            restore()
+        g.rk_step(sync=False)
+    torch.cuda.synchronize()
+    prof = g.profile_read()
+    g.profile(0)
+    per = {k: v[0] / steps for k, v in prof.items()}
+    rhs = per["node"] + per["pairs"] + per["iface"] + per["update"]
+    return {"ms_per_step": per,
+            "rhs_only": {"value": nodes * 3 / (rhs * 1e-3), "unit": "cell-updates/s",
+                         "note": "node, pair, interface and update kernels"},
+            "mesh_only": {"value": nodes / (per["mesh"] * 1e-3) if per["mesh"] > 0 else None,
+                          "unit": "node-updates/s", "note": "one mesh redistribution per step"}}
 
 
 def parse():
@@ -371,6 +425,13 @@ def run_gpu(args):
                 "kernel": "k_iface<double,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
                 "share_of_step": iface_ms / total_ms,
                 "peak_note": "derived FP64 peak: 152 SMs x 4 flop/clk x 2070 MHz"}
+    else:
+        peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        ach = FLOPS_PER_IFACE_F32 * ifaces_per_launch / avg_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": TRAFFIC_IFACE_F32, "kernel": "k_iface<float,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
+                "share_of_step": iface_ms / total_ms,
+                "peak_note": "derived FP32 peak: 152 SMs x 256 flop/clk x 2070 MHz"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.form == "fp64" else "f32+f64",
@@ -378,8 +439,13 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "nodes": n * n, "form": args.form,
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "independent problem per rank" if world > 1 else "single GPU"},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+            "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "hbm": hbm_roofline(value / world, "rhd2")}
     if not args.no_extras:
+        with esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
+                       stream=stream.cuda_stream, **grid_params(args.form)) as gk:
+            gk.state_set(prim, x)
+            line["kinds"] = kind_rates(gk, torch, n * n, 10)
         line["e2e"] = e2e_leg(torch, n, args.form, max(3, min(K, 50)), 2, stream)
         rate, desc, _ = oracle_sample_rate(n, 15.0, 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
@@ -388,7 +454,8 @@ def run_gpu(args):
                            stream=stream.cuda_stream, **grid_params("mixed")) as gm:
                 gm.state_set(prim, x)
                 tm, _, _ = timed_steps(gm, torch, K, W, flush, stream, None)
-            forms = {"mixed": {"value": n * n * 3 * K / (tm * 1e-3), "ms_per_step": tm / K}}
+                forms = {"mixed": {"value": n * n * 3 * K / (tm * 1e-3), "ms_per_step": tm / K,
+                                   "kinds": kind_rates(gm, torch, n * n, 10)}}
             forms["mixed"].update(mixed_vs_fp64(torch, n, stream))
             forms["batched"] = batch_leg(torch, stream)
             line["forms"] = forms
@@ -510,6 +577,9 @@ def run_rmhd(args):
             "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms,
             "peak_note": "derived %s peak: 152 SMs x %d flop/clk x 2070 MHz" % ("FP32" if mixed else "FP64",
                                                                               per_clk)}
+    kinds = None
+    if not args.no_extras:
+        kinds = kind_rates(g, torch, nodes, 3, restore=lambda: g.state_set_cons(c0, J0, x0))
     g.close()
     line = {"metric": METRIC, "value": nodes * 3 * K / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -519,8 +589,11 @@ def run_rmhd(args):
                        "l2": ("working set (~0.5 GB of node data) larger than L2" if three
                               else "flushed (256 MB write) before every timed step"),
                        "parallelism": "single GPU"},
-            "roofline": roof, "clocks": clk}
+            "roofline": roof, "clocks": clk,
+            "hbm": hbm_roofline(nodes * 3 * K / (total_ms * 1e-3), "rmhd3" if three else "rmhd2")}
     line["gpu_launches"] = launches
+    if kinds:
+        line["kinds"] = kinds
     if not three and args.form == "fp64" and not args.no_extras:
         with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
                        stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,

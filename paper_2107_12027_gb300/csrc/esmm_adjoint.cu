@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(128) k_iface_vjp(ProbArg pa, Phys ph, const do
             if (jq == 6) (k == OFF ? r0 : r1).d = 1.0;
             dual diss[4];
             ArrStencil<dual, NS> acc{st};
-            es_dissipation<dual, dual, WW>(nvx, nvy, jt, r0, r1, l0, l1, acc, ph, diss);
+            es_dissipation<dual, dual, WW>(nvx, nvy, jt, r0, r1, l0, l1, r0, r1, acc, ph, diss);
             double gsum = 0.0;
 #pragma unroll
             for (int a = 0; a < 4; ++a) gsum -= lf[a] * diss[a].d;
@@ -289,10 +289,9 @@ __global__ void k_prim_grad(ProbArg pa, double gam, const double *__restrict__ c
     lam += 4 * D.on;
     out += 4 * D.on;
     double iJ = 1.0 / J[id];
-    double rho, vx, vy, pr;
+    double rho, vx, vy, pr, W;
     cons2prim(gam, cons[id] * iJ, cons[g.N + id] * iJ, cons[2 * g.N + id] * iJ, cons[3 * g.N + id] * iJ, -1.0, rho,
-              vx, vy, pr);
-    double W = 1.0 / sqrt(1.0 - (vx * vx + vy * vy));
+              vx, vy, pr, W);
     double g1 = gam / (gam - 1.0), rh = rho + g1 * pr, W2 = W * W, W3 = W2 * W, W4 = W2 * W2;
     double A[4][4] = {
         {W, rho * W3 * vx, rho * W3 * vy, 0.0},

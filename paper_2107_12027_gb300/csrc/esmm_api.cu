@@ -60,6 +60,8 @@ struct esmm_grid {
     double *c1, *J1, *x1, *c2, *J2, *x2;
     // right-hand-side work arrays
     double *q;                       // [NQ][Ptot] (RMHD: [NQ_MHD][Ptot])
+    double *cw;                      // [4][Ntot] Jacobi weights of the mesh iteration
+    float *q32;                      // [NQ32][Ptot] FP32 copies (RHD mixed form)
     double *pg[3];                   // recovery warm starts (p; RMHD: Z), state -> stage 2 -> stage 3
     void *pairs;                     // [2][PMAX][4][Ptot] of the working precision (RHD)
     void *iflux;                     // [2][5][Ptot] (RMHD: [2][NF_MHD][Ptot]) of the working precision
@@ -252,15 +254,22 @@ LaunchDom dom_one(const esmm_grid *g, int b, int kind, int bs = BS)
     return L;
 }
 
+// the FP32 copies of the node arrays, written and read in the RHD mixed form
+float *q32_of(const esmm_grid *g)
+{
+    return g->phys == ESMM_RHD && g->prm.precision == ESMM_MIXED ? g->q32 : nullptr;
+}
+
 void launch_node(const esmm_grid *g, const LaunchDom &L, const double *cons, const double *J, const double *x,
                  const double *xdot, const double *pg_in, double *pg_out, double *q)
 {
+    float *q32 = q32_of(g);
     if (g->p == 1)
-        k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status);
+        k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32);
     else if (g->p == 2)
-        k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status);
+        k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32);
     else
-        k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status);
+        k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32);
 }
 
 void node(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
@@ -288,13 +297,13 @@ void fluxes(esmm_grid *g)
         }
         {
             Prof pr_(g, ESMM_KIND_PAIRS);
-            if (f32) launch_pairs_f32(Lp, ph, g->q, g->pairs, dir, g->st);
-            else launch_pairs_f64(Lp, ph, g->q, g->pairs, dir, g->st);
+            if (f32) launch_pairs_f32(Lp, ph, g->q, g->q32, g->pairs, dir, g->st);
+            else launch_pairs_f64(Lp, ph, g->q, nullptr, g->pairs, dir, g->st);
         }
         {
             Prof pr_(g, ESMM_KIND_IFACE);
-            if (f32) launch_iface_f32(Li, ph, g->q, g->pairs, g->iflux, dir, g->st);
-            else launch_iface_f64(Li, ph, g->q, g->pairs, g->iflux, dir, g->st);
+            if (f32) launch_iface_f32(Li, ph, g->q, g->q32, g->pairs, g->iflux, dir, g->st);
+            else launch_iface_f64(Li, ph, g->q, nullptr, g->pairs, g->iflux, dir, g->st);
         }
     }
 }
@@ -330,7 +339,7 @@ void step_radius(esmm_grid *g, double dt)
     LaunchDom L = dom(g, D_NODE);
     if (g->phys == ESMM_RMHD)
         launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->prm.precision == ESMM_MIXED, g->st);
-    else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red);
+    else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red, q32_of(g));
 }
 
 // the step (and the capped mesh limiter) into dt_dev / slot 1, after the
@@ -379,11 +388,15 @@ int mesh_core(esmm_grid *g, double dt)
         k_mesh_filter<<<L.nblk, L.bs, 0, g->st>>>(L.pa, om, om2);
         std::swap(om, om2);
     }
+    if (g->prm.mu > 0) {
+        Prof pr_(g, ESMM_KIND_MESH);
+        k_mesh_weights<<<L.nblk, L.bs, 0, g->st>>>(L.pa, om, g->cw);
+    }
     const double *src = g->x;
     for (int nu = 0; nu < g->prm.mu; ++nu) {
         double *dst = (nu % 2 == 0) ? g->X : g->Xn;
         Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_jacobi<<<L.nblk, L.bs, 0, g->st>>>(L.pa, om, src, dst);
+        k_mesh_jacobi<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->cw, src, dst);
         src = dst;
     }
     {
@@ -414,7 +427,7 @@ int rk_step_async(esmm_grid *g, double dt)
     {
         Prof pr_(g, ESMM_KIND_NODE);
         LaunchDom L = dom(g, D_PAD);
-        k_tmetric<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->xdot, g->q);
+        k_tmetric<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->xdot, g->q, q32_of(g));
     }
     return stages(g);
 }
@@ -465,12 +478,14 @@ void free_all(esmm_grid *g)
 {
     double **bufs[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2,
                        &g->q, &g->pg[0], &g->pg[1], &g->pg[2], &g->in_cons, &g->in_J, &g->in_x, &g->in_xdot,
-                       &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->X, &g->Xn, &g->dt_dev,
+                       &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->X, &g->Xn, &g->dt_dev,
                        &g->t_dev, &g->partials, &g->tot_dev};
     for (double **b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     drop_graph(g);
     if (g->pairs) cudaFree(g->pairs);
+    if (g->q32) cudaFree(g->q32);
+    g->q32 = nullptr;
     if (g->iflux) cudaFree(g->iflux);
     if (g->red) cudaFree(g->red);
     if (g->status) cudaFree(g->status);
@@ -629,7 +644,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         {&g->cons, nv * N}, {&g->J, N}, {&g->x, 2 * N}, {&g->xdot, 2 * N}, {&g->c1, nv * N}, {&g->J1, N},
         {&g->x1, 2 * N}, {&g->c2, nv * N}, {&g->J2, N}, {&g->x2, 2 * N}, {&g->q, nq * P},
         {&g->pg[0], N}, {&g->pg[1], N}, {&g->pg[2], N}, {&g->out_dc, nv * N}, {&g->out_dJ, N},
-        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->X, 2 * N}, {&g->Xn, 2 * N},
+        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->X, 2 * N}, {&g->Xn, 2 * N},
         {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max},
         {&g->tot_dev, 3 * (size_t)nprob}};
     for (auto &a : al)
@@ -645,7 +660,8 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     }
     size_t npairs = phys == ESMM_RMHD ? 1 : (size_t)2 * PMAX * 4 * P;
     size_t nflux = phys == ESMM_RMHD ? (size_t)2 * NF_MHD * P : (size_t)2 * 5 * P;
-    if (cudaMalloc(&g->pairs, npairs * d) != cudaSuccess || cudaMalloc(&g->iflux, nflux * d) != cudaSuccess ||
+    if ((phys == ESMM_RHD && cudaMalloc((void **)&g->q32, (size_t)NQ32 * P * sizeof(float)) != cudaSuccess) ||
+        cudaMalloc(&g->pairs, npairs * d) != cudaSuccess || cudaMalloc(&g->iflux, nflux * d) != cudaSuccess ||
         cudaMalloc((void **)&g->red, (size_t)NRED * nprob * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void **)&g->status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&g->pin, std::max<size_t>(16, 3 * (size_t)nprob) * sizeof(double)) != cudaSuccess) {
@@ -795,7 +811,7 @@ void step_launches(const esmm_grid *g, double dt, long long per[ESMM_NKINDS])
     per[ESMM_KIND_PAIRS] = g->phys == ESMM_RMHD ? 0 : 6;
     per[ESMM_KIND_IFACE] = 6;
     per[ESMM_KIND_UPDATE] = 3;
-    per[ESMM_KIND_MESH] = g->prm.move_mesh ? (4 + g->prm.n_filter + g->prm.mu) : 0;
+    per[ESMM_KIND_MESH] = g->prm.move_mesh ? (4 + g->prm.n_filter + g->prm.mu + (g->prm.mu > 0)) : 0;
     per[ESMM_KIND_OTHER] = 3 + (dt > 0.0 ? 0 : 1);  // reset, (CFL), dt, time
 }
 
@@ -915,11 +931,11 @@ int tune(esmm_grid *g)
                         for (int dir = 0; dir < 2; ++dir) {
                             LaunchDom L = dom(g, dir ? c.kind2 : c.kind);
                             if (c.kind == D_PAIR0) {
-                                if (f32) launch_pairs_f32(L, ph, g->q, g->pairs, dir, g->st);
-                                else launch_pairs_f64(L, ph, g->q, g->pairs, dir, g->st);
+                                if (f32) launch_pairs_f32(L, ph, g->q, g->q32, g->pairs, dir, g->st);
+                                else launch_pairs_f64(L, ph, g->q, nullptr, g->pairs, dir, g->st);
                             } else {
-                                if (f32) launch_iface_f32(L, ph, g->q, g->pairs, g->iflux, dir, g->st);
-                                else launch_iface_f64(L, ph, g->q, g->pairs, g->iflux, dir, g->st);
+                                if (f32) launch_iface_f32(L, ph, g->q, g->q32, g->pairs, g->iflux, dir, g->st);
+                                else launch_iface_f64(L, ph, g->q, nullptr, g->pairs, g->iflux, dir, g->st);
                             }
                         }
                     });
@@ -1604,8 +1620,8 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     for (int dir = 0; dir < 2; ++dir) {
         long long cp = dir == 0 ? (long long)(nx + p) * ny : (long long)(ny + p) * nx;
         long long ci = dir == 0 ? (long long)(nx + 1) * ny : (long long)(ny + 1) * nx;
-        launch_pairs_f64(one(cp, 128), ph, q, pairs, dir, st);
-        launch_iface_f64(one(ci, 128), ph, q, pairs, iflux, dir, st);
+        launch_pairs_f64(one(cp, 128), ph, q, nullptr, pairs, dir, st);
+        launch_iface_f64(one(ci, 128), ph, q, nullptr, pairs, iflux, dir, st);
     }
     LaunchDom Lu = one(G.N, BS);
     k_update<double><<<Lu.nblk, Lu.bs, 0, st>>>(Lu.pa, iflux, dcons, dJ, nullptr, nullptr, nullptr, nullptr, nullptr,

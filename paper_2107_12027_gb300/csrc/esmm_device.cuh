@@ -1,7 +1,7 @@
 // esmm_device.cuh -- device arithmetic of the ES adaptive moving-mesh scheme
 // (Duan & Tang, arXiv 2107.12027), 2D RHD, templated on the working precision
 // R (double for the FP64 form, float for the mixed form).  The primitive
-// recovery and the near-equal branch of the logarithmic mean are always FP64.
+// recovery is always FP64, and so are the jumps of the logarithmic mean.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,6 +16,12 @@ constexpr int PMAX = 3;      // largest supported p
 enum {
     Q_RHO = 0, Q_P, Q_BETA, Q_UX, Q_UY, Q_W, Q_LNR, Q_LNB,
     Q_M00, Q_M01, Q_M10, Q_M11, Q_MT0, Q_MT1, NQ
+};
+// FP32 copies of the node quantities that the mixed form's flux kernels read
+// (written by the FP64 node pass, so that no flux kernel converts a double).
+enum {
+    Q32_R = 0, Q32_B, Q32_UX, Q32_UY, Q32_W, Q32_LNR, Q32_LNB,
+    Q32_M00, Q32_M01, Q32_M10, Q32_M11, Q32_MT0, Q32_MT1, NQ32
 };
 
 struct Geom {
@@ -121,46 +127,55 @@ __device__ __forceinline__ double mesh_at(const Geom &g, const double *a, int i,
 // most 1e-15 (E + p), the resolution of E + p from which f is evaluated, or
 // when |f| <= 2e-15 (E + p), f's own rounding level (where df/dp is small,
 // steps at that level exceed the first bound and the loop would bisect);
-// p0 is a warm start (ignored when outside the bracket).  Returns 0, 1 for a
-// non-admissible state, 2 when the iteration cap is hit.
+// p0 is a warm start (ignored when outside the bracket).  The Newton step
+// divides by df through an FP32 reciprocal: the slope only steers the step
+// (a relative slope error e contracts the error by e per step), while f, which
+// decides the stopping, is FP64.  W receives the Lorentz factor 1/sqrt(1-v^2)
+// (1 for a non-admissible state).  Returns 0, 1 for a non-admissible state, 2
+// when the iteration cap is hit.
 __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double my, double E,
-                                         double p0, double &rho, double &vx, double &vy, double &p)
+                                         double p0, double &rho, double &vx, double &vy, double &p, double &W)
 {
     double S2 = mx * mx + my * my;
     double S = sqrt(S2);
     double gg = (gam - 1.0) / gam;
-    rho = 0.0; vx = 0.0; vy = 0.0; p = 0.0;
+    rho = 0.0; vx = 0.0; vy = 0.0; p = 0.0; W = 1.0;
     if (!(D > 0.0) || !(E * E > D * D + S2) || !(E > 0.0)) return 1;
     double lo = 0.0, hi = (gam - 1.0) * E;
     double pc = (p0 > lo && p0 < hi) ? p0 : 0.5 * (lo + hi);
     int ok = 0;
+    bool have = false;        // r, iW2, rs below belong to pc
+    double r = 0.0, iW2 = 0.0, rs = 0.0;
     for (int it = 0; it < 200; ++it) {
         double Ep = E + pc;
-        double r = __drcp_rn(Ep);
-        double iW2 = (Ep - S) * (Ep + S) * r * r;   // 1 - v^2
-        double rs = rsqrt(iW2);
+        r = __drcp_rn(Ep);
+        iW2 = (Ep - S) * (Ep + S) * r * r;           // 1 - v^2
+        rs = rsqrt(iW2);
         double iW = iW2 * rs;                        // sqrt(1 - v^2)
         double v2 = S2 * r * r;
         double f = gg * (Ep * iW2 - D * iW) - pc;
         double df = gg * (1.0 + v2 - D * v2 * r * rs) - 1.0;
-        if (fabs(f) <= 2.0e-15 * (E + pc)) { ok = 1; break; }   // residual at rounding level
+        if (fabs(f) <= 2.0e-15 * (E + pc)) { ok = 1; have = true; break; }   // residual at rounding level
         double pn = pc;                              // f = 0: pc is a root
         if (f != 0.0) {
             if (f > 0.0) lo = pc; else hi = pc;
-            pn = pc - f * __drcp_rn(df);
+            pn = pc - f * (double)__frcp_rn((float)df);
             if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
         }
-        if (fabs(pn - pc) <= 1.0e-15 * (E + pn)) { pc = pn; ok = 1; break; }
+        if (fabs(pn - pc) <= 1.0e-15 * (E + pn)) { have = pn == pc; pc = pn; ok = 1; break; }
         pc = pn;
     }
-    double Ep = E + pc;
-    double r = __drcp_rn(Ep);
-    double iW2 = (Ep - S) * (Ep + S) * r * r;
-    double rs = rsqrt(iW2);
+    if (!have) {
+        double Ep = E + pc;
+        r = __drcp_rn(Ep);
+        iW2 = (Ep - S) * (Ep + S) * r * r;
+        rs = rsqrt(iW2);
+    }
     rho = D * (iW2 * rs);
     vx = mx * r;
     vy = my * r;
     p = pc;
+    W = rs;
     return ok ? 0 : 2;
 }
 
@@ -353,6 +368,35 @@ __device__ __forceinline__ void logmean(T a, T b, T la, T lb, double thr, R &mea
     }
 }
 
+// The log mean of two nodes, a32 and b32 being the working-precision copies
+// of a and b: in FP64 and on duals exactly logmean.  In FP32 the jumps b - a
+// and ln b - ln a, which cancel at near-equal states, are taken in FP64 from
+// the FP64 node values; the series (switch at (b-a)^2 < thr (a+b)^2) and the
+// quotients then run in FP32, whose rounding of the result they already are
+// below (the series' terms beyond 1 are < thr/3).
+template <typename R, typename T>
+__device__ __forceinline__ void lmean(T a, T b, T la, T lb, R a32, R b32, double thr, R &mean, R &inv_mean)
+{
+    logmean<R, T>(a, b, la, lb, thr, mean, inv_mean);
+}
+template <>
+__device__ __forceinline__ void lmean<float, double>(double a, double b, double la, double lb, float a32, float b32,
+                                                     double thr, float &mean, float &inv_mean)
+{
+    const float d = (float)(b - a), s = a32 + b32;
+    if (d * d < (float)thr * (s * s)) {
+        const float is = __frcp_rn(s);
+        const float r = d * is, u = r * r;
+        const float F = 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f)));
+        mean = 0.5f * s * __frcp_rn(F);
+        inv_mean = 2.0f * F * is;
+    } else {
+        const float dl = (float)(lb - la);
+        mean = d * __frcp_rn(dl);
+        inv_mean = dl * __frcp_rn(d);
+    }
+}
+
 // Node values of one two-point flux argument (the parameter variables).
 template <typename R>
 struct NodeV {
@@ -377,8 +421,8 @@ __device__ __forceinline__ void ec_pair(const NodeV<R> &l, const NodeV<R> &r, R 
                                         R gm1inv, double thr, R out[4])
 {
     R rln, irln, bln, ibln;
-    logmean<R, typename LogT<R>::type>(l.rho, r.rho, l.lnr, r.lnr, thr, rln, irln);
-    logmean<R, typename LogT<R>::type>(l.beta, r.beta, l.lnb, r.lnb, thr, bln, ibln);
+    lmean<R, typename LogT<R>::type>(l.rho, r.rho, l.lnr, r.lnr, l.r, r.r, thr, rln, irln);
+    lmean<R, typename LogT<R>::type>(l.beta, r.beta, l.lnb, r.lnb, l.b, r.b, thr, bln, ibln);
     R half = (R)0.5;
     R rm = half * (l.r + r.r);
     R bm = half * (l.b + r.b);

@@ -9,31 +9,45 @@
 // read consecutive nodes.
 #pragma once
 
+#include <type_traits>
+
 #include "esmm_device.cuh"
 #include "esmm_launch.h"
 
 namespace esmm {
 
+// One flux argument: the FP64 log-mean arguments from q and the working
+// values from q (FP64) or from the FP32 copies q32 (float).
 template <typename R>
-__device__ __forceinline__ NodeV<R> load_node(const Geom &g, const double *__restrict__ q, long long c)
+__device__ __forceinline__ NodeV<R> load_node(const Geom &g, const double *__restrict__ q,
+                                              const float *__restrict__ q32, long long c)
 {
     NodeV<R> v;
     v.rho = q[Q_RHO * g.P + c];
     v.beta = q[Q_BETA * g.P + c];
     v.lnr = q[Q_LNR * g.P + c];
     v.lnb = q[Q_LNB * g.P + c];
-    v.r = (R)v.rho;
-    v.b = (R)v.beta;
-    v.ux = (R)q[Q_UX * g.P + c];
-    v.uy = (R)q[Q_UY * g.P + c];
-    v.W = (R)q[Q_W * g.P + c];
+    if constexpr (std::is_same<R, float>::value) {
+        v.r = q32[Q32_R * g.P + c];
+        v.b = q32[Q32_B * g.P + c];
+        v.ux = q32[Q32_UX * g.P + c];
+        v.uy = q32[Q32_UY * g.P + c];
+        v.W = q32[Q32_W * g.P + c];
+    } else {
+        v.r = (R)v.rho;
+        v.b = (R)v.beta;
+        v.ux = (R)q[Q_UX * g.P + c];
+        v.uy = (R)q[Q_UY * g.P + c];
+        v.W = (R)q[Q_W * g.P + c];
+    }
     return v;
 }
 
 // The ES dissipation 1/2 lambda^ T^-1 R Y <<V~>> of eq. ESFlux_HO at one
 // interface (to be subtracted from the EC flux).  nvx, nvy, jt: the interface
 // metrics (mean of the two nodes); rho0/1, lnr0/1: density and its log at the
-// two interface nodes (the log-mean arguments); st[k] = (beta, u_x, u_y, W,
+// two interface nodes (the log-mean arguments), r0/1 the densities in the
+// working precision; st[k] = (beta, u_x, u_y, W,
 // ln rho, ln beta) of the w + 1 stencil nodes, the interface nodes at
 // k = (w-1)/2 and (w+1)/2.  The eigen-system is taken at rho = {{rho}}^ln,
 // u = {{u}}, p = {{rho}}/{{beta}}; Y has sign 0 for jumps at rounding level.
@@ -50,6 +64,18 @@ struct QStencil {
     }
 };
 
+// the same from the FP32 copies (the mixed form)
+struct QStencil32 {
+    const float *q;
+    long long P, c0, sd;
+    int off;
+    __device__ __forceinline__ float operator()(int k, int j) const
+    {
+        const int f = j == 0 ? Q32_B : (j == 1 ? Q32_UX : (j == 2 ? Q32_UY : (j == 3 ? Q32_W : (j == 4 ? Q32_LNR : Q32_LNB))));
+        return q[f * P + c0 + (k - off) * sd];
+    }
+};
+
 // stencil values held in an array (the adjoint's seeded duals)
 template <typename R, int NS>
 struct ArrStencil {
@@ -58,7 +84,7 @@ struct ArrStencil {
 };
 
 template <typename R, typename T, int WW, typename ST>
-__device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho1, T lnr0, T lnr1,
+__device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho1, T lnr0, T lnr1, R r0, R r1,
                                                const ST &st, const Phys &ph, R diss[4])
 {
     constexpr int NS = WW + 1, OFF = (WW - 1) / 2;
@@ -69,10 +95,10 @@ __device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho
     R Lk = n2 * iLk;
     R nx = nvx * iLk, ny = nvy * iLk;
     R rho, irho;
-    logmean<R, T>(rho0, rho1, lnr0, lnr1, ph.ln_thr, rho, irho);
+    lmean<R, T>(rho0, rho1, lnr0, lnr1, r0, r1, ph.ln_thr, rho, irho);
     R ux = half * (st(OFF, 1) + st(OFF + 1, 1));
     R uy = half * (st(OFF, 2) + st(OFF + 1, 2));
-    R p = ((R)rho0 + (R)rho1) * rcp<R>(st(OFF, 0) + st(OFF + 1, 0));
+    R p = (r0 + r1) * rcp<R>(st(OFF, 0) + st(OFF + 1, 0));
     R w2 = one + ux * ux + uy * uy;
     R iW = rsq<R>(w2);
     R W = w2 * iW;
@@ -135,13 +161,15 @@ __device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho
 // anchors A in [-P, n_dir - 1] along the sweep, every line of the other index
 template <typename R, int P>
 __global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double *__restrict__ q,
-                                               R *__restrict__ pairs, int dir)
+                                               const float *__restrict__ q32, R *__restrict__ pairs, int dir)
 {
+    constexpr bool F32 = std::is_same<R, float>::value;
     ProbDesc D;
     long long lb;
     locate(pa, D, lb);
     const Geom &g = D.g;
     q += (long long)NQ * D.op;
+    if (F32) q32 += (long long)NQ32 * D.op;
     pairs += (long long)2 * PMAX * 4 * D.op;
     const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
     const long long count = (long long)(nd + P) * no;
@@ -152,19 +180,28 @@ __global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double
     else { i = (int)(idx % no); j = (int)(idx / no) - P; }
     const long long c0 = pidx(g, i, j);
     const long long sd = dir == 0 ? 1 : g.px;
-    const double *Mt = q + (Q_MT0 + dir) * g.P;
-    const double *Mx = q + (Q_M00 + 2 * dir) * g.P;
-    const double *My = q + (Q_M01 + 2 * dir) * g.P;
+    // metrics in the working precision: FP64 node arrays or their FP32 copies
+    using MT = typename std::conditional<F32, float, double>::type;
+    const MT *Mt, *Mx, *My;
+    if constexpr (F32) {
+        Mt = q32 + (Q32_MT0 + dir) * g.P;
+        Mx = q32 + (Q32_M00 + 2 * dir) * g.P;
+        My = q32 + (Q32_M01 + 2 * dir) * g.P;
+    } else {
+        Mt = q + (Q_MT0 + dir) * g.P;
+        Mx = q + (Q_M00 + 2 * dir) * g.P;
+        My = q + (Q_M01 + 2 * dir) * g.P;
+    }
     const R gm1inv = (R)(1.0 / (ph.gamma - 1.0));
-    NodeV<R> l = load_node<R>(g, q, c0);
-    const double mtl = Mt[c0], mxl = Mx[c0], myl = My[c0];
+    NodeV<R> l = load_node<R>(g, q, q32, c0);
+    const MT mtl = Mt[c0], mxl = Mx[c0], myl = My[c0];
 #pragma unroll
     for (int n = 1; n <= P; ++n) {
         const long long cr = c0 + n * sd;
-        NodeV<R> r = load_node<R>(g, q, cr);
-        R mt = (R)(0.5 * (mtl + Mt[cr]));
-        R mx = (R)(0.5 * (mxl + Mx[cr]));
-        R my = (R)(0.5 * (myl + My[cr]));
+        NodeV<R> r = load_node<R>(g, q, q32, cr);
+        R mt = (R)((MT)0.5 * (mtl + Mt[cr]));
+        R mx = (R)((MT)0.5 * (mxl + Mx[cr]));
+        R my = (R)((MT)0.5 * (myl + My[cr]));
         R out[4];
         ec_pair<R>(l, r, mt, mx, my, gm1inv, ph.ln_thr, out);
 #pragma unroll
@@ -176,13 +213,17 @@ __global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double
 // interfaces between left node L in [-1, n_dir - 1] and L + 1
 template <typename R, int P, int WW>
 __global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double *__restrict__ q,
-                                               const R *__restrict__ pairs, R *__restrict__ iflux, int dir)
+                                               const float *__restrict__ q32, const R *__restrict__ pairs,
+                                               R *__restrict__ iflux, int dir)
 {
+    constexpr bool F32 = std::is_same<R, float>::value;
+    using MT = typename std::conditional<F32, float, double>::type;
     ProbDesc D;
     long long lb;
     locate(pa, D, lb);
     const Geom &g = D.g;
     q += (long long)NQ * D.op;
+    if (F32) q32 += (long long)NQ32 * D.op;
     pairs += (long long)2 * PMAX * 4 * D.op;
     iflux += (long long)2 * 5 * D.op;
     const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
@@ -194,39 +235,55 @@ __global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double
     else { i = (int)(idx % no); j = (int)(idx / no) - 1; }
     const long long c0 = pidx(g, i, j);
     const long long sd = dir == 0 ? 1 : g.px;
-    const double *Mt = q + (Q_MT0 + dir) * g.P;
+    // metrics in the working precision: FP64 node arrays or their FP32 copies
+    const MT *Mt, *Mx, *My;
+    if constexpr (F32) {
+        Mt = q32 + (Q32_MT0 + dir) * g.P;
+        Mx = q32 + (Q32_M00 + 2 * dir) * g.P;
+        My = q32 + (Q32_M01 + 2 * dir) * g.P;
+    } else {
+        Mt = q + (Q_MT0 + dir) * g.P;
+        Mx = q + (Q_M00 + 2 * dir) * g.P;
+        My = q + (Q_M01 + 2 * dir) * g.P;
+    }
 
     // eq. ECFlux_O2p: sum_n alpha_{p,n} sum_{s<n} F~(A - s, A - s + n)
     R F[4] = {(R)0, (R)0, (R)0, (R)0};
-    double Ft = 0.0;
+    MT Ft = (MT)0;
 #pragma unroll
     for (int n = 1; n <= P; ++n) {
         R Fs[4] = {(R)0, (R)0, (R)0, (R)0};
-        double Fts = 0.0;
+        MT Fts = (MT)0;
 #pragma unroll
         for (int s = 0; s < n; ++s) {
             const long long ca = c0 - s * sd;
             const R *pr = pairs + ((long long)(dir * PMAX + (n - 1)) * 4) * g.P + ca;
 #pragma unroll
             for (int a = 0; a < 4; ++a) Fs[a] += pr[a * g.P];
-            Fts += 0.5 * (Mt[ca] + Mt[ca + n * sd]);
+            Fts += (MT)0.5 * (Mt[ca] + Mt[ca + n * sd]);
         }
         const R an = (R)ph.alpha[n - 1];
 #pragma unroll
         for (int a = 0; a < 4; ++a) F[a] += an * Fs[a];
-        Ft += ph.alpha[n - 1] * Fts;
+        Ft += (MT)ph.alpha[n - 1] * Fts;
     }
 
     if (WW > 0) {
         // eq. ESFlux_HO: subtract 1/2 lambda^ T^-1 R Y <<V~>>
-        const double *Mx = q + (Q_M00 + 2 * dir) * g.P;
-        const double *My = q + (Q_M01 + 2 * dir) * g.P;
         const long long c1 = c0 + sd;
-        QStencil<R> st{q, g.P, c0, sd, (WW - 1) / 2};
+        const R nvx = (R)((MT)0.5 * (Mx[c0] + Mx[c1])), nvy = (R)((MT)0.5 * (My[c0] + My[c1]));
+        const R jt = (R)((MT)0.5 * (Mt[c0] + Mt[c1]));
+        const double rho0 = q[Q_RHO * g.P + c0], rho1 = q[Q_RHO * g.P + c1];
+        const double lnr0 = q[Q_LNR * g.P + c0], lnr1 = q[Q_LNR * g.P + c1];
         R diss[4];
-        es_dissipation<R, double, WW>((R)(0.5 * (Mx[c0] + Mx[c1])), (R)(0.5 * (My[c0] + My[c1])),
-                                      (R)(0.5 * (Mt[c0] + Mt[c1])), q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1],
-                                      q[Q_LNR * g.P + c0], q[Q_LNR * g.P + c1], st, ph, diss);
+        if constexpr (F32) {
+            QStencil32 st{q32, g.P, c0, sd, (WW - 1) / 2};
+            es_dissipation<R, double, WW>(nvx, nvy, jt, rho0, rho1, lnr0, lnr1, q32[Q32_R * g.P + c0],
+                                          q32[Q32_R * g.P + c1], st, ph, diss);
+        } else {
+            QStencil<R> st{q, g.P, c0, sd, (WW - 1) / 2};
+            es_dissipation<R, double, WW>(nvx, nvy, jt, rho0, rho1, lnr0, lnr1, (R)rho0, (R)rho1, st, ph, diss);
+        }
 #pragma unroll
         for (int a = 0; a < 4; ++a) F[a] -= diss[a];
     }
@@ -237,50 +294,52 @@ __global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double
 }
 
 template <typename R, int P>
-static void launch_pairs_p(const LaunchDom &L, const Phys &ph, const double *q, R *pairs, int dir, cudaStream_t st)
+static void launch_pairs_p(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, R *pairs, int dir,
+                           cudaStream_t st)
 {
-    k_pairs<R, P><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, pairs, dir);
+    k_pairs<R, P><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, q32, pairs, dir);
 }
 
 template <typename R, int P, int WW>
-static void launch_iface_pw(const LaunchDom &L, const Phys &ph, const double *q, const R *pairs, R *iflux,
-                            int dir, cudaStream_t st)
+static void launch_iface_pw(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const R *pairs,
+                            R *iflux, int dir, cudaStream_t st)
 {
-    k_iface<R, P, WW><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, pairs, iflux, dir);
+    k_iface<R, P, WW><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, q32, pairs, iflux, dir);
 }
 
 template <typename R>
-void launch_pairs_t(const LaunchDom &L, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st)
+void launch_pairs_t(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, void *pairs, int dir,
+                    cudaStream_t st)
 {
     R *pr = (R *)pairs;
     switch (ph.p) {
-    case 1: launch_pairs_p<R, 1>(L, ph, q, pr, dir, st); break;
-    case 2: launch_pairs_p<R, 2>(L, ph, q, pr, dir, st); break;
-    default: launch_pairs_p<R, 3>(L, ph, q, pr, dir, st); break;
+    case 1: launch_pairs_p<R, 1>(L, ph, q, q32, pr, dir, st); break;
+    case 2: launch_pairs_p<R, 2>(L, ph, q, q32, pr, dir, st); break;
+    default: launch_pairs_p<R, 3>(L, ph, q, q32, pr, dir, st); break;
     }
 }
 
 template <typename R, int P>
-static void launch_iface_p(const LaunchDom &L, const Phys &ph, const double *q, const R *pr, R *fl, int dir,
-                           cudaStream_t st)
+static void launch_iface_p(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const R *pr, R *fl,
+                           int dir, cudaStream_t st)
 {
     switch (ph.w) {
-    case 0: launch_iface_pw<R, P, 0>(L, ph, q, pr, fl, dir, st); break;
-    case 3: launch_iface_pw<R, P, 3>(L, ph, q, pr, fl, dir, st); break;
-    default: launch_iface_pw<R, P, 5>(L, ph, q, pr, fl, dir, st); break;
+    case 0: launch_iface_pw<R, P, 0>(L, ph, q, q32, pr, fl, dir, st); break;
+    case 3: launch_iface_pw<R, P, 3>(L, ph, q, q32, pr, fl, dir, st); break;
+    default: launch_iface_pw<R, P, 5>(L, ph, q, q32, pr, fl, dir, st); break;
     }
 }
 
 template <typename R>
-void launch_iface_t(const LaunchDom &L, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
-                    cudaStream_t st)
+void launch_iface_t(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const void *pairs,
+                    void *iflux, int dir, cudaStream_t st)
 {
     const R *pr = (const R *)pairs;
     R *fl = (R *)iflux;
     switch (ph.p) {
-    case 1: launch_iface_p<R, 1>(L, ph, q, pr, fl, dir, st); break;
-    case 2: launch_iface_p<R, 2>(L, ph, q, pr, fl, dir, st); break;
-    default: launch_iface_p<R, 3>(L, ph, q, pr, fl, dir, st); break;
+    case 1: launch_iface_p<R, 1>(L, ph, q, q32, pr, fl, dir, st); break;
+    case 2: launch_iface_p<R, 2>(L, ph, q, q32, pr, fl, dir, st); break;
+    default: launch_iface_p<R, 3>(L, ph, q, q32, pr, fl, dir, st); break;
     }
 }
 

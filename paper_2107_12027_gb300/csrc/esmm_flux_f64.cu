@@ -3,15 +3,16 @@
 
 namespace esmm {
 
-void launch_pairs_f64(const LaunchDom &L, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st)
+void launch_pairs_f64(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, void *pairs, int dir,
+                      cudaStream_t st)
 {
-    launch_pairs_t<double>(L, ph, q, pairs, dir, st);
+    launch_pairs_t<double>(L, ph, q, q32, pairs, dir, st);
 }
 
-void launch_iface_f64(const LaunchDom &L, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
-                       cudaStream_t st)
+void launch_iface_f64(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const void *pairs,
+                      void *iflux, int dir, cudaStream_t st)
 {
-    launch_iface_t<double>(L, ph, q, pairs, iflux, dir, st);
+    launch_iface_t<double>(L, ph, q, q32, pairs, iflux, dir, st);
 }
 
 }  // namespace esmm

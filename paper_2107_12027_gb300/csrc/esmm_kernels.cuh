@@ -58,12 +58,14 @@ __device__ __forceinline__ void mesh_deltas(const Geom &g, const double *__restr
 // when given), W, u = W v, beta = rho/p, ln rho, ln beta, the CMM metrics and
 // the temporal metrics J xi_k,t = -xdot . (J xi_k,x) (eq. VCLCoeff).  Ghost
 // nodes take the data of their boundary source node and metrics of the
-// boundary-mapped mesh, so the flux kernels need no boundary logic.
+// boundary-mapped mesh, so the flux kernels need no boundary logic.  With
+// q32 (the mixed form) the node also writes the FP32 copies the flux kernels
+// read.
 template <int P>
 __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
                        const double *__restrict__ x, const double *__restrict__ xdot,
                        const double *__restrict__ pg_in, double *__restrict__ pg_out, double *__restrict__ q,
-                       int *__restrict__ status)
+                       int *__restrict__ status, float *__restrict__ q32 = nullptr)
 {
     ProbDesc D;
     long long lb;
@@ -83,14 +85,13 @@ __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, 
     double iJ = __drcp_rn(J[src]);
     double Dd = cons[src] * iJ, mx = cons[g.N + src] * iJ, my = cons[2 * g.N + src] * iJ,
            E = cons[3 * g.N + src] * iJ;
-    double rho, vx, vy, p;
-    int st = cons2prim(gam, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p);
+    double rho, vx, vy, p, W;
+    int st = cons2prim(gam, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p, W);
     bool interior = I >= 0 && I < g.nx && Jn >= 0 && Jn < g.ny;
     if (interior) {
         if (st) atomicAdd(status, 1);
         if (pg_out) pg_out[src] = p;
     }
-    double W = rsqrt(1.0 - (vx * vx + vy * vy));
     double beta = rho * __drcp_rn(p);
     q[Q_RHO * g.P + t] = rho;
     q[Q_P * g.P + t] = p;
@@ -109,12 +110,31 @@ __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, 
     q[Q_M11 * g.P + t] = M11;
     double xd = 0.0, yd = 0.0;
     if (xdot) { xd = mesh_at(g, xdot, I, Jn, 0, 0); yd = mesh_at(g, xdot, I, Jn, 1, 0); }
-    q[Q_MT0 * g.P + t] = -(xd * M00 + yd * M01);
-    q[Q_MT1 * g.P + t] = -(xd * M10 + yd * M11);
+    const double MT0 = -(xd * M00 + yd * M01), MT1 = -(xd * M10 + yd * M11);
+    q[Q_MT0 * g.P + t] = MT0;
+    q[Q_MT1 * g.P + t] = MT1;
+    if (q32) {
+        q32 += (long long)NQ32 * D.op;
+        q32[Q32_R * g.P + t] = (float)rho;
+        q32[Q32_B * g.P + t] = (float)beta;
+        q32[Q32_UX * g.P + t] = (float)(W * vx);
+        q32[Q32_UY * g.P + t] = (float)(W * vy);
+        q32[Q32_W * g.P + t] = (float)W;
+        q32[Q32_LNR * g.P + t] = (float)q[Q_LNR * g.P + t];
+        q32[Q32_LNB * g.P + t] = (float)q[Q_LNB * g.P + t];
+        q32[Q32_M00 * g.P + t] = (float)M00;
+        q32[Q32_M01 * g.P + t] = (float)M01;
+        q32[Q32_M10 * g.P + t] = (float)M10;
+        q32[Q32_M11 * g.P + t] = (float)M11;
+        q32[Q32_MT0 * g.P + t] = (float)MT0;
+        q32[Q32_MT1 * g.P + t] = (float)MT1;
+    }
 }
 
-// temporal metrics only (the spatial ones and the state are unchanged)
-__global__ void k_tmetric(ProbArg pa, const double *__restrict__ xdot, double *__restrict__ q)
+// temporal metrics only (the spatial ones and the state are unchanged), and
+// their FP32 copies when q32 is given
+__global__ void k_tmetric(ProbArg pa, const double *__restrict__ xdot, double *__restrict__ q,
+                          float *__restrict__ q32 = nullptr)
 {
     ProbDesc D;
     long long lb;
@@ -126,8 +146,15 @@ __global__ void k_tmetric(ProbArg pa, const double *__restrict__ xdot, double *_
     q += (long long)NQ * D.op;
     int I = (int)(t % g.px) - GH, Jn = (int)(t / g.px) - GH;
     double xd = mesh_at(g, xdot, I, Jn, 0, 0), yd = mesh_at(g, xdot, I, Jn, 1, 0);
-    q[Q_MT0 * g.P + t] = -(xd * q[Q_M00 * g.P + t] + yd * q[Q_M01 * g.P + t]);
-    q[Q_MT1 * g.P + t] = -(xd * q[Q_M10 * g.P + t] + yd * q[Q_M11 * g.P + t]);
+    const double MT0 = -(xd * q[Q_M00 * g.P + t] + yd * q[Q_M01 * g.P + t]);
+    const double MT1 = -(xd * q[Q_M10 * g.P + t] + yd * q[Q_M11 * g.P + t]);
+    q[Q_MT0 * g.P + t] = MT0;
+    q[Q_MT1 * g.P + t] = MT1;
+    if (q32) {
+        q32 += (long long)NQ32 * D.op;
+        q32[Q32_MT0 * g.P + t] = (float)MT0;
+        q32[Q32_MT1 * g.P + t] = (float)MT1;
+    }
 }
 
 // d/dt = -sum_k (F_k(i + 1/2) - F_k(i - 1/2)) (eqs. RMHDSemiU_O2p_ES,
@@ -156,9 +183,12 @@ __global__ void k_update(ProbArg pa, const R *__restrict__ fl, double *__restric
     double L[5];
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-        double d0 = (double)f0[a * g.P + c] - (double)f0[a * g.P + c - 1];
-        double d1 = (double)f1[a * g.P + c] - (double)f1[a * g.P + c - g.px];
-        L[a] = -(d0 + d1);
+        // the differences in the fluxes' own precision (an FP32 difference
+        // of two FP32 fluxes is exact when they are within a factor 2 and
+        // rounds once otherwise), summed in FP64
+        R d0 = f0[a * g.P + c] - f0[a * g.P + c - 1];
+        R d1 = f1[a * g.P + c] - f1[a * g.P + c - g.px];
+        L[a] = -((double)d0 + (double)d1);
     }
     if (dcons) {
         dcons += 4 * D.on;
@@ -179,11 +209,54 @@ __global__ void k_update(ProbArg pa, const R *__restrict__ fl, double *__restric
     xo[g.N + id] = A * xn[g.N + id] + B * (xs[g.N + id] + dt * xdot[g.N + id]);
 }
 
+// the spectral radius of k_cfl in FP32 (mixed form): with p = rho/beta,
+// c^2 = Gamma p / (rho h) = Gamma / (beta + Gamma/(Gamma-1))
+__device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const float *__restrict__ q32,
+                                        const double *__restrict__ J, unsigned long long *red)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    q32 += (long long)NQ32 * D.op;
+    J += D.on;
+    double r[2] = {0.0, 0.0};
+    if (id < g.N) {
+        int i = (int)(id % g.nx), j = (int)(id / g.nx);
+        long long c = pidx(g, i, j);
+        float W = q32[Q32_W * g.P + c], beta = q32[Q32_B * g.P + c];
+        float iW = __frcp_rn(W);
+        float vx = q32[Q32_UX * g.P + c] * iW, vy = q32[Q32_UY * g.P + c] * iW;
+        float v2 = vx * vx + vy * vy;
+        float c2 = gam * __frcp_rn(beta + gam / (gam - 1.0f)), cs = sqrtf(c2);
+        float iJ = __frcp_rn((float)J[id]);
+        float iden = __frcp_rn(1.0f - v2 * c2);
+        for (int k = 0; k < 2; ++k) {
+            float mx = q32[(Q32_M00 + 2 * k) * g.P + c], my = q32[(Q32_M01 + 2 * k) * g.P + c];
+            float n2 = mx * mx + my * my, iL = rsqrtf(n2), Lk = n2 * iL;
+            float vn = (mx * vx + my * vy) * iL;
+            float disc = sqrtf(fmaxf((1.0f - v2) * (1.0f - v2 * c2 - vn * vn * (1.0f - c2)), 0.0f));
+            float lm = (vn * (1.0f - c2) - cs * disc) * iden, lp = (vn * (1.0f - c2) + cs * disc) * iden;
+            r[k] = (double)(Lk * fmaxf(fabsf(lm), fabsf(lp)) * iJ);
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        double m = block_reduce<0>(r[k]);
+        if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b + 2 + k, m);
+    }
+}
+
+
 // spectral radius rho_k = L_k max |lambda_+-| / J at every node (eq. cfl,
 // static mesh), reduced to a per-problem maximum per direction
 __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
-                      unsigned long long *red)
+                      unsigned long long *red, const float *__restrict__ q32)
 {
+    if (q32) {   // the mixed form: the same speeds in FP32 from the FP32 node copies
+        cfl_f32(pa, (float)gam, q32, J, red);
+        return;
+    }
     ProbDesc D;
     long long lb;
     int b = locate(pa, D, lb);
@@ -199,7 +272,7 @@ __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, cons
         double iW = __drcp_rn(W);
         double vx = q[Q_UX * g.P + c] * iW, vy = q[Q_UY * g.P + c] * iW;
         double v2 = vx * vx + vy * vy;
-        double rh = rho + gam * p / (gam - 1.0);
+        double rh = rho + p * (gam / (gam - 1.0));
         double c2 = gam * p * __drcp_rn(rh), cs = sqrt(c2);
         double iJ = __drcp_rn(J[id]);
         for (int k = 0; k < 2; ++k) {
@@ -300,14 +373,18 @@ __global__ void k_mesh_omega(ProbArg pa, double alpha, double alpha_lap, const d
     int b = locate(pa, D, lb);
     const Geom &g = D.g;
     long long id = lb * blockDim.x + threadIdx.x;
-    if (id >= g.N) return;
-    double gmax = bits_to_double(red[(long long)NRED * b]);
-    double a = 1.0;
-    if (gmax > 0.0) a += alpha * grad[D.on + id] / gmax;
-    if (alpha_lap > 0.0) {
+    // alpha / max, once per block
+    __shared__ double sc[2];
+    if (threadIdx.x == 0) {
+        double gmax = bits_to_double(red[(long long)NRED * b]);
         double lmax = bits_to_double(red[(long long)NRED * b + 6]);
-        if (lmax > 0.0) a += alpha_lap * lap[D.on + id] / lmax;
+        sc[0] = gmax > 0.0 ? alpha / gmax : 0.0;
+        sc[1] = (alpha_lap > 0.0 && lmax > 0.0) ? alpha_lap / lmax : 0.0;
     }
+    __syncthreads();
+    if (id >= g.N) return;
+    double a = 1.0 + sc[0] * grad[D.on + id];
+    if (sc[1] > 0.0) a += sc[1] * lap[D.on + id];
     om[D.on + id] = sqrt(a);
 }
 
@@ -324,17 +401,20 @@ __global__ void k_mesh_filter(ProbArg pa, const double *__restrict__ om, double 
     om2 += D.on;
     int i = (int)(id % g.nx), j = (int)(id / g.nx);
     double acc = 0.0;
+    const bool inner = i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1;
     for (int bb = -1; bb <= 1; ++bb)
         for (int a = -1; a <= 1; ++a) {
             double wgt = (a == 0 && bb == 0) ? 0.25 : ((a == 0 || bb == 0) ? 0.125 : 0.0625);
-            acc += wgt * om[data_src(g, i + a, j + bb)];
+            acc += wgt * om[inner ? id + bb * g.nx + a : data_src(g, i + a, j + bb)];
         }
     om2[id] = acc;
 }
 
-// one Jacobi sweep of the Winslow mesh equations with omega frozen
-__global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ om, const double *__restrict__ X,
-                              double *__restrict__ Xn)
+// The weights of the Jacobi iteration of the Winslow mesh equations with
+// omega frozen: X_i <- sum_k c_k X_k over the four neighbours (E, W, N, S),
+// c_k = (omega_i + omega_k) / sum_k' (omega_i + omega_k').  Computed once per
+// redistribution (the sweeps then take four FMAs per component).
+__global__ void k_mesh_weights(ProbArg pa, const double *__restrict__ om, double *__restrict__ cw)
 {
     ProbDesc D;
     long long lb;
@@ -343,6 +423,47 @@ __global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ om, const d
     long long id = lb * blockDim.x + threadIdx.x;
     if (id >= g.N) return;
     om += D.on;
+    cw += 4 * D.on;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    double wi = om[id];
+    double we = om[data_src(g, i + 1, j)], ww = om[data_src(g, i - 1, j)];
+    double wn = om[data_src(g, i, j + 1)], ws = om[data_src(g, i, j - 1)];
+    double iden = __drcp_rn((2.0 * wi + we + ww) + (2.0 * wi + wn + ws));
+    cw[id] = (wi + we) * iden;
+    cw[g.N + id] = (wi + ww) * iden;
+    cw[2 * g.N + id] = (wi + wn) * iden;
+    cw[3 * g.N + id] = (wi + ws) * iden;
+}
+
+// mesh_at with the shift for coordinates, out of line (edge paths)
+__device__ __noinline__ double mesh_edge(const Geom &g, const double *__restrict__ x, int i, int j, int comp)
+{
+    return mesh_at(g, x, i, j, comp, 1);
+}
+
+// the Jacobi update of a node next to the boundary (neighbours through the
+// boundary mapping); kept out of line so that the interior path does not
+// evaluate the ghost arithmetic
+__device__ __noinline__ void jacobi_edge(const Geom &g, const double *__restrict__ X, int i, int j, double ce,
+                                         double cwe, double cn, double cs, double *out)
+{
+    for (int comp = 0; comp < 2; ++comp)
+        out[comp] = ce * mesh_at(g, X, i + 1, j, comp, 1) + cwe * mesh_at(g, X, i - 1, j, comp, 1) +
+                    cn * mesh_at(g, X, i, j + 1, comp, 1) + cs * mesh_at(g, X, i, j - 1, comp, 1);
+}
+
+// one Jacobi sweep with the weights of k_mesh_weights; the boundary nodes of
+// an outflow direction stay
+__global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ cw, const double *__restrict__ X,
+                              double *__restrict__ Xn)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    cw += 4 * D.on;
     X += 2 * D.on;
     Xn += 2 * D.on;
     int i = (int)(id % g.nx), j = (int)(id / g.nx);
@@ -352,14 +473,17 @@ __global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ om, const d
         Xn[g.N + id] = X[g.N + id];
         return;
     }
-    double wi = om[id];
-    double we = om[data_src(g, i + 1, j)], ww = om[data_src(g, i - 1, j)];
-    double wn = om[data_src(g, i, j + 1)], ws = om[data_src(g, i, j - 1)];
-    double iden = __drcp_rn((2.0 * wi + we + ww) + (2.0 * wi + wn + ws));
-    for (int comp = 0; comp < 2; ++comp) {
-        double num = (wi + we) * mesh_at(g, X, i + 1, j, comp, 1) + (wi + ww) * mesh_at(g, X, i - 1, j, comp, 1) +
-                     (wi + wn) * mesh_at(g, X, i, j + 1, comp, 1) + (wi + ws) * mesh_at(g, X, i, j - 1, comp, 1);
-        Xn[comp * g.N + id] = num * iden;
+    const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
+    if (i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1) {
+        for (int comp = 0; comp < 2; ++comp) {
+            const double *a = X + comp * g.N + id;
+            Xn[comp * g.N + id] = ce * a[1] + cwe * a[-1] + cn * a[g.nx] + cs * a[-g.nx];
+        }
+    } else {
+        double out[2];
+        jacobi_edge(g, X, i, j, ce, cwe, cn, cs, out);
+        Xn[id] = out[0];
+        Xn[g.N + id] = out[1];
     }
 }
 
@@ -387,14 +511,20 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const doubl
             double d = X[k * g.N + id] - x[k * g.N + id];
             dd[k] = d;
             int di = k == 0, dj = k == 1;
+            const bool inner = k == 0 ? (i > 0 && i < g.nx - 1) : (j > 0 && j < g.ny - 1);
+            const long long step = k == 0 ? 1 : g.nx;
             double bnd = 1.0;
-            if (d < 0.0) bnd = -(x[k * g.N + id] - mesh_at(g, x, i - di, j - dj, k, 1)) / (2.0 * d);
-            else if (d > 0.0) bnd = (mesh_at(g, x, i + di, j + dj, k, 1) - x[k * g.N + id]) / (2.0 * d);
+            if (d != 0.0) {
+                const double xi = x[k * g.N + id];
+                const double xb = inner ? x[k * g.N + id + (d < 0.0 ? -step : step)]
+                                        : mesh_edge(g, x, d < 0.0 ? i - di : i + di, d < 0.0 ? j - dj : j + dj, k);
+                bnd = (xb - xi) * __drcp_rn(2.0 * d);
+            }
             tau = fmin(tau, bnd);
         }
         tau = fmax(tau, 0.0);
         long long c = pidx(g, i, j);
-        double iJ = 1.0 / J[id];
+        double iJ = __drcp_rn(J[id]);
         for (int k = 0; k < 2; ++k)
             cm[k] = fabs(dd[0] * q[(Q_M00 + 2 * k) * g.P + c] + dd[1] * q[(Q_M01 + 2 * k) * g.P + c]) * iJ;
     }
@@ -416,10 +546,12 @@ __global__ void k_mesh_xdot(ProbArg pa, const double *__restrict__ x, const doub
     int b = locate(pa, D, lb);
     const Geom &g = D.g;
     long long id = lb * blockDim.x + threadIdx.x;
+    __shared__ double s;
+    if (threadIdx.x == 0) s = bits_to_double(red[(long long)NRED * b + 1]) / dt_dev[b];
+    __syncthreads();
     if (id >= 2 * g.N) return;
-    double tau = bits_to_double(red[(long long)NRED * b + 1]);
     long long o = 2 * D.on + id;
-    xdot[o] = tau * (X[o] - x[o]) / dt_dev[b];
+    xdot[o] = s * (X[o] - x[o]);
 }
 
 // ---- state set-up and read-out ------------------------------------------------
@@ -470,9 +602,9 @@ __global__ void k_prim_out(ProbArg pa, double gam, const double *__restrict__ co
     J += D.on;
     prim += 4 * D.on;
     double iJ = 1.0 / J[id];
-    double rho, vx, vy, p;
+    double rho, vx, vy, p, W;
     int st = cons2prim(gam, cons[id] * iJ, cons[g.N + id] * iJ, cons[2 * g.N + id] * iJ, cons[3 * g.N + id] * iJ,
-                       -1.0, rho, vx, vy, p);
+                       -1.0, rho, vx, vy, p, W);
     if (st) atomicAdd(status, 1);
     prim[id] = rho;
     prim[g.N + id] = vx;

@@ -20,14 +20,17 @@ struct LaunchDom {
 struct Phys;
 
 // Pair fluxes of direction dir; pairs holds PMAX * 4 * 2 arrays of P elements
-// of the working precision (double or float).
-void launch_pairs_f64(const LaunchDom &L, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st);
-void launch_pairs_f32(const LaunchDom &L, const Phys &ph, const double *q, void *pairs, int dir, cudaStream_t st);
+// of the working precision (double or float).  q32: the FP32 copies of the
+// node arrays ([NQ32][P]), read by the float kernels (unused by the FP64 ones).
+void launch_pairs_f64(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, void *pairs, int dir,
+                      cudaStream_t st);
+void launch_pairs_f32(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, void *pairs, int dir,
+                      cudaStream_t st);
 // Interface fluxes (4 components + metric flux) of direction dir.
-void launch_iface_f64(const LaunchDom &L, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
-                      cudaStream_t st);
-void launch_iface_f32(const LaunchDom &L, const Phys &ph, const double *q, const void *pairs, void *iflux, int dir,
-                      cudaStream_t st);
+void launch_iface_f64(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const void *pairs,
+                      void *iflux, int dir, cudaStream_t st);
+void launch_iface_f32(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const void *pairs,
+                      void *iflux, int dir, cudaStream_t st);
 
 // Adjoint (esmm_adjoint.cu): local Jacobian-vector products of the pair and
 // interface fluxes against the node adjoint mu ([4][N]) of d(cons)/dt, written

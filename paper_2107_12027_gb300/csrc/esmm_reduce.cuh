@@ -24,24 +24,64 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// OP: 0 max, 1 min, 2 sum; the result is valid in thread 0.  Every thread of
-// the block must call it.
+// Max and min of non-negative values on their bit patterns (which order like
+// the values), on the integer pipes rather than the FP64 one.  A NaN is
+// ignored (as fmax/fmin would), a negative value counts as 0.
+__device__ __forceinline__ unsigned long long ord_bits(double v, bool for_min)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) return for_min ? 0x7ff0000000000000ull : 0ull;
+    return (b >> 63) ? 0ull : b;
+}
+__device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_min_bits(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// OP: 0 max, 1 min (of non-negative values, min capped at 1e300), 2 sum; the
+// result is valid in thread 0.  Every thread of the block must call it.
 template <int OP>
 __device__ double block_reduce(double v)
 {
-    __shared__ double sh[32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = OP == 0 ? warp_max(v) : (OP == 1 ? warp_min(v) : warp_sum(v));
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
     int nw = (blockDim.x + 31) >> 5;
+    if (OP == 2) {
+        __shared__ double sh[32];
+        v = warp_sum(v);
+        if (lane == 0) sh[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            v = lane < nw ? sh[lane] : 0.0;
+            v = warp_sum(v);
+        }
+        __syncthreads();
+        return v;
+    }
+    __shared__ unsigned long long shb[32];
+    const unsigned long long init = OP == 0 ? 0ull : (unsigned long long)__double_as_longlong(1.0e300);
+    unsigned long long b = ord_bits(v, OP == 1);
+    if (OP == 1 && b > init) b = init;
+    b = OP == 0 ? warp_max_bits(b) : warp_min_bits(b);
+    if (lane == 0) shb[wid] = b;
+    __syncthreads();
     if (wid == 0) {
-        double init = OP == 0 ? 0.0 : (OP == 1 ? 1.0e300 : 0.0);
-        v = lane < nw ? sh[lane] : init;
-        v = OP == 0 ? warp_max(v) : (OP == 1 ? warp_min(v) : warp_sum(v));
+        b = lane < nw ? shb[lane] : init;
+        b = OP == 0 ? warp_max_bits(b) : warp_min_bits(b);
     }
     __syncthreads();
-    return v;
+    return __longlong_as_double((long long)b);
 }
 
 // Non-negative doubles order like their bit patterns, so the max/min of such
