@@ -145,6 +145,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def job_time_ms(total_ms, world, dist, device):
+    """The job's time over the timed steps: the slowest rank's (a max
+    all-reduce over the ranks; the only collective of a multi-rank run)."""
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(nodes_per_rank, steps, world, job_ms):
+    """Whole-job cell-updates per second per RK stage: every rank advances
+    its own problem of nodes_per_rank nodes (weak scaling)."""
+    return world * nodes_per_rank * 3 * steps / (job_ms * 1e-3)
+
+
 def workload(n, rank=0):
     from paper_2107_12027_gb300 import workloads as wl
     return wl.riemann_config(n, offset=1 + rank)
@@ -395,12 +411,10 @@ def run_gpu(args):
     nfail, msg = g.last_error()
     if nfail:
         raise RuntimeError("primitive recovery failed at %d nodes: %s" % (nfail, msg))
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    total_ms = job_time_ms(total_ms, world, dist, "cuda")
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    total_ms = float(t.item())
-    value = world * n * n * 3 * K / (total_ms * 1e-3)
+    value = job_rate(n * n, K, world, total_ms)
     launches = int(sum(v[1] for v in prof.values()))
     g.close()
     if rank != 0:
