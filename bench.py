@@ -138,6 +138,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="nodes per side (default per workload)")
     ap.add_argument("--workload", default="riemann", choices=["riemann", "rotor", "blast3d"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and mixed-form legs")
+    ap.add_argument("--study", default=None, choices=["um-mm"],
+                    help="um-mm: the efficiency of MM-O5 against UM-O5 on the Sec. 6 problems (one JSON line per run)")
+    ap.add_argument("--problems", default="rp1,rp2,rp3,blast", help="problems of --study um-mm")
     return ap.parse_args()
 
 
@@ -632,8 +635,115 @@ def run_rmhd(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- UM-O5 vs MM-O5
+# The paper's efficiency claim (Sec. 6, Table 6.1 and the Riemann problem
+# figures): MM-O5 on a coarse adaptive mesh resolves what UM-O5 needs a much
+# finer static mesh for, at a fraction of the cost.  Each problem runs MM-O5
+# and UM-O5 at the paper's coarse size, UM-O5 at the paper's fine size, and
+# UM-O5 finer still as the reference (for the blast the fine run itself, as
+# in the paper's comparison); every run is timed on the GPU (wall
+# time of the whole run, synchronised) and its final ln rho is compared with
+# the reference's on a common 400 x 400 sample grid and along the cut line
+# of the paper's figures (x_2 = x_1 for the Riemann problems, x_2 = 0 for the
+# blast), as L1 means.
+STUDY = {   # problem: (sizes (MM-O5, UM-O5 coarse, UM-O5 fine, reference), final time)
+    "rp1": ((200, 200, 500, 1000), 0.4),
+    "rp2": ((200, 200, 500, 1000), 0.4),
+    "rp3": ((200, 200, 500, 1000), 0.4),
+    "blast": ((150, 150, 600, 600), 4.0),   # the fine run is the reference (as in the paper's comparison)
+}
+
+
+def study_grid(problem, n, scheme):
+    from paper_2107_12027_gb300 import esmm
+    from paper_2107_12027_gb300 import workloads as wl
+    if problem == "blast":
+        x, prim = wl.rmhd_blast2_config(n)
+        g = esmm.Grid((n, n), (-6.0, -6.0), (6.0, 6.0), bc=(esmm.OUTFLOW, esmm.OUTFLOW), gamma=4.0 / 3.0,
+                      phys=esmm.RMHD, scheme=scheme, cfl=0.4, alpha=800.0, monitor=esmm.MONITOR_LNRHO)
+    else:
+        x, prim = wl.rhd_rp_config(int(problem[2]), n)
+        g = esmm.Grid((n, n), (0.0, 0.0), (1.0, 1.0), bc=(esmm.OUTFLOW, esmm.OUTFLOW), gamma=5.0 / 3.0,
+                      scheme=scheme, cfl=0.4, alpha=1200.0, monitor=esmm.MONITOR_LNRHO)
+    g.state_set(prim, x)
+    return g
+
+
+def study_run(torch, problem, n, scheme, t_end):
+    """Advance to t_end (CFL steps, the last one cut to land on t_end); return
+    (final nodes, final ln rho, steps, seconds)."""
+    from paper_2107_12027_gb300 import esmm
+    g = study_grid(problem, n, scheme)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, t = 0, 0.0
+    while t_end - t > 1e-12 * t_end:
+        rest = t_end - t
+        dt = g.rk_step(rest if rest <= 0.9 * g.cfl_dt() else 0.0)
+        steps += 1
+        t = g.time()
+        if steps > 200000:
+            raise RuntimeError("study run did not reach t_end")
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nfail, msg = g.last_error()
+    x, prim = g.state_get(esmm.GET_X), g.state_get(esmm.GET_PRIM)
+    g.close()
+    if nfail:
+        raise RuntimeError("primitive recovery failed at %d nodes: %s" % (nfail, msg))
+    return x, np.log(prim[0]), steps, sec
+
+
+def study_sample(x, f, pts, uniform=False):
+    """f (given at the nodes x) at the points pts [2][...] (linear
+    interpolation: on the grid's axes when uniform, else on the Delaunay
+    triangulation of the nodes)."""
+    from scipy.interpolate import RegularGridInterpolator, griddata
+    if uniform:
+        f_ = RegularGridInterpolator((x[1][:, 0], x[0][0, :]), f)
+        return f_(np.stack([pts[1].ravel(), pts[0].ravel()], axis=1)).reshape(pts.shape[1:])
+    return griddata((x[0].ravel(), x[1].ravel()), f.ravel(), (pts[0], pts[1]), method="linear")
+
+
+def study_points(problem, lo, hi, m=400, mc=1000):
+    s = lo + (hi - lo) * (np.arange(m) + 0.5) / m
+    Y, X = np.meshgrid(s, s, indexing="ij")
+    c = lo + (hi - lo) * (np.arange(mc) + 0.5) / mc
+    cut = np.stack([c, 0.0 * c]) if problem == "blast" else np.stack([c, c])
+    return np.stack([X, Y]), cut
+
+
+def run_study(args):
+    import torch
+    from paper_2107_12027_gb300 import esmm
+    esmm.lib()
+    for problem in args.problems.split(","):
+        (n_mm, n_um, n_fine, n_ref), t_end = STUDY[problem]
+        lo, hi = (-6.0, 6.0) if problem == "blast" else (0.0, 1.0)
+        grid, cut = study_points(problem, lo, hi)
+        xr, fr, steps, sec = study_run(torch, problem, n_ref, "UM-O5", t_end)
+        ref, ref_c = study_sample(xr, fr, grid, uniform=True), study_sample(xr, fr, cut, uniform=True)
+        line = {"study": "um-mm", "problem": problem, "scheme": "UM-O5", "n": n_ref, "t": t_end, "steps": steps,
+                "seconds": sec, "role": "reference"}
+        print(json.dumps(line), flush=True)
+        for scheme, n in (("MM-O5", n_mm), ("UM-O5", n_um), ("UM-O5", n_fine)):
+            if scheme == "UM-O5" and n == n_ref:
+                continue
+            x, f, steps, sec = study_run(torch, problem, n, scheme, t_end)
+            got = study_sample(x, f, grid, uniform=scheme == "UM-O5")
+            got_c = study_sample(x, f, cut, uniform=scheme == "UM-O5")
+            print(json.dumps({"study": "um-mm", "problem": problem, "scheme": scheme, "n": n, "t": t_end,
+                              "steps": steps, "seconds": sec,
+                              "l1_lnrho_vs_ref": float(np.nanmean(np.abs(got - ref))),
+                              "l1_lnrho_cut_vs_ref": float(np.nanmean(np.abs(got_c - ref_c))),
+                              "ref": "UM-O5 %d" % n_ref}), flush=True)
+
+
 def main():
     args = parse()
+    if args.study:
+        run_study(args)
+        return
     if args.workload != "riemann":
         run_rmhd(args)
         return

@@ -25,6 +25,26 @@ MONITOR_RHO, MONITOR_LNRHO = 0, 1
 GET_PRIM, GET_CONS, GET_J, GET_X, GET_XDOT = 0, 1, 2, 3, 4
 _ERR = {1: "ESMM_ERR_ARG", 2: "ESMM_ERR_CUDA", 3: "ESMM_ERR_C2P", 4: "ESMM_ERR_TIMEOUT", 5: "ESMM_ERR_STATE"}
 
+#: The paper's named schemes (Sec. 6): EC flux order 2p, WENO order w of the
+#: ES dissipation (0: the EC scheme alone) and whether the mesh adapts.
+SCHEMES = {
+    "MM-O6": dict(p=3, w=0, move_mesh=1),   # sixth-order EC on the moving mesh
+    "MM-O5": dict(p=3, w=5, move_mesh=1),   # fifth-order ES, adaptive moving mesh
+    "UM-O6": dict(p=3, w=0, move_mesh=0),   # the EC scheme on the static mesh
+    "UM-O5": dict(p=3, w=5, move_mesh=0),   # the ES scheme on the static mesh
+}
+
+
+def _apply_scheme(scheme, p, w, params):
+    """(p, w) of a named scheme (or the given ones), with its mesh switch put
+    into params unless the caller set move_mesh."""
+    if scheme is None:
+        return p, w
+    s = SCHEMES[scheme]
+    params.setdefault("move_mesh", s["move_mesh"])
+    return s["p"], s["w"]
+
+
 #: every entry point declared in include/esmm.h
 SYMBOLS = (
     "esmm_grid_create", "esmm_grid_destroy", "esmm_set_stream", "esmm_set_eos", "esmm_set_order",
@@ -166,7 +186,8 @@ class Grid:
     ABI plus argument marshalling."""
 
     def __init__(self, n, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC), gamma=5.0 / 3.0, p=2, w=5,
-                 stream=None, phys=RHD, **params):
+                 stream=None, phys=RHD, scheme=None, **params):
+        p, w = _apply_scheme(scheme, p, w, params)
         self.nx, self.ny = int(n[0]), int(n[1])
         self.N = self.nx * self.ny
         self.phys = phys
@@ -394,7 +415,8 @@ class Grid3(Grid):
     state components and 3 mesh components."""
 
     def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC, PERIODIC, PERIODIC),
-                 gamma=4.0 / 3.0, p=2, w=5, stream=None, **params):
+                 gamma=4.0 / 3.0, p=2, w=5, stream=None, scheme=None, **params):
+        p, w = _apply_scheme(scheme, p, w, params)
         self.nx, self.ny, self.nz = int(n[0]), int(n[1]), int(n[2])
         self.N = self.nx * self.ny * self.nz
         self.phys, self.nv = RMHD, 8
@@ -493,7 +515,8 @@ class Batch(Grid):
     sizes: [(nx, ny), ...]; lo, hi, bc: one pair per problem or one shared."""
 
     def __init__(self, sizes, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC), gamma=5.0 / 3.0, p=2, w=5,
-                 stream=None, **params):
+                 stream=None, scheme=None, **params):
+        p, w = _apply_scheme(scheme, p, w, params)
         self.sizes = [(int(a), int(b)) for a, b in sizes]
         self.phys, self.nv = RHD, 4
         B = len(self.sizes)

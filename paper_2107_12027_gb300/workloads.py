@@ -429,3 +429,42 @@ def rmhd_vortex3(x, t=0.0, R=5.0, gamma=5.0 / 3.0, sigma=0.2, B0=0.05):
     v = [(4.0 * vt[0] + vt[1] - 3.0) / den, (4.0 * vt[1] + vt[0] - 3.0) / den, (vt[0] + vt[1] - 3.0) / den]
     B = [(5.0 * Bt[0] - Bt[1]) / 3.0, (5.0 * Bt[1] - Bt[0]) / 3.0, -(Bt[0] + Bt[1]) / 3.0]
     return np.ascontiguousarray(np.stack([rho, v[0], v[1], v[2], p, B[0], B[1], B[2]]))
+
+
+# ---- the paper's 2D RHD Riemann problems I-III (Sec. 6) --------------------
+# Initial data on [0,1]^2 split at x_1 = x_2 = 0.5, in the quadrant order of
+# quadrant_riemann: q = (x_1 > 0.5) + 2 (x_2 > 0.5), rows (rho, v_1, v_2, p).
+# Gamma = 5/3 (the section's default), outflow boundaries, t = 0.4.
+RHD_RP_STATES = {
+    1: ((3.0, -0.5, 0.5, 5.0), (1.5, -0.5, -0.5, 5.0),        # four contact discontinuities
+        (1.0, 0.5, 0.5, 5.0), (0.5, 0.5, -0.5, 5.0)),
+    2: ((1.0, -0.3529, -0.3529, 1.0), (0.5771, 0.0, -0.3529, 0.4),   # four rarefactions
+        (0.5771, -0.3529, 0.0, 0.4), (1.0, 0.0, 0.0, 1.0)),
+    3: ((0.5, 0.0, 0.0, 1.0), (0.1, 0.0, 0.7, 1.0),           # two contacts, two shocks
+        (0.1, 0.7, 0.0, 1.0), (0.035145216124503, 0.0, 0.0, 0.162931056509027)),
+}
+
+
+def rhd_rp_config(k, n):
+    """Riemann problem k (1, 2 or 3) of Sec. 6 on n x n nodes of [0,1]^2
+    (outflow: nodes on both ends)."""
+    x = uniform_mesh(n, n, (0.0, 0.0), (1.0, 1.0), (False, False))
+    return x, quadrant_riemann(x, np.array(RHD_RP_STATES[k]), split=(0.5, 0.5))
+
+
+def rmhd_blast2(x, r_in=0.8, r_out=1.0, rho_in=1e-2, p_in=1.0, rho_out=1e-4, p_out=5e-4, Bx=0.1):
+    """The 2D RMHD blast of Sec. 6: the explosion zone r < 0.8 (rho = 0.01,
+    p = 1), the ambient medium r > 1 (rho = 1e-4, p = 5e-4), a linear taper
+    of rho and p in between, at rest, B = (0.1, 0, 0); Gamma = 4/3."""
+    r = np.hypot(x[0], x[1])
+    s = np.clip((r - r_in) / (r_out - r_in), 0.0, 1.0)       # 0 inside, 1 outside
+    rho = rho_in + s * (rho_out - rho_in)
+    p = p_in + s * (p_out - p_in)
+    z = 0.0 * r
+    return np.ascontiguousarray(np.stack([rho, z, z, z, p, Bx + z, z, z]))
+
+
+def rmhd_blast2_config(n):
+    """The 2D RMHD blast on n x n nodes of [-6,6]^2 with outflow boundaries."""
+    x = uniform_mesh(n, n, (-6.0, -6.0), (6.0, 6.0), (False, False))
+    return x, rmhd_blast2(x)

@@ -32,3 +32,19 @@ def test_binding_rejects_wrong_array_types():
         esmm._ptr(np.zeros(4, dtype=np.float32))
     with pytest.raises(AssertionError):
         esmm._ptr(np.zeros((4, 4))[:, ::2])
+
+
+def test_named_schemes_host_logic():
+    # Sec. 6: MM-O6 is the sixth-order (p = 3) EC scheme, MM-O5 the ES scheme
+    # with WENO5 dissipation on the 2p = 6 EC flux; UM-* are the same on the
+    # static mesh
+    from paper_2107_12027_gb300 import esmm
+    assert esmm.SCHEMES["MM-O6"] == dict(p=3, w=0, move_mesh=1)
+    assert esmm.SCHEMES["MM-O5"] == dict(p=3, w=5, move_mesh=1)
+    assert esmm.SCHEMES["UM-O5"] == dict(p=3, w=5, move_mesh=0)
+    prm = {}
+    assert esmm._apply_scheme("UM-O5", 2, 3, prm) == (3, 5) and prm == {"move_mesh": 0}
+    prm = {"move_mesh": 1}
+    assert esmm._apply_scheme("UM-O5", 2, 3, prm) == (3, 5) and prm == {"move_mesh": 1}
+    prm = {}
+    assert esmm._apply_scheme(None, 2, 3, prm) == (2, 3) and prm == {}
