@@ -54,6 +54,11 @@ extern "C" {
 #define ESMM_PERIODIC 0     /* boundary: periodic (mesh shifted by the period) */
 #define ESMM_OUTFLOW 1      /* boundary: zero-gradient data, fixed boundary
                                nodes, linearly extrapolated mesh ghosts        */
+#define ESMM_INFLOW 2       /* boundary: the ghosts beyond the LOW end of the
+                               direction hold the state of esmm_set_inflow (the
+                               inflow boundary of the shock-cloud examples of
+                               Sec. 6); the high end is ESMM_OUTFLOW; the mesh
+                               treats both ends as outflow ends              */
 
 #define ESMM_MEM_HOST 0
 #define ESMM_MEM_DEVICE 1
@@ -94,7 +99,7 @@ typedef struct {
 /* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim 2, phys ESMM_RHD or
  * ESMM_RMHD), or of n[0] x n[1] x n[2] nodes (dim 3, phys ESMM_RMHD: the
  * nested metrics of eq. SCLCoeff, FP64; defaults Gamma = 4/3, CFL 0.3,
- * alpha = 800), bc[k] ESMM_PERIODIC or ESMM_OUTFLOW, n[k] >= 4.  3D grids
+ * alpha = 800), bc[k] ESMM_PERIODIC, ESMM_OUTFLOW or ESMM_INFLOW, n[k] >= 4.  3D grids
  * accept the single-problem calls, the adjoint and profiling; batches, the
  * tuner and ESMM_MIXED return ESMM_ERR_ARG for them (RMHD 2D grids take
  * ESMM_MIXED and, in FP64, the adjoint; batches are RHD).  A periodic
@@ -162,6 +167,13 @@ int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, 
  * synchronises and writes the step used.  A recovery failure is reported by
  * esmm_last_error / the next synchronising call. */
 int esmm_rk_step(esmm_grid *g, double dt, double *dt_used);
+/* The primitive state prim[m] (host array; m = 4 for 2D RHD, 8 for RMHD:
+ * rho, v, p (, B)) held by the ghost nodes beyond every ESMM_INFLOW end.  A
+ * grid with an inflow end returns ESMM_ERR_STATE from every call that
+ * evaluates the scheme until this is set; ESMM_ERR_ARG for rho <= 0, p <= 0
+ * or |v| >= 1.  The adjoint calls return ESMM_ERR_ARG for grids with an
+ * inflow end (the adjoint covers periodic and outflow ends). */
+int esmm_set_inflow(esmm_grid *g, const double *prim);
 /* One time step with a prescribed mesh motion (the given-mesh runs of the
  * vortex examples of Sec. 6): the caller's mesh velocity xdot [d][N] (host or
  * device per mem, d = 2 or 3) is held over the step, the mesh of stage s is

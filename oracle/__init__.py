@@ -27,7 +27,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, INFLOW = 0, 1, 2
 MONITOR_RHO, MONITOR_LNRHO = 0, 1
 RHD, RMHD = 0, 1
 
@@ -48,6 +48,7 @@ class Cfg(ctypes.Structure):
         ("move_mesh", ctypes.c_int),
         ("phys", ctypes.c_int),
         ("alpha_lap", ctypes.c_double),
+        ("inflow", ctypes.c_double * 8),
     ]
 
 
@@ -66,6 +67,7 @@ class Cfg3(ctypes.Structure):
         ("mu", ctypes.c_int),
         ("move_mesh", ctypes.c_int),
         ("alpha_lap", ctypes.c_double),
+        ("inflow", ctypes.c_double * 8),
     ]
 
 
@@ -160,7 +162,7 @@ def _vec(a, n=None):
 
 def make_cfg(nx, ny, bc=(PERIODIC, PERIODIC), period=(1.0, 1.0), gamma=5.0 / 3.0,
              p=2, w=5, weno_eps=1e-6, cfl=0.4, monitor=MONITOR_LNRHO, alpha=20.0,
-             n_filter=4, mu=10, move_mesh=1, phys=RHD, alpha_lap=0.0) -> Cfg:
+             n_filter=4, mu=10, move_mesh=1, phys=RHD, alpha_lap=0.0, inflow=None) -> Cfg:
     c = Cfg()
     c.nx, c.ny = nx, ny
     c.bc[0], c.bc[1] = bc
@@ -168,6 +170,8 @@ def make_cfg(nx, ny, bc=(PERIODIC, PERIODIC), period=(1.0, 1.0), gamma=5.0 / 3.0
     c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
     c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
     c.phys, c.alpha_lap = phys, alpha_lap
+    for a, v in enumerate(inflow if inflow is not None else ()):
+        c.inflow[a] = v
     return c
 
 
@@ -418,7 +422,7 @@ def mhd_eigen(gamma, w_rot):
 # ---- 3D RMHD grid functions --------------------------------------------------
 def make_cfg3(nx, ny, nz, bc=(PERIODIC, PERIODIC, PERIODIC), period=(1.0, 1.0, 1.0), gamma=4.0 / 3.0,
               p=2, w=5, weno_eps=1e-6, cfl=0.3, monitor=MONITOR_LNRHO, alpha=800.0, n_filter=4, mu=10,
-              move_mesh=1, alpha_lap=0.0) -> Cfg3:
+              move_mesh=1, alpha_lap=0.0, inflow=None) -> Cfg3:
     c = Cfg3()
     c.nx, c.ny, c.nz = nx, ny, nz
     for k in range(3):
@@ -427,6 +431,8 @@ def make_cfg3(nx, ny, nz, bc=(PERIODIC, PERIODIC, PERIODIC), period=(1.0, 1.0, 1
     c.gamma, c.p, c.w, c.weno_eps, c.cfl = gamma, p, w, weno_eps, cfl
     c.monitor, c.alpha, c.n_filter, c.mu, c.move_mesh = monitor, alpha, n_filter, mu, move_mesh
     c.alpha_lap = alpha_lap
+    for a, v in enumerate(inflow if inflow is not None else ()):
+        c.inflow[a] = v
     return c
 
 

@@ -558,7 +558,8 @@ static int build_pad(const oref_cfg *c, const double *cons, const double *J,
     for (int j = -G; j < ny + G; ++j)
         for (int i = -G; i < nx + G; ++i) {
             int id = pad_index(P, i, j), src = data_index(c, i, j);
-            for (int a = 0; a < nv; ++a) P->prim[a * S + id] = w[a * N + src];
+            int in = (c->bc[0] == OREF_INFLOW && i < 0) || (c->bc[1] == OREF_INFLOW && j < 0);
+            for (int a = 0; a < nv; ++a) P->prim[a * S + id] = in ? c->inflow[a] : w[a * N + src];
             double M[2][2];
             node_metrics(c, x, i, j, M);
             P->M[0 * S + id] = M[0][0];
@@ -902,6 +903,15 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
  * so that by the triangle inequality dt sum_k max_i rho_{k,i}(xdot) <= CFL
  * holds with xdot = d/dt.  A given dt > 0 is used as is (Delta tau capped
  * the same way).  *dt_out receives the step.                                */
+/* sigma at node (i, j) of the index space, ghosts included: the inflow
+ * state's beyond an inflow end (the data the scheme's fluxes see there), else
+ * the boundary-mapped node's */
+static double sigma_at(const oref_cfg *c, const double *sig, double sig_in, int i, int j)
+{
+    if ((c->bc[0] == OREF_INFLOW && i < 0) || (c->bc[1] == OREF_INFLOW && j < 0)) return sig_in;
+    return sig[data_index(c, i, j)];
+}
+
 int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double *om)
 {
     int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
@@ -912,11 +922,12 @@ int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double 
         if (node_prim(c, cons, J, id, w) != 0) status = -1;
         sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
     }
+    double sig_in = (c->monitor == OREF_MONITOR_LNRHO) ? log(c->inflow[0]) : c->inflow[0];
     double gmax = 0.0, lmax = 0.0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
-            double e = sig[data_index(c, i + 1, j)], wv = sig[data_index(c, i - 1, j)];
-            double n = sig[data_index(c, i, j + 1)], s = sig[data_index(c, i, j - 1)];
+            double e = sigma_at(c, sig, sig_in, i + 1, j), wv = sigma_at(c, sig, sig_in, i - 1, j);
+            double n = sigma_at(c, sig, sig_in, i, j + 1), s = sigma_at(c, sig, sig_in, i, j - 1);
             double gx = 0.5 * (e - wv), gy = 0.5 * (n - s);
             double g = sqrt(gx * gx + gy * gy);
             double l = fabs(e + wv + n + s - 4.0 * sig[j * nx + i]);
@@ -968,8 +979,8 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 int id = j * nx + i;
-                int fixed = (c->bc[0] == OREF_OUTFLOW && (i == 0 || i == nx - 1)) ||
-                            (c->bc[1] == OREF_OUTFLOW && (j == 0 || j == ny - 1));
+                int fixed = (c->bc[0] != OREF_PERIODIC && (i == 0 || i == nx - 1)) ||
+                            (c->bc[1] != OREF_PERIODIC && (j == 0 || j == ny - 1));
                 if (fixed) {
                     Xn[id] = X[id];
                     Xn[N + id] = X[N + id];

@@ -25,13 +25,18 @@
 extern "C" {
 #endif
 
-enum { OREF_PERIODIC = 0, OREF_OUTFLOW = 1 };
+/* OREF_INFLOW: the ghost data beyond the low end of that direction take the
+ * fixed primitive state cfg.inflow (the inflow boundary of the shock-cloud
+ * examples of Sec. 6); the high end is outflow, and the mesh treats both ends
+ * as outflow ends (extrapolated ghosts, fixed boundary nodes). */
+enum { OREF_PERIODIC = 0, OREF_OUTFLOW = 1, OREF_INFLOW = 2 };
 enum { OREF_MONITOR_RHO = 0, OREF_MONITOR_LNRHO = 1 };
 enum { OREF_RHD = 0, OREF_RMHD = 1 };
 
 typedef struct {
     int nx, ny;
-    int bc[2];            /* per direction: OREF_PERIODIC or OREF_OUTFLOW     */
+    int bc[2];            /* per direction: OREF_PERIODIC, OREF_OUTFLOW or
+                             OREF_INFLOW                                      */
     double period[2];     /* physical period added to x (or y) across a
                              periodic boundary                              */
     double gamma;         /* ideal-gas adiabatic index, 1 < gamma <= 2        */
@@ -47,6 +52,7 @@ typedef struct {
     int phys;             /* OREF_RHD (4 unknowns) or OREF_RMHD (8 unknowns)  */
     double alpha_lap;     /* strength of the monitor's Laplacian term (the
                              vortex examples of Sec. 6; 0: eq. monitor)     */
+    double inflow[8];     /* primitive inflow state (OREF_INFLOW ends)        */
 } oref_cfg;
 
 /* Sec. 3.2, constraint eq. HOCoeff: alpha_{p,1..p}. */
@@ -159,6 +165,7 @@ typedef struct {
     int mu;
     int move_mesh;
     double alpha_lap;
+    double inflow[8];
 } oref3_cfg;
 
 /* eq. SCLCoeff (nested CMM) and J0 = det(delta_k[x_j]) */

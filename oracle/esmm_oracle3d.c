@@ -195,7 +195,9 @@ static int build_pad3(const oref3_cfg *c, const double *cons, const double *J, c
         for (int j = -G3; j < c->ny + G3; ++j)
             for (int i = -G3; i < c->nx + G3; ++i) {
                 long id = pidx3(P, i, j, k), src = data_index3(c, i, j, k);
-                for (int a = 0; a < 8; ++a) P->prim[a * P->S + id] = w[a * N + src];
+                int in = (c->bc[0] == OREF_INFLOW && i < 0) || (c->bc[1] == OREF_INFLOW && j < 0) ||
+                         (c->bc[2] == OREF_INFLOW && k < 0);
+                for (int a = 0; a < 8; ++a) P->prim[a * P->S + id] = in ? c->inflow[a] : w[a * N + src];
                 double M[3][3];
                 node_metrics3(c, x, i, j, k, M);
                 for (int a = 0; a < 3; ++a)
@@ -500,6 +502,16 @@ int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const 
  * boundary nodes, "(x_1)" read as x_k).                                     */
 /* Sec. 5 monitor (and the Laplacian term of the 3D vortex example), before
  * the low-pass filter; the 3D form of oref_monitor. */
+/* sigma at a node of the index space, ghosts included (see sigma_at of the
+ * 2D oracle) */
+static double sigma_at3(const oref3_cfg *c, const double *sig, double sig_in, int i, int j, int k)
+{
+    if ((c->bc[0] == OREF_INFLOW && i < 0) || (c->bc[1] == OREF_INFLOW && j < 0) ||
+        (c->bc[2] == OREF_INFLOW && k < 0))
+        return sig_in;
+    return sig[data_index3(c, i, j, k)];
+}
+
 int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, double *om)
 {
     long N = (long)c->nx * c->ny * c->nz;
@@ -511,14 +523,15 @@ int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, doubl
         if (node_prim3(c, cons, J, id, w) != 0) status = -1;
         sig[id] = (c->monitor == OREF_MONITOR_LNRHO) ? log(w[0]) : w[0];
     }
+    double sig_in = (c->monitor == OREF_MONITOR_LNRHO) ? log(c->inflow[0]) : c->inflow[0];
     double gmax = 0.0, lmax = 0.0;
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
                 long id = ((long)k * c->ny + j) * c->nx + i;
-                double xp = sig[data_index3(c, i + 1, j, k)], xm = sig[data_index3(c, i - 1, j, k)];
-                double yp = sig[data_index3(c, i, j + 1, k)], ym = sig[data_index3(c, i, j - 1, k)];
-                double zp = sig[data_index3(c, i, j, k + 1)], zm = sig[data_index3(c, i, j, k - 1)];
+                double xp = sigma_at3(c, sig, sig_in, i + 1, j, k), xm = sigma_at3(c, sig, sig_in, i - 1, j, k);
+                double yp = sigma_at3(c, sig, sig_in, i, j + 1, k), ym = sigma_at3(c, sig, sig_in, i, j - 1, k);
+                double zp = sigma_at3(c, sig, sig_in, i, j, k + 1), zm = sigma_at3(c, sig, sig_in, i, j, k - 1);
                 double gx = 0.5 * (xp - xm), gy = 0.5 * (yp - ym), gz = 0.5 * (zp - zm);
                 double g = sqrt(gx * gx + gy * gy + gz * gz);
                 double l = fabs(xp + xm + yp + ym + zp + zm - 6.0 * sig[id]);
@@ -575,9 +588,9 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
             for (int j = 0; j < c->ny; ++j)
                 for (int i = 0; i < c->nx; ++i) {
                     long id = ((long)k * c->ny + j) * c->nx + i;
-                    int fixed = (c->bc[0] == OREF_OUTFLOW && (i == 0 || i == c->nx - 1)) ||
-                                (c->bc[1] == OREF_OUTFLOW && (j == 0 || j == c->ny - 1)) ||
-                                (c->bc[2] == OREF_OUTFLOW && (k == 0 || k == c->nz - 1));
+                    int fixed = (c->bc[0] != OREF_PERIODIC && (i == 0 || i == c->nx - 1)) ||
+                                (c->bc[1] != OREF_PERIODIC && (j == 0 || j == c->ny - 1)) ||
+                                (c->bc[2] != OREF_PERIODIC && (k == 0 || k == c->nz - 1));
                     if (fixed) {
                         for (int comp = 0; comp < 3; ++comp) Xn[comp * N + id] = X[comp * N + id];
                         continue;

@@ -82,7 +82,7 @@ template <int P>
 __global__ void k3_node(Geom3 g, double gam, const double *__restrict__ cons, const double *__restrict__ J,
                         const double *__restrict__ xe, const double *__restrict__ xdot,
                         const double *__restrict__ zg_in, double *__restrict__ zg_out, double *__restrict__ q,
-                        int *__restrict__ status)
+                        int *__restrict__ status, const double *__restrict__ inflow)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.P) return;
@@ -94,7 +94,14 @@ __global__ void k3_node(Geom3 g, double gam, const double *__restrict__ cons, co
     double U[8], w[8], Z;
 #pragma unroll
     for (int a = 0; a < 8; ++a) U[a] = cons[a * g.N + src] * iJ;
-    int st = cons2prim_mhd(gam, U, zg_in ? zg_in[src] : -1.0, w, Z);
+    int st = 0;
+    if (inflow && ((g.bc[0] == 2 && I < 0) || (g.bc[1] == 2 && Jn < 0) || (g.bc[2] == 2 && K < 0))) {
+        // a ghost beyond an inflow end: the given state
+        for (int a = 0; a < 8; ++a) w[a] = inflow[a];
+        Z = 0.0;
+    } else {
+        st = cons2prim_mhd(gam, U, zg_in ? zg_in[src] : -1.0, w, Z);
+    }
     bool interior = I >= 0 && I < g.n[0] && Jn >= 0 && Jn < g.n[1] && K >= 0 && K < g.n[2];
     if (interior) {
         if (st) atomicAdd(status, 1);
@@ -328,8 +335,8 @@ __global__ void k3_mesh_jacobi(Geom3 g, const double *__restrict__ om, const dou
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= g.N) return;
     int i = (int)(id % g.n[0]), j = (int)((id / g.n[0]) % g.n[1]), k = (int)(id / ((long long)g.n[0] * g.n[1]));
-    bool fixed = (g.bc[0] == 1 && (i == 0 || i == g.n[0] - 1)) || (g.bc[1] == 1 && (j == 0 || j == g.n[1] - 1)) ||
-                 (g.bc[2] == 1 && (k == 0 || k == g.n[2] - 1));
+    bool fixed = (g.bc[0] != 0 && (i == 0 || i == g.n[0] - 1)) || (g.bc[1] != 0 && (j == 0 || j == g.n[1] - 1)) ||
+                 (g.bc[2] != 0 && (k == 0 || k == g.n[2] - 1));
     if (fixed) {
         for (int comp = 0; comp < 3; ++comp) Xn[comp * g.N + id] = X[comp * g.N + id];
         return;
@@ -481,6 +488,8 @@ struct esmm3 {
     esmm_params prm;
     cudaStream_t st;
     int has_state, xdot_zero;
+    int needs_inflow, has_inflow;
+    double *inflow_dev;        // [8] primitive inflow state (ESMM_INFLOW ends)
     double *cons, *J, *x, *xdot, *c1, *J1, *x1, *c2, *J2, *x2;
     double *q, *zg[3], *iflux, *out_dc, *out_dJ, *in_cons, *in_J, *in_x, *in_xdot;
     double *grad, *om, *om2, *X, *Xn, *dt_dev, *t_dev, *partials, *tot;
@@ -571,15 +580,16 @@ void node3(esmm3 *g, const double *cons, const double *J, const double *x, const
     unsigned nb = nb3(g->g.P), nbe = nb3(ext_count3(g->g));
     Prof3 pr_(g, ESMM_KIND_NODE, 2);
     double *xe = g->xe;
+    const double *in = g->has_inflow ? g->inflow_dev : nullptr;
     if (g->p == 1) {
         k3_dx<1><<<nbe, BS3, 0, g->st>>>(g->g, x, xe);
-        k3_node<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status);
+        k3_node<1><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status, in);
     } else if (g->p == 2) {
         k3_dx<2><<<nbe, BS3, 0, g->st>>>(g->g, x, xe);
-        k3_node<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status);
+        k3_node<2><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status, in);
     } else {
         k3_dx<3><<<nbe, BS3, 0, g->st>>>(g->g, x, xe);
-        k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status);
+        k3_node<3><<<nb, BS3, 0, g->st>>>(g->g, g->gamma, cons, J, xe, xdot, zi, zo, g->q, g->status, in);
     }
 }
 
@@ -685,7 +695,8 @@ void free3(esmm3 *g)
     double **b[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2, &g->q,
                     &g->zg[0], &g->zg[1], &g->zg[2], &g->iflux, &g->out_dc, &g->out_dJ, &g->in_cons, &g->in_J,
                     &g->in_x, &g->in_xdot, &g->grad, &g->om, &g->om2, &g->X, &g->Xn, &g->dt_dev, &g->t_dev,
-                    &g->partials, &g->tot, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v, &g->lamq, &g->xe};
+                    &g->partials, &g->tot, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v, &g->lamq, &g->xe,
+                    &g->inflow_dev};
     for (double **p : b)
         if (*p) { cudaFree(*p); *p = nullptr; }
     if (g->ck) {
@@ -768,7 +779,8 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
 {
     *out = nullptr;
     for (int k = 0; k < 3; ++k)
-        if (n[k] < 4 || n[k] > 4096 || (bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW) || !(hi[k] > lo[k]))
+        if (n[k] < 4 || n[k] > 4096 || (bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW && bc[k] != ESMM_INFLOW) ||
+            !(hi[k] > lo[k]))
             return ESMM_ERR_ARG;
     esmm3 *g = new (std::nothrow) esmm3;
     if (!g) return ESMM_ERR_ARG;
@@ -777,6 +789,7 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
         g->g.n[k] = n[k];
         g->g.pd[k] = n[k] + 2 * GH;
         g->g.bc[k] = bc[k];
+        if (bc[k] == ESMM_INFLOW) g->needs_inflow = 1;
         g->g.per[k] = hi[k] - lo[k];
         g->lo[k] = lo[k];
         g->hi[k] = hi[k];
@@ -804,7 +817,8 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
         {&g->zg[0], N}, {&g->zg[1], N}, {&g->zg[2], N}, {&g->iflux, (size_t)3 * NF3 * P}, {&g->out_dc, 8 * N},
         {&g->out_dJ, N}, {&g->in_cons, 8 * N}, {&g->in_J, N}, {&g->in_x, 3 * N}, {&g->in_xdot, 3 * N},
         {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->X, 3 * N}, {&g->Xn, 3 * N}, {&g->dt_dev, 1},
-        {&g->t_dev, 1}, {&g->partials, 3 * nb}, {&g->tot, 3}, {&g->xe, (size_t)NXE * ext_count3(g->g)}};
+        {&g->t_dev, 1}, {&g->partials, 3 * nb}, {&g->tot, 3}, {&g->xe, (size_t)NXE * ext_count3(g->g)},
+        {&g->inflow_dev, 8}};
     bool ok = true;
     for (auto &a : al) ok = ok && cudaMalloc((void **)a.p, a.n * d) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&g->red, NR3 * sizeof(unsigned long long)) == cudaSuccess &&
@@ -943,11 +957,27 @@ int esmm3_get_time(esmm3 *g, double *t)
     return ESMM_OK;
 }
 
+// every call that runs a node pass: an inflow end needs its state
+static int inflow_ok3(esmm3 *g)
+{
+    return g->needs_inflow && !g->has_inflow ? fail3(g, ESMM_ERR_STATE, "an inflow end without an inflow state")
+                                             : ESMM_OK;
+}
+
+int esmm3_set_inflow(esmm3 *g, const double *prim)
+{
+    CK3(cudaMemcpyAsync(g->inflow_dev, prim, 8 * sizeof(double), cudaMemcpyHostToDevice, g->st));
+    CK3(cudaStreamSynchronize(g->st));
+    g->has_inflow = 1;
+    return ESMM_OK;
+}
+
 int esmm3_rhs(esmm3 *g, const double *cons, const double *J, const double *x, const double *xdot, double *dcons,
               double *dJ, int mem)
 {
     size_t N = (size_t)g->g.N;
     int rc;
+    if ((rc = inflow_ok3(g))) return rc;
     if (mem == ESMM_MEM_HOST) {
         if ((rc = copy3(g, g->in_cons, cons, 8 * N, mem, true)) || (rc = copy3(g, g->in_J, J, N, mem, true)) ||
             (rc = copy3(g, g->in_x, x, 3 * N, mem, true)))
@@ -976,6 +1006,7 @@ int esmm3_rhs(esmm3 *g, const double *cons, const double *J, const double *x, co
 int esmm3_cfl_dt(esmm3 *g, double *dt)
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    if (int rc = inflow_ok3(g)) return rc;
     node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     g->launches += 3;
     g->nl[ESMM_KIND_OTHER] += 3;
@@ -991,6 +1022,7 @@ int esmm3_cfl_dt(esmm3 *g, double *dt)
 int esmm3_mesh_redistribute(esmm3 *g, double dt, double *xdot, double *dtau, double *dt_used, int mem)
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    if (int rc = inflow_ok3(g)) return rc;
     node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     int rc = mesh_and_dt3(g, dt);
     if (rc) return rc;
@@ -1018,6 +1050,7 @@ static int rk_step_async3(esmm3 *g, double dt)
 int esmm3_rk_step(esmm3 *g, double dt, double *dt_used)
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    if (int rc = inflow_ok3(g)) return rc;
     int rc = rk_step_async3(g, dt);
     if (rc) return rc;
     if (dt_used) {
@@ -1032,6 +1065,7 @@ int esmm3_rk_step(esmm3 *g, double dt, double *dt_used)
 int esmm3_rk_step_given(esmm3 *g, const double *xdot, double dt, int mem)
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    if (int rc = inflow_ok3(g)) return rc;
     int rc = step_given3(g, xdot, dt, mem);
     if (rc) return rc;
     CK3(cudaStreamSynchronize(g->st));
@@ -1041,6 +1075,7 @@ int esmm3_rk_step_given(esmm3 *g, const double *xdot, double dt, int mem)
 int esmm3_advance(esmm3 *g, int nsteps, double dt)
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    if (int rc = inflow_ok3(g)) return rc;
     for (int s = 0; s < nsteps; ++s) {
         int rc = rk_step_async3(g, dt);
         if (rc) return rc;
@@ -1051,6 +1086,7 @@ int esmm3_advance(esmm3 *g, int nsteps, double dt)
 int esmm3_totals(esmm3 *g, double out[3])
 {
     if (!g->has_state) return fail3(g, ESMM_ERR_STATE, "no state");
+    if (int rc = inflow_ok3(g)) return rc;
     node3(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     unsigned nb = nb3(g->g.N);
     g->launches += 2;

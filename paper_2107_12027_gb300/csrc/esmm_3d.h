@@ -25,6 +25,7 @@ int esmm3_mesh_redistribute(esmm3 *g, double dt, double *xdot, double *dtau, dou
 int esmm3_rk_step(esmm3 *g, double dt, double *dt_used);
 int esmm3_rk_step_given(esmm3 *g, const double *xdot, double dt, int mem);
 int esmm3_advance(esmm3 *g, int nsteps, double dt);
+int esmm3_set_inflow(esmm3 *g, const double *prim);
 int esmm3_totals(esmm3 *g, double out[3]);
 int esmm3_last_error(esmm3 *g, int *n_c2p_fail, char *msg, int len);
 long long esmm3_launches(const esmm3 *g);

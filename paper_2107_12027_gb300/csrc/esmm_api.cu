@@ -62,6 +62,8 @@ struct esmm_grid {
     double *q;                       // [NQ][Ptot] (RMHD: [NQ_MHD][Ptot])
     double *cw;                      // [4][Ntot] Jacobi weights of the mesh iteration
     float *q32;                      // [NQ32][Ptot] FP32 copies (RHD mixed form)
+    double *inflow_dev;              // [8] primitive inflow state (ESMM_INFLOW ends)
+    int needs_inflow, has_inflow;
     double *pg[3];                   // recovery warm starts (p; RMHD: Z), state -> stage 2 -> stage 3
     void *pairs;                     // [2][PMAX][4][Ptot] of the working precision (RHD)
     void *iflux;                     // [2][5][Ptot] (RMHD: [2][NF_MHD][Ptot]) of the working precision
@@ -222,6 +224,7 @@ int build_dom(esmm_grid *g, int kind)
 
 int ensure_doms(esmm_grid *g)
 {
+    if (g->needs_inflow && !g->has_inflow) return fail(g, ESMM_ERR_STATE, "an inflow end without an inflow state");
     if (g->doms_valid) return ESMM_OK;
     for (int k = 0; k < ND; ++k) {
         int rc = build_dom(g, k);
@@ -264,12 +267,16 @@ void launch_node(const esmm_grid *g, const LaunchDom &L, const double *cons, con
                  const double *xdot, const double *pg_in, double *pg_out, double *q)
 {
     float *q32 = q32_of(g);
+    const double *in = g->has_inflow ? g->inflow_dev : nullptr;
     if (g->p == 1)
-        k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32);
+        k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
+                                              in);
     else if (g->p == 2)
-        k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32);
+        k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
+                                              in);
     else
-        k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32);
+        k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
+                                              in);
 }
 
 void node(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
@@ -277,7 +284,8 @@ void node(esmm_grid *g, const double *cons, const double *J, const double *x, co
 {
     Prof pr_(g, ESMM_KIND_NODE);
     if (g->phys == ESMM_RMHD)
-        launch_node_mhd(dom(g, D_PAD), g->p, g->gamma, cons, J, x, xdot, pg_in, pg_out, g->q, g->status, g->st);
+        launch_node_mhd(dom(g, D_PAD), g->p, g->gamma, cons, J, x, xdot, pg_in, pg_out, g->q, g->status,
+                        g->has_inflow ? g->inflow_dev : nullptr, g->st);
     else
         launch_node(g, dom(g, D_PAD), cons, J, x, xdot, pg_in, pg_out, g->q);
 }
@@ -479,7 +487,7 @@ void free_all(esmm_grid *g)
     double **bufs[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2,
                        &g->q, &g->pg[0], &g->pg[1], &g->pg[2], &g->in_cons, &g->in_J, &g->in_x, &g->in_xdot,
                        &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->X, &g->Xn, &g->dt_dev,
-                       &g->t_dev, &g->partials, &g->tot_dev};
+                       &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev};
     for (double **b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     drop_graph(g);
@@ -550,6 +558,8 @@ int create3(esmm_grid **out, const int n[3], const double lo[3], const double hi
     esmm_grid *g = new (std::nothrow) esmm_grid;
     if (!g) return ESMM_ERR_ARG;
     memset((void *)g, 0, sizeof *g);
+    for (int d = 0; d < 3; ++d)
+        if (bc[d] == ESMM_INFLOW) g->needs_inflow = 1;
     new (&g->hpd) std::vector<ProbDesc>();
     new (&g->lo) std::vector<double>();
     new (&g->hi) std::vector<double>();
@@ -610,6 +620,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         G.N = (long long)G.nx * G.ny;
         G.bc0 = bc[2 * b];
         G.bc1 = bc[2 * b + 1];
+        if (G.bc0 == ESMM_INFLOW || G.bc1 == ESMM_INFLOW) g->needs_inflow = 1;
         G.per0 = hi[2 * b] - lo[2 * b];
         G.per1 = hi[2 * b + 1] - lo[2 * b + 1];
         D.on = on;
@@ -645,7 +656,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         {&g->x1, 2 * N}, {&g->c2, nv * N}, {&g->J2, N}, {&g->x2, 2 * N}, {&g->q, nq * P},
         {&g->pg[0], N}, {&g->pg[1], N}, {&g->pg[2], N}, {&g->out_dc, nv * N}, {&g->out_dJ, N},
         {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->X, 2 * N}, {&g->Xn, 2 * N},
-        {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max},
+        {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max}, {&g->inflow_dev, 8},
         {&g->tot_dev, 3 * (size_t)nprob}};
     for (auto &a : al)
         if (cudaMalloc((void **)a.p, a.n * d) != cudaSuccess) { release(g); return ESMM_ERR_CUDA; }
@@ -692,7 +703,7 @@ int check_geometry(int n0, int n1, const double *lo, const double *hi, const int
     const int n[2] = {n0, n1};
     for (int k = 0; k < 2; ++k) {
         if (n[k] < 4 || n[k] > (1 << 15)) return ESMM_ERR_ARG;
-        if (bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW) return ESMM_ERR_ARG;
+        if (bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW && bc[k] != ESMM_INFLOW) return ESMM_ERR_ARG;
         if (!(hi[k] > lo[k])) return ESMM_ERR_ARG;
     }
     return ESMM_OK;
@@ -1313,6 +1324,24 @@ int esmm_rk_step_given(esmm_grid *g, const double *xdot, double dt, int mem)
     return check_c2p(g);
 }
 
+int esmm_set_inflow(esmm_grid *g, const double *prim)
+{
+    if (!g || !prim) return ESMM_ERR_ARG;
+    const int nv = g->dim == 3 ? 8 : g->nv;
+    double v2 = 0.0;
+    for (int a = 1; a <= (nv == 8 ? 3 : 2); ++a) v2 += prim[a] * prim[a];
+    const double p = prim[nv == 8 ? 4 : 3];
+    if (!(prim[0] > 0.0) || !(p > 0.0) || !(v2 < 1.0)) return fail(g, ESMM_ERR_ARG, "inadmissible inflow state");
+    if (g->dim == 3) return esmm3_set_inflow(g->g3, prim);
+    double w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < nv; ++a) w[a] = prim[a];
+    CK(cudaMemcpyAsync(g->inflow_dev, w, 8 * sizeof(double), cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    g->has_inflow = 1;
+    g->epoch++;
+    return ESMM_OK;
+}
+
 int esmm_advance(esmm_grid *g, int nsteps, double dt)
 {
     if (!g || nsteps < 0) return ESMM_ERR_ARG;
@@ -1407,6 +1436,7 @@ int esmm_tune(esmm_grid *g, int *block_sizes)
 int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
                  const double *mu, double *lam, int mem)
 {
+    if (g && g->needs_inflow) return fail(g, ESMM_ERR_ARG, "the adjoint takes periodic and outflow ends");
     if (g && g->dim == 3) {
         if (!cons || !J || !x || !mu || !lam) return ESMM_ERR_ARG;
         return esmm3_rhs_vjp(g->g3, cons, J, x, xdot, mu, lam, mem);
@@ -1440,6 +1470,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 {
+    if (g && g->needs_inflow) return fail(g, ESMM_ERR_ARG, "the adjoint takes periodic and outflow ends");
     if (g && g->dim == 3) return nsteps < 0 ? ESMM_ERR_ARG : esmm3_adjoint_record(g->g3, nsteps, dt);
     if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->phys == ESMM_RMHD && g->prm.precision != ESMM_FP64)
@@ -1614,9 +1645,15 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
         return L;
     };
     LaunchDom Ln = one(G.P, BS);
-    if (p == 1) k_node<1><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status);
-    else if (p == 2) k_node<2><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status);
-    else k_node<3><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status);
+    if (p == 1)
+        k_node<1><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, nullptr,
+                                             nullptr);
+    else if (p == 2)
+        k_node<2><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, nullptr,
+                                             nullptr);
+    else
+        k_node<3><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, nullptr,
+                                             nullptr);
     for (int dir = 0; dir < 2; ++dir) {
         long long cp = dir == 0 ? (long long)(nx + p) * ny : (long long)(ny + p) * nx;
         long long ci = dir == 0 ? (long long)(nx + 1) * ny : (long long)(ny + 1) * nx;

@@ -71,7 +71,8 @@ struct QStencil32 {
     int off;
     __device__ __forceinline__ float operator()(int k, int j) const
     {
-        const int f = j == 0 ? Q32_B : (j == 1 ? Q32_UX : (j == 2 ? Q32_UY : (j == 3 ? Q32_W : (j == 4 ? Q32_LNR : Q32_LNB))));
+        const int f = j == 0 ? Q32_B
+                    : (j == 1 ? Q32_UX : (j == 2 ? Q32_UY : (j == 3 ? Q32_W : (j == 4 ? Q32_LNR : Q32_LNB))));
         return q[f * P + c0 + (k - off) * sd];
     }
 };

@@ -65,7 +65,7 @@ template <int P>
 __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
                        const double *__restrict__ x, const double *__restrict__ xdot,
                        const double *__restrict__ pg_in, double *__restrict__ pg_out, double *__restrict__ q,
-                       int *__restrict__ status, float *__restrict__ q32 = nullptr)
+                       int *__restrict__ status, float *__restrict__ q32, const double *__restrict__ inflow)
 {
     ProbDesc D;
     long long lb;
@@ -86,7 +86,15 @@ __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, 
     double Dd = cons[src] * iJ, mx = cons[g.N + src] * iJ, my = cons[2 * g.N + src] * iJ,
            E = cons[3 * g.N + src] * iJ;
     double rho, vx, vy, p, W;
-    int st = cons2prim(gam, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p, W);
+    int st;
+    if (inflow && ((g.bc0 == 2 && I < 0) || (g.bc1 == 2 && Jn < 0))) {
+        // a ghost beyond an inflow end: the given state
+        rho = inflow[0]; vx = inflow[1]; vy = inflow[2]; p = inflow[3];
+        W = rsqrt(1.0 - (vx * vx + vy * vy));
+        st = 0;
+    } else {
+        st = cons2prim(gam, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p, W);
+    }
     bool interior = I >= 0 && I < g.nx && Jn >= 0 && Jn < g.ny;
     if (interior) {
         if (st) atomicAdd(status, 1);
@@ -467,7 +475,7 @@ __global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ cw, const d
     X += 2 * D.on;
     Xn += 2 * D.on;
     int i = (int)(id % g.nx), j = (int)(id / g.nx);
-    bool fixed = (g.bc0 == 1 && (i == 0 || i == g.nx - 1)) || (g.bc1 == 1 && (j == 0 || j == g.ny - 1));
+    bool fixed = (g.bc0 != 0 && (i == 0 || i == g.nx - 1)) || (g.bc1 != 0 && (j == 0 || j == g.ny - 1));
     if (fixed) {
         Xn[id] = X[id];
         Xn[g.N + id] = X[g.N + id];

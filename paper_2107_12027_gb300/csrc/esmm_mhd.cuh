@@ -588,7 +588,7 @@ template <int P>
 __global__ void k_node_mhd(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
                            const double *__restrict__ x, const double *__restrict__ xdot,
                            const double *__restrict__ zg_in, double *__restrict__ zg_out, double *__restrict__ q,
-                           int *__restrict__ status)
+                           int *__restrict__ status, const double *__restrict__ inflow)
 {
     ProbDesc D;
     long long lb;
@@ -602,7 +602,14 @@ __global__ void k_node_mhd(ProbArg pa, double gam, const double *__restrict__ co
     double U[8], w[8], Z;
 #pragma unroll
     for (int a = 0; a < 8; ++a) U[a] = cons[a * g.N + src] * iJ;
-    int st = cons2prim_mhd(gam, U, zg_in ? zg_in[src] : -1.0, w, Z);
+    int st = 0;
+    if (inflow && ((g.bc0 == 2 && I < 0) || (g.bc1 == 2 && Jn < 0))) {
+        // a ghost beyond an inflow end: the given state
+        for (int a = 0; a < 8; ++a) w[a] = inflow[a];
+        Z = 0.0;
+    } else {
+        st = cons2prim_mhd(gam, U, zg_in ? zg_in[src] : -1.0, w, Z);
+    }
     bool interior = I >= 0 && I < g.nx && Jn >= 0 && Jn < g.ny;
     if (interior) {
         if (st) atomicAdd(status, 1);

@@ -18,7 +18,7 @@ from . import build as _build
 
 OK, ERR_ARG, ERR_CUDA, ERR_C2P, ERR_TIMEOUT, ERR_STATE = 0, 1, 2, 3, 4, 5
 RHD, RMHD = 0, 1
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, INFLOW = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 FP64, MIXED = 0, 1
 MONITOR_RHO, MONITOR_LNRHO = 0, 1
@@ -50,6 +50,7 @@ SYMBOLS = (
     "esmm_grid_create", "esmm_grid_destroy", "esmm_set_stream", "esmm_set_eos", "esmm_set_order",
     "esmm_set_params", "esmm_get_params", "esmm_state_set", "esmm_state_set_cons", "esmm_state_get",
     "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step", "esmm_rk_step_given",
+    "esmm_set_inflow",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
     "esmm_rhs_static", "esmm_mhd_eigen", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
     "esmm_batch_times", "esmm_batch_totals", "esmm_tune", "esmm_adjoint_record", "esmm_adjoint_steps",
@@ -93,7 +94,7 @@ def lib():
             "esmm_state_set_cons": [vp, vp, vp, vp, d, i], "esmm_state_get": [vp, i, vp, i],
             "esmm_get_time": [vp, dp], "esmm_rhs": [vp, vp, vp, vp, vp, vp, vp, i],
             "esmm_cfl_dt": [vp, dp], "esmm_mesh_redistribute": [vp, d, vp, dp, dp, i],
-            "esmm_rk_step": [vp, d, dp], "esmm_rk_step_given": [vp, vp, d, i], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
+            "esmm_rk_step": [vp, d, dp], "esmm_rk_step_given": [vp, vp, d, i], "esmm_set_inflow": [vp, dp], "esmm_advance": [vp, i, d], "esmm_totals": [vp, dp],
             "esmm_last_error": [vp, ctypes.POINTER(i), ctypes.c_char_p, i],
             "esmm_profile": [vp, i],
             "esmm_rhs_static": [i, i, ctypes.POINTER(i), dp, dp, d, i, i, vp, vp, vp, vp, vp, vp, vp],
@@ -248,6 +249,11 @@ class Grid:
         prm = Params()
         self._check(lib().esmm_get_params(self.h, ctypes.byref(prm)))
         return {k: getattr(prm, k) for k, _ in Params._fields_}
+
+    def set_inflow(self, prim):
+        """The primitive state held beyond every INFLOW end (nv values)."""
+        a = (ctypes.c_double * self.nv)(*[float(v) for v in prim])
+        self._check(lib().esmm_set_inflow(self.h, a))
 
     def set_params(self, **kw):
         cur = self.get_params()

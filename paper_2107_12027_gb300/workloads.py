@@ -468,3 +468,53 @@ def rmhd_blast2_config(n):
     """The 2D RMHD blast on n x n nodes of [-6,6]^2 with outflow boundaries."""
     x = uniform_mesh(n, n, (-6.0, -6.0), (6.0, 6.0), (False, False))
     return x, rmhd_blast2(x)
+
+
+# ---- the RMHD shock-cloud interactions (Sec. 6) -----------------------------
+# The planar shock's states, primitive (rho, v_1, v_2, v_3, p, B_1, B_2, B_3),
+# Gamma = 5/3.  The post-shock state is printed as given.  The pre-shock
+# state is printed garbled; it is read as rho = 1, v = 0, p = 0.05,
+# B = (0, 0.16106, -0.16106).  With that reading the two states satisfy the
+# RMHD jump conditions for a single shock speed (0.839) to the printed
+# digits; the printed order does not.
+SHOCK_CLOUD_POST = (3.86859, 0.68, 0.0, 0.0, 1.25115, 0.0, 0.84981, -0.84981)
+SHOCK_CLOUD_PRE = (1.0, 0.0, 0.0, 0.0, 0.05, 0.0, 0.16106, -0.16106)
+
+
+def rmhd_shock_cloud(x, x_shock=0.05, r_cloud=0.15, rho_cloud=30.0):
+    """The shock at x_1 = x_shock moving into the pre-shock medium, which
+    holds a cloud of density rho_cloud and radius r_cloud centred at (0.25,
+    0.5) (2D, x [2][...]) or (0.25, 0.5, 0.5) (3D, x [3][...]); the cloud
+    has the medium's velocity, pressure and field."""
+    post, pre = np.array(SHOCK_CLOUD_POST), np.array(SHOCK_CLOUD_PRE)
+    shocked = x[0] < x_shock
+    prim = np.where(shocked[None], post.reshape((8,) + (1,) * (x.ndim - 1)),
+                    pre.reshape((8,) + (1,) * (x.ndim - 1)))
+    c = (0.25, 0.5, 0.5)
+    r2 = sum((x[d] - c[d]) ** 2 for d in range(x.shape[0]))
+    prim[0] = np.where(r2 < r_cloud ** 2, rho_cloud, prim[0])
+    return np.ascontiguousarray(prim)
+
+
+def rmhd_shock_cloud_config(n=(210, 150)):
+    """2D shock-cloud on [-0.2,1.2] x [0,1]: inflow of the post-shock state at
+    x_1 = -0.2, outflow elsewhere (n nodes per direction, both ends)."""
+    x = uniform_mesh(n[0], n[1], (-0.2, 0.0), (1.2, 1.0), (False, False))
+    return x, rmhd_shock_cloud(x)
+
+
+def rmhd_shock_cloud3_config(n=(210, 150, 150)):
+    """3D shock-cloud on [-0.2,1.2] x [0,1]^2 with the spherical cloud."""
+    x = uniform_mesh3(n, (-0.2, 0.0, 0.0), (1.2, 1.0, 1.0), (False, False, False))
+    return x, rmhd_shock_cloud(x)
+
+
+def sphere_rp3(x, r0=0.5):
+    """The 3D spherically symmetric Riemann problem of Sec. 6 (an RHD
+    problem, here on the RMHD system with B = 0): rho = 10, p = 40/3 for
+    r < r0, rho = 1, p = 1e-2 outside, at rest."""
+    r2 = x[0] ** 2 + x[1] ** 2 + x[2] ** 2
+    z = 0.0 * r2
+    inside = r2 < r0 * r0
+    return np.ascontiguousarray(np.stack([np.where(inside, 10.0, 1.0), z, z, z,
+                                          np.where(inside, 40.0 / 3.0, 1e-2), z, z, z]))

@@ -462,3 +462,44 @@ def test_vortex3_is_periodic_on_its_box():
         q = pts.copy()
         q[d] += per
         assert np.abs(wl.rmhd_vortex3(q, 0.3) - base).max() < 1e-13
+
+
+def test_shock_cloud_states_satisfy_the_jump_conditions():
+    # Sec. 6 shock-cloud: the post- and pre-shock states (the latter read as
+    # rho = 1, v = 0, p = 0.05, B = (0, 0.16106, -0.16106) from the garbled
+    # print) are joined by one RMHD shock: F(R) - F(L) = s (U(R) - U(L)) for a
+    # single speed s in all eight components, to the printed 5-6 digits.
+    L, R = np.array(wl.SHOCK_CLOUD_POST), np.array(wl.SHOCK_CLOUD_PRE)
+    dU = oracle.mhd_prim2cons(G53, R) - oracle.mhd_prim2cons(G53, L)
+    dF = oracle.mhd_flux(G53, R, 0) - oracle.mhd_flux(G53, L, 0)
+    s = dU @ dF / (dU @ dU)
+    assert np.abs(dF - s * dU).max() < 2e-6 * np.abs(dF).max()
+    assert 0.83 < s < 0.85                                     # right-moving, sub-luminal
+    # the print's own order of the pre-shock state is not a shock of L
+    P = np.array([1.0, 0, 0, 0, 0, 0.16106, 0.16106, 0.05])
+    P[4] = 1e-3     # (p = 0 is not admissible; any small pressure)
+    dU = oracle.mhd_prim2cons(G53, P) - oracle.mhd_prim2cons(G53, L)
+    dF = oracle.mhd_flux(G53, P, 0) - oracle.mhd_flux(G53, L, 0)
+    s = dU @ dF / (dU @ dU)
+    assert np.abs(dF - s * dU).max() > 1e-3 * np.abs(dF).max()
+
+
+def test_shock_cloud_inflow_equals_outflow_while_the_boundary_is_uniform():
+    # The 2D shock-cloud starts with the post-shock state next to its inflow
+    # end, so inflow ghosts (the post-shock state) and zero-gradient ghosts
+    # (copies of those nodes) hold the same data, up to the recovery's
+    # rounding of the stored state: the same right-hand sides.
+    x, prim = wl.rmhd_shock_cloud_config((42, 30))
+    kw = dict(period=(1.4, 1.0), p=3, w=5, gamma=G53, phys=oracle.RMHD)
+    c_in = oracle.make_cfg(42, 30, bc=(oracle.INFLOW, oracle.OUTFLOW), inflow=wl.SHOCK_CLOUD_POST, **kw)
+    c_out = oracle.make_cfg(42, 30, bc=(oracle.OUTFLOW, oracle.OUTFLOW), **kw)
+    cons, J = oracle.init_state(c_in, prim, x)
+    a, b = oracle.rhs(c_in, cons, J, x), oracle.rhs(c_out, cons, J, x)
+    assert np.abs(a[0] - b[0]).max() < 1e-13 * np.abs(a[0]).max()
+    assert np.array_equal(a[1], b[1])
+    # a different inflow state changes only the first columns
+    c_x = oracle.make_cfg(42, 30, bc=(oracle.INFLOW, oracle.OUTFLOW),
+                          inflow=np.array(wl.SHOCK_CLOUD_POST) * [1.1, 1, 1, 1, 1.1, 1, 1, 1], **kw)
+    d = oracle.rhs(c_x, cons, J, x)[0] - a[0]
+    assert np.abs(d[:, :, :3]).max() > 1e-3 * np.abs(a[0]).max()
+    assert np.abs(d[:, :, 3:]).max() < 1e-13 * np.abs(a[0]).max()

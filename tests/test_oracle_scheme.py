@@ -339,3 +339,63 @@ def test_vortex_es_entropy_decays_every_step():
     e1, e2 = _vortex_run(3, 5, 0.05, 0.4), _vortex_run(3, 5, 0.025, 0.4)
     assert (np.diff(e1) < 0).all() and (np.diff(e2) < 0).all()
     assert abs((e1[-1] - e1[0]) / (e2[-1] - e2[0]) - 1) < 1e-2
+
+
+# ------------------------------------------------------ inflow boundary (Sec. 6)
+def test_inflow_ghosts_enter_the_boundary_flux():
+    # EC scheme, p = 1, uniform static mesh (spacings hx, hy), uniform state w0
+    # with an inflow state w_in at the low x end: the only nonzero right-hand
+    # side is at the first column, -hy (F_1(w0) - F~_1(w_in, w0)), the
+    # two-point flux of Sec. 3.1 between the ghost and the boundary node.
+    nx, ny = 8, 5
+    w0 = np.array([1.0, 0.3, -0.1, 0.8])
+    w_in = np.array([2.0, 0.5, 0.1, 1.5])
+    x = wl.uniform_mesh(nx, ny, periodic=(False, False))
+    hy = 1.0 / (ny - 1)
+    cfg = oracle.make_cfg(nx, ny, bc=(oracle.INFLOW, oracle.OUTFLOW), p=1, w=0, inflow=w_in)
+    prim = np.ascontiguousarray(np.broadcast_to(w0[:, None, None], (4, ny, nx)))
+    cons, J = oracle.init_state(cfg, prim, x)
+    d, dJ = oracle.rhs(cfg, cons, J, x)
+    _, F1t, _ = oracle.ec_flux(G53, w_in, w0)
+    F1 = oracle.flux(G53, w0, 0)
+    want = -hy * (F1 - F1t)
+    scale = np.abs(want).max()
+    for a in range(4):
+        assert np.abs(d[a, :, 0] - want[a]).max() < 1e-13 * scale
+        assert np.abs(d[a, :, 1:]).max() < 1e-13 * scale
+    assert np.abs(dJ).max() == 0.0
+
+
+@pytest.mark.parametrize("p,w", [(2, 5), (3, 5), (3, 0)])
+def test_inflow_free_stream_on_moving_mesh(p, w):
+    # the inflow state everywhere: free stream (Prop. 3.2) on a random moving
+    # mesh with inflow at the low x end
+    nx, ny = 24, 20
+    w_in = np.array([0.7, 0.4, -0.2, 1.3])
+    x = wl.random_mesh(nx, ny, wl.rng(640 + p + w), amp=0.2, periodic=(False, False))
+    xdot = wl.rng(641).uniform(-0.3, 0.3, x.shape)
+    xdot[:, :, 0] = xdot[:, :, -1] = xdot[:, 0, :] = xdot[:, -1, :] = 0.0
+    cfg = oracle.make_cfg(nx, ny, bc=(oracle.INFLOW, oracle.OUTFLOW), p=p, w=w, inflow=w_in)
+    prim = np.ascontiguousarray(np.broadcast_to(w_in[:, None, None], (4, ny, nx)))
+    cons, J = oracle.init_state(cfg, prim, x)
+    d, dJ = oracle.rhs(cfg, cons, J, x, np.ascontiguousarray(xdot))
+    U = cons / J
+    # d(JU)/dt = U dJ/dt for a constant state
+    assert np.abs(d - U * dJ).max() < 1e-12 * np.abs(U * dJ).max()
+
+
+def test_monitor_sees_the_inflow_state():
+    # a uniform state with a different inflow state: the only nonzero
+    # differences of sigma are at the inflow column, where the ghost holds the
+    # inflow state, so omega = sqrt(1 + alpha + alpha_lap) there and 1 elsewhere
+    nx, ny = 10, 6
+    w0, w_in = np.array([1.0, 0.2, 0.1, 1.0]), np.array([3.0, 0.2, 0.1, 1.0])
+    x = wl.uniform_mesh(nx, ny, periodic=(False, False))
+    for mon in (oracle.MONITOR_RHO, oracle.MONITOR_LNRHO):
+        cfg = oracle.make_cfg(nx, ny, bc=(oracle.INFLOW, oracle.OUTFLOW), monitor=mon, alpha=20.0, alpha_lap=10.0,
+                              inflow=w_in)
+        prim = np.ascontiguousarray(np.broadcast_to(w0[:, None, None], (4, ny, nx)))
+        cons, J = oracle.init_state(cfg, prim, x)
+        om = oracle.monitor(cfg, cons, J)
+        assert np.abs(om[:, 0] - np.sqrt(31.0)).max() < 1e-13
+        assert np.abs(om[:, 1:] - 1.0).max() < 1e-13
