@@ -136,7 +136,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--n", type=int, default=None, help="nodes per side (default per workload)")
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "rotor", "blast3d"])
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "rotor", "blast3d", "sphere3d"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and mixed-form legs")
     ap.add_argument("--study", default=None, choices=["um-mm"],
                     help="um-mm: the efficiency of MM-O5 against UM-O5 on the Sec. 6 problems (one JSON line per run)")
@@ -522,12 +522,23 @@ def run_rmhd(args):
     torch.cuda.set_device(local)
     esmm.lib()
     stream = torch.cuda.Stream()
-    three = args.workload == "blast3d"
+    three = args.workload in ("blast3d", "sphere3d")
     if three and args.form != "fp64":
-        raise SystemExit("the 3D blast runs in the FP64 form only")
+        raise SystemExit("the 3D workloads run in the FP64 form only")
     n = args.n or (128 if three else 512)
     K, W = args.steps, args.warmup
-    if three:
+    if args.workload == "sphere3d":
+        x = wl.uniform_mesh3((n, n, n), (-1.0,) * 3, (1.0,) * 3, (False, False, False))
+        prim = wl.sphere_rp3(x)
+        g = esmm.Grid3((n, n, n), (-1.0,) * 3, (1.0,) * 3, bc=(1, 1, 1), gamma=5.0 / 3.0, scheme="MM-O5",
+                       alpha=800.0, monitor=esmm.MONITOR_LNRHO, stream=stream.cuda_stream)
+        nodes = n ** 3
+        ifaces = (n + 1) * n * n
+        desc = ("3D spherical Riemann problem (an RHD problem on the RMHD system, B = 0), %d^3 nodes on [-1,1]^3, "
+                "outflow, Gamma=5/3, r<0.5: rho=10, p=40/3; outside rho=1, p=1e-2; at rest; MM-O5 (6th-order EC "
+                "flux p=3 + WENO5), adaptive moving mesh (sigma=ln rho, alpha=800), SSP-RK3, CFL 0.3" % n)
+        flops, traffic, kname = None, None, "k3_iface<3,5>"
+    elif three:
         x, prim = wl.blast3_config(n)
         g = esmm.Grid3((n, n, n), (-0.5,) * 3, (0.5,) * 3, bc=(1, 1, 1), p=2, w=5, stream=stream.cuda_stream)
         nodes = n ** 3
