@@ -34,7 +34,7 @@ using namespace esmm;
 
 namespace {
 // launch domains: which elements of each problem a kernel covers
-enum { D_PAD = 0, D_PAIR0, D_PAIR1, D_IFACE0, D_IFACE1, D_NODE, D_NODE2, ND };
+enum { D_PAD = 0, D_PAIR0, D_PAIR1, D_IFACE0, D_IFACE1, D_NODE, D_NODE2, D_MTILE, ND };
 }  // namespace
 
 struct esmm_grid {
@@ -61,6 +61,7 @@ struct esmm_grid {
     // right-hand-side work arrays
     double *q;                       // [NQ][Ptot] (RMHD: [NQ_MHD][Ptot])
     double *cw;                      // [4][Ntot] Jacobi weights of the mesh iteration
+    double *rs;                      // [2][Ntot] the iteration's residual on the displacement
     float *q32;                      // [NQ32][Ptot] FP32 copies (RHD mixed form)
     double *inflow_dev;              // [8] primitive inflow state (ESMM_INFLOW ends)
     int needs_inflow, has_inflow;
@@ -187,6 +188,8 @@ long long dom_count(const Geom &G, int kind, int p)
     case D_IFACE0: return (long long)(G.nx + 1) * G.ny;
     case D_IFACE1: return (long long)(G.ny + 1) * G.nx;
     case D_NODE: return G.N;
+    case D_MTILE:   // one block of MT_THREADS per MT_TX x MT_TY tile
+        return (long long)((G.nx + MT_TX - 1) / MT_TX) * ((G.ny + MT_TY - 1) / MT_TY) * MT_THREADS;
     default: return 2 * G.N;
     }
 }
@@ -264,30 +267,32 @@ float *q32_of(const esmm_grid *g)
 }
 
 void launch_node(const esmm_grid *g, const LaunchDom &L, const double *cons, const double *J, const double *x,
-                 const double *xdot, const double *pg_in, double *pg_out, double *q)
+                 const double *xdot, const double *pg_in, double *pg_out, double *q, bool exact_logs)
 {
     float *q32 = q32_of(g);
     const double *in = g->has_inflow ? g->inflow_dev : nullptr;
+    const int f32_logs = q32 && !exact_logs;
     if (g->p == 1)
         k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
-                                              in);
+                                              in, f32_logs);
     else if (g->p == 2)
         k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
-                                              in);
+                                              in, f32_logs);
     else
         k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
-                                              in);
+                                              in, f32_logs);
 }
 
+// the node pass; exact_logs: FP64 logarithms in every form (the totals)
 void node(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
-          const double *pg_in, double *pg_out)
+          const double *pg_in, double *pg_out, bool exact_logs = false)
 {
     Prof pr_(g, ESMM_KIND_NODE);
     if (g->phys == ESMM_RMHD)
         launch_node_mhd(dom(g, D_PAD), g->p, g->gamma, cons, J, x, xdot, pg_in, pg_out, g->q, g->status,
                         g->has_inflow ? g->inflow_dev : nullptr, g->st);
     else
-        launch_node(g, dom(g, D_PAD), cons, J, x, xdot, pg_in, pg_out, g->q);
+        launch_node(g, dom(g, D_PAD), cons, J, x, xdot, pg_in, pg_out, g->q, exact_logs);
 }
 
 // both sweeps of the flux kernels for the node data in g->q
@@ -364,6 +369,69 @@ void red_init(esmm_grid *g)
     k_red_init<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->red);
 }
 
+// sweeps per launch of k_mesh_sweeps in the mixed form (FP32: all ten sweeps
+// of the default in one launch); the FP64 form sweeps once per launch
+// (k_mesh_sweep), since the blocked kernel's halo work costs FP64 issue slots
+constexpr int MT_SB32 = 10;
+
+// The Jacobi sweeps (k_mesh_sweeps), the limiter and the mesh velocity from
+// the displacement, in working type T (the weights are in g->cw).
+template <typename T, int SB>
+int mesh_finish(esmm_grid *g, double dt, const LaunchDom &L, const LaunchDom &L2)
+{
+    T *bufs[2] = {reinterpret_cast<T *>(g->X), reinterpret_cast<T *>(g->Xn)};
+    const T *Dd = bufs[0];
+    if (g->prm.mu == 0) {
+        CK(cudaMemsetAsync(bufs[0], 0, sizeof(T) * 2 * g->Ntot, g->st));
+    } else if constexpr (SB == 1) {   // FP64: one sweep per launch
+        {
+            Prof pr_(g, ESMM_KIND_MESH);
+            k_mesh_resid<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, g->cw, g->rs);
+        }
+        const double *in = nullptr;
+        int b = 0;
+        for (int nu = 0; nu < g->prm.mu; ++nu) {
+            Prof pr_(g, ESMM_KIND_MESH);
+            double *out = reinterpret_cast<double *>(bufs[b]);
+            k_mesh_sweep<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->cw, g->rs, in, out);
+            in = out;
+            b ^= 1;
+        }
+        Dd = reinterpret_cast<const T *>(in);
+    } else {
+        LaunchDom Lt = dom(g, D_MTILE);
+        const T *in = nullptr;
+        int b = 0;
+        for (int done = 0; done < g->prm.mu; done += SB) {
+            Prof pr_(g, ESMM_KIND_MESH);
+            k_mesh_sweeps<T, SB><<<Lt.nblk, MT_THREADS, mesh_sweeps_smem<T, SB>(), g->st>>>(
+                Lt.pa, g->x, g->cw, in, bufs[b], std::min(SB, g->prm.mu - done));
+            in = bufs[b];
+            b ^= 1;
+        }
+        Dd = in;
+    }
+    {
+        Prof pr_(g, ESMM_KIND_MESH);
+        k_mesh_tau<T><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, Dd, g->q, g->J, g->red);
+    }
+    step_dt(g, dt);
+    {
+        Prof pr_(g, ESMM_KIND_MESH);
+        k_mesh_xdot<T><<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, Dd, g->red, g->dt_dev, g->xdot);
+    }
+    return ESMM_OK;
+}
+
+// the shared-memory limit of the sweep kernels (once per process and device
+// is enough; cheap to repeat)
+int mesh_sweeps_init(esmm_grid *g)
+{
+    CK(cudaFuncSetAttribute(k_mesh_sweeps<float, MT_SB32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)mesh_sweeps_smem<float, MT_SB32>()));
+    return ESMM_OK;
+}
+
 // The step: mesh target and limiter (when the mesh moves), dt (k_dt) and the
 // mesh velocity into g->xdot.  Requires g->q of the state, the slots reset
 // and the radius (step_radius) when dt <= 0.
@@ -400,23 +468,9 @@ int mesh_core(esmm_grid *g, double dt)
         Prof pr_(g, ESMM_KIND_MESH);
         k_mesh_weights<<<L.nblk, L.bs, 0, g->st>>>(L.pa, om, g->cw);
     }
-    const double *src = g->x;
-    for (int nu = 0; nu < g->prm.mu; ++nu) {
-        double *dst = (nu % 2 == 0) ? g->X : g->Xn;
-        Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_jacobi<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->cw, src, dst);
-        src = dst;
-    }
-    {
-        Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_tau<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, src, g->q, g->J, g->red);
-    }
-    step_dt(g, dt);
-    {
-        Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_xdot<<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, g->x, src, g->red, g->dt_dev, g->xdot);
-    }
-    return ESMM_OK;
+    // the mu sweeps on the displacement, SB per launch (FP32 in the mixed form)
+    if (g->prm.precision == ESMM_MIXED) return mesh_finish<float, MT_SB32>(g, dt, L, L2);
+    return mesh_finish<double, 1>(g, dt, L, L2);
 }
 
 int stages(esmm_grid *g);
@@ -486,7 +540,8 @@ void free_all(esmm_grid *g)
 {
     double **bufs[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2,
                        &g->q, &g->pg[0], &g->pg[1], &g->pg[2], &g->in_cons, &g->in_J, &g->in_x, &g->in_xdot,
-                       &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->X, &g->Xn, &g->dt_dev,
+                       &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->rs, &g->X, &g->Xn,
+                       &g->dt_dev,
                        &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev};
     for (double **b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
@@ -655,7 +710,8 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         {&g->cons, nv * N}, {&g->J, N}, {&g->x, 2 * N}, {&g->xdot, 2 * N}, {&g->c1, nv * N}, {&g->J1, N},
         {&g->x1, 2 * N}, {&g->c2, nv * N}, {&g->J2, N}, {&g->x2, 2 * N}, {&g->q, nq * P},
         {&g->pg[0], N}, {&g->pg[1], N}, {&g->pg[2], N}, {&g->out_dc, nv * N}, {&g->out_dJ, N},
-        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->X, 2 * N}, {&g->Xn, 2 * N},
+        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->rs, 2 * N}, {&g->X, 2 * N},
+        {&g->Xn, 2 * N},
         {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max}, {&g->inflow_dev, 8},
         {&g->tot_dev, 3 * (size_t)nprob}};
     for (auto &a : al)
@@ -694,6 +750,10 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
          cudaMemsetAsync(g->t_dev, 0, nprob * d, g->st) == cudaSuccess &&
          cudaStreamSynchronize(g->st) == cudaSuccess;
     if (!ok) { release(g); return ESMM_ERR_CUDA; }
+    if (mesh_sweeps_init(g)) {
+        release(g);
+        return ESMM_ERR_CUDA;
+    }
     *out = g;
     return ESMM_OK;
 }
@@ -799,7 +859,7 @@ int totals_async(esmm_grid *g)
 {
     int rc;
     if ((rc = ensure_doms(g))) return rc;
-    node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
+    node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr, true);
     LaunchDom L = dom(g, D_NODE);
     {
         Prof pr_(g, ESMM_KIND_OTHER);
@@ -822,7 +882,9 @@ void step_launches(const esmm_grid *g, double dt, long long per[ESMM_NKINDS])
     per[ESMM_KIND_PAIRS] = g->phys == ESMM_RMHD ? 0 : 6;
     per[ESMM_KIND_IFACE] = 6;
     per[ESMM_KIND_UPDATE] = 3;
-    per[ESMM_KIND_MESH] = g->prm.move_mesh ? (4 + g->prm.n_filter + g->prm.mu + (g->prm.mu > 0)) : 0;
+    const int mu = g->prm.mu;
+    const int sweeps = g->prm.precision == ESMM_MIXED ? (mu + MT_SB32 - 1) / MT_SB32 : (mu > 0) + mu;   // (+ residual)
+    per[ESMM_KIND_MESH] = g->prm.move_mesh ? (4 + g->prm.n_filter + (mu > 0) + sweeps) : 0;
     per[ESMM_KIND_OTHER] = 3 + (dt > 0.0 ? 0 : 1);  // reset, (CFL), dt, time
 }
 

@@ -60,12 +60,16 @@ __device__ __forceinline__ void mesh_deltas(const Geom &g, const double *__restr
 // nodes take the data of their boundary source node and metrics of the
 // boundary-mapped mesh, so the flux kernels need no boundary logic.  With
 // q32 (the mixed form) the node also writes the FP32 copies the flux kernels
-// read.
+// read; with f32_logs (the mixed form's scheme passes) ln rho and ln beta are
+// FP32 logarithms: in that form they enter only FP32 arithmetic and the log
+// mean's jump outside its near-equal branch, while the totals take a pass
+// with FP64 logarithms.
 template <int P>
 __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
                        const double *__restrict__ x, const double *__restrict__ xdot,
                        const double *__restrict__ pg_in, double *__restrict__ pg_out, double *__restrict__ q,
-                       int *__restrict__ status, float *__restrict__ q32, const double *__restrict__ inflow)
+                       int *__restrict__ status, float *__restrict__ q32, const double *__restrict__ inflow,
+                       int f32_logs = 0)
 {
     ProbDesc D;
     long long lb;
@@ -107,8 +111,16 @@ __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, 
     q[Q_UX * g.P + t] = W * vx;
     q[Q_UY * g.P + t] = W * vy;
     q[Q_W * g.P + t] = W;
-    q[Q_LNR * g.P + t] = log(rho);
-    q[Q_LNB * g.P + t] = log(beta);
+    float lr32 = 0.0f, lb32 = 0.0f;
+    if (f32_logs) {
+        lr32 = logf((float)rho);
+        lb32 = logf((float)beta);
+        q[Q_LNR * g.P + t] = (double)lr32;
+        q[Q_LNB * g.P + t] = (double)lb32;
+    } else {
+        q[Q_LNR * g.P + t] = log(rho);
+        q[Q_LNB * g.P + t] = log(beta);
+    }
     double dxi_x, dxi_y, deta_x, deta_y;
     mesh_deltas<P>(g, x, I, Jn, dxi_x, dxi_y, deta_x, deta_y);
     double M00 = deta_y, M01 = -deta_x, M10 = -dxi_y, M11 = dxi_x;
@@ -128,8 +140,8 @@ __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, 
         q32[Q32_UX * g.P + t] = (float)(W * vx);
         q32[Q32_UY * g.P + t] = (float)(W * vy);
         q32[Q32_W * g.P + t] = (float)W;
-        q32[Q32_LNR * g.P + t] = (float)q[Q_LNR * g.P + t];
-        q32[Q32_LNB * g.P + t] = (float)q[Q_LNB * g.P + t];
+        q32[Q32_LNR * g.P + t] = f32_logs ? lr32 : (float)q[Q_LNR * g.P + t];
+        q32[Q32_LNB * g.P + t] = f32_logs ? lb32 : (float)q[Q_LNB * g.P + t];
         q32[Q32_M00 * g.P + t] = (float)M00;
         q32[Q32_M01 * g.P + t] = (float)M01;
         q32[Q32_M10 * g.P + t] = (float)M10;
@@ -449,21 +461,149 @@ __device__ __noinline__ double mesh_edge(const Geom &g, const double *__restrict
     return mesh_at(g, x, i, j, comp, 1);
 }
 
-// the Jacobi update of a node next to the boundary (neighbours through the
-// boundary mapping); kept out of line so that the interior path does not
-// evaluate the ghost arithmetic
-__device__ __noinline__ void jacobi_edge(const Geom &g, const double *__restrict__ X, int i, int j, double ce,
-                                         double cwe, double cn, double cs, double *out)
+// ---- the Jacobi sweeps, temporally blocked ---------------------------------
+// The iteration X_i <- sum_k c_k X_k (k_mesh_weights) written for the
+// displacement D = X - x^n, which starts at 0:
+//   D_i <- sum_k c_k D_k + r_i,   r_i = sum_k c_k x^n_k - x^n_i,
+// the same iterates in exact arithmetic, with D free of the positions'
+// magnitude (so T = float keeps the displacement to FP32 relative precision
+// in the mixed form).  A block owns a TX x TY tile and iterates nsw <= SB
+// sweeps on the tile plus an SB-wide halo in shared memory (the valid region
+// shrinks by one node per sweep), then writes the tile: one launch for SB
+// sweeps.  Halo nodes across a periodic end are the periodic images in
+// unwrapped coordinates; nodes across an outflow or inflow end are read only
+// by fixed boundary nodes and are held at 0.
+constexpr int MT_TX = 32, MT_TY = 16, MT_THREADS = 256;
+
+template <typename T, int SB>
+constexpr size_t mesh_sweeps_smem()
 {
-    for (int comp = 0; comp < 2; ++comp)
-        out[comp] = ce * mesh_at(g, X, i + 1, j, comp, 1) + cwe * mesh_at(g, X, i - 1, j, comp, 1) +
-                    cn * mesh_at(g, X, i, j + 1, comp, 1) + cs * mesh_at(g, X, i, j - 1, comp, 1);
+    return (size_t)(10 * sizeof(T) + 1) * (MT_TX + 2 * SB) * (MT_TY + 2 * SB);
 }
 
-// one Jacobi sweep with the weights of k_mesh_weights; the boundary nodes of
-// an outflow direction stay
-__global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ cw, const double *__restrict__ X,
-                              double *__restrict__ Xn)
+template <typename T, int SB>
+__global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const double *__restrict__ x,
+                                                            const double *__restrict__ cw,
+                                                            const T *__restrict__ Din, T *__restrict__ Dout,
+                                                            int nsw)
+{
+    constexpr int RX = MT_TX + 2 * SB, RY = MT_TY + 2 * SB, RN = RX * RY;
+    extern __shared__ __align__(16) unsigned char mt_smem[];
+    T *sD = reinterpret_cast<T *>(mt_smem);      // [2 buffers][2 components][RN]
+    T *sW = sD + 4 * RN;                         // [4][RN]  c_E, c_W, c_N, c_S
+    T *sR = sW + 4 * RN;                         // [2][RN]  r
+    unsigned char *sF = reinterpret_cast<unsigned char *>(sR + 2 * RN);   // [RN] node held
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    x += 2 * D.on;
+    cw += 4 * D.on;
+    if (Din) Din += 2 * D.on;
+    Dout += 2 * D.on;
+    const int ntx = (g.nx + MT_TX - 1) / MT_TX;
+    const int ti = (int)(lb % ntx) * MT_TX, tj = (int)(lb / ntx) * MT_TY;
+    for (int r = threadIdx.x; r < RN; r += blockDim.x) {
+        const int gi = ti - SB + r % RX, gj = tj - SB + r / RX;
+        const bool outx = gi < 0 || gi >= g.nx, outy = gj < 0 || gj >= g.ny;
+        if ((outx && g.bc0 != 0) || (outy && g.bc1 != 0)) {
+            sF[r] = 1;
+            for (int a = 0; a < 4; ++a) sW[a * RN + r] = (T)0;
+            for (int c = 0; c < 2; ++c) { sD[c * RN + r] = (T)0; sD[(2 + c) * RN + r] = (T)0; sR[c * RN + r] = (T)0; }
+            continue;
+        }
+        const int si = outx ? wrapi(gi, g.nx) : gi, sj = outy ? wrapi(gj, g.ny) : gj;
+        const long long id = (long long)sj * g.nx + si;
+        const bool fixed = (g.bc0 != 0 && (si == 0 || si == g.nx - 1)) || (g.bc1 != 0 && (sj == 0 || sj == g.ny - 1));
+        sF[r] = fixed;
+        const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
+        sW[r] = (T)ce;
+        sW[RN + r] = (T)cwe;
+        sW[2 * RN + r] = (T)cn;
+        sW[3 * RN + r] = (T)cs;
+        for (int c = 0; c < 2; ++c) {
+            double res = 0.0;
+            if (!fixed) {
+                const bool inner = gi > 0 && gi < g.nx - 1 && gj > 0 && gj < g.ny - 1;
+                const double *a = x + c * g.N;
+                const long long o = (long long)gj * g.nx + gi;
+                const double xi = inner ? a[o] : mesh_edge(g, x, gi, gj, c);
+                const double xe = inner ? a[o + 1] : mesh_edge(g, x, gi + 1, gj, c);
+                const double xw = inner ? a[o - 1] : mesh_edge(g, x, gi - 1, gj, c);
+                const double xn = inner ? a[o + g.nx] : mesh_edge(g, x, gi, gj + 1, c);
+                const double xs = inner ? a[o - g.nx] : mesh_edge(g, x, gi, gj - 1, c);
+                res = ce * xe + cwe * xw + cn * xn + cs * xs - xi;
+            }
+            sR[c * RN + r] = (T)res;
+            sD[c * RN + r] = Din ? Din[c * g.N + id] : (T)0;
+        }
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int s = 0; s < nsw; ++s) {
+        const T *Dc = sD + cur * 2 * RN;
+        T *Dn = sD + (cur ^ 1) * 2 * RN;
+        for (int r = threadIdx.x; r < RN; r += blockDim.x) {
+            const int li = r % RX, lj = r / RX;
+            if (li <= s || li >= RX - 1 - s || lj <= s || lj >= RY - 1 - s) continue;
+            for (int c = 0; c < 2; ++c) {
+                const T *d = Dc + c * RN;
+                Dn[c * RN + r] = sF[r] ? d[r]
+                                       : sW[r] * d[r + 1] + sW[RN + r] * d[r - 1] + sW[2 * RN + r] * d[r + RX] +
+                                             sW[3 * RN + r] * d[r - RX] + sR[c * RN + r];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    const T *Df = sD + cur * 2 * RN;
+    for (int r = threadIdx.x; r < MT_TX * MT_TY; r += blockDim.x) {
+        const int gi = ti + r % MT_TX, gj = tj + r / MT_TX;
+        if (gi >= g.nx || gj >= g.ny) continue;
+        const int rr = (r / MT_TX + SB) * RX + (r % MT_TX + SB);
+        const long long id = (long long)gj * g.nx + gi;
+        Dout[id] = Df[rr];
+        Dout[g.N + id] = Df[RN + rr];
+    }
+}
+
+// The same iteration one sweep per launch, for the FP64 form (where the
+// blocked kernel's halo work would cost FP64 issue slots): the residual r
+// once per redistribution, then D_i <- sum_k c_k D_k + r_i.  D needs no ghost
+// arithmetic: it is shift-free across a periodic end and 0 at held nodes,
+// and nodes next to an outflow end read only the held boundary nodes.
+__global__ void k_mesh_resid(ProbArg pa, const double *__restrict__ x, const double *__restrict__ cw,
+                             double *__restrict__ rs)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    x += 2 * D.on;
+    cw += 4 * D.on;
+    rs += 2 * D.on;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    bool fixed = (g.bc0 != 0 && (i == 0 || i == g.nx - 1)) || (g.bc1 != 0 && (j == 0 || j == g.ny - 1));
+    const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
+    const bool inner = i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1;
+    for (int c = 0; c < 2; ++c) {
+        double r = 0.0;
+        if (!fixed) {
+            const double *a = x + c * g.N;
+            const double xe = inner ? a[id + 1] : mesh_edge(g, x, i + 1, j, c);
+            const double xw = inner ? a[id - 1] : mesh_edge(g, x, i - 1, j, c);
+            const double xn = inner ? a[id + g.nx] : mesh_edge(g, x, i, j + 1, c);
+            const double xs = inner ? a[id - g.nx] : mesh_edge(g, x, i, j - 1, c);
+            r = ce * xe + cwe * xw + cn * xn + cs * xs - a[id];
+        }
+        rs[c * g.N + id] = r;
+    }
+}
+
+__global__ void k_mesh_sweep(ProbArg pa, const double *__restrict__ cw, const double *__restrict__ rs,
+                             const double *__restrict__ Din, double *__restrict__ Dout)
 {
     ProbDesc D;
     long long lb;
@@ -472,26 +612,22 @@ __global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ cw, const d
     long long id = lb * blockDim.x + threadIdx.x;
     if (id >= g.N) return;
     cw += 4 * D.on;
-    X += 2 * D.on;
-    Xn += 2 * D.on;
+    rs += 2 * D.on;
+    Dout += 2 * D.on;
     int i = (int)(id % g.nx), j = (int)(id / g.nx);
     bool fixed = (g.bc0 != 0 && (i == 0 || i == g.nx - 1)) || (g.bc1 != 0 && (j == 0 || j == g.ny - 1));
-    if (fixed) {
-        Xn[id] = X[id];
-        Xn[g.N + id] = X[g.N + id];
+    if (!Din || fixed) {        // the first sweep from D = 0, and held nodes
+        for (int c = 0; c < 2; ++c) Dout[c * g.N + id] = fixed ? 0.0 : rs[c * g.N + id];
         return;
     }
+    Din += 2 * D.on;
+    const long long e = i == g.nx - 1 ? id - (g.nx - 1) : id + 1, w = i == 0 ? id + (g.nx - 1) : id - 1;
+    const long long n = j == g.ny - 1 ? id - (long long)(g.ny - 1) * g.nx : id + g.nx;
+    const long long s = j == 0 ? id + (long long)(g.ny - 1) * g.nx : id - g.nx;
     const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
-    if (i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1) {
-        for (int comp = 0; comp < 2; ++comp) {
-            const double *a = X + comp * g.N + id;
-            Xn[comp * g.N + id] = ce * a[1] + cwe * a[-1] + cn * a[g.nx] + cs * a[-g.nx];
-        }
-    } else {
-        double out[2];
-        jacobi_edge(g, X, i, j, ce, cwe, cn, cs, out);
-        Xn[id] = out[0];
-        Xn[g.N + id] = out[1];
+    for (int c = 0; c < 2; ++c) {
+        const double *d = Din + c * g.N;
+        Dout[c * g.N + id] = ce * d[e] + cwe * d[w] + cn * d[n] + cs * d[s] + rs[c * g.N + id];
     }
 }
 
@@ -499,7 +635,9 @@ __global__ void k_mesh_jacobi(ProbArg pa, const double *__restrict__ cw, const d
 // neighbour spacing over the displacement toward it, clipped to [0, 1]; and
 // the displacement's Courant number max |d.(J xi_k,x)|/J per direction (the
 // node metrics of x^n in q, J of the state)
-__global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const double *__restrict__ X,
+// (Dd: the displacement x^[mu] - x^n of k_mesh_sweeps)
+template <typename T>
+__global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const T *__restrict__ Dd,
                            const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red)
 {
     ProbDesc D;
@@ -508,7 +646,7 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const doubl
     const Geom &g = D.g;
     long long id = lb * blockDim.x + threadIdx.x;
     x += 2 * D.on;
-    X += 2 * D.on;
+    Dd += 2 * D.on;
     J += D.on;
     q += (long long)NQ * D.op;
     double tau = 1.0, cm[2] = {0.0, 0.0};
@@ -516,7 +654,7 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const doubl
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
         double dd[2];
         for (int k = 0; k < 2; ++k) {
-            double d = X[k * g.N + id] - x[k * g.N + id];
+            double d = (double)Dd[k * g.N + id];
             dd[k] = d;
             int di = k == 0, dj = k == 1;
             const bool inner = k == 0 ? (i > 0 && i < g.nx - 1) : (j > 0 && j < g.ny - 1);
@@ -544,10 +682,11 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const doubl
     }
 }
 
-// xdot = Delta tau (x^[mu] - x^n) / dt (over 2 N values per problem)
-__global__ void k_mesh_xdot(ProbArg pa, const double *__restrict__ x, const double *__restrict__ X,
-                            const unsigned long long *red, const double *__restrict__ dt_dev,
-                            double *__restrict__ xdot)
+// xdot = Delta tau (x^[mu] - x^n) / dt (over 2 N values per problem; Dd the
+// displacement x^[mu] - x^n)
+template <typename T>
+__global__ void k_mesh_xdot(ProbArg pa, const T *__restrict__ Dd, const unsigned long long *red,
+                            const double *__restrict__ dt_dev, double *__restrict__ xdot)
 {
     ProbDesc D;
     long long lb;
@@ -559,7 +698,7 @@ __global__ void k_mesh_xdot(ProbArg pa, const double *__restrict__ x, const doub
     __syncthreads();
     if (id >= 2 * g.N) return;
     long long o = 2 * D.on + id;
-    xdot[o] = s * (X[o] - x[o]);
+    xdot[o] = s * (double)Dd[o];
 }
 
 // ---- state set-up and read-out ------------------------------------------------
