@@ -290,7 +290,8 @@ void node(esmm_grid *g, const double *cons, const double *J, const double *x, co
     Prof pr_(g, ESMM_KIND_NODE);
     if (g->phys == ESMM_RMHD)
         launch_node_mhd(dom(g, D_PAD), g->p, g->gamma, cons, J, x, xdot, pg_in, pg_out, g->q, g->status,
-                        g->has_inflow ? g->inflow_dev : nullptr, g->st);
+                        g->has_inflow ? g->inflow_dev : nullptr,
+                        g->prm.precision == ESMM_MIXED && !exact_logs, g->st);
     else
         launch_node(g, dom(g, D_PAD), cons, J, x, xdot, pg_in, pg_out, g->q, exact_logs);
 }

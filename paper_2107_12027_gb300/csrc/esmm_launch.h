@@ -55,7 +55,7 @@ constexpr int NQ_MHD = 18;
 constexpr int NF_MHD = 10;
 void launch_node_mhd(const LaunchDom &L, int p, double gam, const double *cons, const double *J, const double *x,
                      const double *xdot, const double *zg_in, double *zg_out, double *q, int *status,
-                     const double *inflow, cudaStream_t st);
+                     const double *inflow, int f32_logs, cudaStream_t st);
 void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, void *iflux, int dir, cudaStream_t st);
 void launch_update_mhd(const LaunchDom &L, const double *q, const void *fl, double *dcons, double *dJ,
                        const double *cn, const double *Jn, const double *xn, const double *cs, const double *Js,

@@ -68,14 +68,17 @@ __global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, 
 
 void launch_node_mhd(const LaunchDom &L, int p, double gam, const double *cons, const double *J, const double *x,
                      const double *xdot, const double *zg_in, double *zg_out, double *q, int *status,
-                     const double *inflow, cudaStream_t st)
+                     const double *inflow, int f32_logs, cudaStream_t st)
 {
     if (p == 1)
-        k_node_mhd<1><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status, inflow);
+        k_node_mhd<1><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status, inflow,
+                                               f32_logs);
     else if (p == 2)
-        k_node_mhd<2><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status, inflow);
+        k_node_mhd<2><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status, inflow,
+                                               f32_logs);
     else
-        k_node_mhd<3><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status, inflow);
+        k_node_mhd<3><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, cons, J, x, xdot, zg_in, zg_out, q, status, inflow,
+                                               f32_logs);
 }
 
 void launch_iface_mhd(const LaunchDom &L, const Phys &ph, const double *q, void *iflux, int dir, cudaStream_t st)

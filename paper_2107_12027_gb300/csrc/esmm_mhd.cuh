@@ -483,8 +483,8 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> 
                                             const R m[3], R out[8])
 {
     R rln, irln, bln, ibln;
-    logmean<R, typename LogT<R>::type>(L.rho, Rn.rho, L.lnr, Rn.lnr, thr, rln, irln);
-    logmean<R, typename LogT<R>::type>(L.beta, Rn.beta, L.lnb, Rn.lnb, thr, bln, ibln);
+    lmean<R, typename LogT<R>::type>(L.rho, Rn.rho, L.lnr, Rn.lnr, L.r, Rn.r, thr, rln, irln);
+    lmean<R, typename LogT<R>::type>(L.beta, Rn.beta, L.lnb, Rn.lnb, L.b, Rn.b, thr, bln, ibln);
     const R half = (R)0.5;
     R bL[3], bR[3], vL[3], vR[3];
     // b^0 = W (v.B) = u.B
@@ -588,7 +588,7 @@ template <int P>
 __global__ void k_node_mhd(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
                            const double *__restrict__ x, const double *__restrict__ xdot,
                            const double *__restrict__ zg_in, double *__restrict__ zg_out, double *__restrict__ q,
-                           int *__restrict__ status, const double *__restrict__ inflow)
+                           int *__restrict__ status, const double *__restrict__ inflow, int f32_logs)
 {
     ProbDesc D;
     long long lb;
@@ -624,8 +624,11 @@ __global__ void k_node_mhd(ProbArg pa, double gam, const double *__restrict__ co
     q[Q_UY * g.P + t] = W * w[2];
     q[QM_UZ * g.P + t] = W * w[3];
     q[Q_W * g.P + t] = W;
-    q[Q_LNR * g.P + t] = log(w[0]);
-    q[Q_LNB * g.P + t] = log(beta);
+    // (f32_logs: the mixed form's scheme passes, where the logarithms enter
+    // only FP32 arithmetic and the log mean's jump outside its near-equal
+    // branch)
+    q[Q_LNR * g.P + t] = f32_logs ? (double)logf((float)w[0]) : log(w[0]);
+    q[Q_LNB * g.P + t] = f32_logs ? (double)logf((float)beta) : log(beta);
     q[QM_B1 * g.P + t] = w[5];
     q[QM_B2 * g.P + t] = w[6];
     q[QM_B3 * g.P + t] = w[7];
@@ -737,8 +740,8 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
         R wm[8], wrot[8];
         {
             R rho, irho;
-            logmean<R, double>(q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1], q[Q_LNR * g.P + c0],
-                               q[Q_LNR * g.P + c1], ph.ln_thr, rho, irho);
+            lmean<R, double>(q[Q_RHO * g.P + c0], q[Q_RHO * g.P + c1], q[Q_LNR * g.P + c0], q[Q_LNR * g.P + c1],
+                             (R)q[Q_RHO * g.P + c0], (R)q[Q_RHO * g.P + c1], ph.ln_thr, rho, irho);
             R um[3] = {half * ((R)q[Q_UX * g.P + c0] + (R)q[Q_UX * g.P + c1]),
                        half * ((R)q[Q_UY * g.P + c0] + (R)q[Q_UY * g.P + c1]),
                        half * ((R)q[QM_UZ * g.P + c0] + (R)q[QM_UZ * g.P + c1])};
