@@ -357,10 +357,13 @@ __device__ __forceinline__ void logmean(T a, T b, T la, T lb, double thr, R &mea
 {
     T d = b - a, s = b + a;
     if (val(d * d) < val(thr * s * s)) {
-        T u = d * d / (s * s);
+        // (two reciprocals for the three quotients: each product is within
+        // an ulp of the quotient it stands for)
+        T is = rcp<T>(s);
+        T r = d * is, u = r * r;
         T F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
-        mean = (R)(s / (2.0 * F));
-        inv_mean = (R)(2.0 * F / s);
+        mean = (R)(0.5 * s * rcp<T>(F));
+        inv_mean = (R)(2.0 * F * is);
     } else {
         R dn = (R)d, dl = (R)(lb - la);
         mean = dn * rcp<R>(dl);
