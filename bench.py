@@ -63,17 +63,17 @@ FLOPS_PER_IFACE_F32 = 1259
 TRAFFIC_IFACE_F32 = 13.08e6
 # The same for the RMHD interface kernels at p = 2, WENO5 (profiles/
 # iface_mhd_ops_rotor512_blast64.md): the FP64 2D kernel on the 512^2 rotor
-# (16,156 FP64 flops per interface; 1.036 GB of DRAM traffic per launch, the
-# eigen-system's per-thread stack), its FP32 instance (12,242 FP32 flops per
-# interface besides 492 FP64 ones; 0.478 GB), and the 3D kernel (20,147 FP64
-# flops per interface; 1.217 GB at 64^3, scaled by the 7.94x interfaces of
+# (11,042 FP64 flops per interface; 1.021 GB of DRAM traffic per launch, the
+# eigen-system's per-thread stack), its FP32 instance (10,832 FP32 flops per
+# interface besides 98 FP64 ones; 0.479 GB), and the 3D kernel (16,409 FP64
+# flops per interface; 1.210 GB at 64^3, scaled by the 7.94x interfaces of
 # a 128^3 launch -- the stack traffic grows with the threads).
-FLOPS_PER_IFACE_MHD2 = 16156
-TRAFFIC_IFACE_MHD2 = 1.036e9
-FLOPS_PER_IFACE_MHD2_F32 = 12242
-TRAFFIC_IFACE_MHD2_F32 = 0.478e9
-FLOPS_PER_IFACE_MHD3 = 20147
-TRAFFIC_IFACE_MHD3 = 9.66e9
+FLOPS_PER_IFACE_MHD2 = 11042
+TRAFFIC_IFACE_MHD2 = 1.021e9
+FLOPS_PER_IFACE_MHD2_F32 = 10832
+TRAFFIC_IFACE_MHD2_F32 = 0.479e9
+FLOPS_PER_IFACE_MHD3 = 16409
+TRAFFIC_IFACE_MHD3 = 9.61e9
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 # Algorithmic HBM bytes per node and RK stage of the whole step, fused to the

@@ -196,7 +196,7 @@ __device__ __forceinline__ dual operator-(dual a) { return dual(-a.v, -a.d); }
 __device__ __forceinline__ dual operator*(dual a, dual b) { return dual(a.v * b.v, a.d * b.v + a.v * b.d); }
 __device__ __forceinline__ dual operator/(dual a, dual b)
 {
-    double r = 1.0 / b.v;
+    double r = __drcp_rn(b.v);
     double q = a.v * r;
     return dual(q, (a.d - q * b.d) * r);
 }
@@ -206,7 +206,11 @@ __device__ __forceinline__ dual operator-(dual a, double b) { return dual(a.v - 
 __device__ __forceinline__ dual operator-(double a, dual b) { return dual(a - b.v, -b.d); }
 __device__ __forceinline__ dual operator*(dual a, double b) { return dual(a.v * b, a.d * b); }
 __device__ __forceinline__ dual operator*(double a, dual b) { return dual(a * b.v, a * b.d); }
-__device__ __forceinline__ dual operator/(dual a, double b) { return dual(a.v / b, a.d / b); }
+__device__ __forceinline__ dual operator/(dual a, double b)
+{
+    const double r = __drcp_rn(b);
+    return dual(a.v * r, a.d * r);
+}
 __device__ __forceinline__ dual operator/(double a, dual b) { return dual(a) / b; }
 __device__ __forceinline__ dual &operator+=(dual &a, dual b) { a = a + b; return a; }
 __device__ __forceinline__ dual &operator-=(dual &a, dual b) { a = a - b; return a; }
@@ -270,7 +274,7 @@ __device__ __forceinline__ hdual hchain(hdual x, double f, double f1, double f2)
 }
 __device__ __forceinline__ hdual hrcp(hdual x)
 {
-    double r = 1.0 / x.v;
+    double r = __drcp_rn(x.v);
     return hchain(x, r, -r * r, 2.0 * r * r * r);
 }
 __device__ __forceinline__ hdual operator/(hdual x, hdual y) { return x * hrcp(y); }
@@ -280,7 +284,7 @@ __device__ __forceinline__ hdual operator-(hdual x, double y) { return hdual(x.v
 __device__ __forceinline__ hdual operator-(double x, hdual y) { return hdual(x - y.v, -y.a, -y.b, -y.ab); }
 __device__ __forceinline__ hdual operator*(hdual x, double y) { return hdual(x.v * y, x.a * y, x.b * y, x.ab * y); }
 __device__ __forceinline__ hdual operator*(double x, hdual y) { return hdual(x * y.v, x * y.a, x * y.b, x * y.ab); }
-__device__ __forceinline__ hdual operator/(hdual x, double y) { return x * (1.0 / y); }
+__device__ __forceinline__ hdual operator/(hdual x, double y) { return x * __drcp_rn(y); }
 __device__ __forceinline__ hdual operator/(double x, hdual y) { return x * hrcp(y); }
 
 // the dual number over a working precision (hdual over dual)
@@ -338,6 +342,23 @@ template <> __device__ __forceinline__ dual rcp<dual>(dual x)
 {
     double r = __drcp_rn(x.v);
     return dual(r, -r * r * x.d);
+}
+template <> __device__ __forceinline__ fdual rcp<fdual>(fdual x)
+{
+    float r = __frcp_rn(x.v);
+    return fdual(r, -r * r * x.d);
+}
+template <> __device__ __forceinline__ hdual rcp<hdual>(hdual x) { return hrcp(x); }
+template <> __device__ __forceinline__ fdual rsq<fdual>(fdual x)
+{
+    float r = rsqrtf(x.v);
+    return fdual(r, -0.5f * r * r * r * x.d);
+}
+template <> __device__ __forceinline__ hdual rsq<hdual>(hdual x)
+{
+    // x^-1/2 and its first two derivatives
+    double r = rsqrt(x.v), ir = __drcp_rn(x.v);
+    return hchain(x, r, -0.5 * r * ir, 0.75 * r * ir * ir);
 }
 template <typename R> __device__ __forceinline__ R sqrt_pos(R x) { return x * rsq<R>(x); }
 template <typename R> __device__ __forceinline__ R fab(R x);

@@ -29,7 +29,10 @@ constexpr int NFM = 10;                          // interface values per directi
 //   f(Z) = Z - p + |B|^2 (1 + |v|^2)/2 - S^2/(2 Z^2) - E,
 // a trial Z with |v|^2 >= 1 lying below the root.  Stops when a step moves Z
 // by at most 1e-15 (E + Z), or where |f| <= 2e-15 (E + Z), f's rounding
-// level (a root, whose tiny steps the open bracket would otherwise reject).  Z0: warm start (ignored outside the bracket).
+// level (a root, whose tiny steps the open bracket would otherwise reject).
+// Z0: warm start (ignored outside the bracket).  Quotients are taken through
+// reciprocals, and the Newton step divides by df through an FP32 reciprocal
+// (the slope only steers the step; f, which decides the stopping, is FP64).
 // Returns 0, 1 (non-admissible) or 2 (iteration cap).
 __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], double Z0, double w[8], double &Zout)
 {
@@ -48,42 +51,42 @@ __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], doub
     int ok = 0;
     for (int it = 0; it < 300; ++it) {
         double ZB = Z + B2;
-        double iZ = 1.0 / Z;
+        double iZ = __drcp_rn(Z);
         double N = m2 + (2.0 * Z + B2) * S2 * iZ * iZ;
-        double iZB = 1.0 / ZB;
+        double iZB = __drcp_rn(ZB);
         double v2 = N * iZB * iZB;
         double Zn;
         if (!(v2 < 1.0)) {
             lo = Z;
             Zn = 0.5 * (lo + hi);
         } else {
-            double iW2 = 1.0 - v2, iW = sqrt(iW2);
+            double iW2 = 1.0 - v2, rs = rsqrt(iW2), iW = iW2 * rs;
             double p = g * (Z * iW2 - D * iW);
             double f = Z - p + 0.5 * B2 * (1.0 + v2) - 0.5 * S2 * iZ * iZ - E;
             double dN = -2.0 * S2 * iZ * iZ - 2.0 * B2 * S2 * iZ * iZ * iZ;
             double dv2 = dN * iZB * iZB - 2.0 * N * iZB * iZB * iZB;
-            double dp = g * (iW2 - Z * dv2 + 0.5 * D * dv2 / iW);
+            double dp = g * (iW2 - Z * dv2 + 0.5 * D * dv2 * rs);
             double df = 1.0 - dp + 0.5 * B2 * dv2 + S2 * iZ * iZ * iZ;
             if (fabs(f) <= 2.0e-15 * (E + Z)) { ok = 1; break; }   // residual at rounding level
             Zn = Z;                          // f = 0: Z is a root
             if (f != 0.0) {
                 if (f < 0.0) lo = Z; else hi = Z;
-                Zn = Z - f / df;
+                Zn = Z - f * (double)__frcp_rn((float)df);
                 if (!(Zn > lo && Zn < hi)) Zn = 0.5 * (lo + hi);
             }
         }
         if (fabs(Zn - Z) <= 1.0e-15 * (E + Zn)) { Z = Zn; ok = 1; break; }
         Z = Zn;
     }
-    double ZB = Z + B2;
-    double v2 = (m2 + (2.0 * Z + B2) * S2 / (Z * Z)) / (ZB * ZB);
+    double ZB = Z + B2, iZ = __drcp_rn(Z), iZB = __drcp_rn(ZB);
+    double v2 = (m2 + (2.0 * Z + B2) * S2 * iZ * iZ) * iZB * iZB;
     if (!(v2 < 1.0)) return 1;
     double iW2 = 1.0 - v2, iW = sqrt(iW2);
-    double vB = S / Z;
+    double vB = S * iZ;
     w[0] = D * iW;
-    w[1] = (m0 + vB * B0) / ZB;
-    w[2] = (m1 + vB * B1) / ZB;
-    w[3] = (m2_ + vB * B2_) / ZB;
+    w[1] = (m0 + vB * B0) * iZB;
+    w[2] = (m1 + vB * B1) * iZB;
+    w[3] = (m2_ + vB * B2_) * iZB;
     w[4] = g * (Z * iW2 - D * iW);
     w[5] = B0; w[6] = B1; w[7] = B2_;
     Zout = Z;
@@ -95,11 +98,11 @@ __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], doub
 // so that dual numbers give directional derivatives.
 template <typename T> __device__ __forceinline__ T lg(T x);
 template <> __device__ __forceinline__ double lg<double>(double x) { return log(x); }
-template <> __device__ __forceinline__ dual lg<dual>(dual x) { return dual(log(x.v), x.d / x.v); }
+template <> __device__ __forceinline__ dual lg<dual>(dual x) { return dual(log(x.v), x.d * __drcp_rn(x.v)); }
 template <> __device__ __forceinline__ fdual lg<fdual>(fdual x) { return fdual(logf(x.v), x.d * __frcp_rn(x.v)); }
 template <> __device__ __forceinline__ hdual lg<hdual>(hdual x)
 {
-    double r = 1.0 / x.v;
+    double r = __drcp_rn(x.v);
     return hchain(x, log(x.v), r, -r * r);
 }
 
@@ -109,8 +112,8 @@ __device__ __forceinline__ void mhd_UFV(double gam, const T w[8], T U[8], T F[8]
     T rho = w[0], p = w[4];
     T v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
     T iW2 = 1.0 - v2;
-    T W2 = 1.0 / iW2;
-    T W = sq_rt<T>(W2);
+    T W = rsq<T>(iW2);                 // (reciprocals and rsqrt: no FP64 quotient)
+    T W2 = W * W;
     T vB = w[1] * w[5] + w[2] * w[6] + w[3] * w[7];
     T B2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
     T bb = B2 * iW2 + vB * vB;
@@ -130,14 +133,15 @@ __device__ __forceinline__ void mhd_UFV(double gam, const T w[8], T U[8], T F[8]
     F[4] = U[1];
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[5 + k] = w[1] * w[5 + k] - w[5] * w[1 + k];
-    T beta = rho / p;
+    T beta = rho * rcp<T>(p);
     T s = lg<T>(p) - gam * lg<T>(rho);
-    V[0] = (gam - s) / (gam - 1.0) + beta;
+    V[0] = (gam - s) * (1.0 / (gam - 1.0)) + beta;
 #pragma unroll
     for (int k = 0; k < 3; ++k) V[1 + k] = beta * W * w[1 + k];
     V[4] = -beta * W;
+    const T bW = beta * iW2 * W;       // beta / W
 #pragma unroll
-    for (int k = 0; k < 3; ++k) V[5 + k] = beta * (w[5 + k] + W2 * w[1 + k] * vB) / W;
+    for (int k = 0; k < 3; ++k) V[5 + k] = bW * (w[5 + k] + W2 * w[1 + k] * vB);
 }
 
 // Images (dU, dV, dF~) of the primitive perturbation dir at w, with the
@@ -222,9 +226,15 @@ __device__ __forceinline__ void jacobi6(S C[6][6], S Q[6][6], bool want_vectors)
 #pragma unroll 1
             for (int q = p + 1; q < 6; ++q) {
                 if (C[p][q] == (S)0) continue;
-                S theta = (C[q][q] - C[p][p]) / ((S)2 * C[p][q]);
-                S t = (theta >= (S)0 ? (S)1 : (S)-1) / (fab<S>(theta) + sq_rt<S>(theta * theta + (S)1));
-                S cs = (S)1 / sq_rt<S>(t * t + (S)1), sn = t * cs;
+                // (reciprocals for the rotation's quotients: FP64 divisions
+                // cost ~15 FP64-pipe instructions each on this GPU).  A tiny
+                // C_pq can have an infinite reciprocal: equal diagonals then
+                // take theta = 0 (as the quotient 0 / (2 C_pq) does), unequal
+                // ones theta = +-inf, hence t = 0 (no rotation)
+                const S diff = C[q][q] - C[p][p];
+                S theta = diff == (S)0 ? (S)0 : diff * ((S)0.5 * rcp<S>(C[p][q]));
+                S t = (theta >= (S)0 ? (S)1 : (S)-1) * rcp<S>(fab<S>(theta) + sq_rt<S>(theta * theta + (S)1));
+                S cs = rsq<S>(t * t + (S)1), sn = t * cs;
 #pragma unroll 1
                 for (int k = 0; k < 6; ++k) {
                     S ckp = C[k][p], ckq = C[k][q];
@@ -260,6 +270,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
     mhd_images(gam, w, a_rho, Pp, Ur, Vr, Fr);
     mhd_images(gam, w, a_div, Pp, Ud, Vd, Fd);
     const R n_rho = dot8(Ur, Vr), n_div = dot8(Ud, Vd);
+    const R in_rho = rcp<R>(n_rho), in_div = rcp<R>(n_div);
     const int comp[6] = {1, 2, 3, 4, 6, 7};
     R Uy[6][8], Vy[6][8], Fy[6][8];
     for (int a = 0; a < 6; ++a) {
@@ -267,7 +278,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
         e[comp[a]] = (R)1;
         R Ue[8], Ve[8], Fe[8];
         mhd_images(gam, w, e, Pp, Ue, Ve, Fe);
-        R cr = dot8(Ue, Vr) / n_rho, cd = dot8(Ue, Vd) / n_div;
+        R cr = dot8(Ue, Vr) * in_rho, cd = dot8(Ue, Vd) * in_div;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             Uy[a][r] = Ue[r] - cr * Ur[r] - cd * Ud[r];
@@ -294,17 +305,20 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
             Gm[a][b] = Gm[b][a] = g;
             C[a][b] = C[b][a] = k;
         }
-    // Cholesky G = L L^T (lower triangle of Gm)
+    // Cholesky G = L L^T (lower triangle of Gm), with the reciprocals of
+    // its diagonal (idg) serving every division of the factor and the solves
+    R idg[6];
     for (int j = 0; j < 6; ++j) {
         R d = Gm[j][j];
         for (int k = 0; k < j; ++k) d -= Gm[j][k] * Gm[j][k];
         if constexpr (std::is_same<R, float>::value)
             if (!(d > (R)1.0e-12)) d = (R)1.0e-12;   // FP32: keep the factor finite
         Gm[j][j] = sq_rt<R>(d);
+        idg[j] = rcp<R>(Gm[j][j]);
         for (int i = j + 1; i < 6; ++i) {
             R s = Gm[i][j];
             for (int k = 0; k < j; ++k) s -= Gm[i][k] * Gm[j][k];
-            Gm[i][j] = s / Gm[j][j];
+            Gm[i][j] = s * idg[j];
         }
     }
     // C <- L^-1 K L^-T (column solves, then row solves)
@@ -312,13 +326,13 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
         for (int i = 0; i < 6; ++i) {
             R s = C[i][c];
             for (int k = 0; k < i; ++k) s -= Gm[i][k] * C[k][c];
-            C[i][c] = s / Gm[i][i];
+            C[i][c] = s * idg[i];
         }
     for (int r = 0; r < 6; ++r)
         for (int i = 0; i < 6; ++i) {
             R s = C[r][i];
             for (int k = 0; k < i; ++k) s -= Gm[i][k] * C[r][k];
-            C[r][i] = s / Gm[i][i];
+            C[r][i] = s * idg[i];
         }
     for (int a = 0; a < 6; ++a)
         for (int b = 0; b < a; ++b) C[a][b] = C[b][a] = (R)0.5 * (C[a][b] + C[b][a]);
@@ -432,7 +446,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
         for (int i = 5; i >= 0; --i) {
             R acc = E6[i][m];
             for (int k = i + 1; k < 6; ++k) acc -= Gm[k][i] * s[k];
-            s[i] = acc / Gm[i][i];
+            s[i] = acc * idg[i];
         }
         for (int r = 0; r < 8; ++r) {
             R acc = (R)0;
@@ -490,7 +504,7 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> 
     // b^0 = W (v.B) = u.B
     R b0L = L.u[0] * L.B[0] + L.u[1] * L.B[1] + L.u[2] * L.B[2];
     R b0R = Rn.u[0] * Rn.B[0] + Rn.u[1] * Rn.B[1] + Rn.u[2] * Rn.B[2];
-    R iWL = (R)1 / L.W, iWR = (R)1 / Rn.W;
+    R iWL = rcp<R>(L.W), iWR = rcp<R>(Rn.W);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         bL[k] = (L.B[k] + b0L * L.u[k]) * iWL;
@@ -513,7 +527,7 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> 
     const R usq = u_m[0] * u_m[0] + u_m[1] * u_m[1] + u_m[2] * u_m[2];
     const R Lam = W_m * W_m - usq;
     const R alpha0 = (R)1 + gm1inv * ibln;
-    const R iW_m = (R)1 / W_m, ibeta_m = (R)1 / beta_m;
+    const R iW_m = rcp<R>(W_m), ibeta_m = rcp<R>(beta_m), iLam = rcp<R>(Lam);
     const R bsq_sum = bsq_m[0] + bsq_m[1] + bsq_m[2];
     // U~
     R Ut[8];
@@ -528,7 +542,7 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> 
         for (int k = 0; k < 3; ++k) R1 += half * Wbsq_m[k] - b_m[k] * UB[k];
 #pragma unroll
         for (int k = 0; k < 3; ++k) Rk[k] = (alpha1 * u_m[k] - beta_m * c_m * b_m[k]) * iW_m;
-        const R U5 = (u_m[0] * Rk[0] + u_m[1] * Rk[1] + u_m[2] * Rk[2] - beta_m * R1) * W_m / (beta_m * Lam);
+        const R U5 = (u_m[0] * Rk[0] + u_m[1] * Rk[1] + u_m[2] * Rk[2] - beta_m * R1) * W_m * ibeta_m * iLam;
         Ut[0] = U1;
 #pragma unroll
         for (int k = 0; k < 3; ++k) Ut[1 + k] = u_m[k] * U5 * iW_m + Rk[k] * ibeta_m;
@@ -574,7 +588,7 @@ __device__ __forceinline__ void ec_pair_mhd(const NodeMT<R> &L, const NodeMT<R> 
         R acc = alpha0 * F[0] - r_beta;
 #pragma unroll
         for (int k = 0; k < 3; ++k) acc += u_m[k] * r_u[k] * ibeta_m + b_m[k] * F[5 + k];
-        F[4] = W_m * acc / Lam;
+        F[4] = W_m * acc * iLam;
 #pragma unroll
         for (int k = 0; k < 3; ++k) F[1 + k] = r_u[k] * ibeta_m + u_m[k] * F[4] * iW_m;
 #pragma unroll
@@ -663,7 +677,7 @@ __device__ __forceinline__ void node_V_mhd(const double *__restrict__ q, long lo
     R u0 = (R)q[Q_UX * P + c], u1 = (R)q[Q_UY * P + c], u2 = (R)q[QM_UZ * P + c];
     R B0 = (R)q[QM_B1 * P + c], B1 = (R)q[QM_B2 * P + c], B2 = (R)q[QM_B3 * P + c];
     R b0 = u0 * B0 + u1 * B1 + u2 * B2;
-    R bW = beta / W;
+    R bW = beta * rcp<R>(W);
     V[0] = c1g + (R)q[Q_LNR * P + c] + ig * (R)q[Q_LNB * P + c] + beta;
     V[1] = beta * u0;
     V[2] = beta * u1;
@@ -735,7 +749,7 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
         const R nvx = (R)(0.5 * (Mx[c0] + Mx[c1])), nvy = (R)(0.5 * (My[c0] + My[c1]));
         const R jt = (R)(0.5 * (Mt[c0] + Mt[c1]));
         const R Lk = sq_rt<R>(nvx * nvx + nvy * nvy);
-        const R nx = nvx / Lk, ny = nvy / Lk;
+        const R iLk = rcp<R>(Lk), nx = nvx * iLk, ny = nvy * iLk;
         // interface state
         R wm[8], wrot[8];
         {
@@ -748,9 +762,10 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
             R W2 = (R)1 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
             R W = sq_rt<R>(W2);
             wm[0] = rho;
-            for (int k = 0; k < 3; ++k) wm[1 + k] = um[k] / W;
-            wm[4] = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) /
-                    ((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
+            const R iW = rcp<R>(W);
+            for (int k = 0; k < 3; ++k) wm[1 + k] = um[k] * iW;
+            wm[4] = ((R)q[Q_RHO * g.P + c0] + (R)q[Q_RHO * g.P + c1]) *
+                    rcp<R>((R)q[Q_BETA * g.P + c0] + (R)q[Q_BETA * g.P + c1]);
             wm[5] = half * ((R)B1[c0] + (R)B1[c1]);
             wm[6] = half * ((R)B2[c0] + (R)B2[c1]);
             wm[7] = half * ((R)q[QM_B3 * g.P + c0] + (R)q[QM_B3 * g.P + c1]);

@@ -6,8 +6,8 @@ accuracy of MM-O6 (p = 3, EC, prescribed mesh, dt ~ h^2) and MM-O5 (p = 3,
 w = 5, adaptive mesh with the Laplacian monitor, dt ~ h^(5/3)) against the
 exact solution, in 2D and 3D.
 
-Tolerances: EC parity 1e-12 and ES parity 1e-10 relative per component, as
-for the other RMHD parity tests; the mesh velocity 1e-11 as for the other
+Tolerances: EC parity 1e-12 and ES parity 1e-10 (3D: 1e-9) relative per
+component, as for the other RMHD parity tests; the mesh velocity 1e-11 as for the other
 mesh parity tests.  The orders are measured on grids the oracle would need
 minutes to hours for, so there the exact solution is the reference."""
 import numpy as np
@@ -130,7 +130,9 @@ def test_rk_step_given_parity_3d(p, w):
             xd = wl.vortex_mesh3_velocity(n, s * dt, R=R)
             cons, J, x = oracle.rk_step3_given(cfg, cons, J, x, xd, dt)
             g.rk_step_given(xd, dt)
-        tol = TOL if w == 0 else ES_TOL
+        # the 3D parity tests' ES tolerance: the 3D frame adds its angle's
+        # rounding to the eigenvectors' eps/gap
+        tol = TOL if w == 0 else 1e-9
         assert _rel(g.state_get(esmm.GET_CONS), cons) < tol
         assert _rel(g.state_get(esmm.GET_J), J) < TOL
         assert _rel(g.state_get(esmm.GET_X), x) < TOL
