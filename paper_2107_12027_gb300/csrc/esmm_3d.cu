@@ -565,6 +565,7 @@ Phys phys3(const esmm3 *g)
     Phys ph;
     ph.gamma = g->gamma;
     ph.eps = g->prm.weno_eps;
+    ph.gm1i = 1.0 / (g->gamma - 1.0);
     ph.ln_thr = 1.0e-4;
     ph.sign_tol = 1.0e-10;
     double a[3][3] = {{1.0, 0.0, 0.0}, {4.0 / 3.0, -1.0 / 6.0, 0.0}, {1.5, -0.3, 1.0 / 30.0}};

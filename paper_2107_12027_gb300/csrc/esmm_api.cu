@@ -170,6 +170,7 @@ Phys phys(const esmm_grid *g)
     // FP64: switch to the series below 1e-4 (its dropped term is < 1e-17);
     // FP32 bulk: below 1e-2, where the FP32 quotient would lose ~6 digits.
     ph.ln_thr = g->prm.precision == ESMM_MIXED ? 1.0e-2 : 1.0e-4;
+    ph.gm1i = 1.0 / (g->gamma - 1.0);
     // sign switch: rounding noise of the projected jump (FP64 / FP32 bulk)
     ph.sign_tol = g->prm.precision == ESMM_MIXED ? 1.0e-5 : 1.0e-10;
     double a[3][3] = {{1.0, 0.0, 0.0}, {4.0 / 3.0, -1.0 / 6.0, 0.0}, {1.5, -0.3, 1.0 / 30.0}};
@@ -1686,6 +1687,7 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     Phys ph;
     ph.gamma = gamma;
     ph.eps = 1e-6;
+    ph.gm1i = 1.0 / (gamma - 1.0);
     ph.ln_thr = 1.0e-4;
     ph.sign_tol = 1.0e-10;
     double a[3][3] = {{1.0, 0.0, 0.0}, {4.0 / 3.0, -1.0 / 6.0, 0.0}, {1.5, -0.3, 1.0 / 30.0}};

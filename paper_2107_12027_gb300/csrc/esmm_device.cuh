@@ -65,6 +65,7 @@ __device__ __forceinline__ int locate(const ProbArg &pa, ProbDesc &D, long long 
 
 struct Phys {
     double gamma;
+    double gm1i;      // 1 / (Gamma - 1), once per launch
     double eps;       // WENO epsilon
     double ln_thr;    // log-mean series switch on ((b-a)/(b+a))^2
     double sign_tol;  // relative size below which [[V~]] counts as zero
@@ -515,13 +516,12 @@ __device__ __forceinline__ bool le(dual a, dual b) { return a.v <= b.v; }
 // with W = 1/sqrt(1 - vn^2 - vt^2): columns dU_m * s_m, s_m = (dU_m . dV_m)^-1/2,
 // for the waves (lambda_-, v_n [entropy, d rho = 1], v_n [shear, d v_t = 1],
 // lambda_+ [acoustic, dp = 1]).  dU (4 x 4, column per wave) and s are returned
-// separately; lam_m, lam_p are the acoustic speeds.
+// separately; lam_m, lam_p are the acoustic speeds; gm1i = 1/(Gamma - 1).
 template <typename R>
-__device__ __forceinline__ void eigen_rhd(R gam, R rho, R vn, R vt, R p, R W,
+__device__ __forceinline__ void eigen_rhd(R gam, R gm1i, R rho, R vn, R vt, R p, R W,
                                           R dU[4][4], R s[4], R &lam_m, R &lam_p)
 {
     R one = (R)1;
-    R gm1i = rcp<R>(gam - one);
     R gg = gam * gm1i;
     R W2 = W * W;
     R iW2 = rcp<R>(W2);                    // 1 - v^2

@@ -106,9 +106,9 @@ __device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho
     R vx = ux * iW, vy = uy * iW;
     R vn = nx * vx + ny * vy, vt = -ny * vx + nx * vy;
     R dU[4][4], s[4], lm, lp;
-    eigen_rhd<R>(gam, rho, vn, vt, p, W, dU, s, lm, lp);
+    const R ig = (R)ph.gm1i, c1g = gam * ig;
+    eigen_rhd<R>(gam, ig, rho, vn, vt, p, W, dU, s, lm, lp);
     R lhat = vmax(fab<R>(jt + Lk * lm), fab<R>(jt + Lk * lp));
-    const R ig = rcp<R>(gam - one), c1g = gam * ig;
     R Vt[NS][4];
     R aT[4] = {(R)0, (R)0, (R)0, (R)0};     // |T V| summed over the two interface nodes
 #pragma unroll
