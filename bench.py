@@ -47,7 +47,7 @@ WORKLOAD = ("2D RHD four-quadrant Riemann problem, 400x400 nodes on [-1,1]^2, ou
 # FP64 operations executed per interface by the FP64 interface kernel (p=2,
 # WENO5), from the ncu SASS counters dadd + dmul + 2 dfma of one capture
 # (profiles/iface_f64_riemann400.md); FLOP = add, mul, or half an FMA.
-FLOPS_PER_IFACE_F64 = 1407
+FLOPS_PER_IFACE_F64 = 1396
 # Derived FP64 peak of GB300: 152 SMs x 4 FP64 flop/clk/SM (1.25 TFLOP/s at
 # the 2070 MHz maximum SM clock).
 FP64_FLOP_PER_CLK_SM = 4
