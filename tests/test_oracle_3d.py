@@ -186,3 +186,21 @@ def test_monitor_closed_form_on_trigonometric_sigma_3d(alpha_lap):
     lmax = sum(2 * a[d] * (1 - np.cos(t[d])) for d in range(3))
     want = np.sqrt(1.0 + 20.0 * g / gmax + alpha_lap * lap / lmax)
     assert np.abs(oracle.monitor3(c, cons, J) - want).max() < 1e-12
+
+
+def test_inflow_free_stream_3d():
+    # the 3D inflow end (the 3D shock-cloud's boundary): the inflow state
+    # everywhere on a random moving mesh is a free stream (Prop. 3.2)
+    n = (8, 7, 6)
+    w_in = np.array([0.7, 0.3, -0.1, 0.2, 1.3, 0.4, -0.2, 0.1])
+    x = wl.random_mesh3(n, wl.rng(660), amp=0.2, periodic=(False, False, True))
+    xdot = wl.rng(661).uniform(-0.2, 0.2, x.shape)
+    xdot[:, :, :, 0] = xdot[:, :, :, -1] = 0.0     # the non-periodic ends' nodes stay
+    xdot[:, :, 0, :] = xdot[:, :, -1, :] = 0.0
+    c = oracle.make_cfg3(*n, bc=(oracle.INFLOW, oracle.OUTFLOW, oracle.PERIODIC), period=(1.0, 1.0, 1.0),
+                         p=2, w=5, inflow=w_in)
+    prim = np.ascontiguousarray(np.broadcast_to(w_in[:, None, None, None], (8,) + tuple(x.shape[1:])))
+    cons, J = oracle.init_state3(c, prim, x)
+    d, dJ = oracle.rhs3(c, cons, J, x, np.ascontiguousarray(xdot))
+    U = cons / J
+    assert np.abs(d - U * dJ).max() < 1e-12 * max(np.abs(U * dJ).max(), 1e-300)
