@@ -18,7 +18,9 @@ plainly in C) on the host cores over a bounded sample of the same workload.
 
 ``--workload rotor`` (2D RMHD rotor, 512^2, Gamma = 4/3, alpha = 800) and
 ``--workload blast3d`` (3D RMHD blast, 128^3, CFL 0.3) time the RMHD paths in
-FP64 on the same metric.  Each timed step advances the workload's initial
+FP64 on the same metric; ``--workload sphere3d`` (the 3D spherical Riemann
+problem, 128^3) and ``--workload bubble3d`` (the 3D shock-bubble, 325 x 90 x
+90) time the 3D RHD examples, MM-O5 on the RMHD system with B = 0.  Each timed step advances the workload's initial
 state by one full step (the state is restored on the device between steps,
 outside the timed events): the untapered rotor loses admissibility after a
 few steps (the scheme has no positivity limiter), and restoring keeps every
@@ -136,7 +138,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--n", type=int, default=None, help="nodes per side (default per workload)")
-    ap.add_argument("--workload", default="riemann", choices=["riemann", "rotor", "blast3d", "sphere3d"])
+    ap.add_argument("--workload", default="riemann", choices=["riemann", "rotor", "blast3d", "sphere3d", "bubble3d"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and mixed-form legs")
     ap.add_argument("--study", default=None, choices=["um-mm"],
                     help="um-mm: the efficiency of MM-O5 against UM-O5 on the Sec. 6 problems (one JSON line per run)")
@@ -522,7 +524,7 @@ def run_rmhd(args):
     torch.cuda.set_device(local)
     esmm.lib()
     stream = torch.cuda.Stream()
-    three = args.workload in ("blast3d", "sphere3d")
+    three = args.workload in ("blast3d", "sphere3d", "bubble3d")
     if three and args.form != "fp64":
         raise SystemExit("the 3D workloads run in the FP64 form only")
     n = args.n or (128 if three else 512)
@@ -537,6 +539,19 @@ def run_rmhd(args):
         desc = ("3D spherical Riemann problem (an RHD problem on the RMHD system, B = 0), %d^3 nodes on [-1,1]^3, "
                 "outflow, Gamma=5/3, r<0.5: rho=10, p=40/3; outside rho=1, p=1e-2; at rest; MM-O5 (6th-order EC "
                 "flux p=3 + WENO5), adaptive moving mesh (sigma=ln rho, alpha=800), SSP-RK3, CFL 0.3" % n)
+        flops, traffic, kname = None, None, "k3_iface<3,5>"
+    elif args.workload == "bubble3d":
+        m = (n, max(8, round(n * 90 / 325)), max(8, round(n * 90 / 325))) if args.n else (325, 90, 90)
+        x, prim = wl.rhd_shock_bubble3_config(m)
+        g = esmm.Grid3(m, (0.0, -45.0, -45.0), (325.0, 45.0, 45.0), bc=(1, 1, 1), gamma=5.0 / 3.0,
+                       scheme="MM-O5", alpha=800.0, monitor=esmm.MONITOR_LNRHO, stream=stream.cuda_stream)
+        nodes = m[0] * m[1] * m[2]
+        ifaces = (m[0] + 1) * m[1] * m[2]
+        desc = ("3D shock-bubble (an RHD problem on the RMHD system, B = 0), %dx%dx%d nodes on [0,325]x[-45,45]^2, "
+                "outflow, Gamma=5/3, planar shock at x1=265 (post-shock rho=1.865225080631180, v1=-0.196781107378299, "
+                "p=0.15) moving into rho=1, p=0.05 at rest, bubble r<=25 at (215,0,0) with rho=0.1358; MM-O5 "
+                "(6th-order EC flux p=3 + WENO5), adaptive moving mesh (sigma=ln rho, alpha=800), SSP-RK3, CFL 0.3"
+                % m)
         flops, traffic, kname = None, None, "k3_iface<3,5>"
     elif three:
         x, prim = wl.blast3_config(n)

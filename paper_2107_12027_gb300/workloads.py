@@ -509,6 +509,36 @@ def rmhd_shock_cloud3_config(n=(210, 150, 150)):
     return x, rmhd_shock_cloud(x)
 
 
+# ---- the 3D RHD shock-bubble interaction (Sec. 6) ---------------------------
+# Primitive (rho, v_1, v_2, v_3, p, B_1, B_2, B_3), Gamma = 5/3: the medium at
+# rest ahead of a planar shock at x_1 = 265, the shocked gas behind it moving
+# to the left, and a light bubble of radius 25 centred at (215, 0, 0).  The
+# 15-digit post-shock state satisfies the RHD jump conditions with the medium
+# to rounding (shock speed -0.4148).
+SHOCK_BUBBLE_PRE = (1.0, 0.0, 0.0, 0.0, 0.05, 0.0, 0.0, 0.0)
+SHOCK_BUBBLE_POST = (1.865225080631180, -0.196781107378299, 0.0, 0.0, 0.15, 0.0, 0.0, 0.0)
+SHOCK_BUBBLE_GAS = (0.1358, 0.0, 0.0, 0.0, 0.05, 0.0, 0.0, 0.0)
+
+
+def rhd_shock_bubble3(x, x_shock=265.0, centre=(215.0, 0.0, 0.0), radius=25.0):
+    """The 3D shock-bubble data at the points x [3][...] (an RHD problem, here
+    on the RMHD system with B = 0)."""
+    pre, post, gas = (np.array(s).reshape((8, 1, 1, 1)) for s in
+                      (SHOCK_BUBBLE_PRE, SHOCK_BUBBLE_POST, SHOCK_BUBBLE_GAS))
+    prim = np.where((x[0] > x_shock)[None], post, pre)
+    r2 = sum((x[d] - centre[d]) ** 2 for d in range(3))
+    prim = np.where((r2 <= radius * radius)[None], gas, prim)
+    return np.ascontiguousarray(prim)
+
+
+def rhd_shock_bubble3_config(n=(325, 90, 90)):
+    """The 3D shock-bubble on [0,325] x [-45,45]^2 with outflow ends (n nodes
+    per direction, both ends): the zero-gradient end at x_1 = 325 keeps the
+    uniform post-shock state that the shock leaves behind."""
+    x = uniform_mesh3(n, (0.0, -45.0, -45.0), (325.0, 45.0, 45.0), (False, False, False))
+    return x, rhd_shock_bubble3(x)
+
+
 def sphere_rp3(x, r0=0.5):
     """The 3D spherically symmetric Riemann problem of Sec. 6 (an RHD
     problem, here on the RMHD system with B = 0): rho = 10, p = 40/3 for

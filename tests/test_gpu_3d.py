@@ -143,6 +143,39 @@ def test_rk_step_blast_3d_within_the_methods_own_sensitivity():
         assert np.abs(got[c] - c1[c]).max() <= 10.0 * sens[c] + ES_TOL * scale
 
 
+@pytest.mark.parametrize("case", ["sphere", "bubble"])
+def test_rhd_examples_3d_rhs_parity_and_short_run(case):
+    # The 3D RHD examples of Sec. 6 (the spherical Riemann problem and the
+    # shock-bubble) run on the RMHD system with B = 0: every interface is then
+    # degenerate (the Alfven, slow and entropy speeds coincide), as on the
+    # rotor.  Right-hand sides of MM-O6 (EC) and MM-O5 (ES) on random outflow
+    # meshes against the oracle, then five MM-O5 adaptive steps that stay
+    # admissible and keep B = 0 up to rounding.
+    n = (13, 9, 9)
+    if case == "sphere":
+        lo, hi, make = (-1.0,) * 3, (1.0,) * 3, wl.sphere_rp3
+    else:
+        lo, hi, make = (150.0, -45.0, -45.0), (325.0, 45.0, 45.0), wl.rhd_shock_bubble3
+    x = wl.random_mesh3(n, wl.rng(540 + (case == "bubble")), amp=0.15, lo=lo, hi=hi, periodic=(False,) * 3)
+    prim = make(x)
+    for w in (0, 5):
+        cfg, g = _pair(n, (1, 1, 1), lo, hi, 3, w, gamma=5.0 / 3.0)
+        cons, J = oracle.init_state3(cfg, prim, x)
+        ref = oracle.rhs3(cfg, cons, J, x)
+        with g:
+            got = g.rhs(cons, J, x)
+        assert _rel(got[0], ref[0]) < (TOL if w == 0 else ES_TOL)
+        assert _rel(got[1], ref[1]) < TOL
+    with esmm.Grid3(n, lo, hi, bc=(1, 1, 1), gamma=5.0 / 3.0, scheme="MM-O5", alpha=800.0,
+                    monitor=esmm.MONITOR_LNRHO) as g:
+        g.state_set(prim, x)
+        g.advance(5)
+        assert g.last_error()[0] == 0 and g.time() > 0
+        got = g.state_get(esmm.GET_PRIM)
+        assert np.isfinite(got).all() and got[0].min() > 0 and got[4].min() > 0
+        assert np.abs(got[5:]).max() < 1e-12
+
+
 def test_free_stream_and_ec_identity_3d():
     n = (9, 8, 7)
     x = wl.random_mesh3(n, wl.rng(520), amp=0.15)
