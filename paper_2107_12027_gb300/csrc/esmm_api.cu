@@ -273,15 +273,16 @@ void launch_node(const esmm_grid *g, const LaunchDom &L, const double *cons, con
     float *q32 = q32_of(g);
     const double *in = g->has_inflow ? g->inflow_dev : nullptr;
     const int f32_logs = q32 && !exact_logs;
+    const double gg = (g->gamma - 1.0) / g->gamma;
     if (g->p == 1)
-        k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
-                                              in, f32_logs);
+        k_node<1><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, gg, cons, J, x, xdot, pg_in, pg_out, q, g->status,
+                                              q32, in, f32_logs);
     else if (g->p == 2)
-        k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
-                                              in, f32_logs);
+        k_node<2><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, gg, cons, J, x, xdot, pg_in, pg_out, q, g->status,
+                                              q32, in, f32_logs);
     else
-        k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, cons, J, x, xdot, pg_in, pg_out, q, g->status, q32,
-                                              in, f32_logs);
+        k_node<3><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, gg, cons, J, x, xdot, pg_in, pg_out, q, g->status,
+                                              q32, in, f32_logs);
 }
 
 // the node pass; exact_logs: FP64 logarithms in every form (the totals)
@@ -1710,15 +1711,16 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
         return L;
     };
     LaunchDom Ln = one(G.P, BS);
+    const double gg = (gamma - 1.0) / gamma;
     if (p == 1)
-        k_node<1><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, nullptr,
-                                             nullptr);
+        k_node<1><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, gg, cons, J, x, xdot, nullptr, nullptr, q, status,
+                                             nullptr, nullptr);
     else if (p == 2)
-        k_node<2><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, nullptr,
-                                             nullptr);
+        k_node<2><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, gg, cons, J, x, xdot, nullptr, nullptr, q, status,
+                                             nullptr, nullptr);
     else
-        k_node<3><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, cons, J, x, xdot, nullptr, nullptr, q, status, nullptr,
-                                             nullptr);
+        k_node<3><<<Ln.nblk, Ln.bs, 0, st>>>(Ln.pa, gamma, gg, cons, J, x, xdot, nullptr, nullptr, q, status,
+                                             nullptr, nullptr);
     for (int dir = 0; dir < 2; ++dir) {
         long long cp = dir == 0 ? (long long)(nx + p) * ny : (long long)(ny + p) * nx;
         long long ci = dir == 0 ? (long long)(nx + 1) * ny : (long long)(ny + 1) * nx;

@@ -133,13 +133,13 @@ __device__ __forceinline__ double mesh_at(const Geom &g, const double *a, int i,
 // (a relative slope error e contracts the error by e per step), while f, which
 // decides the stopping, is FP64.  W receives the Lorentz factor 1/sqrt(1-v^2)
 // (1 for a non-admissible state).  Returns 0, 1 for a non-admissible state, 2
-// when the iteration cap is hit.
-__device__ __forceinline__ int cons2prim(double gam, double D, double mx, double my, double E,
-                                         double p0, double &rho, double &vx, double &vy, double &p, double &W)
+// when the iteration cap is hit.  gg = (Gamma - 1)/Gamma, which a launch can
+// pass in (one division per launch, not per node).
+__device__ __forceinline__ int cons2prim_gg(double gam, double gg, double D, double mx, double my, double E,
+                                            double p0, double &rho, double &vx, double &vy, double &p, double &W)
 {
     double S2 = mx * mx + my * my;
     double S = sqrt(S2);
-    double gg = (gam - 1.0) / gam;
     rho = 0.0; vx = 0.0; vy = 0.0; p = 0.0; W = 1.0;
     if (!(D > 0.0) || !(E * E > D * D + S2) || !(E > 0.0)) return 1;
     double lo = 0.0, hi = (gam - 1.0) * E;
@@ -178,6 +178,12 @@ __device__ __forceinline__ int cons2prim(double gam, double D, double mx, double
     p = pc;
     W = rs;
     return ok ? 0 : 2;
+}
+
+__device__ __forceinline__ int cons2prim(double gam, double D, double mx, double my, double E,
+                                         double p0, double &rho, double &vx, double &vy, double &p, double &W)
+{
+    return cons2prim_gg(gam, (gam - 1.0) / gam, D, mx, my, E, p0, rho, vx, vy, p, W);
 }
 
 // ---------------------------------------------------------------------------

@@ -63,10 +63,10 @@ __device__ __forceinline__ void mesh_deltas(const Geom &g, const double *__restr
 // read; with f32_logs (the mixed form's scheme passes) ln rho and ln beta are
 // FP32 logarithms: in that form they enter only FP32 arithmetic and the log
 // mean's jump outside its near-equal branch, while the totals take a pass
-// with FP64 logarithms.
+// with FP64 logarithms.  gg = (Gamma - 1)/Gamma comes with the launch.
 template <int P>
-__global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, const double *__restrict__ J,
-                       const double *__restrict__ x, const double *__restrict__ xdot,
+__global__ void k_node(ProbArg pa, double gam, double gg, const double *__restrict__ cons,
+                       const double *__restrict__ J, const double *__restrict__ x, const double *__restrict__ xdot,
                        const double *__restrict__ pg_in, double *__restrict__ pg_out, double *__restrict__ q,
                        int *__restrict__ status, float *__restrict__ q32, const double *__restrict__ inflow,
                        int f32_logs = 0)
@@ -97,7 +97,7 @@ __global__ void k_node(ProbArg pa, double gam, const double *__restrict__ cons, 
         W = rsqrt(1.0 - (vx * vx + vy * vy));
         st = 0;
     } else {
-        st = cons2prim(gam, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p, W);
+        st = cons2prim_gg(gam, gg, Dd, mx, my, E, pg_in ? pg_in[src] : -1.0, rho, vx, vy, p, W);
     }
     bool interior = I >= 0 && I < g.nx && Jn >= 0 && Jn < g.ny;
     if (interior) {
