@@ -77,6 +77,22 @@ def test_workload_data_are_the_papers():
     x = wl.vortex_mesh(24, t=0.7)
     sh = x - 1.3 * d["vortex2d.velocity"][:, None, None]
     assert np.allclose(wl.rmhd_vortex(x, t=1.3), wl.rmhd_vortex(sh, t=0.0), rtol=0, atol=1e-12)
+    v3 = _defaults(wl.rmhd_vortex3)
+    assert (v3["R"], v3["gamma"], v3["sigma"], v3["B0"]) == tuple(
+        d["vortex3d." + k][0] for k in ("R", "gamma", "sigma", "B0"))
+    x = wl.vortex_mesh3(6)
+    x0 = wl.uniform_mesh3((6, 6, 30), *np.reshape(d["vortex3d.box"], (3, 2)).T)
+    assert np.allclose(x0, wl.vortex_mesh3(6, t=2.0), rtol=0, atol=1e-12)       # cos(pi t/4) = 0
+    assert np.allclose(x, x0, rtol=0, atol=0.21)
+    # a shift of x by a box period moves the plane coordinates by a printed
+    # lattice vector (x -> x + 2R e_1: (40/3, 10/3)), and leaves the data (up
+    # to ~4e-11: the nearest lattice image jumps where two are equally near,
+    # and the vortex's tail is not quite zero there)
+    lat = d["vortex3d.lattice"].reshape(2, 2)
+    R = d["vortex3d.R"][0]
+    assert np.allclose(lat[0], (2 * R + 2 * R / 3, 2 * R / 3), rtol=0, atol=1e-12)
+    sh = x + np.array([2 * R, 0.0, 0.0])[:, None, None, None]
+    assert np.allclose(wl.rmhd_vortex3(sh, t=0.05), wl.rmhd_vortex3(x, t=0.05), rtol=0, atol=1e-10)
     b = _defaults(wl.rmhd_blast2)
     assert (b["r_in"], b["r_out"]) == (d["blast2d.r_inner"][0], d["blast2d.r_outer"][0])
     assert (b["rho_in"], b["p_in"]) == tuple(d["blast2d.inner_rho_p"])
