@@ -112,6 +112,8 @@ def lib():
                 "oref_rhs": (ctypes.c_int, [c, d, d, d, d, d, d]),
                 "oref_cfl_dt": (ctypes.c_int, [c, d, d, d, d]),
                 "oref_monitor": (ctypes.c_int, [c, d, d, d]),
+                "oref_filter": (None, [c, d, ctypes.c_int]),
+                "oref_jacobi": (None, [c, d, d, ctypes.c_int, d]),
                 "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d, d]),
                 "oref_rk_step": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d]),
                 "oref_rk_step_given": (ctypes.c_int, [c, d, d, d, d, ctypes.c_double]),
@@ -133,6 +135,8 @@ def lib():
                 "oref3_rhs": (ctypes.c_int, [c3, d, d, d, d, d, d]),
                 "oref3_cfl_dt": (ctypes.c_int, [c3, d, d, d, d]),
                 "oref3_monitor": (ctypes.c_int, [c3, d, d, d]),
+                "oref3_filter": (None, [c3, d, ctypes.c_int]),
+                "oref3_jacobi": (None, [c3, d, d, ctypes.c_int, d]),
                 "oref3_mesh": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d, d, d]),
                 "oref3_rk_step": (ctypes.c_int, [c3, d, d, d, ctypes.c_double, d]),
                 "oref3_rk_step_given": (ctypes.c_int, [c3, d, d, d, d, ctypes.c_double]),
@@ -308,6 +312,23 @@ def monitor(cfg, cons, J):
     if st != 0:
         raise RuntimeError("oracle monitor: cons2prim failed")
     return om.reshape(cfg.ny, cfg.nx)
+
+
+def mesh_filter(cfg, om, n):
+    """The Sec. 5 low-pass filter applied n times to om [ny][nx] (a copy)."""
+    N = cfg.nx * cfg.ny
+    om = _vec(om, N).copy()
+    lib().oref_filter(ctypes.byref(cfg), _p(om), int(n))
+    return om.reshape(cfg.ny, cfg.nx)
+
+
+def mesh_jacobi(cfg, om, x, mu):
+    """mu Jacobi sweeps of the Sec. 5 mesh equations with om [ny][nx] frozen,
+    from x [2][ny][nx]; returns X^[mu]."""
+    N = cfg.nx * cfg.ny
+    X = np.zeros(2 * N)
+    lib().oref_jacobi(ctypes.byref(cfg), _p(_vec(om, N)), _p(_vec(x, 2 * N)), int(mu), _p(X))
+    return X.reshape(2, cfg.ny, cfg.nx)
 
 
 def mesh(cfg, cons, J, x, dt=0.0):
@@ -490,6 +511,22 @@ def monitor3(cfg, cons, J):
     if st != 0:
         raise RuntimeError("oracle monitor3: cons2prim failed")
     return om.reshape(cfg.nz, cfg.ny, cfg.nx)
+
+
+def mesh_filter3(cfg, om, n):
+    """:func:`mesh_filter` in 3D ([nz][ny][nx])."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    om = _vec(om, N).copy()
+    lib().oref3_filter(ctypes.byref(cfg), _p(om), int(n))
+    return om.reshape(cfg.nz, cfg.ny, cfg.nx)
+
+
+def mesh_jacobi3(cfg, om, x, mu):
+    """:func:`mesh_jacobi` in 3D: x [3][nz][ny][nx]."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    X = np.zeros(3 * N)
+    lib().oref3_jacobi(ctypes.byref(cfg), _p(_vec(om, N)), _p(_vec(x, 3 * N)), int(mu), _p(X))
+    return X.reshape(_shape3(cfg, 3))
 
 
 def mesh3(cfg, cons, J, x, dt=0.0):

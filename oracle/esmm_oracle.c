@@ -947,23 +947,15 @@ int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double 
     return status;
 }
 
-int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
-              const double *x, double dt, double *xdot, double *dtau, double *dt_out)
+/* The low-pass filter of the Sec. 5 remark, applied n times in place:
+ * om_i <- sum_{j in {-1,0,1}^2} (1/2)^{|j1|+|j2|+2} om_{i+j}, neighbours
+ * through the boundary mapping of the data (periodic wrap or the boundary
+ * node's copy). */
+void oref_filter(const oref_cfg *c, double *om, int n)
 {
-    int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
-    if (!c->move_mesh) {
-        for (int a = 0; a < 2 * N; ++a) xdot[a] = 0.0;
-        if (dtau) *dtau = 0.0;
-        if (!(dt > 0.0)) status |= oref_cfl_dt(c, cons, J, x, &dt);
-        if (dt_out) *dt_out = dt;
-        return status;
-    }
-    double *om = (double *)malloc(sizeof(double) * N);
+    int nx = c->nx, ny = c->ny, N = nx * ny;
     double *om2 = (double *)malloc(sizeof(double) * N);
-    double *X = (double *)malloc(sizeof(double) * 2 * N);
-    double *Xn = (double *)malloc(sizeof(double) * 2 * N);
-    status |= oref_monitor(c, cons, J, om);
-    for (int f = 0; f < c->n_filter; ++f) {
+    for (int f = 0; f < n; ++f) {
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 double acc = 0.0;
@@ -974,8 +966,22 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
             }
         memcpy(om, om2, sizeof(double) * N);
     }
+    free(om2);
+}
+
+/* mu sweeps of the Jacobi iteration of the Sec. 5 mesh equations with the
+ * monitor om frozen, from X^[0] = x: each sweep solves, node by node,
+ *   sum_k [(om_i + om_{i,k,+1})(X^[nu]_{i,k,+1} - X^[nu+1]_i)
+ *          - (om_i + om_{i,k,-1})(X^[nu+1]_i - X^[nu]_{i,k,-1})] = 0
+ * for X^[nu+1]_i.  Nodes on a non-periodic end stay fixed; mesh neighbours
+ * beyond an end come from the mesh's ghost rule (period shift or linear
+ * extrapolation). */
+void oref_jacobi(const oref_cfg *c, const double *om, const double *x, int mu, double *X)
+{
+    int nx = c->nx, ny = c->ny, N = nx * ny;
+    double *Xn = (double *)malloc(sizeof(double) * 2 * N);
     memcpy(X, x, sizeof(double) * 2 * N);
-    for (int nu = 0; nu < c->mu; ++nu) {
+    for (int nu = 0; nu < mu; ++nu) {
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 int id = j * nx + i;
@@ -1000,6 +1006,25 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
             }
         memcpy(X, Xn, sizeof(double) * 2 * N);
     }
+    free(Xn);
+}
+
+int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
+              const double *x, double dt, double *xdot, double *dtau, double *dt_out)
+{
+    int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
+    if (!c->move_mesh) {
+        for (int a = 0; a < 2 * N; ++a) xdot[a] = 0.0;
+        if (dtau) *dtau = 0.0;
+        if (!(dt > 0.0)) status |= oref_cfl_dt(c, cons, J, x, &dt);
+        if (dt_out) *dt_out = dt;
+        return status;
+    }
+    double *om = (double *)malloc(sizeof(double) * N);
+    double *X = (double *)malloc(sizeof(double) * 2 * N);
+    status |= oref_monitor(c, cons, J, om);
+    oref_filter(c, om, c->n_filter);
+    oref_jacobi(c, om, x, c->mu, X);
     double tau = 1.0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -1043,9 +1068,7 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
     if (dtau) *dtau = tau;
     if (dt_out) *dt_out = dt;
     free(om);
-    free(om2);
     free(X);
-    free(Xn);
     return status;
 }
 

@@ -102,6 +102,14 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
  * whose maximum is 0 is left out (alpha_lap = 0 gives eq. monitor). */
 int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double *om);
 
+/* Sec. 5 low-pass filter of the monitor, n passes in place (weights
+ * (1/2)^{|j1|+|j2|+2} over the 3x3 neighbourhood). */
+void oref_filter(const oref_cfg *c, double *om, int n);
+
+/* Sec. 5 Jacobi iteration of the mesh equations: mu sweeps with om frozen
+ * from X^[0] = x, result X[2][N]. */
+void oref_jacobi(const oref_cfg *c, const double *om, const double *x, int mu, double *X);
+
 /* Sec. 5 mesh redistribution and the step: xdot from the state at t^n; dt > 0
  * is used as given, dt <= 0 selects the CFL step with the mesh motion
  * included (written to *dt_out). */
@@ -176,6 +184,8 @@ int oref3_rhs(const oref3_cfg *c, const double *cons, const double *J, const dou
               const double *xdot, double *dcons, double *dJ);
 int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const double *x, double *dt);
 int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, double *om);
+void oref3_filter(const oref3_cfg *c, double *om, int n);
+void oref3_jacobi(const oref3_cfg *c, const double *om, const double *x, int mu, double *X);
 int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
                double *xdot, double *dtau, double *dt_out);
 int oref3_rk_step(const oref3_cfg *c, double *cons, double *J, double *x, double dt, double *dt_used);

@@ -551,24 +551,14 @@ int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, doubl
     return status;
 }
 
-int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
-               double *xdot, double *dtau, double *dt_out)
+/* The low-pass filter of the Sec. 5 remark, applied n times in place:
+ * om_i <- sum_{j in {-1,0,1}^3} (1/2)^{|j1|+|j2|+|j3|+3} om_{i+j}, neighbours
+ * through the boundary mapping of the data. */
+void oref3_filter(const oref3_cfg *c, double *om, int n)
 {
     long N = (long)c->nx * c->ny * c->nz;
-    int status = 0;
-    if (!c->move_mesh) {
-        for (long a = 0; a < 3 * N; ++a) xdot[a] = 0.0;
-        if (dtau) *dtau = 0.0;
-        if (!(dt > 0.0)) status |= oref3_cfl_dt(c, cons, J, x, &dt);
-        if (dt_out) *dt_out = dt;
-        return status;
-    }
-    double *om = (double *)malloc(sizeof(double) * N);
     double *om2 = (double *)malloc(sizeof(double) * N);
-    double *X = (double *)malloc(sizeof(double) * 3 * N);
-    double *Xn = (double *)malloc(sizeof(double) * 3 * N);
-    status |= oref3_monitor(c, cons, J, om);
-    for (int f = 0; f < c->n_filter; ++f) {
+    for (int f = 0; f < n; ++f) {
         for (int k = 0; k < c->nz; ++k)
             for (int j = 0; j < c->ny; ++j)
                 for (int i = 0; i < c->nx; ++i) {
@@ -582,8 +572,20 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
                 }
         memcpy(om, om2, sizeof(double) * N);
     }
+    free(om2);
+}
+
+/* mu sweeps of the Sec. 5 Jacobi iteration with the monitor om frozen, from
+ * X^[0] = x (the three-direction form of the 2D sweep: each node solves
+ * sum_k [(om_i + om_{i,k,+1})(X_{i,k,+1} - X_i) - (om_i + om_{i,k,-1})(X_i -
+ * X_{i,k,-1})] = 0 with the neighbours of the previous sweep); nodes on a
+ * non-periodic face stay fixed. */
+void oref3_jacobi(const oref3_cfg *c, const double *om, const double *x, int mu, double *X)
+{
+    long N = (long)c->nx * c->ny * c->nz;
+    double *Xn = (double *)malloc(sizeof(double) * 3 * N);
     memcpy(X, x, sizeof(double) * 3 * N);
-    for (int nu = 0; nu < c->mu; ++nu) {
+    for (int nu = 0; nu < mu; ++nu) {
         for (int k = 0; k < c->nz; ++k)
             for (int j = 0; j < c->ny; ++j)
                 for (int i = 0; i < c->nx; ++i) {
@@ -619,6 +621,26 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
                 }
         memcpy(X, Xn, sizeof(double) * 3 * N);
     }
+    free(Xn);
+}
+
+int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const double *x, double dt,
+               double *xdot, double *dtau, double *dt_out)
+{
+    long N = (long)c->nx * c->ny * c->nz;
+    int status = 0;
+    if (!c->move_mesh) {
+        for (long a = 0; a < 3 * N; ++a) xdot[a] = 0.0;
+        if (dtau) *dtau = 0.0;
+        if (!(dt > 0.0)) status |= oref3_cfl_dt(c, cons, J, x, &dt);
+        if (dt_out) *dt_out = dt;
+        return status;
+    }
+    double *om = (double *)malloc(sizeof(double) * N);
+    double *X = (double *)malloc(sizeof(double) * 3 * N);
+    status |= oref3_monitor(c, cons, J, om);
+    oref3_filter(c, om, c->n_filter);
+    oref3_jacobi(c, om, x, c->mu, X);
     double tau = 1.0;
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
@@ -666,9 +688,7 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
     if (dtau) *dtau = tau;
     if (dt_out) *dt_out = dt;
     free(om);
-    free(om2);
     free(X);
-    free(Xn);
     return status;
 }
 
