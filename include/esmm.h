@@ -3,8 +3,9 @@
  * high-order entropy-stable adaptive moving-mesh finite difference scheme of
  * Duan & Tang, "High-order accurate entropy stable adaptive moving mesh finite
  * difference schemes for special relativistic (magneto)hydrodynamics"
- * (arXiv 2107.12027), for 2D special relativistic hydrodynamics (RHD) and
- * magnetohydrodynamics (RMHD, with the Godunov-Powell source of eq. RMHDSymm).
+ * (arXiv 2107.12027): 2D special relativistic hydrodynamics (RHD), 2D
+ * special relativistic magnetohydrodynamics (RMHD, with the Godunov-Powell
+ * source of eq. RMHDSymm) and 3D RMHD (the nested metrics of eq. SCLCoeff).
  *
  * Conventions shared by every entry point
  *   - Every function returns an int status: ESMM_OK (0) or one ESMM_ERR_*.
@@ -20,8 +21,8 @@
  *       cons  [m][N]  the curvilinear unknown J*U, U = (D, m_x, m_y, E)
  *                     (RMHD: U = (D, m_1, m_2, m_3, E, B_1, B_2, B_3))
  *       J     [N]     the evolved Jacobian (volume) of each node
- *       x     [d][N]  physical node coordinates (x, y[, z])
- *       xdot  [2][N]  mesh velocity
+ *       x     [d][N]  physical node coordinates (x, y[, z]), d = 2 or 3
+ *       xdot  [d][N]  mesh velocity
  *   - The computational coordinates are node indices (Delta xi_k = 1), so
  *     metrics, J and fluxes are per unit index.
  *   - mem = ESMM_MEM_HOST: pointers are host memory; the call copies in,
@@ -48,8 +49,9 @@ extern "C" {
 #define ESMM_ERR_STATE 5    /* the grid has no state yet                      */
 
 #define ESMM_RHD 0          /* physics: special relativistic hydrodynamics    */
-#define ESMM_RMHD 1         /* physics: special relativistic MHD (2D grids,
-                               3-component v and B; FP64; single problems)    */
+#define ESMM_RMHD 1         /* physics: special relativistic MHD, 3-component
+                               v and B; 2D grids (FP64 or ESMM_MIXED, single
+                               problems) and every 3D grid (FP64)            */
 
 #define ESMM_PERIODIC 0     /* boundary: periodic (mesh shifted by the period) */
 #define ESMM_OUTFLOW 1      /* boundary: zero-gradient data, fixed boundary
@@ -117,13 +119,19 @@ int esmm_set_eos(esmm_grid *g, double gamma);
 /* 2p-th order EC flux (eq. ECFlux_O2p), p in {1, 2, 3}; WENO order w of
  * the ES dissipation (eq. ESFlux_HO), w in {0 (EC scheme), 3, 5}. */
 int esmm_set_order(esmm_grid *g, int p, int w);
-/* (ESMM_ERR_ARG for precision ESMM_MIXED on an RMHD grid.) */
+/* Scheme parameters of Sec. 5 (monitor, filter passes, Jacobi sweeps) and
+ * Sec. 6 (the CFL number of eq. cfl), and the precision form.  ESMM_ERR_ARG
+ * for an out-of-range value, and for ESMM_MIXED on a 3D grid (2D RHD and 2D
+ * RMHD grids take both forms). */
 int esmm_set_params(esmm_grid *g, const esmm_params *prm);
 int esmm_get_params(const esmm_grid *g, esmm_params *prm);
 
 /* Set the state from primitive variables and a mesh (x NULL: the uniform
- * mesh of the grid's box).  J is initialised from the mesh by the same
- * central differences as the metrics, cons = J * U(prim), t = 0.
+ * mesh of the grid's box).  cons = J * U(prim) with U(prim) of eq.
+ * RMHDdiv2's conservative variables (Sec. 1; RHD: B = 0) and J^0 the
+ * Jacobian of Sec. 3.3 from the mesh by the same central differences as the
+ * metrics (2D: delta_xi[x] delta_eta[y] - delta_eta[x] delta_xi[y]; 3D: the
+ * determinant of delta_k[x_j]); after that J evolves by eq. VCL.  t = 0.
  * ESMM_ERR_ARG for a non-admissible state (rho <= 0, p <= 0 or |v| >= 1).
  * prim and cons have m = 4 (RHD) or 8 (RMHD) components. */
 int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem);
@@ -150,25 +158,34 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
 int esmm_cfl_dt(esmm_grid *g, double *dt);
 
 /* Adaptive mesh redistribution of Sec. 5 for the grid's state and time step
- * dt: monitor, low-pass filter, mu Jacobi sweeps, movement limiter.
- * dt <= 0 selects the step of eq. cfl with the mesh velocity in the spectral
- * radius: the limiter Delta tau is capped so that the displacement's Courant
- * number C_m = Delta tau sum_k max_i |(x^[mu] - x^n).(J xi_k,x)|/J stays
- * <= CFL/2, and dt = (CFL - C_m)/sum_k max_i rho_k (static radius).  Stores
- * the mesh velocity in the grid and, when given, writes it to xdot [2][N], the
- * limiter value to *dtau and the step to *dt_used (host scalars). */
+ * dt: monitor, low-pass filter, mu Jacobi sweeps, movement limiter, and the
+ * mesh velocity xdot = Delta tau (x^[mu] - x^n)/dt.
+ * dt <= 0 selects the step of eq. cfl with that mesh velocity in the spectral
+ * radius: dt solves dt sum_k max_i rho_{k,i} = CFL with rho the spectral
+ * radius of d(F_k)/d(JU) including the temporal metric (solved by Newton's
+ * method on the convex piecewise-linear left side, at most 8 evaluations,
+ * else the safe bound (CFL - C_m)/S).  The limiter Delta tau is kept, unless
+ * the displacement's own Courant number C_m = Delta tau sum_k max_i
+ * |(x^[mu] - x^n).(J xi_k,x)|/J reaches CFL (no step exists then): there it is
+ * scaled to C_m = CFL/2.  A given dt > 0 is used as is (the same rule for
+ * Delta tau).  Stores the mesh velocity in the grid and, when given, writes it
+ * to xdot [d][N], the limiter value to *dtau and the step to *dt_used (host
+ * scalars). */
 int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, double *dt_used, int mem);
 
-/* One time step of the fully discrete scheme: CFL step (dt <= 0, with the
- * mesh motion as in esmm_mesh_redistribute) or the given dt, mesh
- * redistribution (unless move_mesh = 0), and three SSP-RK3 stages
- * applied to (cons, J) and to the mesh with the step's mesh velocity.
+/* One time step of the fully discrete scheme of Sec. 3.3 (Prop. 3.2) and
+ * Sec. 6: CFL step of eq. cfl (dt <= 0, with the mesh motion as in
+ * esmm_mesh_redistribute) or the given dt, mesh redistribution of Sec. 5
+ * (unless move_mesh = 0), and the three stages of the third-order SSP
+ * Runge-Kutta method (Shu-Osher form) applied to (cons, J) and to the mesh
+ * with the step's mesh velocity.
  * Asynchronous on the grid's stream; when dt_used is not NULL the call
  * synchronises and writes the step used.  A recovery failure is reported by
  * esmm_last_error / the next synchronising call. */
 int esmm_rk_step(esmm_grid *g, double dt, double *dt_used);
-/* The primitive state prim[m] (host array; m = 4 for 2D RHD, 8 for RMHD:
- * rho, v, p (, B)) held by the ghost nodes beyond every ESMM_INFLOW end.  A
+/* The inflow boundary of the shock-cloud examples of Sec. 6: the primitive
+ * state prim[m] (host array; m = 4 for 2D RHD, 8 for RMHD: rho, v, p (, B))
+ * held by the ghost nodes beyond every ESMM_INFLOW end.  A
  * grid with an inflow end returns ESMM_ERR_STATE from every call that
  * evaluates the scheme until this is set; ESMM_ERR_ARG for rho <= 0, p <= 0
  * or |v| >= 1.  The adjoint calls return ESMM_ERR_ARG for grids with an
@@ -247,8 +264,10 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
  * first). */
 int esmm_tune(esmm_grid *g, int *block_sizes);
 
-/* FP64 totals of the grid's state: out[0] = sum J eta (total entropy),
- * out[1] = sum J D (mass), out[2] = sum J (volume).  Synchronises. */
+/* FP64 totals of the grid's state: out[0] = sum J eta, the total entropy of
+ * the Sec. 6 entropy plots (without their 1/N normalisation; eta the entropy
+ * of the entropy pair of Sec. 2), out[1] = sum J D (mass), out[2] = sum J
+ * (volume, conserved by eq. VCL).  Synchronises. */
 int esmm_totals(esmm_grid *g, double out[3]);
 
 /* Synchronise and return the accumulated error state: the number of nodes
@@ -292,11 +311,23 @@ int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[E
  * ESMM_STATIC_MAX_PADDED_NODES (e.g. grids up to 256 x 256), 48 doubles per
  * padded node (~26 MB), held by every GPU that loads the library until the
  * process exits.  Larger grids return ESMM_ERR_ARG, as do invalid arguments.
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call shares the one array and overwrites it, so calls that
- * overlap on the GPU (other streams, other threads) race; serialise them.
- * Primitive-recovery failures are not reported (those nodes' outputs are
+ * With CUDA's default lazy module loading the driver reserves that array
+ * when the first call on a device looks up its address, so that first call
+ * can fail with ESMM_ERR_CUDA on a device that has no 26 MB left: callers
+ * with a fixed budget make one call up front (any small grid), or load the
+ * library with CUDA_MODULE_LOADING=EAGER.  The first call on a device sets
+ * up the address (with that device current) and must come before any stream
+ * capture; a first call inside a capture returns ESMM_ERR_CUDA.  Calls
+ * outside a capture look the address up again, so a cudaDeviceReset between
+ * calls is harmless; calls inside a capture use the address of the last call
+ * outside one (do not reset the device between that call and the capture).
+ * Every call shares the one array and overwrites it, so calls that overlap
+ * on the GPU (other streams, other threads) race; serialise them.
+ * A CUDA error already pending on the calling thread (cudaPeekAtLastError)
+ * makes the call return ESMM_ERR_CUDA at once, enqueuing nothing and leaving
+ * that error for its owner; a launch error of the call itself is consumed
+ * and returned as ESMM_ERR_CUDA.  Primitive-recovery failures are counted
+ * in the scratch only and not reported (those nodes' outputs are
  * undefined). */
 #define ESMM_STATIC_MAX_PADDED_NODES 68644
 int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const double hi[2], double gamma,

@@ -79,7 +79,10 @@ def build(force: bool = False) -> str:
     if force or not newer:
         tmp = _LIB + ".%d.tmp" % os.getpid()
         # -ffp-contract=off: every product and sum is rounded as written.
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+        # -fopenmp: the per-node and per-interface loops run on all host
+        # threads; every reduction across threads is a max or a min, so the
+        # results equal the single-threaded ones bit for bit.
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
@@ -91,12 +94,17 @@ def lib():
     with _lock:
         if _lib is None:
             path = build()
+            # idle OpenMP threads sleep instead of spinning: the tests make
+            # thousands of small calls, between which spinning threads would
+            # only compete with the caller
+            os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
             L = ctypes.CDLL(path)
             d = ctypes.POINTER(ctypes.c_double)
             i = ctypes.POINTER(ctypes.c_int)
             c = ctypes.POINTER(Cfg)
             c3 = ctypes.POINTER(Cfg3)
             sig = {
+                "oref_set_threads": (ctypes.c_int, [ctypes.c_int]),
                 "oref_alpha": (None, [ctypes.c_int, d]),
                 "oref_logmean": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
                 "oref_prim2cons": (None, [ctypes.c_double, d, d]),
@@ -112,6 +120,8 @@ def lib():
                 "oref_rhs": (ctypes.c_int, [c, d, d, d, d, d, d]),
                 "oref_cfl_dt": (ctypes.c_int, [c, d, d, d, d]),
                 "oref_monitor": (ctypes.c_int, [c, d, d, d]),
+                "oref_cfl_solve": (ctypes.c_double, [ctypes.c_int, ctypes.c_long, ctypes.c_double, d, d, d,
+                                                     ctypes.c_double, d, i]),
                 "oref_filter": (None, [c, d, ctypes.c_int]),
                 "oref_jacobi": (None, [c, d, d, ctypes.c_int, d]),
                 "oref_mesh": (ctypes.c_int, [c, d, d, d, ctypes.c_double, d, d, d]),
@@ -162,6 +172,12 @@ def _vec(a, n=None):
     if n is not None:
         assert a.size == n
     return a
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (n <= 0: all host threads);
+    returns the number in effect.  Results do not depend on it."""
+    return lib().oref_set_threads(int(n))
 
 
 def make_cfg(nx, ny, bc=(PERIODIC, PERIODIC), period=(1.0, 1.0), gamma=5.0 / 3.0,
@@ -312,6 +328,19 @@ def monitor(cfg, cons, J):
     if st != 0:
         raise RuntimeError("oracle monitor: cons2prim failed")
     return om.reshape(cfg.ny, cfg.nx)
+
+
+def cfl_solve(a, bmin, bmax, cfl, tau, dt_given=0.0):
+    """The step of eq. cfl with the mesh velocity in the spectral radius from
+    the per-node terms a, bmin, bmax [ndir][N]: returns (dt, tau used, Newton
+    steps, -1 for the fallback)."""
+    a, bmin, bmax = (np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (a, bmin, bmax))
+    ndir, N = a.shape
+    t = ctypes.c_double(tau)
+    it = ctypes.c_int(0)
+    dt = lib().oref_cfl_solve(ndir, N, float(cfl), _p(a), _p(bmin), _p(bmax), float(dt_given), ctypes.byref(t),
+                              ctypes.byref(it))
+    return dt, t.value, it.value
 
 
 def mesh_filter(cfg, om, n):

@@ -27,9 +27,23 @@
  *                                   entropy identity / inequality, telescoping,
  *                                   order of accuracy)
  *   mesh redistribution             pinned (uniform-monitor fixed point,
- *                                   movement limiter bound, no tangling)
+ *                                   movement limiter bound, no tangling; the
+ *                                   filter's Fourier symbol, the Jacobi
+ *                                   sweep's damping of a mode, its fixed point
+ *                                   = the Euler-Lagrange solution of the
+ *                                   adaption functional)
+ *   step of eq. cfl                 pinned (dt sum_k max rho = CFL with the
+ *                                   mesh velocity, rho from eigenvalues;
+ *                                   brute-force root on random data)
  *   SSP-RK3 step                    pinned (free stream, exact advection error)
+ *
+ * The loops over nodes and interfaces run under OpenMP; they write disjoint
+ * outputs and combine across threads only by max or min, so results do not
+ * depend on the thread count.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "esmm_oracle.h"
 
 #include <math.h>
@@ -44,6 +58,20 @@
 /* Coefficients alpha_{p,n} (Sec. 3.2, constraint eq. HOCoeff):
  *   sum_n n alpha_{p,n} = 1,  sum_n n^{2s-1} alpha_{p,n} = 0 (s = 2..p).
  * Solved by hand: p=1: 1;  p=2: 4/3, -1/6;  p=3: 3/2, -3/10, 1/30.          */
+/* Threads of the parallel loops (OpenMP; n <= 0: all host threads).  The
+ * loops write disjoint outputs and reduce across threads only by max or
+ * min, so every result is independent of the thread count. */
+int oref_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 void oref_alpha(int p, double *alpha)
 {
     if (p == 1) {
@@ -550,11 +578,13 @@ static int build_pad(const oref_cfg *c, const double *cons, const double *J,
     double *w = (double *)malloc(sizeof(double) * nv * N);
     int status = 0;
     /* cons2prim at every node: U = (J U)/J */
+    #pragma omp parallel for reduction(min : status)
     for (int id = 0; id < N; ++id) {
         double wi[NVMAX];
         if (node_prim(c, cons, J, id, wi) != 0) status = -1;
         for (int a = 0; a < nv; ++a) w[a * N + id] = wi[a];
     }
+    #pragma omp parallel for
     for (int j = -G; j < ny + G; ++j)
         for (int i = -G; i < nx + G; ++i) {
             int id = pad_index(P, i, j), src = data_index(c, i, j);
@@ -797,6 +827,7 @@ int oref_rhs(const oref_cfg *c, const double *cons, const double *J,
     /* eqs. RMHDSemiU_O2p_ES and RMHDSemiJ_O2p_ES (Delta xi_k = 1):
      * flux differences, and for RMHD the Godunov-Powell source
      * -Phi'(V_i)^T sum_k (B~_{i+1/2} - B~_{i-1/2}). */
+    #pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int id = j * nx + i;
@@ -848,6 +879,128 @@ int oref_init_state(const oref_cfg *c, const double *prim, const double *x,
     return 0;
 }
 
+/* Speed bounds of every node for eq. cfl: bmin[k][N], bmax[k][N] =
+ * L_k lambda_min / J and L_k lambda_max / J, lambda the eigenvalues of the
+ * flux Jacobian along the unit metric normal of direction k (L_k its
+ * length), i.e. the extreme eigenvalues of d(F_k)/d(JU) on a static mesh. */
+static int speed_bounds(const oref_cfg *c, const double *cons, const double *J, const double *x,
+                        double *bmin, double *bmax)
+{
+    int nx = c->nx, ny = c->ny, N = nx * ny, nv = nvar(c), status = 0;
+    #pragma omp parallel for reduction(min : status)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int id = j * nx + i;
+            double w[NVMAX], M[2][2];
+            if (node_prim(c, cons, J, id, w) != 0) status = -1;
+            node_metrics(c, x, i, j, M);
+            for (int k = 0; k < 2; ++k) {
+                double Lk = sqrt(M[k][0] * M[k][0] + M[k][1] * M[k][1]);
+                double wr[NVMAX], lam[NVMAX], R[NVMAX * NVMAX];
+                rotate(c, M[k][0] / Lk, M[k][1] / Lk, w, wr);
+                eigen(c, wr, lam, R);
+                double lo = lam[0], hi = lam[0];
+                for (int m = 1; m < nv; ++m) {
+                    if (lam[m] < lo) lo = lam[m];
+                    if (lam[m] > hi) hi = lam[m];
+                }
+                bmin[k * N + id] = Lk * lo / J[id];
+                bmax[k * N + id] = Lk * hi / J[id];
+            }
+        }
+    return status;
+}
+
+/* eq. cfl with the mesh velocity in the spectral radius, solved for dt.
+ *
+ * The spectral radius of d(F_k)/d(JU) at node i is
+ *   rho_{k,i} = max_m |(J xi_k)_t + L_k lambda_m| / J_i,
+ * with the temporal metric (J xi_k)_t = -xdot . (J xi_k,x) (eq. VCLCoeff) and
+ * the mesh velocity xdot = Delta tau d / dt of Sec. 5 (d = x^[mu] - x^n).  So
+ *   dt rho_{k,i} = max_m |dt b_{k,i,m} - tau a_{k,i}|,
+ *   a = d.(J xi_k,x)/J,  b_m = L_k lambda_m / J,
+ * and since max over m of |t b_m - c| for t >= 0 is max(t b_max - c,
+ * c - t b_min), eq. cfl, dt sum_k max_i rho_{k,i} = CFL, reads g(dt) = CFL
+ * with
+ *   g(t) = sum_k max_i max(t bmax_{k,i} - tau a_{k,i}, tau a_{k,i} - t bmin_{k,i}),
+ * a convex piecewise-linear function of t (a sum of maxima of lines), with
+ * g(0) = C_m = tau sum_k max_i |a_{k,i}| (the displacement's own Courant
+ * number) and t S - C_m <= g(t) <= t S + C_m, S = sum_k max_i max(|bmin|,
+ * |bmax|) the static radius.  For C_m < CFL the root is unique and lies in
+ * [(CFL - C_m)/S, (CFL + C_m)/S].
+ *
+ * Reading (the paper defines xdot through dt^n and dt^n through xdot):
+ *   - dt^n is that root: Newton's method from the right end, each step to
+ *     the root of the line that is active at the iterate (the smaller slope
+ *     where two lines tie: the left derivative).  A convex function lies
+ *     above each such line, so the iterates decrease monotonically to the
+ *     root and stop on its piece; the iteration ends once g <= CFL, or once
+ *     the Newton step is below 2^-50 t (the root up to rounding).  If
+ *     OREF_CFL_NEWTON evaluations do not end it, the safe lower bound
+ *     (CFL - C_m)/S is used.
+ *   - Delta tau is left as the limiter gave it, unless C_m >= CFL, where no
+ *     dt > 0 satisfies eq. cfl: then Delta tau is scaled so that C_m = CFL/2.
+ *   - A given dt > 0 is used as is, with the same rule for Delta tau.
+ * Arrays [ndir][N]; *tau is the limiter value on entry and the one used on
+ * return; *iters (may be NULL) receives the Newton steps taken (-1: the
+ * fallback).                                                                 */
+double oref_cfl_solve(int ndir, long N, double cfl, const double *a, const double *bmin, const double *bmax,
+                      double dt_given, double *tau, int *iters)
+{
+    double C = 0.0, S = 0.0;
+    for (int k = 0; k < ndir; ++k) {
+        double amax = 0.0, smax = 0.0;
+        for (long i = 0; i < N; ++i) {
+            double av = fabs(a[k * N + i]), sv = fmax(fabs(bmin[k * N + i]), fabs(bmax[k * N + i]));
+            if (av > amax) amax = av;
+            if (sv > smax) smax = sv;
+        }
+        C += amax;
+        S += smax;
+    }
+    C *= *tau;
+    if (C >= cfl) {
+        *tau *= 0.5 * cfl / C;
+        C = 0.5 * cfl;
+    }
+    if (iters) *iters = 0;
+    if (dt_given > 0.0) return dt_given;
+    if (!(C > 0.0)) return cfl / S;
+    double t = (cfl + C) / S;
+    for (int it = 0; it < OREF_CFL_NEWTON; ++it) {
+        double g = 0.0, slope = 0.0;
+        for (int k = 0; k < ndir; ++k) {
+            double vk = -1.0, sk = 0.0;
+            for (long i = 0; i < N; ++i) {
+                double ta = *tau * a[k * N + i];
+                double up = t * bmax[k * N + i] - ta, dn = ta - t * bmin[k * N + i];
+                double v = up > dn ? up : dn;
+                double sl = up > dn ? bmax[k * N + i] : (dn > up ? -bmin[k * N + i]
+                                                                  : fmin(bmax[k * N + i], -bmin[k * N + i]));
+                if (v > vk || (v == vk && sl < sk)) {
+                    vk = v;
+                    sk = sl;
+                }
+            }
+            g += vk;
+            slope += sk;
+        }
+        if (g <= cfl) {
+            if (iters) *iters = it;
+            return t;
+        }
+        if (!(slope > 0.0)) break;
+        double step = (g - cfl) / slope;
+        if (step <= 0x1p-50 * t) {     /* on the root up to rounding */
+            if (iters) *iters = it;
+            return t;
+        }
+        t -= step;
+    }
+    if (iters) *iters = -1;
+    return (cfl - C) / S;
+}
+
 /* eq. cfl: dt = CFL / sum_k max_i rho_{k,i}, rho_{k,i} the spectral radius of
  * d(F_k)/d(JU) at node i.  Reading: the static-mesh radius (xdot = 0) is
  * used, rho_{k,i} = L_{k,i} max_m |lambda_m| / J_i, because the mesh velocity
@@ -857,6 +1010,7 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
 {
     int nx = c->nx, ny = c->ny, nv = nvar(c), status = 0;
     double rmax[2] = {0.0, 0.0};
+    #pragma omp parallel for reduction(min : status) reduction(max : rmax[:2])
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int id = j * nx + i;
@@ -895,14 +1049,7 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
  * coordinate that moves (the printed "(x_1)" read as x_k).
  *
  * Step size (eq. cfl, whose spectral radius includes the temporal metric,
- * i.e. the mesh velocity).  The displacement of the step, d = Delta tau
- * (x^[mu] - x^n), does not depend on dt, and its Courant number is
- *   C_m = sum_k max_i |d_i . (J xi_k,x)_i| / J_i.
- * Reading: Delta tau is also capped so that C_m <= CFL/2, and then
- *   dt = (CFL - C_m) / sum_k max_i rho_{k,i}   (static-mesh radius),
- * so that by the triangle inequality dt sum_k max_i rho_{k,i}(xdot) <= CFL
- * holds with xdot = d/dt.  A given dt > 0 is used as is (Delta tau capped
- * the same way).  *dt_out receives the step.                                */
+ * i.e. the mesh velocity): see oref_cfl_solve.  *dt_out receives the step. */
 /* sigma at node (i, j) of the index space, ghosts included: the inflow
  * state's beyond an inflow end (the data the scheme's fluxes see there), else
  * the boundary-mapped node's */
@@ -917,6 +1064,7 @@ int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double 
     int nx = c->nx, ny = c->ny, N = nx * ny, status = 0;
     double *sig = (double *)malloc(sizeof(double) * N);
     double *lap = (double *)malloc(sizeof(double) * N);
+    #pragma omp parallel for reduction(min : status)
     for (int id = 0; id < N; ++id) {
         double w[NVMAX];
         if (node_prim(c, cons, J, id, w) != 0) status = -1;
@@ -924,6 +1072,7 @@ int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double 
     }
     double sig_in = (c->monitor == OREF_MONITOR_LNRHO) ? log(c->inflow[0]) : c->inflow[0];
     double gmax = 0.0, lmax = 0.0;
+    #pragma omp parallel for reduction(max : gmax, lmax)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double e = sigma_at(c, sig, sig_in, i + 1, j), wv = sigma_at(c, sig, sig_in, i - 1, j);
@@ -956,6 +1105,7 @@ void oref_filter(const oref_cfg *c, double *om, int n)
     int nx = c->nx, ny = c->ny, N = nx * ny;
     double *om2 = (double *)malloc(sizeof(double) * N);
     for (int f = 0; f < n; ++f) {
+        #pragma omp parallel for
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 double acc = 0.0;
@@ -982,6 +1132,7 @@ void oref_jacobi(const oref_cfg *c, const double *om, const double *x, int mu, d
     double *Xn = (double *)malloc(sizeof(double) * 2 * N);
     memcpy(X, x, sizeof(double) * 2 * N);
     for (int nu = 0; nu < mu; ++nu) {
+        #pragma omp parallel for
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 int id = j * nx + i;
@@ -1026,6 +1177,7 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
     oref_filter(c, om, c->n_filter);
     oref_jacobi(c, om, x, c->mu, X);
     double tau = 1.0;
+    #pragma omp parallel for reduction(min : tau)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int id = j * nx + i;
@@ -1044,26 +1196,25 @@ int oref_mesh(const oref_cfg *c, const double *cons, const double *J,
             }
         }
     if (tau < 0.0) tau = 0.0;
-    /* mesh Courant number of the full displacement x^[mu] - x^n */
-    double cm[2] = {0.0, 0.0};
+    /* a_{k,i} = d_i . (J xi_k,x)_i / J_i for the full displacement
+     * d = x^[mu] - x^n, and the speed bounds of every node */
+    double *am = (double *)malloc(sizeof(double) * 2 * N);
+    double *bmin = (double *)malloc(sizeof(double) * 2 * N);
+    double *bmax = (double *)malloc(sizeof(double) * 2 * N);
+    #pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int id = j * nx + i;
             double M[2][2];
             node_metrics(c, x, i, j, M);
             double d0 = X[id] - x[id], d1 = X[N + id] - x[N + id];
-            for (int k = 0; k < 2; ++k) {
-                double r = fabs(d0 * M[k][0] + d1 * M[k][1]) / J[id];
-                if (r > cm[k]) cm[k] = r;
-            }
+            for (int k = 0; k < 2; ++k) am[k * N + id] = (d0 * M[k][0] + d1 * M[k][1]) / J[id];
         }
-    double C1 = cm[0] + cm[1];
-    if (C1 > 0.0 && tau * C1 > 0.5 * c->cfl) tau = 0.5 * c->cfl / C1;
-    if (!(dt > 0.0)) {
-        double dts;
-        status |= oref_cfl_dt(c, cons, J, x, &dts);
-        dt = dts * (1.0 - tau * C1 / c->cfl);
-    }
+    status |= speed_bounds(c, cons, J, x, bmin, bmax);
+    dt = oref_cfl_solve(2, N, c->cfl, am, bmin, bmax, dt, &tau, NULL);
+    free(am);
+    free(bmin);
+    free(bmax);
     for (int a = 0; a < 2 * N; ++a) xdot[a] = tau * (X[a] - x[a]) / dt;
     if (dtau) *dtau = tau;
     if (dt_out) *dt_out = dt;

@@ -102,6 +102,20 @@ int oref_cfl_dt(const oref_cfg *c, const double *cons, const double *J,
  * whose maximum is 0 is left out (alpha_lap = 0 gives eq. monitor). */
 int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double *om);
 
+/* Threads of the oracle's parallel loops (n <= 0: all host threads);
+ * returns the number in effect.  Results do not depend on it. */
+int oref_set_threads(int n);
+
+/* Newton steps of oref_cfl_solve before it falls back to the safe bound. */
+#define OREF_CFL_NEWTON 8
+
+/* eq. cfl with the mesh velocity in the spectral radius, solved for dt (the
+ * reading and the method are stated at the definition).  a, bmin, bmax are
+ * [ndir][N]: the displacement term d.(J xi_k,x)/J and the speed bounds
+ * L_k lambda_min/J, L_k lambda_max/J of every node. */
+double oref_cfl_solve(int ndir, long N, double cfl, const double *a, const double *bmin, const double *bmax,
+                      double dt_given, double *tau, int *iters);
+
 /* Sec. 5 low-pass filter of the monitor, n passes in place (weights
  * (1/2)^{|j1|+|j2|+2} over the 3x3 neighbourhood). */
 void oref_filter(const oref_cfg *c, double *om, int n);

@@ -129,6 +129,7 @@ static void node_metrics3(const oref3_cfg *c, const double *x, int i, int j, int
 void oref3_metrics(const oref3_cfg *c, const double *x, double *m, double *J0)
 {
     long N = (long)c->nx * c->ny * c->nz;
+    #pragma omp parallel for
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -186,11 +187,13 @@ static int build_pad3(const oref3_cfg *c, const double *cons, const double *J, c
     P->Mt = (double *)malloc(sizeof(double) * 3 * P->S);
     double *w = (double *)malloc(sizeof(double) * 8 * N);
     int status = 0;
+    #pragma omp parallel for reduction(min : status)
     for (long id = 0; id < N; ++id) {
         double wi[8];
         if (node_prim3(c, cons, J, id, wi) != 0) status = -1;
         for (int a = 0; a < 8; ++a) w[a * N + id] = wi[a];
     }
+    #pragma omp parallel for
     for (int k = -G3; k < c->nz + G3; ++k)
         for (int j = -G3; j < c->ny + G3; ++j)
             for (int i = -G3; i < c->nx + G3; ++i) {
@@ -417,6 +420,7 @@ int oref3_rhs(const oref3_cfg *c, const double *cons, const double *J, const dou
     for (long a = 0; a < 8 * N; ++a) dcons[a] = 0.0;
     for (long a = 0; a < N; ++a) dJ[a] = 0.0;
     /* eqs. RMHDSemiU_O2p_ES / RMHDSemiJ_O2p_ES with the Powell source */
+    #pragma omp parallel for
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -471,6 +475,7 @@ int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const 
 {
     int status = 0;
     double rmax[3] = {0.0, 0.0, 0.0};
+    #pragma omp parallel for reduction(min : status) reduction(max : rmax[:3])
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -492,6 +497,39 @@ int oref3_cfl_dt(const oref3_cfg *c, const double *cons, const double *J, const 
                 }
             }
     *dt = c->cfl / (rmax[0] + rmax[1] + rmax[2]);
+    return status;
+}
+
+/* Speed bounds of every node for eq. cfl (the 3D form of the 2D oracle's
+ * speed_bounds): L_k lambda_min / J and L_k lambda_max / J per direction. */
+static int speed_bounds3(const oref3_cfg *c, const double *cons, const double *J, const double *x,
+                         double *bmin, double *bmax)
+{
+    long N = (long)c->nx * c->ny * c->nz;
+    int status = 0;
+    #pragma omp parallel for reduction(min : status)
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                long id = ((long)k * c->ny + j) * c->nx + i;
+                double w[8], M[3][3];
+                if (node_prim3(c, cons, J, id, w) != 0) status = -1;
+                node_metrics3(c, x, i, j, k, M);
+                for (int d = 0; d < 3; ++d) {
+                    double Lk = sqrt(M[d][0] * M[d][0] + M[d][1] * M[d][1] + M[d][2] * M[d][2]);
+                    double nn[3] = {M[d][0] / Lk, M[d][1] / Lk, M[d][2] / Lk}, T[3][3], wr[8], lam[8], R[64];
+                    frame3(nn, T);
+                    rot3(T, w, wr);
+                    oref_mhd_eigen(c->gamma, wr, lam, R);
+                    double lo = lam[0], hi = lam[0];
+                    for (int m = 1; m < 8; ++m) {
+                        if (lam[m] < lo) lo = lam[m];
+                        if (lam[m] > hi) hi = lam[m];
+                    }
+                    bmin[d * N + id] = Lk * lo / J[id];
+                    bmax[d * N + id] = Lk * hi / J[id];
+                }
+            }
     return status;
 }
 
@@ -518,6 +556,7 @@ int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, doubl
     int status = 0;
     double *sig = (double *)malloc(sizeof(double) * N);
     double *lap = (double *)malloc(sizeof(double) * N);
+    #pragma omp parallel for reduction(min : status)
     for (long id = 0; id < N; ++id) {
         double w[8];
         if (node_prim3(c, cons, J, id, w) != 0) status = -1;
@@ -525,6 +564,7 @@ int oref3_monitor(const oref3_cfg *c, const double *cons, const double *J, doubl
     }
     double sig_in = (c->monitor == OREF_MONITOR_LNRHO) ? log(c->inflow[0]) : c->inflow[0];
     double gmax = 0.0, lmax = 0.0;
+    #pragma omp parallel for reduction(max : gmax, lmax)
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -559,6 +599,7 @@ void oref3_filter(const oref3_cfg *c, double *om, int n)
     long N = (long)c->nx * c->ny * c->nz;
     double *om2 = (double *)malloc(sizeof(double) * N);
     for (int f = 0; f < n; ++f) {
+        #pragma omp parallel for
         for (int k = 0; k < c->nz; ++k)
             for (int j = 0; j < c->ny; ++j)
                 for (int i = 0; i < c->nx; ++i) {
@@ -586,6 +627,7 @@ void oref3_jacobi(const oref3_cfg *c, const double *om, const double *x, int mu,
     double *Xn = (double *)malloc(sizeof(double) * 3 * N);
     memcpy(X, x, sizeof(double) * 3 * N);
     for (int nu = 0; nu < mu; ++nu) {
+        #pragma omp parallel for
         for (int k = 0; k < c->nz; ++k)
             for (int j = 0; j < c->ny; ++j)
                 for (int i = 0; i < c->nx; ++i) {
@@ -642,6 +684,7 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
     oref3_filter(c, om, c->n_filter);
     oref3_jacobi(c, om, x, c->mu, X);
     double tau = 1.0;
+    #pragma omp parallel for reduction(min : tau)
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -663,8 +706,12 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
                 }
             }
     if (tau < 0.0) tau = 0.0;
-    /* step size with the mesh motion included (the 2D reading, three directions) */
-    double cm[3] = {0.0, 0.0, 0.0};
+    /* the step of eq. cfl with the mesh velocity in the spectral radius
+     * (oref_cfl_solve): the displacement terms and the speed bounds */
+    double *am = (double *)malloc(sizeof(double) * 3 * N);
+    double *bmin = (double *)malloc(sizeof(double) * 3 * N);
+    double *bmax = (double *)malloc(sizeof(double) * 3 * N);
+    #pragma omp parallel for
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -672,18 +719,14 @@ int oref3_mesh(const oref3_cfg *c, const double *cons, const double *J, const do
                 double M[3][3];
                 node_metrics3(c, x, i, j, k, M);
                 double dd[3] = {X[id] - x[id], X[N + id] - x[N + id], X[2 * N + id] - x[2 * N + id]};
-                for (int d = 0; d < 3; ++d) {
-                    double r = fabs(dd[0] * M[d][0] + dd[1] * M[d][1] + dd[2] * M[d][2]) / J[id];
-                    if (r > cm[d]) cm[d] = r;
-                }
+                for (int d = 0; d < 3; ++d)
+                    am[d * N + id] = (dd[0] * M[d][0] + dd[1] * M[d][1] + dd[2] * M[d][2]) / J[id];
             }
-    double C1 = cm[0] + cm[1] + cm[2];
-    if (C1 > 0.0 && tau * C1 > 0.5 * c->cfl) tau = 0.5 * c->cfl / C1;
-    if (!(dt > 0.0)) {
-        double dts;
-        status |= oref3_cfl_dt(c, cons, J, x, &dts);
-        dt = dts * (1.0 - tau * C1 / c->cfl);
-    }
+    status |= speed_bounds3(c, cons, J, x, bmin, bmax);
+    dt = oref_cfl_solve(3, N, c->cfl, am, bmin, bmax, dt, &tau, NULL);
+    free(am);
+    free(bmin);
+    free(bmax);
     for (long a = 0; a < 3 * N; ++a) xdot[a] = tau * (X[a] - x[a]) / dt;
     if (dtau) *dtau = tau;
     if (dt_out) *dt_out = dt;

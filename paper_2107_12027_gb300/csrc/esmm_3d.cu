@@ -213,9 +213,11 @@ __global__ void k3_update(Geom3 g, const double *__restrict__ q, const double *_
         xo[a * g.N + id] = A * xn[a * g.N + id] + B * (xs[a * g.N + id] + dt * xdot[a * g.N + id]);
 }
 
-// static spectral radius per direction (eq. cfl)
+// static spectral radius per direction (eq. cfl); with cflb (the moving-mesh
+// step) also the speed bounds L_k lambda_min/J and L_k lambda_max/J of every
+// node into its rows 3 + d and 6 + d
 __global__ void k3_cfl(Geom3 g, double gam, const double *__restrict__ q, const double *__restrict__ J,
-                       unsigned long long *red)
+                       unsigned long long *red, double *__restrict__ cflb)
 {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double r[3] = {0.0, 0.0, 0.0};
@@ -234,9 +236,17 @@ __global__ void k3_cfl(Geom3 g, double gam, const double *__restrict__ q, const 
             frame3(nn, T);
             rot3(T, w, wr);
             eigen_mhd(gam, wr, lam, R, false);
-            double a = 0.0;
-            for (int mm = 0; mm < 8; ++mm) a = fmax(a, fabs(lam[mm]));
+            double a = 0.0, lo = lam[0], hi = lam[0];
+            for (int mm = 0; mm < 8; ++mm) {
+                a = fmax(a, fabs(lam[mm]));
+                lo = fmin(lo, lam[mm]);
+                hi = fmax(hi, lam[mm]);
+            }
             r[d] = Lk * a * iJ;
+            if (cflb) {
+                cflb[(3 + d) * g.N + id] = Lk * lo * iJ;
+                cflb[(6 + d) * g.N + id] = Lk * hi * iJ;
+            }
         }
     }
     for (int d = 0; d < 3; ++d) {
@@ -251,16 +261,39 @@ __global__ void k3_red_init(unsigned long long *red)
     if (t < NR3) red[t] = t == 1 ? (unsigned long long)__double_as_longlong(1.0) : 0ull;
 }
 
-// the step with the mesh velocity (the 2D rule over three directions)
-__global__ void k3_dt(double cfl, double dt_fixed, unsigned long long *red, double *dt_dev)
+// set-up of the step solve of eq. cfl with the mesh velocity (the 2D rule
+// over three directions, esmm_reduce.cuh dt_setup): slots 5..7 hold A_d,
+// slots 2..4 the static radius, slot 1 the limiter (written back)
+__global__ void k3_dt(double cfl, double dt_fixed, unsigned long long *red, DtSolve *ds, double *dt_dev)
 {
     if (threadIdx.x || blockIdx.x) return;
-    double C1 = bits_to_double(red[5]) + bits_to_double(red[6]) + bits_to_double(red[7]);
     double tau = bits_to_double(red[1]);
-    if (C1 > 0.0 && tau * C1 > 0.5 * cfl) tau = 0.5 * cfl / C1;
+    dt_setup(ds, cfl, dt_fixed, bits_to_double(red[5]) + bits_to_double(red[6]) + bits_to_double(red[7]),
+             bits_to_double(red[2]) + bits_to_double(red[3]) + bits_to_double(red[4]), &tau, dt_dev);
     red[1] = (unsigned long long)__double_as_longlong(tau);
-    double S = bits_to_double(red[2]) + bits_to_double(red[3]) + bits_to_double(red[4]);
-    dt_dev[0] = dt_fixed > 0.0 ? dt_fixed : cfl / S * (1.0 - tau * C1 / cfl);
+}
+
+// one Newton evaluation of the step solve over all nodes: cflb rows 0..2
+// hold a_d, rows 3..8 the speed bounds; part [blocks][3][2]
+__global__ void k3_dt_newton(Geom3 g, double cfl, const double *__restrict__ cflb, const unsigned long long *red,
+                             DtSolve *ds, double *part, double *dt_dev)
+{
+    __shared__ double t_sh, tau_sh;
+    __shared__ int skip;
+    if (threadIdx.x == 0) {
+        skip = ds->done;
+        t_sh = ds->t;
+        tau_sh = bits_to_double(red[1]);
+    }
+    __syncthreads();
+    if (skip) return;
+    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {-1.0, -1.0, -1.0}, sl[3] = {0.0, 0.0, 0.0};
+    if (id < g.N)
+        for (int d = 0; d < 3; ++d)
+            cfl_line(t_sh, tau_sh * cflb[d * g.N + id], cflb[(3 + d) * g.N + id], cflb[(6 + d) * g.N + id], v[d],
+                     sl[d]);
+    dt_newton_block<3>(ds, v, sl, blockIdx.x, 0, gridDim.x, part, cfl, dt_dev);
 }
 
 __global__ void k3_time(const double *dt_dev, double *t_dev)
@@ -361,7 +394,8 @@ __global__ void k3_mesh_jacobi(Geom3 g, const double *__restrict__ om, const dou
 // limiter (half the neighbour spacing toward the displacement, three
 // directions) and the displacement's Courant number per direction
 __global__ void k3_mesh_tau(Geom3 g, const double *__restrict__ x, const double *__restrict__ X,
-                            const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red)
+                            const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red,
+                            double *__restrict__ cflb)
 {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double tau = 1.0, cm[3] = {0.0, 0.0, 0.0};
@@ -385,9 +419,12 @@ __global__ void k3_mesh_tau(Geom3 g, const double *__restrict__ x, const double 
         tau = fmax(tau, 0.0);
         long long c = pidx3(g, i, j, k);
         double iJ = 1.0 / J[id];
-        for (int d = 0; d < 3; ++d)
-            cm[d] = fabs(dd[0] * q[(F_M + 3 * d) * g.P + c] + dd[1] * q[(F_M + 3 * d + 1) * g.P + c] +
-                         dd[2] * q[(F_M + 3 * d + 2) * g.P + c]) * iJ;
+        for (int d = 0; d < 3; ++d) {
+            const double ad = (dd[0] * q[(F_M + 3 * d) * g.P + c] + dd[1] * q[(F_M + 3 * d + 1) * g.P + c] +
+                               dd[2] * q[(F_M + 3 * d + 2) * g.P + c]) * iJ;
+            cm[d] = fabs(ad);
+            cflb[d * g.N + id] = ad;
+        }
     }
     double m = block_reduce<1>(tau);
     if (threadIdx.x == 0) atomic_min_nonneg(red + 1, m);
@@ -402,7 +439,8 @@ __global__ void k3_mesh_xdot(Geom3 g, const double *__restrict__ x, const double
 {
     long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= 3 * g.N) return;
-    xdot[id] = bits_to_double(red[1]) * (X[id] - x[id]) / dt_dev[0];
+    // a step of 0 (a NaN spectral radius) leaves the mesh where it is
+    xdot[id] = dt_dev[0] > 0.0 ? bits_to_double(red[1]) * (X[id] - x[id]) / dt_dev[0] : 0.0;
 }
 
 // initial J = det(delta_k[x_j]) and cons = J U(prim)
@@ -493,6 +531,8 @@ struct esmm3 {
     double *cons, *J, *x, *xdot, *c1, *J1, *x1, *c2, *J2, *x2;
     double *q, *zg[3], *iflux, *out_dc, *out_dJ, *in_cons, *in_J, *in_x, *in_xdot;
     double *grad, *om, *om2, *X, *Xn, *dt_dev, *t_dev, *partials, *tot;
+    double *cflb, *npart;      // the step solve: [9][N] a_d, bmin_d, bmax_d; [blocks][3][2] partials
+    DtSolve *ds;
     unsigned long long *red;
     int *status;
     double *pin;
@@ -620,11 +660,12 @@ int mesh_and_dt3(esmm3 *g, double dt)
     {
         Prof3 pr_(g, ESMM_KIND_OTHER, dt > 0.0 ? 1 : 2);
         k3_red_init<<<1, 32, 0, g->st>>>(g->red);
-        if (!(dt > 0.0)) k3_cfl<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
+        if (!(dt > 0.0))
+            k3_cfl<<<nb, BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red, g->prm.move_mesh ? g->cflb : nullptr);
     }
     if (!g->prm.move_mesh) {
         Prof3 pr_(g, ESMM_KIND_OTHER);
-        k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->dt_dev);
+        k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->ds, g->dt_dev);
         if (!g->xdot_zero) {
             CK3(cudaMemsetAsync(g->xdot, 0, 3 * g->g.N * sizeof(double), g->st));
             g->xdot_zero = 1;
@@ -632,24 +673,33 @@ int mesh_and_dt3(esmm3 *g, double dt)
         return ESMM_OK;
     }
     g->xdot_zero = 0;
-    Prof3 pr_(g, ESMM_KIND_MESH, 6 + g->prm.n_filter + g->prm.mu);
-    // the Laplacian goes to om2, which the filter overwrites only after k3_mesh_omega
-    k3_mesh_grad<<<nb, BS3, 0, g->st>>>(g->g, g->prm.monitor == ESMM_MONITOR_LNRHO, g->prm.alpha_lap > 0.0, g->q,
-                                        g->grad, g->om2, g->red);
-    k3_mesh_omega<<<nb, BS3, 0, g->st>>>(g->g, g->prm.alpha, g->prm.alpha_lap, g->grad, g->om2, g->red, g->om);
-    double *om = g->om, *om2 = g->om2;
-    for (int f = 0; f < g->prm.n_filter; ++f) {
-        k3_mesh_filter<<<nb, BS3, 0, g->st>>>(g->g, om, om2);
-        std::swap(om, om2);
-    }
     const double *src = g->x;
-    for (int nu = 0; nu < g->prm.mu; ++nu) {
-        double *dst = (nu % 2 == 0) ? g->X : g->Xn;
-        k3_mesh_jacobi<<<nb, BS3, 0, g->st>>>(g->g, om, src, dst);
-        src = dst;
+    {
+        Prof3 pr_(g, ESMM_KIND_MESH, 3 + g->prm.n_filter + g->prm.mu);
+        // the Laplacian goes to om2, which the filter overwrites only after k3_mesh_omega
+        k3_mesh_grad<<<nb, BS3, 0, g->st>>>(g->g, g->prm.monitor == ESMM_MONITOR_LNRHO, g->prm.alpha_lap > 0.0,
+                                            g->q, g->grad, g->om2, g->red);
+        k3_mesh_omega<<<nb, BS3, 0, g->st>>>(g->g, g->prm.alpha, g->prm.alpha_lap, g->grad, g->om2, g->red, g->om);
+        double *om = g->om, *om2 = g->om2;
+        for (int f = 0; f < g->prm.n_filter; ++f) {
+            k3_mesh_filter<<<nb, BS3, 0, g->st>>>(g->g, om, om2);
+            std::swap(om, om2);
+        }
+        for (int nu = 0; nu < g->prm.mu; ++nu) {
+            double *dst = (nu % 2 == 0) ? g->X : g->Xn;
+            k3_mesh_jacobi<<<nb, BS3, 0, g->st>>>(g->g, om, src, dst);
+            src = dst;
+        }
+        k3_mesh_tau<<<nb, BS3, 0, g->st>>>(g->g, g->x, src, g->q, g->J, g->red, g->cflb);
     }
-    k3_mesh_tau<<<nb, BS3, 0, g->st>>>(g->g, g->x, src, g->q, g->J, g->red);
-    k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->dt_dev);
+    {
+        Prof3 pr_(g, ESMM_KIND_OTHER, dt > 0.0 ? 1 : 1 + DT_NEWTON);
+        k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->ds, g->dt_dev);
+        if (!(dt > 0.0))
+            for (int it = 0; it < DT_NEWTON; ++it)
+                k3_dt_newton<<<nb, BS3, 0, g->st>>>(g->g, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev);
+    }
+    Prof3 pr_(g, ESMM_KIND_MESH);
     k3_mesh_xdot<<<nb3(3 * g->g.N), BS3, 0, g->st>>>(g->g, g->x, src, g->red, g->dt_dev, g->xdot);
     return ESMM_OK;
 }
@@ -697,7 +747,7 @@ void free3(esmm3 *g)
                     &g->zg[0], &g->zg[1], &g->zg[2], &g->iflux, &g->out_dc, &g->out_dJ, &g->in_cons, &g->in_J,
                     &g->in_x, &g->in_xdot, &g->grad, &g->om, &g->om2, &g->X, &g->Xn, &g->dt_dev, &g->t_dev,
                     &g->partials, &g->tot, &g->lam_a, &g->lam_b, &g->lam_c, &g->lam_v, &g->lamq, &g->xe,
-                    &g->inflow_dev};
+                    &g->inflow_dev, &g->cflb, &g->npart};
     for (double **p : b)
         if (*p) { cudaFree(*p); *p = nullptr; }
     if (g->ck) {
@@ -708,6 +758,8 @@ void free3(esmm3 *g)
     delete g->ck_dt;
     g->ck_dt = nullptr;
     if (g->red) cudaFree(g->red);
+    if (g->ds) cudaFree(g->ds);
+    g->ds = nullptr;
     if (g->status) cudaFree(g->status);
     if (g->pin) cudaFreeHost(g->pin);
 }
@@ -819,10 +871,11 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
         {&g->out_dJ, N}, {&g->in_cons, 8 * N}, {&g->in_J, N}, {&g->in_x, 3 * N}, {&g->in_xdot, 3 * N},
         {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->X, 3 * N}, {&g->Xn, 3 * N}, {&g->dt_dev, 1},
         {&g->t_dev, 1}, {&g->partials, 3 * nb}, {&g->tot, 3}, {&g->xe, (size_t)NXE * ext_count3(g->g)},
-        {&g->inflow_dev, 8}};
+        {&g->inflow_dev, 8}, {&g->cflb, 9 * N}, {&g->npart, 6 * nb}};
     bool ok = true;
     for (auto &a : al) ok = ok && cudaMalloc((void **)a.p, a.n * d) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&g->red, NR3 * sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMalloc((void **)&g->ds, sizeof(DtSolve)) == cudaSuccess &&
          cudaMalloc((void **)&g->status, 2 * sizeof(int)) == cudaSuccess &&
          cudaMallocHost((void **)&g->pin, 16 * sizeof(double)) == cudaSuccess;
     for (int k = 0; ok && k < 3; ++k) ok = cudaMemsetAsync(g->zg[k], 0xff, N * d, g->st) == cudaSuccess;
@@ -1012,8 +1065,8 @@ int esmm3_cfl_dt(esmm3 *g, double *dt)
     g->launches += 3;
     g->nl[ESMM_KIND_OTHER] += 3;
     k3_red_init<<<1, 32, 0, g->st>>>(g->red);
-    k3_cfl<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red);
-    k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, 0.0, g->red, g->dt_dev);
+    k3_cfl<<<nb3(g->g.N), BS3, 0, g->st>>>(g->g, g->gamma, g->q, g->J, g->red, nullptr);
+    k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, 0.0, g->red, g->ds, g->dt_dev);
     CK3(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK3(cudaStreamSynchronize(g->st));
     *dt = g->pin[0];

@@ -73,6 +73,9 @@ struct esmm_grid {
     double *grad, *om, *om2, *X, *Xn;
     unsigned long long *red;         // [nprob][NRED]
     double *dt_dev, *t_dev;          // [nprob]
+    double *cflb;                    // [6][Ntot] the step solve: a_k, bmin_k, bmax_k per node
+    double *npart;                   // [node-domain blocks][2][2] its per-block partial results
+    DtSolve *ds;                     // [nprob] its state
     double *partials;                // totals: per-block partial sums
     double *tot_dev;                 // [nprob][3]
     int *status;                     // [0] failed recoveries, [1] bad initial states
@@ -347,23 +350,36 @@ void update(esmm_grid *g, double *dcons, double *dJ, const double *cn, const dou
 unsigned nprob_blocks(const esmm_grid *g) { return nblk(g->nprob, 128); }
 
 // static spectral radius of the state (when dt is to come from eq. cfl);
-// requires g->q of the state with a static mesh and the slots reset
-void step_radius(esmm_grid *g, double dt)
+// requires g->q of the state with a static mesh and the slots reset.  With a
+// moving mesh the speed bounds of every node go to g->cflb for the step solve.
+void step_radius(esmm_grid *g, double dt, bool moving)
 {
     if (dt > 0.0) return;
     Prof pr_(g, ESMM_KIND_OTHER);
     LaunchDom L = dom(g, D_NODE);
+    double *cflb = moving ? g->cflb : nullptr;
     if (g->phys == ESMM_RMHD)
-        launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->prm.precision == ESMM_MIXED, g->st);
-    else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red, q32_of(g));
+        launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->prm.precision == ESMM_MIXED, cflb, g->st);
+    else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red, q32_of(g), cflb);
 }
 
-// the step (and the capped mesh limiter) into dt_dev / slot 1, after the
-// radius and (when the mesh moves) the mesh chain up to k_mesh_tau
-void step_dt(esmm_grid *g, double dt)
+// the step into dt_dev (and the limiter, scaled where the displacement alone
+// breaks eq. cfl, into slot 1), after the radius and (when the mesh moves) the
+// mesh chain up to k_mesh_tau: the set-up, then, for a CFL step with mesh
+// motion, the DT_NEWTON evaluations of the solve (each a no-op once a
+// problem's solve has ended; a fixed count keeps the step graph-capturable)
+void step_dt(esmm_grid *g, double dt, bool moving)
 {
-    Prof pr_(g, ESMM_KIND_OTHER);
-    k_dt<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->prm.cfl, dt, g->red, g->dt_dev);
+    {
+        Prof pr_(g, ESMM_KIND_OTHER);
+        k_dt<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->prm.cfl, dt, g->red, g->ds, g->dt_dev);
+    }
+    if (dt > 0.0 || !moving) return;
+    LaunchDom L = dom(g, D_NODE);
+    for (int it = 0; it < DT_NEWTON; ++it) {
+        Prof pr_(g, ESMM_KIND_OTHER);
+        k_dt_newton<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev);
+    }
 }
 
 void red_init(esmm_grid *g)
@@ -416,9 +432,9 @@ int mesh_finish(esmm_grid *g, double dt, const LaunchDom &L, const LaunchDom &L2
     }
     {
         Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_tau<T><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, Dd, g->q, g->J, g->red);
+        k_mesh_tau<T><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, Dd, g->q, g->J, g->red, g->cflb);
     }
-    step_dt(g, dt);
+    step_dt(g, dt, true);
     {
         Prof pr_(g, ESMM_KIND_MESH);
         k_mesh_xdot<T><<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, Dd, g->red, g->dt_dev, g->xdot);
@@ -441,7 +457,7 @@ int mesh_sweeps_init(esmm_grid *g)
 int mesh_core(esmm_grid *g, double dt)
 {
     if (!g->prm.move_mesh) {
-        step_dt(g, dt);
+        step_dt(g, dt, false);
         if (!g->xdot_zero) {
             CK(cudaMemsetAsync(g->xdot, 0, sizeof(double) * 2 * g->Ntot, g->st));
             g->xdot_zero = 1;
@@ -486,7 +502,7 @@ int rk_step_async(esmm_grid *g, double dt)
     // the state's node data with a static mesh: CFL step and monitor (Sec. 5)
     node(g, g->cons, g->J, g->x, nullptr, g->pg[0], g->pg[1]);
     red_init(g);
-    step_radius(g, dt);
+    step_radius(g, dt, g->prm.move_mesh);
     if ((rc = mesh_core(g, dt))) return rc;
     // stage 1: y1 = y^n + dt L(y^n); only the temporal metrics change
     {
@@ -545,7 +561,7 @@ void free_all(esmm_grid *g)
                        &g->q, &g->pg[0], &g->pg[1], &g->pg[2], &g->in_cons, &g->in_J, &g->in_x, &g->in_xdot,
                        &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->rs, &g->X, &g->Xn,
                        &g->dt_dev,
-                       &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev};
+                       &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev, &g->cflb, &g->npart};
     for (double **b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     drop_graph(g);
@@ -554,6 +570,8 @@ void free_all(esmm_grid *g)
     g->q32 = nullptr;
     if (g->iflux) cudaFree(g->iflux);
     if (g->red) cudaFree(g->red);
+    if (g->ds) cudaFree(g->ds);
+    g->ds = nullptr;
     if (g->status) cudaFree(g->status);
     if (g->dpd) cudaFree(g->dpd);
     if (g->pin) cudaFreeHost(g->pin);
@@ -716,6 +734,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->rs, 2 * N}, {&g->X, 2 * N},
         {&g->Xn, 2 * N},
         {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max}, {&g->inflow_dev, 8},
+        {&g->cflb, 6 * N}, {&g->npart, 4 * nb_max},
         {&g->tot_dev, 3 * (size_t)nprob}};
     for (auto &a : al)
         if (cudaMalloc((void **)a.p, a.n * d) != cudaSuccess) { release(g); return ESMM_ERR_CUDA; }
@@ -733,6 +752,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     if ((phys == ESMM_RHD && cudaMalloc((void **)&g->q32, (size_t)NQ32 * P * sizeof(float)) != cudaSuccess) ||
         cudaMalloc(&g->pairs, npairs * d) != cudaSuccess || cudaMalloc(&g->iflux, nflux * d) != cudaSuccess ||
         cudaMalloc((void **)&g->red, (size_t)NRED * nprob * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&g->ds, (size_t)nprob * sizeof(DtSolve)) != cudaSuccess ||
         cudaMalloc((void **)&g->status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&g->pin, std::max<size_t>(16, 3 * (size_t)nprob) * sizeof(double)) != cudaSuccess) {
         release(g);
@@ -1136,22 +1156,32 @@ static __device__ __align__(256) double esmm_static_scratch[STATIC_DOUBLES];
 namespace {
 constexpr int STATIC_MAX_DEVICES = 64;
 std::mutex static_mu;
-double *static_ptr[STATIC_MAX_DEVICES];     // device address per device, set once
+double *static_ptr[STATIC_MAX_DEVICES];     // device address per device
 
-// Device address of the scratch on the current device (set-up on the first
-// call per device, with that device current).
-cudaError_t static_scratch(double **out)
+// Device address of the scratch on the current device.  The first call on a
+// device looks it up with that device current (with lazy module loading this
+// is also when the driver reserves the array).  Later calls look it up again
+// unless the stream is being captured, so an address made stale by a
+// cudaDeviceReset (which reloads the module) is never used outside a capture;
+// inside a capture the address cached by an earlier call is used, and a first
+// call inside a capture is refused.
+cudaError_t static_scratch(cudaStream_t st, double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= STATIC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(static_mu);
-    if (!static_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         double *p = nullptr;
         e = cudaGetSymbolAddress((void **)&p, esmm_static_scratch);
         if (e != cudaSuccess) return e;
         static_ptr[dev] = p;
+    } else if (!static_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = static_ptr[dev];
     return cudaSuccess;
@@ -1168,7 +1198,7 @@ int esmm_mhd_eigen(double gamma, int n, const double *w, const double *dw, doubl
     return mhd_eigen_host(gamma, n, w, dw, lam, R, dlam, dR) ? ESMM_ERR_CUDA : ESMM_OK;
 }
 
-const char *esmm_version(void) { return "esmm 0.3 (2D RHD and RMHD, batched RHD, sm_103a)"; }
+const char *esmm_version(void) { return "esmm 0.4 (2D RHD and RMHD, 3D RMHD, batched RHD, sm_103a)"; }
 
 int esmm_grid_create(esmm_grid **out, int dim, const int n[3], const double lo[3], const double hi[3], int phys,
                      const int bc[3], void *stream)
@@ -1333,8 +1363,8 @@ int esmm_cfl_dt(esmm_grid *g, double *dt)
     if ((rc = ensure_doms(g))) return rc;
     node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     red_init(g);
-    step_radius(g, 0.0);
-    step_dt(g, 0.0);   // slots 4, 5 are zero: the static-mesh step
+    step_radius(g, 0.0, false);
+    step_dt(g, 0.0, false);   // slots 4, 5 are zero: the static-mesh step
     CK(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     *dt = g->pin[0];
@@ -1350,7 +1380,7 @@ int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, 
     if ((rc = ensure_doms(g))) return rc;
     node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     red_init(g);
-    step_radius(g, dt);
+    step_radius(g, dt, g->prm.move_mesh);
     if ((rc = mesh_core(g, dt))) return rc;
     if (xdot && (rc = copy_out(g, xdot, g->xdot, 2 * (size_t)g->Ntot, mem))) return rc;
     CK(cudaMemcpyAsync(g->pin, g->red + 1, sizeof(double), cudaMemcpyDeviceToHost, g->st));
@@ -1668,9 +1698,15 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     for (int k = 0; k < 2; ++k)
         if ((bc[k] != ESMM_PERIODIC && bc[k] != ESMM_OUTFLOW) || !(hi[k] > lo[k])) return ESMM_ERR_ARG;
     if (!(gamma > 1.0 && gamma <= 2.0) || p < 1 || p > PMAX || !(w == 0 || w == 3 || w == 5)) return ESMM_ERR_ARG;
-    double *scratch = nullptr;
-    if (static_scratch(&scratch) != cudaSuccess) return ESMM_ERR_CUDA;
+    // an error already pending on this thread is its owner's: leave it there
+    // and enqueue nothing, so that no error of this call can be confused with it
+    if (cudaPeekAtLastError() != cudaSuccess) return ESMM_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    double *scratch = nullptr;
+    if (static_scratch(st, &scratch) != cudaSuccess) {
+        (void)cudaGetLastError();            // this call's own error (none was pending)
+        return ESMM_ERR_CUDA;
+    }
     ProbDesc D;
     Geom &G = D.g;
     G.nx = nx;
@@ -1700,7 +1736,10 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     double *pairs = q + (long long)NQ * G.P;
     double *iflux = pairs + (long long)2 * PMAX * 4 * G.P;
     int *status = (int *)(scratch + STATIC_PER_NODE * ESMM_STATIC_MAX_PADDED_NODES);
-    if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return ESMM_ERR_CUDA;
+    if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ESMM_ERR_CUDA;
+    }
     auto one = [&](long long count, int bs) {
         LaunchDom L;
         L.pa.pd = nullptr;
@@ -1730,7 +1769,13 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     LaunchDom Lu = one(G.N, BS);
     k_update<double><<<Lu.nblk, Lu.bs, 0, st>>>(Lu.pa, iflux, dcons, dJ, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                 nullptr, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr);
-    return cudaGetLastError() == cudaSuccess ? ESMM_OK : ESMM_ERR_CUDA;
+    // nothing was pending on entry, so an error now is this call's own launch
+    // error: consume it and report it
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ESMM_ERR_CUDA;
+    }
+    return ESMM_OK;
 }
 
 int esmm_profile(esmm_grid *g, int mask)

@@ -232,7 +232,7 @@ __global__ void k_update(ProbArg pa, const R *__restrict__ fl, double *__restric
 // the spectral radius of k_cfl in FP32 (mixed form): with p = rho/beta,
 // c^2 = Gamma p / (rho h) = Gamma / (beta + Gamma/(Gamma-1))
 __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const float *__restrict__ q32,
-                                        const double *__restrict__ J, unsigned long long *red)
+                                        const double *__restrict__ J, unsigned long long *red, double *cflb)
 {
     ProbDesc D;
     long long lb;
@@ -241,6 +241,7 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
     long long id = lb * blockDim.x + threadIdx.x;
     q32 += (long long)NQ32 * D.op;
     J += D.on;
+    if (cflb) cflb += 6 * D.on;
     double r[2] = {0.0, 0.0};
     if (id < g.N) {
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
@@ -259,6 +260,10 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
             float disc = sqrtf(fmaxf((1.0f - v2) * (1.0f - v2 * c2 - vn * vn * (1.0f - c2)), 0.0f));
             float lm = (vn * (1.0f - c2) - cs * disc) * iden, lp = (vn * (1.0f - c2) + cs * disc) * iden;
             r[k] = (double)(Lk * fmaxf(fabsf(lm), fabsf(lp)) * iJ);
+            if (cflb) {
+                cflb[(2 + k) * g.N + id] = (double)(Lk * lm * iJ);
+                cflb[(4 + k) * g.N + id] = (double)(Lk * lp * iJ);
+            }
         }
     }
     for (int k = 0; k < 2; ++k) {
@@ -269,12 +274,14 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
 
 
 // spectral radius rho_k = L_k max |lambda_+-| / J at every node (eq. cfl,
-// static mesh), reduced to a per-problem maximum per direction
+// static mesh), reduced to a per-problem maximum per direction; with cflb
+// (the moving-mesh step) also the speed bounds L_k lambda_-/J and
+// L_k lambda_+/J of every node into its rows 2 + k and 4 + k
 __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
-                      unsigned long long *red, const float *__restrict__ q32)
+                      unsigned long long *red, const float *__restrict__ q32, double *__restrict__ cflb)
 {
     if (q32) {   // the mixed form: the same speeds in FP32 from the FP32 node copies
-        cfl_f32(pa, (float)gam, q32, J, red);
+        cfl_f32(pa, (float)gam, q32, J, red, cflb);
         return;
     }
     ProbDesc D;
@@ -284,6 +291,7 @@ __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, cons
     long long id = lb * blockDim.x + threadIdx.x;
     q += (long long)NQ * D.op;
     J += D.on;
+    if (cflb) cflb += 6 * D.on;
     double r[2] = {0.0, 0.0};
     if (id < g.N) {
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
@@ -303,6 +311,10 @@ __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, cons
             double iden = __drcp_rn(1.0 - v2 * c2);
             double lm = (vn * (1.0 - c2) - cs * disc) * iden, lp = (vn * (1.0 - c2) + cs * disc) * iden;
             r[k] = Lk * fmax(fabs(lm), fabs(lp)) * iJ;
+            if (cflb) {
+                cflb[(2 + k) * g.N + id] = Lk * lm * iJ;
+                cflb[(4 + k) * g.N + id] = Lk * lp * iJ;
+            }
         }
     }
     for (int k = 0; k < 2; ++k) {
@@ -325,22 +337,51 @@ __global__ void k_red_init(int nprob, unsigned long long *red)
     red[NRED * b + 7] = 0ull;
 }
 
-// Step of each problem (eq. cfl with the mesh velocity in the spectral
-// radius): the mesh limiter Delta tau is capped so that the displacement's
-// Courant number C_m = Delta tau sum_k max |d.(J xi_k,x)|/J stays <= CFL/2,
-// then dt = (CFL - C_m) / sum_k max rho_k (static radius), or the given step.
-// The capped Delta tau goes back to slot 1.  Without mesh motion C_m = 0.
-__global__ void k_dt(int nprob, double cfl, double dt_fixed, unsigned long long *red, double *dt_dev)
+// Set-up of each problem's step (eq. cfl with the mesh velocity in the
+// spectral radius, esmm_reduce.cuh dt_setup): slots 4, 5 hold A_k = max_i
+// |a_{k,i}|, slots 2, 3 the static radius per direction, slot 1 the limiter
+// Delta tau (written back, scaled where C_m >= CFL).  Without mesh motion
+// C_m = 0 and dt = CFL / sum_k max rho_k.
+__global__ void k_dt(int nprob, double cfl, double dt_fixed, unsigned long long *red, DtSolve *ds, double *dt_dev)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nprob) return;
     unsigned long long *r = red + (long long)NRED * b;
-    double C1 = bits_to_double(r[4]) + bits_to_double(r[5]);
     double tau = bits_to_double(r[1]);
-    if (C1 > 0.0 && tau * C1 > 0.5 * cfl) tau = 0.5 * cfl / C1;
+    dt_setup(ds + b, cfl, dt_fixed, bits_to_double(r[4]) + bits_to_double(r[5]),
+             bits_to_double(r[2]) + bits_to_double(r[3]), &tau, dt_dev + b);
     r[1] = (unsigned long long)__double_as_longlong(tau);
-    dt_dev[b] = dt_fixed > 0.0 ? dt_fixed
-                               : cfl / (bits_to_double(r[2]) + bits_to_double(r[3])) * (1.0 - tau * C1 / cfl);
+}
+
+// One Newton evaluation of the step solve (esmm_reduce.cuh) over the nodes
+// of every problem still solving: cflb rows 0, 1 hold a_{k,i}, rows 2..5 the
+// speed bounds (per problem at 6 D.on).  part: [blocks][2][2].
+__global__ void k_dt_newton(ProbArg pa, double cfl, const double *__restrict__ cflb,
+                            const unsigned long long *red, DtSolve *ds, double *part, double *dt_dev)
+{
+    ProbDesc D;
+    long long lb;
+    int b = locate(pa, D, lb);
+    const Geom &g = D.g;
+    DtSolve *S = ds + b;
+    __shared__ double t_sh, tau_sh;
+    __shared__ int skip;
+    if (threadIdx.x == 0) {
+        skip = S->done;
+        t_sh = S->t;
+        tau_sh = bits_to_double(red[(long long)NRED * b + 1]);
+    }
+    __syncthreads();
+    if (skip) return;
+    long long id = lb * blockDim.x + threadIdx.x;
+    cflb += 6 * D.on;
+    double v[2] = {-1.0, -1.0}, sl[2] = {0.0, 0.0};
+    if (id < g.N)
+        for (int k = 0; k < 2; ++k)
+            cfl_line(t_sh, tau_sh * cflb[k * g.N + id], cflb[(2 + k) * g.N + id], cflb[(4 + k) * g.N + id], v[k],
+                     sl[k]);
+    const long long nb = (g.N + blockDim.x - 1) / blockDim.x;
+    dt_newton_block<2>(S, v, sl, blockIdx.x, (long long)blockIdx.x - lb, nb, part, cfl, dt_dev + b);
 }
 
 __global__ void k_time(int nprob, const double *dt_dev, double *t_dev)
@@ -633,12 +674,14 @@ __global__ void k_mesh_sweep(ProbArg pa, const double *__restrict__ cw, const do
 
 // movement limiter: Delta tau = min over nodes and directions of half the
 // neighbour spacing over the displacement toward it, clipped to [0, 1]; and
-// the displacement's Courant number max |d.(J xi_k,x)|/J per direction (the
-// node metrics of x^n in q, J of the state)
+// the displacement's Courant terms a_k = d.(J xi_k,x)/J per node (into cflb
+// rows 0, 1) and their maximum modulus per direction (the node metrics of x^n
+// in q, J of the state)
 // (Dd: the displacement x^[mu] - x^n of k_mesh_sweeps)
 template <typename T>
 __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const T *__restrict__ Dd,
-                           const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red)
+                           const double *__restrict__ q, const double *__restrict__ J, unsigned long long *red,
+                           double *__restrict__ cflb)
 {
     ProbDesc D;
     long long lb;
@@ -671,8 +714,11 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const T *__
         tau = fmax(tau, 0.0);
         long long c = pidx(g, i, j);
         double iJ = __drcp_rn(J[id]);
-        for (int k = 0; k < 2; ++k)
-            cm[k] = fabs(dd[0] * q[(Q_M00 + 2 * k) * g.P + c] + dd[1] * q[(Q_M01 + 2 * k) * g.P + c]) * iJ;
+        for (int k = 0; k < 2; ++k) {
+            const double ak = (dd[0] * q[(Q_M00 + 2 * k) * g.P + c] + dd[1] * q[(Q_M01 + 2 * k) * g.P + c]) * iJ;
+            cm[k] = fabs(ak);
+            cflb[6 * D.on + k * g.N + id] = ak;
+        }
     }
     double m = block_reduce<1>(tau);
     if (threadIdx.x == 0) atomic_min_nonneg(red + (long long)NRED * b + 1, m);
@@ -694,7 +740,8 @@ __global__ void k_mesh_xdot(ProbArg pa, const T *__restrict__ Dd, const unsigned
     const Geom &g = D.g;
     long long id = lb * blockDim.x + threadIdx.x;
     __shared__ double s;
-    if (threadIdx.x == 0) s = bits_to_double(red[(long long)NRED * b + 1]) / dt_dev[b];
+    // a step of 0 (a NaN spectral radius) leaves the mesh where it is
+    if (threadIdx.x == 0) s = dt_dev[b] > 0.0 ? bits_to_double(red[(long long)NRED * b + 1]) / dt_dev[b] : 0.0;
     __syncthreads();
     if (id >= 2 * g.N) return;
     long long o = 2 * D.on + id;

@@ -68,7 +68,7 @@ void launch_update_mhd_f32(const LaunchDom &L, const double *q, const void *fl, 
                            const double *xs, const double *xdot, double A, double B, const double *dt_dev,
                            double *co, double *Jo, double *xo, cudaStream_t st);
 void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,
-                    bool f32, cudaStream_t st);
+                    bool f32, double *cflb, cudaStream_t st);
 void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, const double *x, double *cons,
                      double *J, int *status, cudaStream_t st);
 void launch_prim_out_mhd(const LaunchDom &L, double gam, const double *cons, const double *J, double *prim,

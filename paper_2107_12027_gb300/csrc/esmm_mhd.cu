@@ -29,9 +29,11 @@ __global__ void k_prim_out_mhd(ProbArg pa, double gam, const double *__restrict_
 // with the speeds from the eigen-system in the working precision R (FP32 in
 // the mixed form: the step carries ~1e-6 relative rounding, harmless for a
 // stability bound).
+// With cflb (the moving-mesh step) also the speed bounds L_k lambda_min/J and
+// L_k lambda_max/J of every node into its rows 2 + k and 4 + k.
 template <typename R>
 __global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
-                          unsigned long long *red)
+                          unsigned long long *red, double *__restrict__ cflb)
 {
     ProbDesc D;
     long long lb;
@@ -55,9 +57,17 @@ __global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, 
                        (R)w[4], (R)(nx * w[5] + ny * w[6]), (R)(-ny * w[5] + nx * w[6]), (R)w[7]};
             R lam[8], Rm[8][8];
             eigen_mhd<R>(gam, wr, lam, Rm, false);
-            double a = 0.0;
-            for (int m = 0; m < 8; ++m) a = fmax(a, fabs((double)lam[m]));
+            double a = 0.0, lo = (double)lam[0], hi = (double)lam[0];
+            for (int m = 0; m < 8; ++m) {
+                a = fmax(a, fabs((double)lam[m]));
+                lo = fmin(lo, (double)lam[m]);
+                hi = fmax(hi, (double)lam[m]);
+            }
             r[k] = Lk * a * iJ;
+            if (cflb) {
+                cflb[6 * D.on + (2 + k) * g.N + id] = Lk * lo * iJ;
+                cflb[6 * D.on + (4 + k) * g.N + id] = Lk * hi * iJ;
+            }
         }
     }
     for (int k = 0; k < 2; ++k) {
@@ -95,10 +105,10 @@ void launch_update_mhd(const LaunchDom &L, const double *q, const void *fl, doub
 }
 
 void launch_cfl_mhd(const LaunchDom &L, double gam, const double *q, const double *J, unsigned long long *red,
-                    bool f32, cudaStream_t st)
+                    bool f32, double *cflb, cudaStream_t st)
 {
-    if (f32) k_cfl_mhd<float><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red);
-    else k_cfl_mhd<double><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red);
+    if (f32) k_cfl_mhd<float><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red, cflb);
+    else k_cfl_mhd<double><<<L.nblk, L.bs, 0, st>>>(L.pa, gam, q, J, red, cflb);
 }
 
 void launch_init_mhd(const LaunchDom &L, int p, double gam, const double *prim, const double *x, double *cons,

@@ -25,12 +25,15 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Max and min of non-negative values on their bit patterns (which order like
-// the values), on the integer pipes rather than the FP64 one.  A NaN is
-// ignored (as fmax/fmin would), a negative value counts as 0.
+// the values), on the integer pipes rather than the FP64 one.  A negative
+// value counts as 0.  A NaN counts as +infinity in a max, so that a node
+// whose recovery failed (NaN speeds) cannot drop out of the CFL spectral
+// radius: the step becomes 0 instead of one sized by the healthy nodes.  In
+// a min a NaN is ignored.
 __device__ __forceinline__ unsigned long long ord_bits(double v, bool for_min)
 {
     unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    if ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) return for_min ? 0x7ff0000000000000ull : 0ull;
+    if ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) return 0x7ff0000000000000ull;
     return (b >> 63) ? 0ull : b;
 }
 __device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long v)
@@ -95,6 +98,165 @@ __device__ __forceinline__ void atomic_min_nonneg(unsigned long long *a, double 
     atomicMin(a, (unsigned long long)__double_as_longlong(v));
 }
 __device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// ---------------------------------------------------------------------------
+// eq. cfl with the mesh velocity in the spectral radius, solved for dt.
+//
+// With the step's displacement d = x^[mu] - x^n, a_{k,i} = d_i.(J xi_k,x)_i / J_i
+// and the speed bounds bmin, bmax = L_k lambda_min / J, L_k lambda_max / J of
+// every node, eq. cfl reads g(dt) = CFL with
+//   g(t) = sum_k max_i max(t bmax_{k,i} - tau a_{k,i}, tau a_{k,i} - t bmin_{k,i}),
+// the left side dt sum_k max_i rho_{k,i} with rho_{k,i} = max_m |(J xi_k)_t +
+// L_k lambda_m| / J_i and (J xi_k)_t = -tau d.(J xi_k,x)/dt.  g is convex and
+// piecewise linear; Newton's method from the right end (CFL + C_m)/S steps to
+// the root of the line active at each iterate (the smaller slope on a tie),
+// which a convex g lies above, so the iterates fall monotonically onto the
+// root's piece.  The solve stops once g <= CFL (1 + 1e-14); after DT_NEWTON
+// evaluations without that, or with a slope <= 0, the safe lower bound
+// (CFL - C_m)/S is used.  k_dt sets the state up; every Newton launch
+// evaluates g at the current iterate over all nodes of a problem, and the
+// last of the problem's blocks to finish reduces their partial results
+// (in any order: the (value, slope) maximum below does not depend on it)
+// and advances the iterate.
+constexpr int DT_NEWTON = 8;
+
+struct DtSolve {
+    double t, t_safe;    // current iterate, the fallback
+    int iter, done;      // evaluations so far; 1 when dt_dev holds the step
+    unsigned count;      // blocks of the current launch that have finished
+    int pad_;
+};
+
+// the line of one node at t that attains its max(t bmax - ta, ta - t bmin),
+// as (value, slope); the smaller slope where the two lines tie
+__device__ __forceinline__ void cfl_line(double t, double ta, double bmin, double bmax, double &v, double &s)
+{
+    const double up = t * bmax - ta, dn = ta - t * bmin;
+    v = up > dn ? up : dn;
+    s = up > dn ? bmax : (dn > up ? -bmin : fmin(bmax, -bmin));
+}
+
+// the larger value, and on equal values the smaller slope (a NaN value never
+// wins): a total order, so reductions in any order agree
+__device__ __forceinline__ void vs_take(double &v, double &s, double v2, double s2)
+{
+    if (v2 > v || (v2 == v && s2 < s)) {
+        v = v2;
+        s = s2;
+    }
+}
+
+// block-wide (value, slope) maximum of NDIR pairs; valid in thread 0
+template <int NDIR>
+__device__ void block_vs_max(double (&v)[NDIR], double (&s)[NDIR])
+{
+    __shared__ double shv[32][NDIR], shs[32][NDIR];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NDIR; ++k)
+        for (int o = 16; o > 0; o >>= 1)
+            vs_take(v[k], s[k], __shfl_xor_sync(0xffffffffu, v[k], o), __shfl_xor_sync(0xffffffffu, s[k], o));
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NDIR; ++k) {
+            shv[wid][k] = v[k];
+            shs[wid][k] = s[k];
+        }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NDIR; ++k) {
+            v[k] = lane < nw ? shv[lane][k] : -1.0;
+            s[k] = lane < nw ? shs[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1)
+                vs_take(v[k], s[k], __shfl_xor_sync(0xffffffffu, v[k], o), __shfl_xor_sync(0xffffffffu, s[k], o));
+        }
+    }
+    __syncthreads();
+}
+
+// The block's part of one Newton evaluation: (v, s) are this thread's values
+// (-1, 0 where it has no node).  gblock is the block's index in the launch,
+// [first, first + nb) the blocks of its problem, part [blocks][NDIR][2] the
+// partial results.  The last block of the problem to finish advances S and
+// writes the step to *dt_out when the solve ends.  Every thread of the block
+// must call it.
+template <int NDIR>
+__device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR], long long gblock, long long first,
+                                long long nb, double *part, double cfl, double *dt_out)
+{
+    __shared__ int last;
+    block_vs_max<NDIR>(v, s);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NDIR; ++k) {
+            part[(gblock * NDIR + k) * 2] = v[k];
+            part[(gblock * NDIR + k) * 2 + 1] = s[k];
+        }
+        __threadfence();
+        last = atomicAdd(&S->count, 1u) == (unsigned)(nb - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NDIR; ++k) {
+        v[k] = -1.0;
+        s[k] = 0.0;
+    }
+    for (long long q = threadIdx.x; q < nb; q += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NDIR; ++k)
+            vs_take(v[k], s[k], __ldcg(part + ((first + q) * NDIR + k) * 2),
+                    __ldcg(part + ((first + q) * NDIR + k) * 2 + 1));
+    block_vs_max<NDIR>(v, s);
+    if (threadIdx.x == 0) {
+        double g = 0.0, slope = 0.0;
+#pragma unroll
+        for (int k = 0; k < NDIR; ++k) {
+            g += v[k];
+            slope += s[k];
+        }
+        S->count = 0u;
+        if (g <= cfl * (1.0 + 1e-14)) {
+            *dt_out = S->t;
+            S->done = 1;
+        } else if (!(slope > 0.0) || S->iter + 1 >= DT_NEWTON) {
+            *dt_out = S->t_safe;
+            S->done = 1;
+        } else {
+            S->t -= (g - cfl) / slope;
+            S->iter += 1;
+        }
+    }
+}
+
+// Set-up of the solve for one problem (one thread): the displacement's
+// Courant number C_m = tau sum_k A_k (A_k = max_i |a_{k,i}|), Delta tau scaled
+// so that C_m = CFL/2 where C_m >= CFL (no step satisfies eq. cfl there; *tau
+// is updated), S = sum_k S_k the static radius.  A given dt > 0, or C_m = 0,
+// ends the solve at once.
+__device__ __forceinline__ void dt_setup(DtSolve *S, double cfl, double dt_fixed, double C1, double Ssum,
+                                         double *tau, double *dt_out)
+{
+    double C = *tau * C1;
+    if (C >= cfl) {
+        *tau = *tau * (0.5 * cfl / C);
+        C = 0.5 * cfl;
+    }
+    S->count = 0u;
+    S->iter = 0;
+    S->done = 1;
+    if (dt_fixed > 0.0) {
+        *dt_out = dt_fixed;
+    } else if (!(C > 0.0)) {
+        *dt_out = cfl / Ssum;
+    } else {
+        S->t = (cfl + C) / Ssum;
+        S->t_safe = (cfl - C) / Ssum;
+        S->done = 0;
+    }
+}
 
 // per-problem reduction slots: [0] max |grad sigma|, [1] Delta tau (min),
 // [2], [3] max spectral radius per direction, [4], [5] max mesh Courant

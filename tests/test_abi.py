@@ -48,3 +48,26 @@ def test_named_schemes_host_logic():
     assert esmm._apply_scheme("UM-O5", 2, 3, prm) == (3, 5) and prm == {"move_mesh": 1}
     prm = {}
     assert esmm._apply_scheme(None, 2, 3, prm) == (2, 3) and prm == {}
+
+
+# the calls that define a step of the method, each of which must cite the
+# passage that defines it (a section, equation, proposition or theorem)
+CITED_CALLS = ("esmm_grid_create", "esmm_set_eos", "esmm_set_order", "esmm_set_params", "esmm_state_set",
+               "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step", "esmm_rk_step_given",
+               "esmm_set_inflow", "esmm_totals", "esmm_mhd_eigen")
+
+
+def _comment_before(src, name):
+    """The comment block documenting a declaration: the last /* ... */ that
+    ends before it, across any declarations that share it."""
+    at = src.index("int %s(" % name)
+    end = src.rindex("*/", 0, at)
+    start = src.rindex("/*", 0, end)
+    return src[start:end]
+
+
+def test_method_calls_cite_their_defining_passage():
+    src = open(os.path.join(ROOT, "include", "esmm.h")).read()
+    cite = re.compile(r"\b(Sec\.|eq\.|eqs\.|Prop\.|Thm\.)\s*[A-Za-z0-9_]")
+    for name in CITED_CALLS:
+        assert cite.search(_comment_before(src, name)), name

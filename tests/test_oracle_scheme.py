@@ -159,19 +159,15 @@ def test_mesh_limiter_and_no_tangling():
     assert J1.min() > 0
 
 
-def test_step_satisfies_cfl_with_mesh_velocity():
-    # eq. cfl: dt sum_k max_i rho_{k,i} <= CFL with rho the spectral radius of
-    # d(F_k)/d(JU) including the temporal metric J xi_k,t = -xdot . (J xi_k,x);
-    # the mesh part of it stays below CFL/2
-    n = 24
-    x, prim = wl.riemann_config(n)
-    cfg = oracle.make_cfg(n, n, bc=(oracle.OUTFLOW, oracle.OUTFLOW), period=(2.0, 2.0), alpha=1200.0)
-    cons, J = oracle.init_state(cfg, prim, x)
-    xdot, tau, dt = oracle.mesh(cfg, cons, J, x)
+def _radius_with_mesh_velocity(cfg, cons, J, x, xdot):
+    """max_i rho_{k,i} per direction, rho the spectral radius of d(F_k)/d(JU)
+    with the temporal metric J xi_k,t = -xdot . (J xi_k,x), from the
+    eigenvalues of every node; and the mesh part max |J xi_k,t| / J."""
+    n = cfg.nx
     m, _ = oracle.metrics(cfg, x)
     pr, _ = oracle.state_prim(cfg, cons, J)
     rmax, cmesh = [0.0, 0.0], [0.0, 0.0]
-    for j in range(n):
+    for j in range(cfg.ny):
         for i in range(n):
             for k in range(2):
                 mx, my = m[2 * k, j, i], m[2 * k + 1, j, i]
@@ -182,13 +178,59 @@ def test_step_satisfies_cfl_with_mesh_velocity():
                 lam, _ = oracle.eigen(cfg.gamma, wr)
                 jt = -(xdot[0, j, i] * mx + xdot[1, j, i] * my)
                 rmax[k] = max(rmax[k], np.abs(jt + L * lam).max() / J[j, i])
-                cmesh[k] = max(cmesh[k], abs(jt) * dt / J[j, i])
+                cmesh[k] = max(cmesh[k], abs(jt) / J[j, i])
+    return rmax, cmesh
+
+
+@pytest.mark.parametrize("n,alpha", [(24, 1200.0), (20, 5.0)])
+def test_step_satisfies_cfl_with_mesh_velocity(n, alpha):
+    # eq. cfl with the mesh velocity in the spectral radius, evaluated
+    # directly: dt sum_k max_i rho_{k,i} = CFL, rho from the eigenvalues of
+    # every node with the temporal metric of xdot = tau d / dt.  alpha = 1200
+    # moves the mesh by more than a Courant number (the limiter then scaled
+    # to C_m = CFL/2); alpha = 5 moves it gently (the limiter's own value).
+    x, prim = wl.riemann_config(n)
+    cfg = oracle.make_cfg(n, n, bc=(oracle.OUTFLOW, oracle.OUTFLOW), period=(2.0, 2.0), alpha=alpha)
+    cons, J = oracle.init_state(cfg, prim, x)
+    xdot, tau, dt = oracle.mesh(cfg, cons, J, x)
+    rmax, cmesh = _radius_with_mesh_velocity(cfg, cons, J, x, xdot)
     assert tau > 0 and np.abs(xdot).max() > 0
-    assert dt * sum(rmax) <= cfg.cfl * (1 + 1e-12)
-    assert sum(cmesh) <= 0.5 * cfg.cfl * (1 + 1e-12)
+    assert abs(dt * sum(rmax) / cfg.cfl - 1.0) < 1e-12
+    assert dt * sum(cmesh) < cfg.cfl
     # with a static mesh the step is the static-radius CFL step
     cfg0 = oracle.make_cfg(n, n, bc=(oracle.OUTFLOW, oracle.OUTFLOW), period=(2.0, 2.0), move_mesh=0)
     assert oracle.mesh(cfg0, cons, J, x)[2] == oracle.cfl_dt(cfg0, cons, J, x)
+
+
+def test_cfl_solve_against_brute_force():
+    # random per-node terms, with the displacement's Courant number below and
+    # above CFL: the step is the root of g(t) = sum_k max_i max_m |t b_m - tau
+    # a| (every m between bmin and bmax, sampled), found by bisection
+    r = wl.rng(77)
+    cfl = 0.4
+    for trial in range(40):
+        N = int(r.integers(1, 60))
+        a = r.normal(0.0, 0.3, (2, N)) * r.uniform(0, 1)
+        b0 = r.normal(0.0, 1.0, (2, N))
+        b1 = b0 + np.abs(r.normal(0.0, 1.0, (2, N)))
+        tau = r.uniform(0.05, 1.0)
+        dt, tau_used, it = oracle.cfl_solve(a, b0, b1, cfl, tau)
+        C = tau * np.abs(a).max(axis=1).sum()
+        if C >= cfl:
+            assert abs(tau_used * np.abs(a).max(axis=1).sum() - 0.5 * cfl) < 1e-15
+        else:
+            assert tau_used == tau
+        lam = np.linspace(0.0, 1.0, 11)[:, None, None]
+        bm = b0[None] + lam * (b1 - b0)[None]          # speeds between the bounds
+
+        def g(t):
+            return np.abs(t * bm - tau_used * a[None]).max(axis=(0, 2)).sum()
+        lo, hi = 0.0, 10.0 / np.maximum(np.abs(b0), np.abs(b1)).max(axis=1).sum()
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if g(mid) <= cfl else (lo, mid)
+        assert it >= 0, trial
+        assert abs(dt / lo - 1.0) < 1e-12, (trial, dt, lo)
 
 
 # ------------------------------------------------------------------- RK steps
