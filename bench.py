@@ -10,8 +10,10 @@ reduction, mesh redistribution and three RK stages.
 
 Metric: cell-updates/s per RK stage = nodes * 3 * steps / device time.  Every
 timed step starts with the L2 cache flushed (a 256 MB write outside the timed
-events).  Under torchrun each rank runs its own independent problem (weak
-scaling, no data-path collective).
+events).  Under torchrun the ranks share one problem: N such 400 x 400
+problems stacked into one 400 x 400N grid, slab-decomposed along x_2 (one
+400-row slab per rank, weak scaling), with the step's reductions and halo
+exchanges between the ranks.
 
 ``--impl reference`` times the FP64 CPU oracle (the paper's method restated
 plainly in C) on the host cores over a bounded sample of the same workload.
@@ -46,30 +48,31 @@ N_SIDE = 400
 WORKLOAD = ("2D RHD four-quadrant Riemann problem, 400x400 nodes on [-1,1]^2, outflow, Gamma=5/3, seeded states "
             "(rho in [0.1,1], |v|<=0.9, p in [0.01,1]), adaptive moving mesh (sigma=ln rho, alpha=1200, 4 filter "
             "passes, 10 Jacobi sweeps), 4th-order EC flux (p=2) + WENO5 dissipation, SSP-RK3, CFL 0.4")
-# FP64 operations executed per interface by the FP64 interface kernel (p=2,
-# WENO5), from the ncu SASS counters dadd + dmul + 2 dfma of one capture
-# (profiles/iface_f64_riemann400.md); FLOP = add, mul, or half an FMA.
+# Flops per interface of the interface kernels are EXECUTED operations, from
+# the ncu SASS counters of one capture of each kernel: dadd + dmul + 2 dfma
+# (FP64) or fadd + fmul + 2 ffma (FP32), i.e. an add, a mul, or half an FMA,
+# including the FP64 instructions inside division, square-root and log
+# sequences.  The FP64 interface kernel (p = 2, WENO5) on the 400^2 Riemann
+# workload executes 1,396 per interface.
 FLOPS_PER_IFACE_F64 = 1396
-# Derived FP64 peak of GB300: 152 SMs x 4 FP64 flop/clk/SM (1.25 TFLOP/s at
-# the 2070 MHz maximum SM clock).
+# Unit counts for the derived peaks, reported beside the measured ones:
+# 4 FP64 flop/clk/SM and 256 FP32 flop/clk/SM at the 2070 MHz maximum clock.
 FP64_FLOP_PER_CLK_SM = 4
-# FP32: 128 FMA lanes per SM, 256 flop/clk/SM (80.5 TFLOP/s at 2070 MHz); the
-# peak of the mixed form's interface kernel.
 FP32_FLOP_PER_CLK_SM = 256
 # DRAM bytes (read + write) of one interface-kernel launch in that capture;
 # None whenever the kernel has changed since the counters were taken.
 TRAFFIC_IFACE_F64 = 23.48e6
-# The mixed form's interface kernel (profiles/flux_f32_riemann400.md): FP32
-# flops per interface (fadd + fmul + 2 ffma) and DRAM bytes per launch.
+# The mixed form's interface kernel on the same workload: FP32 flops per
+# interface and DRAM bytes per launch.
 FLOPS_PER_IFACE_F32 = 1259
 TRAFFIC_IFACE_F32 = 13.08e6
-# The same for the RMHD interface kernels at p = 2, WENO5 (profiles/
-# iface_mhd_ops_rotor512_blast64.md): the FP64 2D kernel on the 512^2 rotor
-# (11,042 FP64 flops per interface; 1.021 GB of DRAM traffic per launch, the
-# eigen-system's per-thread stack), its FP32 instance (10,832 FP32 flops per
-# interface besides 98 FP64 ones; 0.479 GB), and the 3D kernel (16,409 FP64
-# flops per interface; 1.210 GB at 64^3, scaled by the 7.94x interfaces of
-# a 128^3 launch -- the stack traffic grows with the threads).
+# The same for the RMHD interface kernels at p = 2, WENO5: the FP64 2D kernel
+# on the 512^2 rotor (11,042 FP64 flops per interface; 1.021 GB of DRAM
+# traffic per launch, the eigen-system's per-thread stack), its FP32 instance
+# (10,832 FP32 flops per interface besides 98 FP64 ones; 0.479 GB), and the 3D
+# kernel (16,409 FP64 flops per interface; 1.210 GB at 64^3, scaled by the
+# 7.94x interfaces of a 128^3 launch -- the stack traffic grows with the
+# threads).
 FLOPS_PER_IFACE_MHD2 = 11042
 TRAFFIC_IFACE_MHD2 = 1.021e9
 FLOPS_PER_IFACE_MHD2_F32 = 10832
@@ -87,6 +90,45 @@ SM_MAX_MHZ = 2070.0
 #   2D RMHD (m = 8): (176 + 248 + 248)/3 + 40/3 = 237.3 B
 #   3D RMHD (m = 8): (192 + 264 + 264)/3 + 56/3 = 258.7 B
 HBM_BYTES_PER_NODE_STAGE = {"rhd2": 152.0, "rmhd2": 237.3, "rmhd3": 258.7}
+# The untapered 512^2 rotor loses admissibility in its first step at CFL 0.4
+# on a static mesh and with the moving mesh under eq. cfl, in the oracle as
+# on the GPU (the scheme has no positivity limiter); at CFL 0.3 the first
+# step stays admissible.  Every timed rotor step starts from the initial
+# state, so the workload runs at CFL 0.3.
+ROTOR_CFL = 0.3
+
+
+_PEAKS = {}
+
+
+def alu_peak(precision):
+    """(TFLOP/s, source) of the FP64 (precision "fp64") or FP32 pipe:
+    measured once per process by the library's FMA-throughput kernel
+    (esmm_fma_peak, ~1 s), else derived from the unit counts."""
+    from paper_2107_12027_gb300 import esmm
+    if precision not in _PEAKS:
+        try:
+            fl, _ = esmm.fma_peak(esmm.FP64 if precision == "fp64" else esmm.MIXED, 1.0)
+            _PEAKS[precision] = (fl / 1e12, "measured: esmm_fma_peak (independent FMA chains, 8x256 threads per SM, "
+                                            "CUDA events, ~1 s)")
+        except Exception as e:   # noqa: BLE001 -- report the derived peak and why
+            per = FP64_FLOP_PER_CLK_SM if precision == "fp64" else FP32_FLOP_PER_CLK_SM
+            _PEAKS[precision] = (N_SM * per * SM_MAX_MHZ * 1e6 / 1e12, "derived (measurement failed: %s)" % e)
+    return _PEAKS[precision]
+
+
+def cpu_model():
+    """The host CPU's model name and its number of hardware threads."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return name or "unknown", os.cpu_count() or 1
 
 
 def hbm_peak_gbs():
@@ -162,13 +204,27 @@ def job_time_ms(total_ms, world, dist, device):
 
 def job_rate(nodes_per_rank, steps, world, job_ms):
     """Whole-job cell-updates per second per RK stage: every rank advances
-    its own problem of nodes_per_rank nodes (weak scaling)."""
+    nodes_per_rank nodes of its own (its slab's own rows; weak scaling)."""
     return world * nodes_per_rank * 3 * steps / (job_ms * 1e-3)
 
 
 def workload(n, rank=0):
     from paper_2107_12027_gb300 import workloads as wl
     return wl.riemann_config(n, offset=1 + rank)
+
+
+def stacked_workload(n, world):
+    """The sharded workload of a multi-rank run: `world` four-quadrant
+    Riemann problems of n x n nodes stacked along x_2 into one grid of
+    n x (n world) nodes on [-1,1] x [-1, 2 world - 1] (band k holds the
+    seeded states of rank k's single-GPU problem, split at its centre)."""
+    from paper_2107_12027_gb300 import workloads as wl
+    x = wl.uniform_mesh(n, n * world, (-1.0, -1.0), (1.0, 2.0 * world - 1.0), (False, False))
+    prim = np.empty((4, n * world, n))
+    for k in range(world):
+        band = slice(k * n, (k + 1) * n)
+        prim[:, band] = wl.quadrant_riemann(x[:, band], wl.quadrant_states(wl.rng(1 + k)), split=(0.0, 2.0 * k))
+    return x, np.ascontiguousarray(prim)
 
 
 def grid_params(form):
@@ -224,11 +280,12 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample_rate(n, budget_s, nsteps=1, rows=None):
+def oracle_sample_rate(n, budget_s, nsteps=1, rows=None, threads=0):
     """Time the FP64 oracle's rk_step on a 400-wide strip of the workload
-    (rows chosen so the run takes about budget_s); returns (cell-updates/s,
-    description)."""
+    (rows chosen so the run takes about budget_s) on `threads` host threads
+    (0: all); returns (cell-updates/s, description, rows, threads used)."""
     import oracle
+    used = oracle.set_threads(threads)
     x, prim = workload(n)
     if rows is None:
         r0 = 16
@@ -251,9 +308,19 @@ def oracle_sample_rate(n, budget_s, nsteps=1, rows=None):
         cons, J, xs, _ = oracle.rk_step(cfg, cons, J, xs)
     el = time.perf_counter() - t
     rate = n * rows * 3 * nsteps / el
-    desc = ("%d rk_step(s) of the FP64 C oracle (single thread) on the central %dx%d strip of the %dx%d workload"
-            % (nsteps, n, rows, n, n))
-    return rate, desc, rows
+    desc = ("%d rk_step(s) of the FP64 C oracle (%d host thread%s, OpenMP over nodes and interfaces) on the "
+            "central %dx%d strip of the %dx%d workload" % (nsteps, used, "" if used == 1 else "s", n, rows, n, n))
+    return rate, desc, rows, used
+
+
+def cpu_baseline(n, budget_s):
+    """The oracle on all host threads (the reported baseline) and on one."""
+    model, nthreads = cpu_model()
+    rate, desc, _, used = oracle_sample_rate(n, budget_s, 1, threads=0)
+    rate1, desc1, _, _ = oracle_sample_rate(n, budget_s, 1, threads=1)
+    return {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc, "cpu_model": model,
+            "host_threads": nthreads,
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1, "sample": desc1}}
 
 
 def run_reference(args):
@@ -262,10 +329,11 @@ def run_reference(args):
         return
     K, W = args.steps, args.warmup
     budget = 150.0 / max(1, K + W)      # whole run in about 2.5 minutes
-    _, _, rows = oracle_sample_rate(args.n, budget, 1)
+    model, _ = cpu_model()
+    _, _, rows, used = oracle_sample_rate(args.n, budget, 1)
     rates = []
     for s in range(W + K):
-        rate, desc, _ = oracle_sample_rate(args.n, budget, 1, rows=rows)
+        rate, desc, _, used = oracle_sample_rate(args.n, budget, 1, rows=rows)
         if s >= W:
             rates.append(rate)
     value = float(len(rates) / sum(1.0 / r for r in rates))
@@ -274,7 +342,8 @@ def run_reference(args):
             "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": args.n * args.n, "form": "fp64 oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
+                             "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -403,11 +472,22 @@ def run_gpu(args):
     esmm.lib()
     stream = torch.cuda.Stream()
     n, K, W = args.n, args.steps, args.warmup
-    x, prim = workload(n, rank)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    g = esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
-                  stream=stream.cuda_stream, **grid_params(args.form))
+    if world > 1:
+        # one problem sharded over the ranks: slab k of the stacked grid on
+        # rank k, reductions and halo exchanges over a gloo group
+        from paper_2107_12027_gb300.comm import TorchComm
+        x, prim = stacked_workload(n, world)
+        g = esmm.Slab((n, n * world), world, rank, TorchComm(dist.new_group(backend="gloo")), lo=(-1, -1),
+                      hi=(1, 2 * world - 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5, stream=stream.cuda_stream,
+                      **grid_params(args.form))
+    else:
+        x, prim = workload(n, rank)
+        g = esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
+                      stream=stream.cuda_stream, **grid_params(args.form))
     g.state_set(prim, x)
+    if world > 1:
+        x, prim = workload(n, rank)   # the single-GPU problem for the extras below
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -433,31 +513,46 @@ def run_gpu(args):
     ifaces_per_launch = ((n + 1) * n + (n + 1) * n) / 2.0
     avg_launch_s = iface_ms * 1e-3 / max(iface_timed, 1)
     roof = None
+    # the method's operations per interface (the library's flux templates on
+    # a counting type; each divide and root counts once) beside the executed ones
+    ops = esmm.flux_ops(5.0 / 3.0, 2, 5)
+    alg = ops["dissipation"] + ops["combination"]
     if args.form == "fp64":
-        peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
-        if FLOPS_PER_IFACE_F64:
-            ach = FLOPS_PER_IFACE_F64 * ifaces_per_launch / avg_launch_s / 1e12
-        else:
-            ach = None
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": (ach / peak) if ach else None, "traffic": TRAFFIC_IFACE_F64,
-                "kernel": "k_iface<double,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
-                "share_of_step": iface_ms / total_ms,
-                "peak_note": "derived FP64 peak: 152 SMs x 4 flop/clk x 2070 MHz"}
+        peak, src = alu_peak("fp64")
+        ach = FLOPS_PER_IFACE_F64 * ifaces_per_launch / avg_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": TRAFFIC_IFACE_F64, "kernel": "k_iface<double,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
+                "share_of_step": iface_ms / total_ms, "peak_source": src,
+                "peak_derived": N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12,
+                "flops_basis": "executed FP64 operations per interface (ncu: dadd + dmul + 2 dfma), %d per "
+                               "interface" % FLOPS_PER_IFACE_F64,
+                "algorithmic": {"flops_per_interface": alg,
+                                "achieved": alg * ifaces_per_launch / avg_launch_s / 1e12,
+                                "frac": alg * ifaces_per_launch / avg_launch_s / 1e12 / peak,
+                                "basis": "esmm_flux_ops: ES dissipation %d + pair combination %d operations per "
+                                         "interface (add, mul, div, sqrt, rsqrt each 1)" % (ops["dissipation"],
+                                                                                            ops["combination"])}}
     else:
-        peak = N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        peak, src = alu_peak("fp32")
         ach = FLOPS_PER_IFACE_F32 * ifaces_per_launch / avg_launch_s / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": TRAFFIC_IFACE_F32, "kernel": "k_iface<float,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
-                "share_of_step": iface_ms / total_ms,
-                "peak_note": "derived FP32 peak: 152 SMs x 256 flop/clk x 2070 MHz"}
+                "share_of_step": iface_ms / total_ms, "peak_source": src,
+                "peak_derived": N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12,
+                "flops_basis": "executed FP32 operations per interface (ncu: fadd + fmul + 2 ffma), %d per "
+                               "interface" % FLOPS_PER_IFACE_F32,
+                "algorithmic": {"flops_per_interface": alg,
+                                "achieved": alg * ifaces_per_launch / avg_launch_s / 1e12,
+                                "frac": alg * ifaces_per_launch / avg_launch_s / 1e12 / peak}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.form == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes": n * n, "form": args.form,
                        "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": "independent problem per rank" if world > 1 else "single GPU"},
+                       "parallelism": ("one %dx%d grid of %d stacked problems, slab-decomposed along x_2: %d own "
+                                       "rows (+%d-row halos) per rank, halo exchange and reductions over gloo"
+                                       % (n, n * world, world, n, esmm.SLAB_HALO)) if world > 1 else "single GPU"},
             "gpu_launches": launches, "roofline": roof, "clocks": clk,
             "hbm": hbm_roofline(value / world, "rhd2")}
     if not args.no_extras:
@@ -466,8 +561,7 @@ def run_gpu(args):
             gk.state_set(prim, x)
             line["kinds"] = kind_rates(gk, torch, n * n, 10)
         line["e2e"] = e2e_leg(torch, n, args.form, max(3, min(K, 50)), 2, stream)
-        rate, desc, _ = oracle_sample_rate(n, 15.0, 1)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(n, 10.0)
         if args.form == "fp64":
             with esmm.Grid((n, n), (-1, -1), (1, 1), bc=(esmm.OUTFLOW, esmm.OUTFLOW), p=2, w=5,
                            stream=stream.cuda_stream, **grid_params("mixed")) as gm:
@@ -478,6 +572,13 @@ def run_gpu(args):
             forms["mixed"].update(mixed_vs_fp64(torch, n, stream))
             forms["batched"] = batch_leg(torch, stream)
             line["forms"] = forms
+            # the other single-GPU configurations: the 512^2 RMHD rotor (FP64,
+            # with its mixed form) and the 128^3 RMHD blast (FP64)
+            sub = argparse.Namespace(workload="rotor", form="fp64", n=None, steps=5, warmup=3, no_extras=False)
+            blast = argparse.Namespace(workload="blast3d", form="fp64", n=None, steps=3, warmup=2, no_extras=True)
+            line["workloads"] = {"rotor512": rmhd_line(sub), "blast128": rmhd_line(blast)}
+            line["peaks"] = {"fp64_tflops": alu_peak("fp64")[0], "fp32_tflops": alu_peak("fp32")[0],
+                             "source": alu_peak("fp64")[1]}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -496,7 +597,7 @@ def rotor_mixed_vs_fp64(torch, n, stream, nsteps=1):
     out = {}
     for form in ("fp64", "mixed"):
         with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
-                       stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,
+                       stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO, cfl=ROTOR_CFL,
                        precision=esmm.MIXED if form == "mixed" else esmm.FP64) as g:
             g.state_set(prim, x)
             S0 = g.totals()[0]
@@ -515,8 +616,12 @@ def rotor_mixed_vs_fp64(torch, n, stream, nsteps=1):
 
 
 def run_rmhd(args):
-    """Time the 2D RMHD rotor (FP64 or mixed form) or the 3D RMHD blast (FP64)
-    on one GPU."""
+    print(json.dumps(rmhd_line(args)), flush=True)
+
+
+def rmhd_line(args):
+    """Time the 2D RMHD rotor (FP64 or mixed form) or a 3D workload (FP64) on
+    one GPU; returns the bench line."""
     import torch
     from paper_2107_12027_gb300 import esmm
     from paper_2107_12027_gb300 import workloads as wl
@@ -565,13 +670,13 @@ def run_rmhd(args):
     else:
         x, prim = wl.rotor_config(n)
         g = esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
-                      stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,
+                      stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO, cfl=ROTOR_CFL,
                       precision=esmm.MIXED if args.form == "mixed" else esmm.FP64)
         nodes = n * n
         ifaces = (n + 1) * n
         desc = ("2D RMHD rotor, %dx%d nodes on [-0.5,0.5]^2, outflow, Gamma=4/3, disk r<0.1 with rho=10 at angular "
                 "speed 9.95, background rho=1, p=1, B=(1,0,0), adaptive moving mesh (sigma=ln rho, alpha=800), "
-                "4th-order EC flux (p=2) + WENO5 + Powell source, SSP-RK3, CFL 0.4" % (n, n))
+                "4th-order EC flux (p=2) + WENO5 + Powell source, SSP-RK3, CFL %g" % (n, n, ROTOR_CFL))
         flops, traffic, kname = FLOPS_PER_IFACE_MHD2, TRAFFIC_IFACE_MHD2, "k_iface_mhd<double,2,5>"
         if args.form == "mixed":
             flops, traffic, kname = FLOPS_PER_IFACE_MHD2_F32, TRAFFIC_IFACE_MHD2_F32, "k_iface_mhd<float,2,5>"
@@ -613,13 +718,14 @@ def run_rmhd(args):
     avg = iface_ms * 1e-3 / max(iface_timed, 1)
     mixed = args.form == "mixed"
     per_clk = FP32_FLOP_PER_CLK_SM if mixed else FP64_FLOP_PER_CLK_SM
-    peak = N_SM * per_clk * SM_MAX_MHZ * 1e6 / 1e12
+    peak, src = alu_peak("fp32" if mixed else "fp64")
     ach = flops * ifaces / avg / 1e12 if flops else None
     roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": (ach / peak) if ach else None, "traffic": traffic, "kernel": kname,
-            "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms,
-            "peak_note": "derived %s peak: 152 SMs x %d flop/clk x 2070 MHz" % ("FP32" if mixed else "FP64",
-                                                                              per_clk)}
+            "avg_launch_ms": avg * 1e3, "share_of_step": iface_ms / total_ms, "peak_source": src,
+            "peak_derived": N_SM * per_clk * SM_MAX_MHZ * 1e6 / 1e12,
+            "flops_basis": ("executed %s operations per interface (ncu SASS counters), %s per interface"
+                            % ("FP32" if mixed else "FP64", flops)) if flops else None}
     kinds = None
     if not args.no_extras:
         kinds = kind_rates(g, torch, nodes, 3, restore=lambda: g.state_set_cons(c0, J0, x0))
@@ -639,7 +745,7 @@ def run_rmhd(args):
         line["kinds"] = kinds
     if not three and args.form == "fp64" and not args.no_extras:
         with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=4.0 / 3.0, phys=esmm.RMHD,
-                       stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO,
+                       stream=stream.cuda_stream, alpha=800.0, monitor=esmm.MONITOR_LNRHO, cfl=ROTOR_CFL,
                        precision=esmm.MIXED) as gm:
             gm.state_set(prim, x)
             tm = 0.0
@@ -658,7 +764,7 @@ def run_rmhd(args):
                 raise RuntimeError("mixed form: primitive recovery failed")
         line["forms"] = {"mixed": {"value": nodes * 3 * K / (tm * 1e-3), "ms_per_step": tm / K}}
         line["forms"]["mixed"].update(rotor_mixed_vs_fp64(torch, n, stream))
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------- UM-O5 vs MM-O5
@@ -675,7 +781,7 @@ def run_rmhd(args):
 STUDY = {   # problem: (sizes (MM-O5, UM-O5 coarse, UM-O5 fine, reference), final time)
     "rp1": ((200, 200, 500, 1000), 0.4),
     "rp2": ((200, 200, 500, 1000), 0.4),
-    "rp3": ((200, 200, 500, 1000), 0.4),
+    "rp3": ((200, 200, 600, 1000), 0.4),
     "blast": ((150, 150, 600, 600), 4.0),   # the fine run is the reference (as in the paper's comparison)
 }
 

@@ -157,6 +157,56 @@ int esmm_rhs(esmm_grid *g, const double *cons, const double *J, const double *x,
  * radius).  Synchronises. */
 int esmm_cfl_dt(esmm_grid *g, double *dt);
 
+/* Domain decomposition into slabs (multi-GPU, the paper's parallel design:
+ * a structured grid split into subdomains that exchange halos; Sec. 6 runs
+ * on a PLUTO-based MPI code).  A 2D grid of n[0] x n[1] nodes is split along
+ * the second index into nslab slabs of consecutive rows (sizes differing by
+ * at most one, each at least ESMM_SLAB_HALO rows).  Slab s holds its own rows
+ * plus ESMM_SLAB_HALO rows beyond each cut (a periodic second direction has
+ * cuts at both ends of every slab).  A rank's slab is an ordinary grid of
+ * those rows with outflow treatment at its cuts; only its own rows take part
+ * in reductions.  The halo is wide enough that one step's monitor, filter
+ * passes and Jacobi sweeps (1 + n_filter + 1 + mu rows of reach) stay exact
+ * on the own rows, so the step communicates:
+ *   - allreduce max of the spectral radius, max |grad sigma| (and the
+ *     Laplacian's max) and the displacement terms; allreduce min of the
+ *     limiter Delta tau; per Newton evaluation of the eq. cfl solve an
+ *     allreduce max of each direction's value and an allreduce min of the
+ *     slope among the slabs that attain it;
+ *   - a halo exchange of the mesh velocity after the mesh step, and of
+ *     (cons, J, x) after each of the three stages;
+ *   - an allreduce sum for esmm_totals.
+ * The transport is the caller's: comm->allreduce(ctx, buf, n, op) combines
+ * n host doubles in place over all slabs (op ESMM_OP_MAX, _MIN or _SUM);
+ * comm->exchange(ctx, send_lo, send_hi, recv_lo, recv_hi, count) sends count
+ * host doubles to the slab below (send_lo) and above (send_hi) and receives
+ * theirs (recv_lo from below, recv_hi from above; a side without a
+ * neighbour is NULL).  Both return 0 on success; every slab must make the
+ * same calls in the same order.  With max, min and the Newton rule the
+ * result on the own rows equals the undecomposed grid's bit for bit; the
+ * totals differ only by the order of the sum.
+ * Slab handles accept esmm_set_eos, esmm_set_order, esmm_set_params (not
+ * ESMM_INFLOW ends), esmm_state_set (the GLOBAL arrays [m][n1][n0]; every
+ * slab copies its rows), esmm_state_get (the slab's OWN rows), esmm_rhs
+ * (arrays of the slab's rows, halo included), esmm_rk_step, esmm_advance,
+ * esmm_totals, esmm_last_error, esmm_profile* and esmm_grid_destroy; other
+ * calls return ESMM_ERR_ARG.  esmm_slab_rows gives the global row ranges:
+ * own rows [own0, own1), held rows [ext0, ext1) (ext0 < 0 or ext1 > n[1]
+ * wrap periodically).  2D grids only. */
+#define ESMM_SLAB_HALO 16
+#define ESMM_OP_MAX 0
+#define ESMM_OP_MIN 1
+#define ESMM_OP_SUM 2
+typedef struct {
+    void *ctx;
+    int (*allreduce)(void *ctx, double *buf, int n, int op);
+    int (*exchange)(void *ctx, const double *send_lo, const double *send_hi, double *recv_lo, double *recv_hi,
+                    long long count);
+} esmm_comm;
+int esmm_slab_create(esmm_grid **g, const int n[2], const double lo[2], const double hi[2], int phys,
+                     const int bc[2], int nslab, int slab, const esmm_comm *comm, void *stream);
+int esmm_slab_rows(const esmm_grid *g, int *own0, int *own1, int *ext0, int *ext1);
+
 /* Adaptive mesh redistribution of Sec. 5 for the grid's state and time step
  * dt: monitor, low-pass filter, mu Jacobi sweeps, movement limiter, and the
  * mesh velocity xdot = Delta tau (x^[mu] - x^n)/dt.
@@ -292,6 +342,26 @@ int esmm_last_error(esmm_grid *g, int *n_c2p_fail, char *msg, int len);
 int esmm_profile(esmm_grid *g, int mask);
 int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[ESMM_NKINDS],
                       long long timed[ESMM_NKINDS]);
+
+/* FMA throughput of one pipe, a measurement addition (the paper has no
+ * counterpart): precision ESMM_FP64 or ESMM_MIXED (FP32) selects the pipe.
+ * A kernel of independent FMA chains (8 blocks of 256 threads per SM) runs
+ * for about `seconds` (0 < seconds <= 60) on a private stream of the current
+ * device, timed with CUDA events; *flops_per_s receives 2 x FMAs / second,
+ * *ms_per_launch (may be NULL) the time of one launch.  Synchronises. */
+int esmm_fma_peak(int precision, double seconds, double *flops_per_s, double *ms_per_launch);
+
+/* Algorithmic operation counts of the 2D RHD flux arithmetic, a
+ * measurement addition (the paper has no counterpart): the library's own
+ * flux templates evaluated on a counting number type for one node pair and
+ * one interface of a generic state (no near-equal log means), every add,
+ * subtract, multiply, divide, reciprocal, square root and reciprocal square
+ * root counted once.  ops[0]: one two-point EC flux (k_pairs computes p per
+ * anchor node); ops[1]: the ES dissipation of one interface with WENO order w
+ * (3 or 5); ops[2]: the interface kernel's combination of the stored pair
+ * fluxes and the metric flux (eq. ECFlux_O2p, MetricsFlux_O2p) for order p.
+ * Runs one thread on the current device; synchronises. */
+int esmm_flux_ops(double gamma, int p, int w, double ops[3]);
 
 /* Allocation-free right-hand side.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code

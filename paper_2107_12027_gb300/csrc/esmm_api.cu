@@ -104,6 +104,17 @@ struct esmm_grid {
     int ck_n;
     double *adjG, *adjGp;            // local Jacobian-vector contributions
     double *lam_a, *lam_b, *lam_c, *lam_v;
+    // a slab of a decomposed grid (nslab > 0): its rows of the whole grid
+    int nslab, slab;
+    esmm_comm comm;
+    int rows_g;                      // rows of the whole grid
+    int own0, own1, ext0, ext1;      // own rows, held rows (global indices)
+    int periodic1;                   // the whole grid is periodic in its second direction
+    double per1;                     // that period
+    double *xbuf;                    // pinned exchange buffers: send low/high, receive low/high
+    size_t xbuf_n;                   // doubles per buffer
+    double *vs_dev;                  // [2][2] a slab's Newton values and slopes
+    const void *mesh_disp;           // the displacement x^[mu] - x^n of the last mesh step
 };
 
 namespace {
@@ -378,7 +389,8 @@ void step_dt(esmm_grid *g, double dt, bool moving)
     LaunchDom L = dom(g, D_NODE);
     for (int it = 0; it < DT_NEWTON; ++it) {
         Prof pr_(g, ESMM_KIND_OTHER);
-        k_dt_newton<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev);
+        k_dt_newton<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev,
+                                                nullptr);
     }
 }
 
@@ -393,10 +405,10 @@ void red_init(esmm_grid *g)
 // (k_mesh_sweep), since the blocked kernel's halo work costs FP64 issue slots
 constexpr int MT_SB32 = 10;
 
-// The Jacobi sweeps (k_mesh_sweeps), the limiter and the mesh velocity from
-// the displacement, in working type T (the weights are in g->cw).
+// The Jacobi sweeps (k_mesh_sweeps) and the limiter, in working type T (the
+// weights are in g->cw); the displacement is left at g->mesh_disp.
 template <typename T, int SB>
-int mesh_finish(esmm_grid *g, double dt, const LaunchDom &L, const LaunchDom &L2)
+int mesh_sweeps_tau(esmm_grid *g, const LaunchDom &L)
 {
     T *bufs[2] = {reinterpret_cast<T *>(g->X), reinterpret_cast<T *>(g->Xn)};
     const T *Dd = bufs[0];
@@ -434,10 +446,20 @@ int mesh_finish(esmm_grid *g, double dt, const LaunchDom &L, const LaunchDom &L2
         Prof pr_(g, ESMM_KIND_MESH);
         k_mesh_tau<T><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, Dd, g->q, g->J, g->red, g->cflb);
     }
+    g->mesh_disp = Dd;
+    return ESMM_OK;
+}
+
+// ... then the step (step_dt) and the mesh velocity from the displacement
+template <typename T, int SB>
+int mesh_finish(esmm_grid *g, double dt, const LaunchDom &L, const LaunchDom &L2)
+{
+    int rc = mesh_sweeps_tau<T, SB>(g, L);
+    if (rc) return rc;
     step_dt(g, dt, true);
     {
         Prof pr_(g, ESMM_KIND_MESH);
-        k_mesh_xdot<T><<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, Dd, g->red, g->dt_dev, g->xdot);
+        k_mesh_xdot<T><<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, (const T *)g->mesh_disp, g->red, g->dt_dev, g->xdot);
     }
     return ESMM_OK;
 }
@@ -561,7 +583,7 @@ void free_all(esmm_grid *g)
                        &g->q, &g->pg[0], &g->pg[1], &g->pg[2], &g->in_cons, &g->in_J, &g->in_x, &g->in_xdot,
                        &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->rs, &g->X, &g->Xn,
                        &g->dt_dev,
-                       &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev, &g->cflb, &g->npart};
+                       &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev, &g->cflb, &g->npart, &g->vs_dev};
     for (double **b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     drop_graph(g);
@@ -575,6 +597,8 @@ void free_all(esmm_grid *g)
     if (g->status) cudaFree(g->status);
     if (g->dpd) cudaFree(g->dpd);
     if (g->pin) cudaFreeHost(g->pin);
+    if (g->xbuf) cudaFreeHost(g->xbuf);
+    g->xbuf = nullptr;
     for (int k = 0; k < ND; ++k)
         if (g->tiles[k]) { cudaFree(g->tiles[k]); g->tiles[k] = nullptr; }
     if (g->ev) {
@@ -696,6 +720,8 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         G.N = (long long)G.nx * G.ny;
         G.bc0 = bc[2 * b];
         G.bc1 = bc[2 * b + 1];
+        G.own0 = 0;
+        G.own1 = G.ny;
         if (G.bc0 == ESMM_INFLOW || G.bc1 == ESMM_INFLOW) g->needs_inflow = 1;
         G.per0 = hi[2 * b] - lo[2 * b];
         G.per1 = hi[2 * b + 1] - lo[2 * b + 1];
@@ -908,7 +934,8 @@ void step_launches(const esmm_grid *g, double dt, long long per[ESMM_NKINDS])
     const int mu = g->prm.mu;
     const int sweeps = g->prm.precision == ESMM_MIXED ? (mu + MT_SB32 - 1) / MT_SB32 : (mu > 0) + mu;   // (+ residual)
     per[ESMM_KIND_MESH] = g->prm.move_mesh ? (4 + g->prm.n_filter + (mu > 0) + sweeps) : 0;
-    per[ESMM_KIND_OTHER] = 3 + (dt > 0.0 ? 0 : 1);  // reset, (CFL), dt, time
+    // reset, (CFL), dt, time, and the Newton evaluations of a CFL step with mesh motion
+    per[ESMM_KIND_OTHER] = 3 + (dt > 0.0 ? 0 : 1) + (g->prm.move_mesh && !(dt > 0.0) ? DT_NEWTON : 0);
 }
 
 // Advance every problem nsteps steps.  On a capturable stream one step is
@@ -1141,6 +1168,316 @@ int step_given(esmm_grid *g, const double *xd, double dt, int mem)
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Slabs of a decomposed grid (esmm_slab_create).  A slab is a one-problem
+// grid of its held rows; its reductions collect its own rows only, and the
+// host combines them over the slabs through the caller's comm between the
+// kernels that need the combined values.
+namespace {
+
+double host_bits(unsigned long long b)
+{
+    double v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+unsigned long long host_to_bits(double v)
+{
+    unsigned long long b;
+    memcpy(&b, &v, sizeof b);
+    return b;
+}
+
+int slab_allreduce(esmm_grid *g, double *buf, int n, int op)
+{
+    if (n > 0 && g->comm.allreduce(g->comm.ctx, buf, n, op) != 0)
+        return fail(g, ESMM_ERR_CUDA, "slab allreduce failed");
+    return ESMM_OK;
+}
+
+// combine the reduction slots in mx by max and those in mn by min over the
+// slabs (in place on the device)
+int slab_slots(esmm_grid *g, std::initializer_list<int> mx, std::initializer_list<int> mn)
+{
+    unsigned long long h[NRED];
+    CK(cudaMemcpyAsync(h, g->red, sizeof h, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    double b[NRED];
+    int k = 0, rc;
+    for (int i : mx) b[k++] = host_bits(h[i]);
+    if ((rc = slab_allreduce(g, b, k, ESMM_OP_MAX))) return rc;
+    k = 0;
+    for (int i : mx) h[i] = host_to_bits(b[k++]);
+    k = 0;
+    for (int i : mn) b[k++] = host_bits(h[i]);
+    if ((rc = slab_allreduce(g, b, k, ESMM_OP_MIN))) return rc;
+    k = 0;
+    for (int i : mn) h[i] = host_to_bits(b[k++]);
+    CK(cudaMemcpyAsync(g->red, h, sizeof h, cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+// one array [ncomp][N] of the slab to exchange; shift: the component that
+// moves by the period where a halo crosses the periodic seam (-1: none)
+struct XArr {
+    double *p;
+    int ncomp, shift;
+};
+
+// Halo exchange: the slab's lowest and highest ESMM_SLAB_HALO own rows of
+// every array go to the neighbours below and above, whose own rows fill the
+// slab's halo rows.
+int slab_exchange(esmm_grid *g, std::initializer_list<XArr> arrs)
+{
+    const Geom &G = g->hpd[0].g;
+    const long long H = ESMM_SLAB_HALO, row = G.nx, N = G.N, blk = H * row;
+    size_t count = 0;
+    for (const XArr &a : arrs) count += (size_t)a.ncomp * blk;
+    if (count > g->xbuf_n) {
+        if (g->xbuf) cudaFreeHost(g->xbuf);
+        g->xbuf = nullptr;
+        g->xbuf_n = 0;
+        CK(cudaMallocHost((void **)&g->xbuf, 4 * count * sizeof(double)));
+        g->xbuf_n = count;
+    }
+    double *slo = g->xbuf, *shi = slo + count, *rlo = shi + count, *rhi = rlo + count;
+    const bool lo = g->ext0 < g->own0, hi = g->ext1 > g->own1;
+    const long long o0 = g->own0 - g->ext0, o1 = g->own1 - g->ext0;
+    long long off = 0;
+    for (const XArr &a : arrs)
+        for (int c = 0; c < a.ncomp; ++c, off += blk) {
+            if (lo) CK(cudaMemcpyAsync(slo + off, a.p + c * N + o0 * row, blk * sizeof(double),
+                                       cudaMemcpyDeviceToHost, g->st));
+            if (hi) CK(cudaMemcpyAsync(shi + off, a.p + c * N + (o1 - H) * row, blk * sizeof(double),
+                                       cudaMemcpyDeviceToHost, g->st));
+        }
+    CK(cudaStreamSynchronize(g->st));
+    if (g->comm.exchange(g->comm.ctx, lo ? slo : nullptr, hi ? shi : nullptr, lo ? rlo : nullptr,
+                         hi ? rhi : nullptr, (long long)count) != 0)
+        return fail(g, ESMM_ERR_CUDA, "slab halo exchange failed");
+    off = 0;
+    for (const XArr &a : arrs)
+        for (int c = 0; c < a.ncomp; ++c, off += blk) {
+            if (c == a.shift && g->periodic1) {   // halos across the periodic seam
+                if (lo && g->slab == 0)
+                    for (long long q = 0; q < blk; ++q) rlo[off + q] -= g->per1;
+                if (hi && g->slab == g->nslab - 1)
+                    for (long long q = 0; q < blk; ++q) rhi[off + q] += g->per1;
+            }
+            if (lo) CK(cudaMemcpyAsync(a.p + c * N + (o0 - H) * row, rlo + off, blk * sizeof(double),
+                                       cudaMemcpyHostToDevice, g->st));
+            if (hi) CK(cudaMemcpyAsync(a.p + c * N + o1 * row, rhi + off, blk * sizeof(double),
+                                       cudaMemcpyHostToDevice, g->st));
+        }
+    CK(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+int slab_exchange_state(esmm_grid *g, double *cons, double *J, double *x)
+{
+    return slab_exchange(g, {{cons, g->nv, -1}, {J, 1, -1}, {x, 2, 1}});
+}
+
+// The step of eq. cfl on a slab: the Newton evaluations of the solve, each
+// combined over the slabs (max of each direction's value, then min of the
+// slope among the slabs that attain it: the undecomposed rule), with the
+// update of esmm_reduce.cuh applied on the host.
+int slab_newton(esmm_grid *g)
+{
+    DtSolve S;
+    CK(cudaMemcpyAsync(&S, g->ds, sizeof S, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    LaunchDom L = dom(g, D_NODE);
+    double *vs_dev = g->vs_dev;
+    if (S.done) return ESMM_OK;   // ended in the set-up (no mesh motion): dt_dev holds the step
+    double dt = 0.0;
+    int rc = ESMM_OK;
+    while (!S.done) {
+        {
+            Prof pr_(g, ESMM_KIND_OTHER);
+            k_dt_newton<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev,
+                                                    vs_dev);
+        }
+        double h[4];
+        if (cudaMemcpyAsync(h, vs_dev, sizeof h, cudaMemcpyDeviceToHost, g->st) != cudaSuccess ||
+            cudaStreamSynchronize(g->st) != cudaSuccess) {
+            rc = fail(g, ESMM_ERR_CUDA, "slab Newton read-back");
+            break;
+        }
+        double V[2] = {h[0], h[2]}, Sl[2];
+        if ((rc = slab_allreduce(g, V, 2, ESMM_OP_MAX))) break;
+        for (int k = 0; k < 2; ++k) Sl[k] = h[2 * k] == V[k] ? h[2 * k + 1] : HUGE_VAL;
+        if ((rc = slab_allreduce(g, Sl, 2, ESMM_OP_MIN))) break;
+        double gsum = 0.0, slope = 0.0;
+        for (int k = 0; k < 2; ++k) {
+            gsum += V[k];
+            slope += Sl[k];
+        }
+        dt_newton_update(&S, gsum, slope, g->prm.cfl, &dt);
+        if (cudaMemcpyAsync(g->ds, &S, sizeof S, cudaMemcpyHostToDevice, g->st) != cudaSuccess ||
+            cudaStreamSynchronize(g->st) != cudaSuccess) {
+            rc = fail(g, ESMM_ERR_CUDA, "slab Newton update");
+            break;
+        }
+    }
+    if (rc) return rc;
+    g->pin[0] = dt;
+    CK(cudaMemcpyAsync(g->dt_dev, g->pin, sizeof(double), cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return ESMM_OK;
+}
+
+// State of a slab from the GLOBAL arrays (host): its held rows, with the
+// periodic wrap (rows beyond an end shifted by the period in x_2), then a
+// halo exchange so that the halo rows' J and cons are the neighbours' (the
+// slab's own set-up differences them at its cuts).
+int slab_state_set(esmm_grid *g, const double *prim, const double *x, int mem)
+{
+    if (mem != ESMM_MEM_HOST) return fail(g, ESMM_ERR_ARG, "a slab's state is set from host arrays");
+    const Geom &G = g->hpd[0].g;
+    const size_t nx = (size_t)G.nx, nyl = (size_t)G.ny, Nl = nx * nyl, Ng = nx * (size_t)g->rows_g;
+    std::vector<double> hp((size_t)g->nv * Nl), hx(x ? 2 * Nl : 0);
+    for (size_t r = 0; r < nyl; ++r) {
+        const long long gr = g->ext0 + (long long)r;
+        const long long src = ((gr % g->rows_g) + g->rows_g) % g->rows_g;
+        const double shift = (double)((gr - src) / g->rows_g) * g->per1;
+        for (int c = 0; c < g->nv; ++c)
+            memcpy(&hp[c * Nl + r * nx], prim + c * Ng + src * nx, nx * sizeof(double));
+        if (x) {
+            memcpy(&hx[r * nx], x + src * nx, nx * sizeof(double));
+            for (size_t i = 0; i < nx; ++i) hx[Nl + r * nx + i] = x[Ng + src * nx + i] + shift;
+        }
+    }
+    int rc = state_set_one(g, 0, hp.data(), x ? hx.data() : nullptr, ESMM_MEM_HOST);
+    int rx = slab_exchange_state(g, g->cons, g->J, g->x);   // collective: every slab exchanges
+    return rc ? rc : rx;
+}
+
+// the slab's own rows of one field
+int slab_state_get(esmm_grid *g, int what, double *out, int mem)
+{
+    const Geom &G = g->hpd[0].g;
+    const size_t nx = (size_t)G.nx, Nl = (size_t)G.N, rows = (size_t)(g->own1 - g->own0);
+    const size_t o0 = (size_t)(g->own0 - g->ext0) * nx;
+    int nc = (what == ESMM_GET_PRIM || what == ESMM_GET_CONS) ? g->nv : (what == ESMM_GET_J ? 1 : 2);
+    const double *src = nullptr;
+    int rc = ESMM_OK;
+    switch (what) {
+    case ESMM_GET_PRIM: {
+        LaunchDom L = dom_one(g, 0, D_NODE);
+        {
+            Prof pr_(g, ESMM_KIND_NODE);
+            if (g->phys == ESMM_RMHD)
+                launch_prim_out_mhd(L, g->gamma, g->cons, g->J, g->out_dc, g->status, g->st);
+            else
+                k_prim_out<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->cons, g->J, g->out_dc, g->status);
+        }
+        src = g->out_dc;
+        break;
+    }
+    case ESMM_GET_CONS: src = g->cons; break;
+    case ESMM_GET_J: src = g->J; break;
+    case ESMM_GET_X: src = g->x; break;
+    case ESMM_GET_XDOT: src = g->xdot; break;
+    default: return fail(g, ESMM_ERR_ARG, "unknown field");
+    }
+    for (int c = 0; c < nc && !rc; ++c) rc = copy_out(g, out + c * rows * nx, src + c * Nl + o0, rows * nx, mem);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(g->st));
+    return what == ESMM_GET_PRIM ? check_c2p(g) : ESMM_OK;
+}
+
+// One step of a slab (synchronous: the reductions and exchanges go through
+// the host).  The kernels are those of rk_step_async; only the points where
+// a combined value is needed differ.
+int slab_step(esmm_grid *g, double dt)
+{
+    int rc;
+    if ((rc = ensure_doms(g))) return rc;
+    const bool moving = g->prm.move_mesh, solve = moving && !(dt > 0.0);
+    node(g, g->cons, g->J, g->x, nullptr, g->pg[0], g->pg[1]);
+    red_init(g);
+    step_radius(g, dt, moving);
+    LaunchDom L = dom(g, D_NODE), L2 = dom(g, D_NODE2);
+    if (moving) {
+        Prof pr_(g, ESMM_KIND_MESH);
+        k_mesh_grad<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.monitor == ESMM_MONITOR_LNRHO, g->prm.alpha_lap > 0.0,
+                                                g->q, g->grad, g->om2, g->red);
+    }
+    if ((rc = slab_slots(g, {0, 2, 3, 6}, {}))) return rc;
+    if (!moving) {
+        step_dt(g, dt, false);
+        if (!g->xdot_zero) {
+            CK(cudaMemsetAsync(g->xdot, 0, sizeof(double) * 2 * g->Ntot, g->st));
+            g->xdot_zero = 1;
+        }
+    } else {
+        g->xdot_zero = 0;
+        {
+            Prof pr_(g, ESMM_KIND_MESH);
+            k_mesh_omega<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.alpha, g->prm.alpha_lap, g->grad, g->om2, g->red,
+                                                     g->om);
+        }
+        double *om = g->om, *om2 = g->om2;
+        for (int f = 0; f < g->prm.n_filter; ++f) {
+            Prof pr_(g, ESMM_KIND_MESH);
+            k_mesh_filter<<<L.nblk, L.bs, 0, g->st>>>(L.pa, om, om2);
+            std::swap(om, om2);
+        }
+        if (g->prm.mu > 0) {
+            Prof pr_(g, ESMM_KIND_MESH);
+            k_mesh_weights<<<L.nblk, L.bs, 0, g->st>>>(L.pa, om, g->cw);
+        }
+        // the sweeps and the limiter (mesh_finish without its dt and mesh velocity)
+        const bool f32 = g->prm.precision == ESMM_MIXED;
+        if (f32) rc = mesh_sweeps_tau<float, MT_SB32>(g, L);
+        else rc = mesh_sweeps_tau<double, 1>(g, L);
+        if (rc) return rc;
+        if ((rc = slab_slots(g, {4, 5}, {1}))) return rc;
+        {
+            Prof pr_(g, ESMM_KIND_OTHER);
+            k_dt<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->prm.cfl, dt, g->red, g->ds, g->dt_dev);
+        }
+        if (solve && (rc = slab_newton(g))) return rc;
+        {
+            Prof pr_(g, ESMM_KIND_MESH);
+            if (f32)
+                k_mesh_xdot<float><<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, (const float *)g->mesh_disp, g->red,
+                                                                 g->dt_dev, g->xdot);
+            else
+                k_mesh_xdot<double><<<L2.nblk, L2.bs, 0, g->st>>>(L2.pa, (const double *)g->mesh_disp, g->red,
+                                                                  g->dt_dev, g->xdot);
+        }
+        if ((rc = slab_exchange(g, {{g->xdot, 2, -1}}))) return rc;
+    }
+    {
+        Prof pr_(g, ESMM_KIND_NODE);
+        LaunchDom Lp = dom(g, D_PAD);
+        k_tmetric<<<Lp.nblk, Lp.bs, 0, g->st>>>(Lp.pa, g->xdot, g->q, q32_of(g));
+    }
+    fluxes(g);
+    update(g, nullptr, nullptr, g->cons, g->J, g->x, g->cons, g->J, g->x, g->xdot, 0.0, 1.0, g->c1, g->J1, g->x1);
+    if ((rc = slab_exchange_state(g, g->c1, g->J1, g->x1))) return rc;
+    node(g, g->c1, g->J1, g->x1, g->xdot, g->pg[1], g->pg[2]);
+    fluxes(g);
+    update(g, nullptr, nullptr, g->cons, g->J, g->x, g->c1, g->J1, g->x1, g->xdot, 0.75, 0.25, g->c2, g->J2, g->x2);
+    if ((rc = slab_exchange_state(g, g->c2, g->J2, g->x2))) return rc;
+    node(g, g->c2, g->J2, g->x2, g->xdot, g->pg[2], g->pg[0]);
+    fluxes(g);
+    update(g, nullptr, nullptr, g->cons, g->J, g->x, g->c2, g->J2, g->x2, g->xdot, 1.0 / 3.0, 2.0 / 3.0, g->cons,
+           g->J, g->x);
+    if ((rc = slab_exchange_state(g, g->cons, g->J, g->x))) return rc;
+    {
+        Prof pr_(g, ESMM_KIND_OTHER);
+        k_time<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->dt_dev, g->t_dev);
+    }
+    CK(cudaGetLastError());
+    return ESMM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // Allocation-free right-hand side (esmm_rhs_static).
 //
 // Its scratch lives in one file-scope device array: per padded node the NQ
@@ -1213,6 +1550,56 @@ int esmm_grid_create(esmm_grid **out, int dim, const int n[3], const double lo[3
     return create(out, 1, n2, lo2, hi2, bc2, phys, stream, false);
 }
 
+int esmm_slab_create(esmm_grid **out, const int n[2], const double lo[2], const double hi[2], int phys,
+                     const int bc[2], int nslab, int slab, const esmm_comm *comm, void *stream)
+{
+    if (!out || !n || !lo || !hi || !bc || !comm || !comm->allreduce || !comm->exchange) return ESMM_ERR_ARG;
+    *out = nullptr;
+    if ((phys != ESMM_RHD && phys != ESMM_RMHD) || check_geometry(n[0], n[1], lo, hi, bc)) return ESMM_ERR_ARG;
+    if (bc[0] == ESMM_INFLOW || bc[1] == ESMM_INFLOW) return ESMM_ERR_ARG;
+    const int H = ESMM_SLAB_HALO, ny = n[1];
+    if (nslab < 2 || slab < 0 || slab >= nslab || ny / nslab < H) return ESMM_ERR_ARG;
+    const int base = ny / nslab, rem = ny % nslab;
+    const int own0 = slab * base + std::min(slab, rem), own1 = own0 + base + (slab < rem ? 1 : 0);
+    const bool per = bc[1] == ESMM_PERIODIC;
+    const int ext0 = (slab > 0 || per) ? own0 - H : own0, ext1 = (slab < nslab - 1 || per) ? own1 + H : own1;
+    // the held rows as an outflow grid whose uniform mesh is the whole grid's
+    const double dy = (hi[1] - lo[1]) / (per ? ny : ny - 1);
+    int nl[2] = {n[0], ext1 - ext0}, bcl[2] = {bc[0], ESMM_OUTFLOW};
+    double lol[2] = {lo[0], lo[1] + ext0 * dy}, hil[2] = {hi[0], lo[1] + (ext1 - 1) * dy};
+    esmm_grid *g = nullptr;
+    int rc = create(&g, 1, nl, lol, hil, bcl, phys, stream, false);
+    if (rc) return rc;
+    g->nslab = nslab;
+    g->slab = slab;
+    g->comm = *comm;
+    g->rows_g = ny;
+    g->own0 = own0;
+    g->own1 = own1;
+    g->ext0 = ext0;
+    g->ext1 = ext1;
+    g->periodic1 = per;
+    g->per1 = hi[1] - lo[1];
+    g->hpd[0].g.own0 = own0 - ext0;
+    g->hpd[0].g.own1 = own1 - ext0;
+    if (cudaMalloc((void **)&g->vs_dev, 4 * sizeof(double)) != cudaSuccess) {
+        release(g);
+        return ESMM_ERR_CUDA;
+    }
+    *out = g;
+    return ESMM_OK;
+}
+
+int esmm_slab_rows(const esmm_grid *g, int *own0, int *own1, int *ext0, int *ext1)
+{
+    if (!g || g->nslab == 0) return ESMM_ERR_ARG;
+    if (own0) *own0 = g->own0;
+    if (own1) *own1 = g->own1;
+    if (ext0) *ext0 = g->ext0;
+    if (ext1) *ext1 = g->ext1;
+    return ESMM_OK;
+}
+
 int esmm_grid_destroy(esmm_grid *g)
 {
     if (!g) return ESMM_ERR_ARG;
@@ -1278,6 +1665,11 @@ int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem)
 {
     if (!g || !prim || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_state_set(g->g3, prim, x, mem);
+    if (g->nslab) {
+        int rc = slab_state_set(g, prim, x, mem);
+        g->has_state = rc == ESMM_OK;
+        return rc;
+    }
     int rc = state_set_one(g, 0, prim, x, mem);
     g->has_state = rc == ESMM_OK;
     return rc;
@@ -1285,6 +1677,7 @@ int esmm_state_set(esmm_grid *g, const double *prim, const double *x, int mem)
 
 int esmm_state_set_cons(esmm_grid *g, const double *cons, const double *J, const double *x, double t, int mem)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (!g || !cons || !J || !x || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_state_set_cons(g->g3, cons, J, x, t, mem);
     size_t N = (size_t)g->Ntot, nv = (size_t)g->nv;
@@ -1307,6 +1700,7 @@ int esmm_state_get(esmm_grid *g, int what, double *out, int mem)
     if (!g || !out || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_state_get(g->g3, what, out, mem);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
+    if (g->nslab) return slab_state_get(g, what, out, mem);
     return state_get_one(g, 0, what, out, mem);
 }
 
@@ -1364,6 +1758,7 @@ int esmm_cfl_dt(esmm_grid *g, double *dt)
     node(g, g->cons, g->J, g->x, nullptr, nullptr, nullptr);
     red_init(g);
     step_radius(g, 0.0, false);
+    if (g->nslab && (rc = slab_slots(g, {2, 3}, {}))) return rc;   // the radius over every slab's own rows
     step_dt(g, 0.0, false);   // slots 4, 5 are zero: the static-mesh step
     CK(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
@@ -1373,6 +1768,7 @@ int esmm_cfl_dt(esmm_grid *g, double *dt)
 
 int esmm_mesh_redistribute(esmm_grid *g, double dt, double *xdot, double *dtau, double *dt_used, int mem)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (!g || g->nprob != 1) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_mesh_redistribute(g->g3, dt, xdot, dtau, dt_used, mem);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
@@ -1396,7 +1792,7 @@ int esmm_rk_step(esmm_grid *g, double dt, double *dt_used)
     if (!g) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_rk_step(g->g3, dt, dt_used);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
-    int rc = rk_step_async(g, dt);
+    int rc = g->nslab ? slab_step(g, dt) : rk_step_async(g, dt);
     if (rc) return rc;
     if (dt_used) {
         CK(cudaMemcpyAsync(g->pin, g->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, g->st));
@@ -1409,6 +1805,7 @@ int esmm_rk_step(esmm_grid *g, double dt, double *dt_used)
 
 int esmm_rk_step_given(esmm_grid *g, const double *xdot, double dt, int mem)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (!g || !xdot || !(dt > 0.0) || (mem != ESMM_MEM_HOST && mem != ESMM_MEM_DEVICE)) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_rk_step_given(g->g3, xdot, dt, mem);
     if (g->nprob != 1) return fail(g, ESMM_ERR_ARG, "a batch steps with its adaptive meshes");
@@ -1421,6 +1818,7 @@ int esmm_rk_step_given(esmm_grid *g, const double *xdot, double dt, int mem)
 
 int esmm_set_inflow(esmm_grid *g, const double *prim)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (!g || !prim) return ESMM_ERR_ARG;
     const int nv = g->dim == 3 ? 8 : g->nv;
     double v2 = 0.0;
@@ -1442,6 +1840,11 @@ int esmm_advance(esmm_grid *g, int nsteps, double dt)
     if (!g || nsteps < 0) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_advance(g->g3, nsteps, dt);
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
+    if (g->nslab) {   // no graph: every step reduces and exchanges through the host
+        for (int k = 0; k < nsteps; ++k)
+            if (int rc = slab_step(g, dt)) return rc;
+        return ESMM_OK;
+    }
     return advance(g, nsteps, dt);
 }
 
@@ -1455,6 +1858,7 @@ int esmm_totals(esmm_grid *g, double out[3])
     CK(cudaMemcpyAsync(g->pin, g->tot_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     for (int k = 0; k < 3; ++k) out[k] = g->pin[k];
+    if (g->nslab && (rc = slab_allreduce(g, out, 3, ESMM_OP_SUM))) return rc;   // own rows of every slab
     return check_c2p(g);
 }
 
@@ -1519,6 +1923,7 @@ int esmm_batch_totals(esmm_grid *g, double *out)
 
 int esmm_tune(esmm_grid *g, int *block_sizes)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (g && g->dim == 3) return ESMM_ERR_ARG;   // RHD / 2D only
     if (!g) return ESMM_ERR_ARG;
     int rc = tune(g);
@@ -1531,6 +1936,7 @@ int esmm_tune(esmm_grid *g, int *block_sizes)
 int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double *x, const double *xdot,
                  const double *mu, double *lam, int mem)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (g && g->needs_inflow) return fail(g, ESMM_ERR_ARG, "the adjoint takes periodic and outflow ends");
     if (g && g->dim == 3) {
         if (!cons || !J || !x || !mu || !lam) return ESMM_ERR_ARG;
@@ -1565,6 +1971,7 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 
 int esmm_adjoint_record(esmm_grid *g, int nsteps, double dt)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (g && g->needs_inflow) return fail(g, ESMM_ERR_ARG, "the adjoint takes periodic and outflow ends");
     if (g && g->dim == 3) return nsteps < 0 ? ESMM_ERR_ARG : esmm3_adjoint_record(g->g3, nsteps, dt);
     if (!g || nsteps < 0 || g->nprob != 1) return ESMM_ERR_ARG;
@@ -1626,6 +2033,7 @@ int esmm_adjoint_checkpoint(esmm_grid *g, int step, int what, double *out, int m
 
 int esmm_adjoint_replay(esmm_grid *g, int nsteps)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (g && g->dim == 3) return esmm3_adjoint_replay(g->g3, nsteps);
     if (!g || nsteps < 0 || nsteps > g->ck_n || g->nprob != 1) return ESMM_ERR_ARG;
     if (!g->has_state) return fail(g, ESMM_ERR_STATE, "no state");
@@ -1640,6 +2048,7 @@ int esmm_adjoint_replay(esmm_grid *g, int nsteps)
 
 int esmm_adjoint_vjp(esmm_grid *g, const double *lam_final, double *lam_cons0, double *lam_prim0, int mem)
 {
+    if (g && g->nslab) return fail(g, ESMM_ERR_ARG, "not available on a slab");
     if (g && g->dim == 3) return lam_final ? esmm3_adjoint_vjp(g->g3, lam_final, lam_cons0, lam_prim0, mem)
                                            : ESMM_ERR_ARG;
     if (!g || !lam_final || g->nprob != 1) return ESMM_ERR_ARG;
@@ -1717,6 +2126,8 @@ int esmm_rhs_static(int nx, int ny, const int bc[2], const double lo[2], const d
     G.N = (long long)nx * ny;
     G.bc0 = bc[0];
     G.bc1 = bc[1];
+    G.own0 = 0;
+    G.own1 = ny;
     G.per0 = hi[0] - lo[0];
     G.per1 = hi[1] - lo[1];
     D.on = 0;

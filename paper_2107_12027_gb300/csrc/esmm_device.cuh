@@ -31,7 +31,12 @@ struct Geom {
     long long N;      // nx * ny
     int bc0, bc1;     // 0 periodic, 1 outflow
     double per0, per1;
+    int own0, own1;   // rows j in [own0, own1) take part in the reductions
+                      // (0, ny except on a slab of a decomposed grid)
 };
+
+// a node in the rows whose values the problem's reductions collect
+__device__ __forceinline__ bool owned_row(const Geom &g, int j) { return j >= g.own0 && j < g.own1; }
 
 // One problem of a batch: its geometry and the offsets of its slices in the
 // concatenated arrays (on: node arrays, in units of nodes; op: padded-node

@@ -259,7 +259,7 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
             float vn = (mx * vx + my * vy) * iL;
             float disc = sqrtf(fmaxf((1.0f - v2) * (1.0f - v2 * c2 - vn * vn * (1.0f - c2)), 0.0f));
             float lm = (vn * (1.0f - c2) - cs * disc) * iden, lp = (vn * (1.0f - c2) + cs * disc) * iden;
-            r[k] = (double)(Lk * fmaxf(fabsf(lm), fabsf(lp)) * iJ);
+            r[k] = owned_row(g, j) ? (double)(Lk * fmaxf(fabsf(lm), fabsf(lp)) * iJ) : 0.0;
             if (cflb) {
                 cflb[(2 + k) * g.N + id] = (double)(Lk * lm * iJ);
                 cflb[(4 + k) * g.N + id] = (double)(Lk * lp * iJ);
@@ -310,7 +310,7 @@ __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, cons
             double disc = sqrt((1.0 - v2) * (1.0 - v2 * c2 - vn * vn * (1.0 - c2)));
             double iden = __drcp_rn(1.0 - v2 * c2);
             double lm = (vn * (1.0 - c2) - cs * disc) * iden, lp = (vn * (1.0 - c2) + cs * disc) * iden;
-            r[k] = Lk * fmax(fabs(lm), fabs(lp)) * iJ;
+            r[k] = owned_row(g, j) ? Lk * fmax(fabs(lm), fabs(lp)) * iJ : 0.0;
             if (cflb) {
                 cflb[(2 + k) * g.N + id] = Lk * lm * iJ;
                 cflb[(4 + k) * g.N + id] = Lk * lp * iJ;
@@ -357,7 +357,8 @@ __global__ void k_dt(int nprob, double cfl, double dt_fixed, unsigned long long 
 // of every problem still solving: cflb rows 0, 1 hold a_{k,i}, rows 2..5 the
 // speed bounds (per problem at 6 D.on).  part: [blocks][2][2].
 __global__ void k_dt_newton(ProbArg pa, double cfl, const double *__restrict__ cflb,
-                            const unsigned long long *red, DtSolve *ds, double *part, double *dt_dev)
+                            const unsigned long long *red, DtSolve *ds, double *part, double *dt_dev,
+                            double *vs_out)
 {
     ProbDesc D;
     long long lb;
@@ -376,12 +377,12 @@ __global__ void k_dt_newton(ProbArg pa, double cfl, const double *__restrict__ c
     long long id = lb * blockDim.x + threadIdx.x;
     cflb += 6 * D.on;
     double v[2] = {-1.0, -1.0}, sl[2] = {0.0, 0.0};
-    if (id < g.N)
+    if (id < g.N && owned_row(g, (int)(id / g.nx)))
         for (int k = 0; k < 2; ++k)
             cfl_line(t_sh, tau_sh * cflb[k * g.N + id], cflb[(2 + k) * g.N + id], cflb[(4 + k) * g.N + id], v[k],
                      sl[k]);
     const long long nb = (g.N + blockDim.x - 1) / blockDim.x;
-    dt_newton_block<2>(S, v, sl, blockIdx.x, (long long)blockIdx.x - lb, nb, part, cfl, dt_dev + b);
+    dt_newton_block<2>(S, v, sl, blockIdx.x, (long long)blockIdx.x - lb, nb, part, cfl, dt_dev + b, vs_out);
 }
 
 __global__ void k_time(int nprob, const double *dt_dev, double *t_dev)
@@ -417,6 +418,7 @@ __global__ void k_mesh_grad(ProbArg pa, int lnrho, int with_lap, const double *_
             lv = fabs(e + w + n + so - 4.0 * s[c]);
             lap[id] = lv;
         }
+        if (!owned_row(g, j)) gv = lv = 0.0;
     }
     double m = block_reduce<0>(gv);
     if (threadIdx.x == 0) atomic_max_nonneg(red + (long long)NRED * b, m);
@@ -714,11 +716,13 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const T *__
         tau = fmax(tau, 0.0);
         long long c = pidx(g, i, j);
         double iJ = __drcp_rn(J[id]);
+        const bool own = owned_row(g, j);
         for (int k = 0; k < 2; ++k) {
             const double ak = (dd[0] * q[(Q_M00 + 2 * k) * g.P + c] + dd[1] * q[(Q_M01 + 2 * k) * g.P + c]) * iJ;
-            cm[k] = fabs(ak);
+            cm[k] = own ? fabs(ak) : 0.0;
             cflb[6 * D.on + k * g.N + id] = ak;
         }
+        if (!own) tau = 1.0;
     }
     double m = block_reduce<1>(tau);
     if (threadIdx.x == 0) atomic_min_nonneg(red + (long long)NRED * b + 1, m);
@@ -825,9 +829,11 @@ __global__ void k_totals(ProbArg pa, double gam, const double *__restrict__ q, c
         double rho = q[Q_RHO * g.P + c], W = q[Q_W * g.P + c];
         double lnr = q[Q_LNR * g.P + c], lnb = q[Q_LNB * g.P + c];
         double s = (lnr - lnb) - gam * lnr;        // ln(p / rho^Gamma)
-        v[0] = J[id] * (-rho * W * s / (gam - 1.0));
-        v[1] = cons[id];
-        v[2] = J[id];
+        if (owned_row(g, j)) {
+            v[0] = J[id] * (-rho * W * s / (gam - 1.0));
+            v[1] = cons[id];
+            v[2] = J[id];
+        }
     }
     for (int k = 0; k < 3; ++k) {
         double s = block_reduce<2>(v[k]);

@@ -63,7 +63,7 @@ __global__ void k_cfl_mhd(ProbArg pa, double gam, const double *__restrict__ q, 
                 lo = fmin(lo, (double)lam[m]);
                 hi = fmax(hi, (double)lam[m]);
             }
-            r[k] = Lk * a * iJ;
+            r[k] = owned_row(g, j) ? Lk * a * iJ : 0.0;
             if (cflb) {
                 cflb[6 * D.on + (2 + k) * g.N + id] = Lk * lo * iJ;
                 cflb[6 * D.on + (4 + k) * g.N + id] = Lk * hi * iJ;

@@ -111,9 +111,9 @@ __device__ __forceinline__ double bits_to_double(unsigned long long b) { return 
 // piecewise linear; Newton's method from the right end (CFL + C_m)/S steps to
 // the root of the line active at each iterate (the smaller slope on a tie),
 // which a convex g lies above, so the iterates fall monotonically onto the
-// root's piece.  The solve stops once g <= CFL (1 + 1e-14); after DT_NEWTON
-// evaluations without that, or with a slope <= 0, the safe lower bound
-// (CFL - C_m)/S is used.  k_dt sets the state up; every Newton launch
+// root's piece.  The solve stops once g <= CFL or the Newton step is below
+// 2^-50 t (the root up to rounding); after DT_NEWTON evaluations without
+// that, or with a slope <= 0, the safe lower bound (CFL - C_m)/S is used.  k_dt sets the state up; every Newton launch
 // evaluates g at the current iterate over all nodes of a problem, and the
 // last of the problem's blocks to finish reduces their partial results
 // (in any order: the (value, slope) maximum below does not depend on it)
@@ -175,15 +175,37 @@ __device__ void block_vs_max(double (&v)[NDIR], double (&s)[NDIR])
     __syncthreads();
 }
 
+// One Newton update from g(t) and the active slope: the solve ends at
+// g <= CFL or at a step below 2^-50 t (the root up to rounding), falls back
+// to the safe bound without a positive slope or after DT_NEWTON evaluations,
+// and otherwise steps to the root of the active line.
+__host__ __device__ inline void dt_newton_update(DtSolve *S, double g, double slope, double cfl, double *dt_out)
+{
+    const double step = (g - cfl) / slope;
+    if (g <= cfl || (slope > 0.0 && step <= 0x1p-50 * S->t)) {
+        *dt_out = S->t;
+        S->done = 1;
+    } else if (!(slope > 0.0) || S->iter + 1 >= DT_NEWTON) {
+        *dt_out = S->t_safe;
+        S->done = 1;
+    } else {
+        S->t -= step;
+        S->iter += 1;
+    }
+}
+
 // The block's part of one Newton evaluation: (v, s) are this thread's values
 // (-1, 0 where it has no node).  gblock is the block's index in the launch,
 // [first, first + nb) the blocks of its problem, part [blocks][NDIR][2] the
 // partial results.  The last block of the problem to finish advances S and
 // writes the step to *dt_out when the solve ends.  Every thread of the block
 // must call it.
+//   With vs_out (a slab of a decomposed grid) the last block writes the
+// problem's (value, slope) per direction to vs_out[2k], vs_out[2k + 1] for
+// the host to combine over the slabs, and leaves S as it is.
 template <int NDIR>
 __device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR], long long gblock, long long first,
-                                long long nb, double *part, double cfl, double *dt_out)
+                                long long nb, double *part, double cfl, double *dt_out, double *vs_out = nullptr)
 {
     __shared__ int last;
     block_vs_max<NDIR>(v, s);
@@ -210,6 +232,15 @@ __device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR]
             vs_take(v[k], s[k], __ldcg(part + ((first + q) * NDIR + k) * 2),
                     __ldcg(part + ((first + q) * NDIR + k) * 2 + 1));
     block_vs_max<NDIR>(v, s);
+    if (threadIdx.x == 0 && vs_out) {
+        S->count = 0u;
+#pragma unroll
+        for (int k = 0; k < NDIR; ++k) {
+            vs_out[2 * k] = v[k];
+            vs_out[2 * k + 1] = s[k];
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         double g = 0.0, slope = 0.0;
 #pragma unroll
@@ -218,16 +249,7 @@ __device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR]
             slope += s[k];
         }
         S->count = 0u;
-        if (g <= cfl * (1.0 + 1e-14)) {
-            *dt_out = S->t;
-            S->done = 1;
-        } else if (!(slope > 0.0) || S->iter + 1 >= DT_NEWTON) {
-            *dt_out = S->t_safe;
-            S->done = 1;
-        } else {
-            S->t -= (g - cfl) / slope;
-            S->iter += 1;
-        }
+        dt_newton_update(S, g, slope, cfl, dt_out);
     }
 }
 

@@ -52,10 +52,21 @@ SYMBOLS = (
     "esmm_get_time", "esmm_rhs", "esmm_cfl_dt", "esmm_mesh_redistribute", "esmm_rk_step", "esmm_rk_step_given",
     "esmm_set_inflow",
     "esmm_advance", "esmm_totals", "esmm_last_error", "esmm_version", "esmm_profile", "esmm_profile_read",
-    "esmm_rhs_static", "esmm_mhd_eigen", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
+    "esmm_rhs_static", "esmm_fma_peak", "esmm_flux_ops", "esmm_mhd_eigen", "esmm_batch_create", "esmm_batch_size", "esmm_batch_state_set", "esmm_batch_state_get",
     "esmm_batch_times", "esmm_batch_totals", "esmm_tune", "esmm_adjoint_record", "esmm_adjoint_steps",
     "esmm_adjoint_checkpoint", "esmm_adjoint_replay", "esmm_adjoint_vjp", "esmm_rhs_vjp",
+    "esmm_slab_create", "esmm_slab_rows",
 )
+SLAB_HALO = 16
+OP_MAX, OP_MIN, OP_SUM = 0, 1, 2
+_dptr = ctypes.POINTER(ctypes.c_double)
+#: comm callbacks of esmm_slab_create (include/esmm.h esmm_comm)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, _dptr, ctypes.c_int, ctypes.c_int)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, _dptr, _dptr, _dptr, _dptr, ctypes.c_longlong)
+
+
+class Comm(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("allreduce", ALLREDUCE_FN), ("exchange", EXCHANGE_FN)]
 STATIC_MAX_PADDED_NODES = 68644
 KIND_NODE, KIND_PAIRS, KIND_IFACE, KIND_UPDATE, KIND_MESH, KIND_OTHER = range(6)
 KINDS = ("node", "pairs", "iface", "update", "mesh", "other")
@@ -99,6 +110,8 @@ def lib():
             "esmm_profile": [vp, i],
             "esmm_rhs_static": [i, i, ctypes.POINTER(i), dp, dp, d, i, i, vp, vp, vp, vp, vp, vp, vp],
             "esmm_mhd_eigen": [d, i, vp, vp, vp, vp, vp, vp],
+            "esmm_fma_peak": [i, d, dp, dp],
+            "esmm_flux_ops": [d, i, i, dp],
             "esmm_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(i), dp, dp, ctypes.POINTER(i), i, vp],
             "esmm_batch_size": [vp, ctypes.POINTER(i)],
             "esmm_batch_state_set": [vp, i, vp, vp, i],
@@ -109,6 +122,9 @@ def lib():
             "esmm_adjoint_checkpoint": [vp, i, i, vp, i], "esmm_adjoint_replay": [vp, i],
             "esmm_adjoint_vjp": [vp, vp, vp, vp, i], "esmm_rhs_vjp": [vp, vp, vp, vp, vp, vp, vp, i],
             "esmm_profile_read": [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+            "esmm_slab_create": [ctypes.POINTER(vp), ctypes.POINTER(i), dp, dp, i, ctypes.POINTER(i), i, i,
+                                 ctypes.POINTER(Comm), vp],
+            "esmm_slab_rows": [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -139,6 +155,26 @@ def mhd_eigen(gamma, w, dw=None):
     if rc != OK:
         raise EsmmError(rc, "esmm_mhd_eigen")
     return (lam, R) if dw is None else (lam, R, dlam, dR)
+
+
+def fma_peak(precision, seconds=1.0):
+    """esmm_fma_peak: measured FMA throughput (flop/s, ms per launch) of the
+    FP64 (precision FP64) or FP32 (precision MIXED) pipe."""
+    fl, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib().esmm_fma_peak(int(precision), float(seconds), ctypes.byref(fl), ctypes.byref(ms))
+    if rc != OK:
+        raise EsmmError(rc, "esmm_fma_peak")
+    return fl.value, ms.value
+
+
+def flux_ops(gamma, p, w):
+    """esmm_flux_ops: algorithmic operations of one two-point flux, of one
+    interface's ES dissipation and of the interface kernel's combination."""
+    ops = (ctypes.c_double * 3)()
+    rc = lib().esmm_flux_ops(float(gamma), int(p), int(w), ops)
+    if rc != OK:
+        raise EsmmError(rc, "esmm_flux_ops")
+    return {"pair": ops[0], "dissipation": ops[1], "combination": ops[2]}
 
 
 def rhs_static(nx, ny, bc, lo, hi, gamma, p, w, cons, J, x, xdot, dcons, dJ, stream=None):
@@ -513,6 +549,79 @@ class Grid3(Grid):
         self._check(lib().esmm_mesh_redistribute(self.h, float(dt), ctypes.c_void_p(xdot.ctypes.data),
                                                   ctypes.byref(tau), ctypes.byref(dtu), MEM_HOST))
         return xdot, tau.value, dtu.value
+
+
+def _as_array(ptr, n):
+    return None if not ptr else np.ctypeslib.as_array(ptr, shape=(int(n),))
+
+
+class Slab(Grid):
+    """One slab of a 2D grid decomposed along its second index
+    (esmm_slab_create).  ``transport`` combines and exchanges host buffers
+    between the slabs: an object with ``allreduce(buf, op)`` (in place, op
+    OP_MAX / OP_MIN / OP_SUM) and ``exchange(send_lo, send_hi, recv_lo,
+    recv_hi)`` (numpy arrays, None where the slab has no neighbour), e.g.
+    :class:`paper_2107_12027_gb300.comm.LocalComm` or ``TorchComm``.  state_set
+    takes the whole grid's arrays; state_get returns the slab's own rows."""
+
+    def __init__(self, n, nslab, slab, transport, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(PERIODIC, PERIODIC),
+                 gamma=5.0 / 3.0, p=2, w=5, stream=None, phys=RHD, scheme=None, **params):
+        p, w = _apply_scheme(scheme, p, w, params)
+        self.transport = transport
+
+        def allreduce(ctx, buf, n_, op):
+            try:
+                transport.allreduce(_as_array(buf, n_), int(op))
+                return 0
+            except Exception:   # noqa: BLE001 -- reported to the library as a failed call
+                return 1
+
+        def exchange(ctx, slo, shi, rlo, rhi, count):
+            try:
+                transport.exchange(_as_array(slo, count), _as_array(shi, count), _as_array(rlo, count),
+                                   _as_array(rhi, count))
+                return 0
+            except Exception:   # noqa: BLE001
+                return 1
+        self._fns = (ALLREDUCE_FN(allreduce), EXCHANGE_FN(exchange))   # kept alive with the handle
+        self._comm = Comm(None, self._fns[0], self._fns[1])
+        h = ctypes.c_void_p()
+        nn = (ctypes.c_int * 2)(int(n[0]), int(n[1]))
+        lo2 = (ctypes.c_double * 2)(lo[0], lo[1])
+        hi2 = (ctypes.c_double * 2)(hi[0], hi[1])
+        bc2 = (ctypes.c_int * 2)(bc[0], bc[1])
+        st = ctypes.c_void_p(stream) if stream is not None else None
+        self._check(lib().esmm_slab_create(ctypes.byref(h), nn, lo2, hi2, phys, bc2, int(nslab), int(slab),
+                                           ctypes.byref(self._comm), st))
+        self.h = h
+        r = [ctypes.c_int() for _ in range(4)]
+        self._check(lib().esmm_slab_rows(h, *[ctypes.byref(v) for v in r]))
+        self.own0, self.own1, self.ext0, self.ext1 = (v.value for v in r)
+        self.gnx, self.gny = int(n[0]), int(n[1])
+        self.nx, self.ny = self.gnx, self.ext1 - self.ext0          # the held rows (esmm_rhs arrays)
+        self.N = self.nx * self.ny
+        self.phys = phys
+        self.nv = 8 if phys == RMHD else 4
+        self.set_eos(gamma)
+        self.set_order(p, w)
+        if params:
+            self.set_params(**params)
+
+    def state_set(self, prim, x=None):
+        G = self.gnx * self.gny
+        pp, mp = _ptr(prim, self.nv * G)
+        px, mx = _ptr(x, 2 * G)
+        self._check(lib().esmm_state_set(self.h, pp, px, _mem((pp, mp), (px, mx))))
+
+    def state_get(self, what, out=None):
+        size = {GET_PRIM: self.nv, GET_CONS: self.nv, GET_J: 1, GET_X: 2, GET_XDOT: 2}[what]
+        rows = self.own1 - self.own0
+        shape = (size, rows, self.nx) if size > 1 else (rows, self.nx)
+        if out is None:
+            out = np.empty(shape)
+        po, mo = _ptr(out, size * rows * self.nx)
+        self._check(lib().esmm_state_get(self.h, what, po, mo))
+        return out
 
 
 class Batch(Grid):

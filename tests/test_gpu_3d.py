@@ -1,19 +1,22 @@
 """GPU (sm_103a) 3D RMHD path against the 3D FP64 oracle, element by element,
-through the C ABI (dim = 3 grids).  Tolerances as for 2D RMHD: the EC scheme
-to 1e-12, the ES scheme (through the eigen-system of the symmetrized
-Jacobian, eigenvectors resolved to ~eps/gap) to 1e-10.  At the full 128^3
+through the C ABI (dim = 3 grids).  Tolerances as for 2D RMHD: 1e-12, or,
+where the oracle's own output moves by more than 1e-13 when its input is
+perturbed at rounding level (the ES scheme's eigen-system resolves
+eigenvectors only to ~eps/gap, and the sign switch and cluster membership
+are discrete), ten times that measured self-sensitivity.  At the full 128^3
 blast size the oracle is too slow for the whole right-hand side, so there the
 GPU output is checked against properties the exact scheme has: the mirror
 symmetries of the problem, and a short run that stays admissible.
 
 Components are compared relative to their own max-norm, floored at 1e-8 of
 the largest component (a field that is zero up to rounding, as the
-transverse field of the blast early on, is compared at that scale).  ES_TOL:
-columns of the eigen-system whose speeds differ by just over the cluster
-tolerance 1e-5 carry ~eps/1e-5 ~ 2e-11 relative error on either side; with
-the amplification through the WENO weights and the flux differences,
-deviations up to ~1e-10 appear on random meshes (the blast at rest with
-B along x_1 puts near-degenerate speeds on every tilted interface)."""
+transverse field of the blast early on, is compared at that scale).  Columns
+of the eigen-system whose speeds differ by just over the cluster tolerance
+1e-5 carry ~eps/1e-5 ~ 2e-11 relative error on either side; amplified
+through the WENO weights and the flux differences, the oracle itself moves
+by ~7e-10 under 1e-14 input noise on the blast (at rest, B along x_1: near-
+degenerate speeds on every tilted interface), and by ~2e-12 on smooth data
+with WENO3."""
 import numpy as np
 import pytest
 
@@ -23,8 +26,20 @@ from paper_2107_12027_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
-ES_TOL = 1e-9
+ES_TOL = 1e-12
 FLOOR = 1e-8
+
+
+def _bound(fn, cons, seeds=2, eps=1e-14):
+    """max(ES_TOL, 10 x the oracle's self-sensitivity): the largest relative
+    change (as _rel) of fn(cons) under eps relative noise on cons."""
+    ref = fn(cons)
+    r = wl.rng(4343)
+    s = 0.0
+    for _ in range(seeds):
+        pert = np.ascontiguousarray(cons * (1.0 + eps * r.standard_normal(cons.shape)))
+        s = max(s, _rel(fn(pert), ref))
+    return max(ES_TOL, 10.0 * s)
 
 
 def _rel(a, b):
@@ -54,7 +69,8 @@ def test_rhs_parity_smooth_periodic_moving_mesh_3d(p, w):
     ref = oracle.rhs3(cfg, cons, J, x, xd)
     with g:
         got = g.rhs(cons, J, x, xd)
-    assert _rel(got[0], ref[0]) < (TOL if w == 0 else ES_TOL)
+    bound = TOL if w == 0 else _bound(lambda c: oracle.rhs3(cfg, c, J, x, xd)[0], cons)
+    assert _rel(got[0], ref[0]) < bound, bound
     assert _rel(got[1], ref[1]) < TOL
 
 
@@ -69,7 +85,8 @@ def test_rhs_parity_blast_outflow_random_mesh_3d(p, w):
     ref = oracle.rhs3(cfg, cons, J, x)
     with g:
         got = g.rhs(cons, J, x)
-    assert _rel(got[0], ref[0]) < (TOL if w == 0 else ES_TOL)
+    bound = TOL if w == 0 else _bound(lambda c: oracle.rhs3(cfg, c, J, x)[0], cons)
+    assert _rel(got[0], ref[0]) < bound, bound
     assert _rel(got[1], ref[1]) < TOL
 
 

@@ -1,13 +1,19 @@
 """GPU (sm_103a) RMHD path against the FP64 oracle, element by element,
 through the C ABI.
 
-The EC scheme (w = 0) is pure arithmetic and matches to 1e-12 relative.  The
-ES scheme goes through the eigen-system of the symmetrized RMHD Jacobian,
-whose eigenvectors are determined only to ~eps/gap by any algorithm when two
-wave speeds come close (Alfven and slow or fast waves where B_t or B_n
-vanishes); speeds closer than the cluster tolerance share a canonical basis
-on both sides.  Its tolerance, ES_TOL, covers the conditioning of the
-separated pairs just above that tolerance.
+Both schemes match the oracle to 1e-12 relative where the data allow it.
+The ES scheme goes through the eigen-system of the symmetrized RMHD
+Jacobian, whose eigenvectors are determined only to ~eps/gap by any
+algorithm when two wave speeds come close (Alfven and slow or fast waves
+where B_t or B_n vanishes), and through discrete decisions (the sign switch
+Y, cluster membership) that rounding can flip at degenerate states.  Where
+the oracle's own output moves by more than 1e-13 when its input is perturbed
+at rounding level (1e-14 relative), the bound is ten times that measured
+self-sensitivity: the GPU then agrees with the oracle as closely as the
+oracle agrees with itself.  (Building the device code without FMA
+contraction, to match the oracle's -ffp-contract=off, changed none of these
+differences by more than a factor 2: they are not an arithmetic-order
+effect.)
 """
 import numpy as np
 import pytest
@@ -18,8 +24,21 @@ from paper_2107_12027_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
-ES_TOL = 1e-10
+ES_TOL = 1e-12
 G43 = 4.0 / 3.0
+
+
+def _bound(fn, cons, seeds=2, eps=1e-14):
+    """max(ES_TOL, 10 x the oracle's self-sensitivity): the largest relative
+    change (per component, as _rel) of fn(cons) when cons is perturbed by
+    eps relative noise."""
+    ref = fn(cons)
+    r = wl.rng(4242)
+    s = 0.0
+    for _ in range(seeds):
+        pert = np.ascontiguousarray(cons * (1.0 + eps * r.standard_normal(cons.shape)))
+        s = max(s, _rel(fn(pert), ref))
+    return max(ES_TOL, 10.0 * s)
 
 
 def _rel(a, b):
@@ -139,13 +158,21 @@ def test_rk_step_parity_rotor():
     x, prim = wl.rotor_config(n)
     cfg, g = _pair(n, n, (1, 1), (-0.5, -0.5), (0.5, 0.5), 2, 5, alpha=800.0)
     cons, J = oracle.init_state(cfg, prim, x)
+
+    def steps(c, k):
+        cc, JJ, xx = c, J, x
+        for _ in range(k):
+            cc, JJ, xx, _dt = oracle.rk_step(cfg, cc, JJ, xx)
+        return cc
+    c0 = cons
     with g:
         g.state_set(prim, x)
-        for _ in range(3):
+        for k in range(3):
             cons, J, x, dt = oracle.rk_step(cfg, cons, J, x)
             dtg = g.rk_step()
             assert abs(dtg - dt) <= 1e-12 * dt
-            assert _rel(g.state_get(esmm.GET_CONS), cons) < ES_TOL
+            bound = _bound(lambda c: steps(c, k + 1), c0)
+            assert _rel(g.state_get(esmm.GET_CONS), cons) < bound, (k, bound)
             assert _rel(g.state_get(esmm.GET_J), J) < 1e-12
             assert _rel(g.state_get(esmm.GET_X), x) < 1e-12
 
@@ -160,7 +187,8 @@ def test_rotor_512_full_size_rhs():
     ref = oracle.rhs(cfg, cons, J, x)
     with g:
         got = g.rhs(cons, J, x)
-    assert _rel(got[0], ref[0]) < ES_TOL
+    bound = _bound(lambda c: oracle.rhs(cfg, c, J, x)[0], cons, seeds=1)
+    assert _rel(got[0], ref[0]) < bound, bound
     assert _rel(got[1], ref[1]) < TOL
 
 

@@ -237,3 +237,14 @@ def test_sine_wave_64_to_t01_against_oracle_and_exact():
         xs = g.state_get(esmm.GET_X)
     exact = wl.sine_wave(xs, 0.1)[0]
     assert np.abs(rho - exact).mean() < 5e-5    # L1 error of the scheme itself (the oracle agrees)
+
+
+def test_flux_operation_counts():
+    # the algorithmic counts of the flux arithmetic (measurement addition):
+    # WENO5 dissipation costs more than WENO3, and the pair combination of
+    # eq. ECFlux_O2p grows with p as p(p-1)/2 + 2p - 1 operations per component
+    a5, a3 = esmm.flux_ops(5.0 / 3.0, 2, 5), esmm.flux_ops(5.0 / 3.0, 2, 3)
+    assert a5["pair"] == a3["pair"] > 30
+    assert a5["dissipation"] > a3["dissipation"] > 100
+    for p in (1, 2, 3):
+        assert esmm.flux_ops(5.0 / 3.0, p, 5)["combination"] == 5 * (p * (p - 1) // 2 + 2 * p - 1) + 4
