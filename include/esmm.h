@@ -213,7 +213,7 @@ int esmm_slab_rows(const esmm_grid *g, int *own0, int *own1, int *ext0, int *ext
  * dt <= 0 selects the step of eq. cfl with that mesh velocity in the spectral
  * radius: dt solves dt sum_k max_i rho_{k,i} = CFL with rho the spectral
  * radius of d(F_k)/d(JU) including the temporal metric (solved by Newton's
- * method on the convex piecewise-linear left side, at most 8 evaluations,
+ * method on the convex piecewise-linear left side, at most 6 evaluations,
  * else the safe bound (CFL - C_m)/S).  The limiter Delta tau is kept, unless
  * the displacement's own Courant number C_m = Delta tau sum_k max_i
  * |(x^[mu] - x^n).(J xi_k,x)|/J reaches CFL (no step exists then): there it is
@@ -307,11 +307,18 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
                  const double *mu, double *lam, int mem);
 
 /* Launch autotuner: for each kernel kind (node pass, pair fluxes, interface
- * fluxes, per-node kernels) time the candidate block sizes -- and, for
- * batches, the tile orders natural / largest problem first -- on the current
- * state, and keep the fastest.  Requires a state.  When block_sizes is given
- * it receives the 7 chosen launch domains' block sizes (negative: largest
- * first). */
+ * fluxes, per-node kernels) time the candidates on the current state and keep
+ * the fastest: block sizes, for batches the tile order (natural / largest
+ * problem first), and for the 2D RHD pair and interface kernels, per sweep
+ * direction, the tile shape (flat runs of sites along the sweep, or tiles of
+ * tx sites along x_1 by bs/tx along x_2) and whether a persistent grid (the
+ * blocks the SMs hold at once) strides over the (problem, tile) queue or
+ * each tile gets its own block.  Requires a state.  When block_sizes is given
+ * it receives ESMM_TUNE_SLOTS ints: [0, 13) the block size of each launch
+ * domain (negative: largest problem first), [13, 17) the tile shape of the
+ * tiled pair (x_1, x_2) and interface (x_1, x_2) launches: tx (0: flat runs)
+ * plus 1000 for a persistent grid. */
+#define ESMM_TUNE_SLOTS 17
 int esmm_tune(esmm_grid *g, int *block_sizes);
 
 /* FP64 totals of the grid's state: out[0] = sum J eta, the total entropy of

@@ -107,7 +107,7 @@ int oref_monitor(const oref_cfg *c, const double *cons, const double *J, double 
 int oref_set_threads(int n);
 
 /* Newton steps of oref_cfl_solve before it falls back to the safe bound. */
-#define OREF_CFL_NEWTON 8
+#define OREF_CFL_NEWTON 6
 
 /* eq. cfl with the mesh velocity in the spectral radius, solved for dt (the
  * reading and the method are stated at the definition).  a, bmin, bmax are

@@ -287,13 +287,19 @@ __global__ void k3_dt_newton(Geom3 g, double cfl, const double *__restrict__ cfl
     }
     __syncthreads();
     if (skip) return;
-    long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double v[3] = {-1.0, -1.0, -1.0}, sl[3] = {0.0, 0.0, 0.0};
-    if (id < g.N)
-        for (int d = 0; d < 3; ++d)
-            cfl_line(t_sh, tau_sh * cflb[d * g.N + id], cflb[(3 + d) * g.N + id], cflb[(6 + d) * g.N + id], v[d],
-                     sl[d]);
-    dt_newton_block<3>(ds, v, sl, blockIdx.x, 0, gridDim.x, part, cfl, dt_dev);
+    unsigned long long v[3] = {0ull, 0ull, 0ull}, sl[3] = {~0ull, ~0ull, ~0ull};
+    const long long base = (long long)blockIdx.x * blockDim.x * DT_NPT + threadIdx.x;
+    for (int r = 0; r < DT_NPT; ++r) {
+        const long long id = base + (long long)r * blockDim.x;
+        if (id < g.N)
+            for (int d = 0; d < 3; ++d) {
+                unsigned long long vk, sk;
+                cfl_line(t_sh, tau_sh * cflb[d * g.N + id], cflb[(3 + d) * g.N + id], cflb[(6 + d) * g.N + id], vk,
+                         sk);
+                vs_take(v[d], sl[d], vk, sk);
+            }
+    }
+    dt_newton_block<3>(ds, v, sl, blockIdx.x, 0, gridDim.x, (unsigned long long *)part, cfl, dt_dev);
 }
 
 __global__ void k3_time(const double *dt_dev, double *t_dev)
@@ -697,7 +703,8 @@ int mesh_and_dt3(esmm3 *g, double dt)
         k3_dt<<<1, 32, 0, g->st>>>(g->prm.cfl, dt, g->red, g->ds, g->dt_dev);
         if (!(dt > 0.0))
             for (int it = 0; it < DT_NEWTON; ++it)
-                k3_dt_newton<<<nb, BS3, 0, g->st>>>(g->g, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev);
+                k3_dt_newton<<<nb3(g->g.N, BS3 * DT_NPT), BS3, 0, g->st>>>(g->g, g->prm.cfl, g->cflb, g->red, g->ds,
+                                                                          g->npart, g->dt_dev);
     }
     Prof3 pr_(g, ESMM_KIND_MESH);
     k3_mesh_xdot<<<nb3(3 * g->g.N), BS3, 0, g->st>>>(g->g, g->x, src, g->red, g->dt_dev, g->xdot);

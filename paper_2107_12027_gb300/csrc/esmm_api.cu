@@ -34,7 +34,12 @@ using namespace esmm;
 
 namespace {
 // launch domains: which elements of each problem a kernel covers
-enum { D_PAD = 0, D_PAIR0, D_PAIR1, D_IFACE0, D_IFACE1, D_NODE, D_NODE2, D_MTILE, ND };
+// (D_TPAIR*, D_TIFACE*: the tiled launches of the RHD pair and interface
+// kernels of the forward step, whose tile shape and persistence the tuner
+// picks; the flat D_PAIR*, D_IFACE* serve the adjoint and RMHD kernels)
+enum { D_PAD = 0, D_PAIR0, D_PAIR1, D_IFACE0, D_IFACE1, D_NODE, D_NODE2, D_MTILE, D_NEWTON,
+       D_TPAIR0, D_TPAIR1, D_TIFACE0, D_TIFACE1, ND };
+static_assert(ND + 4 == ESMM_TUNE_SLOTS, "esmm_tune reports every domain's block size and four tile shapes");
 }  // namespace
 
 struct esmm_grid {
@@ -84,6 +89,9 @@ struct esmm_grid {
     // launch domains: block size and tile order per kind (autotuned)
     int bs[ND];
     int order_lpt[ND];               // 1: largest problems first
+    int tx[ND];                      // tile shape of the tiled flux launches (0: flat runs)
+    int persist[ND];                 // 1: a persistent grid strides over the tiles
+    int sms;                         // SMs of the grid's device
     int2 *tiles[ND];
     unsigned nblk[ND];
     size_t tiles_cap[ND];
@@ -198,34 +206,50 @@ long long dom_count(const Geom &G, int kind, int p)
 {
     switch (kind) {
     case D_PAD: return G.P;
-    case D_PAIR0: return (long long)(G.nx + p) * G.ny;
-    case D_PAIR1: return (long long)(G.ny + p) * G.nx;
-    case D_IFACE0: return (long long)(G.nx + 1) * G.ny;
-    case D_IFACE1: return (long long)(G.ny + 1) * G.nx;
+    case D_PAIR0: case D_TPAIR0: return (long long)(G.nx + p) * G.ny;
+    case D_PAIR1: case D_TPAIR1: return (long long)(G.ny + p) * G.nx;
+    case D_IFACE0: case D_TIFACE0: return (long long)(G.nx + 1) * G.ny;
+    case D_IFACE1: case D_TIFACE1: return (long long)(G.ny + 1) * G.nx;
     case D_NODE: return G.N;
     case D_MTILE:   // one block of MT_THREADS per MT_TX x MT_TY tile
         return (long long)((G.nx + MT_TX - 1) / MT_TX) * ((G.ny + MT_TY - 1) / MT_TY) * MT_THREADS;
+    case D_NEWTON:  // DT_NPT nodes per thread
+        return (G.N + DT_NPT - 1) / DT_NPT;
     default: return 2 * G.N;
     }
+}
+
+// tiles (blocks) of one problem in a domain: flat runs of bs sites, or, for
+// a tiled flux launch with tx > 0, tx x (bs / tx) tiles of the sweep's sites
+long long dom_blocks(const esmm_grid *g, const Geom &G, int kind)
+{
+    const int bs = g->bs[kind], tx = g->tx[kind];
+    if (tx > 0 && kind >= D_TPAIR0 && kind <= D_TIFACE1) {
+        const int dir = (kind == D_TPAIR1 || kind == D_TIFACE1) ? 1 : 0;
+        const int ext = kind <= D_TPAIR1 ? g->p : 1;
+        const long long nd = dir == 0 ? G.nx : G.ny, no = dir == 0 ? G.ny : G.nx;
+        const long long Ei = dir == 0 ? nd + ext : no, Ej = dir == 0 ? no : nd + ext, ty = bs / tx;
+        return ((Ei + tx - 1) / tx) * ((Ej + ty - 1) / ty);
+    }
+    return (long long)nblk(dom_count(G, kind, g->p), bs);
 }
 
 // (Re)build the block -> (problem, tile) map of one kind.
 int build_dom(esmm_grid *g, int kind)
 {
-    int bs = g->bs[kind];
     if (g->nprob == 1) {
-        g->nblk[kind] = nblk(dom_count(g->hpd[0].g, kind, g->p), bs);
+        g->nblk[kind] = (unsigned)dom_blocks(g, g->hpd[0].g, kind);
         return ESMM_OK;
     }
     std::vector<int> order(g->nprob);
     std::iota(order.begin(), order.end(), 0);
     if (g->order_lpt[kind])
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return dom_count(g->hpd[a].g, kind, g->p) > dom_count(g->hpd[b].g, kind, g->p);
+            return dom_blocks(g, g->hpd[a].g, kind) > dom_blocks(g, g->hpd[b].g, kind);
         });
     std::vector<int2> map;
     for (int b : order) {
-        long long nb = (long long)nblk(dom_count(g->hpd[b].g, kind, g->p), bs);
+        long long nb = dom_blocks(g, g->hpd[b].g, kind);
         for (long long k = 0; k < nb; ++k) map.push_back(make_int2(b, (int)k));
     }
     if (map.size() > g->tiles_cap[kind]) {
@@ -260,6 +284,16 @@ LaunchDom dom(const esmm_grid *g, int kind)
     L.pa.one = g->hpd[0];
     L.nblk = g->nblk[kind];
     L.bs = g->bs[kind];
+    if (kind >= D_TPAIR0 && kind <= D_TIFACE1) {
+        L.tx = g->tx[kind];
+        L.ntiles = g->nblk[kind];
+        if (g->persist[kind]) {   // as many blocks as the SMs hold at once
+            const int k = kind <= D_TPAIR1 ? 0 : 1;
+            const int per_sm = g->prm.precision == ESMM_MIXED ? flux_occupancy_f32(k, g->p, g->w, L.bs)
+                                                               : flux_occupancy_f64(k, g->p, g->w, L.bs);
+            L.nblk = (unsigned)std::min<long long>(L.ntiles, (long long)per_sm * g->sms);
+        }
+    }
     return L;
 }
 
@@ -318,8 +352,10 @@ void fluxes(esmm_grid *g)
     Phys ph = phys(g);
     bool f32 = g->prm.precision == ESMM_MIXED;
     for (int dir = 0; dir < 2; ++dir) {
-        LaunchDom Lp = dom(g, dir == 0 ? D_PAIR0 : D_PAIR1), Li = dom(g, dir == 0 ? D_IFACE0 : D_IFACE1);
-        if (g->phys == ESMM_RMHD) {   // two-point fluxes summed inside the interface kernel
+        const bool rmhd = g->phys == ESMM_RMHD;
+        LaunchDom Lp = dom(g, dir == 0 ? D_TPAIR0 : D_TPAIR1);
+        LaunchDom Li = dom(g, rmhd ? (dir == 0 ? D_IFACE0 : D_IFACE1) : (dir == 0 ? D_TIFACE0 : D_TIFACE1));
+        if (rmhd) {   // two-point fluxes summed inside the interface kernel
             Prof pr_(g, ESMM_KIND_IFACE);
             if (f32) launch_iface_mhd_f32(Li, ph, g->q, g->iflux, dir, g->st);
             else launch_iface_mhd(Li, ph, g->q, g->iflux, dir, g->st);
@@ -386,7 +422,7 @@ void step_dt(esmm_grid *g, double dt, bool moving)
         k_dt<<<nprob_blocks(g), 128, 0, g->st>>>(g->nprob, g->prm.cfl, dt, g->red, g->ds, g->dt_dev);
     }
     if (dt > 0.0 || !moving) return;
-    LaunchDom L = dom(g, D_NODE);
+    LaunchDom L = dom(g, D_NEWTON);
     for (int it = 0; it < DT_NEWTON; ++it) {
         Prof pr_(g, ESMM_KIND_OTHER);
         k_dt_newton<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->prm.cfl, g->cflb, g->red, g->ds, g->npart, g->dt_dev,
@@ -748,7 +784,13 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     g->prm.mu = 10;
     g->prm.move_mesh = 1;
     g->prm.precision = ESMM_FP64;
-    for (int k = 0; k < ND; ++k) g->bs[k] = (k >= D_PAIR0 && k <= D_IFACE1) ? 128 : BS;
+    for (int k = 0; k < ND; ++k) {
+        g->bs[k] = ((k >= D_PAIR0 && k <= D_IFACE1) || k >= D_TPAIR0) ? 128 : BS;
+        g->tx[k] = 0;
+        g->persist[k] = 0;
+    }
+    if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev) != cudaSuccess || g->sms < 1)
+        g->sms = 1;
 
     size_t N = (size_t)g->Ntot, P = (size_t)g->Ptot, d = sizeof(double), nv = (size_t)g->nv;
     size_t nb_max = (size_t)(N / 64 + (size_t)nprob + 64);   // node-domain blocks at >= 64 threads
@@ -1015,11 +1057,58 @@ int tune(esmm_grid *g)
     run_node();
     struct Cand { int kind; int kind2; std::vector<int> bs; };
     std::vector<Cand> cands = {{D_PAD, D_PAD, {128, 256, 512}},
-                               {D_PAIR0, D_PAIR1, {64, 128}},
-                               {D_IFACE0, D_IFACE1, {64, 128}},
                                {D_NODE, D_NODE2, {128, 256, 512}}};
+    if (g->phys == ESMM_RMHD) cands.push_back({D_IFACE0, D_IFACE1, {64, 128}});
     Phys ph = phys(g);
     bool f32 = g->prm.precision == ESMM_MIXED;
+    if (g->phys == ESMM_RHD) {
+        // the tiled pair and interface launches, each direction on its own:
+        // block size x tile shape (flat runs, or tx sites along x_1 by bs / tx
+        // along x_2) x one block per tile or a persistent grid (x the tile
+        // order of a batch)
+        fluxes(g);   // pair fluxes in place for the interface timings
+        for (int kind = D_TPAIR0; kind <= D_TIFACE1; ++kind) {
+            const int dir = (kind == D_TPAIR1 || kind == D_TIFACE1) ? 1 : 0;
+            const bool pairs = kind <= D_TPAIR1;
+            std::vector<int> orders = g->nprob > 1 ? std::vector<int>{0, 1} : std::vector<int>{0};
+            float best = 1e30f;
+            int bb = g->bs[kind], bt = g->tx[kind], bp = g->persist[kind], bo = g->order_lpt[kind];
+            for (int bs : {64, 128})
+                for (int tx : {0, 8, 16, 32, 64, 128}) {
+                    if (tx > bs) continue;
+                    for (int per : {0, 1})
+                        for (int ord : orders) {
+                            g->bs[kind] = bs;
+                            g->tx[kind] = tx;
+                            g->persist[kind] = per;
+                            g->order_lpt[kind] = ord;
+                            if ((rc = build_dom(g, kind))) return rc;
+                            const float ms = time_it([&]() {
+                                LaunchDom L = dom(g, kind);
+                                if (pairs) {
+                                    if (f32) launch_pairs_f32(L, ph, g->q, g->q32, g->pairs, dir, g->st);
+                                    else launch_pairs_f64(L, ph, g->q, nullptr, g->pairs, dir, g->st);
+                                } else {
+                                    if (f32) launch_iface_f32(L, ph, g->q, g->q32, g->pairs, g->iflux, dir, g->st);
+                                    else launch_iface_f64(L, ph, g->q, nullptr, g->pairs, g->iflux, dir, g->st);
+                                }
+                            });
+                            if (ms < best) {
+                                best = ms;
+                                bb = bs;
+                                bt = tx;
+                                bp = per;
+                                bo = ord;
+                            }
+                        }
+                }
+            g->bs[kind] = bb;
+            g->tx[kind] = bt;
+            g->persist[kind] = bp;
+            g->order_lpt[kind] = bo;
+            if ((rc = build_dom(g, kind))) return rc;
+        }
+    }
     for (auto &c : cands) {
         std::vector<int> orders = g->nprob > 1 ? std::vector<int>{0, 1} : std::vector<int>{0};
         float best = 1e30f;
@@ -1287,7 +1376,7 @@ int slab_newton(esmm_grid *g)
     DtSolve S;
     CK(cudaMemcpyAsync(&S, g->ds, sizeof S, cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
-    LaunchDom L = dom(g, D_NODE);
+    LaunchDom L = dom(g, D_NEWTON);
     double *vs_dev = g->vs_dev;
     if (S.done) return ESMM_OK;   // ended in the set-up (no mesh motion): dt_dev holds the step
     double dt = 0.0;
@@ -1928,8 +2017,11 @@ int esmm_tune(esmm_grid *g, int *block_sizes)
     if (!g) return ESMM_ERR_ARG;
     int rc = tune(g);
     if (rc) return rc;
-    if (block_sizes)
+    if (block_sizes) {
         for (int k = 0; k < ND; ++k) block_sizes[k] = g->bs[k] * (g->order_lpt[k] ? -1 : 1);
+        for (int k = 0; k < 4; ++k)   // tile shapes of the tiled pair / interface launches, x_1 then x_2
+            block_sizes[ND + k] = g->tx[D_TPAIR0 + k] + (g->persist[D_TPAIR0 + k] ? 1000 : 0);
+    }
     return ESMM_OK;
 }
 

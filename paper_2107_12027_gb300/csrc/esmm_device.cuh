@@ -68,6 +68,47 @@ __device__ __forceinline__ int locate(const ProbArg &pa, ProbDesc &D, long long 
     return 0;
 }
 
+// locate() for tile t of a strided launch (the block -> tile map of a
+// batch, or tile t itself)
+__device__ __forceinline__ int locate_tile(const ProbArg &pa, long long t, ProbDesc &D, long long &local_block)
+{
+    if (pa.tiles) {
+        int2 tt = pa.tiles[t];
+        D = pa.pd[tt.x];
+        local_block = tt.y;
+        return tt.x;
+    }
+    D = pa.one;
+    local_block = t;
+    return 0;
+}
+
+// The site (i, j) of thread threadIdx.x in tile lb of a sweep of direction
+// dir over sites with ext extra positions before the first node along the
+// sweep (p node pairs, 1 interface).  tx = 0: tiles are flat runs along the
+// sweep's storage order; tx > 0: tiles of tx sites along x_1 by
+// blockDim.x / tx along x_2.  false: no site (ragged tile).
+__device__ __forceinline__ bool sweep_site(const Geom &g, int dir, int ext, int tx, long long lb, int &i, int &j)
+{
+    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
+    if (tx == 0) {
+        const long long idx = lb * blockDim.x + threadIdx.x;
+        if (idx >= (long long)(nd + ext) * no) return false;
+        if (dir == 0) { j = (int)(idx / (nd + ext)); i = (int)(idx % (nd + ext)) - ext; }
+        else { i = (int)(idx % no); j = (int)(idx / no) - ext; }
+        return true;
+    }
+    const int ty = blockDim.x / tx;
+    const int Ei = dir == 0 ? nd + ext : no, Ej = dir == 0 ? no : nd + ext;
+    const long long nbi = (Ei + tx - 1) / tx;
+    const int ii = (int)(lb % nbi) * tx + (int)threadIdx.x % tx;
+    const int jj = (int)(lb / nbi) * ty + (int)threadIdx.x / tx;
+    if (ii >= Ei || jj >= Ej) return false;
+    i = dir == 0 ? ii - ext : ii;
+    j = dir == 0 ? jj : jj - ext;
+    return true;
+}
+
 struct Phys {
     double gamma;
     double gm1i;      // 1 / (Gamma - 1), once per launch

@@ -159,26 +159,23 @@ __device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho
     diss[3] = hl * d[3];
 }
 
-// anchors A in [-P, n_dir - 1] along the sweep, every line of the other index
+// anchors A in [-P, n_dir - 1] along the sweep, every line of the other
+// index: the sites of tile t (sweep_site)
 template <typename R, int P>
-__global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double *__restrict__ q,
-                                               const float *__restrict__ q32, R *__restrict__ pairs, int dir)
+__device__ __forceinline__ void pairs_tile(const ProbArg &pa, const Phys &ph, const double *__restrict__ q,
+                                           const float *__restrict__ q32, R *__restrict__ pairs, int dir, int tx,
+                                           long long t)
 {
     constexpr bool F32 = std::is_same<R, float>::value;
     ProbDesc D;
     long long lb;
-    locate(pa, D, lb);
+    locate_tile(pa, t, D, lb);
     const Geom &g = D.g;
     q += (long long)NQ * D.op;
     if (F32) q32 += (long long)NQ32 * D.op;
     pairs += (long long)2 * PMAX * 4 * D.op;
-    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
-    const long long count = (long long)(nd + P) * no;
-    const long long idx = lb * blockDim.x + threadIdx.x;
-    if (idx >= count) return;
     int i, j;
-    if (dir == 0) { j = (int)(idx / (nd + P)); i = (int)(idx % (nd + P)) - P; }
-    else { i = (int)(idx % no); j = (int)(idx / no) - P; }
+    if (!sweep_site(g, dir, P, tx, lb, i, j)) return;
     const long long c0 = pidx(g, i, j);
     const long long sd = dir == 0 ? 1 : g.px;
     // metrics in the working precision: FP64 node arrays or their FP32 copies
@@ -211,29 +208,35 @@ __global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double
     }
 }
 
-// interfaces between left node L in [-1, n_dir - 1] and L + 1
+// the blocks stride over the ntiles tiles (one tile each when the grid has
+// ntiles blocks; a persistent grid when it has fewer)
+template <typename R, int P>
+__global__ void __launch_bounds__(128) k_pairs(ProbArg pa, Phys ph, const double *__restrict__ q,
+                                               const float *__restrict__ q32, R *__restrict__ pairs, int dir, int tx,
+                                               long long ntiles)
+{
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) pairs_tile<R, P>(pa, ph, q, q32, pairs, dir, tx, t);
+}
+
+// interfaces between left node L in [-1, n_dir - 1] and L + 1: the sites of
+// tile t (sweep_site)
 template <typename R, int P, int WW>
-__global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double *__restrict__ q,
-                                               const float *__restrict__ q32, const R *__restrict__ pairs,
-                                               R *__restrict__ iflux, int dir)
+__device__ __forceinline__ void iface_tile(const ProbArg &pa, const Phys &ph, const double *__restrict__ q,
+                                           const float *__restrict__ q32, const R *__restrict__ pairs,
+                                           R *__restrict__ iflux, int dir, int tx, long long t)
 {
     constexpr bool F32 = std::is_same<R, float>::value;
     using MT = typename std::conditional<F32, float, double>::type;
     ProbDesc D;
     long long lb;
-    locate(pa, D, lb);
+    locate_tile(pa, t, D, lb);
     const Geom &g = D.g;
     q += (long long)NQ * D.op;
     if (F32) q32 += (long long)NQ32 * D.op;
     pairs += (long long)2 * PMAX * 4 * D.op;
     iflux += (long long)2 * 5 * D.op;
-    const int nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
-    const long long count = (long long)(nd + 1) * no;
-    const long long idx = lb * blockDim.x + threadIdx.x;
-    if (idx >= count) return;
     int i, j;
-    if (dir == 0) { j = (int)(idx / (nd + 1)); i = (int)(idx % (nd + 1)) - 1; }
-    else { i = (int)(idx % no); j = (int)(idx / no) - 1; }
+    if (!sweep_site(g, dir, 1, tx, lb, i, j)) return;
     const long long c0 = pidx(g, i, j);
     const long long sd = dir == 0 ? 1 : g.px;
     // metrics in the working precision: FP64 node arrays or their FP32 copies
@@ -294,18 +297,48 @@ __global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double
     out[4 * g.P] = (R)Ft;
 }
 
+template <typename R, int P, int WW>
+__global__ void __launch_bounds__(128) k_iface(ProbArg pa, Phys ph, const double *__restrict__ q,
+                                               const float *__restrict__ q32, const R *__restrict__ pairs,
+                                               R *__restrict__ iflux, int dir, int tx, long long ntiles)
+{
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x)
+        iface_tile<R, P, WW>(pa, ph, q, q32, pairs, iflux, dir, tx, t);
+}
+
+inline long long tiles_of(const LaunchDom &L) { return L.ntiles < 0 ? (long long)L.nblk : L.ntiles; }
+
 template <typename R, int P>
 static void launch_pairs_p(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, R *pairs, int dir,
                            cudaStream_t st)
 {
-    k_pairs<R, P><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, q32, pairs, dir);
+    k_pairs<R, P><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, q32, pairs, dir, L.tx, tiles_of(L));
 }
 
 template <typename R, int P, int WW>
 static void launch_iface_pw(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, const R *pairs,
                             R *iflux, int dir, cudaStream_t st)
 {
-    k_iface<R, P, WW><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, q32, pairs, iflux, dir);
+    k_iface<R, P, WW><<<L.nblk, L.bs, 0, st>>>(L.pa, ph, q, q32, pairs, iflux, dir, L.tx, tiles_of(L));
+}
+
+// resident blocks per SM of one instance at block size bs
+template <typename K>
+static int occ(K kern, int bs)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, bs, 0) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
+template <typename R>
+int flux_occupancy_t(int kind, int p, int w, int bs)
+{
+    if (kind == 0) return p == 1 ? occ(k_pairs<R, 1>, bs) : (p == 2 ? occ(k_pairs<R, 2>, bs) : occ(k_pairs<R, 3>, bs));
+    auto pick = [&](auto k0, auto k3, auto k5) { return w == 0 ? occ(k0, bs) : (w == 3 ? occ(k3, bs) : occ(k5, bs)); };
+    if (p == 1) return pick(k_iface<R, 1, 0>, k_iface<R, 1, 3>, k_iface<R, 1, 5>);
+    if (p == 2) return pick(k_iface<R, 2, 0>, k_iface<R, 2, 3>, k_iface<R, 2, 5>);
+    return pick(k_iface<R, 3, 0>, k_iface<R, 3, 3>, k_iface<R, 3, 5>);
 }
 
 template <typename R>

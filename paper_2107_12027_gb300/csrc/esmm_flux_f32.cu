@@ -15,4 +15,6 @@ void launch_iface_f32(const LaunchDom &L, const Phys &ph, const double *q, const
     launch_iface_t<float>(L, ph, q, q32, pairs, iflux, dir, st);
 }
 
+int flux_occupancy_f32(int kind, int p, int w, int bs) { return flux_occupancy_t<float>(kind, p, w, bs); }
+
 }  // namespace esmm

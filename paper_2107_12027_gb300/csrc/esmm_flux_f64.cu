@@ -15,4 +15,6 @@ void launch_iface_f64(const LaunchDom &L, const Phys &ph, const double *q, const
     launch_iface_t<double>(L, ph, q, q32, pairs, iflux, dir, st);
 }
 
+int flux_occupancy_f64(int kind, int p, int w, int bs) { return flux_occupancy_t<double>(kind, p, w, bs); }
+
 }  // namespace esmm

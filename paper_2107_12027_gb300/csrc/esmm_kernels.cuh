@@ -355,7 +355,8 @@ __global__ void k_dt(int nprob, double cfl, double dt_fixed, unsigned long long 
 
 // One Newton evaluation of the step solve (esmm_reduce.cuh) over the nodes
 // of every problem still solving: cflb rows 0, 1 hold a_{k,i}, rows 2..5 the
-// speed bounds (per problem at 6 D.on).  part: [blocks][2][2].
+// speed bounds (per problem at 6 D.on).  part: [blocks][2][2].  A block
+// covers blockDim.x * DT_NPT nodes.
 __global__ void k_dt_newton(ProbArg pa, double cfl, const double *__restrict__ cflb,
                             const unsigned long long *red, DtSolve *ds, double *part, double *dt_dev,
                             double *vs_out)
@@ -374,15 +375,23 @@ __global__ void k_dt_newton(ProbArg pa, double cfl, const double *__restrict__ c
     }
     __syncthreads();
     if (skip) return;
-    long long id = lb * blockDim.x + threadIdx.x;
     cflb += 6 * D.on;
-    double v[2] = {-1.0, -1.0}, sl[2] = {0.0, 0.0};
-    if (id < g.N && owned_row(g, (int)(id / g.nx)))
-        for (int k = 0; k < 2; ++k)
-            cfl_line(t_sh, tau_sh * cflb[k * g.N + id], cflb[(2 + k) * g.N + id], cflb[(4 + k) * g.N + id], v[k],
-                     sl[k]);
-    const long long nb = (g.N + blockDim.x - 1) / blockDim.x;
-    dt_newton_block<2>(S, v, sl, blockIdx.x, (long long)blockIdx.x - lb, nb, part, cfl, dt_dev + b, vs_out);
+    unsigned long long v[2] = {0ull, 0ull}, sl[2] = {~0ull, ~0ull};
+    // DT_NPT nodes per thread, consecutive threads on consecutive nodes
+    const long long base = lb * blockDim.x * DT_NPT + threadIdx.x;
+    for (int r = 0; r < DT_NPT; ++r) {
+        const long long id = base + (long long)r * blockDim.x;
+        if (id < g.N && owned_row(g, (int)(id / g.nx)))
+            for (int k = 0; k < 2; ++k) {
+                unsigned long long vk, sk;
+                cfl_line(t_sh, tau_sh * cflb[k * g.N + id], cflb[(2 + k) * g.N + id], cflb[(4 + k) * g.N + id],
+                         vk, sk);
+                vs_take(v[k], sl[k], vk, sk);
+            }
+    }
+    const long long nb = (g.N + (long long)blockDim.x * DT_NPT - 1) / ((long long)blockDim.x * DT_NPT);
+    dt_newton_block<2>(S, v, sl, blockIdx.x, (long long)blockIdx.x - lb, nb, (unsigned long long *)part, cfl,
+                       dt_dev + b, vs_out);
 }
 
 __global__ void k_time(int nprob, const double *dt_dev, double *t_dev)

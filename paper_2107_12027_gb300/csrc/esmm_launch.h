@@ -11,11 +11,22 @@
 namespace esmm {
 
 // Launch domain of one kernel: the problem addressing and the grid shape.
+// The RHD flux kernels also take a tile shape (tx threads along x_1 by
+// bs / tx along x_2; 0: one flat run of sites along the sweep) and the
+// number of tiles, over which a grid of nblk <= ntiles blocks strides
+// (nblk < ntiles: a persistent grid).  ntiles < 0 means nblk.
 struct LaunchDom {
     ProbArg pa;
     unsigned nblk;
     int bs;
+    int tx = 0;
+    long long ntiles = -1;
 };
+
+// resident blocks per SM of the RHD flux kernels at block size bs (the
+// persistent grid of a tiled launch): kind 0 pairs, 1 interfaces
+int flux_occupancy_f64(int kind, int p, int w, int bs);
+int flux_occupancy_f32(int kind, int p, int w, int bs);
 
 struct Phys;
 

@@ -118,7 +118,8 @@ __device__ __forceinline__ double bits_to_double(unsigned long long b) { return 
 // last of the problem's blocks to finish reduces their partial results
 // (in any order: the (value, slope) maximum below does not depend on it)
 // and advances the iterate.
-constexpr int DT_NEWTON = 8;
+constexpr int DT_NEWTON = 6;
+constexpr int DT_NPT = 8;   // nodes per thread of a Newton evaluation (fewer blocks, a shorter tail)
 
 struct DtSolve {
     double t, t_safe;    // current iterate, the fallback
@@ -127,18 +128,30 @@ struct DtSolve {
     int pad_;
 };
 
-// the line of one node at t that attains its max(t bmax - ta, ta - t bmin),
-// as (value, slope); the smaller slope where the two lines tie
-__device__ __forceinline__ void cfl_line(double t, double ta, double bmin, double bmax, double &v, double &s)
+// The (value, slope) maximum -- the larger value, on equal values the
+// smaller slope -- reduced on order-preserving 64-bit integer keys: the
+// values are >= 0, so their bit patterns order like them (a NaN maps to 0
+// and never wins), and the slopes' bits are mapped so that unsigned order is
+// their order.  On this GPU FP64 compares run on the FP64 pipe, at a small
+// fraction of the integer pipes' rate.  A total order, so reductions in any
+// order agree.  No site: (0, ~0).  (The values max(t bmax - ta, ta - t bmin)
+// are never negative: the two lines sum to t (bmax - bmin) >= 0.)
+__device__ __forceinline__ unsigned long long vkey(double v)
 {
-    const double up = t * bmax - ta, dn = ta - t * bmin;
-    v = up > dn ? up : dn;
-    s = up > dn ? bmax : (dn > up ? -bmin : fmin(bmax, -bmin));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull || (b >> 63)) ? 0ull : b;   // NaN, -0
 }
-
-// the larger value, and on equal values the smaller slope (a NaN value never
-// wins): a total order, so reductions in any order agree
-__device__ __forceinline__ void vs_take(double &v, double &s, double v2, double s2)
+__device__ __forceinline__ unsigned long long skey(double s)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double skey_inv(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+__device__ __forceinline__ void vs_take(unsigned long long &v, unsigned long long &s, unsigned long long v2,
+                                        unsigned long long s2)
 {
     if (v2 > v || (v2 == v && s2 < s)) {
         v = v2;
@@ -146,11 +159,22 @@ __device__ __forceinline__ void vs_take(double &v, double &s, double v2, double 
     }
 }
 
-// block-wide (value, slope) maximum of NDIR pairs; valid in thread 0
-template <int NDIR>
-__device__ void block_vs_max(double (&v)[NDIR], double (&s)[NDIR])
+// the line of one node at t that attains its max(t bmax - ta, ta - t bmin),
+// as the keys of (value, slope); the smaller slope where the two lines tie
+__device__ __forceinline__ void cfl_line(double t, double ta, double bmin, double bmax, unsigned long long &v,
+                                         unsigned long long &s)
 {
-    __shared__ double shv[32][NDIR], shs[32][NDIR];
+    const double up = t * bmax - ta, dn = ta - t * bmin;
+    const unsigned long long ku = skey(up), kd = skey(dn), kmax = skey(bmax), kmin = skey(-bmin);
+    v = vkey(ku > kd ? up : dn);
+    s = ku > kd ? kmax : (kd > ku ? kmin : (kmax < kmin ? kmax : kmin));
+}
+
+// block-wide (value, slope) maximum of NDIR key pairs; valid in thread 0
+template <int NDIR>
+__device__ void block_vs_max(unsigned long long (&v)[NDIR], unsigned long long (&s)[NDIR])
+{
+    __shared__ unsigned long long shv[32][NDIR], shs[32][NDIR];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NDIR; ++k)
@@ -166,8 +190,8 @@ __device__ void block_vs_max(double (&v)[NDIR], double (&s)[NDIR])
     if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < NDIR; ++k) {
-            v[k] = lane < nw ? shv[lane][k] : -1.0;
-            s[k] = lane < nw ? shs[lane][k] : 0.0;
+            v[k] = lane < nw ? shv[lane][k] : 0ull;
+            s[k] = lane < nw ? shs[lane][k] : ~0ull;
             for (int o = 16; o > 0; o >>= 1)
                 vs_take(v[k], s[k], __shfl_xor_sync(0xffffffffu, v[k], o), __shfl_xor_sync(0xffffffffu, s[k], o));
         }
@@ -204,8 +228,9 @@ __host__ __device__ inline void dt_newton_update(DtSolve *S, double g, double sl
 // problem's (value, slope) per direction to vs_out[2k], vs_out[2k + 1] for
 // the host to combine over the slabs, and leaves S as it is.
 template <int NDIR>
-__device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR], long long gblock, long long first,
-                                long long nb, double *part, double cfl, double *dt_out, double *vs_out = nullptr)
+__device__ void dt_newton_block(DtSolve *S, unsigned long long (&v)[NDIR], unsigned long long (&s)[NDIR],
+                                long long gblock, long long first, long long nb, unsigned long long *part, double cfl,
+                                double *dt_out, double *vs_out = nullptr)
 {
     __shared__ int last;
     block_vs_max<NDIR>(v, s);
@@ -223,8 +248,8 @@ __device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR]
     __threadfence();
 #pragma unroll
     for (int k = 0; k < NDIR; ++k) {
-        v[k] = -1.0;
-        s[k] = 0.0;
+        v[k] = 0ull;
+        s[k] = ~0ull;
     }
     for (long long q = threadIdx.x; q < nb; q += blockDim.x)
 #pragma unroll
@@ -236,8 +261,8 @@ __device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR]
         S->count = 0u;
 #pragma unroll
         for (int k = 0; k < NDIR; ++k) {
-            vs_out[2 * k] = v[k];
-            vs_out[2 * k + 1] = s[k];
+            vs_out[2 * k] = __longlong_as_double((long long)v[k]);
+            vs_out[2 * k + 1] = skey_inv(s[k]);
         }
         return;
     }
@@ -245,8 +270,8 @@ __device__ void dt_newton_block(DtSolve *S, double (&v)[NDIR], double (&s)[NDIR]
         double g = 0.0, slope = 0.0;
 #pragma unroll
         for (int k = 0; k < NDIR; ++k) {
-            g += v[k];
-            slope += s[k];
+            g += __longlong_as_double((long long)v[k]);
+            slope += skey_inv(s[k]);
         }
         S->count = 0u;
         dt_newton_update(S, g, slope, cfl, dt_out);

@@ -58,6 +58,7 @@ SYMBOLS = (
     "esmm_slab_create", "esmm_slab_rows",
 )
 SLAB_HALO = 16
+TUNE_SLOTS = 17
 OP_MAX, OP_MIN, OP_SUM = 0, 1, 2
 _dptr = ctypes.POINTER(ctypes.c_double)
 #: comm callbacks of esmm_slab_create (include/esmm.h esmm_comm)
@@ -439,9 +440,10 @@ class Grid:
         return lam
 
     def tune(self):
-        """Run the launch autotuner on the current state; returns the 7 chosen
-        block sizes (negative: largest problem first)."""
-        bs = (ctypes.c_int * 7)()
+        """Run the launch autotuner on the current state; returns the 13 chosen
+        block sizes (negative: largest problem first) and the 4 tile shapes of
+        the pair and interface launches (tx, + 1000 for a persistent grid)."""
+        bs = (ctypes.c_int * TUNE_SLOTS)()
         self._check(lib().esmm_tune(self.h, bs))
         return list(bs)
 

@@ -257,9 +257,9 @@ def test_stated_cpu_time_shares_follow_from_the_printed_times():
 
 def test_study_runs_the_papers_comparisons():
     # The UM-O5 against MM-O5 study of bench.py runs to the paper's final
-    # times on its MM-O5 meshes.  The fine UM-O5 mesh is the paper's for RP I,
-    # RP II and the blast (with the blast's coarse UM-O5 mesh); RP III's fine
-    # run, 600^2 in the paper, is 500^2 here, as for RP I and II.
+    # times on the paper's MM-O5 meshes and its fine UM-O5 meshes (500^2 for
+    # RP I and II, 600^2 for RP III), and for the blast also its coarse
+    # UM-O5 mesh.
     import bench
     d, rec = _data(), _records("paper_cpu_times.txt")
     for k in (1, 2, 3):
@@ -267,7 +267,7 @@ def test_study_runs_the_papers_comparisons():
         assert t_end == d["rp%d.t_end" % k][0]
         meshes = {(r[0], int(r[1].split("x")[0])) for r in rec["rp%d" % k] if r[0] != "stated_percent"}
         assert ("MM-O5", sizes[0]) in meshes
-        assert (("UM-O5", sizes[2]) in meshes) == (k != 3)
+        assert ("UM-O5", sizes[2]) in meshes
     sizes, t_end = bench.STUDY["blast"]
     assert t_end == d["blast2d.t_end"][0]
     meshes = {(r[0], int(r[1].split("x")[0])) for r in rec["blast2d"] if r[0] != "stated_percent"}

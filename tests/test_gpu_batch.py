@@ -74,7 +74,9 @@ def test_batch_problem_against_oracle_and_tuning_invariance():
         for k, pr in enumerate(probs):
             b.state_set(k, pr[5], pr[4])
         shapes = b.tune()
-        assert len(shapes) == 7 and all(abs(s) in (64, 128, 256, 512) for s in shapes)
+        assert len(shapes) == esmm.TUNE_SLOTS
+        assert all(abs(s) in (64, 128, 256, 512) for s in shapes[:13])
+        assert all(s % 1000 in (0, 8, 16, 32, 64, 128) and s // 1000 in (0, 1) for s in shapes[13:])
         b.advance(2)
         got = b.state_get(1, esmm.GET_CONS)
         totals = b.totals()
@@ -101,3 +103,22 @@ def test_graph_replay_equals_step_by_step():
                     b.rk_step(sync=False)
             res.append(b.state_get(0, esmm.GET_CONS))
     assert _rel(res[1], res[0]) < 1e-15
+
+
+@pytest.mark.parametrize("precision", [esmm.FP64, esmm.MIXED])
+def test_tile_shapes_and_persistent_grids_change_nothing(precision):
+    # each pair and interface is computed by one thread whatever tile holds
+    # it and whichever block of a persistent grid takes that tile: a tuned
+    # grid (tile shapes, persistence) steps bit for bit as an untuned one
+    x, prim = wl.riemann_config(72)
+    res = []
+    for tuned in (False, True):
+        with esmm.Grid((72, 72), (-1, -1), (1, 1), bc=(1, 1), p=2, w=5, alpha=1200.0, precision=precision) as g:
+            g.state_set(prim, x)
+            if tuned:
+                shapes = g.tune()
+                assert len(shapes) == esmm.TUNE_SLOTS
+            for _ in range(3):
+                g.rk_step()
+            res.append(g.state_get(esmm.GET_CONS))
+    assert np.array_equal(res[0], res[1])

@@ -8,8 +8,12 @@ undecomposed, through the C ABI:
     its own rows, bit for bit;
   * three SSP-RK3 steps with the adaptive mesh and the eq. cfl step leave
     every slab's own rows of cons, J and x, and every step size, equal to
-    the undecomposed run's bit for bit (periodic and outflow second
-    direction, RHD in both forms, RMHD);
+    the undecomposed run's bit for bit with an outflow second direction
+    (RHD in both forms, RMHD).  Across a periodic seam the halo rows hold
+    x_2 minus or plus the period, and the redundant mesh iteration on them
+    rounds differently from the owner's (the whole grid adds the period
+    only where it reads a ghost), so there the own rows agree to rounding
+    (1e-12 relative); with a static mesh they are bitwise again;
   * the totals (a sum over slabs) agree to rounding.
 """
 from concurrent.futures import ThreadPoolExecutor
@@ -67,7 +71,7 @@ def _slabs(nslab, n, lo, hi, bc, prim, x, steps, kw):
 
 
 CASES = [("riemann", 48, 80, 2, "fp64"), ("smooth", 40, 96, 3, "fp64"), ("riemann", 40, 66, 2, "mixed"),
-         ("rotor", 48, 64, 2, "fp64")]
+         ("rotor", 48, 64, 2, "fp64"), ("riemann", 40, 99, 3, "fp64")]
 
 
 @pytest.mark.parametrize("kind,nx,ny,nslab,form", CASES)
@@ -83,14 +87,23 @@ def test_slabs_step_bitwise_as_the_whole_grid(kind, nx, ny, nslab, form):
                    tot=g.totals())
     out = _slabs(nslab, (nx, ny), lo, hi, bc, prim, x, steps, kw)
     rows = []
+    seam = bc[1] == esmm.PERIODIC
+
+    def same(u, v):
+        if not seam:
+            return np.array_equal(u, v)
+        return np.abs(u - v).max() <= 1e-12 * np.abs(v).max()
     for s in range(nslab):
         o = out[s]
         a, b = o["own"]
         rows.append((a, b))
-        assert o["dts"] == dts, (s, o["dts"], dts)
-        assert np.array_equal(o["cons"], ref["cons"][:, a:b]), s
-        assert np.array_equal(o["J"], ref["J"][a:b]), s
-        assert np.array_equal(o["x"], ref["x"][:, a:b]), s
+        if seam:
+            assert np.allclose(o["dts"], dts, rtol=1e-12, atol=0), (s, o["dts"], dts)
+        else:
+            assert o["dts"] == dts, (s, o["dts"], dts)
+        assert same(o["cons"], ref["cons"][:, a:b]), s
+        assert same(o["J"], ref["J"][a:b]), s
+        assert same(o["x"], ref["x"][:, a:b]), s
         assert np.allclose(o["tot0"], tot0, rtol=1e-13, atol=0)
         assert np.allclose(o["tot"], ref["tot"], rtol=1e-13, atol=0)
     # the own rows tile the grid
