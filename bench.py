@@ -53,8 +53,8 @@ WORKLOAD = ("2D RHD four-quadrant Riemann problem, 400x400 nodes on [-1,1]^2, ou
 # (FP64) or fadd + fmul + 2 ffma (FP32), i.e. an add, a mul, or half an FMA,
 # including the FP64 instructions inside division, square-root and log
 # sequences.  The FP64 interface kernel (p = 2, WENO5) on the 400^2 Riemann
-# workload executes 1,396 per interface.
-FLOPS_PER_IFACE_F64 = 1396
+# workload executes 1,395 per interface.
+FLOPS_PER_IFACE_F64 = 1395
 # Unit counts for the derived peaks, reported beside the measured ones:
 # 4 FP64 flop/clk/SM and 256 FP32 flop/clk/SM at the 2070 MHz maximum clock.
 FP64_FLOP_PER_CLK_SM = 4
@@ -64,7 +64,7 @@ FP32_FLOP_PER_CLK_SM = 256
 TRAFFIC_IFACE_F64 = 23.48e6
 # The mixed form's interface kernel on the same workload: FP32 flops per
 # interface and DRAM bytes per launch.
-FLOPS_PER_IFACE_F32 = 1259
+FLOPS_PER_IFACE_F32 = 1253
 TRAFFIC_IFACE_F32 = 13.08e6
 # The same for the RMHD interface kernels at p = 2, WENO5: the FP64 2D kernel
 # on the 512^2 rotor (11,042 FP64 flops per interface; 1.021 GB of DRAM
@@ -79,6 +79,14 @@ FLOPS_PER_IFACE_MHD2_F32 = 10832
 TRAFFIC_IFACE_MHD2_F32 = 0.479e9
 FLOPS_PER_IFACE_MHD3 = 16409
 TRAFFIC_IFACE_MHD3 = 9.61e9
+# The fused sweep kernel (pair and interface fluxes in one launch) on the
+# same workload, from one capture of each form: executed flops per interface
+# (its pair fluxes included: 32 anchors per 31 interfaces) and DRAM bytes
+# per launch; None whenever the kernel has changed since.
+FLOPS_PER_SWEEP_F64 = 1685
+TRAFFIC_SWEEP_F64 = 13.11e6
+FLOPS_PER_SWEEP_F32 = 1475
+TRAFFIC_SWEEP_F32 = 11.74e6
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 # Algorithmic HBM bytes per node and RK stage of the whole step, fused to the
@@ -521,49 +529,50 @@ def run_gpu(args):
         dist.barrier()
     value = job_rate(n * n, K, world, total_ms)
     launches = int(sum(v[1] for v in prof.values()))
+    fused = g.get_params()["sweep"] != esmm.SWEEP_SPLIT   # untuned: AUTO runs the fused sweep
     g.close()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel: the FP64 interface kernel is bound by
-    # the FP64 pipe (no dense contraction, ~20 FP64 flop per byte)
+    # roofline of the dominant kernel, the flux kernel of a sweep (the fused
+    # sweep kernel, or the interface kernel when the pair and interface
+    # kernels run apart): bound by the FP64 pipe in the FP64 form (no dense
+    # contraction, ~20 FP64 flop per byte), by the FP32 pipes in the mixed one
     iface_ms, iface_n, iface_timed = prof["iface"]
     ifaces_per_launch = ((n + 1) * n + (n + 1) * n) / 2.0
     avg_launch_s = iface_ms * 1e-3 / max(iface_timed, 1)
-    roof = None
     # the method's operations per interface (the library's flux templates on
     # a counting type; each divide and root counts once) beside the executed ones
     ops = esmm.flux_ops(5.0 / 3.0, 2, 5)
-    alg = ops["dissipation"] + ops["combination"]
-    if args.form == "fp64":
-        peak, src = alu_peak("fp64")
-        ach = FLOPS_PER_IFACE_F64 * ifaces_per_launch / avg_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": TRAFFIC_IFACE_F64, "kernel": "k_iface<double,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
-                "share_of_step": iface_ms / total_ms, "peak_source": src,
-                "peak_derived": N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12,
-                "flops_basis": "executed FP64 operations per interface (ncu: dadd + dmul + 2 dfma), %d per "
-                               "interface" % FLOPS_PER_IFACE_F64,
-                "algorithmic": {"flops_per_interface": alg,
-                                "achieved": alg * ifaces_per_launch / avg_launch_s / 1e12,
-                                "frac": alg * ifaces_per_launch / avg_launch_s / 1e12 / peak,
-                                "basis": "esmm_flux_ops: ES dissipation %d + pair combination %d operations per "
-                                         "interface (add, mul, div, sqrt, rsqrt each 1)" % (ops["dissipation"],
-                                                                                            ops["combination"])}}
+    alg = ops["dissipation"] + ops["combination"] + (2 * ops["pair"] if fused else 0)
+    f64 = args.form == "fp64"
+    peak, src = alu_peak("fp64" if f64 else "fp32")
+    if fused:
+        flops = FLOPS_PER_SWEEP_F64 if f64 else FLOPS_PER_SWEEP_F32
+        traffic = TRAFFIC_SWEEP_F64 if f64 else TRAFFIC_SWEEP_F32
+        kname = "k_sweep<%s,2,5>" % ("double" if f64 else "float")
     else:
-        peak, src = alu_peak("fp32")
-        ach = FLOPS_PER_IFACE_F32 * ifaces_per_launch / avg_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": TRAFFIC_IFACE_F32, "kernel": "k_iface<float,2,5>", "avg_launch_ms": avg_launch_s * 1e3,
-                "share_of_step": iface_ms / total_ms, "peak_source": src,
-                "peak_derived": N_SM * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12,
-                "flops_basis": "executed FP32 operations per interface (ncu: fadd + fmul + 2 ffma), %d per "
-                               "interface" % FLOPS_PER_IFACE_F32,
-                "algorithmic": {"flops_per_interface": alg,
-                                "achieved": alg * ifaces_per_launch / avg_launch_s / 1e12,
-                                "frac": alg * ifaces_per_launch / avg_launch_s / 1e12 / peak}}
+        flops = FLOPS_PER_IFACE_F64 if f64 else FLOPS_PER_IFACE_F32
+        traffic = TRAFFIC_IFACE_F64 if f64 else TRAFFIC_IFACE_F32
+        kname = "k_iface<%s,2,5>" % ("double" if f64 else "float")
+    ach = flops * ifaces_per_launch / avg_launch_s / 1e12 if flops else None
+    prec = "FP64" if f64 else "FP32"
+    ops_names = "dadd + dmul + 2 dfma" if f64 else "fadd + fmul + 2 ffma"
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if ach else None, "traffic": traffic, "kernel": kname,
+            "avg_launch_ms": avg_launch_s * 1e3, "share_of_step": iface_ms / total_ms, "peak_source": src,
+            "peak_derived": N_SM * (FP64_FLOP_PER_CLK_SM if f64 else FP32_FLOP_PER_CLK_SM) * SM_MAX_MHZ * 1e6 / 1e12,
+            "flops_basis": ("executed %s operations per interface (ncu: %s), %d per interface"
+                            % (prec, ops_names, flops)) if flops else "not measured for this kernel",
+            "algorithmic": {"flops_per_interface": alg,
+                            "achieved": alg * ifaces_per_launch / avg_launch_s / 1e12,
+                            "frac": alg * ifaces_per_launch / avg_launch_s / 1e12 / peak,
+                            "basis": "esmm_flux_ops: ES dissipation %d + pair combination %d%s operations per "
+                                     "interface (add, mul, div, sqrt, rsqrt each 1)"
+                                     % (ops["dissipation"], ops["combination"],
+                                        " + two pair fluxes of %d" % ops["pair"] if fused else "")}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.form == "fp64" else "f32+f64",

@@ -96,7 +96,24 @@ typedef struct {
                           + alpha_lap |lap sigma|/max), the monitor of the
                           vortex examples of Sec. 6 (there sigma = rho,
                           alpha = 20, alpha_lap = 10); 0: eq. monitor   [0]   */
+    int sweep;         /* 2D RHD flux kernels of a sweep direction:
+                          ESMM_SWEEP_AUTO, ESMM_SWEEP_FUSED or
+                          ESMM_SWEEP_SPLIT (below)                     [AUTO] */
 } esmm_params;
+
+/* The flux kernels of one 2D RHD sweep direction (esmm_params.sweep).  Both
+ * compute the same interface fluxes bit for bit:
+ *   ESMM_SWEEP_FUSED: one launch; the pair fluxes of a tile and its node
+ *                     data stay in shared memory;
+ *   ESMM_SWEEP_SPLIT: a pair-flux launch writing every two-point flux to
+ *                     global memory, then an interface launch reading them;
+ *   ESMM_SWEEP_AUTO:  the fused kernel until esmm_tune has timed both and
+ *                     kept the faster per direction.
+ * RMHD and 3D grids sum their pair fluxes inside the interface kernel and
+ * ignore the field. */
+#define ESMM_SWEEP_AUTO 0
+#define ESMM_SWEEP_FUSED 1
+#define ESMM_SWEEP_SPLIT 2
 
 /* Create a grid of n[0] x n[1] nodes on [lo, hi] (dim 2, phys ESMM_RHD or
  * ESMM_RMHD), or of n[0] x n[1] x n[2] nodes (dim 3, phys ESMM_RMHD: the
@@ -309,15 +326,19 @@ int esmm_rhs_vjp(esmm_grid *g, const double *cons, const double *J, const double
 /* Launch autotuner: for each kernel kind (node pass, pair fluxes, interface
  * fluxes, per-node kernels) time the candidates on the current state and keep
  * the fastest: block sizes, for batches the tile order (natural / largest
- * problem first), and for the 2D RHD pair and interface kernels, per sweep
- * direction, the tile shape (flat runs of sites along the sweep, or tiles of
- * tx sites along x_1 by bs/tx along x_2) and whether a persistent grid (the
- * blocks the SMs hold at once) strides over the (problem, tile) queue or
- * each tile gets its own block.  Requires a state.  When block_sizes is given
- * it receives ESMM_TUNE_SLOTS ints: [0, 13) the block size of each launch
- * domain (negative: largest problem first), [13, 17) the tile shape of the
- * tiled pair (x_1, x_2) and interface (x_1, x_2) launches: tx (0: flat runs)
- * plus 1000 for a persistent grid. */
+ * problem first), and for the 2D RHD fluxes, per sweep direction, the
+ * variant (the fused sweep kernel against the pair and interface kernels,
+ * unless esmm_params.sweep fixes one), with, for the pair and interface
+ * kernels, the tile shape (flat runs of sites along the sweep, or tiles of
+ * tx sites along x_1 by bs/tx along x_2), and for every variant whether a
+ * persistent grid (the blocks the SMs hold at once) strides over the
+ * (problem, tile) queue or each tile gets its own block.  Requires a state.
+ * When block_sizes is given it receives ESMM_TUNE_SLOTS ints: [0, 13) the
+ * block size of each launch domain (negative: largest problem first; the
+ * interface slots hold the fused kernel's when it was kept), [13, 17) the
+ * tile shape of the pair (x_1, x_2) and interface (x_1, x_2) launches: tx
+ * (0: flat runs; -1 in the interface slots: the fused sweep kernel, whose
+ * tiles are one line segment per warp) plus 1000 for a persistent grid. */
 #define ESMM_TUNE_SLOTS 17
 int esmm_tune(esmm_grid *g, int *block_sizes);
 

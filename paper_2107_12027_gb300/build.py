@@ -14,7 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libesmm.so")
-SOURCES = ["esmm_api.cu", "esmm_flux_f64.cu", "esmm_flux_f32.cu", "esmm_adjoint.cu", "esmm_mhd.cu", "esmm_mhd_f32.cu",
+SOURCES = ["esmm_api.cu", "esmm_flux_f64.cu", "esmm_flux_f32.cu", "esmm_sweep_f64.cu", "esmm_sweep_f32.cu",
+           "esmm_adjoint.cu", "esmm_mhd.cu", "esmm_mhd_f32.cu",
            "esmm_mhd_adjoint.cu", "esmm_3d.cu", "esmm_3d_iface.cu",
            "esmm_3d_adjoint.cu", "esmm_peak.cu", "esmm_count.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

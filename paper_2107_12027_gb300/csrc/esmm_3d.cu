@@ -865,6 +865,7 @@ int esmm3_create(esmm3 **out, const int n[3], const double lo[3], const double h
     g->prm.monitor = ESMM_MONITOR_LNRHO;
     g->prm.alpha = 800.0;
     g->prm.alpha_lap = 0.0;
+    g->prm.sweep = ESMM_SWEEP_AUTO;   // 2D RHD only; kept for esmm_get_params
     g->prm.n_filter = 4;
     g->prm.mu = 10;
     g->prm.move_mesh = 1;

@@ -224,6 +224,8 @@ long long dom_count(const Geom &G, int kind, int p)
 long long dom_blocks(const esmm_grid *g, const Geom &G, int kind)
 {
     const int bs = g->bs[kind], tx = g->tx[kind];
+    if (tx < 0 && (kind == D_TIFACE0 || kind == D_TIFACE1))   // the fused sweep: bs / 32 lines per tile
+        return sweep_tiles(G, kind == D_TIFACE1 ? 1 : 0, g->p, bs / 32);
     if (tx > 0 && kind >= D_TPAIR0 && kind <= D_TIFACE1) {
         const int dir = (kind == D_TPAIR1 || kind == D_TIFACE1) ? 1 : 0;
         const int ext = kind <= D_TPAIR1 ? g->p : 1;
@@ -232,6 +234,21 @@ long long dom_blocks(const esmm_grid *g, const Geom &G, int kind)
         return ((Ei + tx - 1) / tx) * ((Ej + ty - 1) / ty);
     }
     return (long long)nblk(dom_count(G, kind, g->p), bs);
+}
+
+// The 2D RHD flux variant of both sweep directions (esmm_params.sweep):
+// the fused kernel (tx = -1 in the interface domains, 128 threads = 4 lines
+// per block) or the pair and interface kernels (flat runs of 128 sites);
+// ESMM_SWEEP_AUTO starts from the fused kernel until the tuner decides.
+void set_sweep(esmm_grid *g, int sweep)
+{
+    for (int k : {D_TPAIR0, D_TPAIR1, D_TIFACE0, D_TIFACE1}) {
+        g->bs[k] = 128;
+        g->tx[k] = 0;
+        g->persist[k] = 0;
+    }
+    if (sweep != ESMM_SWEEP_SPLIT) g->tx[D_TIFACE0] = g->tx[D_TIFACE1] = -1;
+    g->doms_valid = 0;
 }
 
 // (Re)build the block -> (problem, tile) map of one kind.
@@ -289,8 +306,11 @@ LaunchDom dom(const esmm_grid *g, int kind)
         L.ntiles = g->nblk[kind];
         if (g->persist[kind]) {   // as many blocks as the SMs hold at once
             const int k = kind <= D_TPAIR1 ? 0 : 1;
-            const int per_sm = g->prm.precision == ESMM_MIXED ? flux_occupancy_f32(k, g->p, g->w, L.bs)
-                                                               : flux_occupancy_f64(k, g->p, g->w, L.bs);
+            const bool f32 = g->prm.precision == ESMM_MIXED;
+            const int per_sm = L.tx < 0 ? (f32 ? sweep_occupancy_f32(g->p, g->w, L.bs)
+                                               : sweep_occupancy_f64(g->p, g->w, L.bs))
+                                        : (f32 ? flux_occupancy_f32(k, g->p, g->w, L.bs)
+                                               : flux_occupancy_f64(k, g->p, g->w, L.bs));
             L.nblk = (unsigned)std::min<long long>(L.ntiles, (long long)per_sm * g->sms);
         }
     }
@@ -359,6 +379,12 @@ void fluxes(esmm_grid *g)
             Prof pr_(g, ESMM_KIND_IFACE);
             if (f32) launch_iface_mhd_f32(Li, ph, g->q, g->iflux, dir, g->st);
             else launch_iface_mhd(Li, ph, g->q, g->iflux, dir, g->st);
+            continue;
+        }
+        if (Li.tx < 0) {   // the fused sweep: pair fluxes kept in shared memory
+            Prof pr_(g, ESMM_KIND_IFACE);
+            if (f32) launch_sweep_f32(Li, ph, g->q, g->q32, g->iflux, dir, g->st);
+            else launch_sweep_f64(Li, ph, g->q, nullptr, g->iflux, dir, g->st);
             continue;
         }
         {
@@ -781,6 +807,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     g->prm.alpha = 20.0;
     g->prm.n_filter = 4;
     g->prm.alpha_lap = 0.0;
+    g->prm.sweep = ESMM_SWEEP_AUTO;
     g->prm.mu = 10;
     g->prm.move_mesh = 1;
     g->prm.precision = ESMM_FP64;
@@ -789,6 +816,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         g->tx[k] = 0;
         g->persist[k] = 0;
     }
+    set_sweep(g, ESMM_SWEEP_AUTO);
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev) != cudaSuccess || g->sms < 1)
         g->sms = 1;
 
@@ -1066,7 +1094,12 @@ int tune(esmm_grid *g)
         // block size x tile shape (flat runs, or tx sites along x_1 by bs / tx
         // along x_2) x one block per tile or a persistent grid (x the tile
         // order of a batch)
-        fluxes(g);   // pair fluxes in place for the interface timings
+        for (int dir = 0; dir < 2; ++dir) {   // pair fluxes in place for the interface timings
+            LaunchDom L = dom(g, dir ? D_TPAIR1 : D_TPAIR0);
+            if (f32) launch_pairs_f32(L, ph, g->q, g->q32, g->pairs, dir, g->st);
+            else launch_pairs_f64(L, ph, g->q, nullptr, g->pairs, dir, g->st);
+        }
+        float split_ms[2] = {0.0f, 0.0f};
         for (int kind = D_TPAIR0; kind <= D_TIFACE1; ++kind) {
             const int dir = (kind == D_TPAIR1 || kind == D_TIFACE1) ? 1 : 0;
             const bool pairs = kind <= D_TPAIR1;
@@ -1106,6 +1139,42 @@ int tune(esmm_grid *g)
             g->tx[kind] = bt;
             g->persist[kind] = bp;
             g->order_lpt[kind] = bo;
+            if ((rc = build_dom(g, kind))) return rc;
+            split_ms[dir] += best;
+        }
+        // the fused sweep kernel against the best pair + interface launches,
+        // per direction (unless the parameters fix the variant)
+        for (int dir = 0; dir < 2 && g->prm.sweep != ESMM_SWEEP_SPLIT; ++dir) {
+            const int kind = dir ? D_TIFACE1 : D_TIFACE0;
+            std::vector<int> orders = g->nprob > 1 ? std::vector<int>{0, 1} : std::vector<int>{0};
+            const int sb = g->bs[kind], st_ = g->tx[kind], sp = g->persist[kind], so = g->order_lpt[kind];
+            float best = 1e30f;
+            int bb = 128, bp = 0, bo = 0;
+            for (int bs : {64, 128, 256})
+                for (int per : {0, 1})
+                    for (int ord : orders) {
+                        g->bs[kind] = bs;
+                        g->tx[kind] = -1;
+                        g->persist[kind] = per;
+                        g->order_lpt[kind] = ord;
+                        if ((rc = build_dom(g, kind))) return rc;
+                        const float ms = time_it([&]() {
+                            LaunchDom L = dom(g, kind);
+                            if (f32) launch_sweep_f32(L, ph, g->q, g->q32, g->iflux, dir, g->st);
+                            else launch_sweep_f64(L, ph, g->q, nullptr, g->iflux, dir, g->st);
+                        });
+                        if (ms < best) {
+                            best = ms;
+                            bb = bs;
+                            bp = per;
+                            bo = ord;
+                        }
+                    }
+            const bool fused = g->prm.sweep == ESMM_SWEEP_FUSED || best < split_ms[dir];
+            g->bs[kind] = fused ? bb : sb;
+            g->tx[kind] = fused ? -1 : st_;
+            g->persist[kind] = fused ? bp : sp;
+            g->order_lpt[kind] = fused ? bo : so;
             if ((rc = build_dom(g, kind))) return rc;
         }
     }
@@ -1736,7 +1805,10 @@ int esmm_set_params(esmm_grid *g, const esmm_params *prm)
         prm->mu < 0 || (prm->precision != ESMM_FP64 && prm->precision != ESMM_MIXED) ||
         (prm->monitor != ESMM_MONITOR_RHO && prm->monitor != ESMM_MONITOR_LNRHO))
         return fail(g, ESMM_ERR_ARG, "invalid parameter");
+    if (prm->sweep != ESMM_SWEEP_AUTO && prm->sweep != ESMM_SWEEP_FUSED && prm->sweep != ESMM_SWEEP_SPLIT)
+        return fail(g, ESMM_ERR_ARG, "invalid parameter");
     if (g->dim == 3) return esmm3_set_params(g->g3, prm);
+    if (prm->sweep != g->prm.sweep) set_sweep(g, prm->sweep);
     g->prm = *prm;
     g->epoch++;
     return ESMM_OK;

@@ -1,6 +1,7 @@
 // esmm_launch.h -- host-side launchers of the kernels that live outside
 // esmm_api.cu: the RHD flux kernels (one translation unit per working
-// precision: esmm_flux_f64.cu, esmm_flux_f32.cu), the adjoint
+// precision: esmm_flux_f64.cu, esmm_flux_f32.cu, and the fused sweep in
+// esmm_sweep_f64.cu, esmm_sweep_f32.cu), the adjoint
 // (esmm_adjoint.cu) and the RMHD kernels (esmm_mhd.cu).
 #pragma once
 
@@ -27,6 +28,23 @@ struct LaunchDom {
 // persistent grid of a tiled launch): kind 0 pairs, 1 interfaces
 int flux_occupancy_f64(int kind, int p, int w, int bs);
 int flux_occupancy_f32(int kind, int p, int w, int bs);
+
+// The fused sweep kernel of one 2D RHD direction (esmm_sweep_f64.cu,
+// esmm_sweep_f32.cu): pair and interface fluxes in one launch, bs / 32
+// lines per block, one segment of 33 - p interfaces per line and tile.
+void launch_sweep_f64(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, void *iflux, int dir,
+                      cudaStream_t st);
+void launch_sweep_f32(const LaunchDom &L, const Phys &ph, const double *q, const float *q32, void *iflux, int dir,
+                      cudaStream_t st);
+int sweep_occupancy_f64(int p, int w, int bs);
+int sweep_occupancy_f32(int p, int w, int bs);
+// tiles of one problem in the fused sweep of direction dir with nw lines per block
+inline long long sweep_tiles(const Geom &g, int dir, int p, int nw)
+{
+    const long long nd = dir == 0 ? g.nx : g.ny, no = dir == 0 ? g.ny : g.nx;
+    const long long ta = 33 - p;
+    return ((no + nw - 1) / nw) * ((nd + 1 + ta - 1) / ta);
+}
 
 struct Phys;
 

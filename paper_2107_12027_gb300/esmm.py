@@ -21,6 +21,7 @@ RHD, RMHD = 0, 1
 PERIODIC, OUTFLOW, INFLOW = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 FP64, MIXED = 0, 1
+SWEEP_AUTO, SWEEP_FUSED, SWEEP_SPLIT = 0, 1, 2
 MONITOR_RHO, MONITOR_LNRHO = 0, 1
 GET_PRIM, GET_CONS, GET_J, GET_X, GET_XDOT = 0, 1, 2, 3, 4
 _ERR = {1: "ESMM_ERR_ARG", 2: "ESMM_ERR_CUDA", 3: "ESMM_ERR_C2P", 4: "ESMM_ERR_TIMEOUT", 5: "ESMM_ERR_STATE"}
@@ -77,7 +78,7 @@ class Params(ctypes.Structure):
     _fields_ = [("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("monitor", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("n_filter", ctypes.c_int), ("mu", ctypes.c_int),
                 ("move_mesh", ctypes.c_int), ("precision", ctypes.c_int),
-                ("alpha_lap", ctypes.c_double)]
+                ("alpha_lap", ctypes.c_double), ("sweep", ctypes.c_int)]
 
 
 _lib = None

@@ -76,7 +76,11 @@ def test_batch_problem_against_oracle_and_tuning_invariance():
         shapes = b.tune()
         assert len(shapes) == esmm.TUNE_SLOTS
         assert all(abs(s) in (64, 128, 256, 512) for s in shapes[:13])
-        assert all(s % 1000 in (0, 8, 16, 32, 64, 128) and s // 1000 in (0, 1) for s in shapes[13:])
+        # pair slots: a tile shape (+1000: persistent); interface slots also
+        # -1 / 999: the fused sweep kernel (+1000: persistent)
+        split = lambda s: s % 1000 in (0, 8, 16, 32, 64, 128) and s // 1000 in (0, 1)
+        assert all(split(s) for s in shapes[13:15])
+        assert all(split(s) or s in (-1, 999) for s in shapes[15:17])
         b.advance(2)
         got = b.state_get(1, esmm.GET_CONS)
         totals = b.totals()
