@@ -8,6 +8,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "esmm_conv.h"
+
 namespace esmm {
 
 constexpr int GH = 3;        // ghost layers of the padded node arrays
@@ -109,6 +111,17 @@ __device__ __forceinline__ bool sweep_site(const Geom &g, int dir, int ext, int 
     return true;
 }
 
+// FP64 <-> FP32 conversions on the integer pipes (esmm_conv.h), equal bit
+// for bit to the hardware conversions, which issue on the FP64 pipe
+template <typename T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return d2f_int(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_int(x); }
+
 struct Phys {
     double gamma;
     double gm1i;      // 1 / (Gamma - 1), once per launch
@@ -206,7 +219,7 @@ __device__ __forceinline__ int cons2prim_gg(double gam, double gg, double D, dou
         double pn = pc;                              // f = 0: pc is a root
         if (f != 0.0) {
             if (f > 0.0) lo = pc; else hi = pc;
-            pn = pc - f * (double)__frcp_rn((float)df);
+            pn = pc - f * f2d_int(__frcp_rn(d2f_int(df)));
             if (!(pn > lo && pn < hi)) pn = 0.5 * (lo + hi);
         }
         if (fabs(pn - pc) <= 1.0e-15 * (E + pn)) { have = pn == pc; pc = pn; ok = 1; break; }

@@ -113,10 +113,10 @@ __global__ void k_node(ProbArg pa, double gam, double gg, const double *__restri
     q[Q_W * g.P + t] = W;
     float lr32 = 0.0f, lb32 = 0.0f;
     if (f32_logs) {
-        lr32 = logf((float)rho);
-        lb32 = logf((float)beta);
-        q[Q_LNR * g.P + t] = (double)lr32;
-        q[Q_LNB * g.P + t] = (double)lb32;
+        lr32 = logf(d2f_int(rho));
+        lb32 = logf(d2f_int(beta));
+        q[Q_LNR * g.P + t] = f2d_int(lr32);
+        q[Q_LNB * g.P + t] = f2d_int(lb32);
     } else {
         q[Q_LNR * g.P + t] = log(rho);
         q[Q_LNB * g.P + t] = log(beta);
@@ -135,19 +135,19 @@ __global__ void k_node(ProbArg pa, double gam, double gg, const double *__restri
     q[Q_MT1 * g.P + t] = MT1;
     if (q32) {
         q32 += (long long)NQ32 * D.op;
-        q32[Q32_R * g.P + t] = (float)rho;
-        q32[Q32_B * g.P + t] = (float)beta;
-        q32[Q32_UX * g.P + t] = (float)(W * vx);
-        q32[Q32_UY * g.P + t] = (float)(W * vy);
-        q32[Q32_W * g.P + t] = (float)W;
-        q32[Q32_LNR * g.P + t] = f32_logs ? lr32 : (float)q[Q_LNR * g.P + t];
-        q32[Q32_LNB * g.P + t] = f32_logs ? lb32 : (float)q[Q_LNB * g.P + t];
-        q32[Q32_M00 * g.P + t] = (float)M00;
-        q32[Q32_M01 * g.P + t] = (float)M01;
-        q32[Q32_M10 * g.P + t] = (float)M10;
-        q32[Q32_M11 * g.P + t] = (float)M11;
-        q32[Q32_MT0 * g.P + t] = (float)MT0;
-        q32[Q32_MT1 * g.P + t] = (float)MT1;
+        q32[Q32_R * g.P + t] = d2f_int(rho);
+        q32[Q32_B * g.P + t] = d2f_int(beta);
+        q32[Q32_UX * g.P + t] = d2f_int(W * vx);
+        q32[Q32_UY * g.P + t] = d2f_int(W * vy);
+        q32[Q32_W * g.P + t] = d2f_int(W);
+        q32[Q32_LNR * g.P + t] = f32_logs ? lr32 : d2f_int(q[Q_LNR * g.P + t]);
+        q32[Q32_LNB * g.P + t] = f32_logs ? lb32 : d2f_int(q[Q_LNB * g.P + t]);
+        q32[Q32_M00 * g.P + t] = d2f_int(M00);
+        q32[Q32_M01 * g.P + t] = d2f_int(M01);
+        q32[Q32_M10 * g.P + t] = d2f_int(M10);
+        q32[Q32_M11 * g.P + t] = d2f_int(M11);
+        q32[Q32_MT0 * g.P + t] = d2f_int(MT0);
+        q32[Q32_MT1 * g.P + t] = d2f_int(MT1);
     }
 }
 
@@ -172,8 +172,8 @@ __global__ void k_tmetric(ProbArg pa, const double *__restrict__ xdot, double *_
     q[Q_MT1 * g.P + t] = MT1;
     if (q32) {
         q32 += (long long)NQ32 * D.op;
-        q32[Q32_MT0 * g.P + t] = (float)MT0;
-        q32[Q32_MT1 * g.P + t] = (float)MT1;
+        q32[Q32_MT0 * g.P + t] = d2f_int(MT0);
+        q32[Q32_MT1 * g.P + t] = d2f_int(MT1);
     }
 }
 
@@ -208,7 +208,7 @@ __global__ void k_update(ProbArg pa, const R *__restrict__ fl, double *__restric
         // rounds once otherwise), summed in FP64
         R d0 = f0[a * g.P + c] - f0[a * g.P + c - 1];
         R d1 = f1[a * g.P + c] - f1[a * g.P + c - g.px];
-        L[a] = -((double)d0 + (double)d1);
+        L[a] = -(to_f64(d0) + to_f64(d1));
     }
     if (dcons) {
         dcons += 4 * D.on;
@@ -251,7 +251,7 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
         float vx = q32[Q32_UX * g.P + c] * iW, vy = q32[Q32_UY * g.P + c] * iW;
         float v2 = vx * vx + vy * vy;
         float c2 = gam * __frcp_rn(beta + gam / (gam - 1.0f)), cs = sqrtf(c2);
-        float iJ = __frcp_rn((float)J[id]);
+        float iJ = __frcp_rn(d2f_int(J[id]));
         float iden = __frcp_rn(1.0f - v2 * c2);
         for (int k = 0; k < 2; ++k) {
             float mx = q32[(Q32_M00 + 2 * k) * g.P + c], my = q32[(Q32_M01 + 2 * k) * g.P + c];
@@ -259,10 +259,10 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
             float vn = (mx * vx + my * vy) * iL;
             float disc = sqrtf(fmaxf((1.0f - v2) * (1.0f - v2 * c2 - vn * vn * (1.0f - c2)), 0.0f));
             float lm = (vn * (1.0f - c2) - cs * disc) * iden, lp = (vn * (1.0f - c2) + cs * disc) * iden;
-            r[k] = owned_row(g, j) ? (double)(Lk * fmaxf(fabsf(lm), fabsf(lp)) * iJ) : 0.0;
+            r[k] = owned_row(g, j) ? f2d_int(Lk * fmaxf(fabsf(lm), fabsf(lp)) * iJ) : 0.0;
             if (cflb) {
-                cflb[(2 + k) * g.N + id] = (double)(Lk * lm * iJ);
-                cflb[(4 + k) * g.N + id] = (double)(Lk * lp * iJ);
+                cflb[(2 + k) * g.N + id] = f2d_int(Lk * lm * iJ);
+                cflb[(4 + k) * g.N + id] = f2d_int(Lk * lp * iJ);
             }
         }
     }
@@ -569,10 +569,10 @@ __global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const do
         const bool fixed = (g.bc0 != 0 && (si == 0 || si == g.nx - 1)) || (g.bc1 != 0 && (sj == 0 || sj == g.ny - 1));
         sF[r] = fixed;
         const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
-        sW[r] = (T)ce;
-        sW[RN + r] = (T)cwe;
-        sW[2 * RN + r] = (T)cn;
-        sW[3 * RN + r] = (T)cs;
+        sW[r] = from_f64<T>(ce);
+        sW[RN + r] = from_f64<T>(cwe);
+        sW[2 * RN + r] = from_f64<T>(cn);
+        sW[3 * RN + r] = from_f64<T>(cs);
         for (int c = 0; c < 2; ++c) {
             double res = 0.0;
             if (!fixed) {
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const do
                 const double xs = inner ? a[o - g.nx] : mesh_edge(g, x, gi, gj - 1, c);
                 res = ce * xe + cwe * xw + cn * xn + cs * xs - xi;
             }
-            sR[c * RN + r] = (T)res;
+            sR[c * RN + r] = from_f64<T>(res);
             sD[c * RN + r] = Din ? Din[c * g.N + id] : (T)0;
         }
     }
@@ -708,7 +708,7 @@ __global__ void k_mesh_tau(ProbArg pa, const double *__restrict__ x, const T *__
         int i = (int)(id % g.nx), j = (int)(id / g.nx);
         double dd[2];
         for (int k = 0; k < 2; ++k) {
-            double d = (double)Dd[k * g.N + id];
+            double d = to_f64(Dd[k * g.N + id]);
             dd[k] = d;
             int di = k == 0, dj = k == 1;
             const bool inner = k == 0 ? (i > 0 && i < g.nx - 1) : (j > 0 && j < g.ny - 1);
@@ -758,7 +758,7 @@ __global__ void k_mesh_xdot(ProbArg pa, const T *__restrict__ Dd, const unsigned
     __syncthreads();
     if (id >= 2 * g.N) return;
     long long o = 2 * D.on + id;
-    xdot[o] = s * (double)Dd[o];
+    xdot[o] = s * to_f64(Dd[o]);
 }
 
 // ---- state set-up and read-out ------------------------------------------------

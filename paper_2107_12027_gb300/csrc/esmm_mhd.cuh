@@ -71,7 +71,7 @@ __device__ __forceinline__ int cons2prim_mhd(double gam, const double U[8], doub
             Zn = Z;                          // f = 0: Z is a root
             if (f != 0.0) {
                 if (f < 0.0) lo = Z; else hi = Z;
-                Zn = Z - f * (double)__frcp_rn((float)df);
+                Zn = Z - f * f2d_int(__frcp_rn(d2f_int(df)));
                 if (!(Zn > lo && Zn < hi)) Zn = 0.5 * (lo + hi);
             }
         }
@@ -641,8 +641,8 @@ __global__ void k_node_mhd(ProbArg pa, double gam, const double *__restrict__ co
     // (f32_logs: the mixed form's scheme passes, where the logarithms enter
     // only FP32 arithmetic and the log mean's jump outside its near-equal
     // branch)
-    q[Q_LNR * g.P + t] = f32_logs ? (double)logf((float)w[0]) : log(w[0]);
-    q[Q_LNB * g.P + t] = f32_logs ? (double)logf((float)beta) : log(beta);
+    q[Q_LNR * g.P + t] = f32_logs ? f2d_int(logf(d2f_int(w[0]))) : log(w[0]);
+    q[Q_LNB * g.P + t] = f32_logs ? f2d_int(logf(d2f_int(beta))) : log(beta);
     q[QM_B1 * g.P + t] = w[5];
     q[QM_B2 * g.P + t] = w[6];
     q[QM_B3 * g.P + t] = w[7];
@@ -909,8 +909,8 @@ __global__ void k_update_mhd(ProbArg pa, const double *__restrict__ q, const R *
     double L[10];
 #pragma unroll
     for (int a = 0; a < 10; ++a) {
-        double d0 = (double)f0[a * g.P + c] - (double)f0[a * g.P + c - 1];
-        double d1 = (double)f1[a * g.P + c] - (double)f1[a * g.P + c - g.px];
+        double d0 = to_f64(f0[a * g.P + c]) - to_f64(f0[a * g.P + c - 1]);
+        double d1 = to_f64(f1[a * g.P + c]) - to_f64(f1[a * g.P + c - g.px]);
         L[a] = -(d0 + d1);
     }
     // Powell source: L[9] = -div B~ here
