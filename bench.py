@@ -53,39 +53,40 @@ WORKLOAD = ("2D RHD four-quadrant Riemann problem, 400x400 nodes on [-1,1]^2, ou
 # (FP64) or fadd + fmul + 2 ffma (FP32), i.e. an add, a mul, or half an FMA,
 # including the FP64 instructions inside division, square-root and log
 # sequences.  The FP64 interface kernel (p = 2, WENO5) on the 400^2 Riemann
-# workload executes 1,395 per interface.
-FLOPS_PER_IFACE_F64 = 1395
+# workload executed 1,395 per interface before the paired WENO reconstructions
+# (not recaptured since: None).
+FLOPS_PER_IFACE_F64 = None
 # Unit counts for the derived peaks, reported beside the measured ones:
 # 4 FP64 flop/clk/SM and 256 FP32 flop/clk/SM at the 2070 MHz maximum clock.
 FP64_FLOP_PER_CLK_SM = 4
 FP32_FLOP_PER_CLK_SM = 256
 # DRAM bytes (read + write) of one interface-kernel launch in that capture;
 # None whenever the kernel has changed since the counters were taken.
-TRAFFIC_IFACE_F64 = 23.48e6
+TRAFFIC_IFACE_F64 = None
 # The mixed form's interface kernel on the same workload: FP32 flops per
 # interface and DRAM bytes per launch.
-FLOPS_PER_IFACE_F32 = 1253
-TRAFFIC_IFACE_F32 = 13.08e6
+FLOPS_PER_IFACE_F32 = None
+TRAFFIC_IFACE_F32 = None
 # The same for the RMHD interface kernels at p = 2, WENO5: the FP64 2D kernel
-# on the 512^2 rotor (11,042 FP64 flops per interface; 1.021 GB of DRAM
+# on the 512^2 rotor (10,898 FP64 flops per interface; 1.021 GB of DRAM
 # traffic per launch, the eigen-system's per-thread stack), its FP32 instance
-# (10,832 FP32 flops per interface besides 98 FP64 ones; 0.479 GB), and the 3D
-# kernel (16,409 FP64 flops per interface; 1.210 GB at 64^3, scaled by the
+# (10,688 FP32 flops per interface besides 98 FP64 ones; 0.480 GB), and the 3D
+# kernel (16,265 FP64 flops per interface; 1.211 GB at 64^3, scaled by the
 # 7.94x interfaces of a 128^3 launch -- the stack traffic grows with the
 # threads).
-FLOPS_PER_IFACE_MHD2 = 11042
+FLOPS_PER_IFACE_MHD2 = 10898
 TRAFFIC_IFACE_MHD2 = 1.021e9
-FLOPS_PER_IFACE_MHD2_F32 = 10832
-TRAFFIC_IFACE_MHD2_F32 = 0.479e9
-FLOPS_PER_IFACE_MHD3 = 16409
-TRAFFIC_IFACE_MHD3 = 9.61e9
+FLOPS_PER_IFACE_MHD2_F32 = 10688
+TRAFFIC_IFACE_MHD2_F32 = 0.480e9
+FLOPS_PER_IFACE_MHD3 = 16265
+TRAFFIC_IFACE_MHD3 = 9.62e9
 # The fused sweep kernel (pair and interface fluxes in one launch) on the
 # same workload, from one capture of each form: executed flops per interface
 # (its pair fluxes included: 32 anchors per 31 interfaces) and DRAM bytes
 # per launch; None whenever the kernel has changed since.
-FLOPS_PER_SWEEP_F64 = 1685
-TRAFFIC_SWEEP_F64 = 13.11e6
-FLOPS_PER_SWEEP_F32 = 1475
+FLOPS_PER_SWEEP_F64 = 1573
+TRAFFIC_SWEEP_F64 = 13.10e6
+FLOPS_PER_SWEEP_F32 = 1363
 TRAFFIC_SWEEP_F32 = 11.74e6
 N_SM = 152
 SM_MAX_MHZ = 2070.0

@@ -312,13 +312,10 @@ __global__ void __launch_bounds__(128) k3_iface(Geom3 g, Phys ph, const double *
         double z[8];
         for (int m = 0; m < 8; ++m) {
             double vminus, vplus;
-            if (WW == 5) {
-                vminus = weno5<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], ph.eps);
-                vplus = weno5<double>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
-            } else {
-                vminus = weno3<double>(Vt[0][m], Vt[1][m], Vt[2][m], ph.eps);
-                vplus = weno3<double>(Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
-            }
+            if (WW == 5)
+                weno5_lr<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], Vt[5][m], ph.eps, vminus, vplus);
+            else
+                weno3_lr<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], ph.eps, vminus, vplus);
             double jw = vplus - vminus;
             double jump = Vt[OFF + 1][m] - Vt[OFF][m];
             int sj = fabs(jump) <= ph.sign_tol * scale[m] ? 0 : sgn_d(jump);

@@ -558,6 +558,45 @@ __device__ __forceinline__ R weno5(R s0, R s1, R s2, R s3, R s4, R eps)
     return (a0 * q0 + a1 * q1 + a2 * q2) * rcp<R>(a0 + a1 + a2);
 }
 
+// The two WENO5 edge values of one interface from its six stencil values
+// V0..V5 (V2, V3 the interface's nodes): vm as weno5(V0..V4) (upwind left)
+// and vp as weno5(V5..V1) (upwind right), each with one division.  The
+// candidate values and second differences of the two middle candidate
+// stencils, {V1, V2, V3} and {V2, V3, V4}, serve both reconstructions
+// (left's 2nd and 3rd candidates are right's 3rd and 2nd) and are formed
+// once.
+template <typename R>
+__device__ __forceinline__ void weno5_lr(R V0, R V1, R V2, R V3, R V4, R V5, R eps, R &vm, R &vp)
+{
+    const R c13_12 = (R)(13.0 / 12.0), c1_4 = (R)0.25, c1_6 = (R)(1.0 / 6.0);
+    const R qa = (-V1 + (R)5 * V2 + (R)2 * V3) * c1_6;
+    const R qb = ((R)2 * V2 + (R)5 * V3 - V4) * c1_6;
+    const R ta = V1 - (R)2 * V2 + V3, tb = V2 - (R)2 * V3 + V4;
+    const R sa = c13_12 * ta * ta, sb = c13_12 * tb * tb;
+    {
+        R q0 = ((R)2 * V0 - (R)7 * V1 + (R)11 * V2) * c1_6;
+        R t0 = V0 - (R)2 * V1 + V2, r0 = V0 - (R)4 * V1 + (R)3 * V2;
+        R r1 = V1 - V3, r2 = (R)3 * V2 - (R)4 * V3 + V4;
+        R e0 = eps + c13_12 * t0 * t0 + c1_4 * r0 * r0;
+        R e1 = eps + sa + c1_4 * r1 * r1;
+        R e2 = eps + sb + c1_4 * r2 * r2;
+        e0 *= e0; e1 *= e1; e2 *= e2;
+        R a0 = (R)0.1 * e1 * e2, a1 = (R)0.6 * e0 * e2, a2 = (R)0.3 * e0 * e1;
+        vm = (a0 * q0 + a1 * qa + a2 * qb) * rcp<R>(a0 + a1 + a2);
+    }
+    {
+        R q0 = ((R)2 * V5 - (R)7 * V4 + (R)11 * V3) * c1_6;
+        R t0 = V5 - (R)2 * V4 + V3, r0 = V5 - (R)4 * V4 + (R)3 * V3;
+        R r1 = V4 - V2, r2 = (R)3 * V3 - (R)4 * V2 + V1;
+        R e0 = eps + c13_12 * t0 * t0 + c1_4 * r0 * r0;
+        R e1 = eps + sb + c1_4 * r1 * r1;
+        R e2 = eps + sa + c1_4 * r2 * r2;
+        e0 *= e0; e1 *= e1; e2 *= e2;
+        R a0 = (R)0.1 * e1 * e2, a1 = (R)0.6 * e0 * e2, a2 = (R)0.3 * e0 * e1;
+        vp = (a0 * q0 + a1 * qb + a2 * qa) * rcp<R>(a0 + a1 + a2);
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ R weno3(R s0, R s1, R s2, R eps)
 {
@@ -568,6 +607,31 @@ __device__ __forceinline__ R weno3(R s0, R s1, R s2, R eps)
     e0 *= e0; e1 *= e1;
     R a0 = (R)(1.0 / 3.0) * e1, a1 = (R)(2.0 / 3.0) * e0;
     return (a0 * q0 + a1 * q1) * rcp<R>(a0 + a1);
+}
+
+// The two WENO3 edge values of one interface from V0..V3 (V1, V2 its
+// nodes): vm as weno3(V0, V1, V2), vp as weno3(V3, V2, V1); the candidate
+// on {V1, V2} and its smoothness term serve both.
+template <typename R>
+__device__ __forceinline__ void weno3_lr(R V0, R V1, R V2, R V3, R eps, R &vm, R &vp)
+{
+    const R q1 = (V1 + V2) * (R)0.5;
+    R e1 = eps + (V2 - V1) * (V2 - V1);
+    e1 *= e1;
+    {
+        R q0 = (-V0 + (R)3 * V1) * (R)0.5;
+        R e0 = eps + (V1 - V0) * (V1 - V0);
+        e0 *= e0;
+        R a0 = (R)(1.0 / 3.0) * e1, a1 = (R)(2.0 / 3.0) * e0;
+        vm = (a0 * q0 + a1 * q1) * rcp<R>(a0 + a1);
+    }
+    {
+        R q0 = (-V3 + (R)3 * V2) * (R)0.5;
+        R e0 = eps + (V2 - V3) * (V2 - V3);
+        e0 *= e0;
+        R a0 = (R)(1.0 / 3.0) * e1, a1 = (R)(2.0 / 3.0) * e0;
+        vp = (a0 * q0 + a1 * q1) * rcp<R>(a0 + a1);
+    }
 }
 
 __device__ __forceinline__ int sgn_d(double a) { return (a > 0.0) - (a < 0.0); }

@@ -51,6 +51,40 @@ __device__ __forceinline__ NodeV<R> load_node(const Geom &g, const double *__res
 // ln rho, ln beta) of the w + 1 stencil nodes, the interface nodes at
 // k = (w-1)/2 and (w+1)/2.  The eigen-system is taken at rho = {{rho}}^ln,
 // u = {{u}}, p = {{rho}}/{{beta}}; Y has sign 0 for jumps at rounding level.
+// The entropy variables (V_1, V_x, V_y, V_E) of one node (Sec. 2, B = 0)
+// from beta, u, W, ln rho, ln beta: V_1 = Gamma/(Gamma-1) + ln rho +
+// ln beta/(Gamma-1) + beta, (V_x, V_y) = beta u, V_E = -beta W.  Every
+// stencil type below forms them with this one function, so a kernel that
+// stores them per node gets the values a kernel forming them per interface
+// gets: in FP64 and FP32 each operation is an explicitly rounded intrinsic,
+// which leaves the compiler no choice of contraction between the two.
+template <typename R>
+__device__ __forceinline__ void entropy_vars4(R b, R ux, R uy, R W, R lnr, R lnb, R c1g, R ig, R V[4])
+{
+    V[0] = c1g + lnr + ig * lnb + b;
+    V[1] = b * ux;
+    V[2] = b * uy;
+    V[3] = -b * W;
+}
+template <>
+__device__ __forceinline__ void entropy_vars4<double>(double b, double ux, double uy, double W, double lnr,
+                                                      double lnb, double c1g, double ig, double V[4])
+{
+    V[0] = __dadd_rn(__fma_rn(ig, lnb, __dadd_rn(c1g, lnr)), b);
+    V[1] = __dmul_rn(b, ux);
+    V[2] = __dmul_rn(b, uy);
+    V[3] = -__dmul_rn(b, W);
+}
+template <>
+__device__ __forceinline__ void entropy_vars4<float>(float b, float ux, float uy, float W, float lnr, float lnb,
+                                                     float c1g, float ig, float V[4])
+{
+    V[0] = __fadd_rn(__fmaf_rn(ig, lnb, __fadd_rn(c1g, lnr)), b);
+    V[1] = __fmul_rn(b, ux);
+    V[2] = __fmul_rn(b, uy);
+    V[3] = -__fmul_rn(b, W);
+}
+
 // stencil values read straight from the node arrays (forward kernels)
 template <typename R>
 struct QStencil {
@@ -61,6 +95,11 @@ struct QStencil {
     {
         const int f = j == 0 ? Q_BETA : (j == 1 ? Q_UX : (j == 2 ? Q_UY : (j == 3 ? Q_W : (j == 4 ? Q_LNR : Q_LNB))));
         return (R)q[f * P + c0 + (k - off) * sd];
+    }
+    __device__ __forceinline__ void V(int k, R c1g, R ig, R v[4]) const
+    {
+        entropy_vars4<R>((*this)(k, 0), (*this)(k, 1), (*this)(k, 2), (*this)(k, 3), (*this)(k, 4), (*this)(k, 5), c1g,
+                         ig, v);
     }
 };
 
@@ -75,6 +114,11 @@ struct QStencil32 {
                     : (j == 1 ? Q32_UX : (j == 2 ? Q32_UY : (j == 3 ? Q32_W : (j == 4 ? Q32_LNR : Q32_LNB))));
         return q[f * P + c0 + (k - off) * sd];
     }
+    __device__ __forceinline__ void V(int k, float c1g, float ig, float v[4]) const
+    {
+        entropy_vars4<float>((*this)(k, 0), (*this)(k, 1), (*this)(k, 2), (*this)(k, 3), (*this)(k, 4), (*this)(k, 5),
+                             c1g, ig, v);
+    }
 };
 
 // stencil values held in an array (the adjoint's seeded duals)
@@ -82,6 +126,10 @@ template <typename R, int NS>
 struct ArrStencil {
     const R (*a)[6];
     __device__ __forceinline__ R operator()(int k, int j) const { return a[k][j]; }
+    __device__ __forceinline__ void V(int k, R c1g, R ig, R v[4]) const
+    {
+        entropy_vars4<R>(a[k][0], a[k][1], a[k][2], a[k][3], a[k][4], a[k][5], c1g, ig, v);
+    }
 };
 
 template <typename R, typename T, int WW, typename ST>
@@ -109,22 +157,30 @@ __device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho
     const R ig = (R)ph.gm1i, c1g = gam * ig;
     eigen_rhd<R>(gam, ig, rho, vn, vt, p, W, dU, s, lm, lp);
     R lhat = vmax(fab<R>(jt + Lk * lm), fab<R>(jt + Lk * lp));
+    // Vt_m = s_m dU_m . (T V): the rotation T and the scale s_m folded into
+    // the projection row Ar[m] once per interface
+    R Ar[4][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        Ar[m][0] = s[m] * dU[0][m];
+        Ar[m][1] = s[m] * (nx * dU[1][m] - ny * dU[2][m]);
+        Ar[m][2] = s[m] * (ny * dU[1][m] + nx * dU[2][m]);
+        Ar[m][3] = s[m] * dU[3][m];
+    }
     R Vt[NS][4];
     R aT[4] = {(R)0, (R)0, (R)0, (R)0};     // |T V| summed over the two interface nodes
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        R b = st(k, 0);
-        R V0 = c1g + st(k, 4) + ig * st(k, 5) + b;
-        R Vx = b * st(k, 1);
-        R Vy = b * st(k, 2);
-        R VE = -b * st(k, 3);
-        R T1 = nx * Vx + ny * Vy, T2 = -ny * Vx + nx * Vy;
+        R V[4];
+        st.V(k, c1g, ig, V);
         if (k == OFF || k == OFF + 1) {
-            aT[0] += fab<R>(V0); aT[1] += fab<R>(T1); aT[2] += fab<R>(T2); aT[3] += fab<R>(VE);
+            aT[0] += fab<R>(V[0]);
+            aT[1] += fab<R>(nx * V[1] + ny * V[2]);
+            aT[2] += fab<R>(-ny * V[1] + nx * V[2]);
+            aT[3] += fab<R>(V[3]);
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-            Vt[k][m] = s[m] * (dU[0][m] * V0 + dU[1][m] * T1 + dU[2][m] * T2 + dU[3][m] * VE);
+        for (int m = 0; m < 4; ++m) Vt[k][m] = Ar[m][0] * V[0] + Ar[m][1] * V[1] + Ar[m][2] * V[2] + Ar[m][3] * V[3];
     }
     const R eps = (R)ph.eps;
     const R sign_tol = (R)ph.sign_tol;
@@ -132,13 +188,10 @@ __device__ __forceinline__ void es_dissipation(R nvx, R nvy, R jt, T rho0, T rho
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         R vminus, vplus;
-        if (WW == 5) {
-            vminus = weno5<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
-            vplus = weno5<R>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
-        } else {
-            vminus = weno3<R>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
-            vplus = weno3<R>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
-        }
+        if (WW == 5)
+            weno5_lr<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], Vt[5][m], eps, vminus, vplus);
+        else
+            weno3_lr<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], eps, vminus, vplus);
         R jw = vplus - vminus;
         R jump = Vt[OFF + 1][m] - Vt[OFF][m];
         // a jump within sign_tol of the magnitudes forming V~_m at the two

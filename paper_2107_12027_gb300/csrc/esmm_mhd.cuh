@@ -812,13 +812,10 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
         const R eps = (R)ph.eps, sign_tol = (R)ph.sign_tol;
         for (int m = 0; m < 8; ++m) {
             R vminus, vplus;
-            if (WW == 5) {
-                vminus = weno5<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], eps);
-                vplus = weno5<R>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], eps);
-            } else {
-                vminus = weno3<R>(Vt[0][m], Vt[1][m], Vt[2][m], eps);
-                vplus = weno3<R>(Vt[3][m], Vt[2][m], Vt[1][m], eps);
-            }
+            if (WW == 5)
+                weno5_lr<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], Vt[5][m], eps, vminus, vplus);
+            else
+                weno3_lr<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], eps, vminus, vplus);
             R jw = vplus - vminus;
             R jump = Vt[OFF + 1][m] - Vt[OFF][m];
             int sj = le(fab<R>(jump), sign_tol * scale[m]) ? 0 : sgn_d(jump);

@@ -247,13 +247,10 @@ __global__ void __launch_bounds__(128) k_iface_vjp_mhd(ProbArg pa, Phys ph, cons
     bool ym[8];
     for (int m = 0; m < 8; ++m) {
         double vminus, vplus;
-        if (WW == 5) {
-            vminus = weno5<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], ph.eps);
-            vplus = weno5<double>(Vt[5][m], Vt[4][m], Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
-        } else {
-            vminus = weno3<double>(Vt[0][m], Vt[1][m], Vt[2][m], ph.eps);
-            vplus = weno3<double>(Vt[3][m], Vt[2][m], Vt[1][m], ph.eps);
-        }
+        if (WW == 5)
+            weno5_lr<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], Vt[5][m], ph.eps, vminus, vplus);
+        else
+            weno3_lr<double>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], ph.eps, vminus, vplus);
         const double jw = vplus - vminus;
         const double jump = Vt[OFF + 1][m] - Vt[OFF][m];
         const int sj = fabs(jump) <= ph.sign_tol * scale[m] ? 0 : sgn_d(jump);
@@ -280,13 +277,10 @@ __global__ void __launch_bounds__(128) k_iface_vjp_mhd(ProbArg pa, Phys ph, cons
         for (int m = 0; m < 8; ++m) {
             for (int kk = 0; kk < NS; ++kk) s[kk] = dual(Vt[kk][m], kk == k ? 1.0 : 0.0);
             dual vminus, vplus;
-            if (WW == 5) {
-                vminus = weno5<dual>(s[0], s[1], s[2], s[3], s[4], epsd);
-                vplus = weno5<dual>(s[5], s[4], s[3], s[2], s[1], epsd);
-            } else {
-                vminus = weno3<dual>(s[0], s[1], s[2], epsd);
-                vplus = weno3<dual>(s[3], s[2], s[1], epsd);
-            }
+            if (WW == 5)
+                weno5_lr<dual>(s[0], s[1], s[2], s[3], s[4], s[5], epsd, vminus, vplus);
+            else
+                weno3_lr<dual>(s[0], s[1], s[2], s[3], epsd, vminus, vplus);
             lVt[k][m] = ym[m] ? qm[m] * (vplus.d - vminus.d) : 0.0;
         }
     }

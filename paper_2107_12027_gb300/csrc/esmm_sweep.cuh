@@ -36,10 +36,12 @@ template <typename R, int P>
 struct SweepLayout {
     static constexpr bool F32 = std::is_same<R, float>::value;
     // FP64 fields: rho, beta, ln rho, ln beta (the log-mean arguments), and in
-    // the FP64 form also u_x, u_y, W and the direction's metrics Mt, Mx, My
-    static constexpr int NF64 = F32 ? 4 : 10;
-    // FP32 fields of the mixed form: r, b, u_x, u_y, W, ln rho, ln beta, Mt, Mx, My
-    static constexpr int NF32 = F32 ? 10 : 0;
+    // the FP64 form also u_x, u_y, W, the direction's metrics Mt, Mx, My and
+    // the entropy variables V_1, V_x, V_y, V_E
+    static constexpr int NF64 = F32 ? 4 : 14;
+    // FP32 fields of the mixed form: r, b, u_x, u_y, W, ln rho, ln beta, Mt,
+    // Mx, My, V_1, V_x, V_y, V_E
+    static constexpr int NF32 = F32 ? 14 : 0;
     static constexpr int PAIR_VALUES = P * 4 * 32;   // pair fluxes of the warp's 32 anchors
     static constexpr size_t bytes_per_warp =
         (size_t)NF64 * SW_NNP * 8 + (size_t)NF32 * SW_NNP * 4 + (size_t)PAIR_VALUES * sizeof(R);
@@ -65,6 +67,12 @@ struct SmemStencil<double> {
         const int f = j == 0 ? 1 : (j == 1 ? 4 : (j == 2 ? 5 : (j == 3 ? 6 : (j == 4 ? 2 : 3))));
         return s[f * SW_NNP + base + k];
     }
+    // the entropy variables staged with the node (fields 10 .. 13)
+    __device__ __forceinline__ void V(int k, double, double, double v[4]) const
+    {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = s[(10 + a) * SW_NNP + base + k];
+    }
 };
 template <>
 struct SmemStencil<float> {
@@ -75,13 +83,20 @@ struct SmemStencil<float> {
         const int f = j == 0 ? 1 : (j == 1 ? 2 : (j == 2 ? 3 : (j == 3 ? 4 : (j == 4 ? 5 : 6))));
         return s[f * SW_NNP + base + k];
     }
+    __device__ __forceinline__ void V(int k, float, float, float v[4]) const
+    {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = s[(10 + a) * SW_NNP + base + k];
+    }
 };
 
-// one node of global padded index c into staged slot e of a warp's arrays
+// one node of global padded index c into staged slot e of a warp's arrays,
+// with its entropy variables (entropy_vars4 on the staged values, as the
+// stencils of the two-kernel path form them per interface)
 template <typename R>
 __device__ __forceinline__ void sweep_stage(const Geom &g, const double *__restrict__ q,
-                                            const float *__restrict__ q32, long long c, int dir, double *sd,
-                                            float *sf, int e)
+                                            const float *__restrict__ q32, long long c, int dir, R c1g, R ig,
+                                            double *sd, float *sf, int e)
 {
     if constexpr (std::is_same<R, float>::value) {
         sd[0 * SW_NNP + e] = q[Q_RHO * g.P + c];
@@ -90,13 +105,23 @@ __device__ __forceinline__ void sweep_stage(const Geom &g, const double *__restr
         sd[3 * SW_NNP + e] = q[Q_LNB * g.P + c];
         const int fl[10] = {Q32_R, Q32_B, Q32_UX, Q32_UY, Q32_W, Q32_LNR, Q32_LNB, Q32_MT0 + dir, Q32_M00 + 2 * dir,
                             Q32_M01 + 2 * dir};
+        float v[10];
 #pragma unroll
-        for (int f = 0; f < 10; ++f) sf[f * SW_NNP + e] = q32[fl[f] * g.P + c];
+        for (int f = 0; f < 10; ++f) sf[f * SW_NNP + e] = v[f] = q32[fl[f] * g.P + c];
+        float V[4];
+        entropy_vars4<float>(v[1], v[2], v[3], v[4], v[5], v[6], c1g, ig, V);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) sf[(10 + a) * SW_NNP + e] = V[a];
     } else {
         const int fl[10] = {Q_RHO, Q_BETA, Q_LNR, Q_LNB, Q_UX, Q_UY, Q_W, Q_MT0 + dir, Q_M00 + 2 * dir,
                             Q_M01 + 2 * dir};
+        double v[10];
 #pragma unroll
-        for (int f = 0; f < 10; ++f) sd[f * SW_NNP + e] = q[fl[f] * g.P + c];
+        for (int f = 0; f < 10; ++f) sd[f * SW_NNP + e] = v[f] = q[fl[f] * g.P + c];
+        double V[4];
+        entropy_vars4<double>(v[1], v[4], v[5], v[6], v[2], v[3], c1g, ig, V);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) sd[(10 + a) * SW_NNP + e] = V[a];
     }
 }
 
@@ -145,6 +170,7 @@ __global__ void __launch_bounds__(256) k_sweep(ProbArg pa, Phys ph, const double
     const MT *sMx = F32 ? (const MT *)(sf + 8 * SW_NNP) : (const MT *)(sd + 8 * SW_NNP);
     const MT *sMy = F32 ? (const MT *)(sf + 9 * SW_NNP) : (const MT *)(sd + 9 * SW_NNP);
     const R gm1inv = (R)(1.0 / (ph.gamma - 1.0));
+    const R ig = (R)ph.gm1i, c1g = (R)ph.gamma * ig;   // as es_dissipation forms them
 
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         ProbDesc D;
@@ -166,12 +192,13 @@ __global__ void __launch_bounds__(256) k_sweep(ProbArg pa, Phys ph, const double
         // the padded range [-GH, nd - 1 + GH] since HL, HR <= GH
         if (dir == 0) {
             if (line < no)
-                for (int e = lane; e < nn; e += 32) sweep_stage<R>(g, qq, qq32, pidx(g, nlo + e, line), 0, sd, sf, e);
+                for (int e = lane; e < nn; e += 32)
+                    sweep_stage<R>(g, qq, qq32, pidx(g, nlo + e, line), 0, c1g, ig, sd, sf, e);
         } else {
             for (int e = threadIdx.x; e < nn * NW; e += blockDim.x) {
                 const int ww = e % NW, node = e / NW;
                 if (grp * NW + ww < no)
-                    sweep_stage<R>(g, qq, qq32, pidx(g, grp * NW + ww, nlo + node), 1,
+                    sweep_stage<R>(g, qq, qq32, pidx(g, grp * NW + ww, nlo + node), 1, c1g, ig,
                                    (double *)sw_smem + (size_t)ww * LY::NF64 * SW_NNP,
                                    (float *)((double *)sw_smem + (size_t)NW * LY::NF64 * SW_NNP) +
                                        (size_t)ww * LY::NF32 * SW_NNP,
