@@ -267,7 +267,14 @@ int esmm_set_inflow(esmm_grid *g, const double *prim);
  * or a batch, ESMM_ERR_STATE without a state, ESMM_ERR_C2P if a recovery
  * failed. */
 int esmm_rk_step_given(esmm_grid *g, const double *xdot, double dt, int mem);
-/* nsteps asynchronous esmm_rk_step calls (dt as there). */
+/* nsteps asynchronous esmm_rk_step calls (dt as there).  On a grid or batch
+ * with its own stream (not the legacy or per-thread default stream) the step
+ * is captured once as a CUDA graph, for nsteps >= 2, and replayed for every
+ * later step with the same dt argument, including single-step calls, until
+ * the parameters, order, EOS, launch shapes, stream or profiling mask
+ * change.  With profiling on, the graph holds event nodes around the
+ * profiled kinds; each replay's times are read (the call then waits for the
+ * previous replay) before the next replay records them again. */
 int esmm_advance(esmm_grid *g, int nsteps, double dt);
 
 /* Batches: nprob independent problems of (possibly) different sizes in one

@@ -96,16 +96,25 @@ struct esmm_grid {
     unsigned nblk[ND];
     size_t tiles_cap[ND];
     int doms_valid;
-    // CUDA graph of one step (keyed by the dt argument and a parameter epoch)
+    // CUDA graph of one step (keyed by the dt argument, a parameter epoch and
+    // the profiling mask it was captured with)
     cudaGraphExec_t graph;
     double graph_dt;
-    int graph_epoch, epoch;
+    int graph_epoch, epoch, graph_prof;
+    int capturing;                   // this library is capturing the step graph
     int tuned;
     // profiling: launches per kind, CUDA events around the kinds in prof_mask
     int prof_mask;
     long long launches[ESMM_NKINDS];
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *ev;
     std::vector<cudaEvent_t> *pool;
+    // event pairs recorded inside the step graph (re-recorded by every
+    // replay), whether a replay's are still to be read, and the times and
+    // counts read from replays so far
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *gev;
+    int gev_pending;
+    double gms[ESMM_NKINDS];
+    long long gtimed[ESMM_NKINDS];
     // adjoint: per-step checkpoints [cons 4N | J N | x 2N | xdot 2N] and steps
     std::vector<double *> *ck;
     std::vector<double> *ck_dt;
@@ -149,20 +158,30 @@ struct Prof {
     esmm_grid *g;
     int kind;
     cudaEvent_t a = nullptr;
+    bool in_graph = false;
     Prof(esmm_grid *g_, int kind_) : g(g_), kind(kind_)
     {
         g->launches[kind] += 1;
+        if (!(g->prof_mask & (1 << kind))) return;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (g->prof_mask & (1 << kind)) cudaStreamIsCapturing(g->st, &cs);
-        if ((g->prof_mask & (1 << kind)) && cs == cudaStreamCaptureStatusNone) {
+        cudaStreamIsCapturing(g->st, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {
             a = pool_get(g);
             cudaEventRecord(a, g->st);
+        } else if (g->capturing) {   // inside the library's own step graph: an event node
+            a = pool_get(g);
+            in_graph = true;
+            cudaEventRecordWithFlags(a, g->st, cudaEventRecordExternal);
         }
     }
     ~Prof()
     {
-        if (a) {
-            cudaEvent_t b = pool_get(g);
+        if (!a) return;
+        cudaEvent_t b = pool_get(g);
+        if (in_graph) {
+            cudaEventRecordWithFlags(b, g->st, cudaEventRecordExternal);
+            g->gev[kind].push_back({a, b});
+        } else {
             cudaEventRecord(b, g->st);
             g->ev[kind].push_back({a, b});
         }
@@ -635,8 +654,35 @@ int check_c2p(esmm_grid *g)
 
 void drop_graph(esmm_grid *g)
 {
-    if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->graph) {
+        // a replay may still be recording the graph's events
+        cudaStreamSynchronize(g->st);
+        cudaGraphExecDestroy(g->graph);
+    }
     g->graph = nullptr;
+    if (g->gev)
+        for (int k = 0; k < ESMM_NKINDS; ++k) {
+            for (auto &pr : g->gev[k]) { g->pool->push_back(pr.first); g->pool->push_back(pr.second); }
+            g->gev[k].clear();
+        }
+    g->gev_pending = 0;
+}
+
+// Add the device times of the last replay's graph events to the profile
+// (before the next replay records them again).
+int collect_graph_prof(esmm_grid *g)
+{
+    if (!g->gev_pending) return ESMM_OK;
+    for (int k = 0; k < ESMM_NKINDS; ++k)
+        for (auto &pr : g->gev[k]) {
+            float t = 0.0f;
+            CK(cudaEventSynchronize(pr.second));
+            CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+            g->gms[k] += t;
+            g->gtimed[k] += 1;
+        }
+    g->gev_pending = 0;
+    return ESMM_OK;
 }
 
 void free_all(esmm_grid *g)
@@ -668,6 +714,10 @@ void free_all(esmm_grid *g)
             for (auto &pr : g->ev[k]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
         delete[] g->ev;
         g->ev = nullptr;
+    }
+    if (g->gev) {   // drop_graph above returned them to the pool
+        delete[] g->gev;
+        g->gev = nullptr;
     }
     if (g->pool) {
         for (cudaEvent_t e : *g->pool) cudaEventDestroy(e);
@@ -754,10 +804,11 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
     }
     g->dim = 2;
     g->ev = new (std::nothrow) std::vector<std::pair<cudaEvent_t, cudaEvent_t>>[ESMM_NKINDS];
+    g->gev = new (std::nothrow) std::vector<std::pair<cudaEvent_t, cudaEvent_t>>[ESMM_NKINDS];
     g->pool = new (std::nothrow) std::vector<cudaEvent_t>;
     g->ck = new (std::nothrow) std::vector<double *>;
     g->ck_dt = new (std::nothrow) std::vector<double>;
-    if (!g->ev || !g->pool || !g->ck || !g->ck_dt || cudaGetDevice(&g->dev) != cudaSuccess) {
+    if (!g->ev || !g->gev || !g->pool || !g->ck || !g->ck_dt || cudaGetDevice(&g->dev) != cudaSuccess) {
         release(g);
         return ESMM_ERR_CUDA;
     }
@@ -1017,19 +1068,23 @@ int advance(esmm_grid *g, int nsteps, double dt)
     int rc;
     if ((rc = ensure_doms(g))) return rc;
     bool capturable = g->st != nullptr && g->st != cudaStreamLegacy && g->st != cudaStreamPerThread &&
-                      g->prof_mask == 0 && !(g->prm.move_mesh == 0 && !g->xdot_zero);
-    if (!capturable || nsteps < 2) {
+                      !(g->prm.move_mesh == 0 && !g->xdot_zero);
+    const bool have = g->graph && g->graph_dt == dt && g->graph_epoch == g->epoch && g->graph_prof == g->prof_mask;
+    // one step replays an existing graph; a new one is captured for two or more
+    if (!capturable || (nsteps < 2 && !have)) {
         for (int s = 0; s < nsteps; ++s)
             if ((rc = rk_step_async(g, dt))) return rc;
         return ESMM_OK;
     }
-    if (!g->graph || g->graph_dt != dt || g->graph_epoch != g->epoch) {
+    if (!have) {
         drop_graph(g);
         long long before[ESMM_NKINDS];
         memcpy(before, g->launches, sizeof before);
         cudaGraph_t gr = nullptr;
         CK(cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
+        g->capturing = 1;
         rc = rk_step_async(g, dt);
+        g->capturing = 0;
         cudaError_t e = cudaStreamEndCapture(g->st, &gr);
         memcpy(g->launches, before, sizeof before);
         if (rc) {
@@ -1045,11 +1100,17 @@ int advance(esmm_grid *g, int nsteps, double dt)
         }
         g->graph_dt = dt;
         g->graph_epoch = g->epoch;
+        g->graph_prof = g->prof_mask;
     }
     long long per[ESMM_NKINDS];
     step_launches(g, dt, per);
+    bool timed = false;
+    for (int k = 0; k < ESMM_NKINDS; ++k) timed = timed || !g->gev[k].empty();
     for (int s = 0; s < nsteps; ++s) {
+        // a profiled graph re-records its events: read the last replay's first
+        if ((rc = collect_graph_prof(g))) return rc;
         CK(cudaGraphLaunch(g->graph, g->st));
+        g->gev_pending = timed;
         for (int k = 0; k < ESMM_NKINDS; ++k) g->launches[k] += per[k];
     }
     return ESMM_OK;
@@ -2362,7 +2423,10 @@ int esmm_profile(esmm_grid *g, int mask)
         for (auto &pr : g->ev[k]) { g->pool->push_back(pr.first); g->pool->push_back(pr.second); }
         g->ev[k].clear();
         g->launches[k] = 0;
+        g->gms[k] = 0.0;
+        g->gtimed[k] = 0;
     }
+    g->gev_pending = 0;   // a finished replay's graph events are dropped with the counters
     g->prof_mask = mask;
     return ESMM_OK;
 }
@@ -2373,8 +2437,10 @@ int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[E
     if (!g) return ESMM_ERR_ARG;
     if (g->dim == 3) return esmm3_profile_read(g->g3, ms, launches, timed);
     CK(cudaStreamSynchronize(g->st));
+    int rc = collect_graph_prof(g);
+    if (rc) return rc;
     for (int k = 0; k < ESMM_NKINDS; ++k) {
-        double acc = 0.0;
+        double acc = g->gms[k];
         for (auto &pr : g->ev[k]) {
             float t = 0.0f;
             CK(cudaEventElapsedTime(&t, pr.first, pr.second));
@@ -2382,7 +2448,7 @@ int esmm_profile_read(esmm_grid *g, double ms[ESMM_NKINDS], long long launches[E
         }
         if (ms) ms[k] = acc;
         if (launches) launches[k] = g->launches[k];
-        if (timed) timed[k] = (long long)g->ev[k].size();
+        if (timed) timed[k] = (long long)g->ev[k].size() + g->gtimed[k];
     }
     return ESMM_OK;
 }
