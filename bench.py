@@ -5,8 +5,10 @@ Workload (default): the 2D RHD four-quadrant Riemann problem on [-1,1]^2 with
 400 x 400 nodes, outflow boundaries, Gamma = 5/3, seeded states (rho in
 [0.1,1], |v| <= 0.9, p in [0.01,1]), adaptive moving mesh (sigma = ln rho,
 alpha = 1200, 4 filter passes, 10 Jacobi sweeps), 4th-order EC flux (p = 2)
-with WENO5 dissipation, SSP-RK3 at CFL 0.4.  A step is one full rk_step: CFL
-reduction, mesh redistribution and three RK stages.
+with WENO5 dissipation, SSP-RK3 at CFL 0.4.  A step is one full time step
+(CFL reduction with the eq. cfl solve, mesh redistribution and three RK
+stages), timed as one esmm_advance call that replays the step's CUDA graph
+captured in the warm-up.
 
 Metric: cell-updates/s per RK stage = nodes * 3 * steps / device time.  Every
 timed step starts with the L2 cache flushed (a 256 MB write outside the timed
@@ -17,6 +19,8 @@ exchanges between the ranks.
 
 ``--impl reference`` times the FP64 CPU oracle (the paper's method restated
 plainly in C) on the host cores over a bounded sample of the same workload.
+
+``--workload batched`` times the 256-problem batch alone (mixed form).
 
 ``--workload rotor`` (2D RMHD rotor, 512^2, Gamma = 4/3, alpha = 800) and
 ``--workload blast3d`` (3D RMHD blast, 128^3, CFL 0.3) time the RMHD paths in
