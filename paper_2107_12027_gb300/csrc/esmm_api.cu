@@ -452,7 +452,9 @@ void step_radius(esmm_grid *g, double dt, bool moving)
     double *cflb = moving ? g->cflb : nullptr;
     if (g->phys == ESMM_RMHD)
         launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->prm.precision == ESMM_MIXED, cflb, g->st);
-    else k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->q, g->J, g->red, q32_of(g), cflb);
+    else
+        k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->gamma / (g->gamma - 1.0), g->q, g->J, g->red,
+                                          q32_of(g), cflb);
 }
 
 // the step into dt_dev (and the limiter, scaled where the displacement alone

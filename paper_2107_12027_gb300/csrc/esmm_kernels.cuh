@@ -277,7 +277,8 @@ __device__ __forceinline__ void cfl_f32(const ProbArg &pa, float gam, const floa
 // static mesh), reduced to a per-problem maximum per direction; with cflb
 // (the moving-mesh step) also the speed bounds L_k lambda_-/J and
 // L_k lambda_+/J of every node into its rows 2 + k and 4 + k
-__global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, const double *__restrict__ J,
+// gg = Gamma/(Gamma - 1) comes with the launch
+__global__ void k_cfl(ProbArg pa, double gam, double gg, const double *__restrict__ q, const double *__restrict__ J,
                       unsigned long long *red, const float *__restrict__ q32, double *__restrict__ cflb)
 {
     if (q32) {   // the mixed form: the same speeds in FP32 from the FP32 node copies
@@ -300,15 +301,15 @@ __global__ void k_cfl(ProbArg pa, double gam, const double *__restrict__ q, cons
         double iW = __drcp_rn(W);
         double vx = q[Q_UX * g.P + c] * iW, vy = q[Q_UY * g.P + c] * iW;
         double v2 = vx * vx + vy * vy;
-        double rh = rho + p * (gam / (gam - 1.0));
+        double rh = rho + p * gg;
         double c2 = gam * p * __drcp_rn(rh), cs = sqrt(c2);
         double iJ = __drcp_rn(J[id]);
+        const double iden = __drcp_rn(1.0 - v2 * c2);   // the same for both directions
         for (int k = 0; k < 2; ++k) {
             double mx = q[(Q_M00 + 2 * k) * g.P + c], my = q[(Q_M01 + 2 * k) * g.P + c];
-            double Lk = sqrt(mx * mx + my * my);
-            double vn = (mx * vx + my * vy) * __drcp_rn(Lk);
+            const double n2 = mx * mx + my * my, iL = rsqrt(n2), Lk = n2 * iL;
+            double vn = (mx * vx + my * vy) * iL;
             double disc = sqrt((1.0 - v2) * (1.0 - v2 * c2 - vn * vn * (1.0 - c2)));
-            double iden = __drcp_rn(1.0 - v2 * c2);
             double lm = (vn * (1.0 - c2) - cs * disc) * iden, lp = (vn * (1.0 - c2) + cs * disc) * iden;
             r[k] = owned_row(g, j) ? Lk * fmax(fabs(lm), fabs(lp)) * iJ : 0.0;
             if (cflb) {
