@@ -211,6 +211,32 @@ def test_rhs_parity_full_size_riemann_400(p, w):
     assert _rel(got[1], ref[1]) < TOL
 
 
+def test_steps_full_size_riemann_400_as_benchmarked():
+    # the benchmark's 400^2 workload in the configuration it times: its own
+    # stream, the default (fused) sweep kernels, three steps through
+    # esmm_advance (two from a freshly captured graph, then a single-step
+    # replay), against three oracle steps
+    import torch
+    import bench
+    n = 400
+    x, prim = bench.workload(n)
+    cfg = _cfg(n, n, (1, 1), (-1, -1), (1, 1), 2, 5, alpha=1200.0, monitor=oracle.MONITOR_LNRHO)
+    cons, J = oracle.init_state(cfg, prim, x)
+    xs = x
+    for _ in range(3):
+        cons, J, xs, _ = oracle.rk_step(cfg, cons, J, xs)
+    st = torch.cuda.Stream()
+    with esmm.Grid((n, n), (-1, -1), (1, 1), bc=(1, 1), p=2, w=5, stream=st.cuda_stream,
+                   **bench.grid_params("fp64")) as g:
+        g.state_set(prim, x)
+        g.advance(2)
+        g.advance(1)
+        torch.cuda.synchronize()
+        assert _rel(g.state_get(esmm.GET_CONS), cons) < TOL
+        assert _rel(g.state_get(esmm.GET_J), J) < TOL
+        assert _rel(g.state_get(esmm.GET_X), xs) < TOL
+
+
 def test_sine_wave_64_to_t01_against_oracle_and_exact():
     # 2D RHD smooth sine wave on periodic [0,1]^2, 64x64, Gamma = 5/3,
     # rho = 1 + 0.2 sin(2 pi (x + y)), v = (0.2, 0.2), p = 1, p = 2 + WENO5,
