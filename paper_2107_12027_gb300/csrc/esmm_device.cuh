@@ -537,34 +537,15 @@ __device__ __forceinline__ void ec_pair(const NodeV<R> &l, const NodeV<R> &r, R 
     out[3] = mt * UE + Es;
 }
 
-// Jiang-Shu WENO edge value on s[0..4] (far upwind .. far downwind), written
-// with a single division: sum_k (d_k/(eps+b_k)^2) q_k / sum_k d_k/(eps+b_k)^2
-// multiplied through by the three squared denominators.
-template <typename R>
-__device__ __forceinline__ R weno5(R s0, R s1, R s2, R s3, R s4, R eps)
-{
-    const R c13_12 = (R)(13.0 / 12.0), c1_4 = (R)0.25, c1_6 = (R)(1.0 / 6.0);
-    R q0 = ((R)2 * s0 - (R)7 * s1 + (R)11 * s2) * c1_6;
-    R q1 = (-s1 + (R)5 * s2 + (R)2 * s3) * c1_6;
-    R q2 = ((R)2 * s2 + (R)5 * s3 - s4) * c1_6;
-    R t0 = s0 - (R)2 * s1 + s2, r0 = s0 - (R)4 * s1 + (R)3 * s2;
-    R t1 = s1 - (R)2 * s2 + s3, r1 = s1 - s3;
-    R t2 = s2 - (R)2 * s3 + s4, r2 = (R)3 * s2 - (R)4 * s3 + s4;
-    R e0 = eps + c13_12 * t0 * t0 + c1_4 * r0 * r0;
-    R e1 = eps + c13_12 * t1 * t1 + c1_4 * r1 * r1;
-    R e2 = eps + c13_12 * t2 * t2 + c1_4 * r2 * r2;
-    e0 *= e0; e1 *= e1; e2 *= e2;
-    R a0 = (R)0.1 * e1 * e2, a1 = (R)0.6 * e0 * e2, a2 = (R)0.3 * e0 * e1;
-    return (a0 * q0 + a1 * q1 + a2 * q2) * rcp<R>(a0 + a1 + a2);
-}
-
-// The two WENO5 edge values of one interface from its six stencil values
-// V0..V5 (V2, V3 the interface's nodes): vm as weno5(V0..V4) (upwind left)
-// and vp as weno5(V5..V1) (upwind right), each with one division.  The
-// candidate values and second differences of the two middle candidate
-// stencils, {V1, V2, V3} and {V2, V3, V4}, serve both reconstructions
-// (left's 2nd and 3rd candidates are right's 3rd and 2nd) and are formed
-// once.
+// The two Jiang-Shu WENO5 edge values of one interface from its six stencil
+// values V0..V5 (V2, V3 the interface's nodes): vm from V0..V4 (upwind
+// left) and vp from V5..V1 (upwind right).  Each is
+//   sum_k (d_k/(eps+b_k)^2) q_k / sum_k d_k/(eps+b_k)^2, d = (0.1, 0.6, 0.3),
+// written with a single division by multiplying through by the three
+// squared denominators.  The candidate values and second differences of the
+// two middle candidate stencils, {V1, V2, V3} and {V2, V3, V4}, serve both
+// reconstructions (left's 2nd and 3rd candidates are right's 3rd and 2nd)
+// and are formed once.
 template <typename R>
 __device__ __forceinline__ void weno5_lr(R V0, R V1, R V2, R V3, R V4, R V5, R eps, R &vm, R &vp)
 {
@@ -597,21 +578,11 @@ __device__ __forceinline__ void weno5_lr(R V0, R V1, R V2, R V3, R V4, R V5, R e
     }
 }
 
-template <typename R>
-__device__ __forceinline__ R weno3(R s0, R s1, R s2, R eps)
-{
-    R q0 = (-s0 + (R)3 * s1) * (R)0.5;
-    R q1 = (s1 + s2) * (R)0.5;
-    R e0 = eps + (s1 - s0) * (s1 - s0);
-    R e1 = eps + (s2 - s1) * (s2 - s1);
-    e0 *= e0; e1 *= e1;
-    R a0 = (R)(1.0 / 3.0) * e1, a1 = (R)(2.0 / 3.0) * e0;
-    return (a0 * q0 + a1 * q1) * rcp<R>(a0 + a1);
-}
-
 // The two WENO3 edge values of one interface from V0..V3 (V1, V2 its
-// nodes): vm as weno3(V0, V1, V2), vp as weno3(V3, V2, V1); the candidate
-// on {V1, V2} and its smoothness term serve both.
+// nodes): vm from V0, V1, V2 and vp from V3, V2, V1, each
+// (a0 q0 + a1 q1)/(a0 + a1) with a_k = d_k/(eps+b_k)^2, d = (1/3, 2/3),
+// multiplied through; the candidate on {V1, V2} and its smoothness term
+// serve both.
 template <typename R>
 __device__ __forceinline__ void weno3_lr(R V0, R V1, R V2, R V3, R eps, R &vm, R &vp)
 {
