@@ -67,6 +67,7 @@ struct esmm_grid {
     double *q;                       // [NQ][Ptot] (RMHD: [NQ_MHD][Ptot])
     double *cw;                      // [4][Ntot] Jacobi weights of the mesh iteration
     double *rs;                      // [2][Ntot] the iteration's residual on the displacement
+    double *wr;                      // [6][Ntot] floats: weights and residual of the blocked sweeps
     float *q32;                      // [NQ32][Ptot] FP32 copies (RHD mixed form)
     double *inflow_dev;              // [8] primitive inflow state (ESMM_INFLOW ends)
     int needs_inflow, has_inflow;
@@ -489,7 +490,8 @@ void red_init(esmm_grid *g)
 constexpr int MT_SB32 = 10;
 
 // The Jacobi sweeps (k_mesh_sweeps) and the limiter, in working type T (the
-// weights are in g->cw); the displacement is left at g->mesh_disp.
+// weights are in g->cw; the blocked sweeps read them, with the residual, in
+// T from g->wr); the displacement is left at g->mesh_disp.
 template <typename T, int SB>
 int mesh_sweeps_tau(esmm_grid *g, const LaunchDom &L)
 {
@@ -514,12 +516,17 @@ int mesh_sweeps_tau(esmm_grid *g, const LaunchDom &L)
         Dd = reinterpret_cast<const T *>(in);
     } else {
         LaunchDom Lt = dom(g, D_MTILE);
+        T *wr = reinterpret_cast<T *>(g->wr);
+        {
+            Prof pr_(g, ESMM_KIND_MESH);
+            k_mesh_wr<T><<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->x, g->cw, wr);
+        }
         const T *in = nullptr;
         int b = 0;
         for (int done = 0; done < g->prm.mu; done += SB) {
             Prof pr_(g, ESMM_KIND_MESH);
             k_mesh_sweeps<T, SB><<<Lt.nblk, MT_THREADS, mesh_sweeps_smem<T, SB>(), g->st>>>(
-                Lt.pa, g->x, g->cw, in, bufs[b], std::min(SB, g->prm.mu - done));
+                Lt.pa, wr, in, bufs[b], std::min(SB, g->prm.mu - done));
             in = bufs[b];
             b ^= 1;
         }
@@ -691,7 +698,7 @@ void free_all(esmm_grid *g)
 {
     double **bufs[] = {&g->cons, &g->J, &g->x, &g->xdot, &g->c1, &g->J1, &g->x1, &g->c2, &g->J2, &g->x2,
                        &g->q, &g->pg[0], &g->pg[1], &g->pg[2], &g->in_cons, &g->in_J, &g->in_x, &g->in_xdot,
-                       &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->rs, &g->X, &g->Xn,
+                       &g->out_dc, &g->out_dJ, &g->grad, &g->om, &g->om2, &g->cw, &g->rs, &g->wr, &g->X, &g->Xn,
                        &g->dt_dev,
                        &g->t_dev, &g->partials, &g->tot_dev, &g->inflow_dev, &g->cflb, &g->npart, &g->vs_dev};
     for (double **b : bufs)
@@ -880,7 +887,7 @@ int create(esmm_grid **out, int nprob, const int *n, const double *lo, const dou
         {&g->cons, nv * N}, {&g->J, N}, {&g->x, 2 * N}, {&g->xdot, 2 * N}, {&g->c1, nv * N}, {&g->J1, N},
         {&g->x1, 2 * N}, {&g->c2, nv * N}, {&g->J2, N}, {&g->x2, 2 * N}, {&g->q, nq * P},
         {&g->pg[0], N}, {&g->pg[1], N}, {&g->pg[2], N}, {&g->out_dc, nv * N}, {&g->out_dJ, N},
-        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->rs, 2 * N}, {&g->X, 2 * N},
+        {&g->grad, N}, {&g->om, N}, {&g->om2, N}, {&g->cw, 4 * N}, {&g->rs, 2 * N}, {&g->wr, 3 * N}, {&g->X, 2 * N},
         {&g->Xn, 2 * N},
         {&g->dt_dev, (size_t)nprob}, {&g->t_dev, (size_t)nprob}, {&g->partials, 3 * nb_max}, {&g->inflow_dev, 8},
         {&g->cflb, 6 * N}, {&g->npart, 4 * nb_max},

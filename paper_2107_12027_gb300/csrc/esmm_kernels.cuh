@@ -523,9 +523,10 @@ __device__ __noinline__ double mesh_edge(const Geom &g, const double *__restrict
 // in the mixed form).  A block owns a TX x TY tile and iterates nsw <= SB
 // sweeps on the tile plus an SB-wide halo in shared memory (the valid region
 // shrinks by one node per sweep), then writes the tile: one launch for SB
-// sweeps.  Halo nodes across a periodic end are the periodic images in
-// unwrapped coordinates; nodes across an outflow or inflow end are read only
-// by fixed boundary nodes and are held at 0.
+// sweeps.  The weights and r come per node from k_mesh_wr, in T; halo nodes
+// across a periodic end take their source node's (D, the weights and r do
+// not depend on the period's shift); nodes across an outflow or inflow end
+// are read only by fixed boundary nodes and are held at 0.
 constexpr int MT_TX = 32, MT_TY = 16, MT_THREADS = 256;
 
 template <typename T, int SB>
@@ -535,8 +536,7 @@ constexpr size_t mesh_sweeps_smem()
 }
 
 template <typename T, int SB>
-__global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const double *__restrict__ x,
-                                                            const double *__restrict__ cw,
+__global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const T *__restrict__ wr,
                                                             const T *__restrict__ Din, T *__restrict__ Dout,
                                                             int nsw)
 {
@@ -550,8 +550,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const do
     long long lb;
     locate(pa, D, lb);
     const Geom &g = D.g;
-    x += 2 * D.on;
-    cw += 4 * D.on;
+    wr += 6 * D.on;
     if (Din) Din += 2 * D.on;
     Dout += 2 * D.on;
     const int ntx = (g.nx + MT_TX - 1) / MT_TX;
@@ -569,25 +568,10 @@ __global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const do
         const long long id = (long long)sj * g.nx + si;
         const bool fixed = (g.bc0 != 0 && (si == 0 || si == g.nx - 1)) || (g.bc1 != 0 && (sj == 0 || sj == g.ny - 1));
         sF[r] = fixed;
-        const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
-        sW[r] = from_f64<T>(ce);
-        sW[RN + r] = from_f64<T>(cwe);
-        sW[2 * RN + r] = from_f64<T>(cn);
-        sW[3 * RN + r] = from_f64<T>(cs);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) sW[a * RN + r] = wr[a * g.N + id];
         for (int c = 0; c < 2; ++c) {
-            double res = 0.0;
-            if (!fixed) {
-                const bool inner = gi > 0 && gi < g.nx - 1 && gj > 0 && gj < g.ny - 1;
-                const double *a = x + c * g.N;
-                const long long o = (long long)gj * g.nx + gi;
-                const double xi = inner ? a[o] : mesh_edge(g, x, gi, gj, c);
-                const double xe = inner ? a[o + 1] : mesh_edge(g, x, gi + 1, gj, c);
-                const double xw = inner ? a[o - 1] : mesh_edge(g, x, gi - 1, gj, c);
-                const double xn = inner ? a[o + g.nx] : mesh_edge(g, x, gi, gj + 1, c);
-                const double xs = inner ? a[o - g.nx] : mesh_edge(g, x, gi, gj - 1, c);
-                res = ce * xe + cwe * xw + cn * xn + cs * xs - xi;
-            }
-            sR[c * RN + r] = from_f64<T>(res);
+            sR[c * RN + r] = wr[(4 + c) * g.N + id];   // 0 at a fixed node
             sD[c * RN + r] = Din ? Din[c * g.N + id] : (T)0;
         }
     }
@@ -625,6 +609,46 @@ __global__ void __launch_bounds__(MT_THREADS) k_mesh_sweeps(ProbArg pa, const do
 // once per redistribution, then D_i <- sum_k c_k D_k + r_i.  D needs no ghost
 // arithmetic: it is shift-free across a periodic end and 0 at held nodes,
 // and nodes next to an outflow end read only the held boundary nodes.
+// The blocked sweeps' inputs in working type T, once per node: wr[0..3] the
+// Jacobi weights c_E, c_W, c_N, c_S and wr[4..5] the residual of k_mesh_resid
+// (FP64 arithmetic, then rounded), so that the sweep kernel's halo nodes,
+// each staged by several tiles, only load them.  A ghost beyond a periodic
+// end takes its source node's values.
+template <typename T>
+__global__ void k_mesh_wr(ProbArg pa, const double *__restrict__ x, const double *__restrict__ cw,
+                          T *__restrict__ wr)
+{
+    ProbDesc D;
+    long long lb;
+    locate(pa, D, lb);
+    const Geom &g = D.g;
+    long long id = lb * blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    x += 2 * D.on;
+    cw += 4 * D.on;
+    wr += 6 * D.on;
+    int i = (int)(id % g.nx), j = (int)(id / g.nx);
+    bool fixed = (g.bc0 != 0 && (i == 0 || i == g.nx - 1)) || (g.bc1 != 0 && (j == 0 || j == g.ny - 1));
+    const double ce = cw[id], cwe = cw[g.N + id], cn = cw[2 * g.N + id], cs = cw[3 * g.N + id];
+    wr[id] = from_f64<T>(ce);
+    wr[g.N + id] = from_f64<T>(cwe);
+    wr[2 * g.N + id] = from_f64<T>(cn);
+    wr[3 * g.N + id] = from_f64<T>(cs);
+    const bool inner = i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1;
+    for (int c = 0; c < 2; ++c) {
+        double r = 0.0;
+        if (!fixed) {
+            const double *a = x + c * g.N;
+            const double xe = inner ? a[id + 1] : mesh_edge(g, x, i + 1, j, c);
+            const double xw = inner ? a[id - 1] : mesh_edge(g, x, i - 1, j, c);
+            const double xn = inner ? a[id + g.nx] : mesh_edge(g, x, i, j + 1, c);
+            const double xs = inner ? a[id - g.nx] : mesh_edge(g, x, i, j - 1, c);
+            r = ce * xe + cwe * xw + cn * xn + cs * xs - a[id];
+        }
+        wr[(4 + c) * g.N + id] = from_f64<T>(r);
+    }
+}
+
 __global__ void k_mesh_resid(ProbArg pa, const double *__restrict__ x, const double *__restrict__ cw,
                              double *__restrict__ rs)
 {
