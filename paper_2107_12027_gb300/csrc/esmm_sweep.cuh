@@ -22,6 +22,9 @@
 // addresses per row) and each warp then walks its column.  Per-warp arrays
 // are laid out [field][node] with a stride of 41 nodes (conflict-free for
 // both the row reads of the lanes and the column-interleaved staging writes).
+// The staging also forms each node's entropy variables once (entropy_vars4,
+// the rounded operations the two-kernel path applies per interface), which
+// the dissipation then reads for every stencil that holds the node.
 #pragma once
 
 #include <type_traits>
