@@ -451,8 +451,11 @@ void step_radius(esmm_grid *g, double dt, bool moving)
     Prof pr_(g, ESMM_KIND_OTHER);
     LaunchDom L = dom(g, D_NODE);
     double *cflb = moving ? g->cflb : nullptr;
-    if (g->phys == ESMM_RMHD)
-        launch_cfl_mhd(L, g->gamma, g->q, g->J, g->red, g->prm.precision == ESMM_MIXED, cflb, g->st);
+    if (g->phys == ESMM_RMHD)   // at most 256 threads per block, whatever the node kind's tuned size: the
+                                // eigen-system holds up to 255 registers per thread (RMHD grids are single
+                                // problems)
+        launch_cfl_mhd(dom_one(g, 0, D_NODE, std::min(L.bs, 256)), g->gamma, g->q, g->J, g->red,
+                       g->prm.precision == ESMM_MIXED, cflb, g->st);
     else
         k_cfl<<<L.nblk, L.bs, 0, g->st>>>(L.pa, g->gamma, g->gamma / (g->gamma - 1.0), g->q, g->J, g->red,
                                           q32_of(g), cflb);

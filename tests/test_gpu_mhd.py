@@ -177,6 +177,28 @@ def test_rk_step_parity_rotor():
             assert _rel(g.state_get(esmm.GET_X), x) < 1e-12
 
 
+@pytest.mark.parametrize("precision", [esmm.FP64, esmm.MIXED])
+def test_tuned_rmhd_grid_steps_as_untuned(precision):
+    # the tuner picks block sizes per kernel kind (node kinds up to 512
+    # threads); every RMHD launch, the CFL pass with its eigen-system
+    # included, still runs, and the steps are unchanged bit for bit (each
+    # node and interface is one thread's work, the reductions are exact)
+    n = 48
+    x, prim = wl.rotor_config(n)
+    res = []
+    for tuned in (False, True):
+        with esmm.Grid((n, n), (-0.5, -0.5), (0.5, 0.5), bc=(1, 1), p=2, w=5, gamma=G43, phys=esmm.RMHD,
+                       alpha=800.0, precision=precision) as g:
+            g.state_set(prim, x)
+            if tuned:
+                assert len(g.tune()) == esmm.TUNE_SLOTS
+            dts = [g.rk_step() for _ in range(3)]
+            res.append((g.state_get(esmm.GET_CONS), g.state_get(esmm.GET_X), dts))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
+
+
 def test_rotor_512_full_size_rhs():
     # the 512^2 rotor (Gamma = 4/3) at full size, in the launch configuration
     # of the step, against the oracle's right-hand side
