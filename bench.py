@@ -72,18 +72,18 @@ TRAFFIC_IFACE_F64 = None
 FLOPS_PER_IFACE_F32 = None
 TRAFFIC_IFACE_F32 = None
 # The same for the RMHD interface kernels at p = 2, WENO5: the FP64 2D kernel
-# on the 512^2 rotor (10,898 FP64 flops per interface; 1.021 GB of DRAM
+# on the 512^2 rotor (10,898 FP64 flops per interface; 1.019 GB of DRAM
 # traffic per launch, the eigen-system's per-thread stack), its FP32 instance
-# (10,688 FP32 flops per interface besides 98 FP64 ones; 0.480 GB), and the 3D
-# kernel (16,265 FP64 flops per interface; 1.213 GB at 64^3, scaled by the
+# (10,712 FP32 flops per interface besides 103 FP64 ones; 0.467 GB), and the 3D
+# kernel (16,265 FP64 flops per interface; 1.212 GB at 64^3, scaled by the
 # 7.94x interfaces of a 128^3 launch -- the stack traffic grows with the
 # threads).
 FLOPS_PER_IFACE_MHD2 = 10898
-TRAFFIC_IFACE_MHD2 = 1.021e9
-FLOPS_PER_IFACE_MHD2_F32 = 10688
-TRAFFIC_IFACE_MHD2_F32 = 0.480e9
+TRAFFIC_IFACE_MHD2 = 1.019e9
+FLOPS_PER_IFACE_MHD2_F32 = 10712
+TRAFFIC_IFACE_MHD2_F32 = 0.467e9
 FLOPS_PER_IFACE_MHD3 = 16265
-TRAFFIC_IFACE_MHD3 = 9.63e9
+TRAFFIC_IFACE_MHD3 = 9.62e9
 # The fused sweep kernel (pair and interface fluxes in one launch) on the
 # same workload, from one capture of each form: executed flops per interface
 # (its pair fluxes included: 32 anchors per 31 interfaces) and DRAM bytes
@@ -102,7 +102,7 @@ COUNTER_SOURCES = {
     "mhd2": ("esmm_mhd.cuh", "esmm_device.cuh", "esmm_conv.h"),
     "mhd3": ("esmm_3d.cuh", "esmm_3d_iface.cu", "esmm_mhd.cuh", "esmm_device.cuh", "esmm_conv.h"),
 }
-COUNTER_DIGEST = {"sweep": "5c6fe845469dcca2", "mhd2": "a1a92570348fbd1c", "mhd3": "dc646ae5a42e4d6f"}
+COUNTER_DIGEST = {"sweep": "5c6fe845469dcca2", "mhd2": "154efcb90ff39846", "mhd3": "dd8daf5262c5c5b3"}
 
 
 def source_digest(kind, csrc=None):

@@ -172,6 +172,20 @@ __device__ __forceinline__ R dot8(const R *a, const R *b)
     return s;
 }
 
+// f(0) ... f(n - 1), in a rolled loop in the FP32 instances, whose kernels are
+// limited by instruction fetch (the unrolled copies of these loop bodies do
+// not fit the instruction cache); as the compiler chooses otherwise.
+template <typename R, typename F>
+__device__ __forceinline__ void each_index(int n, F &&f)
+{
+    if constexpr (std::is_same<R, float>::value) {
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) f(i);
+    } else {
+        for (int i = 0; i < n; ++i) f(i);
+    }
+}
+
 // Phi'(V) = (0, B/W^2 + v (v.B), v.B, v) (eq. Phi)
 template <typename R>
 __device__ __forceinline__ void mhd_phiprime(const R w[8], R P[8])
@@ -273,7 +287,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
     const R in_rho = rcp<R>(n_rho), in_div = rcp<R>(n_div);
     const int comp[6] = {1, 2, 3, 4, 6, 7};
     R Uy[6][8], Vy[6][8], Fy[6][8];
-    for (int a = 0; a < 6; ++a) {
+    each_index<R>(6, [&](int a) {
         R e[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
         e[comp[a]] = (R)1;
         R Ue[8], Ve[8], Fe[8];
@@ -296,15 +310,16 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
                 Fy[a][r] *= sa;
             }
         }
-    }
+    });
     R Gm[6][6], C[6][6];
-    for (int a = 0; a < 6; ++a)
-        for (int b = 0; b <= a; ++b) {
+    each_index<R>(6, [&](int a) {
+        each_index<R>(a + 1, [&](int b) {
             R g = (R)0.5 * (dot8(Uy[a], Vy[b]) + dot8(Uy[b], Vy[a]));
             R k = (R)0.5 * (dot8(Vy[a], Fy[b]) + dot8(Vy[b], Fy[a]));
             Gm[a][b] = Gm[b][a] = g;
             C[a][b] = C[b][a] = k;
-        }
+        });
+    });
     // Cholesky G = L L^T (lower triangle of Gm), with the reciprocals of
     // its diagonal (idg) serving every division of the factor and the solves
     R idg[6];
@@ -441,7 +456,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
         Rv[r][0] = Ur[r] * srho;
         Rv[r][1] = Ud[r] * sdiv;
     }
-    for (int m = 0; m < 6; ++m) {
+    each_index<R>(6, [&](int m) {
         R s[6];
         for (int i = 5; i >= 0; --i) {
             R acc = E6[i][m];
@@ -453,7 +468,7 @@ static __device__ __noinline__ void eigen_mhd(double gam, const R w[8], R lam[8]
             for (int a = 0; a < 6; ++a) acc += s[a] * Uy[a][r];
             Rv[r][2 + m] = acc;
         }
-    }
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -719,11 +734,12 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
 
     R F[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
     double Ft = 0.0, Bt = 0.0;
-#pragma unroll
+    // (rolled in FP32, for instruction fetch, as in each_index)
+#pragma unroll (sizeof(R) == 4 ? 1 : P)
     for (int n = 1; n <= P; ++n) {
         R Fs[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
         double Fts = 0.0, Bts = 0.0;
-#pragma unroll
+#pragma unroll (sizeof(R) == 4 ? 1 : P)
         for (int s = 0; s < n; ++s) {
             const long long cl = c0 - s * sd, cr = cl + n * sd;
             NodeMT<R> l = load_node_m<R>(q, g.P, cl), r = load_node_m<R>(q, g.P, cr);
@@ -810,7 +826,7 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
         }
         R z[8];
         const R eps = (R)ph.eps, sign_tol = (R)ph.sign_tol;
-        for (int m = 0; m < 8; ++m) {
+        each_index<R>(8, [&](int m) {
             R vminus, vplus;
             if (WW == 5)
                 weno5_lr<R>(Vt[0][m], Vt[1][m], Vt[2][m], Vt[3][m], Vt[4][m], Vt[5][m], eps, vminus, vplus);
@@ -820,7 +836,7 @@ __global__ void __launch_bounds__(128) k_iface_mhd(ProbArg pa, Phys ph, const do
             R jump = Vt[OFF + 1][m] - Vt[OFF][m];
             int sj = le(fab<R>(jump), sign_tol * scale[m]) ? 0 : sgn_d(jump);
             z[m] = (sgn_d(jw) == sj) ? jw : (R)0;
-        }
+        });
         R d[8];
         for (int a = 0; a < 8; ++a) {
             R acc = (R)0;
